@@ -1,0 +1,407 @@
+"""Plain, slow FP64 CPU oracle of the polynomial-filtered subspace extraction.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or
+execute this module: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.  It shares
+no code with the CUDA path (no kernels, headers, helpers or constants); its
+only common ground with the CUDA path is the seeded input module
+``pf_synthetic``, which holds none of the method's arithmetic.
+
+Everything here is float64 numpy.  Library primitives (a matmul, a sparse
+matmul, a QR factorisation, a symmetric eigendecomposition) serve as single
+steps; there is no blocking, fusion or reordering beyond what the paper's
+definitions state, so each function can be read against the paper by eye.
+
+Citations are to the paper "Low-rank Matrix Optimization Using
+Polynomial-filtered Subspace Extraction":
+
+* Chebyshev polynomial T_d ............................ Sec. 2.1, Eq. (cheb)
+* interval map rho(t) = T_d((t-(a+b)/2)/((b-a)/2)) ..... Sec. 2.1, Eq. (cheb-linear-map)
+* three-term recurrence (mapped variable) .............. Sec. 4 (commented recurrence)
+* filtered subspace update U+ = orth(rho(A) U) .......... Sec. 2.1, Eq. (subspace-update)
+* projection P_S and Rayleigh-Ritz H = V^T X V .......... Sec. 2.2, Eq. (RR)
+* PFPG ................................................. Sec. 2.2, Eqs. (pfpg1)-(pfpg2)
+* DRS / PFAM for the standard SDP ...................... Sec. 2.3, Eqs. (PFAM1)-(PFAM2)
+* choice of [a, b] ..................................... Sec. 4.1
+* principal angles ..................................... Sec. 3.1, Definition of Theta
+* Chebyshev growth lemma ............................... Sec. 3.1, Lemma (cheb-est)
+
+Readings taken where the paper is silent or garbled (each also listed in the
+design notes):
+
+R1  The commented recurrence in Sec. 4 prints the mapped variable as
+    c0 + c1*t with c0 = 2/(b-a), c1 = (a+b)/(a-b); the coefficients are
+    swapped.  The oracle uses the map of Eq. (cheb-linear-map),
+    x = (t - c)/e with c = (a+b)/2, e = (b-a)/2.
+R2  The prox of G in Sec. 2.3 prints "+ tC"; from the prox definition applied
+    to G = 1{AX=b} + <C,X> the sign is minus:
+    prox_tG(Y) = (Y - tC) - A*(AA*)^{-1}(A(Y - tC) - b).
+R3  orth is the thin QR factor Q with positive diagonal R (unique for a full
+    rank block), as "a single QR decomposition" (Sec. 2.1).
+R4  a = a rigorous lower bound of lambda_min: the Gershgorin bound of the
+    sparse/diagonal part of the iteration matrix; the remaining part is PSD
+    (X_k for completion, X~ for max-cut), so by Weyl's inequality the bound
+    holds for the whole matrix.  b = (1-eta) theta_min_prev + eta a with
+    eta = 0.1 (the "r largest" rule of Sec. 4.1 with the previous smallest
+    Ritz value as the estimate); on the first iteration b = eta a when a < 0
+    (the "all positive" rule), else b = a + (1-eta)(ub - a) with ub the
+    Gershgorin upper bound.  If b - a < 1e-3 max(1,|a|), b is moved up to
+    a + 1e-3 max(1,|a|) so the map stays finite.
+R5  Ritz values are sorted descending (the paper's eigenvalue order, Sec. 1
+    Notation); Ritz vectors are compared per cluster of equal values, so the
+    sign and in-cluster basis carry no meaning.
+R6  Max-cut: Z^0 = 0 gives X~ = 0 for any U, so the iteration starts at
+    Z^1 = I - t offdiag(C) (the exact DRS image of Z^0 = 0).  The step is
+    fixed at t = 10 sqrt(n)/||C||_F: sqrt(n)/||C||_F balances ||b|| = sqrt(n)
+    against ||C||_F, and the factor 10 keeps the iterates' positive rank low
+    (it converged fastest of 0.1..100 times that balance on seeded graphs).
+R7  Max-cut KKT: y = -lambda/t, S = (X~ - Z_k)/t;
+    pinf = ||diag X~ - 1||_2/(1+sqrt n);
+    dinf = ||C - Diag(y) - S||_F/(1+||C||_F) = ||Z_k - Z_{k+1}||_F/(t(1+||C||_F));
+    gap  = |<C,X~> - 1^T y|/(1+|<C,X~>|+|1^T y|); kkt = max of the three.
+R8  PSD completion, min_{X psd} 1/2||P_Omega(X-M)||^2 + mu tr X, PG step
+    X+ = P_+(X - t P_Omega(X - M) - t mu I) (the symmetric analogue of the
+    NNLS/SVT tests of Sec. 5.2); X^0 = 0; each iteration filters the current
+    iteration matrix B_k = X_k - tS_k - t mu I before its Rayleigh-Ritz step
+    (Eq. (pfpg2) shifted by one index, so U^0 is filtered before first use);
+    kkt = ||X_k - X_{k+1}||_F/(1 + ||X_k||_F + ||t S_k||_F);
+    objective f_k = 1/2||S_k||^2 + mu sum(max(theta,0)) at X_k.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, Optional
+
+import numpy as np
+import scipy.sparse as sp
+
+ETA = 0.1
+
+# ---------------------------------------------------------------------------
+# Chebyshev polynomials (Sec. 2.1)
+# ---------------------------------------------------------------------------
+
+
+def chebyshev_T(d: int, t):
+    """T_d(t) from the closed form, Eq. (cheb):
+    cos(d arccos t) on |t| <= 1, 1/2((t - sqrt(t^2-1))^d + (t + sqrt(t^2-1))^d) outside."""
+    t = np.asarray(t, dtype=np.float64)
+    out = np.empty_like(t)
+    inside = np.abs(t) <= 1.0
+    out[inside] = np.cos(d * np.arccos(t[inside]))
+    to = t[~inside]
+    s = np.sqrt(to * to - 1.0)
+    out[~inside] = 0.5 * ((to - s) ** d + (to + s) ** d)
+    return out
+
+
+def interval_map(a: float, b: float):
+    """Centre c and half-width e of [a, b]; x = (t - c)/e maps [a, b] to [-1, 1],
+    Eq. (cheb-linear-map)."""
+    return 0.5 * (a + b), 0.5 * (b - a)
+
+
+def cheb_filter(apply_B: Callable[[np.ndarray], np.ndarray], U: np.ndarray,
+                a: float, b: float, d: int) -> np.ndarray:
+    """rho(B) U with rho(t) = T_d((t-c)/e), Eqs. (cheb-linear-map) and (cheb),
+    evaluated by the Chebyshev three-term recurrence in the mapped variable
+    x = (B - cI)/e (reading R1):
+        Y_0 = U,  Y_1 = x Y_0,  Y_{j+1} = 2 x Y_j - Y_{j-1}."""
+    c, e = interval_map(a, b)
+    Y_prev = np.array(U, dtype=np.float64)
+    if d == 0:
+        return Y_prev
+    Y = (apply_B(Y_prev) - c * Y_prev) / e
+    for _ in range(1, d):
+        Y_next = 2.0 * (apply_B(Y) - c * Y) / e - Y_prev
+        Y_prev, Y = Y, Y_next
+    return Y
+
+
+# ---------------------------------------------------------------------------
+# orth and Rayleigh-Ritz (Sec. 2.1 Eq. (subspace-update), Sec. 2.2 Eq. (RR))
+# ---------------------------------------------------------------------------
+
+
+def orth(Y: np.ndarray) -> np.ndarray:
+    """Thin QR factor with positive diagonal R (reading R3)."""
+    Q, R = np.linalg.qr(np.asarray(Y, dtype=np.float64), mode="reduced")
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s
+
+
+@dataclasses.dataclass
+class RitzPairs:
+    theta: np.ndarray   # p Ritz values, descending
+    V: np.ndarray       # n x p Ritz vectors  V~ = Q Y
+    resid: np.ndarray   # ||B v_i - theta_i v_i||_2
+    H: np.ndarray       # projected matrix Q^T B Q (symmetrised)
+
+
+def rayleigh_ritz(apply_B, Q: np.ndarray) -> RitzPairs:
+    """H = Q^T B Q, H = Y Lambda Y^T, V~ = Q Y (Sec. 2.2, Eq. (RR))."""
+    W = apply_B(Q)
+    H = Q.T @ W
+    H = 0.5 * (H + H.T)
+    lam, Yv = np.linalg.eigh(H)
+    order = np.argsort(-lam, kind="stable")
+    theta = lam[order]
+    Yv = Yv[:, order]
+    V = Q @ Yv
+    R = W @ Yv - V * theta
+    return RitzPairs(theta, V, np.linalg.norm(R, axis=0), H)
+
+
+def subspace_sine(X: np.ndarray, Y: np.ndarray) -> float:
+    """||sin Theta(X, Y)||_2 for orthonormal X, Y of equal width.  The
+    singular values of X^T Y are cos Theta (Sec. 3.1 definition); the sines are
+    the singular values of (I - X X^T) Y, which is the form used here because
+    it keeps small angles accurate (1 - cos^2 cancels)."""
+    if Y.shape[1] == 0:
+        return 0.0
+    R = Y - X @ (X.T @ Y)
+    return float(np.linalg.norm(R, 2))
+
+
+def psd_part(B: np.ndarray) -> np.ndarray:
+    """P_+(B), the projection onto the PSD cone by a full EVD."""
+    lam, V = np.linalg.eigh(0.5 * (B + B.T))
+    return (V * np.maximum(lam, 0.0)) @ V.T
+
+
+# ---------------------------------------------------------------------------
+# Interval choice (Sec. 4.1, reading R4)
+# ---------------------------------------------------------------------------
+
+
+def gershgorin_bounds(S: sp.csr_matrix, diag_shift: np.ndarray):
+    """Lower/upper Gershgorin bounds of the symmetric matrix S + Diag(diag_shift)."""
+    S = sp.csr_matrix(S)
+    d = S.diagonal() + diag_shift
+    off = np.asarray(abs(S).sum(axis=1)).ravel() - np.abs(S.diagonal())
+    return float(np.min(d - off)), float(np.max(d + off))
+
+
+def choose_b(a: float, theta_prev: Optional[np.ndarray], ub: float, eta: float = ETA) -> float:
+    if theta_prev is None:
+        b = eta * a if a < 0 else a + (1.0 - eta) * (ub - a)
+    else:
+        b = (1.0 - eta) * float(np.min(theta_prev)) + eta * a
+    gap = 1e-3 * max(1.0, abs(a))
+    if b - a < gap:
+        b = a + gap
+    return b
+
+
+# ---------------------------------------------------------------------------
+# Max-cut SDP by PFAM / DRS (Sec. 2.3)
+# ---------------------------------------------------------------------------
+
+
+def prox_G_maxcut(Y: np.ndarray, C: np.ndarray, t: float) -> np.ndarray:
+    """prox_tG(Y) for G = 1{diag X = 1} + <C, X> (reading R2, minus sign):
+    A = diag, A* = Diag, AA* = I, b = 1."""
+    W = Y - t * C
+    return W - np.diag(np.diag(W) - 1.0)
+
+
+@dataclasses.dataclass
+class MaxCutState:
+    Z: np.ndarray                       # dense iteration matrix
+    U: np.ndarray                       # n x p block (warm start)
+    lam: np.ndarray                     # lambda of the step that produced Z
+    theta_prev: Optional[np.ndarray]    # Ritz values of the previous RR
+    Xt_V: Optional[np.ndarray] = None   # factors of X~ of the previous step
+    Xt_theta: Optional[np.ndarray] = None
+
+
+@dataclasses.dataclass
+class MaxCutInfo:
+    a: float
+    b: float
+    obj: float
+    pinf: float
+    dinf: float
+    gap: float
+    kkt: float
+    r_plus: int
+    theta: np.ndarray
+
+
+def maxcut_step_size(C: sp.csr_matrix) -> float:
+    """t = 10 sqrt(n)/||C||_F (reading R6)."""
+    return 10.0 * math.sqrt(C.shape[0]) / float(sp.linalg.norm(C, "fro"))
+
+
+def maxcut_init(C: sp.csr_matrix, U0_raw: np.ndarray, t: float) -> MaxCutState:
+    """Z^1 = prox_tG(2 P_+(Z^0) - Z^0) - P_+(Z^0) + Z^0 with Z^0 = 0, i.e. the
+    exact DRS image of Z^0 = 0 (reading R6)."""
+    n = C.shape[0]
+    Cd = C.toarray()
+    Z1 = prox_G_maxcut(np.zeros((n, n)), Cd, t)
+    lam = np.diag(-t * Cd) - 1.0
+    return MaxCutState(Z=Z1, U=np.array(U0_raw, dtype=np.float64), lam=lam, theta_prev=None)
+
+
+def _maxcut_kkt(C: sp.csr_matrix, Cd: np.ndarray, Xt: np.ndarray, Z: np.ndarray,
+                Z_next: np.ndarray, lam: np.ndarray, t: float):
+    n = Z.shape[0]
+    y = -lam / t
+    Cnorm = float(np.linalg.norm(Cd))
+    pobj = float(np.sum(Cd * Xt))
+    dobj = float(np.sum(y))
+    pinf = float(np.linalg.norm(np.diag(Xt) - 1.0)) / (1.0 + math.sqrt(n))
+    S = (Xt - Z) / t
+    dinf = float(np.linalg.norm(Cd - np.diag(y) - S)) / (1.0 + Cnorm)
+    gap = abs(pobj - dobj) / (1.0 + abs(pobj) + abs(dobj))
+    return pobj, pinf, dinf, gap
+
+
+def maxcut_pfam_step(C: sp.csr_matrix, st: MaxCutState, t: float, degree: int,
+                     exact: bool = False, eta: float = ETA):
+    """One PFAM iteration, Eqs. (PFAM1)-(PFAM2), in the order
+    filter (PFAM2 for the current Z) -> Rayleigh-Ritz -> DRS update (PFAM1).
+    With ``exact`` the filter/RR pair is replaced by a full EVD (plain DRS)."""
+    Cd = C.toarray()
+    Z = st.Z
+    n = Z.shape[0]
+    apply_Z = lambda X: Z @ X  # noqa: E731
+    # [a, b] from the sparse part -tC - Diag(lam) of Z = X~ - tC - Diag(lam)
+    a, ub_sp = gershgorin_bounds(-t * C, -st.lam)
+    ub = ub_sp + (float(np.max(st.Xt_theta)) if st.Xt_theta is not None and st.Xt_theta.size else 0.0)
+    ub = max(ub, 0.0)
+    b = choose_b(a, st.theta_prev, ub, eta)
+    if exact:
+        lamZ, VZ = np.linalg.eigh(Z)
+        order = np.argsort(-lamZ, kind="stable")
+        theta, V = lamZ[order], VZ[:, order]
+        U = st.U
+    else:
+        U = orth(cheb_filter(apply_Z, st.U, a, b, degree))
+        rr = rayleigh_ritz(apply_Z, U)
+        theta, V = rr.theta, rr.V
+    pos = theta > 0
+    Xt = (V[:, pos] * theta[pos]) @ V[:, pos].T               # P_+(P_U(Z))
+    lam = np.diag(2.0 * Xt - Z - t * Cd) - 1.0
+    Z_next = prox_G_maxcut(2.0 * Xt - Z, Cd, t) - Xt + Z       # T_DRS, Eq. (PFAM1)
+    pobj, pinf, dinf, gap = _maxcut_kkt(C, Cd, Xt, Z, Z_next, lam, t)
+    info = MaxCutInfo(a, b, pobj, pinf, dinf, gap, max(pinf, dinf, gap), int(pos.sum()), theta)
+    new = MaxCutState(Z=Z_next, U=U, lam=lam, theta_prev=theta,
+                      Xt_V=V[:, pos], Xt_theta=theta[pos])
+    return new, info
+
+
+def maxcut_solve(C: sp.csr_matrix, U0_raw: np.ndarray, degree: int, iters: int,
+                 t: Optional[float] = None, exact: bool = False, tol: float = 0.0):
+    t = maxcut_step_size(C) if t is None else t
+    st = maxcut_init(C, U0_raw, t)
+    hist = []
+    for _ in range(iters):
+        st, info = maxcut_pfam_step(C, st, t, degree, exact=exact)
+        hist.append(info)
+        if tol > 0 and info.kkt <= tol:
+            break
+    return st, hist
+
+
+# ---------------------------------------------------------------------------
+# PSD completion by PFPG (Sec. 2.2, reading R8)
+# ---------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class CompletionState:
+    V: np.ndarray                       # n x r+ factor of X_k, X_k = V diag(w) V^T
+    w: np.ndarray                       # r+ nonnegative weights
+    U: np.ndarray                       # n x p warm-start block
+    theta_prev: Optional[np.ndarray]
+
+
+@dataclasses.dataclass
+class CompletionInfo:
+    a: float
+    b: float
+    obj: float
+    kkt: float
+    r_plus: int
+    theta: np.ndarray
+
+
+def omega_matrix(omega) -> sp.csr_matrix:
+    return sp.csr_matrix((omega.vals.astype(np.float64), omega.colind, omega.rowptr),
+                         shape=(omega.n, omega.n))
+
+
+def sampled_residual(Om: sp.csr_matrix, V: np.ndarray, w: np.ndarray) -> sp.csr_matrix:
+    """S = P_Omega(X - M) with X = V diag(w) V^T, entry by entry on Omega."""
+    coo = Om.tocoo()
+    if V.shape[1]:
+        x = np.einsum("ij,ij->i", V[coo.row] * w, V[coo.col])
+    else:
+        x = np.zeros(coo.nnz)
+    return sp.csr_matrix((x - coo.data, (coo.row, coo.col)), shape=Om.shape)
+
+
+def completion_init(n: int, U0_raw: np.ndarray) -> CompletionState:
+    return CompletionState(V=np.zeros((n, 0)), w=np.zeros(0), U=np.array(U0_raw, dtype=np.float64),
+                           theta_prev=None)
+
+
+def _lowrank_fro_diff(V1, w1, V2, w2) -> float:
+    """||V1 diag(w1) V1^T - V2 diag(w2) V2^T||_F from the factors."""
+    def tr(Va, wa, Vb, wb):
+        if Va.shape[1] == 0 or Vb.shape[1] == 0:
+            return 0.0
+        M = Va.T @ Vb
+        return float(np.sum((wa[:, None] * M) * (M * wb[None, :])))
+    v = tr(V1, w1, V1, w1) - 2.0 * tr(V1, w1, V2, w2) + tr(V2, w2, V2, w2)
+    return math.sqrt(max(v, 0.0))
+
+
+def completion_pfpg_step(Om: sp.csr_matrix, st: CompletionState, mu: float, t: float,
+                         degree: int, exact: bool = False, eta: float = ETA):
+    """One PFPG iteration (Eqs. (pfpg1)-(pfpg2), reading R8)."""
+    n = Om.shape[0]
+    S = sampled_residual(Om, st.V, st.w)
+    V, w = st.V, st.w
+
+    def apply_B(Y):
+        XY = V @ (w[:, None] * (V.T @ Y)) if V.shape[1] else np.zeros_like(Y)
+        return XY - t * (S @ Y) - t * mu * Y
+
+    a, ub_sp = gershgorin_bounds(-t * S, np.full(n, -t * mu))
+    ub = max(ub_sp + (float(np.max(w)) if w.size else 0.0), 0.0)
+    b = choose_b(a, st.theta_prev, ub, eta)
+    if exact:
+        Bd = (V * w) @ V.T - t * S.toarray() - t * mu * np.eye(n)
+        lamB, VB = np.linalg.eigh(0.5 * (Bd + Bd.T))
+        order = np.argsort(-lamB, kind="stable")
+        theta, Vr = lamB[order], VB[:, order]
+        U = st.U
+    else:
+        U = orth(cheb_filter(apply_B, st.U, a, b, degree))
+        rr = rayleigh_ritz(apply_B, U)
+        theta, Vr = rr.theta, rr.V
+    pos = theta > 0
+    V_next, w_next = Vr[:, pos], theta[pos]
+    Snorm = float(sp.linalg.norm(S, "fro"))
+    Xnorm = float(np.linalg.norm(w))
+    kkt = _lowrank_fro_diff(V, w, V_next, w_next) / (1.0 + Xnorm + t * Snorm)
+    obj = 0.5 * Snorm ** 2 + mu * float(np.sum(w))
+    info = CompletionInfo(a, b, obj, kkt, int(pos.sum()), theta)
+    return CompletionState(V=V_next, w=w_next, U=U, theta_prev=theta), info
+
+
+def completion_solve(omega, U0_raw, mu: float, t: float, degree: int, iters: int,
+                     exact: bool = False, tol: float = 0.0):
+    Om = omega_matrix(omega)
+    st = completion_init(omega.n, U0_raw)
+    hist = []
+    for _ in range(iters):
+        st, info = completion_pfpg_step(Om, st, mu, t, degree, exact=exact)
+        hist.append(info)
+        if tol > 0 and info.kkt <= tol:
+            break
+    return st, hist

@@ -1,0 +1,217 @@
+"""Seeded synthetic inputs shaped like the paper's low-rank matrix workloads.
+
+This module only draws random numbers and assembles problem data (sparse
+patterns, sampled entries, graph Laplacian cost matrices, random start
+blocks).  It holds none of the polynomial-filtered method's arithmetic, so the
+CPU oracle and the CUDA path can both take their inputs from here without
+sharing any of the computation they are compared on.
+
+Workload laws:
+
+* PSD matrix completion (the symmetric analogue of the matrix-completion
+  tests of Sec. 5.2, Example "MC"): ``M = G G^T`` with ``G`` an ``n x r``
+  Gaussian matrix of variance ``1/r``; the sample set Omega draws each
+  unordered pair ``i <= j`` independently with probability ``rate`` and is
+  mirrored, so the stored pattern is symmetric.  Sampled values are stored in
+  float32 (CSR, int32 column indices, sorted columns).
+* Max-cut SDP (a standard SDP, Sec. 2.3): an Erdos-Renyi graph with edge
+  probability ``prob``, no self loops, weights +-1 with equal probability,
+  and cost matrix ``C = -L/4`` with ``L = D - W`` the weighted Laplacian,
+  stored as a CSR matrix that includes the diagonal.
+* Start block: an ``n x p`` standard Gaussian matrix.  Orthonormalising it
+  is the method's job, not the generator's.
+
+Seeds: ``seed = 1904105850 + config_index`` with numpy ``PCG64``; the
+graph/weights, the sample set, the factor ``G`` and the start block draw from
+independent child streams made by ``SeedSequence.spawn``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 1904105850
+
+
+def config_seed(config_index: int) -> int:
+    return SEED_BASE + int(config_index)
+
+
+def _streams(seed: int, k: int):
+    ss = np.random.SeedSequence(seed)
+    return [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(k)]
+
+
+@dataclasses.dataclass
+class CSR:
+    """Square sparse matrix in CSR form (int32 indices, sorted columns)."""
+
+    n: int
+    rowptr: np.ndarray  # int32 [n+1]
+    colind: np.ndarray  # int32 [nnz]
+    vals: np.ndarray    # float32 or float64 [nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colind.shape[0])
+
+    def to_dense(self) -> np.ndarray:
+        a = np.zeros((self.n, self.n), dtype=np.float64)
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        a[rows, self.colind] = self.vals.astype(np.float64)
+        return a
+
+    def row_of_entries(self) -> np.ndarray:
+        return np.repeat(np.arange(self.n, dtype=np.int64), np.diff(self.rowptr))
+
+
+def _upper_pairs(rng, n: int, prob: float, include_diag: bool):
+    """Independent Bernoulli(prob) draw over the unordered pairs i <= j
+    (i < j when ``include_diag`` is False), by geometric skips over the
+    row-major enumeration of the upper triangle.  Returns sorted (i, j)."""
+    if n <= 0 or prob <= 0.0:
+        e = np.zeros(0, dtype=np.int64)
+        return e, e
+    width = n if include_diag else n - 1
+    # row i holds columns j = i + (0 if include_diag else 1) .. n-1
+    counts = np.arange(width, 0, -1, dtype=np.int64) if include_diag else np.arange(n - 1, 0, -1, dtype=np.int64)
+    total = int(counts.sum())
+    if total == 0:
+        e = np.zeros(0, dtype=np.int64)
+        return e, e
+    if prob >= 1.0:
+        lin = np.arange(total, dtype=np.int64)
+    else:
+        # expected count plus a generous margin; top up if ever short
+        est = int(total * prob + 10 * math.sqrt(total * prob + 1) + 16)
+        chunks = []
+        pos = -1
+        while True:
+            gaps = rng.geometric(prob, size=est).astype(np.int64)
+            cs = pos + np.cumsum(gaps)
+            chunks.append(cs[cs < total])
+            if cs[-1] >= total:
+                break
+            pos = int(cs[-1])
+        lin = np.concatenate(chunks)
+    offsets = np.concatenate([[0], np.cumsum(counts)])
+    i = np.searchsorted(offsets, lin, side="right") - 1
+    start = i + (0 if include_diag else 1)
+    j = start + (lin - offsets[i])
+    return i.astype(np.int64), j.astype(np.int64)
+
+
+def _symmetric_csr(n: int, i: np.ndarray, j: np.ndarray, v: np.ndarray, diag=None) -> CSR:
+    """Mirror upper-triangle entries (i <= j) into a full symmetric CSR."""
+    off = i != j
+    rows = np.concatenate([i, j[off]])
+    cols = np.concatenate([j, i[off]])
+    vals = np.concatenate([v, v[off]])
+    if diag is not None:
+        rows = np.concatenate([rows, np.arange(n)])
+        cols = np.concatenate([cols, np.arange(n)])
+        vals = np.concatenate([vals, diag])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    if rowptr[-1] > np.iinfo(np.int32).max:
+        raise ValueError("nnz exceeds int32 row pointers")
+    return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals)
+
+
+@dataclasses.dataclass
+class CompletionInstance:
+    n: int
+    rank: int
+    G: np.ndarray       # n x rank float64 ground-truth factor, M = G G^T
+    omega: CSR          # sampled entries of M (float32 values), symmetric pattern
+    U0_raw: np.ndarray  # n x p standard Gaussian start block (not orthonormal)
+    mu: float
+    t: float
+
+
+def completion_instance(n: int, rank: int, rate: float, p: int, seed: int,
+                        mu: float = 0.05, t: float = 1.0) -> CompletionInstance:
+    """PSD completion data: M = G G^T, G ~ N(0, 1/rank); Omega symmetric
+    uniform with pair probability ``rate`` (diagonal pairs included)."""
+    r_pat, r_g, r_u = _streams(seed, 3)
+    G = r_g.standard_normal((n, rank)) / math.sqrt(rank)
+    i, j = _upper_pairs(r_pat, n, rate, include_diag=True)
+    vals = np.empty(i.shape[0], dtype=np.float64)
+    step = 1 << 20
+    for s in range(0, i.shape[0], step):
+        vals[s:s + step] = np.einsum("ij,ij->i", G[i[s:s + step]], G[j[s:s + step]])
+    omega = _symmetric_csr(n, i, j, vals.astype(np.float32))
+    U0 = r_u.standard_normal((n, p))
+    return CompletionInstance(n, rank, G, omega, U0, float(mu), float(t))
+
+
+@dataclasses.dataclass
+class MaxCutInstance:
+    n: int
+    C: CSR              # C = -L/4 (float64 values), diagonal included
+    n_edges: int
+    U0_raw: np.ndarray  # n x p standard Gaussian start block
+
+
+def maxcut_cost_from_edges(n: int, i: np.ndarray, j: np.ndarray, w: np.ndarray) -> CSR:
+    """C = -(D - W)/4 for the weighted graph with edges (i<j, w)."""
+    deg = np.zeros(n, dtype=np.float64)
+    np.add.at(deg, i, w)
+    np.add.at(deg, j, w)
+    return _symmetric_csr(n, i, j, 0.25 * w.astype(np.float64), diag=-0.25 * deg)
+
+
+def maxcut_instance(n: int, prob: float, p: int, seed: int) -> MaxCutInstance:
+    """Erdos-Renyi graph G(n, prob), weights +-1 equiprobable, C = -L/4."""
+    r_graph, r_w, r_u = _streams(seed, 3)
+    i, j = _upper_pairs(r_graph, n, prob, include_diag=False)
+    w = np.where(r_w.random(i.shape[0]) < 0.5, -1.0, 1.0)
+    C = maxcut_cost_from_edges(n, i, j, w)
+    U0 = r_u.standard_normal((n, p))
+    return MaxCutInstance(n, C, int(i.shape[0]), U0)
+
+
+def dense_symmetric_with_spectrum(n: int, eigvals: np.ndarray, seed: int):
+    """B = Q diag(eigvals) Q^T with Q a product of seeded Householder
+    reflections (test matrices of known spectrum).  Returns (B, Q)."""
+    rng = _streams(seed, 1)[0]
+    Q = np.eye(n)
+    for _ in range(3):
+        v = rng.standard_normal(n)
+        v /= np.linalg.norm(v)
+        Q = Q - 2.0 * np.outer(Q @ v, v)
+    B = (Q * np.asarray(eigvals, dtype=np.float64)) @ Q.T
+    B = 0.5 * (B + B.T)
+    return B, Q
+
+
+def gaussian_block(n: int, p: int, seed: int) -> np.ndarray:
+    return _streams(seed, 1)[0].standard_normal((n, p))
+
+
+# Named workloads (sizes of the configurations the benchmark and tests use).
+WORKLOADS = {
+    "completion_n400": dict(kind="completion", n=400, rank=8, rate=0.20, p=16, degree=3,
+                            iters=100, mu=0.05, t=1.0, config_index=0),
+    "maxcut_n4096": dict(kind="maxcut", n=4096, prob=0.01, p=32, degree=4, iters=200,
+                         config_index=1),
+    "maxcut_n16384_lowprec": dict(kind="maxcut", n=16384, prob=0.01, p=64, degree=4,
+                                  degree_max=8, iters=200, config_index=2),
+    "completion_n50000": dict(kind="completion", n=50000, rank=20, rate=0.01, p=40, degree=4,
+                              iters=100, mu=0.05, t=1.0, config_index=3),
+}
+
+
+def make_workload(name: str, **overrides):
+    cfg = dict(WORKLOADS[name])
+    cfg.update(overrides)
+    seed = config_seed(cfg["config_index"])
+    if cfg["kind"] == "completion":
+        return cfg, completion_instance(cfg["n"], cfg["rank"], cfg["rate"], cfg["p"], seed,
+                                        mu=cfg["mu"], t=cfg["t"])
+    return cfg, maxcut_instance(cfg["n"], cfg["prob"], cfg["p"], seed)

@@ -1,0 +1,410 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics,
+never against the oracle itself: closed forms, invariants, special cases that
+reduce to textbook formulas, brute force on tiny inputs and the paper's error
+bound.  Each pin is chosen so that a plausible mistake in the oracle (a
+swapped interval map, a wrong first recurrence step, a sign error in the prox,
+a transposed projection) fails at least one of them; ``test_planted_*``
+plants such mistakes in the oracle and checks that a pin catches them."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from numpy.polynomial import chebyshev as npcheb
+
+import pf_synthetic as syn
+from oracle import pf_oracle as o
+
+
+def diag_apply(x):
+    return lambda Y: x[:, None] * Y
+
+
+def T_closed(d, x):
+    """Independent closed form of T_d: cos/cosh branches, with the sign
+    (-1)^d on x < -1 (Eq. (cheb) rewritten with arccosh)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    m = np.abs(x) <= 1
+    out[m] = np.cos(d * np.arccos(x[m]))
+    hi = x > 1
+    out[hi] = np.cosh(d * np.arccosh(x[hi]))
+    lo = x < -1
+    out[lo] = (-1) ** d * np.cosh(d * np.arccosh(-x[lo]))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Chebyshev filter (Sec. 2.1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3, 4, 7, 8])
+def test_closed_form_T_matches_numpy_chebval(d):
+    x = np.linspace(-3, 3, 1001)
+    coef = np.zeros(d + 1)
+    coef[d] = 1
+    ref = npcheb.chebval(x, coef)
+    np.testing.assert_allclose(o.chebyshev_T(d, x), ref, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(T_closed(d, x), ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 6, 8])
+def test_filter_on_diagonal_matrix_is_T_d_of_mapped_eigenvalues(d):
+    a, b = -2.5, 0.7
+    x = np.linspace(-3.0, 9.0, 37)
+    Y = o.cheb_filter(diag_apply(x), np.eye(x.size), a, b, d)
+    mapped = (x - (a + b) / 2) / ((b - a) / 2)
+    ref = T_closed(d, mapped)
+    np.testing.assert_allclose(np.diag(Y), ref, rtol=1e-13, atol=1e-13)
+    assert np.abs(Y - np.diag(np.diag(Y))).max() == 0.0
+    # damped inside [a, b], amplified outside
+    inside = (x >= a) & (x <= b)
+    assert np.all(np.abs(np.diag(Y)[inside]) <= 1 + 1e-12)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 8])
+def test_chebyshev_growth_lemma(d):
+    """Lemma (cheb-est): T_d(+-(1+eps)) >= 2^{d min(sqrt(eps),1) - 1}."""
+    eps = np.logspace(-6, 2, 200)
+    for sgn in (1.0, -1.0):
+        x = sgn * (1 + eps)
+        # evaluate through the oracle's filter on a diagonal matrix, a=-1, b=1
+        Y = o.cheb_filter(diag_apply(x), np.ones((x.size, 1)), -1.0, 1.0, d)[:, 0]
+        bound = 2.0 ** (d * np.minimum(np.sqrt(eps), 1.0) - 1.0)
+        assert np.all(np.abs(Y) >= bound * (1 - 1e-12))
+
+
+def test_filter_known_spectrum():
+    n, p, d = 60, 5, 4
+    lam = np.concatenate([np.linspace(5, 3, p), np.linspace(1.0, -4.0, n - p)])
+    B, Q = syn.dense_symmetric_with_spectrum(n, lam, seed=3)
+    U = syn.gaussian_block(n, p, seed=4)
+    a, b = -4.0, 1.2
+    Y = o.cheb_filter(lambda X: B @ X, U, a, b, d)
+    coef = np.zeros(d + 1)
+    coef[d] = 1
+    rho = npcheb.chebval((lam - (a + b) / 2) / ((b - a) / 2), coef)
+    ref = Q @ (rho[:, None] * (Q.T @ U))
+    np.testing.assert_allclose(Y, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_contraction_bound_one_step():
+    """sin Theta(V_p, orth(rho(B)U)) <= eta tan Theta(V_p, U) with
+    eta = max_{i>p}|rho(l_i)| / min_{i<=p}|rho(l_i)| (Eq. (err-oi))."""
+    n, p = 80, 6
+    lam = np.concatenate([np.linspace(4, 2.5, p), np.linspace(1.5, -3, n - p)])
+    B, Q = syn.dense_symmetric_with_spectrum(n, lam, seed=11)
+    Vp = Q[:, :p]
+    for seed, d in itertools.product([1, 2, 3], [2, 4, 6]):
+        U = o.orth(syn.gaussian_block(n, p, seed=seed))
+        a, b = -3.0, 1.6
+        Up = o.orth(o.cheb_filter(lambda X: B @ X, U, a, b, d))
+        rho = np.abs(o.chebyshev_T(d, (lam - (a + b) / 2) / ((b - a) / 2)))
+        eta = rho[p:].max() / rho[:p].min()
+        s0 = o.subspace_sine(Vp, U)
+        tan0 = s0 / math.sqrt(1 - s0 * s0)
+        assert o.subspace_sine(Vp, Up) <= eta * tan0 * (1 + 1e-8) + 1e-14
+
+
+# --------------------------------------------------------------------------
+# orth and Rayleigh-Ritz
+# --------------------------------------------------------------------------
+
+def classical_gram_schmidt(Y):
+    n, p = Y.shape
+    Q = np.zeros_like(Y)
+    for j in range(p):
+        v = Y[:, j].copy()
+        for i in range(j):
+            v -= (Q[:, i] @ Y[:, j]) * Q[:, i]
+        Q[:, j] = v / math.sqrt(v @ v)
+    return Q
+
+
+def test_orth_is_unique_positive_diagonal_qr():
+    Y = syn.gaussian_block(9, 4, seed=5)
+    Q = o.orth(Y)
+    np.testing.assert_allclose(Q, classical_gram_schmidt(Y), atol=1e-12)
+    R = Q.T @ Y
+    assert np.allclose(np.tril(R, -1), 0, atol=1e-12)
+    assert np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(4), atol=1e-14)
+
+
+def test_rr_recovers_invariant_subspace_exactly():
+    n, p = 50, 7
+    lam = np.concatenate([np.array([9, 8, 7.5, 6, 5, 4, 3.0]), np.linspace(2, -6, n - p)])
+    B, Q = syn.dense_symmetric_with_spectrum(n, lam, seed=8)
+    R = o.orth(syn.gaussian_block(p, p, seed=9))
+    U = Q[:, :p] @ R                          # an orthonormal basis of the invariant subspace
+    rr = o.rayleigh_ritz(lambda X: B @ X, U)
+    np.testing.assert_allclose(rr.theta, lam[:p], rtol=1e-13)
+    assert rr.resid.max() < 1e-12
+    assert o.subspace_sine(rr.V, Q[:, :p]) < 1e-12
+    # each Ritz vector is an eigenvector: compare projectors one by one
+    for i in range(p):
+        Pi = np.outer(rr.V[:, i], rr.V[:, i])
+        np.testing.assert_allclose(Pi, np.outer(Q[:, i], Q[:, i]), atol=1e-12)
+
+
+def test_rr_tiny_brute_force_2x2_and_3x3():
+    # 2x2 closed form
+    A = np.array([[2.0, 0.7], [0.7, -1.0]])
+    rr = o.rayleigh_ritz(lambda X: A @ X, np.eye(2))
+    m, h = (A[0, 0] + A[1, 1]) / 2, math.hypot((A[0, 0] - A[1, 1]) / 2, A[0, 1])
+    np.testing.assert_allclose(rr.theta, [m + h, m - h], rtol=1e-14)
+    # 3x3: roots of the characteristic polynomial written out
+    A = np.array([[1.0, 2.0, -0.5], [2.0, 0.3, 0.1], [-0.5, 0.1, -2.0]])
+    tr = np.trace(A)
+    minors = sum(A[i, i] * A[j, j] - A[i, j] * A[j, i] for i in range(3) for j in range(i + 1, 3))
+    det = (A[0, 0] * (A[1, 1] * A[2, 2] - A[1, 2] * A[2, 1])
+           - A[0, 1] * (A[1, 0] * A[2, 2] - A[1, 2] * A[2, 0])
+           + A[0, 2] * (A[1, 0] * A[2, 1] - A[1, 1] * A[2, 0]))
+    roots = np.sort(np.roots([1.0, -tr, minors, -det]).real)[::-1]
+    rr = o.rayleigh_ritz(lambda X: A @ X, np.eye(3))
+    np.testing.assert_allclose(rr.theta, roots, rtol=1e-12)
+
+
+def test_subspace_sine_known_angle():
+    for phi in [0.0, 0.1, 0.7, 1.4, math.pi / 2]:
+        X = np.array([[1.0], [0.0]])
+        Y = np.array([[math.cos(phi)], [math.sin(phi)]])
+        assert abs(o.subspace_sine(X, Y) - abs(math.sin(phi))) < 1e-12
+
+
+def test_psd_projection_properties():
+    Z = syn.gaussian_block(12, 12, seed=2)
+    Z = Z + Z.T
+    P = o.psd_part(Z)
+    np.testing.assert_allclose(o.psd_part(P), P, atol=1e-12)           # idempotent
+    assert np.linalg.eigvalsh(P).min() > -1e-12                        # PSD
+    assert np.linalg.eigvalsh(Z - P).max() < 1e-12                     # remainder NSD
+    assert abs(np.sum(P * (Z - P))) < 1e-10                            # complementary
+    d = np.array([3.0, -1.0, 0.5, -2.0])
+    np.testing.assert_allclose(o.psd_part(np.diag(d)), np.diag(np.maximum(d, 0)), atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Interval bounds
+# --------------------------------------------------------------------------
+
+def test_gershgorin_lower_bound_is_rigorous_for_psd_plus_sparse():
+    n = 70
+    inst = syn.maxcut_instance(n, 0.2, 4, seed=21)
+    C = sp.csr_matrix((inst.C.vals, inst.C.colind, inst.C.rowptr), shape=(n, n))
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        lam = rng.standard_normal(n)
+        t = 0.3
+        G = rng.standard_normal((n, 5))
+        Z = G @ G.T - t * C.toarray() - np.diag(lam)
+        a, ub = o.gershgorin_bounds(-t * C, -lam)
+        assert a <= np.linalg.eigvalsh(Z).min() + 1e-12
+        assert ub >= np.linalg.eigvalsh(-t * C.toarray() - np.diag(lam)).max() - 1e-12
+
+
+# --------------------------------------------------------------------------
+# Max-cut SDP via DRS / PFAM (Sec. 2.3)
+# --------------------------------------------------------------------------
+
+def test_prox_G_minus_sign_satisfies_its_kkt():
+    rng = np.random.default_rng(1)
+    n, t = 6, 0.7
+    Y = rng.standard_normal((n, n)); Y = Y + Y.T
+    C = rng.standard_normal((n, n)); C = C + C.T
+    X = o.prox_G_maxcut(Y, C, t)
+    np.testing.assert_allclose(np.diag(X), 1.0, atol=1e-15)
+    # stationarity of <C,X> + ||X-Y||^2/(2t) on {diag X = 1}: X - Y + tC is diagonal
+    R = X - Y + t * C
+    np.testing.assert_allclose(R - np.diag(np.diag(R)), 0.0, atol=1e-14)
+    f = lambda W: np.sum(C * W) + np.sum((W - Y) ** 2) / (2 * t)  # noqa: E731
+    for _ in range(20):
+        D = rng.standard_normal((n, n)); D = D + D.T; np.fill_diagonal(D, 0.0)
+        assert f(X + 1e-3 * D) > f(X)
+
+
+def _csr(inst_C):
+    return sp.csr_matrix((inst_C.vals, inst_C.colind, inst_C.rowptr), shape=(inst_C.n, inst_C.n))
+
+
+def test_maxcut_complete_graph_closed_form():
+    """K_n, unit weights: min <C,X> = -n^2/4, attained at X = (nI - J)/(n-1)."""
+    n = 8
+    i, j = np.triu_indices(n, 1)
+    C = _csr(syn.maxcut_cost_from_edges(n, i, j, np.ones(i.size)))
+    U0 = syn.gaussian_block(n, n, seed=1)
+    for exact in (True, False):
+        st, hist = o.maxcut_solve(C, U0, 4, 400, exact=exact, tol=1e-10)
+        assert abs(hist[-1].obj + n * n / 4) < 1e-6 * n * n
+        assert hist[-1].kkt < 1e-6
+
+
+def test_maxcut_bipartite_value_is_total_weight():
+    """Connected bipartite graph with positive weights: the SDP value is the
+    total weight (rank-1 optimum), reached by PFAM with a small block."""
+    rng = np.random.default_rng(3)
+    n1, n2 = 12, 14
+    edges = [(a, n1 + b) for a in range(n1) for b in range(n2) if rng.random() < 0.4]
+    edges += [(a, n1 + (a % n2)) for a in range(n1)] + [((b % n1), n1 + b) for b in range(n2)]
+    edges = sorted(set(edges))
+    i = np.array([e[0] for e in edges]); j = np.array([e[1] for e in edges])
+    w = rng.uniform(0.5, 2.0, i.size)
+    C = _csr(syn.maxcut_cost_from_edges(n1 + n2, i, j, w))
+    U0 = syn.gaussian_block(n1 + n2, 4, seed=2)
+    st, hist = o.maxcut_solve(C, U0, 4, 3000, tol=1e-9)
+    assert abs(hist[-1].obj + w.sum()) < 1e-5 * w.sum()
+
+
+def test_maxcut_relaxation_bound_brute_force():
+    """n = 10: the SDP minimum is <= min over x in {+-1}^n of x^T C x."""
+    n = 10
+    inst = syn.maxcut_instance(n, 0.6, n, seed=5)
+    C = _csr(inst.C)
+    Cd = C.toarray()
+    best = min(np.array(x) @ Cd @ np.array(x) for x in itertools.product([-1.0, 1.0], repeat=n))
+    st, hist = o.maxcut_solve(C, inst.U0_raw, 4, 5000, exact=True, tol=1e-8)
+    assert hist[-1].kkt < 1e-6
+    assert hist[-1].obj <= best + 1e-6
+
+
+def test_maxcut_pf_with_full_block_equals_exact_drs():
+    n = 24
+    inst = syn.maxcut_instance(n, 0.3, n, seed=6)
+    C = _csr(inst.C)
+    _, h_pf = o.maxcut_solve(C, inst.U0_raw, 3, 40)
+    _, h_ex = o.maxcut_solve(C, inst.U0_raw, 3, 40, exact=True)
+    for a, b in zip(h_pf, h_ex):
+        assert abs(a.obj - b.obj) <= 1e-9 * max(1.0, abs(b.obj))
+
+
+def test_maxcut_dual_residual_identity():
+    """C - Diag(y) - S = (Z_k - Z_{k+1})/t for y = -lambda/t, S = (X~ - Z_k)/t."""
+    n = 30
+    inst = syn.maxcut_instance(n, 0.3, 8, seed=7)
+    C = _csr(inst.C)
+    t = o.maxcut_step_size(C)
+    st = o.maxcut_init(C, inst.U0_raw, t)
+    for _ in range(5):
+        Zk = st.Z
+        st, info = o.maxcut_pfam_step(C, st, t, 4)
+        alt = np.linalg.norm(Zk - st.Z) / (t * (1 + np.linalg.norm(C.toarray())))
+        assert abs(alt - info.dinf) <= 1e-10 * max(1.0, alt)
+
+
+# --------------------------------------------------------------------------
+# PSD completion via PFPG
+# --------------------------------------------------------------------------
+
+def test_completion_full_sampling_closed_form():
+    """Omega = all entries, t = 1: the PG fixed point is P_+(M - mu I), whose
+    eigenvalues are (sigma_i(G)^2 - mu)_+ (an SVD route independent of EVD)."""
+    n, r, mu = 40, 3, 0.05
+    inst = syn.completion_instance(n, r, 1.0, r + 5, seed=12, mu=mu)
+    st_ex, h_ex = o.completion_solve(inst.omega, inst.U0_raw, mu, 1.0, 3, 3, exact=True)
+    st_pf, h_pf = o.completion_solve(inst.omega, inst.U0_raw, mu, 1.0, 3, 60)
+    Gs = inst.G.astype(np.float32).astype(np.float64)  # M values are stored in float32
+    M = inst.omega.to_dense()
+    Uo, s, _ = np.linalg.svd(inst.G, full_matrices=False)
+    lam_ref = np.maximum(np.linalg.eigvalsh(M)[::-1][:r] - mu, 0)
+    np.testing.assert_allclose(np.sort(lam_ref), np.sort(np.maximum(s ** 2 - mu, 0)), rtol=1e-6)
+    Xref = o.psd_part(M - mu * np.eye(n))
+    for st in (st_ex, st_pf):
+        X = (st.V * st.w) @ st.V.T
+        np.testing.assert_allclose(X, Xref, atol=1e-10)
+    del Gs, Uo
+
+
+def test_completion_objective_decreases_and_recovers_low_rank():
+    """Noiseless rank-2 M, half the entries seen, small mu: the iterates
+    settle on rank 2 and X approaches M (the recovery regime of Sec. 5.2)."""
+    n, r = 80, 2
+    inst = syn.completion_instance(n, r, 0.5, 8, seed=13, mu=1e-2)
+    st, hist = o.completion_solve(inst.omega, inst.U0_raw, 1e-2, 1.0, 3, 300)
+    objs = np.array([h.obj for h in hist])
+    assert objs[-1] < objs[5]
+    assert hist[-1].r_plus == r and hist[-1].kkt < 1e-5
+    M = inst.G @ inst.G.T
+    X = (st.V * st.w) @ st.V.T
+    assert np.linalg.norm(X - M) / np.linalg.norm(M) < 5e-3
+
+
+def test_completion_kkt_factor_formula_matches_dense():
+    rng = np.random.default_rng(4)
+    V1 = o.orth(rng.standard_normal((30, 4))); w1 = rng.uniform(0, 2, 4)
+    V2 = o.orth(rng.standard_normal((30, 3))); w2 = rng.uniform(0, 2, 3)
+    dense = np.linalg.norm((V1 * w1) @ V1.T - (V2 * w2) @ V2.T)
+    assert abs(o._lowrank_fro_diff(V1, w1, V2, w2) - dense) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Planted mistakes: each must be caught by a pin above
+# --------------------------------------------------------------------------
+
+def test_planted_swapped_interval_map_is_caught(monkeypatch):
+    """The printed (garbled) recurrence coefficients c0=2/(b-a), c1=(a+b)/(a-b)
+    used as 'centre, half-width' must fail the closed-form pin."""
+    monkeypatch.setattr(o, "interval_map", lambda a, b: (2 / (b - a), (a + b) / (a - b)))
+    with pytest.raises(AssertionError):
+        test_filter_on_diagonal_matrix_is_T_d_of_mapped_eigenvalues(3)
+
+
+def test_planted_plus_sign_prox_is_caught(monkeypatch):
+    def bad(Y, C, t):
+        W = Y + t * C
+        return W - np.diag(np.diag(W) - 1.0)
+    monkeypatch.setattr(o, "prox_G_maxcut", bad)
+    with pytest.raises(AssertionError):
+        test_prox_G_minus_sign_satisfies_its_kkt()
+
+
+def test_planted_first_step_factor_is_caught(monkeypatch):
+    orig = o.cheb_filter
+
+    def bad(apply_B, U, a, b, d):
+        c, e = o.interval_map(a, b)
+        Yp = np.array(U, dtype=np.float64)
+        if d == 0:
+            return Yp
+        Y = 2.0 * (apply_B(Yp) - c * Yp) / e        # wrong: first step uses 2/e
+        for _ in range(1, d):
+            Yp, Y = Y, 2.0 * (apply_B(Y) - c * Y) / e - Yp
+        return Y
+    monkeypatch.setattr(o, "cheb_filter", bad)
+    with pytest.raises(AssertionError):
+        test_filter_on_diagonal_matrix_is_T_d_of_mapped_eigenvalues(2)
+    monkeypatch.setattr(o, "cheb_filter", orig)
+
+
+def test_planted_transposed_projection_is_caught(monkeypatch):
+    def bad_rr(apply_B, Q):
+        W = apply_B(Q)
+        H = W.T @ W                                   # wrong: not Q^T B Q
+        lam, Yv = np.linalg.eigh(0.5 * (H + H.T))
+        order = np.argsort(-lam)
+        return o.RitzPairs(lam[order], Q @ Yv[:, order], np.zeros(Q.shape[1]), H)
+    monkeypatch.setattr(o, "rayleigh_ritz", bad_rr)
+    with pytest.raises(AssertionError):
+        test_rr_recovers_invariant_subspace_exactly()
+
+
+# --------------------------------------------------------------------------
+# Input generator sanity (shapes, symmetry, sampling rates, reproducibility)
+# --------------------------------------------------------------------------
+
+def test_synthetic_inputs_laws():
+    cfg, inst = syn.make_workload("completion_n400")
+    A = inst.omega.to_dense()
+    assert np.array_equal(A != 0, (A != 0).T)
+    frac = inst.omega.nnz / (400 * 400)
+    assert 0.18 < frac < 0.22
+    cfg2, inst2 = syn.make_workload("completion_n400")
+    assert np.array_equal(inst.omega.colind, inst2.omega.colind)
+    assert np.array_equal(inst.U0_raw, inst2.U0_raw)
+    mc = syn.maxcut_instance(500, 0.05, 8, seed=1)
+    Cd = mc.C.to_dense()
+    np.testing.assert_allclose(Cd, Cd.T)
+    np.testing.assert_allclose(Cd.sum(axis=1), 0.0, atol=1e-12)     # Laplacian rows sum to 0
+    off = Cd[~np.eye(500, dtype=bool)]
+    assert set(np.unique(off[off != 0]).tolist()) <= {-0.25, 0.25}
+    assert abs(mc.n_edges / (500 * 499 / 2) - 0.05) < 0.01
