@@ -1,0 +1,377 @@
+"""Benchmark of the polynomial-filtered subspace extraction on GB300.
+
+One step = one whole solve of the workload through the hot path (interval,
+Chebyshev filter, CholQR2, Rayleigh-Ritz, prox/DRS update, KKT report) from a
+fresh initial state:  default workload ``maxcut_n4096``, the max-cut SDP of an
+Erdos-Renyi graph (n = 4096, edge probability 0.01, weights +-1) solved by
+PFAM with a dense FP64 iteration matrix, p = 32, degree 4, up to 200
+iterations or relative KKT <= 1e-4 (checked every 10 iterations).
+
+Metric: solves/s (whole job), with p50/p99 solve latency; the dominant
+kernel (the dense FP64 filter product) is reported against its roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs as replicas (torchrun, one process per GPU, no data-path
+collective): every rank solves its own copy of the workload, value = all
+solves / max-over-ranks time.  ``--impl reference`` times the CPU oracle on
+this host's cores (a bounded sample of each solve).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pf_synthetic as syn  # noqa: E402
+
+WORKLOAD = "maxcut_n4096"
+TOL = 1e-4
+CHECK_EVERY = 10
+FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 nominal (no measured FP64 peak is provided)
+FP64_CUBLAS_MEASURED = 1.09    # torch float64 matmul 16384x16384x64 on this pool (context)
+# dram bytes per launch of the dominant kernel from the committed ncu capture
+# (None until a capture of the current kernel exists)
+NCU_TRAFFIC_BYTES = None
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (200 ms period)."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle, bounded samples
+# ---------------------------------------------------------------------------
+
+def oracle_sample(cfg, inst, iters_sample: int):
+    """Time `iters_sample` PFAM iterations of the oracle; returns seconds."""
+    import scipy.sparse as sp
+    from oracle import pf_oracle as o
+    C = sp.csr_matrix((inst.C.vals, inst.C.colind, inst.C.rowptr), shape=(inst.n, inst.n))
+    t = o.maxcut_step_size(C)
+    t0 = time.perf_counter()
+    st = o.maxcut_init(C, inst.U0_raw[:, :cfg["p"]], t)
+    for _ in range(iters_sample):
+        st, info = o.maxcut_pfam_step(C, st, t, cfg["degree"])
+    return time.perf_counter() - t0
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    cfg, inst = syn.make_workload(WORKLOAD)
+    iters_sample = 2
+    for _ in range(args.warmup):
+        oracle_sample(cfg, inst, iters_sample)
+    times = []
+    for _ in range(args.steps):
+        times.append(oracle_sample(cfg, inst, iters_sample))
+    per_solve = [tt * cfg["iters"] / iters_sample for tt in times]
+    value = len(per_solve) / sum(per_solve)
+    sample = (f"{iters_sample} of {cfg['iters']} PFAM iterations per step (initial state + "
+              f"iterations), scaled to a {cfg['iters']}-iteration solve")
+    line = {
+        "impl": "reference", "metric": "solves/s", "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(per_solve), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(cfg),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": host_cores(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(cfg):
+    return {"workload": WORKLOAD, "problem": "max-cut SDP (PFAM, dense FP64 iteration matrix)",
+            "n": cfg["n"], "p": cfg["p"], "degree": cfg["degree"], "max_iters": cfg["iters"],
+            "tol_kkt": TOL, "graph": "Erdos-Renyi p=0.01, weights +-1",
+            "l2": "inputs larger than L2: Z is n^2 FP64 = 134 MB > 129 MB L2, re-written "
+                  "every iteration"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    import paper_1904_10585_gb300 as pkg
+    from paper_1904_10585_gb300 import solver as S
+
+    cfg, inst = syn.make_workload(WORKLOAD)
+    n, p, d, iters = cfg["n"], cfg["p"], cfg["degree"], cfg["iters"]
+    stream = torch.cuda.Stream(device=dev)
+    ctx = S.Context(p=p, n_max=n, degree=d, stream=stream)
+    rp, ci, cv = S.csr_to_device(inst.C, dev, torch.float64)
+    U0 = torch.from_numpy(np.ascontiguousarray(inst.U0_raw[:, :p])).to(dev)
+    pr = S.maxcut_problem(rp, ci, cv, U0)
+
+    def solve_once(problem):
+        problem.U.copy_(U0)             # fresh start block (on the library stream below)
+        S.problem_init(ctx, problem)
+        return S.solve(ctx, problem, iters, TOL, CHECK_EVERY)
+
+    # launch counting (non-graph calls): init + one step
+    with torch.cuda.stream(stream):
+        c0 = pkg.pf_kernel_launch_count()
+        pr.U.copy_(U0)
+        S.problem_init(ctx, pr)
+        c1 = pkg.pf_kernel_launch_count()
+        S.prox_step(ctx, pr, want_info=False)
+        c2 = pkg.pf_kernel_launch_count()
+    init_launches, step_launches = c1 - c0, c2 - c1
+    if args.profile:
+        # short run for profiler captures: a few more non-graph iterations
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                S.prox_step(ctx, pr, want_info=False)
+        stream.synchronize()
+        print(json.dumps({"profile_run": WORKLOAD, "launches_per_iteration": step_launches}))
+        ctx.close()
+        return 0
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            solve_once(pr)
+    stream.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    results = []
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(args.steps):
+            results.append(solve_once(pr))
+            ev[k + 1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    iters_run = [int(r.iters) for r in results]
+    gpu_launches = sum(init_launches + it * step_launches for it in iters_run)
+
+    # dominant kernel: the dense FP64 product Y = Z X (split-K GEMM + combine),
+    # timed with CUDA events on the library stream over R launches on the
+    # resident iteration matrix left by the timed solves.
+    R = 20
+    X = pr.U.clone()
+    Y = torch.empty_like(X)
+    op = S.dense_operator(pr.Z)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            S.apply(ctx, op, X, Y)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(R):
+            S.apply(ctx, op, X, Y)
+        e1.record(stream)
+    stream.synchronize()
+    apply_ms = e0.elapsed_time(e1) / R
+    flops = 2.0 * n * n * p
+    achieved = flops / (apply_ms * 1e-3) / 1e12
+
+    # end to end through the public API: host (pinned) inputs copied in and the
+    # solution factors read back inside the timed region
+    h_rp = rp.cpu().pin_memory()
+    h_ci = ci.cpu().pin_memory()
+    h_cv = cv.cpu().pin_memory()
+    h_u0 = U0.cpu().pin_memory()
+    h_V = torch.empty((n, p), dtype=torch.float64).pin_memory()
+    h_th = torch.empty((p,), dtype=torch.float64).pin_memory()
+    d_rp, d_ci, d_cv = torch.empty_like(rp), torch.empty_like(ci), torch.empty_like(cv)
+    d_u0 = torch.empty_like(U0)
+    pe = S.maxcut_problem(d_rp, d_ci, d_cv, d_u0)
+    h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_ci, h_cv, h_u0))
+    d2h = h_V.numel() * 8 + h_th.numel() * 8
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def e2e_once():
+        d_rp.copy_(h_rp, non_blocking=True)
+        d_ci.copy_(h_ci, non_blocking=True)
+        d_cv.copy_(h_cv, non_blocking=True)
+        d_u0.copy_(h_u0, non_blocking=True)
+        pe.U.copy_(d_u0)
+        S.problem_init(ctx, pe)
+        S.solve(ctx, pe, iters, TOL, CHECK_EVERY)
+        h_V.copy_(pe.V, non_blocking=True)
+        h_th.copy_(pe.theta, non_blocking=True)
+        stream.synchronize()
+
+    with torch.cuda.stream(stream):
+        e2e_once()                      # warm-up (captures this problem's graph)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            e2e_once()
+    e2e_s = time.perf_counter() - t0
+
+    # max over ranks
+    tot = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+    if pg:
+        pg.all_reduce(tot, op=pg.ReduceOp.MAX)
+    total_ms, e2e_s = float(tot[0]), float(tot[1])
+    value = world * args.steps / (total_ms * 1e-3)
+    e2e_value = world * e2e_steps / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters_sample = 15
+        secs = oracle_sample(cfg, inst, iters_sample)
+        cpu = {"value": 1.0 / (secs * iters / iters_sample), "unit": "solves/s",
+               "cores": host_cores(), "kind": "oracle",
+               "sample": f"initial state + {iters_sample} of {iters} PFAM iterations of the same "
+                         f"workload ({secs:.1f} s), scaled to one {iters}-iteration solve"}
+
+    last = results[-1].last
+    line = {
+        "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(cfg),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "solve": {"iters": iters_run[-1], "kkt": float(last.kkt), "obj": float(last.obj),
+                  "pinf": float(last.pinf), "dinf": float(last.dinf), "gap": float(last.gap),
+                  "r_plus": int(last.r_plus), "reached_tol": bool(last.kkt <= TOL)},
+        "roofline": {"kernel": "k_gemm_f64_splitk + k_combine (Y = Z X, dense FP64 filter product)",
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": NCU_TRAFFIC_BYTES,
+                     "flops_per_launch": flops, "avg_launch_ms": apply_ms,
+                     "peak_source": "recipe nominal FP64 1.25 TFLOP/s (no measured FP64 peak; "
+                                    f"cuBLAS DGEMM reached {FP64_CUBLAS_MEASURED} on this pool)"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": gpu_launches,
+        "launches_per_iteration": step_launches,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="short run for profiler captures (init + 4 iterations, no timing)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

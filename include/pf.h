@@ -1,0 +1,215 @@
+/*
+ * pf.h - C ABI of the GB300 polynomial-filtered subspace extraction library
+ * (libpf.so).
+ *
+ * The library computes, on one GPU, the hot path of the polynomial-filtered
+ * proximal-gradient / ADMM framework of "Low-rank Matrix Optimization Using
+ * Polynomial-filtered Subspace Extraction": a warm-started Chebyshev filter on
+ * an n x p block (Sec. 2.1, Eqs. (cheb), (cheb-linear-map),
+ * (subspace-update)), CholQR2 orthonormalisation, the Rayleigh-Ritz
+ * projection with a p x p eigensolve (Sec. 2.2, Eq. (RR)), and the low-rank
+ * prox reconstruction of PFPG (Eqs. (pfpg1)-(pfpg2)) and PFAM
+ * (Eqs. (PFAM1)-(PFAM2)).
+ *
+ * Conventions shared by every call:
+ *  - All array pointers are DEVICE pointers owned by the caller, unless a
+ *    parameter says "host".  The library never frees caller memory.
+ *  - A context owns only its workspace, allocated by pf_create; no call
+ *    allocates device memory afterwards (pf_solve's CUDA graph is the one
+ *    exception: it is instantiated once per context and problem shape).
+ *  - Calls are asynchronous and ordered on the stream given to pf_create.
+ *    Calls that return host values (pf_prox_step with a non-NULL info,
+ *    pf_solve, pf_problem_init) synchronise that stream.
+ *  - Dense blocks are row-major: element (i, j) of an n x p block U with
+ *    leading dimension ldu >= p is U[i*ldu + j].  A dense symmetric n x n
+ *    matrix A is row-major with lda >= n.
+ *  - Errors are returned as pf_status and never abort.  A CUDA error is
+ *    reported as PF_ERR_CUDA; the context must then be destroyed.  The text
+ *    of the last error is available from pf_last_error.
+ *  - p (the block width) is fixed per context, 1 <= p <= PF_MAX_P, and every
+ *    call needs p <= n.
+ *  - Symbols are plain C; no CUDA, C++ or PyTorch types appear here.  The
+ *    stream is passed as an opaque pointer (a cudaStream_t value; NULL means
+ *    the legacy default stream).
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF_MAX_P 64
+
+typedef struct pf_ctx pf_ctx;
+
+typedef enum {
+  PF_OK = 0,
+  PF_ERR_INVALID_ARG = 1,      /* a size, pointer or option is out of range      */
+  PF_ERR_OOM = 2,              /* workspace allocation failed in pf_create        */
+  PF_ERR_CUDA = 3,             /* a CUDA call or kernel failed (context unusable) */
+  PF_ERR_CHOL_BREAKDOWN = 4,   /* CholQR2 failed even with the shifted pass       */
+  PF_ERR_NAN = 5,              /* a non-finite value reached the Ritz values      */
+  PF_ERR_NOT_CONVERGED = 6,    /* pf_solve hit max_iter above its tolerance       */
+  PF_ERR_DEVICE_TIMEOUT = 7,   /* a bounded device wait ran out                   */
+  PF_ERR_UNSUPPORTED = 8       /* valid request this build does not implement     */
+} pf_status;
+
+/* Iteration-matrix kinds accepted by pf_filter / pf_rayleigh_ritz. */
+typedef enum {
+  PF_OP_DENSE = 0,           /* op(X) = A X, A dense symmetric FP64 n x n             */
+  PF_OP_LOWRANK_SPARSE = 1   /* op(X) = Uf diag(lam) Uf^T X + sparse_scale S X + shift X */
+} pf_op_kind;
+
+typedef enum { PF_PREC_FP64 = 0, PF_PREC_TF32 = 1, PF_PREC_BF16 = 2 } pf_precision;
+
+typedef enum { PF_PROBLEM_MAXCUT = 0, PF_PROBLEM_COMPLETION = 1 } pf_problem_kind;
+
+/* Solver options (Sec. 2.2-2.3 and Sec. 4: degree d, q, eta, block width p). */
+typedef struct {
+  int32_t p;            /* block width, 1..PF_MAX_P                                  */
+  int32_t degree;       /* Chebyshev degree d >= 1 (Eq. (cheb))                       */
+  int32_t degree_max;   /* upper degree for the adaptive low-precision ladder         */
+  int32_t q;            /* filter applications before orth (q = 1 is the only value   */
+                        /* this build accepts; Eqs. (pfpg2)/(PFAM2) allow 1..3)       */
+  double eta;           /* interval parameter of Sec. 4.1 (0 < eta < 1), e.g. 0.1    */
+  int32_t precision;    /* pf_precision of the filter products                       */
+  int32_t adaptive;     /* nonzero: raise degree/precision when the KKT stalls        */
+} pf_options;
+
+/*
+ * Iteration matrix descriptor (all pointers device, caller-owned, read only).
+ * PF_OP_DENSE:          A (n x n, row-major, lda), symmetric.  Optional
+ *                       low-precision shadow A_lp (bf16 or fp32 per the
+ *                       context precision) holding A / lp_scale, lda_lp.
+ * PF_OP_LOWRANK_SPARSE: op(X) = Uf diag(lam) Uf^T X + sparse_scale * S X
+ *                       + shift * X, with Uf n x r (row-major, lduf), lam r
+ *                       values (r <= PF_MAX_P), and S a symmetric CSR matrix
+ *                       (rowptr n+1 int32, colind nnz int32 sorted per row,
+ *                       vals nnz FP64).
+ */
+typedef struct {
+  int32_t kind;
+  int64_t n;
+  const double *A; int64_t lda;
+  const void *A_lp; int64_t lda_lp; double lp_scale;
+  const double *Uf; int64_t lduf; const double *lam; int32_t r;
+  const int32_t *rowptr; const int32_t *colind; const double *vals; int64_t nnz;
+  double sparse_scale; double shift;
+} pf_operator;
+
+/*
+ * Problem state for pf_prox_step / pf_solve.  Data (read only):
+ *  MAXCUT:      C = -L/4 as a symmetric CSR with its diagonal (vals_f64).
+ *  COMPLETION:  the sampled entries of M on Omega as a symmetric CSR
+ *               (vals_f32); mu > 0; t the step size.
+ * Resident state (read and written by every step; device, caller-owned):
+ *  U     n x p block (ldu), the warm start of the filter.  On entry to
+ *        pf_problem_init it holds the start block (any full-rank n x p).
+ *  V     n x p Ritz vectors of the last Rayleigh-Ritz step (ldv); with theta
+ *        they hold the low-rank iterate X = V diag(max(theta,0)) V^T.
+ *  theta p Ritz values of the last step, descending.
+ *  Z     MAXCUT only: dense FP64 n x n iteration matrix (ldz).
+ *  lam   MAXCUT only: n-vector lambda of the last DRS update.
+ *  S     COMPLETION only: nnz FP64 values of P_Omega(X - M) (workspace).
+ * t: MAXCUT step; if t <= 0 on entry to pf_problem_init it is set to
+ *    10 sqrt(n)/||C||_F.  COMPLETION step (t = 1 matches the Lipschitz
+ *    constant of P_Omega).
+ */
+typedef struct {
+  int32_t kind;
+  int64_t n;
+  const int32_t *rowptr; const int32_t *colind;
+  const double *vals_f64; const float *vals_f32; int64_t nnz;
+  double t; double mu;
+  double *U; int64_t ldu;
+  double *V; int64_t ldv;
+  double *theta;
+  double *Z; int64_t ldz;
+  double *lam;
+  double *S;
+  int64_t iter;          /* host-side counter, advanced by each step */
+} pf_problem;
+
+/* Per-step report (host struct).  MAXCUT: obj = <C, X~>, pinf/dinf/gap as in
+ * the standard SDP report of Sec. 5.4; COMPLETION: obj = 1/2||P_Omega(X-M)||^2
+ * + mu tr X and kkt the relative fixed-point residual; pinf/dinf/gap are 0. */
+typedef struct {
+  double a, b;               /* filter interval used by the step (Sec. 4.1) */
+  double obj, kkt, pinf, dinf, gap;
+  double theta_max, theta_min;
+  int32_t r_plus;            /* number of positive Ritz values               */
+  int32_t flags;             /* bit 0: shifted CholQR pass used; bit 1: Cholesky
+                                breakdown; bit 2: non-finite Ritz value        */
+  int32_t degree;            /* degree used by the step                      */
+  int32_t precision;         /* precision used by the step                   */
+} pf_iter_info;
+
+typedef struct {
+  int64_t iters;
+  double kkt, obj;
+  pf_iter_info last;
+} pf_result;
+
+/* Create a context for problems of size n <= n_max with the given options.
+ * Allocates all workspace.  stream: cudaStream_t (opaque).  out: host. */
+pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx **out);
+
+/* Release the context and its workspace (after synchronising its stream). */
+pf_status pf_destroy(pf_ctx *ctx);
+
+/* U <- orth(rho(op) U) with rho(t) = T_d((t - (a+b)/2)/((b-a)/2)),
+ * Sec. 2.1 Eqs. (cheb), (cheb-linear-map), (subspace-update); orth is
+ * CholQR2 (QR with positive diagonal R).  a < b host scalars, degree >= 1,
+ * U n x p device (ldu >= p), overwritten in place. */
+pf_status pf_filter(pf_ctx *ctx, const pf_operator *op, double a, double b, int32_t degree,
+                    double *U, int64_t ldu);
+
+/* Rayleigh-Ritz on span(Q), Sec. 2.2 Eq. (RR): H = Q^T op(Q), H = Y Theta Y^T,
+ * V = Q Y.  Q n x p orthonormal (ldq), V n x p out (ldv), theta p out
+ * (descending), resid p out (||op(v_i) - theta_i v_i||_2); resid may be NULL. */
+pf_status pf_rayleigh_ritz(pf_ctx *ctx, const pf_operator *op, const double *Q, int64_t ldq,
+                           double *V, int64_t ldv, double *theta, double *resid);
+
+/* Y = op(X): one product of the iteration matrix with an n x p block, the
+ * building block of the Chebyshev recurrence of Sec. 2.1 (Eq. (cheb)).
+ * X, Y device n x p (ldx, ldy >= p), distinct.  Asynchronous. */
+pf_status pf_apply(pf_ctx *ctx, const pf_operator *op, const double *X, int64_t ldx, double *Y,
+                   int64_t ldy);
+
+/* Prepare the resident state of a problem: MAXCUT sets Z = Z^1 = I - t offdiag(C)
+ * (the DRS image of Z^0 = 0), lam = -t diag(C) - 1, theta = 0; COMPLETION sets
+ * theta = 0 (X^0 = 0).  Computes t for MAXCUT when t <= 0.  Synchronises. */
+pf_status pf_problem_init(pf_ctx *ctx, pf_problem *prob);
+
+/* One PFAM (MAXCUT, Eqs. (PFAM1)-(PFAM2)) or PFPG (COMPLETION,
+ * Eqs. (pfpg1)-(pfpg2)) iteration: interval, filter, CholQR2, Rayleigh-Ritz,
+ * prox/DRS update, KKT.  info (host) may be NULL; when given, the call
+ * synchronises and fills it. */
+pf_status pf_prox_step(pf_ctx *ctx, pf_problem *prob, pf_iter_info *info);
+
+/* Iterate pf_prox_step until kkt <= tol (checked every check_every steps,
+ * tol <= 0 disables the test) or max_iter steps.  The step is captured once
+ * in a CUDA graph and replayed.  out (host) receives the final report.
+ * Returns PF_ERR_NOT_CONVERGED if tol > 0 was not reached. */
+pf_status pf_solve(pf_ctx *ctx, pf_problem *prob, int64_t max_iter, double tol,
+                   int32_t check_every, pf_result *out);
+
+/* Copy the report of the most recent step to host (synchronises). */
+pf_status pf_get_info(pf_ctx *ctx, pf_iter_info *info);
+
+/* Number of kernels this library has enqueued in this process (host-side
+ * count; a replayed CUDA graph adds nothing).  Instrumentation with no
+ * counterpart in the paper: it lets a caller count the GPU launches of a
+ * step by differencing around a non-graph call. */
+int64_t pf_kernel_launch_count(void);
+
+const char *pf_status_string(pf_status s);
+const char *pf_last_error(const pf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

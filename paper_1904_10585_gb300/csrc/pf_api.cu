@@ -1,0 +1,591 @@
+// C ABI of libpf: context and workspace management, the filter and
+// Rayleigh-Ritz entry points, the PFAM / PFPG steps and the graph-captured
+// solve loop.  Every step of the path is a kernel launched on the context's
+// stream; the host only validates arguments, enqueues and (where a call
+// returns host values) synchronises.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pf_internal.cuh"
+
+using namespace pf;
+
+namespace pf {
+std::atomic<int64_t> g_launches{0};
+}
+
+struct pf_ctx {
+  pf_options opt;
+  int64_t n_max;
+  int p;
+  cudaStream_t stream;
+  Workspace ws;
+  void *base;
+  size_t bytes;
+  char err[512];
+  // graph of one step, cached per problem description
+  cudaGraphExec_t gexec;
+  pf_problem gkey;
+  bool have_graph;
+};
+
+namespace {
+
+pf_status set_err(pf_ctx *ctx, pf_status s, const char *fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+#define PF_CUDA(call)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return set_err(ctx, PF_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                     __LINE__);                                                                  \
+  } while (0)
+
+#define PF_TRY(expr)                  \
+  do {                                \
+    pf_status s_ = (expr);            \
+    if (s_ != PF_OK) return s_;       \
+  } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+pf_status make_op(pf_ctx *ctx, const pf_operator *op, Op *out) {
+  if (!op) return set_err(ctx, PF_ERR_INVALID_ARG, "operator is NULL");
+  if (op->n < ctx->p || op->n > ctx->n_max)
+    return set_err(ctx, PF_ERR_INVALID_ARG, "operator n=%lld outside [p=%d, n_max=%lld]",
+                   (long long)op->n, ctx->p, (long long)ctx->n_max);
+  Op o = {};
+  o.kind = op->kind;
+  o.n = (int)op->n;
+  if (op->kind == PF_OP_DENSE) {
+    const bool lp = ctx->opt.precision != PF_PREC_FP64;
+    if (!lp && (!op->A || op->lda < op->n))
+      return set_err(ctx, PF_ERR_INVALID_ARG, "dense operator needs A and lda >= n");
+    if (lp) {
+      const int esz = ctx->opt.precision == PF_PREC_TF32 ? 4 : 2;
+      if (!op->A_lp || op->lda_lp < op->n || (op->lda_lp * esz) % 16 != 0 ||
+          ((uintptr_t)op->A_lp & 15) != 0 || !(op->lp_scale > 0.0))
+        return set_err(ctx, PF_ERR_INVALID_ARG,
+                       "low-precision dense operator needs A_lp 16-byte aligned, lda_lp >= n with "
+                       "a 16-byte row pitch, and lp_scale > 0");
+    }
+    o.A = op->A;
+    o.lda = op->lda;
+    o.A_lp = op->A_lp;
+    o.lda_lp = op->lda_lp;
+    o.lp_scale = op->lp_scale;
+  } else if (op->kind == PF_OP_LOWRANK_SPARSE) {
+    if (op->r < 0 || op->r > kMaxP)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "low-rank width r=%d outside [0, %d]", op->r, kMaxP);
+    if (op->r > 0 && (!op->Uf || !op->lam || op->lduf < op->r))
+      return set_err(ctx, PF_ERR_INVALID_ARG, "low-rank part needs Uf, lam and lduf >= r");
+    if (op->nnz > 0 && (!op->rowptr || !op->colind || !op->vals))
+      return set_err(ctx, PF_ERR_INVALID_ARG, "sparse part needs rowptr, colind and vals");
+    if (op->nnz < 0 || op->nnz > INT32_MAX)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "nnz out of range");
+    o.Uf = op->Uf;
+    o.lduf = op->lduf;
+    o.lam = op->lam;
+    o.r = op->r;
+    o.clamp = 0;
+    o.rowptr = op->rowptr;
+    o.colind = op->colind;
+    o.vals = op->nnz > 0 ? op->vals : nullptr;
+    o.sscale = op->sparse_scale;
+    o.shift = op->shift;
+    if (op->nnz == 0 && op->rowptr == nullptr) {
+      o.vals = nullptr;  // pure low-rank + shift operator
+    }
+  } else {
+    return set_err(ctx, PF_ERR_INVALID_ARG, "unknown operator kind %d", op->kind);
+  }
+  *out = o;
+  return PF_OK;
+}
+
+pf_status apply(pf_ctx *ctx, const Op &op, const double *X, int64_t ldx, const double *Yprev,
+                int64_t ldp, double *Ynext, int64_t ldn, int mode) {
+  if (op.kind == PF_OP_DENSE)
+    PF_CUDA(launch_dense_apply(ctx->stream, ctx->ws, op, X, ldx, Yprev, ldp, Ynext, ldn, mode));
+  else
+    PF_CUDA(launch_lowrank_sparse_apply(ctx->stream, ctx->ws, op, X, ldx, Yprev, ldp, Ynext, ldn,
+                                        mode));
+  return PF_OK;
+}
+
+// Q = orth(Y) by CholQR2 (a third pass follows a shifted first pass).
+pf_status cholqr2(pf_ctx *ctx, const double *Y, int64_t ldy, double *U, int64_t ldu, int n) {
+  const int p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  const Workspace &ws = ctx->ws;
+  int nb = 0;
+  PF_CUDA(launch_gram(s, ws, Y, ldy, Y, ldy, n, p, p, 0, &nb));
+  PF_CUDA(launch_chol_inv(s, ws, nb, n, p, 0));
+  PF_CUDA(launch_apply_right(s, ws, Y, ldy, U, ldu, n, p, ws.Rinv, 1, 0));
+  for (int pass = 1; pass <= 2; ++pass) {
+    const int cond = pass == 2 ? 1 : 0;
+    PF_CUDA(launch_gram(s, ws, U, ldu, U, ldu, n, p, p, cond, &nb));
+    PF_CUDA(launch_chol_inv(s, ws, nb, n, p, pass));
+    PF_CUDA(launch_apply_right(s, ws, U, ldu, U, ldu, n, p, ws.Rinv, 1, cond));
+  }
+  return PF_OK;
+}
+
+// Low-precision filter (tensor cores): fp32 recurrence, bf16/tf32 operands,
+// then CholQR2 in FP64.
+pf_status filter_core_lp(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
+  const int p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  const Workspace &ws = ctx->ws;
+  const bool tf32 = ctx->opt.precision == PF_PREC_TF32;
+  PF_CUDA(launch_prep_lp(s, ws, tf32, U, ldu, op.n, ws.U32, ws.Xt[0]));
+  for (int j = 0; j < degree; ++j) {
+    const float *cur = j == 0 ? ws.U32 : ws.Y32[(j - 1) & 1];
+    const float *prev = j == 1 ? ws.U32 : ws.Y32[j & 1];
+    float *next = ws.Y32[j & 1];
+    void *xt_next = (j + 1 < degree) ? ws.Xt[(j + 1) & 1] : nullptr;
+    PF_CUDA(launch_tc_product(s, ws, tf32, op.A_lp, op.lda_lp, op.lp_scale, op.n, ws.Xt[j & 1],
+                              cur, prev, next, xt_next, j == 0 ? MODE_FIRST : MODE_RECUR));
+  }
+  PF_CUDA(launch_f32_to_f64(s, ws, ws.Y32[(degree - 1) & 1], (int64_t)op.n * p, ws.Y[0]));
+  return cholqr2(ctx, ws.Y[0], p, U, ldu, op.n);
+}
+
+// U <- orth(rho(op) U) with the interval already in the device parameters.
+pf_status filter_core(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
+  const int p = ctx->p;
+  if (op.kind == PF_OP_DENSE && op.A_lp != nullptr && ctx->opt.precision != PF_PREC_FP64)
+    return filter_core_lp(ctx, op, U, ldu, degree);
+  double *const *Y = ctx->ws.Y;
+  PF_TRY(apply(ctx, op, U, ldu, nullptr, 0, Y[0], p, MODE_FIRST));
+  for (int j = 1; j < degree; ++j) {
+    const double *cur = Y[(j - 1) & 1];
+    const double *prev = (j == 1) ? U : Y[j & 1];
+    const int64_t ldprev = (j == 1) ? ldu : p;
+    PF_TRY(apply(ctx, op, cur, p, prev, ldprev, Y[j & 1], p, MODE_RECUR));
+  }
+  return cholqr2(ctx, Y[(degree - 1) & 1], p, U, ldu, op.n);
+}
+
+pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, double *V, int64_t ldv,
+                  double *theta, double *resid) {
+  const int p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  const Workspace &ws = ctx->ws;
+  PF_TRY(apply(ctx, op, Q, ldq, nullptr, 0, ws.W, p, MODE_PLAIN));
+  int nb = 0;
+  PF_CUDA(launch_gram(s, ws, Q, ldq, ws.W, p, op.n, p, p, 0, &nb));
+  PF_CUDA(launch_jacobi(s, ws, nb, p, theta));
+  PF_CUDA(launch_rotate_resid(s, ws, Q, ldq, ws.W, p, op.n, p, theta, V, ldv, resid));
+  return PF_OK;
+}
+
+pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
+  if (!pr) return set_err(ctx, PF_ERR_INVALID_ARG, "problem is NULL");
+  const int p = ctx->p;
+  if (pr->n < p || pr->n > ctx->n_max)
+    return set_err(ctx, PF_ERR_INVALID_ARG, "problem n=%lld outside [p=%d, n_max=%lld]",
+                   (long long)pr->n, p, (long long)ctx->n_max);
+  if (!pr->rowptr || !pr->colind || pr->nnz < 0 || pr->nnz > INT32_MAX)
+    return set_err(ctx, PF_ERR_INVALID_ARG, "problem needs a CSR matrix (rowptr, colind, nnz)");
+  if (!pr->U || pr->ldu < p || !pr->V || pr->ldv < p || !pr->theta)
+    return set_err(ctx, PF_ERR_INVALID_ARG, "problem needs U, V (ld >= p) and theta");
+  if (pr->kind == PF_PROBLEM_MAXCUT) {
+    if (!pr->vals_f64) return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut needs vals_f64 (C)");
+    if (!pr->Z || pr->ldz < pr->n || !pr->lam)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut needs Z (ldz >= n) and lam");
+  } else if (pr->kind == PF_PROBLEM_COMPLETION) {
+    if (!pr->vals_f32 || !pr->S)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "completion needs vals_f32 (M on Omega) and S");
+    if (!(pr->t > 0.0) || !(pr->mu >= 0.0))
+      return set_err(ctx, PF_ERR_INVALID_ARG, "completion needs t > 0 and mu >= 0");
+  } else {
+    return set_err(ctx, PF_ERR_INVALID_ARG, "unknown problem kind %d", pr->kind);
+  }
+  return PF_OK;
+}
+
+// One PFAM / PFPG step, enqueued only (graph-capturable).
+pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
+  const int p = ctx->p;
+  const int n = (int)pr->n;
+  cudaStream_t s = ctx->stream;
+  const Workspace &ws = ctx->ws;
+  const int degree = ctx->opt.degree;
+  if (pr->kind == PF_PROBLEM_MAXCUT) {
+    PF_CUDA(launch_interval(s, ws, PF_PROBLEM_MAXCUT, pr->rowptr, pr->colind, pr->vals_f64, n,
+                            pr->lam, pr->theta, p));
+    Op op = {};
+    op.kind = PF_OP_DENSE;
+    op.n = n;
+    op.A = pr->Z;
+    op.lda = pr->ldz;
+    PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
+    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_CUDA(launch_maxcut_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv,
+                                 pr->theta, pr->Z, pr->ldz, pr->lam));
+  } else {
+    PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
+    PF_CUDA(launch_completion_residual(s, ws, pr->rowptr, pr->colind, pr->vals_f32, n, p, ws.Vprev,
+                                       p, ws.thprev, pr->S));
+    PF_CUDA(launch_interval(s, ws, PF_PROBLEM_COMPLETION, pr->rowptr, pr->colind, pr->S, n, nullptr,
+                            ws.thprev, p));
+    Op op = {};
+    op.kind = PF_OP_LOWRANK_SPARSE;
+    op.n = n;
+    op.Uf = ws.Vprev;
+    op.lduf = p;
+    op.lam = ws.thprev;
+    op.r = p;
+    op.clamp = 1;
+    op.rowptr = pr->rowptr;
+    op.colind = pr->colind;
+    op.vals = pr->S;
+    op.sscale = -pr->t;
+    op.shift = -pr->t * pr->mu;
+    PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
+    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_CUDA(launch_completion_kkt(s, ws, pr->V, pr->ldv, pr->theta, n, p));
+  }
+  return PF_OK;
+}
+
+void params_to_info(const Params &h, pf_iter_info *info) {
+  info->a = h.a;
+  info->b = h.b;
+  info->obj = h.obj;
+  info->kkt = h.kkt;
+  info->pinf = h.pinf;
+  info->dinf = h.dinf;
+  info->gap = h.gap;
+  info->theta_max = h.theta_max;
+  info->theta_min = h.theta_min;
+  info->r_plus = h.r_plus;
+  info->flags = h.flags;
+  info->degree = h.degree;
+  info->precision = h.precision;
+}
+
+pf_status read_params(pf_ctx *ctx, Params *h) {
+  PF_CUDA(cudaMemcpyAsync(h, ctx->ws.prm, sizeof(Params), cudaMemcpyDeviceToHost, ctx->stream));
+  PF_CUDA(cudaStreamSynchronize(ctx->stream));
+  return PF_OK;
+}
+
+bool same_problem(const pf_problem &a, const pf_problem &b) {
+  return a.kind == b.kind && a.n == b.n && a.rowptr == b.rowptr && a.colind == b.colind &&
+         a.vals_f64 == b.vals_f64 && a.vals_f32 == b.vals_f32 && a.nnz == b.nnz && a.t == b.t &&
+         a.mu == b.mu && a.U == b.U && a.ldu == b.ldu && a.V == b.V && a.ldv == b.ldv &&
+         a.theta == b.theta && a.Z == b.Z && a.ldz == b.ldz && a.lam == b.lam && a.S == b.S;
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx **out) {
+  if (!out) return PF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!opt) return PF_ERR_INVALID_ARG;
+  if (opt->p < 1 || opt->p > kMaxP || opt->degree < 1 || opt->degree > 64 || opt->q != 1 ||
+      !(opt->eta > 0.0 && opt->eta < 1.0) || n_max < opt->p || n_max > (int64_t)INT32_MAX / 2)
+    return PF_ERR_INVALID_ARG;
+  if (opt->precision != PF_PREC_FP64 && opt->precision != PF_PREC_BF16 &&
+      opt->precision != PF_PREC_TF32)
+    return PF_ERR_INVALID_ARG;
+  const bool lp = opt->precision != PF_PREC_FP64;
+  pf_ctx *ctx = new (std::nothrow) pf_ctx();
+  if (!ctx) return PF_ERR_OOM;
+  ctx->opt = *opt;
+  ctx->n_max = n_max;
+  ctx->p = opt->p;
+  ctx->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = configure_skinny();
+  if (e == cudaSuccess && lp) e = configure_tc();
+  if (e != cudaSuccess) {
+    delete ctx;
+    return PF_ERR_CUDA;
+  }
+  const int p = opt->p;
+  const size_t np = (size_t)n_max * p;
+  // largest split-K partial buffer over all n <= n_max
+  size_t part = 0;
+  for (int n = p; n <= n_max; ++n) {
+    int kc = 0;
+    const size_t v = (size_t)dense_splits(n, sms, &kc) * n * p;
+    if (v > part) part = v;
+  }
+  const size_t sq = (size_t)kMaxP * kMaxP;
+  size_t off[16];
+  size_t tot = 0;
+  const size_t sizes[] = {np, np, np, np, part, (size_t)kMaxGramBlocks * sq,
+                          (size_t)kRedSlots * kMaxRedBlocks * kRedWidth, sq, sq, sq, kMaxP, kMaxP};
+  const int nsz = sizeof(sizes) / sizeof(sizes[0]);
+  for (int i = 0; i < nsz; ++i) {
+    off[i] = tot;
+    tot += align_up(sizes[i] * sizeof(double));
+  }
+  const size_t prm_off = tot;
+  tot += align_up(sizeof(Params));
+  // low-precision buffers: Y32[2], U32 (fp32 n x p); Xt[2] (p x ldxt, 4-byte elements)
+  const int64_t ldxt = ((n_max + 63) / 64) * 64;
+  size_t lp_off[5] = {0, 0, 0, 0, 0};
+  if (lp) {
+    for (int i = 0; i < 3; ++i) {
+      lp_off[i] = tot;
+      tot += align_up(np * sizeof(float));
+    }
+    for (int i = 3; i < 5; ++i) {
+      lp_off[i] = tot;
+      tot += align_up((size_t)p * ldxt * sizeof(float));
+    }
+  }
+  void *base = nullptr;
+  if (cudaMalloc(&base, tot) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return PF_ERR_OOM;
+  }
+  char *b = (char *)base;
+  Workspace &ws = ctx->ws;
+  ws.n_max = (int)n_max;
+  ws.p = p;
+  ws.num_sms = sms;
+  ws.Y[0] = (double *)(b + off[0]);
+  ws.Y[1] = (double *)(b + off[1]);
+  ws.W = (double *)(b + off[2]);
+  ws.Vprev = (double *)(b + off[3]);
+  ws.part = (double *)(b + off[4]);
+  ws.gpart = (double *)(b + off[5]);
+  ws.red = (double *)(b + off[6]);
+  ws.Rinv = (double *)(b + off[7]);
+  ws.Yeig = (double *)(b + off[8]);
+  ws.T = (double *)(b + off[9]);
+  ws.thprev = (double *)(b + off[10]);
+  ws.resid = (double *)(b + off[11]);
+  ws.prm = (Params *)(b + prm_off);
+  ws.ldxt = ldxt;
+  if (lp) {
+    ws.Y32[0] = (float *)(b + lp_off[0]);
+    ws.Y32[1] = (float *)(b + lp_off[1]);
+    ws.U32 = (float *)(b + lp_off[2]);
+    ws.Xt[0] = (void *)(b + lp_off[3]);
+    ws.Xt[1] = (void *)(b + lp_off[4]);
+  }
+  ctx->base = base;
+  ctx->bytes = tot;
+  if (cudaMemsetAsync(base, 0, tot, ctx->stream) != cudaSuccess ||
+      launch_params_init(ctx->stream, ws.prm, opt->eta, 0.0, 0.0, opt->degree, opt->precision) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaFree(base);
+    delete ctx;
+    return PF_ERR_CUDA;
+  }
+  *out = ctx;
+  return PF_OK;
+}
+
+pf_status pf_destroy(pf_ctx *ctx) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->have_graph) cudaGraphExecDestroy(ctx->gexec);
+  cudaFree(ctx->base);
+  delete ctx;
+  return PF_OK;
+}
+
+pf_status pf_filter(pf_ctx *ctx, const pf_operator *op, double a, double b, int32_t degree,
+                    double *U, int64_t ldu) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  Op o;
+  PF_TRY(make_op(ctx, op, &o));
+  if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
+    return set_err(ctx, PF_ERR_INVALID_ARG, "interval needs finite a < b");
+  if (degree < 1 || degree > 64) return set_err(ctx, PF_ERR_INVALID_ARG, "degree must be 1..64");
+  if (!U || ldu < ctx->p) return set_err(ctx, PF_ERR_INVALID_ARG, "U needs ldu >= p");
+  PF_CUDA(launch_set_interval(ctx->stream, ctx->ws.prm, a, b));
+  return filter_core(ctx, o, U, ldu, degree);
+}
+
+pf_status pf_rayleigh_ritz(pf_ctx *ctx, const pf_operator *op, const double *Q, int64_t ldq,
+                           double *V, int64_t ldv, double *theta, double *resid) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  Op o;
+  PF_TRY(make_op(ctx, op, &o));
+  if (!Q || ldq < ctx->p || !V || ldv < ctx->p || !theta)
+    return set_err(ctx, PF_ERR_INVALID_ARG, "rayleigh_ritz needs Q, V (ld >= p) and theta");
+  return rr_core(ctx, o, Q, ldq, V, ldv, theta, resid);
+}
+
+pf_status pf_apply(pf_ctx *ctx, const pf_operator *op, const double *X, int64_t ldx, double *Y,
+                   int64_t ldy) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  Op o;
+  PF_TRY(make_op(ctx, op, &o));
+  if (!X || !Y || X == Y || ldx < ctx->p || ldy < ctx->p)
+    return set_err(ctx, PF_ERR_INVALID_ARG, "apply needs distinct X, Y with ld >= p");
+  if (o.kind == PF_OP_DENSE && o.A_lp != nullptr && ctx->opt.precision != PF_PREC_FP64) {
+    const bool tf32 = ctx->opt.precision == PF_PREC_TF32;
+    const Workspace &ws = ctx->ws;
+    PF_CUDA(launch_prep_lp(ctx->stream, ws, tf32, X, ldx, o.n, ws.U32, ws.Xt[0]));
+    PF_CUDA(launch_tc_product(ctx->stream, ws, tf32, o.A_lp, o.lda_lp, o.lp_scale, o.n, ws.Xt[0],
+                              ws.U32, nullptr, ws.Y32[0], nullptr, MODE_PLAIN));
+    if (ldy == ctx->p)
+      PF_CUDA(launch_f32_to_f64(ctx->stream, ws, ws.Y32[0], (int64_t)o.n * ctx->p, Y));
+    else
+      return set_err(ctx, PF_ERR_INVALID_ARG, "low-precision apply needs ldy == p");
+    return PF_OK;
+  }
+  return apply(ctx, o, X, ldx, nullptr, 0, Y, ldy, MODE_PLAIN);
+}
+
+int64_t pf_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  PF_TRY(check_problem(ctx, pr));
+  const int n = (int)pr->n, p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  const Workspace &ws = ctx->ws;
+  double t = pr->t;
+  PF_CUDA(launch_params_init(s, ws.prm, ctx->opt.eta, t, pr->mu, ctx->opt.degree,
+                             ctx->opt.precision));
+  PF_CUDA(launch_fill(s, pr->V, n, p, pr->ldv, 0.0));
+  PF_CUDA(launch_fill(s, pr->theta, 1, p, p, 0.0));
+  if (pr->kind == PF_PROBLEM_MAXCUT) {
+    PF_CUDA(launch_cnorm(s, ws, pr->vals_f64, pr->nnz));
+    Params h;
+    PF_TRY(read_params(ctx, &h));
+    if (!(h.Cnorm > 0.0) || !std::isfinite(h.Cnorm))
+      return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut cost matrix has zero or non-finite norm");
+    if (!(t > 0.0)) t = 10.0 * std::sqrt((double)n) / h.Cnorm;
+    pr->t = t;
+    PF_CUDA(launch_params_init(s, ws.prm, ctx->opt.eta, t, 0.0, ctx->opt.degree,
+                               ctx->opt.precision));
+    PF_CUDA(launch_cnorm(s, ws, pr->vals_f64, pr->nnz));
+    PF_CUDA(launch_maxcut_init(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, t, pr->Z, pr->ldz,
+                               pr->lam));
+  }
+  PF_CUDA(cudaStreamSynchronize(s));
+  PF_CUDA(cudaGetLastError());
+  pr->iter = 0;
+  return PF_OK;
+}
+
+pf_status pf_prox_step(pf_ctx *ctx, pf_problem *pr, pf_iter_info *info) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  PF_TRY(check_problem(ctx, pr));
+  PF_TRY(step_core(ctx, pr));
+  pr->iter += 1;
+  if (info) {
+    Params h;
+    PF_TRY(read_params(ctx, &h));
+    params_to_info(h, info);
+    if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
+    if (h.flags & 4) return set_err(ctx, PF_ERR_NAN, "non-finite Ritz value");
+  }
+  return PF_OK;
+}
+
+pf_status pf_get_info(pf_ctx *ctx, pf_iter_info *info) {
+  if (!ctx || !info) return PF_ERR_INVALID_ARG;
+  Params h;
+  PF_TRY(read_params(ctx, &h));
+  params_to_info(h, info);
+  return PF_OK;
+}
+
+pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, int32_t check_every,
+                   pf_result *out) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  PF_TRY(check_problem(ctx, pr));
+  if (max_iter < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "max_iter must be >= 0");
+  if (check_every < 1) check_every = 1;
+  const bool use_graph = ctx->stream != nullptr;
+  if (use_graph && !(ctx->have_graph && same_problem(ctx->gkey, *pr))) {
+    if (ctx->have_graph) {
+      cudaGraphExecDestroy(ctx->gexec);
+      ctx->have_graph = false;
+    }
+    cudaGraph_t g = nullptr;
+    PF_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    pf_status st = step_core(ctx, pr);
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (st != PF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    PF_CUDA(ce);
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    PF_CUDA(ie);
+    ctx->gexec = ge;
+    ctx->gkey = *pr;
+    ctx->have_graph = true;
+  }
+  Params h = {};
+  int64_t it = 0;
+  bool converged = false;
+  for (; it < max_iter;) {
+    if (use_graph) PF_CUDA(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    else PF_TRY(step_core(ctx, pr));
+    ++it;
+    pr->iter += 1;
+    if (tol > 0.0 && (it % check_every == 0 || it == max_iter)) {
+      PF_TRY(read_params(ctx, &h));
+      if (h.kkt <= tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  PF_TRY(read_params(ctx, &h));
+  if (out) {
+    out->iters = it;
+    out->kkt = h.kkt;
+    out->obj = h.obj;
+    params_to_info(h, &out->last);
+  }
+  if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
+  if (h.flags & 4) return set_err(ctx, PF_ERR_NAN, "non-finite Ritz value");
+  if (tol > 0.0 && !converged && max_iter > 0)
+    return set_err(ctx, PF_ERR_NOT_CONVERGED, "kkt %.3e above tol %.3e after %lld steps", h.kkt,
+                   tol, (long long)it);
+  return PF_OK;
+}
+
+const char *pf_status_string(pf_status s) {
+  switch (s) {
+    case PF_OK: return "ok";
+    case PF_ERR_INVALID_ARG: return "invalid argument";
+    case PF_ERR_OOM: return "out of device memory";
+    case PF_ERR_CUDA: return "CUDA error";
+    case PF_ERR_CHOL_BREAKDOWN: return "CholQR2 breakdown";
+    case PF_ERR_NAN: return "non-finite value";
+    case PF_ERR_NOT_CONVERGED: return "not converged";
+    case PF_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case PF_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *pf_last_error(const pf_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// Internal declarations shared by the CUDA translation units of libpf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "pf.h"
+
+namespace pf {
+
+constexpr int kMaxP = PF_MAX_P;
+constexpr int kRedSlots = 6;        // independent reduction slots per step
+constexpr int kRedWidth = 4;        // doubles per block in a reduction slot
+constexpr int kMaxRedBlocks = 1024; // max blocks of a row reduction
+constexpr int kMaxGramBlocks = 256; // max blocks of a Gram (X^T Y) reduction
+constexpr int kMaxSplitK = 16;      // max K-splits of the dense FP64 product
+
+enum RedSlot { SLOT_INTERVAL = 0, SLOT_LAMBDA = 1, SLOT_EXPAND = 2, SLOT_SDDMM = 3, SLOT_RESID = 4,
+               SLOT_MISC = 5 };
+
+// Filter epilogue modes: Ynext = alpha (op(Ycur) - c Ycur) - beta Yprev.
+enum CombineMode { MODE_PLAIN = 0, MODE_FIRST = 1, MODE_RECUR = 2 };
+
+// Device-resident scalars of one context.  Written and read by kernels only
+// (stream ordered), copied to host by pf_get_info.
+struct Params {
+  double a, b, c, e;      // filter interval [a, b], centre c, half-width e
+  double ub;              // Gershgorin upper bound of the iteration matrix
+  double eta;
+  double t, mu;           // step size, completion weight
+  double Cnorm;           // ||C||_F (max-cut)
+  double obj, kkt, pinf, dinf, gap;
+  double theta_max, theta_min;
+  int have_prev;          // a previous Rayleigh-Ritz step exists
+  int flags;              // bit0 shifted CholQR pass, bit1 breakdown, bit2 non-finite
+  int r_plus;
+  int degree;
+  int precision;
+  int pad;
+};
+
+// Internal iteration-matrix description.
+struct Op {
+  int kind;               // PF_OP_DENSE / PF_OP_LOWRANK_SPARSE
+  int n;
+  const double *A; int64_t lda;
+  const void *A_lp; int64_t lda_lp; double lp_scale;   // low-precision shadow A / lp_scale
+  const double *Uf; int64_t lduf; const double *lam; int r; int clamp;
+  const int32_t *rowptr; const int32_t *colind; const double *vals;
+  double sscale, shift;
+};
+
+struct Workspace {
+  int n_max, p, num_sms;
+  double *Y[2];           // filter recurrence buffers, n_max x p
+  double *W;              // op(Q), n_max x p
+  double *Vprev;          // previous Ritz vectors (completion), n_max x p
+  double *part;           // split-K partials, kMaxSplitK x n_max x p
+  double *gpart;          // Gram partials, kMaxGramBlocks x p x p
+  double *red;            // reduction partials, kRedSlots x kMaxRedBlocks x kRedWidth
+  double *Rinv;           // p x p
+  double *Yeig;           // p x p eigenvectors of H
+  double *T;              // p x p low-rank coefficients diag(w) Uf^T X
+  double *thprev;         // p
+  double *resid;          // p
+  Params *prm;
+  // low-precision filter (allocated only for a bf16 / tf32 context)
+  float *Y32[2];          // fp32 recurrence buffers, n_max x p
+  float *U32;             // fp32 copy of the start block
+  void *Xt[2];            // transposed low-precision operands, p x ldxt
+  int64_t ldxt;
+};
+
+// Host-side count of kernels enqueued by this library (see pf_kernel_launch_count).
+extern std::atomic<int64_t> g_launches;
+#define PF_LAUNCHED() (::pf::g_launches.fetch_add(1, std::memory_order_relaxed))
+
+// ---------------------------------------------------------------------------
+// set-up
+// ---------------------------------------------------------------------------
+cudaError_t configure_skinny();
+cudaError_t configure_tc();
+// K splits of the dense FP64 product for size n (returns S, sets the chunk).
+int dense_splits(int n, int num_sms, int *kchunk);
+
+// ---------------------------------------------------------------------------
+// launchers (each returns the launch error, if any)
+// ---------------------------------------------------------------------------
+cudaError_t launch_set_interval(cudaStream_t s, Params *prm, double a, double b);
+cudaError_t launch_dense_apply(cudaStream_t s, const Workspace &ws, const Op &op, const double *X,
+                               int64_t ldx, const double *Yprev, int64_t ldp, double *Ynext,
+                               int64_t ldn, int mode);
+cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, const Op &op,
+                                        const double *X, int64_t ldx, const double *Yprev,
+                                        int64_t ldp, double *Ynext, int64_t ldn, int mode);
+cudaError_t launch_gram(cudaStream_t s, const Workspace &ws, const double *X, int64_t ldx,
+                        const double *Y, int64_t ldy, int n, int px, int py, int cond_flag,
+                        int *nblocks_out);
+cudaError_t launch_chol_inv(cudaStream_t s, const Workspace &ws, int nparts, int n, int p, int pass);
+cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double *Y, int64_t ldy,
+                               double *Q, int64_t ldq, int n, int p, const double *R, int upper,
+                               int cond_flag);
+cudaError_t launch_jacobi(cudaStream_t s, const Workspace &ws, int nparts, int p, double *theta);
+cudaError_t launch_rotate_resid(cudaStream_t s, const Workspace &ws, const double *Q, int64_t ldq,
+                                const double *W, int64_t ldw, int n, int p, const double *theta,
+                                double *V, int64_t ldv, double *resid_out);
+cudaError_t launch_lowrank_coef(cudaStream_t s, const Workspace &ws, int nparts, const double *lam,
+                                int r, int p, int clamp);
+
+// tensor-core (tcgen05) low-precision filter product and its conversions
+cudaError_t launch_tc_product(cudaStream_t s, const Workspace &ws, bool tf32, const void *A_lp,
+                              int64_t lda_lp, double lp_scale, int n, const void *Xt,
+                              const float *Ycur, const float *Yprev, float *Ynext, void *Xt_next,
+                              int mode);
+cudaError_t launch_prep_lp(cudaStream_t s, const Workspace &ws, bool tf32, const double *U,
+                           int64_t ldu, int n, float *U32, void *Xt);
+cudaError_t launch_f32_to_f64(cudaStream_t s, const Workspace &ws, const float *src, int64_t total,
+                              double *dst);
+
+// problem-level kernels
+cudaError_t launch_interval(cudaStream_t s, const Workspace &ws, int kind, const int32_t *rowptr,
+                            const int32_t *colind, const double *vals, int n, const double *lam,
+                            const double *theta, int p);
+cudaError_t launch_maxcut_init(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                               const int32_t *colind, const double *vals, int n, double t,
+                               double *Z, int64_t ldz, double *lam);
+cudaError_t launch_cnorm(cudaStream_t s, const Workspace &ws, const double *vals, int64_t nnz);
+cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                 const int32_t *colind, const double *vals, int n, int p,
+                                 const double *V, int64_t ldv, const double *theta, double *Z,
+                                 int64_t ldz, double *lam);
+cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                       const int32_t *colind, const float *mvals, int n, int p,
+                                       const double *V, int64_t ldv, const double *theta,
+                                       double *S);
+cudaError_t launch_completion_kkt(cudaStream_t s, const Workspace &ws, const double *V, int64_t ldv,
+                                  const double *theta, int n, int p);
+cudaError_t launch_save_prev(cudaStream_t s, const Workspace &ws, const double *V, int64_t ldv,
+                             const double *theta, int n, int p);
+cudaError_t launch_fill(cudaStream_t s, double *x, int64_t rows, int64_t cols, int64_t ld, double v);
+cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,
+                               int degree, int precision);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// Deterministic block reduction (fixed tree).  `sh` holds >= 32 doubles.
+// op: 0 sum, 1 min, 2 max.  Result valid in all threads.
+__device__ __forceinline__ double block_reduce(double v, double *sh, int op) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = op == 0 ? warp_sum(v) : (op == 1 ? warp_min(v) : warp_max(v));
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double init = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
+  double w = (threadIdx.x < nw) ? sh[threadIdx.x] : init;
+  if (wid == 0) w = op == 0 ? warp_sum(w) : (op == 1 ? warp_min(w) : warp_max(w));
+  if (threadIdx.x == 0) sh[0] = w;
+  __syncthreads();
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+#endif
+
+}  // namespace pf

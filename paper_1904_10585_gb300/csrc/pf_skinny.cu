@@ -1,0 +1,512 @@
+// Skinny FP64 kernels of the subspace extraction:
+//  * Gram partials X^T Y over row blocks (CholQR2's Y^T Y, Rayleigh-Ritz's
+//    Q^T (A Q), the low-rank coefficient Uf^T X), reduced in a fixed order;
+//  * one-block Cholesky of the Gram matrix with a triangular inverse, with the
+//    shifted CholeskyQR fallback of Fukaya, Kannan, Nakatsukasa, Yamamoto and
+//    Yanagisawa (SIAM J. Sci. Comput., 2020) when a pivot collapses;
+//  * the right multiplication Q = Y R^{-1} (orth of Eq. (subspace-update),
+//    realised as CholQR2 = QR with positive diagonal R in exact arithmetic);
+//  * one-block cyclic Jacobi on the p x p projected matrix H = Q^T A Q and the
+//    Ritz rotation V = Q Y with residuals ||A v_i - theta_i v_i|| (Eq. (RR)).
+#include "pf_internal.cuh"
+
+namespace pf {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int RC = 32;  // rows staged per step
+
+template <int PT>
+__global__ void __launch_bounds__(NT) k_gram(const double *__restrict__ X, int64_t ldx,
+                                             const double *__restrict__ Y, int64_t ldy, int n,
+                                             int px, int py, int rows_per_block,
+                                             double *__restrict__ gpart, const Params *prm,
+                                             int cond_flag) {
+  if (cond_flag && !(prm->flags & 1)) return;
+  constexpr int TM = PT / 16, TN = PT / 16;
+  __shared__ double Xs[RC][PT + 1];
+  __shared__ double Ys[RC][PT + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  const int r0 = blockIdx.x * rows_per_block;
+  const int r1 = min(n, r0 + rows_per_block);
+  for (int rb = r0; rb < r1; rb += RC) {
+    for (int e = tid; e < RC * PT; e += NT) {
+      const int r = e / PT, c = e % PT, gr = rb + r;
+      Xs[r][c] = (gr < r1 && c < px) ? X[(int64_t)gr * ldx + c] : 0.0;
+      Ys[r][c] = (gr < r1 && c < py) ? Y[(int64_t)gr * ldy + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < RC; ++r) {
+      double a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = Xs[r][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Ys[r][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double *out = gpart + (int64_t)blockIdx.x * px * py;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int a = ty * TM + i;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int b = tx + 16 * j;
+      if (a < px && b < py) out[a * py + b] = acc[i][j];
+    }
+  }
+}
+
+// Sum Gram partials, Cholesky G = R^T R (upper R), write R^{-1}.
+// pass 0: on a collapsed pivot retry once with the shift
+//         s = 11 (n p + p (p+1)) u tr(G) and set flags bit 0;
+// pass 1: plain; pass 2: only runs when flags bit 0 is set.
+// A failure with no retry left sets flags bit 1 and writes R^{-1} = I.
+__global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpart, int nparts,
+                                                 int n, int p, int pass, double *__restrict__ Rinv,
+                                                 Params *prm) {
+  if (pass == 2 && !(prm->flags & 1)) return;
+  extern __shared__ double dyn[];
+  double(*G)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn);
+  double(*R)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn + kMaxP * (kMaxP + 1));
+  __shared__ int fail;
+  __shared__ double trace_s;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < p * p; idx += NT) {
+    double s = 0.0;
+    for (int q = 0; q < nparts; ++q) s += gpart[(int64_t)q * p * p + idx];
+    G[idx / p][idx % p] = s;
+  }
+  __syncthreads();
+  double sh = 0.0;
+  bool ok = false;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    for (int idx = tid; idx < p * p; idx += NT) {
+      const int a = idx / p, b = idx % p;
+      R[a][b] = G[a][b] + (a == b ? sh : 0.0);
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int k = 0; k < p; ++k) {
+      if (tid == 0) {
+        const double piv = R[k][k];
+        const double ref = G[k][k] + sh;
+        if (!(piv > 1e-13 * ref) || !isfinite(piv)) fail = 1;
+        else R[k][k] = sqrt(piv);
+      }
+      __syncthreads();
+      if (fail) break;
+      const double rkk = R[k][k];
+      for (int j = k + 1 + tid; j < p; j += NT) R[k][j] /= rkk;
+      __syncthreads();
+      const int m = p - k - 1;
+      for (int idx = tid; idx < m * m; idx += NT) {
+        const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+        R[i][j] -= R[k][i] * R[k][j];
+      }
+      __syncthreads();
+    }
+    if (!fail) {
+      ok = true;
+      break;
+    }
+    if (pass != 0) break;
+    // shifted retry
+    if (tid == 0) {
+      double tr = 0.0;
+      for (int k = 0; k < p; ++k) tr += G[k][k];
+      trace_s = tr;
+      atomicOr(&prm->flags, 1);
+    }
+    __syncthreads();
+    sh = 11.0 * ((double)n * p + (double)p * (p + 1)) * 1.1102230246251565e-16 * trace_s;
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(&prm->flags, 2);
+    for (int idx = tid; idx < p * p; idx += NT) Rinv[idx] = (idx / p == idx % p) ? 1.0 : 0.0;
+    return;
+  }
+  // inverse of the upper-triangular R, column j by thread j (into G)
+  for (int j = tid; j < p; j += NT) {
+    for (int i = j + 1; i < p; ++i) G[i][j] = 0.0;
+    G[j][j] = 1.0 / R[j][j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s = fma(R[i][k], G[k][j], s);
+      G[i][j] = -s / R[i][i];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < p * p; idx += NT) Rinv[idx] = G[idx / p][idx % p];
+}
+
+// Q = Y R (R p x p; `upper` skips the zero lower part).  In place allowed.
+template <int PT>
+__global__ void __launch_bounds__(NT) k_apply_right(const double *Y, int64_t ldy, double *Q,
+                                                    int64_t ldq, int n, int p,
+                                                    const double *__restrict__ R, int upper,
+                                                    int rows_per_block, const Params *prm,
+                                                    int cond_flag) {
+  if (cond_flag && !(prm->flags & 1)) return;
+  extern __shared__ double dyn[];
+  double(*Rs)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(dyn);
+  double(*Ys)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(dyn + PT * (PT + 1));
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < PT * PT; idx += NT) {
+    const int a = idx / PT, b = idx % PT;
+    Rs[a][b] = (a < p && b < p) ? R[a * p + b] : 0.0;
+  }
+  const int r0 = blockIdx.x * rows_per_block;
+  const int r1 = min(n, r0 + rows_per_block);
+  for (int rb = r0; rb < r1; rb += RC) {
+    __syncthreads();
+    for (int e = tid; e < RC * PT; e += NT) {
+      const int r = e / PT, c = e % PT, gr = rb + r;
+      Ys[r][c] = (gr < r1 && c < p) ? Y[(int64_t)gr * ldy + c] : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < RC * PT; e += NT) {
+      const int r = e / PT, c = e % PT, gr = rb + r;
+      if (gr >= r1 || c >= p) continue;
+      const int kend = upper ? c + 1 : p;
+      double s = 0.0;
+      for (int k = 0; k < kend; ++k) s = fma(Ys[r][k], Rs[k][c], s);
+      Q[(int64_t)gr * ldq + c] = s;
+    }
+  }
+}
+
+// V = Q Yeig and per-block column sums of (W Yeig - theta V)^2.
+template <int PT>
+__global__ void __launch_bounds__(NT) k_rotate_resid(const double *__restrict__ Q, int64_t ldq,
+                                                     const double *__restrict__ W, int64_t ldw,
+                                                     int n, int p, const double *__restrict__ Yeig,
+                                                     const double *__restrict__ theta, double *V,
+                                                     int64_t ldv, int rows_per_block,
+                                                     double *__restrict__ rpart) {
+  static_assert(NT % PT == 0, "thread count must be a multiple of the padded width");
+  extern __shared__ double dyn[];
+  double(*Ys)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(dyn);
+  double(*Qs)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(dyn + PT * (PT + 1));
+  double(*Ws)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(dyn + (PT + RC) * (PT + 1));
+  double *red = dyn + (PT + 2 * RC) * (PT + 1);
+  const int tid = threadIdx.x;
+  const int c = tid % PT;
+  for (int idx = tid; idx < PT * PT; idx += NT) {
+    const int a = idx / PT, b = idx % PT;
+    Ys[a][b] = (a < p && b < p) ? Yeig[a * p + b] : 0.0;
+  }
+  const double th = c < p ? theta[c] : 0.0;
+  double racc = 0.0;
+  const int r0 = blockIdx.x * rows_per_block;
+  const int r1 = min(n, r0 + rows_per_block);
+  for (int rb = r0; rb < r1; rb += RC) {
+    __syncthreads();
+    for (int e = tid; e < RC * PT; e += NT) {
+      const int r = e / PT, cc = e % PT, gr = rb + r;
+      const bool in = gr < r1 && cc < p;
+      Qs[r][cc] = in ? Q[(int64_t)gr * ldq + cc] : 0.0;
+      Ws[r][cc] = in ? W[(int64_t)gr * ldw + cc] : 0.0;
+    }
+    __syncthreads();
+    for (int r = tid / PT; r < RC; r += NT / PT) {
+      const int gr = rb + r;
+      if (gr >= r1 || c >= p) continue;
+      double v = 0.0, w = 0.0;
+      for (int k = 0; k < p; ++k) {
+        v = fma(Qs[r][k], Ys[k][c], v);
+        w = fma(Ws[r][k], Ys[k][c], w);
+      }
+      V[(int64_t)gr * ldv + c] = v;
+      const double d = w - th * v;
+      racc = fma(d, d, racc);
+    }
+  }
+  red[tid] = racc;
+  __syncthreads();
+  if (tid < PT) {
+    double s = 0.0;
+    for (int t = tid; t < NT; t += PT) s += red[t];
+    if (tid < p) rpart[(int64_t)blockIdx.x * p + tid] = s;
+  }
+}
+
+__global__ void k_resid_final(const double *__restrict__ rpart, int nparts, int p,
+                              double *__restrict__ resid) {
+  const int j = threadIdx.x;
+  if (j >= p) return;
+  double s = 0.0;
+  for (int q = 0; q < nparts; ++q) s += rpart[(int64_t)q * p + j];
+  resid[j] = sqrt(s);
+}
+
+// T[l][j] = w_l (Uf^T X)[l][j], w_l = lam_l (clamped at 0 when `clamp`).
+__global__ void k_lowrank_coef(const double *__restrict__ gpart, int nparts, const double *lam,
+                               int r, int p, int clamp, double *__restrict__ T) {
+  for (int idx = threadIdx.x; idx < r * p; idx += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nparts; ++q) s += gpart[(int64_t)q * r * p + idx];
+    double w = lam[idx / p];
+    if (clamp) w = w > 0.0 ? w : 0.0;
+    T[idx] = w * s;
+  }
+}
+
+// One-block cyclic Jacobi (parallel round-robin ordering) on the symmetric
+// part of H = sum of Gram partials.  Writes eigenvalues descending into
+// theta and the matching eigenvectors as the columns of Yeig (p x p).
+__global__ void __launch_bounds__(NT) k_jacobi(const double *__restrict__ gpart, int nparts, int p,
+                                               double *__restrict__ Yeig,
+                                               double *__restrict__ theta, Params *prm) {
+  extern __shared__ double dyn[];
+  double(*H)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn);
+  double(*V)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn + kMaxP * (kMaxP + 1));
+  __shared__ double cs[kMaxP / 2], sn[kMaxP / 2];
+  __shared__ int pk[kMaxP / 2], pl[kMaxP / 2];
+  __shared__ double redsh[32];
+  __shared__ double lam_s[kMaxP];
+  const int tid = threadIdx.x;
+  // H = sym(sum of partials); V = I
+  for (int idx = tid; idx < p * p; idx += NT) {
+    const int a = idx / p, b = idx % p;
+    double s = 0.0, s2 = 0.0;
+    for (int q = 0; q < nparts; ++q) {
+      s += gpart[(int64_t)q * p * p + a * p + b];
+      s2 += gpart[(int64_t)q * p * p + b * p + a];
+    }
+    H[a][b] = 0.5 * (s + s2);
+    V[a][b] = (a == b) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int m = p + (p & 1);  // even number of players; index p (if odd) is a dummy
+  const int half = m / 2;
+  for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int idx = tid; idx < p * p; idx += NT) {
+      const int a = idx / p, b = idx % p;
+      const double h = H[a][b];
+      tot = fma(h, h, tot);
+      if (a != b) off = fma(h, h, off);
+    }
+    off = block_reduce(off, redsh, 0);
+    tot = block_reduce(tot, redsh, 0);
+    if (!(off > 1e-30 * tot)) break;  // off(H) <= 1e-15 ||H||_F (also stops on NaN)
+    for (int round = 0; round < m - 1; ++round) {
+      if (tid < half) {
+        const int i = tid;
+        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (m - 1)); };
+        int k = player(i), l = player(m - 1 - i);
+        if (k > l) { const int t = k; k = l; l = t; }
+        double c = 1.0, s = 0.0;
+        if (l < p) {
+          const double hkl = H[k][l];
+          if (hkl != 0.0) {
+            const double tau = (H[l][l] - H[k][k]) / (2.0 * hkl);
+            double t;
+            if (fabs(tau) > 1e150) t = 0.5 / tau;
+            else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        cs[i] = c; sn[i] = s; pk[i] = k; pl[i] = l;
+      }
+      __syncthreads();
+      // rows: H <- J^T H
+      for (int idx = tid; idx < half * p; idx += NT) {
+        const int i = idx / p, col = idx % p;
+        const int k = pk[i], l = pl[i];
+        if (l >= p) continue;
+        const double c = cs[i], s = sn[i];
+        const double hk = H[k][col], hl = H[l][col];
+        H[k][col] = c * hk - s * hl;
+        H[l][col] = s * hk + c * hl;
+      }
+      __syncthreads();
+      // columns: H <- H J, V <- V J
+      for (int idx = tid; idx < half * p; idx += NT) {
+        const int i = idx / p, row = idx % p;
+        const int k = pk[i], l = pl[i];
+        if (l >= p) continue;
+        const double c = cs[i], s = sn[i];
+        const double hk = H[row][k], hl = H[row][l];
+        H[row][k] = c * hk - s * hl;
+        H[row][l] = s * hk + c * hl;
+        const double vk = V[row][k], vl = V[row][l];
+        V[row][k] = c * vk - s * vl;
+        V[row][l] = s * vk + c * vl;
+      }
+      __syncthreads();
+      if (tid < half) {
+        const int k = pk[tid], l = pl[tid];
+        if (l < p && sn[tid] != 0.0) { H[k][l] = 0.0; H[l][k] = 0.0; }
+      }
+      __syncthreads();
+    }
+  }
+  // sort descending (ties by index) and write out
+  if (tid < p) lam_s[tid] = H[tid][tid];
+  __syncthreads();
+  bool bad = false;
+  for (int j = tid; j < p; j += NT) {
+    const double lj = lam_s[j];
+    if (!isfinite(lj)) bad = true;
+    int rank = 0;
+    for (int i = 0; i < p; ++i) {
+      const double li = lam_s[i];
+      if (li > lj || (li == lj && i < j)) ++rank;
+    }
+    theta[rank] = lj;
+    for (int a = 0; a < p; ++a) Yeig[a * p + rank] = V[a][j];
+  }
+  if (bad) atomicOr(&prm->flags, 4);
+}
+
+constexpr size_t kSqBytes = 2 * kMaxP * (kMaxP + 1) * sizeof(double);
+constexpr size_t apply_bytes(int PT) { return (size_t)(PT + RC) * (PT + 1) * sizeof(double); }
+constexpr size_t rotate_bytes(int PT) {
+  return ((size_t)(PT + 2 * RC) * (PT + 1) + NT) * sizeof(double);
+}
+
+}  // namespace
+
+cudaError_t configure_skinny() {
+  cudaError_t e;
+#define PF_SET(fn, bytes)                                                                   \
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+  if (e != cudaSuccess) return e;
+  PF_SET(k_chol_inv, kSqBytes)
+  PF_SET(k_jacobi, kSqBytes)
+  PF_SET(k_apply_right<16>, apply_bytes(16))
+  PF_SET(k_apply_right<32>, apply_bytes(32))
+  PF_SET(k_apply_right<64>, apply_bytes(64))
+  PF_SET(k_rotate_resid<16>, rotate_bytes(16))
+  PF_SET(k_rotate_resid<32>, rotate_bytes(32))
+  PF_SET(k_rotate_resid<64>, rotate_bytes(64))
+#undef PF_SET
+  return cudaSuccess;
+}
+
+static void row_split(int n, int max_blocks, int min_rows, int *nb, int *rpb) {
+  int b = (n + min_rows - 1) / min_rows;
+  if (b > max_blocks) b = max_blocks;
+  if (b < 1) b = 1;
+  int r = (n + b - 1) / b;
+  r = ((r + RC - 1) / RC) * RC;
+  *rpb = r;
+  *nb = (n + r - 1) / r;
+  if (*nb < 1) *nb = 1;
+}
+
+cudaError_t launch_gram(cudaStream_t s, const Workspace &ws, const double *X, int64_t ldx,
+                        const double *Y, int64_t ldy, int n, int px, int py, int cond_flag,
+                        int *nblocks_out) {
+  int nb, rpb;
+  row_split(n, kMaxGramBlocks, 64, &nb, &rpb);
+  const int pm = px > py ? px : py;
+  if (pm <= 16)
+    {
+      k_gram<16><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      PF_LAUNCHED();
+    }
+  else if (pm <= 32)
+    {
+      k_gram<32><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      PF_LAUNCHED();
+    }
+  else if (pm <= 48)
+    {
+      k_gram<48><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      PF_LAUNCHED();
+    }
+  else
+    {
+      k_gram<64><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      PF_LAUNCHED();
+    }
+  *nblocks_out = nb;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_inv(cudaStream_t s, const Workspace &ws, int nparts, int n, int p, int pass) {
+  k_chol_inv<<<1, NT, kSqBytes, s>>>(ws.gpart, nparts, n, p, pass, ws.Rinv, ws.prm);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double *Y, int64_t ldy,
+                               double *Q, int64_t ldq, int n, int p, const double *R, int upper,
+                               int cond_flag) {
+  int nb, rpb;
+  row_split(n, 4 * ws.num_sms, 64, &nb, &rpb);
+  if (p <= 16)
+    {
+      k_apply_right<16><<<nb, NT, apply_bytes(16), s>>>(Y, ldy, Q, ldq, n, p, R, upper, rpb, ws.prm, cond_flag);
+      PF_LAUNCHED();
+    }
+  else if (p <= 32)
+    {
+      k_apply_right<32><<<nb, NT, apply_bytes(32), s>>>(Y, ldy, Q, ldq, n, p, R, upper, rpb, ws.prm, cond_flag);
+      PF_LAUNCHED();
+    }
+  else
+    {
+      k_apply_right<64><<<nb, NT, apply_bytes(64), s>>>(Y, ldy, Q, ldq, n, p, R, upper, rpb, ws.prm, cond_flag);
+      PF_LAUNCHED();
+    }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(cudaStream_t s, const Workspace &ws, int nparts, int p, double *theta) {
+  k_jacobi<<<1, NT, kSqBytes, s>>>(ws.gpart, nparts, p, ws.Yeig, theta, ws.prm);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_resid(cudaStream_t s, const Workspace &ws, const double *Q, int64_t ldq,
+                                const double *W, int64_t ldw, int n, int p, const double *theta,
+                                double *V, int64_t ldv, double *resid_out) {
+  int nb, rpb;
+  row_split(n, kMaxGramBlocks, 64, &nb, &rpb);
+  if (p <= 16)
+    {
+      k_rotate_resid<16><<<nb, NT, rotate_bytes(16), s>>>(Q, ldq, W, ldw, n, p, ws.Yeig, theta, V, ldv, rpb, ws.gpart);
+      PF_LAUNCHED();
+    }
+  else if (p <= 32)
+    {
+      k_rotate_resid<32><<<nb, NT, rotate_bytes(32), s>>>(Q, ldq, W, ldw, n, p, ws.Yeig, theta, V, ldv, rpb, ws.gpart);
+      PF_LAUNCHED();
+    }
+  else
+    {
+      k_rotate_resid<64><<<nb, NT, rotate_bytes(64), s>>>(Q, ldq, W, ldw, n, p, ws.Yeig, theta, V, ldv, rpb, ws.gpart);
+      PF_LAUNCHED();
+    }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_resid_final<<<1, kMaxP, 0, s>>>(ws.gpart, nb, p, resid_out ? resid_out : ws.resid);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lowrank_coef(cudaStream_t s, const Workspace &ws, int nparts, const double *lam,
+                                int r, int p, int clamp) {
+  k_lowrank_coef<<<1, NT, 0, s>>>(ws.gpart, nparts, lam, r, p, clamp, ws.T);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+}  // namespace pf

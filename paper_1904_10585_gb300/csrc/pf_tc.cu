@@ -1,0 +1,415 @@
+// Low-precision dense filter product on the 5th-generation tensor cores.
+//
+// One Chebyshev step (Sec. 2.1, Eq. (cheb) by the three-term recurrence in
+// the mapped variable of Eq. (cheb-linear-map)) with the dense iteration
+// matrix held as a low-precision shadow A_lp = A / s (bf16, or fp32 read as
+// tf32), scaled into [-1, 1]:
+//     Ynext = alpha (s * A_lp Xlp - c Ycur) - beta Yprev
+// Xlp is the current block in the same low precision, stored transposed
+// (p x n, K-major); Ycur / Yprev / Ynext are fp32 row-major n x p.  The
+// epilogue also writes Ynext transposed in low precision, the B operand of
+// the next product.
+//
+// Kernel structure (one CTA per 128-row block, 128 threads):
+//   warp 0, one lane : TMA producer, 128B-swizzled A and B tiles into a ring
+//                      of shared-memory stages (mbarrier complete_tx);
+//   warp 1, one lane : MMA issuer, tcgen05.mma (kind::f16 or kind::tf32,
+//                      M = 128, N = p, K = 32 bytes per instruction) into a
+//                      TMEM accumulator; tcgen05.commit frees each stage;
+//   all 4 warps      : epilogue, tcgen05.ld of the 128 x p fp32 accumulator
+//                      (warp w owns TMEM lanes 32w..32w+31 = its rows).
+// Every wait is bounded (about 2 s of %globaltimer); on expiry the CTA sets
+// flags bit 3 in the context parameters, skips the rest and frees its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_THREADS = 128;
+constexpr int TC_STAGES = 6;
+constexpr int TC_ROWB = 128;                       // bytes of K per tile row (one swizzle row)
+constexpr int TC_A_BYTES = TC_BM * TC_ROWB;        // 16 KB per stage
+constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;  // bounded waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a barrier phase; false on timeout or when another thread
+// of the CTA has already given up.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > TC_TIMEOUT_NS) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row
+// groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+template <bool TF32>
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accum) {
+  if (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Instruction descriptor: fp32 accumulator, A/B K-major, M = 128, N = NB.
+template <bool TF32, int NB>
+__host__ __device__ constexpr uint32_t make_idesc() {
+  return (1u << 4)                              // D format fp32
+         | ((TF32 ? 2u : 1u) << 7)              // A format: bf16 (kind::f16) / tf32
+         | ((TF32 ? 2u : 1u) << 10)             // B format
+         | ((uint32_t)(NB >> 3) << 17)          // N >> 3
+         | ((uint32_t)(TC_BM >> 4) << 24);      // M >> 4
+}
+
+template <int NB, bool TF32>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_filter(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                int n, int p, int num_kb, float scale, const float *Ycur, const float *Yprev,
+                float *Ynext, void *Xt_next, int64_t ldxt, Params *prm, int mode) {
+  constexpr int B_BYTES = NB * TC_ROWB;
+  constexpr int STAGE_TX = TC_A_BYTES + B_BYTES;
+  constexpr uint32_t TMEM_COLS = NB <= 32 ? 32 : (NB <= 64 ? 64 : 128);
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t sA = base;
+  const uint32_t sB = base + TC_STAGES * TC_A_BYTES;
+  const int row0 = blockIdx.x * TC_BM;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&acc_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const int s = kb % TC_STAGES;
+      if (kb >= TC_STAGES) {
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ((kb / TC_STAGES) - 1) & 1, &abort_flag)) break;
+      }
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, STAGE_TX);
+      const int kx = kb * (TC_ROWB / (TF32 ? 4 : 2));
+      tma_load_2d(sA + s * TC_A_BYTES, &tmA, fb, kx, row0);
+      tma_load_2d(sB + s * B_BYTES, &tmB, fb, kx, 0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = make_idesc<TF32, NB>();
+    bool ok = true;
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const int s = kb % TC_STAGES;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (kb / TC_STAGES) & 1, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t ad = sw128_desc(sA + s * TC_A_BYTES);
+      const uint64_t bd = sw128_desc(sB + s * B_BYTES);
+#pragma unroll
+      for (int k = 0; k < TC_ROWB / 32; ++k) {
+        // advance 32 bytes along K inside the swizzled row: +2 in the >>4 field
+        mma_issue<TF32>(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      }
+      mma_commit(smem_u32(&empty_bar[s]));
+    }
+    if (ok) mma_commit(smem_u32(&acc_bar));
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns TMEM lanes / rows 32w .. 32w+31
+  const bool have_acc = mbar_wait(smem_u32(&acc_bar), 0, &abort_flag);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have_acc) {
+    double c = 0.0, alpha = 1.0;
+    if (mode != MODE_PLAIN) {
+      c = prm->c;
+      alpha = (mode == MODE_FIRST ? 1.0 : 2.0) / prm->e;
+    }
+    const float cf = (float)c, af = (float)alpha;
+    const int row = row0 + warp * 32 + lane;
+    const bool in = row < n;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int c0 = 0; c0 < NB; c0 += 16) {
+      float v[16];
+      tmem_ld16(taddr + c0, v);
+      if (!in) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int j = c0 + i;
+        if (j >= p) break;
+        const int64_t idx = (int64_t)row * p + j;
+        const float prod = scale * v[i];
+        float y;
+        if (mode == MODE_PLAIN) {
+          y = prod;
+        } else {
+          y = af * (prod - cf * Ycur[idx]);
+          if (mode == MODE_RECUR) y -= Yprev[idx];
+        }
+        Ynext[idx] = y;
+        if (Xt_next != nullptr) {
+          if (TF32)
+            reinterpret_cast<float *>(Xt_next)[(int64_t)j * ldxt + row] = y;
+          else
+            reinterpret_cast<__nv_bfloat16 *>(Xt_next)[(int64_t)j * ldxt + row] =
+                __float2bfloat16_rn(y);
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && (abort_flag || !have_acc)) atomicOr(&prm->flags, 8);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// U (fp64, ldu) -> Y32 (fp32 n x p) and the transposed low-precision operand.
+template <bool TF32>
+__global__ void k_prep_lp(const double *__restrict__ U, int64_t ldu, int n, int p,
+                          float *__restrict__ U32, void *__restrict__ Xt, int64_t ldxt) {
+  const int64_t total = (int64_t)n * p;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    // column-major walk so that the transposed write is coalesced
+    const int j = (int)(idx / n);
+    const int i = (int)(idx - (int64_t)j * n);
+    const float v = (float)U[(int64_t)i * ldu + j];
+    U32[(int64_t)i * p + j] = v;
+    if (TF32) reinterpret_cast<float *>(Xt)[(int64_t)j * ldxt + i] = v;
+    else reinterpret_cast<__nv_bfloat16 *>(Xt)[(int64_t)j * ldxt + i] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void k_f32_to_f64(const float *__restrict__ src, int64_t total, double *__restrict__ dst) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    dst[idx] = (double)src[idx];
+}
+
+size_t tc_smem_bytes(int NB) { return 1024 + (size_t)TC_STAGES * (TC_A_BYTES + NB * TC_ROWB); }
+
+template <int NB, bool TF32>
+cudaError_t set_attr() {
+  return cudaFuncSetAttribute(k_tc_filter<NB, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes(NB));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+}  // namespace
+
+cudaError_t configure_tc() {
+  if (g_encode == nullptr) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  cudaError_t e;
+#define PF_TC_ATTR(NB)                          \
+  if ((e = set_attr<NB, false>()) != cudaSuccess) return e; \
+  if ((e = set_attr<NB, true>()) != cudaSuccess) return e;
+  PF_TC_ATTR(16)
+  PF_TC_ATTR(32)
+  PF_TC_ATTR(48)
+  PF_TC_ATTR(64)
+#undef PF_TC_ATTR
+  return cudaSuccess;
+}
+
+// 2-D row-major tensor map: rows x cols elements, leading dimension ld
+// elements, box = box_rows x (128 bytes of columns), 128-byte swizzle.
+static cudaError_t encode_map(CUtensorMap *m, const void *ptr, bool tf32, int64_t rows,
+                              int64_t cols, int64_t ld, int box_rows) {
+  if (g_encode == nullptr) return cudaErrorNotSupported;
+  const int esz = tf32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+  cuuint32_t box[2] = {(cuuint32_t)(TC_ROWB / esz), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        2, const_cast<void *>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static int tc_nb(int p) { return p <= 16 ? 16 : p <= 32 ? 32 : p <= 48 ? 48 : 64; }
+
+cudaError_t launch_tc_product(cudaStream_t s, const Workspace &ws, bool tf32, const void *A_lp,
+                              int64_t lda_lp, double lp_scale, int n, const void *Xt,
+                              const float *Ycur, const float *Yprev, float *Ynext, void *Xt_next,
+                              int mode) {
+  const int p = ws.p;
+  const int NB = tc_nb(p);
+  CUtensorMap ma, mb;
+  cudaError_t e = encode_map(&ma, A_lp, tf32, n, n, lda_lp, TC_BM);
+  if (e != cudaSuccess) return e;
+  e = encode_map(&mb, Xt, tf32, p, n, ws.ldxt, NB);
+  if (e != cudaSuccess) return e;
+  const int kel = TC_ROWB / (tf32 ? 4 : 2);
+  const int num_kb = (n + kel - 1) / kel;
+  const dim3 grid((n + TC_BM - 1) / TC_BM);
+  const size_t smem = tc_smem_bytes(NB);
+  const float sc = (float)lp_scale;
+#define PF_TC_LAUNCH(NBV, TFV)                                                                    \
+  k_tc_filter<NBV, TFV><<<grid, TC_THREADS, smem, s>>>(ma, mb, n, p, num_kb, sc, Ycur, Yprev,   \
+                                                       Ynext, Xt_next, ws.ldxt, ws.prm, mode)
+  if (tf32) {
+    switch (NB) {
+      case 16: PF_TC_LAUNCH(16, true); break;
+      case 32: PF_TC_LAUNCH(32, true); break;
+      case 48: PF_TC_LAUNCH(48, true); break;
+      default: PF_TC_LAUNCH(64, true); break;
+    }
+  } else {
+    switch (NB) {
+      case 16: PF_TC_LAUNCH(16, false); break;
+      case 32: PF_TC_LAUNCH(32, false); break;
+      case 48: PF_TC_LAUNCH(48, false); break;
+      default: PF_TC_LAUNCH(64, false); break;
+    }
+  }
+#undef PF_TC_LAUNCH
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_lp(cudaStream_t s, const Workspace &ws, bool tf32, const double *U,
+                           int64_t ldu, int n, float *U32, void *Xt) {
+  const int64_t total = (int64_t)n * ws.p;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4 * ws.num_sms) blocks = 4 * ws.num_sms;
+  if (tf32) k_prep_lp<true><<<(int)blocks, 256, 0, s>>>(U, ldu, n, ws.p, U32, Xt, ws.ldxt);
+  else k_prep_lp<false><<<(int)blocks, 256, 0, s>>>(U, ldu, n, ws.p, U32, Xt, ws.ldxt);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(cudaStream_t s, const Workspace &ws, const float *src, int64_t total,
+                              double *dst) {
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4 * ws.num_sms) blocks = 4 * ws.num_sms;
+  if (blocks < 1) blocks = 1;
+  k_f32_to_f64<<<(int)blocks, 256, 0, s>>>(src, total, dst);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -1,0 +1,178 @@
+"""PyTorch-facing helpers around the C ABI: they hold device tensors (memory
+and streams are PyTorch's) and fill the pf_* structs with their pointers.
+No arithmetic of the method happens here."""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import torch
+
+from . import _binding as B
+
+
+def _ptr(t: Optional[torch.Tensor]) -> int:
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise ValueError("libpf takes device tensors; got a host tensor")
+    if not t.is_contiguous() and t.dim() == 1:
+        raise ValueError("vectors must be contiguous")
+    return t.data_ptr()
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("blocks must be row-major 2-D tensors with unit column stride")
+    return t.stride(0)
+
+
+class Context:
+    """Owns one pf_ctx (workspace only) bound to a CUDA stream."""
+
+    def __init__(self, p: int, n_max: int, degree: int, eta: float = 0.1,
+                 precision: int = B.PF_PREC_FP64, stream: Optional[torch.cuda.Stream] = None,
+                 degree_max: int = 0, adaptive: int = 0):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.opt = B.pf_options(p=p, degree=degree, degree_max=degree_max or degree, q=1,
+                                eta=eta, precision=precision, adaptive=adaptive)
+        self.p = p
+        self.n_max = n_max
+        self.handle = B.pf_create(self.opt, n_max, self.stream.cuda_stream)
+
+    def close(self):
+        if self.handle:
+            B.pf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def dense_operator(A: torch.Tensor) -> B.pf_operator:
+    assert A.dtype == torch.float64 and A.shape[0] == A.shape[1]
+    return B.pf_operator(kind=B.PF_OP_DENSE, n=A.shape[0], A=_ptr(A), lda=_ld(A))
+
+
+def lowrank_sparse_operator(n: int, Uf: Optional[torch.Tensor], lam: Optional[torch.Tensor],
+                            rowptr: Optional[torch.Tensor], colind: Optional[torch.Tensor],
+                            vals: Optional[torch.Tensor], sparse_scale: float, shift: float
+                            ) -> B.pf_operator:
+    r = 0 if Uf is None else Uf.shape[1]
+    return B.pf_operator(kind=B.PF_OP_LOWRANK_SPARSE, n=n,
+                         Uf=_ptr(Uf), lduf=(_ld(Uf) if Uf is not None else 0), lam=_ptr(lam), r=r,
+                         rowptr=_ptr(rowptr), colind=_ptr(colind), vals=_ptr(vals),
+                         nnz=0 if vals is None else vals.numel(),
+                         sparse_scale=sparse_scale, shift=shift)
+
+
+def filter_(ctx: Context, op: B.pf_operator, a: float, b: float, degree: int,
+            U: torch.Tensor) -> None:
+    B.pf_filter(ctx.handle, op, a, b, degree, _ptr(U), _ld(U))
+
+
+def apply(ctx: Context, op: B.pf_operator, X: torch.Tensor, Y: torch.Tensor) -> None:
+    B.pf_apply(ctx.handle, op, _ptr(X), _ld(X), _ptr(Y), _ld(Y))
+
+
+def rayleigh_ritz(ctx: Context, op: B.pf_operator, Q: torch.Tensor):
+    n, p = Q.shape
+    V = torch.empty_like(Q)
+    theta = torch.empty(p, dtype=torch.float64, device=Q.device)
+    resid = torch.empty(p, dtype=torch.float64, device=Q.device)
+    B.pf_rayleigh_ritz(ctx.handle, op, _ptr(Q), _ld(Q), _ptr(V), _ld(V), _ptr(theta), _ptr(resid))
+    return V, theta, resid
+
+
+@dataclasses.dataclass
+class Problem:
+    """Device-resident data and state of one solve (caller-owned buffers)."""
+
+    kind: int
+    n: int
+    rowptr: torch.Tensor
+    colind: torch.Tensor
+    vals: torch.Tensor
+    U: torch.Tensor
+    V: torch.Tensor
+    theta: torch.Tensor
+    Z: Optional[torch.Tensor] = None
+    lam: Optional[torch.Tensor] = None
+    S: Optional[torch.Tensor] = None
+    t: float = 0.0
+    mu: float = 0.0
+    struct: Optional[B.pf_problem] = None
+
+    def make_struct(self) -> B.pf_problem:
+        s = B.pf_problem(kind=self.kind, n=self.n, rowptr=_ptr(self.rowptr),
+                         colind=_ptr(self.colind), nnz=self.colind.numel(), t=self.t, mu=self.mu,
+                         U=_ptr(self.U), ldu=_ld(self.U), V=_ptr(self.V), ldv=_ld(self.V),
+                         theta=_ptr(self.theta))
+        if self.kind == B.PF_PROBLEM_MAXCUT:
+            s.vals_f64 = _ptr(self.vals)
+            s.Z = _ptr(self.Z)
+            s.ldz = _ld(self.Z)
+            s.lam = _ptr(self.lam)
+        else:
+            s.vals_f32 = _ptr(self.vals)
+            s.S = _ptr(self.S)
+        self.struct = s
+        return s
+
+
+def maxcut_problem(rowptr, colind, vals, U0: torch.Tensor, t: float = 0.0) -> Problem:
+    """Max-cut SDP with cost C (CSR, float64 values incl. diagonal); U0 is the
+    n x p start block (copied)."""
+    n, p = U0.shape
+    dev = U0.device
+    pr = Problem(kind=B.PF_PROBLEM_MAXCUT, n=n, rowptr=rowptr, colind=colind, vals=vals,
+                 U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
+                 theta=torch.zeros(p, dtype=torch.float64, device=dev),
+                 Z=torch.empty(n, n, dtype=torch.float64, device=dev),
+                 lam=torch.empty(n, dtype=torch.float64, device=dev), t=t)
+    pr.make_struct()
+    return pr
+
+
+def completion_problem(rowptr, colind, mvals_f32, U0: torch.Tensor, mu: float, t: float = 1.0
+                       ) -> Problem:
+    n, p = U0.shape
+    dev = U0.device
+    pr = Problem(kind=B.PF_PROBLEM_COMPLETION, n=n, rowptr=rowptr, colind=colind, vals=mvals_f32,
+                 U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
+                 theta=torch.zeros(p, dtype=torch.float64, device=dev),
+                 S=torch.empty(colind.numel(), dtype=torch.float64, device=dev), t=t, mu=mu)
+    pr.make_struct()
+    return pr
+
+
+def problem_init(ctx: Context, pr: Problem) -> None:
+    B.pf_problem_init(ctx.handle, pr.struct)
+    pr.t = pr.struct.t
+
+
+def prox_step(ctx: Context, pr: Problem, want_info: bool = True):
+    return B.pf_prox_step(ctx.handle, pr.struct, want_info)
+
+
+def solve(ctx: Context, pr: Problem, max_iter: int, tol: float = 0.0, check_every: int = 10):
+    return B.pf_solve(ctx.handle, pr.struct, max_iter, tol, check_every)
+
+
+def csr_to_device(csr, device, vals_dtype=None):
+    """Copy a pf_synthetic.CSR to the device (int32 indices)."""
+    rp = torch.from_numpy(csr.rowptr).to(device=device, dtype=torch.int32)
+    ci = torch.from_numpy(csr.colind).to(device=device, dtype=torch.int32)
+    v = torch.from_numpy(csr.vals)
+    if vals_dtype is not None:
+        v = v.to(vals_dtype)
+    return rp, ci, v.to(device)

@@ -1,0 +1,130 @@
+"""Low-precision (tcgen05) dense filter: the tensor-core product and the
+bf16/tf32 filter against plain PyTorch references of the same operation.
+
+* product: Y = s * (A_lp X_lp) with A_lp = A/s in bf16 (or fp32 read as tf32)
+  and X_lp the block rounded the same way; reference = float64 matmul of the
+  identically rounded bf16 inputs (exact products, so only the kernel's fp32
+  accumulation order differs): |Y - ref| <= 1e-5 * max|ref|.  For tf32 the
+  hardware's input rounding is not emulated; the bound is the tf32 unit
+  roundoff: |Y - ref| <= 4e-3 * max|ref| against the unrounded fp64 product.
+* filter: the bf16 filter step against an fp32 PyTorch emulation of the same
+  recurrence (bf16 operands each step, fp32 recurrence, CholQR2 in fp64),
+  elementwise 2e-3; and the subspace it spans against the FP64 oracle's,
+  within the bf16 floor.
+"""
+import numpy as np
+import pytest
+
+import pf_synthetic as syn
+from oracle import pf_oracle as o
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_1904_10585_gb300  # noqa: F401
+    from paper_1904_10585_gb300 import solver
+    return solver
+
+
+def lp_operator(S, A_lp, scale):
+    import paper_1904_10585_gb300 as B
+    n = A_lp.shape[0]
+    return B.pf_operator(kind=B.PF_OP_DENSE, n=n, A=0, lda=n, A_lp=A_lp.data_ptr(),
+                         lda_lp=A_lp.stride(0), lp_scale=scale)
+
+
+def sym_matrix(n, seed):
+    g = torch.Generator().manual_seed(seed)
+    A = torch.randn(n, n, generator=g, dtype=torch.float64)
+    return (A + A.T) / 2
+
+
+@pytest.mark.parametrize("n,p", [(256, 64), (300, 16), (1000, 32), (513, 40), (129, 48), (2048, 64)])
+def test_bf16_product_matches_fp32_reference(S, n, p):
+    import paper_1904_10585_gb300 as B
+    A = sym_matrix(n, n + p)
+    s = float(A.abs().max())
+    A_lp = (A / s).to(torch.bfloat16).to(DEV)
+    X = torch.randn(n, p, dtype=torch.float64, generator=torch.Generator().manual_seed(p)).to(DEV)
+    Y = torch.empty(n, p, dtype=torch.float64, device=DEV)
+    with S.Context(p=p, n_max=n, degree=1, precision=B.PF_PREC_BF16) as ctx:
+        S.apply(ctx, lp_operator(S, A_lp, s), X, Y)
+        torch.cuda.synchronize()
+    ref = s * (A_lp.double() @ X.to(torch.float32).to(torch.bfloat16).double())
+    err = (Y - ref).abs().max().item()
+    assert err <= 1e-5 * ref.abs().max().item(), err
+
+
+@pytest.mark.parametrize("n,p", [(256, 32), (300, 64), (777, 16)])
+def test_tf32_product_within_tf32_roundoff(S, n, p):
+    import paper_1904_10585_gb300 as B
+    A = sym_matrix(n, 3 * n)
+    s = float(A.abs().max())
+    A_lp = (A / s).to(torch.float32).to(DEV).contiguous()
+    X = torch.randn(n, p, dtype=torch.float64, generator=torch.Generator().manual_seed(1)).to(DEV)
+    Y = torch.empty(n, p, dtype=torch.float64, device=DEV)
+    with S.Context(p=p, n_max=n, degree=1, precision=B.PF_PREC_TF32) as ctx:
+        S.apply(ctx, lp_operator(S, A_lp, s), X, Y)
+        torch.cuda.synchronize()
+    ref = A.to(DEV) @ X
+    err = (Y - ref).abs().max().item()
+    assert err <= 4e-3 * ref.abs().max().item(), err
+
+
+def emulate_bf16_filter(A_lp, s, U, a, b, d):
+    """Plain PyTorch reference of the bf16 filter step: fp32 recurrence with
+    the block rounded to bf16 before every product, then QR with a positive
+    diagonal in fp64."""
+    c, e = (a + b) / 2, (b - a) / 2
+    Af = A_lp.float()
+    Y0 = U.float()
+    Y1 = (s * (Af @ Y0.to(torch.bfloat16).float()) - c * Y0) / e
+    prev, cur = Y0, Y1
+    for _ in range(1, d):
+        nxt = 2 * (s * (Af @ cur.to(torch.bfloat16).float()) - c * cur) / e - prev
+        prev, cur = cur, nxt
+    Q, R = torch.linalg.qr(cur.double())
+    return Q * torch.sign(torch.diagonal(R))
+
+
+@pytest.mark.parametrize("n,p,d", [(512, 32, 4), (700, 64, 3), (300, 16, 6)])
+def test_bf16_filter_matches_emulation_and_oracle_subspace(S, n, p, d):
+    import paper_1904_10585_gb300 as B
+    lam = np.concatenate([np.linspace(6.0, 4.0, p), np.linspace(1.0, -3.0, n - p)])
+    Bm, Qm = syn.dense_symmetric_with_spectrum(n, lam, seed=n)
+    U0 = syn.gaussian_block(n, p, seed=p)
+    a, b = -3.2, 1.4
+    s = float(np.abs(Bm).max())
+    A_lp = torch.from_numpy(Bm / s).to(torch.bfloat16).to(DEV)
+    U = torch.from_numpy(U0).to(DEV)
+    with S.Context(p=p, n_max=n, degree=d, precision=B.PF_PREC_BF16) as ctx:
+        S.filter_(ctx, lp_operator(S, A_lp, s), a, b, d, U)
+        info = B.pf_get_info(ctx.handle)
+        torch.cuda.synchronize()
+    assert not (info.flags & 8), "device wait timed out"
+    ref = emulate_bf16_filter(A_lp, s, torch.from_numpy(U0).to(DEV), a, b, d)
+    assert (U - ref).abs().max().item() <= 2e-3
+    exact = o.orth(o.cheb_filter(lambda X: Bm @ X, U0, a, b, d))
+    Ug = U.cpu().numpy()
+    assert o.subspace_sine(exact, Ug) <= 0.05
+    # the filter helps: closer to the top-p eigenspace than the start block
+    assert o.subspace_sine(Qm[:, :p], Ug) < 0.5 * o.subspace_sine(Qm[:, :p], o.orth(U0))
+
+
+def test_lowprec_operator_validation(S):
+    import paper_1904_10585_gb300 as B
+    n, p = 64, 16
+    with S.Context(p=p, n_max=n, degree=2, precision=B.PF_PREC_BF16) as ctx:
+        A_lp = torch.zeros(n, n, dtype=torch.bfloat16, device=DEV)
+        U = torch.randn(n, p, dtype=torch.float64, device=DEV)
+        bad = lp_operator(S, A_lp, 0.0)          # scale must be positive
+        with pytest.raises(B.PFError):
+            S.filter_(ctx, bad, -1.0, 0.0, 2, U)
+        odd = torch.zeros(n, n + 1, dtype=torch.bfloat16, device=DEV)[:, :n]
+        with pytest.raises(B.PFError):           # row pitch not a multiple of 16 bytes
+            S.filter_(ctx, lp_operator(S, odd, 1.0), -1.0, 0.0, 2, U)
