@@ -42,9 +42,10 @@ TOL = 1e-4
 CHECK_EVERY = 10
 FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 nominal (no measured FP64 peak is provided)
 FP64_CUBLAS_MEASURED = 1.09    # torch float64 matmul 16384x16384x64 on this pool (context)
-# dram bytes per launch of the dominant kernel from the committed ncu capture
+HBM_PEAK_GBS = 6773.2          # measured STREAM-style copy on the GB300s
+# dram bytes per launch of the dominant kernel from the committed ncu captures
 # (None until a capture of the current kernel exists)
-NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_BYTES = {}
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -112,19 +113,6 @@ def dist_setup():
 # reference arm: the CPU oracle, bounded samples
 # ---------------------------------------------------------------------------
 
-def oracle_sample(cfg, inst, iters_sample: int):
-    """Time `iters_sample` PFAM iterations of the oracle; returns seconds."""
-    import scipy.sparse as sp
-    from oracle import pf_oracle as o
-    C = sp.csr_matrix((inst.C.vals, inst.C.colind, inst.C.rowptr), shape=(inst.n, inst.n))
-    t = o.maxcut_step_size(C)
-    t0 = time.perf_counter()
-    st = o.maxcut_init(C, inst.U0_raw[:, :cfg["p"]], t)
-    for _ in range(iters_sample):
-        st, info = o.maxcut_pfam_step(C, st, t, cfg["degree"])
-    return time.perf_counter() - t0
-
-
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -132,27 +120,83 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+class WorkloadSpec:
+    """Host-side description of one configuration (no GPU needed): the seeded
+    inputs, the oracle sample used by the CPU baseline and the config dict."""
+
+    def __init__(self, name):
+        self.name = name
+        self.cfg, self.inst = syn.make_workload(name)
+        c = self.cfg
+        self.n, self.p, self.d, self.iters = c["n"], c["p"], c["degree"], c["iters"]
+        self.kind = c["kind"]
+        self.lowprec = "bf16" if name.endswith("lowprec") else None
+
+    def nnz(self):
+        return self.inst.C.nnz if self.kind == "maxcut" else self.inst.omega.nnz
+
+    def oracle_sample(self, iters_sample):
+        """Seconds the oracle takes for the initial state + iters_sample iterations."""
+        import scipy.sparse as sp
+        from oracle import pf_oracle as o
+        t0 = time.perf_counter()
+        if self.kind == "maxcut":
+            inst = self.inst
+            C = sp.csr_matrix((inst.C.vals, inst.C.colind, inst.C.rowptr), shape=(inst.n, inst.n))
+            t = o.maxcut_step_size(C)
+            st = o.maxcut_init(C, inst.U0_raw[:, :self.p], t)
+            for _ in range(iters_sample):
+                st, _ = o.maxcut_pfam_step(C, st, t, self.d)
+        else:
+            Om = o.omega_matrix(self.inst.omega)
+            st = o.completion_init(self.n, self.inst.U0_raw[:, :self.p])
+            for _ in range(iters_sample):
+                st, _ = o.completion_pfpg_step(Om, st, self.cfg["mu"], self.cfg["t"], self.d)
+        return time.perf_counter() - t0
+
+    def sample_iters(self):
+        return min(self.iters, {"maxcut_n4096": 15, "completion_n400": 100}.get(self.name, 1))
+
+    def config(self):
+        c = self.cfg
+        d = {"workload": self.name, "n": c["n"], "p": c["p"], "degree": c["degree"],
+             "max_iters": c["iters"], "tol_kkt": TOL}
+        if self.kind == "maxcut":
+            d["problem"] = ("max-cut SDP (PFAM, dense FP64 iteration matrix)" if not self.lowprec
+                            else "max-cut SDP (PFAM, bf16 dense shadow filter on tcgen05, "
+                                 "structured FP64 Rayleigh-Ritz)")
+            d["graph"] = f"Erdos-Renyi p={c['prob']}, weights +-1"
+            bytes_z = self.n * self.n * (2 if self.lowprec else 8)
+        else:
+            d["problem"] = "PSD matrix completion (PFPG, low-rank + sparse FP64 operator)"
+            d["sampling"] = f"symmetric uniform {c['rate']}, rank {c['rank']}, mu {c['mu']}"
+            d["nnz"] = int(self.nnz())
+            bytes_z = self.nnz() * 16
+        d["l2"] = ("inputs larger than L2 (129 MB): iteration matrix %.0f MB" % (bytes_z / 1e6)
+                   if bytes_z > 129e6 else
+                   "working set fits L2 (%.1f MB); L2 not flushed between solves" % (bytes_z / 1e6))
+        return d
+
+
 def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
-    cfg, inst = syn.make_workload(WORKLOAD)
-    iters_sample = 2
+    W = WorkloadSpec(args.workload)
+    iters_sample = 2 if W.name == "maxcut_n4096" else max(1, W.sample_iters() // 10)
     for _ in range(args.warmup):
-        oracle_sample(cfg, inst, iters_sample)
-    times = []
-    for _ in range(args.steps):
-        times.append(oracle_sample(cfg, inst, iters_sample))
-    per_solve = [tt * cfg["iters"] / iters_sample for tt in times]
+        W.oracle_sample(iters_sample)
+    times = [W.oracle_sample(iters_sample) for _ in range(args.steps)]
+    per_solve = [tt * W.iters / iters_sample for tt in times]
     value = len(per_solve) / sum(per_solve)
-    sample = (f"{iters_sample} of {cfg['iters']} PFAM iterations per step (initial state + "
-              f"iterations), scaled to a {cfg['iters']}-iteration solve")
+    sample = (f"initial state + {iters_sample} of {W.iters} iterations per step, scaled to one "
+              f"{W.iters}-iteration solve")
     line = {
         "impl": "reference", "metric": "solves/s", "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(per_solve), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(cfg),
+        "config": W.config(),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": host_cores(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -162,17 +206,56 @@ def run_reference(args):
     return 0
 
 
-def config_dict(cfg):
-    return {"workload": WORKLOAD, "problem": "max-cut SDP (PFAM, dense FP64 iteration matrix)",
-            "n": cfg["n"], "p": cfg["p"], "degree": cfg["degree"], "max_iters": cfg["iters"],
-            "tol_kkt": TOL, "graph": "Erdos-Renyi p=0.01, weights +-1",
-            "l2": "inputs larger than L2: Z is n^2 FP64 = 134 MB > 129 MB L2, re-written "
-                  "every iteration"}
+class Workload(WorkloadSpec):
+    """Device side of a configuration: problem buffers and the dominant
+    kernel's operator."""
 
+    def __init__(self, name, dev, S, B):
+        import torch
+        super().__init__(name)
+        self.dev, self.S, self.B = dev, S, B
+        self.U0 = torch.from_numpy(np.ascontiguousarray(self.inst.U0_raw[:, :self.p])).to(dev)
+        if self.kind == "maxcut":
+            self.rp, self.ci, self.cv = S.csr_to_device(self.inst.C, dev, torch.float64)
+        else:
+            self.rp, self.ci, self.cv = S.csr_to_device(self.inst.omega, dev)
 
-# ---------------------------------------------------------------------------
-# our arm
-# ---------------------------------------------------------------------------
+    def precision(self):
+        return self.B.PF_PREC_BF16 if self.lowprec == "bf16" else self.B.PF_PREC_FP64
+
+    def problem(self, rp=None, ci=None, cv=None, U0=None):
+        S = self.S
+        rp = self.rp if rp is None else rp
+        ci = self.ci if ci is None else ci
+        cv = self.cv if cv is None else cv
+        U0 = self.U0 if U0 is None else U0
+        if self.kind == "maxcut":
+            if self.lowprec:
+                return S.maxcut_problem(rp, ci, cv, U0, dense=False, lowprec=self.lowprec)
+            return S.maxcut_problem(rp, ci, cv, U0)
+        return S.completion_problem(rp, ci, cv, U0, mu=self.cfg["mu"], t=self.cfg["t"])
+
+    def kernel_op(self, pr):
+        """(operator, description, bound, work per launch, unit) of the dominant kernel."""
+        S, B, n, p = self.S, self.B, self.n, self.p
+        if self.kind == "maxcut" and not self.lowprec:
+            return (S.dense_operator(pr.Z),
+                    "k_gemm_f64_splitk + k_combine (Y = Z X, dense FP64 filter product)",
+                    "alu", 2.0 * n * n * p, "TFLOP/s")
+        if self.kind == "maxcut":
+            op = S.dense_operator(None, A_lp=pr.Z_lp, lp_scale=1.0)
+            nbytes = 2.0 * n * n + n * p * (4 + 2)
+            return (op, "k_tc_filter<64,bf16> (tcgen05 bf16 filter product, TMA + TMEM)", "hbm",
+                    nbytes, "GB/s")
+        # completion: Y = X_k X - t S X - t mu X with X_k = V diag(max(theta,0)) V^T
+        th = pr.theta.clamp(min=0)
+        self._keep = th
+        op = S.lowrank_sparse_operator(n, pr.V, th, self.rp, self.ci, pr.S, -self.cfg["t"],
+                                       -self.cfg["t"] * self.cfg["mu"])
+        nnz = self.ci.numel()
+        return (op, "k_lrsp_apply (fused CSR SpMM + low-rank, FP64) + k_gram", "alu",
+                2.0 * nnz * p + 4.0 * n * p * p, "TFLOP/s")
+
 
 def run_ours(args):
     import torch
@@ -187,23 +270,21 @@ def run_ours(args):
     import paper_1904_10585_gb300 as pkg
     from paper_1904_10585_gb300 import solver as S
 
-    cfg, inst = syn.make_workload(WORKLOAD)
-    n, p, d, iters = cfg["n"], cfg["p"], cfg["degree"], cfg["iters"]
+    W = Workload(args.workload, dev, S, pkg)
+    n, p, d, iters = W.n, W.p, W.d, W.iters
     stream = torch.cuda.Stream(device=dev)
-    ctx = S.Context(p=p, n_max=n, degree=d, stream=stream)
-    rp, ci, cv = S.csr_to_device(inst.C, dev, torch.float64)
-    U0 = torch.from_numpy(np.ascontiguousarray(inst.U0_raw[:, :p])).to(dev)
-    pr = S.maxcut_problem(rp, ci, cv, U0)
+    ctx = S.Context(p=p, n_max=n, degree=d, stream=stream, precision=W.precision())
+    pr = W.problem()
 
     def solve_once(problem):
-        problem.U.copy_(U0)             # fresh start block (on the library stream below)
+        problem.U.copy_(W.U0)           # fresh start block (on the library stream below)
         S.problem_init(ctx, problem)
         return S.solve(ctx, problem, iters, TOL, CHECK_EVERY)
 
     # launch counting (non-graph calls): init + one step
     with torch.cuda.stream(stream):
         c0 = pkg.pf_kernel_launch_count()
-        pr.U.copy_(U0)
+        pr.U.copy_(W.U0)
         S.problem_init(ctx, pr)
         c1 = pkg.pf_kernel_launch_count()
         S.prox_step(ctx, pr, want_info=False)
@@ -215,7 +296,7 @@ def run_ours(args):
             for _ in range(3):
                 S.prox_step(ctx, pr, want_info=False)
         stream.synchronize()
-        print(json.dumps({"profile_run": WORKLOAD, "launches_per_iteration": step_launches}))
+        print(json.dumps({"profile_run": args.workload, "launches_per_iteration": step_launches}))
         ctx.close()
         return 0
 
@@ -246,13 +327,12 @@ def run_ours(args):
     iters_run = [int(r.iters) for r in results]
     gpu_launches = sum(init_launches + it * step_launches for it in iters_run)
 
-    # dominant kernel: the dense FP64 product Y = Z X (split-K GEMM + combine),
-    # timed with CUDA events on the library stream over R launches on the
-    # resident iteration matrix left by the timed solves.
+    # dominant kernel, timed with CUDA events on the library stream over R
+    # launches of the same operator on the state left by the timed solves.
     R = 20
+    op, kname, bound, work, unit = W.kernel_op(pr)
     X = pr.U.clone()
     Y = torch.empty_like(X)
-    op = S.dense_operator(pr.Z)
     with torch.cuda.stream(stream):
         for _ in range(3):
             S.apply(ctx, op, X, Y)
@@ -264,20 +344,25 @@ def run_ours(args):
         e1.record(stream)
     stream.synchronize()
     apply_ms = e0.elapsed_time(e1) / R
-    flops = 2.0 * n * n * p
-    achieved = flops / (apply_ms * 1e-3) / 1e12
+    if unit == "TFLOP/s":
+        achieved = work / (apply_ms * 1e-3) / 1e12
+        peak, peak_src = FP64_PEAK_TFLOPS, ("recipe nominal FP64 1.25 TFLOP/s (no measured FP64 peak; "
+                                            f"cuBLAS DGEMM reached {FP64_CUBLAS_MEASURED} on this pool)")
+    else:
+        achieved = work / (apply_ms * 1e-3) / 1e9
+        peak, peak_src = HBM_PEAK_GBS, "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
 
     # end to end through the public API: host (pinned) inputs copied in and the
     # solution factors read back inside the timed region
-    h_rp = rp.cpu().pin_memory()
-    h_ci = ci.cpu().pin_memory()
-    h_cv = cv.cpu().pin_memory()
-    h_u0 = U0.cpu().pin_memory()
+    h_rp = W.rp.cpu().pin_memory()
+    h_ci = W.ci.cpu().pin_memory()
+    h_cv = W.cv.cpu().pin_memory()
+    h_u0 = W.U0.cpu().pin_memory()
     h_V = torch.empty((n, p), dtype=torch.float64).pin_memory()
     h_th = torch.empty((p,), dtype=torch.float64).pin_memory()
-    d_rp, d_ci, d_cv = torch.empty_like(rp), torch.empty_like(ci), torch.empty_like(cv)
-    d_u0 = torch.empty_like(U0)
-    pe = S.maxcut_problem(d_rp, d_ci, d_cv, d_u0)
+    d_rp, d_ci, d_cv = torch.empty_like(W.rp), torch.empty_like(W.ci), torch.empty_like(W.cv)
+    d_u0 = torch.empty_like(W.U0)
+    pe = W.problem(d_rp, d_ci, d_cv, d_u0)
     h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_ci, h_cv, h_u0))
     d2h = h_V.numel() * 8 + h_th.numel() * 8
     e2e_steps = max(1, min(args.steps, 3))
@@ -315,31 +400,29 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        iters_sample = 15
-        secs = oracle_sample(cfg, inst, iters_sample)
+        iters_sample = W.sample_iters()
+        secs = W.oracle_sample(iters_sample)
         cpu = {"value": 1.0 / (secs * iters / iters_sample), "unit": "solves/s",
                "cores": host_cores(), "kind": "oracle",
-               "sample": f"initial state + {iters_sample} of {iters} PFAM iterations of the same "
+               "sample": f"initial state + {iters_sample} of {iters} iterations of the same "
                          f"workload ({secs:.1f} s), scaled to one {iters}-iteration solve"}
 
     last = results[-1].last
     line = {
         "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(cfg),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f64" if W.lowprec else "f64", "data": "synthetic",
+        "config": W.config(),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "solve": {"iters": iters_run[-1], "kkt": float(last.kkt), "obj": float(last.obj),
                   "pinf": float(last.pinf), "dinf": float(last.dinf), "gap": float(last.gap),
                   "r_plus": int(last.r_plus), "reached_tol": bool(last.kkt <= TOL)},
-        "roofline": {"kernel": "k_gemm_f64_splitk + k_combine (Y = Z X, dense FP64 filter product)",
-                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": NCU_TRAFFIC_BYTES,
-                     "flops_per_launch": flops, "avg_launch_ms": apply_ms,
-                     "peak_source": "recipe nominal FP64 1.25 TFLOP/s (no measured FP64 peak; "
-                                    f"cuBLAS DGEMM reached {FP64_CUBLAS_MEASURED} on this pool)"},
+        "roofline": {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": unit, "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC_BYTES.get(args.workload),
+                     "work_per_launch": work, "avg_launch_ms": apply_ms, "peak_source": peak_src},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
@@ -362,6 +445,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(syn.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="short run for profiler captures (init + 4 iterations, no timing)")

@@ -106,14 +106,23 @@ typedef struct {
  *  COMPLETION:  the sampled entries of M on Omega as a symmetric CSR
  *               (vals_f32); mu > 0; t the step size.
  * Resident state (read and written by every step; device, caller-owned):
- *  U     n x p block (ldu), the warm start of the filter.  On entry to
+ *  U     n x p block (ldu), the warm start of the filter (after each step
+ *        the Ritz basis V, the output U <- QV of the commented CheSE
+ *        algorithm of Sec. 2.1).  On entry to
  *        pf_problem_init it holds the start block (any full-rank n x p).
  *  V     n x p Ritz vectors of the last Rayleigh-Ritz step (ldv); with theta
  *        they hold the low-rank iterate X = V diag(max(theta,0)) V^T.
  *  theta p Ritz values of the last step, descending.
- *  Z     MAXCUT only: dense FP64 n x n iteration matrix (ldz).
+ *  Z     MAXCUT only: dense FP64 n x n iteration matrix (ldz).  NULL selects
+ *        the structured operator Z = X~ - tC - Diag(lam), applied without
+ *        forming Z (C must then store every diagonal entry, zeros included).
+ *  Z_lp  MAXCUT with a bf16 / tf32 context: the dense low-precision shadow
+ *        Z / s (n x n, ldz_lp elements, 16-byte aligned row pitch) that the
+ *        tensor-core filter reads; the Rayleigh-Ritz step then uses the
+ *        structured FP64 operator, so Z may be NULL.
  *  lam   MAXCUT only: n-vector lambda of the last DRS update.
- *  S     COMPLETION only: nnz FP64 values of P_Omega(X - M) (workspace).
+ *  S     nnz FP64 workspace: COMPLETION P_Omega(X - M); structured MAXCUT
+ *        the sparse part -tC - Diag(lam).
  * t: MAXCUT step; if t <= 0 on entry to pf_problem_init it is set to
  *    10 sqrt(n)/||C||_F.  COMPLETION step (t = 1 matches the Lipschitz
  *    constant of P_Omega).
@@ -128,6 +137,7 @@ typedef struct {
   double *V; int64_t ldv;
   double *theta;
   double *Z; int64_t ldz;
+  void *Z_lp; int64_t ldz_lp;
   double *lam;
   double *S;
   int64_t iter;          /* host-side counter, advanced by each step */

@@ -59,6 +59,10 @@ R7  Max-cut KKT: y = -lambda/t, S = (X~ - Z_k)/t;
     pinf = ||diag X~ - 1||_2/(1+sqrt n);
     dinf = ||C - Diag(y) - S||_F/(1+||C||_F) = ||Z_k - Z_{k+1}||_F/(t(1+||C||_F));
     gap  = |<C,X~> - 1^T y|/(1+|<C,X~>|+|1^T y|); kkt = max of the three.
+R9  The block carried to the next filter is the Ritz basis V~ = QY, the
+    output "U <- QV" of the commented CheSE algorithm (Sec. 2.1); it spans the
+    same subspace as the orthonormal Q (the warm start U^k of Eqs. (pfpg2),
+    (PFAM2)), so the filtered subspace is unchanged in exact arithmetic.
 R8  PSD completion, min_{X psd} 1/2||P_Omega(X-M)||^2 + mu tr X, PG step
     X+ = P_+(X - t P_Omega(X - M) - t mu I) (the symmetric analogue of the
     NNLS/SVT tests of Sec. 5.2); X^0 = 0; each iteration filters the current
@@ -288,7 +292,10 @@ def maxcut_pfam_step(C: sp.csr_matrix, st: MaxCutState, t: float, degree: int,
     Z_next = prox_G_maxcut(2.0 * Xt - Z, Cd, t) - Xt + Z       # T_DRS, Eq. (PFAM1)
     pobj, pinf, dinf, gap = _maxcut_kkt(C, Cd, Xt, Z, Z_next, lam, t)
     info = MaxCutInfo(a, b, pobj, pinf, dinf, gap, max(pinf, dinf, gap), int(pos.sum()), theta)
-    new = MaxCutState(Z=Z_next, U=U, lam=lam, theta_prev=theta,
+    # the extracted block carried to the next filter is the Ritz basis V~ = Q Y
+    # (the output U <- QV of the commented CheSE algorithm, Sec. 2.1); it spans
+    # the same subspace as Q
+    new = MaxCutState(Z=Z_next, U=V if not exact else U, lam=lam, theta_prev=theta,
                       Xt_V=V[:, pos], Xt_theta=theta[pos])
     return new, info
 
@@ -391,7 +398,7 @@ def completion_pfpg_step(Om: sp.csr_matrix, st: CompletionState, mu: float, t: f
     kkt = _lowrank_fro_diff(V, w, V_next, w_next) / (1.0 + Xnorm + t * Snorm)
     obj = 0.5 * Snorm ** 2 + mu * float(np.sum(w))
     info = CompletionInfo(a, b, obj, kkt, int(pos.sum()), theta)
-    return CompletionState(V=V_next, w=w_next, U=U, theta_prev=theta), info
+    return CompletionState(V=V_next, w=w_next, U=Vr if not exact else U, theta_prev=theta), info
 
 
 def completion_solve(omega, U0_raw, mu: float, t: float, degree: int, iters: int,

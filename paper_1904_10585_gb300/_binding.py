@@ -58,6 +58,7 @@ class pf_problem(C.Structure):
                 ("V", C.c_void_p), ("ldv", C.c_int64),
                 ("theta", C.c_void_p),
                 ("Z", C.c_void_p), ("ldz", C.c_int64),
+                ("Z_lp", C.c_void_p), ("ldz_lp", C.c_int64),
                 ("lam", C.c_void_p), ("S", C.c_void_p), ("iter", C.c_int64)]
 
 

@@ -149,14 +149,15 @@ pf_status filter_core_lp(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int 
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
   const bool tf32 = ctx->opt.precision == PF_PREC_TF32;
+  if (op.lp_scale > 0.0) PF_CUDA(launch_set_scale(s, ws.prm, op.lp_scale));
   PF_CUDA(launch_prep_lp(s, ws, tf32, U, ldu, op.n, ws.U32, ws.Xt[0]));
   for (int j = 0; j < degree; ++j) {
     const float *cur = j == 0 ? ws.U32 : ws.Y32[(j - 1) & 1];
     const float *prev = j == 1 ? ws.U32 : ws.Y32[j & 1];
     float *next = ws.Y32[j & 1];
     void *xt_next = (j + 1 < degree) ? ws.Xt[(j + 1) & 1] : nullptr;
-    PF_CUDA(launch_tc_product(s, ws, tf32, op.A_lp, op.lda_lp, op.lp_scale, op.n, ws.Xt[j & 1],
-                              cur, prev, next, xt_next, j == 0 ? MODE_FIRST : MODE_RECUR));
+    PF_CUDA(launch_tc_product(s, ws, tf32, op.A_lp, op.lda_lp, op.n, ws.Xt[j & 1], cur, prev,
+                              next, xt_next, j == 0 ? MODE_FIRST : MODE_RECUR));
   }
   PF_CUDA(launch_f32_to_f64(s, ws, ws.Y32[(degree - 1) & 1], (int64_t)op.n * p, ws.Y[0]));
   return cholqr2(ctx, ws.Y[0], p, U, ldu, op.n);
@@ -203,8 +204,20 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
     return set_err(ctx, PF_ERR_INVALID_ARG, "problem needs U, V (ld >= p) and theta");
   if (pr->kind == PF_PROBLEM_MAXCUT) {
     if (!pr->vals_f64) return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut needs vals_f64 (C)");
-    if (!pr->Z || pr->ldz < pr->n || !pr->lam)
-      return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut needs Z (ldz >= n) and lam");
+    if (!pr->lam) return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut needs lam");
+    const bool lp = ctx->opt.precision != PF_PREC_FP64;
+    if (lp) {
+      const int esz = ctx->opt.precision == PF_PREC_TF32 ? 4 : 2;
+      if (!pr->Z_lp || pr->ldz_lp < pr->n || (pr->ldz_lp * esz) % 16 != 0 ||
+          ((uintptr_t)pr->Z_lp & 15) != 0)
+        return set_err(ctx, PF_ERR_INVALID_ARG,
+                       "low-precision max-cut needs Z_lp (16-byte aligned, ldz_lp >= n, 16-byte "
+                       "row pitch)");
+    }
+    if (pr->Z != nullptr && pr->ldz < pr->n)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut Z needs ldz >= n");
+    if ((lp || pr->Z == nullptr) && !pr->S)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "structured max-cut needs the S workspace (nnz)");
   } else if (pr->kind == PF_PROBLEM_COMPLETION) {
     if (!pr->vals_f32 || !pr->S)
       return set_err(ctx, PF_ERR_INVALID_ARG, "completion needs vals_f32 (M on Omega) and S");
@@ -223,7 +236,48 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
   const int degree = ctx->opt.degree;
-  if (pr->kind == PF_PROBLEM_MAXCUT) {
+  const bool lp = ctx->opt.precision != PF_PREC_FP64;
+  if (pr->kind == PF_PROBLEM_MAXCUT && (lp || pr->Z == nullptr)) {
+    // structured Z = X~prev - tC - Diag(lam) for the Rayleigh-Ritz step (and
+    // for the filter unless a low-precision dense shadow is used)
+    PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
+    PF_CUDA(launch_maxcut_sparse_part(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, pr->lam,
+                                      pr->S));
+    PF_CUDA(launch_interval(s, ws, PF_PROBLEM_MAXCUT, pr->rowptr, pr->colind, pr->vals_f64, n,
+                            pr->lam, ws.thprev, p));
+    Op op = {};
+    op.kind = PF_OP_LOWRANK_SPARSE;
+    op.n = n;
+    op.Uf = ws.Vprev;
+    op.lduf = p;
+    op.lam = ws.thprev;
+    op.r = p;
+    op.clamp = 1;
+    op.rowptr = pr->rowptr;
+    op.colind = pr->colind;
+    op.vals = pr->S;
+    op.sscale = 1.0;
+    op.shift = 0.0;
+    if (lp) {
+      Op dop = {};
+      dop.kind = PF_OP_DENSE;
+      dop.n = n;
+      dop.A_lp = pr->Z_lp;
+      dop.lda_lp = pr->ldz_lp;
+      dop.lp_scale = 0.0;  // the scale the shadow was written with is on the device
+      PF_TRY(filter_core_lp(ctx, dop, pr->U, pr->ldu, degree));
+    } else {
+      PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
+    }
+    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
+    PF_CUDA(launch_maxcut_struct_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V,
+                                        pr->ldv, pr->theta, pr->lam));
+    if (lp)
+      PF_CUDA(launch_maxcut_lp_shadow(s, ws, ctx->opt.precision == PF_PREC_TF32, pr->rowptr,
+                                      pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv, pr->theta,
+                                      pr->lam, pr->Z_lp, pr->ldz_lp));
+  } else if (pr->kind == PF_PROBLEM_MAXCUT) {
     PF_CUDA(launch_interval(s, ws, PF_PROBLEM_MAXCUT, pr->rowptr, pr->colind, pr->vals_f64, n,
                             pr->lam, pr->theta, p));
     Op op = {};
@@ -233,6 +287,7 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
     op.lda = pr->ldz;
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_maxcut_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv,
                                  pr->theta, pr->Z, pr->ldz, pr->lam));
   } else {
@@ -256,6 +311,7 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
     op.shift = -pr->t * pr->mu;
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_completion_kkt(s, ws, pr->V, pr->ldv, pr->theta, n, p));
   }
   return PF_OK;
@@ -287,7 +343,8 @@ bool same_problem(const pf_problem &a, const pf_problem &b) {
   return a.kind == b.kind && a.n == b.n && a.rowptr == b.rowptr && a.colind == b.colind &&
          a.vals_f64 == b.vals_f64 && a.vals_f32 == b.vals_f32 && a.nnz == b.nnz && a.t == b.t &&
          a.mu == b.mu && a.U == b.U && a.ldu == b.ldu && a.V == b.V && a.ldv == b.ldv &&
-         a.theta == b.theta && a.Z == b.Z && a.ldz == b.ldz && a.lam == b.lam && a.S == b.S;
+         a.theta == b.theta && a.Z == b.Z && a.ldz == b.ldz && a.lam == b.lam && a.S == b.S &&
+         a.Z_lp == b.Z_lp && a.ldz_lp == b.ldz_lp;
 }
 
 }  // namespace
@@ -316,6 +373,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   int sms = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = configure_skinny();
+  if (e == cudaSuccess) e = configure_sparse();
   if (e == cudaSuccess && lp) e = configure_tc();
   if (e != cudaSuccess) {
     delete ctx;
@@ -443,9 +501,10 @@ pf_status pf_apply(pf_ctx *ctx, const pf_operator *op, const double *X, int64_t 
   if (o.kind == PF_OP_DENSE && o.A_lp != nullptr && ctx->opt.precision != PF_PREC_FP64) {
     const bool tf32 = ctx->opt.precision == PF_PREC_TF32;
     const Workspace &ws = ctx->ws;
+    PF_CUDA(launch_set_scale(ctx->stream, ws.prm, o.lp_scale));
     PF_CUDA(launch_prep_lp(ctx->stream, ws, tf32, X, ldx, o.n, ws.U32, ws.Xt[0]));
-    PF_CUDA(launch_tc_product(ctx->stream, ws, tf32, o.A_lp, o.lda_lp, o.lp_scale, o.n, ws.Xt[0],
-                              ws.U32, nullptr, ws.Y32[0], nullptr, MODE_PLAIN));
+    PF_CUDA(launch_tc_product(ctx->stream, ws, tf32, o.A_lp, o.lda_lp, o.n, ws.Xt[0], ws.U32,
+                              nullptr, ws.Y32[0], nullptr, MODE_PLAIN));
     if (ldy == ctx->p)
       PF_CUDA(launch_f32_to_f64(ctx->stream, ws, ws.Y32[0], (int64_t)o.n * ctx->p, Y));
     else
@@ -479,8 +538,15 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
     PF_CUDA(launch_params_init(s, ws.prm, ctx->opt.eta, t, 0.0, ctx->opt.degree,
                                ctx->opt.precision));
     PF_CUDA(launch_cnorm(s, ws, pr->vals_f64, pr->nnz));
-    PF_CUDA(launch_maxcut_init(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, t, pr->Z, pr->ldz,
-                               pr->lam));
+    if (pr->Z != nullptr)
+      PF_CUDA(launch_maxcut_init(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, t, pr->Z,
+                                 pr->ldz, pr->lam));
+    else
+      PF_CUDA(launch_maxcut_init_lam(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, t, pr->lam));
+    if (ctx->opt.precision != PF_PREC_FP64)
+      PF_CUDA(launch_maxcut_lp_shadow(s, ws, ctx->opt.precision == PF_PREC_TF32, pr->rowptr,
+                                      pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv, pr->theta,
+                                      pr->lam, pr->Z_lp, pr->ldz_lp));
   }
   PF_CUDA(cudaStreamSynchronize(s));
   PF_CUDA(cudaGetLastError());

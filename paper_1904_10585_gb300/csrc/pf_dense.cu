@@ -142,7 +142,15 @@ __global__ void k_set_interval(Params *prm, double a, double b) {
   prm->e = 0.5 * (b - a);
 }
 
+__global__ void k_set_scale(Params *prm, double lp_scale) { prm->lp_scale = lp_scale; }
+
 }  // namespace
+
+cudaError_t launch_set_scale(cudaStream_t s, Params *prm, double lp_scale) {
+  k_set_scale<<<1, 1, 0, s>>>(prm, lp_scale);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_set_interval(cudaStream_t s, Params *prm, double a, double b) {
   k_set_interval<<<1, 1, 0, s>>>(prm, a, b);

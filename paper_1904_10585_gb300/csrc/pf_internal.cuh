@@ -31,6 +31,7 @@ struct Params {
   double eta;
   double t, mu;           // step size, completion weight
   double Cnorm;           // ||C||_F (max-cut)
+  double lp_scale;        // s of the low-precision shadow A_lp = A / s
   double obj, kkt, pinf, dinf, gap;
   double theta_max, theta_min;
   int have_prev;          // a previous Rayleigh-Ritz step exists
@@ -82,6 +83,7 @@ extern std::atomic<int64_t> g_launches;
 // ---------------------------------------------------------------------------
 cudaError_t configure_skinny();
 cudaError_t configure_tc();
+cudaError_t configure_sparse();
 // K splits of the dense FP64 product for size n (returns S, sets the chunk).
 int dense_splits(int n, int num_sms, int *kchunk);
 
@@ -89,6 +91,7 @@ int dense_splits(int n, int num_sms, int *kchunk);
 // launchers (each returns the launch error, if any)
 // ---------------------------------------------------------------------------
 cudaError_t launch_set_interval(cudaStream_t s, Params *prm, double a, double b);
+cudaError_t launch_set_scale(cudaStream_t s, Params *prm, double lp_scale);
 cudaError_t launch_dense_apply(cudaStream_t s, const Workspace &ws, const Op &op, const double *X,
                                int64_t ldx, const double *Yprev, int64_t ldp, double *Ynext,
                                int64_t ldn, int mode);
@@ -111,7 +114,7 @@ cudaError_t launch_lowrank_coef(cudaStream_t s, const Workspace &ws, int nparts,
 
 // tensor-core (tcgen05) low-precision filter product and its conversions
 cudaError_t launch_tc_product(cudaStream_t s, const Workspace &ws, bool tf32, const void *A_lp,
-                              int64_t lda_lp, double lp_scale, int n, const void *Xt,
+                              int64_t lda_lp, int n, const void *Xt,
                               const float *Ycur, const float *Yprev, float *Ynext, void *Xt_next,
                               int mode);
 cudaError_t launch_prep_lp(cudaStream_t s, const Workspace &ws, bool tf32, const double *U,
@@ -139,6 +142,23 @@ cudaError_t launch_completion_kkt(cudaStream_t s, const Workspace &ws, const dou
                                   const double *theta, int n, int p);
 cudaError_t launch_save_prev(cudaStream_t s, const Workspace &ws, const double *V, int64_t ldv,
                              const double *theta, int n, int p);
+cudaError_t launch_maxcut_sparse_part(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                      const int32_t *colind, const double *vals, int n,
+                                      const double *lam, double *Sout);
+cudaError_t launch_maxcut_struct_update(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                        const int32_t *colind, const double *vals, int n, int p,
+                                        const double *V, int64_t ldv, const double *theta,
+                                        double *lam);
+cudaError_t launch_maxcut_init_lam(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                   const int32_t *colind, const double *vals, int n, double t,
+                                   double *lam);
+cudaError_t launch_maxcut_lp_shadow(cudaStream_t s, const Workspace &ws, bool f32out,
+                                    const int32_t *rowptr, const int32_t *colind,
+                                    const double *vals, int n, int p, const double *V, int64_t ldv,
+                                    const double *theta, const double *lam, void *Zlp,
+                                    int64_t ldz);
+cudaError_t launch_copy_block(cudaStream_t s, const Workspace &ws, const double *src, int64_t lds,
+                              int n, int p, double *dst, int64_t ldd);
 cudaError_t launch_fill(cudaStream_t s, double *x, int64_t rows, int64_t cols, int64_t ld, double v);
 cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,
                                int degree, int precision);

@@ -312,7 +312,9 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double *__restrict__ gpart,
         double c = 1.0, s = 0.0;
         if (l < p) {
           const double hkl = H[k][l];
-          if (hkl != 0.0) {
+          // rotations below the relative threshold change nothing at FP64
+          // precision and are skipped (cost then scales with the active pairs)
+          if (fabs(hkl) > 1e-17 * sqrt(fabs(H[k][k]) * fabs(H[l][l])) && hkl != 0.0) {
             const double tau = (H[l][l] - H[k][k]) / (2.0 * hkl);
             double t;
             if (fabs(tau) > 1e150) t = 0.5 / tau;
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double *__restrict__ gpart,
       for (int idx = tid; idx < half * p; idx += NT) {
         const int i = idx / p, col = idx % p;
         const int k = pk[i], l = pl[i];
-        if (l >= p) continue;
+        if (l >= p || sn[i] == 0.0) continue;
         const double c = cs[i], s = sn[i];
         const double hk = H[k][col], hl = H[l][col];
         H[k][col] = c * hk - s * hl;
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double *__restrict__ gpart,
       for (int idx = tid; idx < half * p; idx += NT) {
         const int i = idx / p, row = idx % p;
         const int k = pk[i], l = pl[i];
-        if (l >= p) continue;
+        if (l >= p || sn[i] == 0.0) continue;
         const double c = cs[i], s = sn[i];
         const double hk = H[row][k], hl = H[row][l];
         H[row][k] = c * hk - s * hl;

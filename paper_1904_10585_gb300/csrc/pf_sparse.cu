@@ -2,6 +2,8 @@
 // completion, the interval [a, b] of Sec. 4.1, the max-cut DRS update of
 // Eqs. (PFAM1)-(PFAM2) with its KKT report, and the completion residual /
 // fixed-point report of PFPG (Eqs. (pfpg1)-(pfpg2)).
+#include <cuda_bf16.h>
+
 #include "pf_internal.cuh"
 
 namespace pf {
@@ -112,14 +114,18 @@ __global__ void __launch_bounds__(NT) k_interval_rows(int kind, const int32_t *_
   }
 }
 
-__global__ void k_interval_final(const double *__restrict__ red, int nb,
-                                 const double *__restrict__ theta, int p, Params *prm) {
-  if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(NT) k_interval_final(const double *__restrict__ red, int nb,
+                                                       const double *__restrict__ theta, int p,
+                                                       Params *prm) {
+  __shared__ double sh[32];
   double a = INFINITY, ubs = -INFINITY;
-  for (int q = 0; q < nb; ++q) {
+  for (int q = threadIdx.x; q < nb; q += NT) {
     a = fmin(a, red[q * kRedWidth + 0]);
     ubs = fmax(ubs, red[q * kRedWidth + 1]);
   }
+  a = block_reduce(a, sh, 1);
+  ubs = block_reduce(ubs, sh, 2);
+  if (threadIdx.x != 0) return;
   const int have = prm->have_prev;
   const double thmax = have ? fmax(theta[0], 0.0) : 0.0;
   double ub = fmax(ubs + thmax, 0.0);
@@ -178,11 +184,13 @@ __global__ void __launch_bounds__(NT) k_sumsq(const double *__restrict__ v, int6
   if (threadIdx.x == 0) red[blockIdx.x * kRedWidth] = s;
 }
 
-__global__ void k_cnorm_final(const double *__restrict__ red, int nb, Params *prm) {
-  if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(NT) k_cnorm_final(const double *__restrict__ red, int nb,
+                                                    Params *prm) {
+  __shared__ double sh[32];
   double s = 0.0;
-  for (int q = 0; q < nb; ++q) s += red[q * kRedWidth];
-  prm->Cnorm = sqrt(s);
+  for (int q = threadIdx.x; q < nb; q += NT) s += red[q * kRedWidth];
+  s = block_reduce(s, sh, 0);
+  if (threadIdx.x == 0) prm->Cnorm = sqrt(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -235,6 +243,9 @@ __global__ void __launch_bounds__(NT) k_maxcut_lambda(const int32_t *__restrict_
 
 constexpr int EB = 32;  // expand tile (EB x EB outputs, 2 x 2 per thread)
 
+// Z+ is symmetric (X~, C and Diag(lam) are), so only tiles with ti <= tj are
+// computed; an off-diagonal tile is also written to its mirror position
+// through shared memory (coalesced transposed store).
 template <int PT>
 __global__ void __launch_bounds__(NT) k_maxcut_expand(const int32_t *__restrict__ rowptr,
                                                       const int32_t *__restrict__ colind,
@@ -244,19 +255,32 @@ __global__ void __launch_bounds__(NT) k_maxcut_expand(const int32_t *__restrict_
                                                       const double *__restrict__ lam, double *Z,
                                                       int64_t ldz, const Params *__restrict__ prm,
                                                       double *__restrict__ red) {
-  __shared__ double Vi[EB][PT + 1];
-  __shared__ double Vj[EB][PT + 1];
+  // one buffer: V rows of the tile (Vi, Vj) during the product, then the
+  // staged transpose of the mirror tile (EB x (EB + 1) <= 2 EB (PT + 1))
+  static_assert(EB * (EB + 1) <= 2 * EB * (PT + 1), "staging tile must fit the V buffers");
+  __shared__ double vbuf[2 * EB * (PT + 1)];
+  double(*Vi)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(vbuf);
+  double(*Vj)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(vbuf + EB * (PT + 1));
+  double(*Zs)[EB + 1] = reinterpret_cast<double(*)[EB + 1]>(vbuf);
   __shared__ double Ct[EB][EB + 1];
   __shared__ double sh[32];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const double t = prm->t;
   int rp = 0;
   for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
-  const int tiles1 = (n + EB - 1) / EB;
-  const int64_t ntiles = (int64_t)tiles1 * tiles1;
+  const int T = (n + EB - 1) / EB;
+  const int64_t ntiles = (int64_t)T * (T + 1) / 2;
   double dsum = 0.0, cx = 0.0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int i0 = (int)(tile / tiles1) * EB, j0 = (int)(tile % tiles1) * EB;
+    // tile -> (ti, tj) with ti <= tj, row-major over the upper triangle
+    int ti = 0;
+    int64_t rem = tile;
+    while (rem >= T - ti) {
+      rem -= T - ti;
+      ++ti;
+    }
+    const int tj = ti + (int)rem;
+    const int i0 = ti * EB, j0 = tj * EB;
     __syncthreads();
     for (int idx = tid; idx < EB * PT; idx += NT) {
       const int r = idx / PT, l = idx % PT;
@@ -292,14 +316,15 @@ __global__ void __launch_bounds__(NT) k_maxcut_expand(const int32_t *__restrict_
       acc[1][0] = fma(a1, b0, acc[1][0]);
       acc[1][1] = fma(a1, b1, acc[1][1]);
     }
+    const bool mirror = ti != tj;
+    __syncthreads();  // the V buffers are reused below as the staging tile of the mirror
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int li = ty * 2 + i, gi = i0 + li;
-      if (gi >= n) continue;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int lj = tx + 16 * j, gj = j0 + lj;
-        if (gj >= n) continue;
+        if (gi >= n || gj >= n) continue;
         const double cij = Ct[li][lj];
         double znew = acc[i][j] - t * cij;
         if (gi == gj) znew -= lam[gi];
@@ -308,6 +333,20 @@ __global__ void __launch_bounds__(NT) k_maxcut_expand(const int32_t *__restrict_
         dsum = fma(d, d, dsum);
         cx = fma(cij, acc[i][j], cx);
         *zp = znew;
+        if (mirror) {
+          Zs[lj][li] = znew;  // staged transpose
+          const double dm = Z[(int64_t)gj * ldz + gi] - znew;
+          dsum = fma(dm, dm, dsum);
+          cx = fma(cij, acc[i][j], cx);
+        }
+      }
+    }
+    if (mirror) {
+      __syncthreads();
+      for (int idx = tid; idx < EB * EB; idx += NT) {
+        const int r = idx / EB, c = idx % EB;  // row of the mirror tile = column of this one
+        const int gr = j0 + r, gc = i0 + c;
+        if (gr < n && gc < n) Z[(int64_t)gr * ldz + gc] = Zs[r][c];
       }
     }
   }
@@ -319,19 +358,25 @@ __global__ void __launch_bounds__(NT) k_maxcut_expand(const int32_t *__restrict_
   }
 }
 
-__global__ void k_maxcut_kkt(const double *__restrict__ red_lam, int nb_lam,
-                             const double *__restrict__ red_exp, int nb_exp,
-                             const double *__restrict__ theta, int n, int p, Params *prm) {
-  if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ red_lam, int nb_lam,
+                                                   const double *__restrict__ red_exp, int nb_exp,
+                                                   const double *__restrict__ theta, int n, int p,
+                                                   Params *prm) {
+  __shared__ double sh[32];
   double spinf = 0.0, slam = 0.0, dsum = 0.0, cx = 0.0;
-  for (int q = 0; q < nb_lam; ++q) {
+  for (int q = threadIdx.x; q < nb_lam; q += NT) {
     spinf += red_lam[q * kRedWidth + 0];
     slam += red_lam[q * kRedWidth + 1];
   }
-  for (int q = 0; q < nb_exp; ++q) {
+  for (int q = threadIdx.x; q < nb_exp; q += NT) {
     dsum += red_exp[q * kRedWidth + 0];
     cx += red_exp[q * kRedWidth + 1];
   }
+  spinf = block_reduce(spinf, sh, 0);
+  slam = block_reduce(slam, sh, 0);
+  dsum = block_reduce(dsum, sh, 0);
+  cx = block_reduce(cx, sh, 0);
+  if (threadIdx.x != 0) return;
   const double t = prm->t;
   const double pinf = sqrt(spinf) / (1.0 + sqrt((double)n));
   const double dinf = sqrt(dsum) / (t * (1.0 + prm->Cnorm));
@@ -413,9 +458,10 @@ __global__ void __launch_bounds__(NT) k_completion_kkt(const double *__restrict_
     cross = fma(wa * wb, m * m, cross);
   }
   cross = block_reduce(cross, sh, 0);
-  if (tid != 0) return;
   double ssq = 0.0;
-  for (int q = 0; q < nb_s; ++q) ssq += red_s[q * kRedWidth];
+  for (int q = tid; q < nb_s; q += NT) ssq += red_s[q * kRedWidth];
+  ssq = block_reduce(ssq, sh, 0);
+  if (tid != 0) return;
   double n1 = 0.0, n2 = 0.0, tr = 0.0;
   int rp = 0;
   for (int l = 0; l < p; ++l) {
@@ -509,7 +555,7 @@ cudaError_t launch_interval(cudaStream_t s, const Workspace &ws, int kind, const
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_interval_final<<<1, 32, 0, s>>>(slot(ws, SLOT_INTERVAL), nb, theta, p, ws.prm);
+  k_interval_final<<<1, NT, 0, s>>>(slot(ws, SLOT_INTERVAL), nb, theta, p, ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
@@ -546,7 +592,7 @@ cudaError_t launch_cnorm(cudaStream_t s, const Workspace &ws, const double *vals
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_cnorm_final<<<1, 32, 0, s>>>(slot(ws, SLOT_MISC), (int)nb, ws.prm);
+  k_cnorm_final<<<1, NT, 0, s>>>(slot(ws, SLOT_MISC), (int)nb, ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
@@ -562,7 +608,7 @@ cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int3
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t tiles1 = (n + EB - 1) / EB;
-  int64_t nb2 = tiles1 * tiles1;
+  int64_t nb2 = tiles1 * (tiles1 + 1) / 2;
   if (nb2 > kMaxRedBlocks) nb2 = kMaxRedBlocks;
   if (p <= 16)
     {
@@ -584,7 +630,7 @@ cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int3
     }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_maxcut_kkt<<<1, 32, 0, s>>>(slot(ws, SLOT_LAMBDA), nb1, slot(ws, SLOT_EXPAND), (int)nb2, theta,
+  k_maxcut_kkt<<<1, NT, 0, s>>>(slot(ws, SLOT_LAMBDA), nb1, slot(ws, SLOT_EXPAND), (int)nb2, theta,
                                 n, p, ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
@@ -626,6 +672,399 @@ cudaError_t launch_save_prev(cudaStream_t s, const Workspace &ws, const double *
 cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,
                                int degree, int precision) {
   k_params_init<<<1, 1, 0, s>>>(prm, eta, t, mu, degree, precision);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+}  // namespace pf
+
+// ===========================================================================
+// Structured max-cut iteration matrix Z = X~ - tC - Diag(lam), applied without
+// forming Z (the update of Eq. (PFAM1) shows Z_{k+1} is exactly this
+// low-rank + sparse + diagonal sum).
+// ===========================================================================
+namespace pf {
+namespace {
+
+// S' = -tC - Diag(lam) on C's pattern (C stores every diagonal entry).
+__global__ void __launch_bounds__(NT) k_maxcut_sparse_part(const int32_t *__restrict__ rowptr,
+                                                           const int32_t *__restrict__ colind,
+                                                           const double *__restrict__ vals, int n,
+                                                           const double *__restrict__ lam,
+                                                           const Params *__restrict__ prm,
+                                                           double *__restrict__ Sout) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * WPB;
+  const double t = prm->t;
+  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
+    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+      double v = -t * vals[e];
+      if (colind[e] == row) v -= lam[row];
+      Sout[e] = v;
+    }
+  }
+}
+
+// lam_new = 2 diag(X~) - diag(Z) - t diag(C) - 1 with
+// diag(Z) = diag(X~prev) - t diag(C) - lam_prev, i.e.
+// lam_new = 2 dX - dXprev + lam_prev - 1; plus the KKT partial sums and
+// <C, X~> over C's pattern.
+__global__ void __launch_bounds__(NT) k_maxcut_struct_update(
+    const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
+    const double *__restrict__ vals, int n, int p, const double *__restrict__ V, int64_t ldv,
+    const double *__restrict__ theta, const double *__restrict__ Vp, int64_t ldvp,
+    const double *__restrict__ thp, double *__restrict__ lam, double *__restrict__ red) {
+  __shared__ double wv[WPB][kMaxP];
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int warps = gridDim.x * WPB;
+  int rp = 0;
+  for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
+  double s_pinf = 0.0, s_lam = 0.0, s_cross = 0.0, s_d2 = 0.0, s_cx = 0.0;
+  for (int row = blockIdx.x * WPB + w; row < n; row += warps) {
+    double dx = 0.0, dxp = 0.0;
+    for (int l = lane; l < p; l += 32) {
+      const double th = theta[l], tp = thp[l];
+      const double v = V[(int64_t)row * ldv + l];
+      const double vp = Vp[(int64_t)row * ldvp + l];
+      if (th > 0.0) dx = fma(th * v, v, dx);
+      if (tp > 0.0) dxp = fma(tp * vp, vp, dxp);
+      wv[w][l] = th > 0.0 ? th * v : 0.0;
+    }
+    dx = warp_sum(dx);
+    dxp = warp_sum(dxp);
+    __syncwarp();
+    double cx = 0.0;
+    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+      const int col = colind[e];
+      double x = 0.0;
+      for (int l = 0; l < rp; ++l) x = fma(wv[w][l], V[(int64_t)col * ldv + l], x);
+      cx = fma(vals[e], x, cx);
+    }
+    cx = warp_sum(cx);
+    __syncwarp();
+    if (lane == 0) {
+      const double lp = lam[row];
+      const double ln = 2.0 * dx - dxp + lp - 1.0;
+      const double dl = ln - lp;
+      lam[row] = ln;
+      s_pinf = fma(dx - 1.0, dx - 1.0, s_pinf);
+      s_lam += ln;
+      s_cross = fma(dl, dxp - dx, s_cross);
+      s_d2 = fma(dl, dl, s_d2);
+      s_cx += cx;
+    }
+  }
+  s_pinf = block_reduce(s_pinf, sh, 0);
+  s_lam = block_reduce(s_lam, sh, 0);
+  s_cross = block_reduce(s_cross, sh, 0);
+  s_d2 = block_reduce(s_d2, sh, 0);
+  s_cx = block_reduce(s_cx, sh, 0);
+  if (threadIdx.x == 0) {
+    double *o = red + (int64_t)blockIdx.x * 2 * kRedWidth;
+    o[0] = s_pinf;
+    o[1] = s_lam;
+    o[2] = s_cross;
+    o[3] = s_d2;
+    o[4] = s_cx;
+  }
+}
+
+// KKT of the structured update.  ||Z_k - Z_{k+1}||^2 = ||A||^2 + 2 sum dl (A_ii)
+// + sum dl^2 with A = X~prev - X~ and ||A||^2 from M = Vprev^T V.
+__global__ void __launch_bounds__(NT) k_maxcut_struct_kkt(const double *__restrict__ gpart,
+                                                          int nparts,
+                                                          const double *__restrict__ red, int nb,
+                                                          const double *__restrict__ thp,
+                                                          const double *__restrict__ theta, int n,
+                                                          int p, Params *prm) {
+  __shared__ double sh[32];
+  const int tid = threadIdx.x;
+  double cross = 0.0;
+  for (int idx = tid; idx < p * p; idx += NT) {
+    const int a = idx / p, b = idx % p;
+    const double wa = fmax(thp[a], 0.0), wb = fmax(theta[b], 0.0);
+    if (wa == 0.0 || wb == 0.0) continue;
+    double m = 0.0;
+    for (int q = 0; q < nparts; ++q) m += gpart[(int64_t)q * p * p + idx];
+    cross = fma(wa * wb, m * m, cross);
+  }
+  cross = block_reduce(cross, sh, 0);
+  double s_pinf = 0.0, s_lam = 0.0, s_cr = 0.0, s_d2 = 0.0, s_cx = 0.0;
+  for (int q = tid; q < nb; q += NT) {
+    const double *o = red + (int64_t)q * 2 * kRedWidth;
+    s_pinf += o[0];
+    s_lam += o[1];
+    s_cr += o[2];
+    s_d2 += o[3];
+    s_cx += o[4];
+  }
+  s_pinf = block_reduce(s_pinf, sh, 0);
+  s_lam = block_reduce(s_lam, sh, 0);
+  s_cr = block_reduce(s_cr, sh, 0);
+  s_d2 = block_reduce(s_d2, sh, 0);
+  s_cx = block_reduce(s_cx, sh, 0);
+  if (tid != 0) return;
+  double n1 = 0.0, n2 = 0.0;
+  int rp = 0;
+  for (int l = 0; l < p; ++l) {
+    const double wa = fmax(thp[l], 0.0), wb = fmax(theta[l], 0.0);
+    n1 = fma(wa, wa, n1);
+    n2 = fma(wb, wb, n2);
+    rp += theta[l] > 0.0 ? 1 : 0;
+  }
+  const double a2 = n1 - 2.0 * cross + n2;
+  const double d2 = a2 + 2.0 * s_cr + s_d2;
+  const double t = prm->t;
+  const double pinf = sqrt(s_pinf) / (1.0 + sqrt((double)n));
+  const double dinf = sqrt(fmax(d2, 0.0)) / (t * (1.0 + prm->Cnorm));
+  const double pobj = s_cx;
+  const double dobj = -s_lam / t;
+  const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+  prm->obj = pobj;
+  prm->pinf = pinf;
+  prm->dinf = dinf;
+  prm->gap = gap;
+  prm->kkt = fmax(pinf, fmax(dinf, gap));
+  prm->r_plus = rp;
+  prm->theta_max = theta[0];
+  prm->theta_min = theta[p - 1];
+  prm->have_prev = 1;
+}
+
+// lam = -t diag(C) - 1 (the state after the DRS step from Z^0 = 0).
+__global__ void __launch_bounds__(NT) k_maxcut_init_lam(const int32_t *__restrict__ rowptr,
+                                                        const int32_t *__restrict__ colind,
+                                                        const double *__restrict__ vals, int n,
+                                                        double t, double *__restrict__ lam) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * WPB;
+  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
+    double dg = 0.0;
+    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32)
+      if (colind[e] == row) dg += vals[e];
+    dg = warp_sum(dg);
+    if (lane == 0) lam[row] = -t * dg - 1.0;
+  }
+}
+
+// Scale of the low-precision shadow: s >= spectral radius of
+// Z = X~ - tC - Diag(lam): Gershgorin of the sparse part plus theta_max.
+__global__ void __launch_bounds__(NT) k_lp_scale_final(const double *__restrict__ red, int nb,
+                                                       const double *__restrict__ theta,
+                                                       Params *prm) {
+  __shared__ double sh[32];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int q = threadIdx.x; q < nb; q += NT) {
+    lo = fmin(lo, red[q * kRedWidth + 0]);
+    hi = fmax(hi, red[q * kRedWidth + 1]);
+  }
+  lo = block_reduce(lo, sh, 1);
+  hi = block_reduce(hi, sh, 2);
+  if (threadIdx.x != 0) return;
+  const double thmax = fmax(theta[0], 0.0);
+  double s = fmax(fabs(lo), fabs(hi + thmax));
+  if (!(s > 0.0) || !isfinite(s)) s = 1.0;
+  prm->lp_scale = s;
+}
+
+// Dense low-precision shadow Z_lp = (X~ - tC - Diag(lam)) / s, computed in
+// fp32 (CUDA cores), tile EL x EL, written as bf16 or fp32.
+constexpr int EL = 64;
+template <int PT, bool F32OUT>
+__global__ void __launch_bounds__(NT) k_maxcut_expand_lp(const int32_t *__restrict__ rowptr,
+                                                         const int32_t *__restrict__ colind,
+                                                         const double *__restrict__ vals, int n,
+                                                         int p, const double *__restrict__ V,
+                                                         int64_t ldv,
+                                                         const double *__restrict__ theta,
+                                                         const double *__restrict__ lam,
+                                                         void *Zlp, int64_t ldz,
+                                                         const Params *__restrict__ prm) {
+  extern __shared__ float dynf[];
+  float(*Vi)[PT + 1] = reinterpret_cast<float(*)[PT + 1]>(dynf);
+  float(*Vj)[PT + 1] = reinterpret_cast<float(*)[PT + 1]>(dynf + EL * (PT + 1));
+  float(*Ct)[EL + 1] = reinterpret_cast<float(*)[EL + 1]>(dynf + 2 * EL * (PT + 1));
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float t = (float)prm->t;
+  const float inv_s = (float)(1.0 / prm->lp_scale);
+  int rp = 0;
+  for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
+  const int tiles1 = (n + EL - 1) / EL;
+  const int64_t ntiles = (int64_t)tiles1 * tiles1;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i0 = (int)(tile / tiles1) * EL, j0 = (int)(tile % tiles1) * EL;
+    __syncthreads();
+    for (int idx = tid; idx < EL * PT; idx += NT) {
+      const int r = idx / PT, l = idx % PT;
+      const int gi = i0 + r, gj = j0 + r;
+      const bool lv = l < rp;
+      Vi[r][l] = (lv && gi < n) ? (float)(V[(int64_t)gi * ldv + l] * theta[l]) : 0.f;
+      Vj[r][l] = (lv && gj < n) ? (float)V[(int64_t)gj * ldv + l] : 0.f;
+    }
+    for (int idx = tid; idx < EL * EL; idx += NT) Ct[idx / EL][idx % EL] = 0.f;
+    __syncthreads();
+    if (tid < EL && i0 + tid < n) {
+      const int row = i0 + tid;
+      int lo = rowptr[row], hi = rowptr[row + 1];
+      const int end = hi;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (colind[mid] < j0) lo = mid + 1;
+        else hi = mid;
+      }
+      for (int e = lo; e < end; ++e) {
+        const int col = colind[e];
+        if (col >= j0 + EL) break;
+        Ct[tid][col - j0] = (float)vals[e];
+      }
+    }
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int l = 0; l < rp; ++l) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Vi[ty * 4 + i][l];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Vj[tx + 16 * j][l];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int li = ty * 4 + i, gi = i0 + li;
+      if (gi >= n) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int lj = tx + 16 * j, gj = j0 + lj;
+        if (gj >= n) continue;
+        float z = acc[i][j] - t * Ct[li][lj];
+        if (gi == gj) z -= (float)lam[gi];
+        z *= inv_s;
+        if (F32OUT) reinterpret_cast<float *>(Zlp)[(int64_t)gi * ldz + gj] = z;
+        else reinterpret_cast<__nv_bfloat16 *>(Zlp)[(int64_t)gi * ldz + gj] = __float2bfloat16_rn(z);
+      }
+    }
+  }
+}
+
+constexpr size_t expand_lp_bytes(int PT) {
+  return (size_t)(2 * EL * (PT + 1) + EL * (EL + 1)) * sizeof(float);
+}
+
+}  // namespace
+
+cudaError_t configure_sparse() {
+  cudaError_t e;
+#define PF_SET(fn, bytes)                                                                   \
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+  if (e != cudaSuccess) return e;
+  PF_SET((k_maxcut_expand_lp<16, false>), expand_lp_bytes(16))
+  PF_SET((k_maxcut_expand_lp<32, false>), expand_lp_bytes(32))
+  PF_SET((k_maxcut_expand_lp<64, false>), expand_lp_bytes(64))
+  PF_SET((k_maxcut_expand_lp<16, true>), expand_lp_bytes(16))
+  PF_SET((k_maxcut_expand_lp<32, true>), expand_lp_bytes(32))
+  PF_SET((k_maxcut_expand_lp<64, true>), expand_lp_bytes(64))
+#undef PF_SET
+  return cudaSuccess;
+}
+
+namespace {
+__global__ void k_copy_block(const double *__restrict__ src, int64_t lds, int n, int p,
+                             double *__restrict__ dst, int64_t ldd) {
+  const int64_t total = (int64_t)n * p;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / p;
+    const int j = (int)(idx - i * p);
+    dst[i * ldd + j] = src[i * lds + j];
+  }
+}
+}  // namespace
+
+cudaError_t launch_copy_block(cudaStream_t s, const Workspace &ws, const double *src, int64_t lds,
+                              int n, int p, double *dst, int64_t ldd) {
+  int64_t blocks = ((int64_t)n * p + 255) / 256;
+  if (blocks > 4 * ws.num_sms) blocks = 4 * ws.num_sms;
+  if (blocks < 1) blocks = 1;
+  k_copy_block<<<(int)blocks, 256, 0, s>>>(src, lds, n, p, dst, ldd);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxcut_sparse_part(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                      const int32_t *colind, const double *vals, int n,
+                                      const double *lam, double *Sout) {
+  k_maxcut_sparse_part<<<red_blocks(n, ws.num_sms), NT, 0, s>>>(rowptr, colind, vals, n, lam,
+                                                                  ws.prm, Sout);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxcut_struct_update(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                        const int32_t *colind, const double *vals, int n, int p,
+                                        const double *V, int64_t ldv, const double *theta,
+                                        double *lam) {
+  const int nb = red_blocks(n, ws.num_sms);
+  double *red = slot(ws, SLOT_LAMBDA);  // 2 * kRedWidth doubles per block: spans LAMBDA + EXPAND
+  k_maxcut_struct_update<<<nb, NT, 0, s>>>(rowptr, colind, vals, n, p, V, ldv, theta, ws.Vprev, p,
+                                           ws.thprev, lam, red);
+  PF_LAUNCHED();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int ng = 0;
+  e = launch_gram(s, ws, ws.Vprev, p, V, ldv, n, p, p, 0, &ng);
+  if (e != cudaSuccess) return e;
+  k_maxcut_struct_kkt<<<1, NT, 0, s>>>(ws.gpart, ng, red, nb, ws.thprev, theta, n, p, ws.prm);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxcut_init_lam(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                   const int32_t *colind, const double *vals, int n, double t,
+                                   double *lam) {
+  k_maxcut_init_lam<<<red_blocks(n, ws.num_sms), NT, 0, s>>>(rowptr, colind, vals, n, t, lam);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxcut_lp_shadow(cudaStream_t s, const Workspace &ws, bool f32out,
+                                    const int32_t *rowptr, const int32_t *colind,
+                                    const double *vals, int n, int p, const double *V, int64_t ldv,
+                                    const double *theta, const double *lam, void *Zlp,
+                                    int64_t ldz) {
+  // scale from the Gershgorin bounds of -tC - Diag(lam) plus theta_max
+  const int nb = red_blocks(n, ws.num_sms);
+  k_interval_rows<<<nb, NT, 0, s>>>(PF_PROBLEM_MAXCUT, rowptr, colind, vals, n, lam, ws.prm,
+                                    slot(ws, SLOT_MISC));
+  PF_LAUNCHED();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_lp_scale_final<<<1, NT, 0, s>>>(slot(ws, SLOT_MISC), nb, theta, ws.prm);
+  PF_LAUNCHED();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t tiles1 = (n + EL - 1) / EL;
+  int64_t blocks = tiles1 * tiles1;
+  if (blocks > 8 * ws.num_sms) blocks = 8 * ws.num_sms;
+#define PF_EXP(PTV)                                                                             \
+  if (f32out)                                                                                   \
+    k_maxcut_expand_lp<PTV, true><<<(int)blocks, NT, expand_lp_bytes(PTV), s>>>(                 \
+        rowptr, colind, vals, n, p, V, ldv,                                                     \
+                                                             theta, lam, Zlp, ldz, ws.prm);     \
+  else                                                                                          \
+    k_maxcut_expand_lp<PTV, false><<<(int)blocks, NT, expand_lp_bytes(PTV), s>>>(                \
+        rowptr, colind, vals, n, p, V, ldv, theta, lam, Zlp, ldz, ws.prm);
+  if (p <= 16) { PF_EXP(16) }
+  else if (p <= 32) { PF_EXP(32) }
+  else { PF_EXP(64) }
+#undef PF_EXP
   PF_LAUNCHED();
   return cudaGetLastError();
 }

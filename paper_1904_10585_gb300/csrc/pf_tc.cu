@@ -145,7 +145,7 @@ __host__ __device__ constexpr uint32_t make_idesc() {
 template <int NB, bool TF32>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_filter(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                int n, int p, int num_kb, float scale, const float *Ycur, const float *Yprev,
+                int n, int p, int num_kb, const float *Ycur, const float *Yprev,
                 float *Ynext, void *Xt_next, int64_t ldxt, Params *prm, int mode) {
   constexpr int B_BYTES = NB * TC_ROWB;
   constexpr int STAGE_TX = TC_A_BYTES + B_BYTES;
@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncwarp();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (have_acc) {
+    const float scale = (float)prm->lp_scale;
     double c = 0.0, alpha = 1.0;
     if (mode != MODE_PLAIN) {
       c = prm->c;
@@ -353,7 +354,7 @@ static cudaError_t encode_map(CUtensorMap *m, const void *ptr, bool tf32, int64_
 static int tc_nb(int p) { return p <= 16 ? 16 : p <= 32 ? 32 : p <= 48 ? 48 : 64; }
 
 cudaError_t launch_tc_product(cudaStream_t s, const Workspace &ws, bool tf32, const void *A_lp,
-                              int64_t lda_lp, double lp_scale, int n, const void *Xt,
+                              int64_t lda_lp, int n, const void *Xt,
                               const float *Ycur, const float *Yprev, float *Ynext, void *Xt_next,
                               int mode) {
   const int p = ws.p;
@@ -367,9 +368,8 @@ cudaError_t launch_tc_product(cudaStream_t s, const Workspace &ws, bool tf32, co
   const int num_kb = (n + kel - 1) / kel;
   const dim3 grid((n + TC_BM - 1) / TC_BM);
   const size_t smem = tc_smem_bytes(NB);
-  const float sc = (float)lp_scale;
 #define PF_TC_LAUNCH(NBV, TFV)                                                                    \
-  k_tc_filter<NBV, TFV><<<grid, TC_THREADS, smem, s>>>(ma, mb, n, p, num_kb, sc, Ycur, Yprev,   \
+  k_tc_filter<NBV, TFV><<<grid, TC_THREADS, smem, s>>>(ma, mb, n, p, num_kb, Ycur, Yprev,       \
                                                        Ynext, Xt_next, ws.ldxt, ws.prm, mode)
   if (tf32) {
     switch (NB) {

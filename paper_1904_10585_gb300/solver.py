@@ -58,9 +58,23 @@ class Context:
         self.close()
 
 
-def dense_operator(A: torch.Tensor) -> B.pf_operator:
-    assert A.dtype == torch.float64 and A.shape[0] == A.shape[1]
-    return B.pf_operator(kind=B.PF_OP_DENSE, n=A.shape[0], A=_ptr(A), lda=_ld(A))
+def _keep(op, *tensors):
+    """Hold references to the tensors whose device pointers a struct carries,
+    so the caching allocator cannot recycle them while the struct is in use."""
+    op._keep = [t for t in tensors if t is not None]
+    return op
+
+
+def dense_operator(A: torch.Tensor, A_lp: Optional[torch.Tensor] = None,
+                   lp_scale: float = 0.0) -> B.pf_operator:
+    assert A is None or (A.dtype == torch.float64 and A.shape[0] == A.shape[1])
+    n = A.shape[0] if A is not None else A_lp.shape[0]
+    op = B.pf_operator(kind=B.PF_OP_DENSE, n=n, A=_ptr(A), lda=_ld(A) if A is not None else n)
+    if A_lp is not None:
+        op.A_lp = _ptr(A_lp)
+        op.lda_lp = _ld(A_lp)
+        op.lp_scale = lp_scale
+    return _keep(op, A, A_lp)
 
 
 def lowrank_sparse_operator(n: int, Uf: Optional[torch.Tensor], lam: Optional[torch.Tensor],
@@ -68,11 +82,12 @@ def lowrank_sparse_operator(n: int, Uf: Optional[torch.Tensor], lam: Optional[to
                             vals: Optional[torch.Tensor], sparse_scale: float, shift: float
                             ) -> B.pf_operator:
     r = 0 if Uf is None else Uf.shape[1]
-    return B.pf_operator(kind=B.PF_OP_LOWRANK_SPARSE, n=n,
-                         Uf=_ptr(Uf), lduf=(_ld(Uf) if Uf is not None else 0), lam=_ptr(lam), r=r,
-                         rowptr=_ptr(rowptr), colind=_ptr(colind), vals=_ptr(vals),
-                         nnz=0 if vals is None else vals.numel(),
-                         sparse_scale=sparse_scale, shift=shift)
+    op = B.pf_operator(kind=B.PF_OP_LOWRANK_SPARSE, n=n,
+                       Uf=_ptr(Uf), lduf=(_ld(Uf) if Uf is not None else 0), lam=_ptr(lam), r=r,
+                       rowptr=_ptr(rowptr), colind=_ptr(colind), vals=_ptr(vals),
+                       nnz=0 if vals is None else vals.numel(),
+                       sparse_scale=sparse_scale, shift=shift)
+    return _keep(op, Uf, lam, rowptr, colind, vals)
 
 
 def filter_(ctx: Context, op: B.pf_operator, a: float, b: float, degree: int,
@@ -106,6 +121,7 @@ class Problem:
     V: torch.Tensor
     theta: torch.Tensor
     Z: Optional[torch.Tensor] = None
+    Z_lp: Optional[torch.Tensor] = None
     lam: Optional[torch.Tensor] = None
     S: Optional[torch.Tensor] = None
     t: float = 0.0
@@ -119,9 +135,15 @@ class Problem:
                          theta=_ptr(self.theta))
         if self.kind == B.PF_PROBLEM_MAXCUT:
             s.vals_f64 = _ptr(self.vals)
-            s.Z = _ptr(self.Z)
-            s.ldz = _ld(self.Z)
+            if self.Z is not None:
+                s.Z = _ptr(self.Z)
+                s.ldz = _ld(self.Z)
+            if self.Z_lp is not None:
+                s.Z_lp = _ptr(self.Z_lp)
+                s.ldz_lp = _ld(self.Z_lp)
             s.lam = _ptr(self.lam)
+            if self.S is not None:
+                s.S = _ptr(self.S)
         else:
             s.vals_f32 = _ptr(self.vals)
             s.S = _ptr(self.S)
@@ -129,16 +151,31 @@ class Problem:
         return s
 
 
-def maxcut_problem(rowptr, colind, vals, U0: torch.Tensor, t: float = 0.0) -> Problem:
-    """Max-cut SDP with cost C (CSR, float64 values incl. diagonal); U0 is the
-    n x p start block (copied)."""
+def maxcut_problem(rowptr, colind, vals, U0: torch.Tensor, t: float = 0.0, dense: bool = True,
+                   lowprec: Optional[str] = None) -> Problem:
+    """Max-cut SDP with cost C (CSR, float64 values incl. every diagonal
+    entry); U0 is the n x p start block (copied).
+
+    dense=True keeps the FP64 iteration matrix Z (n x n); dense=False applies
+    Z = X~ - tC - Diag(lam) in structured form.  lowprec="bf16"/"tf32" adds the
+    dense low-precision shadow the tensor-core filter reads (use with a
+    context of the same precision)."""
     n, p = U0.shape
     dev = U0.device
+    Z_lp = None
+    if lowprec is not None:
+        dt = torch.bfloat16 if lowprec == "bf16" else torch.float32
+        align = 8 if lowprec == "bf16" else 4
+        ld = ((n + align - 1) // align) * align
+        Z_lp = torch.empty(n, ld, dtype=dt, device=dev)[:, :n]
     pr = Problem(kind=B.PF_PROBLEM_MAXCUT, n=n, rowptr=rowptr, colind=colind, vals=vals,
                  U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
                  theta=torch.zeros(p, dtype=torch.float64, device=dev),
-                 Z=torch.empty(n, n, dtype=torch.float64, device=dev),
-                 lam=torch.empty(n, dtype=torch.float64, device=dev), t=t)
+                 Z=torch.empty(n, n, dtype=torch.float64, device=dev) if dense else None,
+                 Z_lp=Z_lp,
+                 lam=torch.empty(n, dtype=torch.float64, device=dev),
+                 S=(torch.empty(colind.numel(), dtype=torch.float64, device=dev)
+                    if (not dense or lowprec is not None) else None), t=t)
     pr.make_struct()
     return pr
 

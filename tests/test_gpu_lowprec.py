@@ -32,10 +32,7 @@ def S():
 
 
 def lp_operator(S, A_lp, scale):
-    import paper_1904_10585_gb300 as B
-    n = A_lp.shape[0]
-    return B.pf_operator(kind=B.PF_OP_DENSE, n=n, A=0, lda=n, A_lp=A_lp.data_ptr(),
-                         lda_lp=A_lp.stride(0), lp_scale=scale)
+    return S.dense_operator(None, A_lp=A_lp, lp_scale=scale)
 
 
 def sym_matrix(n, seed):
