@@ -210,6 +210,27 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *prob, int64_t max_iter, double tol,
 /* Copy the report of the most recent step to host (synchronises). */
 pf_status pf_get_info(pf_ctx *ctx, pf_iter_info *info);
 
+/* Y = A X for a dense symmetric FP64 A (n x n, row-major, lda >= n) and an
+ * n x p block X (ldx >= p, 1 <= p <= PF_MAX_P), written to Y (ldy >= p,
+ * distinct from X), enqueued on `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  No counterpart in the paper: it is pf_apply's dense FP64
+ * product for callers that cannot allocate device memory -- code that has no
+ * pf_ctx to own a workspace, or that runs under a memory manager which owns
+ * all device memory, or on a path that must not pay for cudaMalloc (which
+ * may synchronise the device).  It allocates nothing: the split-K partial
+ * sums live in one fixed device array inside the library of
+ * 2 Mi doubles (16 MiB), which every GPU that loads the library keeps until
+ * the process exits; calls need n * p <= 2,097,152 (PF_ERR_INVALID_ARG
+ * otherwise).  The first call on each device looks up that array's device
+ * address (with the device current) and should come before any stream
+ * capture.  All calls share the array: calls whose kernels can overlap on a
+ * GPU (different streams without ordering) race and must be serialised by
+ * the caller.  Nothing in the array needs to start at zero (every partial
+ * sum a call reads it has written itself).  Errors: PF_ERR_INVALID_ARG,
+ * PF_ERR_CUDA, PF_ERR_UNSUPPORTED (device index >= 64). */
+pf_status pf_apply_dense_noalloc(const double *A, int64_t lda, const double *X, int64_t ldx,
+                                 double *Y, int64_t ldy, int64_t n, int32_t p, void *stream);
+
 /* Number of kernels this library has enqueued in this process (host-side
  * count; a replayed CUDA graph adds nothing).  Instrumentation with no
  * counterpart in the paper: it lets a caller count the GPU launches of a

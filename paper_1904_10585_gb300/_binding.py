@@ -94,6 +94,8 @@ def _load():
                                        P, P]),
         "pf_apply": (C.c_int, [P, C.POINTER(pf_operator), P, C.c_int64, P, C.c_int64]),
         "pf_kernel_launch_count": (C.c_int64, []),
+        "pf_apply_dense_noalloc": (C.c_int, [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int64,
+                                             C.c_int32, P]),
         "pf_problem_init": (C.c_int, [P, C.POINTER(pf_problem)]),
         "pf_prox_step": (C.c_int, [P, C.POINTER(pf_problem), C.POINTER(pf_iter_info)]),
         "pf_solve": (C.c_int, [P, C.POINTER(pf_problem), C.c_int64, C.c_double, C.c_int32,
@@ -112,7 +114,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("pf_create", "pf_destroy", "pf_filter", "pf_rayleigh_ritz", "pf_apply",
             "pf_problem_init", "pf_prox_step", "pf_solve", "pf_get_info",
-            "pf_kernel_launch_count", "pf_status_string", "pf_last_error")
+            "pf_kernel_launch_count", "pf_apply_dense_noalloc", "pf_status_string",
+            "pf_last_error")
 
 
 class PFError(RuntimeError):
@@ -163,6 +166,15 @@ def pf_apply(ctx, op: pf_operator, X: int, ldx: int, Y: int, ldy: int) -> None:
 
 def pf_kernel_launch_count() -> int:
     return int(_lib.pf_kernel_launch_count())
+
+
+def pf_apply_dense_noalloc(A: int, lda: int, X: int, ldx: int, Y: int, ldy: int, n: int, p: int,
+                           stream: int = 0) -> None:
+    """Y = A X without any device allocation (the library's fixed scratch
+    array holds the partial sums); for callers that cannot allocate."""
+    _check(_lib.pf_apply_dense_noalloc(C.c_void_p(A), int(lda), C.c_void_p(X), int(ldx),
+                                       C.c_void_p(Y), int(ldy), int(n), int(p),
+                                       C.c_void_p(stream or None)))
 
 
 def pf_problem_init(ctx, prob: pf_problem) -> None:

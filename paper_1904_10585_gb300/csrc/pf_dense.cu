@@ -204,3 +204,96 @@ cudaError_t launch_dense_apply(cudaStream_t s, const Workspace &ws, const Op &op
 }
 
 }  // namespace pf
+
+// ===========================================================================
+// Allocation-free dense product (no counterpart in the paper).
+//
+// Y = A X with the split-K partial sums kept in a file-scope device array
+// instead of a context's workspace, for callers that cannot allocate device
+// memory themselves.  The array is part of the library image: every GPU on
+// which the library is loaded holds it until the process exits.
+// ===========================================================================
+#include <mutex>
+
+namespace pf {
+namespace {
+
+constexpr int64_t kStaticScratchDoubles = (int64_t)2 << 20;  // 2 Mi doubles = 16 MiB
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+
+std::mutex g_static_mutex;
+double *g_static_addr[kStaticMaxDevices] = {};
+int g_static_sms[kStaticMaxDevices] = {};
+
+// Device address of the scratch array (and SM count) for the current
+// device, looked up once per device.  In host code the array's name only
+// stands in for the device copy, so the address must come from
+// cudaGetSymbolAddress with the device current.
+pf_status static_scratch_for_current_device(double **addr, int *sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PF_ERR_CUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return PF_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (g_static_addr[dev] == nullptr) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr)
+      return PF_ERR_CUDA;
+    int count = 0;
+    if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return PF_ERR_CUDA;
+    g_static_addr[dev] = (double *)p;
+    g_static_sms[dev] = count;
+  }
+  *addr = g_static_addr[dev];
+  *sms = g_static_sms[dev];
+  return PF_OK;
+}
+
+}  // namespace
+}  // namespace pf
+
+extern "C" pf_status pf_apply_dense_noalloc(const double *A, int64_t lda, const double *X,
+                                            int64_t ldx, double *Y, int64_t ldy, int64_t n,
+                                            int32_t p, void *stream) {
+  using namespace pf;
+  if (!A || !X || !Y || X == Y || n < 1 || n > (int64_t)INT32_MAX / 2 || p < 1 || p > kMaxP ||
+      lda < n || ldx < p || ldy < p)
+    return PF_ERR_INVALID_ARG;
+  if (n * (int64_t)p > kStaticScratchDoubles) return PF_ERR_INVALID_ARG;
+  double *scratch = nullptr;
+  int sms = 0;
+  const pf_status st = static_scratch_for_current_device(&scratch, &sms);
+  if (st != PF_OK) return st;
+  const int ni = (int)n;
+  // as many K splits as the workspace path would use, capped by the array
+  int kchunk = 0;
+  int S = dense_splits(ni, sms, &kchunk);
+  const int64_t fit = kStaticScratchDoubles / (n * (int64_t)p);
+  if (S > fit) {
+    const int ktiles = (ni + BK - 1) / BK;
+    const int tiles_per = (int)((ktiles + fit - 1) / fit);
+    kchunk = tiles_per * BK;
+    S = (ni + kchunk - 1) / kchunk;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const dim3 grid((ni + BM - 1) / BM, S);
+  if (p <= 16)
+    k_gemm_f64_splitk<16><<<grid, NT, 0, s>>>(A, lda, X, ldx, ni, p, kchunk, scratch);
+  else if (p <= 32)
+    k_gemm_f64_splitk<32><<<grid, NT, 0, s>>>(A, lda, X, ldx, ni, p, kchunk, scratch);
+  else
+    k_gemm_f64_splitk<64><<<grid, NT, 0, s>>>(A, lda, X, ldx, ni, p, kchunk, scratch);
+  if (cudaGetLastError() != cudaSuccess) return PF_ERR_CUDA;
+  PF_LAUNCHED();
+  const int64_t total = n * p;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4 * sms) blocks = 4 * sms;
+  // MODE_PLAIN reads no device parameters
+  k_combine<<<blocks, 256, 0, s>>>(scratch, S, ni, p, X, ldx, nullptr, 0, Y, ldy, nullptr,
+                                   MODE_PLAIN);
+  if (cudaGetLastError() != cudaSuccess) return PF_ERR_CUDA;
+  PF_LAUNCHED();
+  return PF_OK;
+}
