@@ -210,6 +210,18 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *prob, int64_t max_iter, double tol,
 /* Copy the report of the most recent step to host (synchronises). */
 pf_status pf_get_info(pf_ctx *ctx, pf_iter_info *info);
 
+/* Enqueue n_steps iterations of pf_prox_step (replays of the step's CUDA
+ * graph when the stream is not the legacy default stream) and return without
+ * synchronising.  The adaptive ladder is not applied.  Used by request loops
+ * that keep several solves in flight on different streams. */
+pf_status pf_enqueue_steps(pf_ctx *ctx, pf_problem *prob, int64_t n_steps);
+
+/* Enqueue a copy of the latest step report into `info` (host memory owned
+ * by the caller; page-locked memory keeps the copy asynchronous).  The
+ * report is valid once the context's stream has reached this point (e.g.
+ * after an event recorded behind it has completed). */
+pf_status pf_report_async(pf_ctx *ctx, pf_iter_info *info);
+
 /* Y = A X for a dense symmetric FP64 A (n x n, row-major, lda >= n) and an
  * n x p block X (ldx >= p, 1 <= p <= PF_MAX_P), written to Y (ldy >= p,
  * distinct from X), enqueued on `stream` (a cudaStream_t; NULL = legacy

@@ -101,6 +101,8 @@ def _load():
         "pf_solve": (C.c_int, [P, C.POINTER(pf_problem), C.c_int64, C.c_double, C.c_int32,
                                C.POINTER(pf_result)]),
         "pf_get_info": (C.c_int, [P, C.POINTER(pf_iter_info)]),
+        "pf_enqueue_steps": (C.c_int, [P, C.POINTER(pf_problem), C.c_int64]),
+        "pf_report_async": (C.c_int, [P, P]),
         "pf_status_string": (C.c_char_p, [C.c_int]),
         "pf_last_error": (C.c_char_p, [P]),
     }
@@ -113,7 +115,8 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("pf_create", "pf_destroy", "pf_filter", "pf_rayleigh_ritz", "pf_apply",
-            "pf_problem_init", "pf_prox_step", "pf_solve", "pf_get_info",
+            "pf_problem_init", "pf_prox_step", "pf_solve", "pf_get_info", "pf_enqueue_steps",
+            "pf_report_async",
             "pf_kernel_launch_count", "pf_apply_dense_noalloc", "pf_status_string",
             "pf_last_error")
 
@@ -194,6 +197,16 @@ def pf_solve(ctx, prob: pf_problem, max_iter: int, tol: float = 0.0, check_every
     _check(_lib.pf_solve(ctx, C.byref(prob), int(max_iter), float(tol), int(check_every),
                          C.byref(res)), ctx, allow)
     return res
+
+
+def pf_enqueue_steps(ctx, prob: pf_problem, n_steps: int) -> None:
+    _check(_lib.pf_enqueue_steps(ctx, C.byref(prob), int(n_steps)), ctx)
+
+
+def pf_report_async(ctx, info_addr: int) -> None:
+    """Enqueue the latest step report into host memory at `info_addr`
+    (a pinned buffer of sizeof(pf_iter_info) bytes)."""
+    _check(_lib.pf_report_async(ctx, C.c_void_p(info_addr)), ctx)
 
 
 def pf_get_info(ctx) -> pf_iter_info:

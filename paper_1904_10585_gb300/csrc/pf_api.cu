@@ -26,10 +26,15 @@ struct pf_ctx {
   void *base;
   size_t bytes;
   char err[512];
-  // graph of one step, cached per problem description
+  // graph of one step, cached per problem description and ladder state
   cudaGraphExec_t gexec;
   pf_problem gkey;
+  int gdegree;
+  bool glp;
   bool have_graph;
+  // adaptive ladder state (degree and low-precision filter currently used)
+  int cur_degree;
+  bool cur_lp;
 };
 
 namespace {
@@ -235,9 +240,12 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
   const int n = (int)pr->n;
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
-  const int degree = ctx->opt.degree;
-  const bool lp = ctx->opt.precision != PF_PREC_FP64;
-  if (pr->kind == PF_PROBLEM_MAXCUT && (lp || pr->Z == nullptr)) {
+  const int degree = ctx->cur_degree;
+  const bool lp = ctx->cur_lp;
+  // a low-precision context keeps no FP64 dense Z up to date, so it always
+  // uses the structured operator (also after the ladder has dropped to FP64)
+  const bool structured = ctx->opt.precision != PF_PREC_FP64 || pr->Z == nullptr;
+  if (pr->kind == PF_PROBLEM_MAXCUT && structured) {
     // structured Z = X~prev - tC - Diag(lam) for the Rayleigh-Ritz step (and
     // for the filter unless a low-precision dense shadow is used)
     PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
@@ -317,7 +325,7 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
   return PF_OK;
 }
 
-void params_to_info(const Params &h, pf_iter_info *info) {
+void params_to_info(const Params &h, pf_iter_info *info, const pf_ctx *ctx = nullptr) {
   info->a = h.a;
   info->b = h.b;
   info->obj = h.obj;
@@ -329,8 +337,8 @@ void params_to_info(const Params &h, pf_iter_info *info) {
   info->theta_min = h.theta_min;
   info->r_plus = h.r_plus;
   info->flags = h.flags;
-  info->degree = h.degree;
-  info->precision = h.precision;
+  info->degree = ctx ? ctx->cur_degree : h.degree;
+  info->precision = ctx ? (ctx->cur_lp ? ctx->opt.precision : (int)PF_PREC_FP64) : h.precision;
 }
 
 pf_status read_params(pf_ctx *ctx, Params *h) {
@@ -351,6 +359,8 @@ bool same_problem(const pf_problem &a, const pf_problem &b) {
 
 extern "C" {
 
+static pf_status capture_step(pf_ctx *ctx, pf_problem *pr);
+
 pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx **out) {
   if (!out) return PF_ERR_INVALID_ARG;
   *out = nullptr;
@@ -368,6 +378,8 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   ctx->n_max = n_max;
   ctx->p = opt->p;
   ctx->stream = (cudaStream_t)stream;
+  ctx->cur_degree = opt->degree;
+  ctx->cur_lp = opt->precision != PF_PREC_FP64;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   int sms = 0;
@@ -400,6 +412,8 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   }
   const size_t prm_off = tot;
   tot += align_up(sizeof(Params));
+  const size_t info_off = tot;
+  tot += align_up(sizeof(pf_iter_info));
   // low-precision buffers: Y32[2], U32 (fp32 n x p); Xt[2] (p x ldxt, 4-byte elements)
   const int64_t ldxt = ((n_max + 63) / 64) * 64;
   size_t lp_off[5] = {0, 0, 0, 0, 0};
@@ -437,6 +451,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   ws.thprev = (double *)(b + off[10]);
   ws.resid = (double *)(b + off[11]);
   ws.prm = (Params *)(b + prm_off);
+  ws.info = (pf_iter_info *)(b + info_off);
   ws.ldxt = ldxt;
   if (lp) {
     ws.Y32[0] = (float *)(b + lp_off[0]);
@@ -551,6 +566,8 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
   PF_CUDA(cudaStreamSynchronize(s));
   PF_CUDA(cudaGetLastError());
   pr->iter = 0;
+  ctx->cur_degree = ctx->opt.degree;
+  ctx->cur_lp = ctx->opt.precision != PF_PREC_FP64;
   return PF_OK;
 }
 
@@ -562,7 +579,8 @@ pf_status pf_prox_step(pf_ctx *ctx, pf_problem *pr, pf_iter_info *info) {
   if (info) {
     Params h;
     PF_TRY(read_params(ctx, &h));
-    params_to_info(h, info);
+    params_to_info(h, info, ctx);
+    if (h.flags & 8) return set_err(ctx, PF_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
     if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
     if (h.flags & 4) return set_err(ctx, PF_ERR_NAN, "non-finite Ritz value");
   }
@@ -573,7 +591,61 @@ pf_status pf_get_info(pf_ctx *ctx, pf_iter_info *info) {
   if (!ctx || !info) return PF_ERR_INVALID_ARG;
   Params h;
   PF_TRY(read_params(ctx, &h));
-  params_to_info(h, info);
+  params_to_info(h, info, ctx);
+  return PF_OK;
+}
+
+pf_status pf_enqueue_steps(pf_ctx *ctx, pf_problem *pr, int64_t n_steps) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  PF_TRY(check_problem(ctx, pr));
+  if (n_steps < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "n_steps must be >= 0");
+  const bool use_graph = ctx->stream != nullptr;
+  for (int64_t k = 0; k < n_steps; ++k) {
+    if (use_graph) {
+      if (!(ctx->have_graph && same_problem(ctx->gkey, *pr) && ctx->gdegree == ctx->cur_degree &&
+            ctx->glp == ctx->cur_lp))
+        PF_TRY(capture_step(ctx, pr));
+      PF_CUDA(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    } else {
+      PF_TRY(step_core(ctx, pr));
+    }
+    pr->iter += 1;
+  }
+  return PF_OK;
+}
+
+pf_status pf_report_async(pf_ctx *ctx, pf_iter_info *info) {
+  if (!ctx || !info) return PF_ERR_INVALID_ARG;
+  PF_CUDA(launch_export_info(ctx->stream, ctx->ws, ctx->cur_degree,
+                             ctx->cur_lp ? ctx->opt.precision : (int)PF_PREC_FP64));
+  PF_CUDA(cudaMemcpyAsync(info, ctx->ws.info, sizeof(pf_iter_info), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  return PF_OK;
+}
+
+static pf_status capture_step(pf_ctx *ctx, pf_problem *pr) {
+  if (ctx->have_graph) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->have_graph = false;
+  }
+  cudaGraph_t g = nullptr;
+  PF_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  pf_status st = step_core(ctx, pr);
+  cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+  if (st != PF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  PF_CUDA(ce);
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  PF_CUDA(ie);
+  ctx->gexec = ge;
+  ctx->gkey = *pr;
+  ctx->gdegree = ctx->cur_degree;
+  ctx->glp = ctx->cur_lp;
+  ctx->have_graph = true;
   return PF_OK;
 }
 
@@ -584,41 +656,50 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
   if (max_iter < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (check_every < 1) check_every = 1;
   const bool use_graph = ctx->stream != nullptr;
-  if (use_graph && !(ctx->have_graph && same_problem(ctx->gkey, *pr))) {
-    if (ctx->have_graph) {
-      cudaGraphExecDestroy(ctx->gexec);
-      ctx->have_graph = false;
-    }
-    cudaGraph_t g = nullptr;
-    PF_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    pf_status st = step_core(ctx, pr);
-    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
-    if (st != PF_OK) {
-      if (g) cudaGraphDestroy(g);
-      return st;
-    }
-    PF_CUDA(ce);
-    cudaGraphExec_t ge = nullptr;
-    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
-    cudaGraphDestroy(g);
-    PF_CUDA(ie);
-    ctx->gexec = ge;
-    ctx->gkey = *pr;
-    ctx->have_graph = true;
-  }
+  // adaptive ladder: KKT history at the checks; a stall (< 5% decrease over
+  // the last 5 checks) raises the degree by one up to degree_max, then drops
+  // the low-precision filter for the FP64 one
+  const bool adaptive = ctx->opt.adaptive != 0;
+  const bool check = tol > 0.0 || adaptive;
+  double hist[5] = {0, 0, 0, 0, 0};
+  int nhist = 0;
   Params h = {};
   int64_t it = 0;
   bool converged = false;
   for (; it < max_iter;) {
-    if (use_graph) PF_CUDA(cudaGraphLaunch(ctx->gexec, ctx->stream));
-    else PF_TRY(step_core(ctx, pr));
+    if (use_graph) {
+      if (!(ctx->have_graph && same_problem(ctx->gkey, *pr) && ctx->gdegree == ctx->cur_degree &&
+            ctx->glp == ctx->cur_lp))
+        PF_TRY(capture_step(ctx, pr));
+      PF_CUDA(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    } else {
+      PF_TRY(step_core(ctx, pr));
+    }
     ++it;
     pr->iter += 1;
-    if (tol > 0.0 && (it % check_every == 0 || it == max_iter)) {
+    if (check && (it % check_every == 0 || it == max_iter)) {
       PF_TRY(read_params(ctx, &h));
-      if (h.kkt <= tol) {
+      if (tol > 0.0 && h.kkt <= tol) {
         converged = true;
         break;
+      }
+      if (adaptive) {
+        if (nhist == 5) {
+          for (int i = 0; i < 4; ++i) hist[i] = hist[i + 1];
+          nhist = 4;
+        }
+        hist[nhist++] = h.kkt;
+        if (nhist == 5 && !(hist[4] < 0.95 * hist[0])) {
+          const int dmax = ctx->opt.degree_max > ctx->opt.degree ? ctx->opt.degree_max
+                                                                 : ctx->opt.degree;
+          if (ctx->cur_degree < dmax) {
+            ctx->cur_degree += 1;
+            nhist = 0;
+          } else if (ctx->cur_lp) {
+            ctx->cur_lp = false;
+            nhist = 0;
+          }
+        }
       }
     }
   }
@@ -627,8 +708,9 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
     out->iters = it;
     out->kkt = h.kkt;
     out->obj = h.obj;
-    params_to_info(h, &out->last);
+    params_to_info(h, &out->last, ctx);
   }
+  if (h.flags & 8) return set_err(ctx, PF_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
   if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
   if (h.flags & 4) return set_err(ctx, PF_ERR_NAN, "non-finite Ritz value");
   if (tol > 0.0 && !converged && max_iter > 0)

@@ -67,6 +67,7 @@ struct Workspace {
   double *thprev;         // p
   double *resid;          // p
   Params *prm;
+  pf_iter_info *info;     // device copy of the step report (pf_report_async)
   // low-precision filter (allocated only for a bf16 / tf32 context)
   float *Y32[2];          // fp32 recurrence buffers, n_max x p
   float *U32;             // fp32 copy of the start block
@@ -160,6 +161,7 @@ cudaError_t launch_maxcut_lp_shadow(cudaStream_t s, const Workspace &ws, bool f3
 cudaError_t launch_copy_block(cudaStream_t s, const Workspace &ws, const double *src, int64_t lds,
                               int n, int p, double *dst, int64_t ldd);
 cudaError_t launch_fill(cudaStream_t s, double *x, int64_t rows, int64_t cols, int64_t ld, double v);
+cudaError_t launch_export_info(cudaStream_t s, const Workspace &ws, int degree, int precision);
 cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,
                                int degree, int precision);
 

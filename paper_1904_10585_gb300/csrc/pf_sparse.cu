@@ -669,6 +669,34 @@ cudaError_t launch_save_prev(cudaStream_t s, const Workspace &ws, const double *
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_export_info(const Params *__restrict__ prm, pf_iter_info *__restrict__ info,
+                              int degree, int precision) {
+  if (threadIdx.x != 0) return;
+  pf_iter_info r;
+  r.a = prm->a;
+  r.b = prm->b;
+  r.obj = prm->obj;
+  r.kkt = prm->kkt;
+  r.pinf = prm->pinf;
+  r.dinf = prm->dinf;
+  r.gap = prm->gap;
+  r.theta_max = prm->theta_max;
+  r.theta_min = prm->theta_min;
+  r.r_plus = prm->r_plus;
+  r.flags = prm->flags;
+  r.degree = degree;
+  r.precision = precision;
+  *info = r;
+}
+}  // namespace
+
+cudaError_t launch_export_info(cudaStream_t s, const Workspace &ws, int degree, int precision) {
+  k_export_info<<<1, 32, 0, s>>>(ws.prm, ws.info, degree, precision);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,
                                int degree, int precision) {
   k_params_init<<<1, 1, 0, s>>>(prm, eta, t, mu, degree, precision);

@@ -215,3 +215,40 @@ def make_workload(name: str, **overrides):
         return cfg, completion_instance(cfg["n"], cfg["rank"], cfg["rate"], cfg["p"], seed,
                                         mu=cfg["mu"], t=cfg["t"])
     return cfg, maxcut_instance(cfg["n"], cfg["prob"], cfg["p"], seed)
+
+
+def serving_mix(n_requests: int, seed: int, p: int = 32,
+                maxcut_n=(512, 8192), completion_n=(2000, 50000), rank=(5, 20),
+                rate=(0.01, 0.10), maxcut_prob=0.01):
+    """Mixed request stream: half max-cut SDPs (n log-uniform in maxcut_n,
+    G(n, maxcut_prob) with +-1 weights), half PSD completions (n log-uniform
+    in completion_n, rank uniform in `rank`, sampling rate uniform in `rate`),
+    in a seeded random order.  Returns a list of dicts (kind, n, instance)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    kinds = ["maxcut"] * (n_requests // 2) + ["completion"] * (n_requests - n_requests // 2)
+    rng.shuffle(kinds)
+    out = []
+    for i, kind in enumerate(kinds):
+        sub = int(rng.integers(0, 2**31 - 1))
+        if kind == "maxcut":
+            lo, hi = maxcut_n
+            n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+            n = max(n, p + 1)
+            out.append(dict(kind=kind, n=n, inst=maxcut_instance(n, maxcut_prob, p, sub)))
+        else:
+            lo, hi = completion_n
+            n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+            n = max(n, p + 1)
+            r = int(rng.integers(rank[0], rank[1] + 1))
+            rt = float(rng.uniform(rate[0], rate[1]))
+            out.append(dict(kind=kind, n=n, rank=r, rate=rt,
+                            inst=completion_instance(n, r, rt, p, sub)))
+    return out
+
+
+def poisson_arrivals(n_requests: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process with the given rate."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if rate_per_s <= 0 or not math.isfinite(rate_per_s):
+        return np.zeros(n_requests)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, n_requests))
