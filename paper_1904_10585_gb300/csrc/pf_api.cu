@@ -416,7 +416,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   tot += align_up(sizeof(pf_iter_info));
   // low-precision buffers: Y32[2], U32 (fp32 n x p); Xt[2] (p x ldxt, 4-byte elements)
   const int64_t ldxt = ((n_max + 63) / 64) * 64;
-  size_t lp_off[5] = {0, 0, 0, 0, 0};
+  size_t lp_off[7] = {0, 0, 0, 0, 0, 0, 0};
   if (lp) {
     for (int i = 0; i < 3; ++i) {
       lp_off[i] = tot;
@@ -425,6 +425,10 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
     for (int i = 3; i < 5; ++i) {
       lp_off[i] = tot;
       tot += align_up((size_t)p * ldxt * sizeof(float));
+    }
+    for (int i = 5; i < 7; ++i) {
+      lp_off[i] = tot;
+      tot += align_up((size_t)n_max * 64 * sizeof(float));
     }
   }
   void *base = nullptr;
@@ -459,6 +463,8 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
     ws.U32 = (float *)(b + lp_off[2]);
     ws.Xt[0] = (void *)(b + lp_off[3]);
     ws.Xt[1] = (void *)(b + lp_off[4]);
+    ws.Wf = (float *)(b + lp_off[5]);
+    ws.Vf = (float *)(b + lp_off[6]);
   }
   ctx->base = base;
   ctx->bytes = tot;

@@ -72,6 +72,7 @@ struct Workspace {
   float *Y32[2];          // fp32 recurrence buffers, n_max x p
   float *U32;             // fp32 copy of the start block
   void *Xt[2];            // transposed low-precision operands, p x ldxt
+  float *Wf, *Vf;         // fp32 factors of the shadow expansion, n_max x 64
   int64_t ldxt;
 };
 
@@ -118,6 +119,10 @@ cudaError_t launch_tc_product(cudaStream_t s, const Workspace &ws, bool tf32, co
                               int64_t lda_lp, int n, const void *Xt,
                               const float *Ycur, const float *Yprev, float *Ynext, void *Xt_next,
                               int mode);
+cudaError_t launch_tc_expand(cudaStream_t s, const Workspace &ws, bool f32out, const int32_t *rowptr,
+                             const int32_t *colind, const double *vals, int n, const double *V,
+                             int64_t ldv, const double *theta, const double *lam, void *Zlp,
+                             int64_t ldz);
 cudaError_t launch_prep_lp(cudaStream_t s, const Workspace &ws, bool tf32, const double *U,
                            int64_t ldu, int n, float *U32, void *Xt);
 cudaError_t launch_f32_to_f64(cudaStream_t s, const Workspace &ws, const float *src, int64_t total,

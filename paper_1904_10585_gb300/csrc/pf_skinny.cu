@@ -68,6 +68,17 @@ __global__ void __launch_bounds__(NT) k_gram(const double *__restrict__ X, int64
   }
 }
 
+// In-place fixed-order reduction of the Gram partials into partial 0:
+// out[idx] = sum_q part[q][idx], one thread per output element.
+__global__ void k_gram_reduce(double *__restrict__ gpart, int nparts, int m) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m) return;
+  double s = gpart[idx];
+#pragma unroll 8
+  for (int q = 1; q < nparts; ++q) s += gpart[(int64_t)q * m + idx];
+  gpart[idx] = s;
+}
+
 // Sum Gram partials, Cholesky G = R^T R (upper R), write R^{-1}.
 // pass 0: on a collapsed pivot retry once with the shift
 //         s = 11 (n p + p (p+1)) u tr(G) and set flags bit 0;
@@ -438,8 +449,17 @@ cudaError_t launch_gram(cudaStream_t s, const Workspace &ws, const double *X, in
       k_gram<64><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
       PF_LAUNCHED();
     }
-  *nblocks_out = nb;
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // reduce the partials in place so that consumers read one matrix
+  if (nb > 1) {
+    const int m = px * py;
+    k_gram_reduce<<<(m + 255) / 256, 256, 0, s>>>(ws.gpart, nb, m);
+    PF_LAUNCHED();
+    e = cudaGetLastError();
+  }
+  *nblocks_out = 1;
+  return e;
 }
 
 cudaError_t launch_chol_inv(cudaStream_t s, const Workspace &ws, int nparts, int n, int p, int pass) {

@@ -17,9 +17,12 @@ constexpr int WPB = NT / 32;  // warps per block
 // Low-rank + sparse operator with the Chebyshev epilogue:
 //   op(X)_i = sum_l Uf_il T_l. + sscale * sum_e S_e X_{col_e} + shift X_i
 //   Ynext   = alpha (op(X) - c X) - beta Yprev   (mode as in the dense path)
-// One warp per row; lanes own columns j = lane, lane + 32.
+// One warp per row.  The two half-warps take alternate entries of the row
+// (and alternate terms of the low-rank sum); lane h of a half covers columns
+// h, h + 16, ... (JG groups of 16), so every lane does useful FP64 work for
+// any p.  The halves are combined by one shuffle in a fixed order.
 // ---------------------------------------------------------------------------
-template <int JN>
+template <int JG>
 __global__ void __launch_bounds__(NT) k_lrsp_apply(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const double *__restrict__ svals, int n, int p, const double *__restrict__ Uf, int64_t lduf,
@@ -34,12 +37,12 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
     c = prm->c;
     alpha = (mode == MODE_FIRST ? 1.0 : 2.0) / prm->e;
   }
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
   const int warps = gridDim.x * WPB;
   for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
-    double acc[JN];
+    double acc[JG], lr[JG];
 #pragma unroll
-    for (int q = 0; q < JN; ++q) acc[q] = 0.0;
+    for (int g = 0; g < JG; ++g) acc[g] = lr[g] = 0.0;
     if (svals != nullptr) {
       const int e0 = rowptr[row], e1 = rowptr[row + 1];
       for (int base = e0; base < e1; base += 32) {
@@ -47,32 +50,49 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
         const int mcol = my < e1 ? colind[my] : 0;
         const double mv = my < e1 ? svals[my] : 0.0;
         const int cnt = min(32, e1 - base);
-        for (int k = 0; k < cnt; ++k) {
-          const int col = __shfl_sync(0xffffffffu, mcol, k);
-          const double v = __shfl_sync(0xffffffffu, mv, k);
+        for (int k = 0; k < cnt; k += 2) {
+          const int kk = k + half;  // half 0: even entries, half 1: odd entries
+          const int col = __shfl_sync(0xffffffffu, mcol, kk);
+          const double v = __shfl_sync(0xffffffffu, mv, kk);
+          const double *xr = X + (int64_t)col * ldx;
 #pragma unroll
-          for (int q = 0; q < JN; ++q) {
-            const int j = lane + 32 * q;
-            if (j < p) acc[q] = fma(v, X[(int64_t)col * ldx + j], acc[q]);
+          for (int g = 0; g < JG; ++g) {
+            const int j = hl + 16 * g;
+            if (j < p) acc[g] = fma(v, xr[j], acc[g]);
           }
         }
       }
     }
+    // low-rank part, terms l = half, half + 2, ...
+    const double *ur = Uf + (int64_t)row * lduf;
+    for (int l = half; l < r; l += 2) {
+      const double u = ur[l];
 #pragma unroll
-    for (int q = 0; q < JN; ++q) {
-      const int j = lane + 32 * q;
-      if (j >= p) continue;
-      double lr = 0.0;
-      for (int l = 0; l < r; ++l) lr = fma(Uf[(int64_t)row * lduf + l], Ts[l * p + j], lr);
-      const double xij = X[(int64_t)row * ldx + j];
-      const double o = lr + sscale * acc[q] + shift * xij;
-      double y;
-      if (mode == MODE_PLAIN) y = o;
-      else {
-        y = alpha * (o - c * xij);
-        if (mode == MODE_RECUR) y -= Yprev[(int64_t)row * ldp + j];
+      for (int g = 0; g < JG; ++g) {
+        const int j = hl + 16 * g;
+        if (j < p) lr[g] = fma(u, Ts[l * p + j], lr[g]);
       }
-      Ynext[(int64_t)row * ldn + j] = y;
+    }
+#pragma unroll
+    for (int g = 0; g < JG; ++g) {
+      acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], 16);
+      lr[g] += __shfl_xor_sync(0xffffffffu, lr[g], 16);
+    }
+    if (half == 0) {
+#pragma unroll
+      for (int g = 0; g < JG; ++g) {
+        const int j = hl + 16 * g;
+        if (j >= p) continue;
+        const double xij = X[(int64_t)row * ldx + j];
+        const double o = lr[g] + sscale * acc[g] + shift * xij;
+        double y;
+        if (mode == MODE_PLAIN) y = o;
+        else {
+          y = alpha * (o - c * xij);
+          if (mode == MODE_RECUR) y -= Yprev[(int64_t)row * ldp + j];
+        }
+        Ynext[(int64_t)row * ldn + j] = y;
+      }
     }
   }
 }
@@ -525,20 +545,16 @@ cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, con
   }
   int blocks = (n + WPB - 1) / WPB;
   if (blocks > 8 * ws.num_sms) blocks = 8 * ws.num_sms;
-  if (p <= 32)
-    {
-      k_lrsp_apply<1><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf, op.lduf, r,
-                                            ws.T, op.sscale, op.shift, X, ldx, Yprev, ldp, Ynext,
-                                            ldn, ws.prm, mode);
-      PF_LAUNCHED();
-    }
-  else
-    {
-      k_lrsp_apply<2><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf, op.lduf, r,
-                                            ws.T, op.sscale, op.shift, X, ldx, Yprev, ldp, Ynext,
-                                            ldn, ws.prm, mode);
-      PF_LAUNCHED();
-    }
+#define PF_LRSP(JGV)                                                                            \
+  k_lrsp_apply<JGV><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf, op.lduf, r, \
+                                          ws.T, op.sscale, op.shift, X, ldx, Yprev, ldp, Ynext,   \
+                                          ldn, ws.prm, mode)
+  if (p <= 16) { PF_LRSP(1); }
+  else if (p <= 32) { PF_LRSP(2); }
+  else if (p <= 48) { PF_LRSP(3); }
+  else { PF_LRSP(4); }
+#undef PF_LRSP
+  PF_LAUNCHED();
   return cudaGetLastError();
 }
 
@@ -1078,6 +1094,16 @@ cudaError_t launch_maxcut_lp_shadow(cudaStream_t s, const Workspace &ws, bool f3
   PF_LAUNCHED();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // tensor-core expansion (tf32 MMA over the r+ <= 64 factors)
+  return launch_tc_expand(s, ws, f32out, rowptr, colind, vals, n, V, ldv, theta, lam, Zlp, ldz);
+}
+
+// fp32 CUDA-core expansion (the reference form of the tensor-core kernel).
+cudaError_t launch_maxcut_lp_shadow_fp32(cudaStream_t s, const Workspace &ws, bool f32out,
+                                         const int32_t *rowptr, const int32_t *colind,
+                                         const double *vals, int n, int p, const double *V,
+                                         int64_t ldv, const double *theta, const double *lam,
+                                         void *Zlp, int64_t ldz) {
   const int64_t tiles1 = (n + EL - 1) / EL;
   int64_t blocks = tiles1 * tiles1;
   if (blocks > 8 * ws.num_sms) blocks = 8 * ws.num_sms;

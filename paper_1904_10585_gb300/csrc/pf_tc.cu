@@ -300,6 +300,179 @@ __global__ void k_f32_to_f64(const float *__restrict__ src, int64_t total, doubl
     dst[idx] = (double)src[idx];
 }
 
+// ---------------------------------------------------------------------------
+// Low-precision shadow of the max-cut iteration matrix (Eq. (PFAM1)):
+//     Z_lp[i][j] = ( sum_l W[i][l] V[j][l] - t C_ij - [i == j] lam_i ) / s
+// with W = V diag(max(theta, 0)) (fp32, K-padded to KP columns, zero beyond
+// r+).  One CTA per 128 x 128 output tile: TMA loads the 128 x KP tiles of W
+// and V (tf32 operands), tcgen05.mma (kind::tf32, M = N = 128) accumulates in
+// 128 TMEM columns, and the epilogue adds the sparse and diagonal parts,
+// scales and stores bf16 (or fp32) rows.
+// ---------------------------------------------------------------------------
+constexpr int EX_TILE = 128;
+
+template <int KP, bool F32OUT>
+__global__ void __launch_bounds__(TC_THREADS)
+    k_tc_expand(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmV,
+                int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
+                const double *__restrict__ vals, const double *__restrict__ lam, void *Zlp,
+                int64_t ldz, Params *prm) {
+  constexpr int KB = KP / 32;                 // 128-byte k-blocks of tf32
+  constexpr int TILE_BYTES = EX_TILE * TC_ROWB;  // 16 KB per operand per k-block
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar;
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t sW = base, sV = base + KB * TILE_BYTES;
+  const int i0 = blockIdx.y * EX_TILE, j0 = blockIdx.x * EX_TILE;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(smem_u32(&full_bar), 1);
+    mbar_init(smem_u32(&acc_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(128u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const uint32_t fb = smem_u32(&full_bar);
+    mbar_expect_tx(fb, 2 * KB * TILE_BYTES);
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) {
+      tma_load_2d(sW + kb * TILE_BYTES, &tmW, fb, kb * 32, i0);
+      tma_load_2d(sV + kb * TILE_BYTES, &tmV, fb, kb * 32, j0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(EX_TILE >> 3) << 17) |
+                               ((uint32_t)(EX_TILE >> 4) << 24);
+    if (mbar_wait(smem_u32(&full_bar), 0, &abort_flag)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kb = 0; kb < KB; ++kb) {
+        const uint64_t ad = sw128_desc(sW + kb * TILE_BYTES);
+        const uint64_t bd = sw128_desc(sV + kb * TILE_BYTES);
+#pragma unroll
+        for (int k = 0; k < TC_ROWB / 32; ++k)
+          mma_issue<true>(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      }
+      mma_commit(smem_u32(&acc_bar));
+    }
+  }
+  __syncwarp();
+  const bool have_acc = mbar_wait(smem_u32(&acc_bar), 0, &abort_flag);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have_acc) {
+    const float t = (float)prm->t;
+    const float inv_s = (float)(1.0 / prm->lp_scale);
+    const int row = i0 + warp * 32 + lane;
+    const bool in = row < n;
+    // this row's sparse entries with columns in [j0, j0 + 128)
+    int e = 0, e_end = 0;
+    if (in) {
+      int lo = rowptr[row], hi = rowptr[row + 1];
+      e_end = hi;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (colind[mid] < j0) lo = mid + 1;
+        else hi = mid;
+      }
+      e = lo;
+    }
+    const float lrow = in ? (float)lam[row] : 0.f;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < EX_TILE; c0 += 16) {
+      float v[16];
+      tmem_ld16(taddr + c0, v);
+      if (!in || j0 + c0 >= n) continue;
+      // sparse part on columns j0 + c0 .. j0 + c0 + 15
+      while (e < e_end) {
+        const int col = colind[e];
+        if (col >= j0 + c0 + 16) break;
+        const int q = col - (j0 + c0);
+        const float tc = t * (float)vals[e];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] -= (k == q) ? tc : 0.f;
+        ++e;
+      }
+      const int dj = row - (j0 + c0);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] -= (k == dj) ? lrow : 0.f;
+      const int64_t off = (int64_t)row * ldz + j0 + c0;
+      const int valid = min(16, n - (j0 + c0));
+      if (F32OUT) {
+        float *zp = reinterpret_cast<float *>(Zlp) + off;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (q < valid) zp[q] = v[q] * inv_s;
+      } else {
+        __nv_bfloat16 *zp = reinterpret_cast<__nv_bfloat16 *>(Zlp) + off;
+        if (valid == 16 && ((off & 7) == 0)) {
+          uint32_t w[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q] * inv_s, v[2 * q + 1] * inv_s);
+            w[q] = *reinterpret_cast<const uint32_t *>(&h2);
+          }
+          uint4 *dst = reinterpret_cast<uint4 *>(zp);
+          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (q < valid) zp[q] = __float2bfloat16_rn(v[q] * inv_s);
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && (abort_flag || !have_acc)) atomicOr(&prm->flags, 8);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u)
+                 : "memory");
+  }
+}
+
+// W = V diag(max(theta,0)) and V in fp32, K-padded to KP (zero beyond r+).
+__global__ void k_expand_prep(const double *__restrict__ V, int64_t ldv,
+                              const double *__restrict__ theta, int n, int p, int KP,
+                              float *__restrict__ Wf, float *__restrict__ Vf) {
+  const int64_t total = (int64_t)n * KP;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / KP;
+    const int l = (int)(idx - i * KP);
+    float w = 0.f, v = 0.f;
+    if (l < p) {
+      const double th = theta[l];
+      if (th > 0.0) {
+        const double x = V[i * ldv + l];
+        w = (float)(x * th);
+        v = (float)x;
+      }
+    }
+    Wf[idx] = w;
+    Vf[idx] = v;
+  }
+}
+
+size_t expand_smem_bytes(int KP) { return 1024 + (size_t)2 * (KP / 32) * EX_TILE * TC_ROWB; }
+
 size_t tc_smem_bytes(int NB) { return 1024 + (size_t)TC_STAGES * (TC_A_BYTES + NB * TC_ROWB); }
 
 template <int NB, bool TF32>
@@ -331,6 +504,16 @@ cudaError_t configure_tc() {
   PF_TC_ATTR(48)
   PF_TC_ATTR(64)
 #undef PF_TC_ATTR
+#define PF_EX_ATTR(KPV, F32)                                                                 \
+  if ((e = cudaFuncSetAttribute(k_tc_expand<KPV, F32>,                                       \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
+                                (int)expand_smem_bytes(KPV))) != cudaSuccess)                \
+    return e;
+  PF_EX_ATTR(32, false)
+  PF_EX_ATTR(64, false)
+  PF_EX_ATTR(32, true)
+  PF_EX_ATTR(64, true)
+#undef PF_EX_ATTR
   return cudaSuccess;
 }
 
@@ -408,6 +591,38 @@ cudaError_t launch_f32_to_f64(cudaStream_t s, const Workspace &ws, const float *
   if (blocks > 4 * ws.num_sms) blocks = 4 * ws.num_sms;
   if (blocks < 1) blocks = 1;
   k_f32_to_f64<<<(int)blocks, 256, 0, s>>>(src, total, dst);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_expand(cudaStream_t s, const Workspace &ws, bool f32out, const int32_t *rowptr,
+                             const int32_t *colind, const double *vals, int n, const double *V,
+                             int64_t ldv, const double *theta, const double *lam, void *Zlp,
+                             int64_t ldz) {
+  const int p = ws.p;
+  const int KP = p <= 32 ? 32 : 64;
+  int64_t blocks = ((int64_t)n * KP + 255) / 256;
+  if (blocks > 4 * ws.num_sms) blocks = 4 * ws.num_sms;
+  k_expand_prep<<<(int)blocks, 256, 0, s>>>(V, ldv, theta, n, p, KP, ws.Wf, ws.Vf);
+  PF_LAUNCHED();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mw, mv;
+  if ((e = encode_map(&mw, ws.Wf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
+  if ((e = encode_map(&mv, ws.Vf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
+  const dim3 grid((n + EX_TILE - 1) / EX_TILE, (n + EX_TILE - 1) / EX_TILE);
+  const size_t smem = expand_smem_bytes(KP);
+#define PF_EX_LAUNCH(KPV, F32)                                                                    \
+  k_tc_expand<KPV, F32><<<grid, TC_THREADS, smem, s>>>(mw, mv, n, rowptr, colind, vals, lam, Zlp, \
+                                                       ldz, ws.prm)
+  if (KP == 32) {
+    if (f32out) PF_EX_LAUNCH(32, true);
+    else PF_EX_LAUNCH(32, false);
+  } else {
+    if (f32out) PF_EX_LAUNCH(64, true);
+    else PF_EX_LAUNCH(64, false);
+  }
+#undef PF_EX_LAUNCH
   PF_LAUNCHED();
   return cudaGetLastError();
 }

@@ -69,3 +69,31 @@ def test_lowprec_maxcut_tracks_fp64(S, lowprec):
     o64, olp = h64[-1].obj, hlp[-1].obj
     assert abs(olp - o64) <= 1e-3 * abs(o64), (olp, o64)
     assert hlp[-1].kkt < 0.5 * hlp[10].kkt
+
+
+@pytest.mark.parametrize("lowprec,p,n", [("bf16", 32, 700), ("bf16", 64, 1000), ("tf32", 40, 517)])
+def test_lowprec_shadow_matches_state(S, lowprec, p, n):
+    """The shadow written by the tensor-core expansion equals
+    (V diag(theta+) V^T - tC - Diag(lam)) / s rebuilt in PyTorch FP64 from the
+    problem's state, to the storage precision (bf16: 4e-3, fp32: 2e-3 of the
+    unit scale; the tf32 products contribute ~1e-3 at most)."""
+    import paper_1904_10585_gb300 as B
+    inst = syn.maxcut_instance(n, 0.03, p, seed=n + p)
+    pr, hist = _run(S, inst, p, 3, 6, dense=False, lowprec=lowprec)
+    V = pr.V.double()
+    th = pr.theta.double()
+    lam = pr.lam.double()
+    C = torch.from_numpy(inst.C.to_dense()).to(DEV)
+    t = pr.t
+    Xt = (V * th.clamp(min=0)) @ V.T
+    Zref = Xt - t * C - torch.diag(lam)
+    # the scale: Gershgorin bounds of -tC - Diag(lam), plus theta_max
+    D = -t * C - torch.diag(lam)
+    off = D.abs().sum(1) - D.diagonal().abs()
+    lo = (D.diagonal() - off).min().item()
+    hi = (D.diagonal() + off).max().item()
+    s = max(abs(lo), abs(hi + max(th[0].item(), 0.0)))
+    got = pr.Z_lp.double()
+    err = (got - Zref / s).abs().max().item()
+    tol = 4e-3 if lowprec == "bf16" else 2e-3
+    assert err <= tol, err
