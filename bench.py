@@ -113,6 +113,16 @@ def dist_setup():
 # reference arm: the CPU oracle, bounded samples
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(values, pg, device=None):
+    """Element-wise max of per-rank timings over the process group (the whole
+    job is as slow as its slowest replica); identity on a single process."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -131,6 +141,7 @@ class WorkloadSpec:
         self.n, self.p, self.d, self.iters = c["n"], c["p"], c["degree"], c["iters"]
         self.kind = c["kind"]
         self.lowprec = "bf16" if name.endswith("lowprec") else None
+        self.structured = name.endswith("structured")
 
     def nnz(self):
         return self.inst.C.nnz if self.kind == "maxcut" else self.inst.omega.nnz
@@ -155,18 +166,25 @@ class WorkloadSpec:
         return time.perf_counter() - t0
 
     def sample_iters(self):
-        return min(self.iters, {"maxcut_n4096": 15, "completion_n400": 100}.get(self.name, 1))
+        return min(self.iters, {"maxcut_n4096": 15, "maxcut_n4096_structured": 15,
+                                "completion_n400": 100}.get(self.name, 1))
 
     def config(self):
         c = self.cfg
         d = {"workload": self.name, "n": c["n"], "p": c["p"], "degree": c["degree"],
              "max_iters": c["iters"], "tol_kkt": TOL}
         if self.kind == "maxcut":
-            d["problem"] = ("max-cut SDP (PFAM, dense FP64 iteration matrix)" if not self.lowprec
-                            else "max-cut SDP (PFAM, bf16 dense shadow filter on tcgen05, "
-                                 "structured FP64 Rayleigh-Ritz)")
+            if self.structured:
+                d["problem"] = ("max-cut SDP (PFAM, structured FP64 iteration matrix "
+                                "Z = X~ - tC - Diag(lam), never formed)")
+            elif self.lowprec:
+                d["problem"] = ("max-cut SDP (PFAM, bf16 dense shadow filter on tcgen05, "
+                                "structured FP64 Rayleigh-Ritz)")
+            else:
+                d["problem"] = "max-cut SDP (PFAM, dense FP64 iteration matrix)"
             d["graph"] = f"Erdos-Renyi p={c['prob']}, weights +-1"
-            bytes_z = self.n * self.n * (2 if self.lowprec else 8)
+            bytes_z = (self.nnz() * 16 if self.structured
+                       else self.n * self.n * (2 if self.lowprec else 8))
         else:
             d["problem"] = "PSD matrix completion (PFPG, low-rank + sparse FP64 operator)"
             d["sampling"] = f"symmetric uniform {c['rate']}, rank {c['rank']}, mu {c['mu']}"
@@ -230,7 +248,7 @@ class Workload(WorkloadSpec):
         cv = self.cv if cv is None else cv
         U0 = self.U0 if U0 is None else U0
         if self.kind == "maxcut":
-            if self.lowprec:
+            if self.lowprec or self.structured:
                 return S.maxcut_problem(rp, ci, cv, U0, dense=False, lowprec=self.lowprec)
             return S.maxcut_problem(rp, ci, cv, U0)
         return S.completion_problem(rp, ci, cv, U0, mu=self.cfg["mu"], t=self.cfg["t"])
@@ -238,6 +256,16 @@ class Workload(WorkloadSpec):
     def kernel_op(self, pr):
         """(operator, description, bound, work per launch, unit) of the dominant kernel."""
         S, B, n, p = self.S, self.B, self.n, self.p
+        if self.kind == "maxcut" and self.structured:
+            # the structured product Z X = X~ X - tC X - lam o X (one SpMM + low-rank)
+            th = pr.theta.clamp(min=0)
+            Sv = torch.empty_like(pr.S)
+            Sv.copy_(-pr.t * self.cv)
+            self._keep = (th, Sv)
+            op = S.lowrank_sparse_operator(n, pr.V, th, self.rp, self.ci, Sv, 1.0, 0.0)
+            nnz = self.ci.numel()
+            return (op, "k_lrsp_apply (structured Z X: CSR SpMM + low-rank, FP64) + k_gram",
+                    "alu", 2.0 * nnz * p + 4.0 * n * p * p, "TFLOP/s")
         if self.kind == "maxcut" and not self.lowprec:
             return (S.dense_operator(pr.Z),
                     "k_gemm_f64_splitk + k_combine (Y = Z X, dense FP64 filter product)",
@@ -333,17 +361,33 @@ def run_ours(args):
     op, kname, bound, work, unit = W.kernel_op(pr)
     X = pr.U.clone()
     Y = torch.empty_like(X)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            S.apply(ctx, op, X, Y)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(R):
-            S.apply(ctx, op, X, Y)
-        e1.record(stream)
-    stream.synchronize()
-    apply_ms = e0.elapsed_time(e1) / R
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    if W.lowprec:
+        # the tensor-core product alone: a degree-5 filter minus a degree-1
+        # filter on the same block is exactly four product launches (the
+        # operand preparation and CholQR2 cancel)
+        info = pkg.pf_get_info(ctx.handle)
+        a_int, b_int = info.a, info.b
+        Ub = pr.U.clone()
+
+        def filt(deg):
+            return lambda: (X.copy_(Ub), S.filter_(ctx, op, a_int, b_int, deg, X))
+        apply_ms = (timed(filt(5), R) - timed(filt(1), R)) / 4.0
+    else:
+        apply_ms = timed(lambda: S.apply(ctx, op, X, Y), R)
     if unit == "TFLOP/s":
         achieved = work / (apply_ms * 1e-3) / 1e12
         peak, peak_src = FP64_PEAK_TFLOPS, ("recipe nominal FP64 1.25 TFLOP/s (no measured FP64 peak; "
@@ -391,10 +435,7 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
 
     # max over ranks
-    tot = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
-    if pg:
-        pg.all_reduce(tot, op=pg.ReduceOp.MAX)
-    total_ms, e2e_s = float(tot[0]), float(tot[1])
+    total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], pg, dev)
     value = world * args.steps / (total_ms * 1e-3)
     e2e_value = world * e2e_steps / e2e_s
 
@@ -467,7 +508,7 @@ def run_serving(args):
     slots = [("maxcut", mc_n[1], 8), ("completion", cp_n[1], 8)]
     budget = 16 << 30
     srv = SV.Server(slots, p=p, degree=degree, tol=TOL, chunk=10, hbm_budget=budget,
-                    maxcut_lowprec=True, device=dev)
+                    maxcut_lowprec=True, completion_lowprec=True, device=dev)
     # warm-up: two small requests of each kind
     warm = sorted(reqs, key=lambda r: r.n)[:4]
     srv.run([dataclasses_replace(r, arrival=0.0, max_iter=20) for r in warm])
@@ -524,7 +565,7 @@ def run_serving(args):
                    "completion_n": cp_n, "rank": [5, 20], "sampling": [0.01, 0.10], "p": p,
                    "degree": degree, "slots": slots, "hbm_budget_bytes": budget,
                    "maxcut_filter": "bf16 dense shadow on tcgen05 + FP64 structured RR",
-                   "completion_filter": "FP64 low-rank + sparse operator",
+                   "completion_filter": "fp32 low-rank + sparse products + FP64 RR",
                    "l2": "requests' matrices mostly exceed L2; not flushed between requests"},
         "latency_s": {"poisson_0.8x_p50": p50, "poisson_0.8x_p99": p99,
                       "saturation_p50": sp50, "saturation_p99": sp99},

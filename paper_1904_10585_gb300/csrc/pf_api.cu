@@ -168,9 +168,34 @@ pf_status filter_core_lp(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int 
   return cholqr2(ctx, ws.Y[0], p, U, ldu, op.n);
 }
 
+// Low-precision context, low-rank + sparse operator: fp32 products on the
+// CUDA cores, fp32 recurrence, then CholQR2 in FP64.
+pf_status filter_core_lp_sparse(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
+  const int p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  const Workspace &ws = ctx->ws;
+  const float *Uf32 = nullptr;
+  if (op.r > 0 && op.Uf != nullptr) {
+    PF_CUDA(launch_to_f32(s, ws, op.Uf, op.lduf, op.n, op.r, ws.Wf));
+    Uf32 = ws.Wf;
+  }
+  PF_CUDA(launch_to_f32(s, ws, U, ldu, op.n, p, ws.U32));
+  for (int j = 0; j < degree; ++j) {
+    const float *cur = j == 0 ? ws.U32 : ws.Y32[(j - 1) & 1];
+    const float *prev = j == 1 ? ws.U32 : ws.Y32[j & 1];
+    float *next = ws.Y32[j & 1];
+    PF_CUDA(launch_lowrank_sparse_apply32(s, ws, op, Uf32, cur, prev, next,
+                                          j == 0 ? MODE_FIRST : MODE_RECUR));
+  }
+  PF_CUDA(launch_f32_to_f64(s, ws, ws.Y32[(degree - 1) & 1], (int64_t)op.n * p, ws.Y[0]));
+  return cholqr2(ctx, ws.Y[0], p, U, ldu, op.n);
+}
+
 // U <- orth(rho(op) U) with the interval already in the device parameters.
 pf_status filter_core(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
   const int p = ctx->p;
+  if (op.kind == PF_OP_LOWRANK_SPARSE && ctx->cur_lp)
+    return filter_core_lp_sparse(ctx, op, U, ldu, degree);
   if (op.kind == PF_OP_DENSE && op.A_lp != nullptr && ctx->opt.precision != PF_PREC_FP64)
     return filter_core_lp(ctx, op, U, ldu, degree);
   double *const *Y = ctx->ws.Y;
@@ -192,7 +217,8 @@ pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, doubl
   PF_TRY(apply(ctx, op, Q, ldq, nullptr, 0, ws.W, p, MODE_PLAIN));
   int nb = 0;
   PF_CUDA(launch_gram(s, ws, Q, ldq, ws.W, p, op.n, p, p, 0, &nb));
-  PF_CUDA(launch_jacobi(s, ws, nb, p, theta));
+  // launch_gram leaves the reduced H = Q^T W in the first Gram slot
+  PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, theta));
   PF_CUDA(launch_rotate_resid(s, ws, Q, ldq, ws.W, p, op.n, p, theta, V, ldv, resid));
   return PF_OK;
 }
@@ -386,6 +412,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = configure_skinny();
   if (e == cudaSuccess) e = configure_sparse();
+  if (e == cudaSuccess) e = configure_jacobi();
   if (e == cudaSuccess && lp) e = configure_tc();
   if (e != cudaSuccess) {
     delete ctx;

@@ -86,6 +86,7 @@ extern std::atomic<int64_t> g_launches;
 cudaError_t configure_skinny();
 cudaError_t configure_tc();
 cudaError_t configure_sparse();
+cudaError_t configure_jacobi();
 // K splits of the dense FP64 product for size n (returns S, sets the chunk).
 int dense_splits(int n, int num_sms, int *kchunk);
 
@@ -108,6 +109,8 @@ cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double
                                double *Q, int64_t ldq, int n, int p, const double *R, int upper,
                                int cond_flag);
 cudaError_t launch_jacobi(cudaStream_t s, const Workspace &ws, int nparts, int p, double *theta);
+cudaError_t launch_jacobi_cluster(cudaStream_t s, const Workspace &ws, const double *H, int p,
+                                  double *theta);
 cudaError_t launch_rotate_resid(cudaStream_t s, const Workspace &ws, const double *Q, int64_t ldq,
                                 const double *W, int64_t ldw, int n, int p, const double *theta,
                                 double *V, int64_t ldv, double *resid_out);
@@ -123,6 +126,11 @@ cudaError_t launch_tc_expand(cudaStream_t s, const Workspace &ws, bool f32out, c
                              const int32_t *colind, const double *vals, int n, const double *V,
                              int64_t ldv, const double *theta, const double *lam, void *Zlp,
                              int64_t ldz);
+cudaError_t launch_to_f32(cudaStream_t s, const Workspace &ws, const double *src, int64_t lds,
+                          int n, int p, float *dst);
+cudaError_t launch_lowrank_sparse_apply32(cudaStream_t s, const Workspace &ws, const Op &op,
+                                          const float *Uf32, const float *X, const float *Yprev,
+                                          float *Ynext, int mode);
 cudaError_t launch_prep_lp(cudaStream_t s, const Workspace &ws, bool tf32, const double *U,
                            int64_t ldu, int n, float *U32, void *Xt);
 cudaError_t launch_f32_to_f64(cudaStream_t s, const Workspace &ws, const float *src, int64_t total,

@@ -106,14 +106,16 @@ class Server:
     are shared.  hbm_budget bounds the summed footprint of admitted requests."""
 
     def __init__(self, slots, p=32, degree=4, tol=1e-4, chunk=10, hbm_budget=16 << 30,
-                 maxcut_lowprec=True, device=None):
+                 maxcut_lowprec=True, completion_lowprec=False, device=None):
         self.dev = device or torch.device("cuda", torch.cuda.current_device())
         self.p, self.degree, self.tol, self.chunk = p, degree, tol, chunk
         self.budget = int(hbm_budget)
         self.maxcut_lowprec = maxcut_lowprec
+        self.completion_lowprec = completion_lowprec
         self.slots: List[_Slot] = []
         for kind, n_max, count in slots:
-            prec = B.PF_PREC_BF16 if (kind == "maxcut" and maxcut_lowprec) else B.PF_PREC_FP64
+            lp = maxcut_lowprec if kind == "maxcut" else completion_lowprec
+            prec = B.PF_PREC_BF16 if lp else B.PF_PREC_FP64
             for _ in range(count):
                 self.slots.append(_Slot(kind, p, n_max, degree, prec, self.dev))
         self.used = 0

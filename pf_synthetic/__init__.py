@@ -200,6 +200,8 @@ WORKLOADS = {
                             iters=100, mu=0.05, t=1.0, config_index=0),
     "maxcut_n4096": dict(kind="maxcut", n=4096, prob=0.01, p=32, degree=4, iters=200,
                          config_index=1),
+    "maxcut_n4096_structured": dict(kind="maxcut", n=4096, prob=0.01, p=32, degree=4, iters=200,
+                                    config_index=1),
     "maxcut_n16384_lowprec": dict(kind="maxcut", n=16384, prob=0.01, p=64, degree=4,
                                   degree_max=8, iters=200, config_index=2),
     "completion_n50000": dict(kind="completion", n=50000, rank=20, rate=0.01, p=40, degree=4,

@@ -139,3 +139,33 @@ def test_lowprec_operator_validation(S):
         odd = torch.zeros(n, n + 1, dtype=torch.bfloat16, device=DEV)[:, :n]
         with pytest.raises(B.PFError):           # row pitch not a multiple of 16 bytes
             S.filter_(ctx, lp_operator(S, odd, 1.0), -1.0, 0.0, 2, U)
+
+
+@pytest.mark.parametrize("n,p,r,d", [(400, 16, 5, 3), (333, 40, 12, 4), (1000, 64, 20, 2)])
+def test_fp32_lowrank_sparse_filter_tracks_fp64(S, n, p, r, d):
+    """A bf16 context filters a low-rank + sparse operator with fp32 products
+    (CUDA cores) and FP64 CholQR2: the block agrees with the FP64 oracle's
+    filter to fp32 accuracy (elementwise 2e-5 relative to the block's scale)."""
+    import paper_1904_10585_gb300 as B
+    inst = syn.completion_instance(n, 4, 0.2, p, seed=n + r)
+    Om = o.omega_matrix(inst.omega)
+    Uf = o.orth(syn.gaussian_block(n, max(r, 1), seed=9))[:, :r]
+    lam_f = np.linspace(3.0, 0.5, r)
+    sscale, shift = -0.7, -0.05
+
+    def apply_B(X):
+        return Uf @ (lam_f[:, None] * (Uf.T @ X)) + sscale * (Om @ X) + shift * X
+
+    U0 = syn.gaussian_block(n, p, seed=11)
+    a, _ = o.gershgorin_bounds(sscale * Om, np.full(n, shift))
+    b = 0.1 * a
+    ref = o.orth(o.cheb_filter(apply_B, U0, a, b, d))
+    rp, ci, vals = S.csr_to_device(inst.omega, DEV, torch.float64)
+    with S.Context(p=p, n_max=n, degree=d, precision=B.PF_PREC_BF16) as ctx:
+        op = S.lowrank_sparse_operator(n, torch.from_numpy(Uf).to(DEV),
+                                       torch.from_numpy(lam_f).to(DEV), rp, ci, vals, sscale, shift)
+        U = torch.from_numpy(U0).to(DEV)
+        S.filter_(ctx, op, a, b, d, U)
+        torch.cuda.synchronize()
+    err = np.abs(U.cpu().numpy() - ref).max()
+    assert err <= 2e-5 * np.abs(ref).max(), err

@@ -97,3 +97,46 @@ def test_lowprec_shadow_matches_state(S, lowprec, p, n):
     err = (got - Zref / s).abs().max().item()
     tol = 4e-3 if lowprec == "bf16" else 2e-3
     assert err <= tol, err
+
+
+def test_adaptive_ladder_raises_degree_then_drops_to_fp64(S):
+    """pf_solve with the adaptive ladder: once the FP64-evaluated KKT stops
+    decreasing (here: a small solve run far past its accuracy floor), the
+    degree rises to degree_max and then the bf16 filter is replaced by the
+    FP64 one.  The solve itself stays correct (objective close to the plain
+    FP64 solve)."""
+    import paper_1904_10585_gb300 as B
+    n, p = 200, 16
+    inst = syn.maxcut_instance(n, 0.1, p, seed=21)
+    rp, ci, cv = S.csr_to_device(inst.C, DEV, torch.float64)
+    U0 = torch.from_numpy(np.ascontiguousarray(inst.U0_raw[:, :p])).to(DEV)
+    with S.Context(p=p, n_max=n, degree=2, degree_max=3, precision=B.PF_PREC_BF16, adaptive=1,
+                   stream=torch.cuda.Stream()) as ctx:
+        pr = S.maxcut_problem(rp, ci, cv, U0, dense=False, lowprec="bf16")
+        S.problem_init(ctx, pr)
+        res = S.solve(ctx, pr, 1500, 0.0, 10)
+        ctx.stream.synchronize()
+    assert res.last.degree == 3
+    assert res.last.precision == B.PF_PREC_FP64
+    _, h64 = _run(S, inst, p, 3, 1500, dense=False)
+    assert abs(res.obj - h64[-1].obj) <= 1e-4 * abs(h64[-1].obj)
+
+
+def test_fp32_completion_solve_tracks_fp64(S):
+    """PSD completion in a bf16 context (fp32 filter products, FP64 CholQR2 /
+    Rayleigh-Ritz / prox) follows the FP64 PFPG trajectory: objective within
+    1e-6 relative at every iteration."""
+    import paper_1904_10585_gb300 as B
+    cfg, inst = syn.make_workload("completion_n400")
+    p, d = cfg["p"], cfg["degree"]
+    rp, ci, vals = S.csr_to_device(inst.omega, DEV)
+    U0 = torch.from_numpy(np.ascontiguousarray(inst.U0_raw[:, :p])).to(DEV)
+    hist = {}
+    for prec in (B.PF_PREC_FP64, B.PF_PREC_BF16):
+        with S.Context(p=p, n_max=inst.n, degree=d, precision=prec,
+                       stream=torch.cuda.Stream()) as ctx:
+            pr = S.completion_problem(rp, ci, vals, U0, mu=cfg["mu"], t=cfg["t"])
+            S.problem_init(ctx, pr)
+            hist[prec] = [S.prox_step(ctx, pr) for _ in range(60)]
+    for a, b in zip(hist[B.PF_PREC_BF16], hist[B.PF_PREC_FP64]):
+        assert abs(a.obj - b.obj) <= 1e-6 * max(1.0, abs(b.obj)), (a.obj, b.obj)

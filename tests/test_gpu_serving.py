@@ -38,7 +38,7 @@ def test_results_alone_equal_results_in_mix(maxcut_lowprec):
     from paper_1904_10585_gb300 import serving as SV
     reqs = _requests()
     kw = dict(slots=[("maxcut", 600, 3), ("completion", 900, 3)], p=16, degree=3, tol=0.0,
-              chunk=5, maxcut_lowprec=maxcut_lowprec)
+              chunk=5, maxcut_lowprec=maxcut_lowprec, completion_lowprec=maxcut_lowprec)
     srv = SV.Server(**kw)
     try:
         mix = {r.rid: r for r in srv.run(reqs)}
