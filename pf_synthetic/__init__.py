@@ -254,3 +254,16 @@ def poisson_arrivals(n_requests: int, rate_per_s: float, seed: int) -> np.ndarra
     if rate_per_s <= 0 or not math.isfinite(rate_per_s):
         return np.zeros(n_requests)
     return np.cumsum(rng.exponential(1.0 / rate_per_s, n_requests))
+
+
+def nce_matrix(n: int, example: str, seed: int) -> np.ndarray:
+    """Symmetric test matrices of the nearest-correlation examples (Sec. 5.1):
+    "5.6": off-diagonal entries uniform in [-1, 1], unit diagonal;
+    "5.7": off-diagonal entries uniform in [0, 2], unit diagonal."""
+    rng = _streams(seed, 1)[0]
+    lo, hi = {"5.6": (-1.0, 1.0), "5.7": (0.0, 2.0)}[example]
+    A = rng.uniform(lo, hi, (n, n))
+    A = np.triu(A, 1)
+    A = A + A.T
+    np.fill_diagonal(A, 1.0)
+    return A

@@ -1,7 +1,12 @@
 import os
 import sys
 
-import pytest
+# The oracle's matrices in the tests are small; a single BLAS thread is much
+# faster for them than a thread pool (set before numpy is imported).
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import pytest  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:

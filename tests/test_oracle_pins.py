@@ -408,3 +408,61 @@ def test_synthetic_inputs_laws():
     off = Cd[~np.eye(500, dtype=bool)]
     assert set(np.unique(off[off != 0]).tolist()) <= {-0.25, 0.25}
     assert abs(mc.n_edges / (500 * 499 / 2) - 0.05) < 0.01
+
+
+# --------------------------------------------------------------------------
+# Nearest correlation estimation (Sec. 5.1)
+# --------------------------------------------------------------------------
+
+def test_nce_gradient_matches_finite_differences_of_the_dual():
+    """grad F(x) = diag(P_+(G + Diag x)) - 1 (Eq. (NCE-gradient)) against
+    central differences of F computed from eigenvalues only."""
+    n = 12
+    G = syn.nce_matrix(n, "5.7", seed=3)
+    x = np.random.default_rng(0).uniform(-2, 0, n)
+    st = o.NCEState(x=x, U=np.eye(n), theta_prev=None)
+    _, info = o.nce_step(G, st, 3, exact=True)
+    lam, V = np.linalg.eigh(G + np.diag(x))
+    g_ref = np.array([(o.nce_objective(G, x + 1e-6 * e) - o.nce_objective(G, x - 1e-6 * e)) / 2e-6
+                      for e in np.eye(n)])
+    pos = lam > 0
+    g_oracle = np.sum((V[:, pos] ** 2) * lam[pos], axis=1) - 1.0
+    np.testing.assert_allclose(g_oracle, g_ref, atol=1e-6)
+    assert abs(info.gnorm - np.linalg.norm(g_ref)) < 1e-6
+
+
+def test_nce_closed_forms():
+    """A correlation matrix is its own nearest correlation matrix (x* = 0 is
+    a fixed point); for G = 2I the answer is I with x* = -1."""
+    n = 20
+    Y = syn.gaussian_block(n, 4, seed=1)
+    Cm = Y @ Y.T
+    d = np.sqrt(np.diag(Cm))
+    Cm = Cm / np.outer(d, d)                      # PSD with unit diagonal
+    st = o.NCEState(x=np.zeros(n), U=syn.gaussian_block(n, n, seed=2), theta_prev=None)
+    st2, info = o.nce_step(Cm, st, 3, exact=True)
+    assert info.gnorm < 1e-12 and np.abs(st2.x).max() < 1e-12
+    st, hist = o.nce_solve(2.0 * np.eye(n), syn.gaussian_block(n, n, seed=3), 3, 50, exact=True)
+    np.testing.assert_allclose(st.x, -1.0, atol=1e-12)
+
+
+def test_nce_pf_with_full_block_equals_gradient_method():
+    n = 30
+    G = syn.nce_matrix(n, "5.7", seed=4)
+    U0 = syn.gaussian_block(n, n, seed=5)
+    _, h_pf = o.nce_solve(G, U0, 3, 30)
+    _, h_ex = o.nce_solve(G, U0, 3, 30, exact=True)
+    for a, b in zip(h_pf, h_ex):
+        assert abs(a.obj - b.obj) <= 1e-9 * max(1.0, abs(b.obj))
+        assert abs(a.gnorm - b.gnorm) <= 1e-8 * max(1.0, b.gnorm)
+
+
+def test_nce_pf_converges_on_example_5_7_law():
+    """PFPG with a 24-wide block reaches the gradient method's objective on a
+    small Example-5.7-law matrix (few positive eigenvalues at the solution)."""
+    n = 80
+    G = syn.nce_matrix(n, "5.7", seed=6)
+    _, h_ex = o.nce_solve(G, syn.gaussian_block(n, n, seed=7), 3, 1500, exact=True, tol=1e-5)
+    _, h_pf = o.nce_solve(G, syn.gaussian_block(n, 24, seed=7), 3, 1500, tol=1e-5)
+    assert h_pf[-1].rel <= 1e-5 and h_ex[-1].rel <= 1e-5
+    assert abs(h_pf[-1].obj - h_ex[-1].obj) <= 1e-7 * abs(h_ex[-1].obj)
