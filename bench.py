@@ -144,6 +144,8 @@ class WorkloadSpec:
         self.structured = name.endswith("structured")
 
     def nnz(self):
+        if self.kind == "nce":
+            return self.n * self.n
         return self.inst.C.nnz if self.kind == "maxcut" else self.inst.omega.nnz
 
     def oracle_sample(self, iters_sample):
@@ -151,7 +153,11 @@ class WorkloadSpec:
         import scipy.sparse as sp
         from oracle import pf_oracle as o
         t0 = time.perf_counter()
-        if self.kind == "maxcut":
+        if self.kind == "nce":
+            st = o.nce_init(self.inst.G, self.inst.U0_raw[:, :self.p])
+            for _ in range(iters_sample):
+                st, _ = o.nce_step(self.inst.G, st, self.d)
+        elif self.kind == "maxcut":
             inst = self.inst
             C = sp.csr_matrix((inst.C.vals, inst.C.colind, inst.C.rowptr), shape=(inst.n, inst.n))
             t = o.maxcut_step_size(C)
@@ -165,15 +171,24 @@ class WorkloadSpec:
                 st, _ = o.completion_pfpg_step(Om, st, self.cfg["mu"], self.cfg["t"], self.d)
         return time.perf_counter() - t0
 
+    def tol(self):
+        return 1e-7 if self.kind == "nce" else TOL
+
     def sample_iters(self):
         return min(self.iters, {"maxcut_n4096": 15, "maxcut_n4096_structured": 15,
-                                "completion_n400": 100}.get(self.name, 1))
+                                "completion_n400": 100, "nce_n4000": 10}.get(self.name, 1))
 
     def config(self):
         c = self.cfg
         d = {"workload": self.name, "n": c["n"], "p": c["p"], "degree": c["degree"],
              "max_iters": c["iters"], "tol_kkt": TOL}
-        if self.kind == "maxcut":
+        if self.kind == "nce":
+            d["problem"] = ("nearest correlation estimation, PFPG on the dual (dense FP64 "
+                            "G + Diag(x))")
+            d["matrix"] = f"Example {c['example']} law (off-diagonal uniform, unit diagonal)"
+            d["tol"] = "relative gradient norm 1e-7 (the paper's stopping rule)"
+            bytes_z = self.n * self.n * 8
+        elif self.kind == "maxcut":
             if self.structured:
                 d["problem"] = ("max-cut SDP (PFAM, structured FP64 iteration matrix "
                                 "Z = X~ - tC - Diag(lam), never formed)")
@@ -233,16 +248,32 @@ class Workload(WorkloadSpec):
         super().__init__(name)
         self.dev, self.S, self.B = dev, S, B
         self.U0 = torch.from_numpy(np.ascontiguousarray(self.inst.U0_raw[:, :self.p])).to(dev)
-        if self.kind == "maxcut":
+        if self.kind == "nce":
+            self.G = torch.from_numpy(self.inst.G).to(dev)
+        elif self.kind == "maxcut":
             self.rp, self.ci, self.cv = S.csr_to_device(self.inst.C, dev, torch.float64)
         else:
             self.rp, self.ci, self.cv = S.csr_to_device(self.inst.omega, dev)
+
+    def inputs(self):
+        """Device tensors holding this workload's inputs (copied from the host
+        in the end-to-end measurement), start block last."""
+        if self.kind == "nce":
+            return [self.G, self.U0]
+        return [self.rp, self.ci, self.cv, self.U0]
+
+    def problem_from(self, tensors):
+        if self.kind == "nce":
+            return self.S.nce_problem(tensors[0], tensors[1])
+        return self.problem(*tensors)
 
     def precision(self):
         return self.B.PF_PREC_BF16 if self.lowprec == "bf16" else self.B.PF_PREC_FP64
 
     def problem(self, rp=None, ci=None, cv=None, U0=None):
         S = self.S
+        if self.kind == "nce":
+            return S.nce_problem(self.G, self.U0 if U0 is None else U0)
         rp = self.rp if rp is None else rp
         ci = self.ci if ci is None else ci
         cv = self.cv if cv is None else cv
@@ -255,7 +286,12 @@ class Workload(WorkloadSpec):
 
     def kernel_op(self, pr):
         """(operator, description, bound, work per launch, unit) of the dominant kernel."""
+        import torch
         S, B, n, p = self.S, self.B, self.n, self.p
+        if self.kind == "nce":
+            return (S.dense_operator(pr.Z),
+                    "k_gemm_f64_splitk + k_combine (Y = (G + Diag x) X, dense FP64 filter product)",
+                    "alu", 2.0 * n * n * p, "TFLOP/s")
         if self.kind == "maxcut" and self.structured:
             # the structured product Z X = X~ X - tC X - lam o X (one SpMM + low-rank)
             th = pr.theta.clamp(min=0)
@@ -306,22 +342,27 @@ def run_ours(args):
 
     def solve_once(problem):
         problem.U.copy_(W.U0)           # fresh start block (on the library stream below)
+        if W.kind == "nce":
+            problem.Z.copy_(W.G)        # the iteration matrix starts from G again
         S.problem_init(ctx, problem)
-        return S.solve(ctx, problem, iters, TOL, CHECK_EVERY)
+        return S.solve(ctx, problem, iters, W.tol(), CHECK_EVERY)
 
     # launch counting (non-graph calls): init + one step
     with torch.cuda.stream(stream):
         c0 = pkg.pf_kernel_launch_count()
         pr.U.copy_(W.U0)
+        if W.kind == "nce":
+            pr.Z.copy_(W.G)
         S.problem_init(ctx, pr)
         c1 = pkg.pf_kernel_launch_count()
         S.prox_step(ctx, pr, want_info=False)
         c2 = pkg.pf_kernel_launch_count()
     init_launches, step_launches = c1 - c0, c2 - c1
     if args.profile:
-        # short run for profiler captures: a few more non-graph iterations
+        # short run for profiler captures: --profile-iters more non-graph
+        # iterations (skip the first ones in the profiler to see steady state)
         with torch.cuda.stream(stream):
-            for _ in range(3):
+            for _ in range(args.profile_iters):
                 S.prox_step(ctx, pr, want_info=False)
         stream.synchronize()
         print(json.dumps({"profile_run": args.workload, "launches_per_iteration": step_launches}))
@@ -398,27 +439,23 @@ def run_ours(args):
 
     # end to end through the public API: host (pinned) inputs copied in and the
     # solution factors read back inside the timed region
-    h_rp = W.rp.cpu().pin_memory()
-    h_ci = W.ci.cpu().pin_memory()
-    h_cv = W.cv.cpu().pin_memory()
-    h_u0 = W.U0.cpu().pin_memory()
+    h_in = [t.cpu().pin_memory() for t in W.inputs()]
+    d_in = [torch.empty_like(t) for t in W.inputs()]
     h_V = torch.empty((n, p), dtype=torch.float64).pin_memory()
     h_th = torch.empty((p,), dtype=torch.float64).pin_memory()
-    d_rp, d_ci, d_cv = torch.empty_like(W.rp), torch.empty_like(W.ci), torch.empty_like(W.cv)
-    d_u0 = torch.empty_like(W.U0)
-    pe = W.problem(d_rp, d_ci, d_cv, d_u0)
-    h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_ci, h_cv, h_u0))
+    pe = W.problem_from(d_in)
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = h_V.numel() * 8 + h_th.numel() * 8
     e2e_steps = max(1, min(args.steps, 3))
 
     def e2e_once():
-        d_rp.copy_(h_rp, non_blocking=True)
-        d_ci.copy_(h_ci, non_blocking=True)
-        d_cv.copy_(h_cv, non_blocking=True)
-        d_u0.copy_(h_u0, non_blocking=True)
-        pe.U.copy_(d_u0)
+        for hd, dd in zip(h_in, d_in):
+            dd.copy_(hd, non_blocking=True)
+        pe.U.copy_(d_in[-1])
+        if W.kind == "nce":
+            pe.Z.copy_(d_in[0])
         S.problem_init(ctx, pe)
-        S.solve(ctx, pe, iters, TOL, CHECK_EVERY)
+        S.solve(ctx, pe, iters, W.tol(), CHECK_EVERY)
         h_V.copy_(pe.V, non_blocking=True)
         h_th.copy_(pe.theta, non_blocking=True)
         stream.synchronize()
@@ -459,7 +496,8 @@ def run_ours(args):
                        "p99": float(np.percentile(step_ms, 99))},
         "solve": {"iters": iters_run[-1], "kkt": float(last.kkt), "obj": float(last.obj),
                   "pinf": float(last.pinf), "dinf": float(last.dinf), "gap": float(last.gap),
-                  "r_plus": int(last.r_plus), "reached_tol": bool(last.kkt <= TOL)},
+                  "r_plus": int(last.r_plus), "reached_tol": bool(last.kkt <= W.tol()),
+                  "jacobi_sweeps_last": int(last.jacobi_sweeps)},
         "roofline": {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
                      "traffic": NCU_TRAFFIC_BYTES.get(args.workload),
@@ -593,7 +631,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
-                    help="short run for profiler captures (init + 4 iterations, no timing)")
+                    help="short run for profiler captures (init + 1 + --profile-iters "
+                         "iterations, no timing)")
+    ap.add_argument("--profile-iters", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

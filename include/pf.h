@@ -65,7 +65,11 @@ typedef enum {
 
 typedef enum { PF_PREC_FP64 = 0, PF_PREC_TF32 = 1, PF_PREC_BF16 = 2 } pf_precision;
 
-typedef enum { PF_PROBLEM_MAXCUT = 0, PF_PROBLEM_COMPLETION = 1 } pf_problem_kind;
+typedef enum {
+  PF_PROBLEM_MAXCUT = 0,       /* max-cut SDP by PFAM (Sec. 2.3)                          */
+  PF_PROBLEM_COMPLETION = 1,   /* PSD matrix completion by PFPG (Sec. 2.2)                */
+  PF_PROBLEM_NCE = 2           /* nearest correlation estimation, PFPG on the dual (Sec. 5.1) */
+} pf_problem_kind;
 
 /* Solver options (Sec. 2.2-2.3 and Sec. 4: degree d, q, eta, block width p). */
 typedef struct {
@@ -123,6 +127,12 @@ typedef struct {
  *  lam   MAXCUT only: n-vector lambda of the last DRS update.
  *  S     nnz FP64 workspace: COMPLETION P_Omega(X - M); structured MAXCUT
  *        the sparse part -tC - Diag(lam).
+ * NCE (min 1/2||G - X||^2 s.t. diag X = 1, X psd, solved on its dual
+ *  F(x) = 1/2||P_+(G + Diag x)||^2 - 1^T x by the filtered gradient method):
+ *  Z holds G (dense FP64, ldz) on entry to pf_problem_init and G + Diag(x)
+ *  afterwards; lam is the dual vector x (n); no CSR data; t is the gradient
+ *  step (t <= 0 selects 1); the report's kkt is ||grad F(x_k)|| /
+ *  ||grad F(x_0)|| and obj is F(x_k).
  * t: MAXCUT step; if t <= 0 on entry to pf_problem_init it is set to
  *    10 sqrt(n)/||C||_F.  COMPLETION step (t = 1 matches the Lipschitz
  *    constant of P_Omega).
@@ -155,6 +165,8 @@ typedef struct {
                                 breakdown; bit 2: non-finite Ritz value        */
   int32_t degree;            /* degree used by the step                      */
   int32_t precision;         /* precision used by the step                   */
+  int32_t jacobi_sweeps;     /* sweeps of the p x p eigensolve of the step   */
+  int32_t reserved;
 } pf_iter_info;
 
 typedef struct {

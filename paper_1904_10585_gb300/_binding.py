@@ -32,6 +32,7 @@ PF_PREC_TF32 = 1
 PF_PREC_BF16 = 2
 PF_PROBLEM_MAXCUT = 0
 PF_PROBLEM_COMPLETION = 1
+PF_PROBLEM_NCE = 2
 
 
 class pf_options(C.Structure):
@@ -67,7 +68,7 @@ class pf_iter_info(C.Structure):
                 ("pinf", C.c_double), ("dinf", C.c_double), ("gap", C.c_double),
                 ("theta_max", C.c_double), ("theta_min", C.c_double),
                 ("r_plus", C.c_int32), ("flags", C.c_int32), ("degree", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("jacobi_sweeps", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -229,7 +229,8 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
   if (pr->n < p || pr->n > ctx->n_max)
     return set_err(ctx, PF_ERR_INVALID_ARG, "problem n=%lld outside [p=%d, n_max=%lld]",
                    (long long)pr->n, p, (long long)ctx->n_max);
-  if (!pr->rowptr || !pr->colind || pr->nnz < 0 || pr->nnz > INT32_MAX)
+  if (pr->kind != PF_PROBLEM_NCE &&
+      (!pr->rowptr || !pr->colind || pr->nnz < 0 || pr->nnz > INT32_MAX))
     return set_err(ctx, PF_ERR_INVALID_ARG, "problem needs a CSR matrix (rowptr, colind, nnz)");
   if (!pr->U || pr->ldu < p || !pr->V || pr->ldv < p || !pr->theta)
     return set_err(ctx, PF_ERR_INVALID_ARG, "problem needs U, V (ld >= p) and theta");
@@ -249,6 +250,11 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
       return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut Z needs ldz >= n");
     if ((lp || pr->Z == nullptr) && !pr->S)
       return set_err(ctx, PF_ERR_INVALID_ARG, "structured max-cut needs the S workspace (nnz)");
+  } else if (pr->kind == PF_PROBLEM_NCE) {
+    if (!pr->Z || pr->ldz < pr->n || !pr->lam)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "NCE needs Z (G, ldz >= n) and lam (x)");
+    if (ctx->opt.precision != PF_PREC_FP64)
+      return set_err(ctx, PF_ERR_UNSUPPORTED, "NCE runs in an FP64 context");
   } else if (pr->kind == PF_PROBLEM_COMPLETION) {
     if (!pr->vals_f32 || !pr->S)
       return set_err(ctx, PF_ERR_INVALID_ARG, "completion needs vals_f32 (M on Omega) and S");
@@ -268,6 +274,20 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
   const Workspace &ws = ctx->ws;
   const int degree = ctx->cur_degree;
   const bool lp = ctx->cur_lp;
+  if (pr->kind == PF_PROBLEM_NCE) {
+    PF_CUDA(launch_nce_interval(s, ws, pr->Z, pr->ldz, n, pr->theta, p));
+    Op op = {};
+    op.kind = PF_OP_DENSE;
+    op.n = n;
+    op.A = pr->Z;
+    op.lda = pr->ldz;
+    PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
+    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
+    PF_CUDA(launch_nce_update(s, ws, pr->Z, pr->ldz, n, p, pr->V, pr->ldv, pr->theta, pr->lam,
+                              pr->t > 0.0 ? pr->t : 1.0));
+    return PF_OK;
+  }
   // a low-precision context keeps no FP64 dense Z up to date, so it always
   // uses the structured operator (also after the ladder has dropped to FP64)
   const bool structured = ctx->opt.precision != PF_PREC_FP64 || pr->Z == nullptr;
@@ -363,6 +383,8 @@ void params_to_info(const Params &h, pf_iter_info *info, const pf_ctx *ctx = nul
   info->theta_min = h.theta_min;
   info->r_plus = h.r_plus;
   info->flags = h.flags;
+  info->jacobi_sweeps = h.sweeps;
+  info->reserved = 0;
   info->degree = ctx ? ctx->cur_degree : h.degree;
   info->precision = ctx ? (ctx->cur_lp ? ctx->opt.precision : (int)PF_PREC_FP64) : h.precision;
 }
@@ -431,7 +453,8 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   size_t off[16];
   size_t tot = 0;
   const size_t sizes[] = {np, np, np, np, part, (size_t)kMaxGramBlocks * sq,
-                          (size_t)kRedSlots * kMaxRedBlocks * kRedWidth, sq, sq, sq, kMaxP, kMaxP};
+                          (size_t)kRedSlots * kMaxRedBlocks * kRedWidth, sq, sq, sq, kMaxP, kMaxP,
+                          (size_t)n_max, (size_t)n_max};
   const int nsz = sizeof(sizes) / sizeof(sizes[0]);
   for (int i = 0; i < nsz; ++i) {
     off[i] = tot;
@@ -481,6 +504,8 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   ws.T = (double *)(b + off[9]);
   ws.thprev = (double *)(b + off[10]);
   ws.resid = (double *)(b + off[11]);
+  ws.gdiag = (double *)(b + off[12]);
+  ws.rsum = (double *)(b + off[13]);
   ws.prm = (Params *)(b + prm_off);
   ws.info = (pf_iter_info *)(b + info_off);
   ws.ldxt = ldxt;
@@ -575,6 +600,12 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
                              ctx->opt.precision));
   PF_CUDA(launch_fill(s, pr->V, n, p, pr->ldv, 0.0));
   PF_CUDA(launch_fill(s, pr->theta, 1, p, p, 0.0));
+  if (pr->kind == PF_PROBLEM_NCE) {
+    if (!(pr->t > 0.0)) pr->t = 1.0;
+    PF_CUDA(launch_params_init(s, ws.prm, ctx->opt.eta, pr->t, 0.0, ctx->opt.degree,
+                               ctx->opt.precision));
+    PF_CUDA(launch_nce_init(s, ws, pr->Z, pr->ldz, n, pr->lam));
+  }
   if (pr->kind == PF_PROBLEM_MAXCUT) {
     PF_CUDA(launch_cnorm(s, ws, pr->vals_f64, pr->nnz));
     Params h;

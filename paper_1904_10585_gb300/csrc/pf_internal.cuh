@@ -32,6 +32,7 @@ struct Params {
   double t, mu;           // step size, completion weight
   double Cnorm;           // ||C||_F (max-cut)
   double lp_scale;        // s of the low-precision shadow A_lp = A / s
+  double g0;              // NCE: ||grad F(x_0)||
   double obj, kkt, pinf, dinf, gap;
   double theta_max, theta_min;
   int have_prev;          // a previous Rayleigh-Ritz step exists
@@ -39,7 +40,7 @@ struct Params {
   int r_plus;
   int degree;
   int precision;
-  int pad;
+  int sweeps;             // sweeps of the last p x p eigensolve
 };
 
 // Internal iteration-matrix description.
@@ -73,6 +74,7 @@ struct Workspace {
   float *U32;             // fp32 copy of the start block
   void *Xt[2];            // transposed low-precision operands, p x ldxt
   float *Wf, *Vf;         // fp32 factors of the shadow expansion, n_max x 64
+  double *gdiag, *rsum;   // NCE: diag(G) and off-diagonal |G| row sums, n_max each
   int64_t ldxt;
 };
 
@@ -108,7 +110,6 @@ cudaError_t launch_chol_inv(cudaStream_t s, const Workspace &ws, int nparts, int
 cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double *Y, int64_t ldy,
                                double *Q, int64_t ldq, int n, int p, const double *R, int upper,
                                int cond_flag);
-cudaError_t launch_jacobi(cudaStream_t s, const Workspace &ws, int nparts, int p, double *theta);
 cudaError_t launch_jacobi_cluster(cudaStream_t s, const Workspace &ws, const double *H, int p,
                                   double *theta);
 cudaError_t launch_rotate_resid(cudaStream_t s, const Workspace &ws, const double *Q, int64_t ldq,
@@ -173,6 +174,13 @@ cudaError_t launch_maxcut_lp_shadow(cudaStream_t s, const Workspace &ws, bool f3
                                     int64_t ldz);
 cudaError_t launch_copy_block(cudaStream_t s, const Workspace &ws, const double *src, int64_t lds,
                               int n, int p, double *dst, int64_t ldd);
+cudaError_t launch_nce_init(cudaStream_t s, const Workspace &ws, double *Z, int64_t ldz, int n,
+                            double *x);
+cudaError_t launch_nce_interval(cudaStream_t s, const Workspace &ws, const double *Z, int64_t ldz,
+                                int n, const double *theta, int p);
+cudaError_t launch_nce_update(cudaStream_t s, const Workspace &ws, double *Z, int64_t ldz, int n,
+                              int p, const double *V, int64_t ldv, const double *theta, double *x,
+                              double tau);
 cudaError_t launch_fill(cudaStream_t s, double *x, int64_t rows, int64_t cols, int64_t ld, double v);
 cudaError_t launch_export_info(cudaStream_t s, const Workspace &ws, int degree, int precision);
 cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,

@@ -60,6 +60,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
   }
   cluster.sync();  // every CTA has started before any remote store
   int cur = 0;
+  int sweeps_done = 0;
   for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
     const double *H = Hb[cur];
     double off = 0.0, tot = 0.0;
@@ -134,6 +135,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
       cluster.sync();
       cur ^= 1;
     }
+    sweeps_done = sweep + 1;
   }
   // eigenvalues, descending (ties by index); every CTA computes the ranks
   const double *H = Hb[cur];
@@ -152,6 +154,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
     for (int r = row0; r < row1; ++r) Yeig[r * p + rk] = Vloc[(r - row0) * JLD + j];
   }
   if (bad && rank == 0) atomicOr(&prm->flags, 4);
+  if (rank == 0 && tid == 0) prm->sweeps = sweeps_done;
   cluster.sync();  // no CTA leaves while its shared memory may still be written
 }
 

@@ -6,8 +6,8 @@
 //    Yanagisawa (SIAM J. Sci. Comput., 2020) when a pivot collapses;
 //  * the right multiplication Q = Y R^{-1} (orth of Eq. (subspace-update),
 //    realised as CholQR2 = QR with positive diagonal R in exact arithmetic);
-//  * one-block cyclic Jacobi on the p x p projected matrix H = Q^T A Q and the
-//    Ritz rotation V = Q Y with residuals ||A v_i - theta_i v_i|| (Eq. (RR)).
+//  * the Ritz rotation V = Q Y with residuals ||A v_i - theta_i v_i|| (Eq. (RR));
+//    the p x p eigensolve itself is the cluster Jacobi of pf_jacobi.cu.
 #include "pf_internal.cuh"
 
 namespace pf {
@@ -275,118 +275,6 @@ __global__ void k_lowrank_coef(const double *__restrict__ gpart, int nparts, con
   }
 }
 
-// One-block cyclic Jacobi (parallel round-robin ordering) on the symmetric
-// part of H = sum of Gram partials.  Writes eigenvalues descending into
-// theta and the matching eigenvectors as the columns of Yeig (p x p).
-__global__ void __launch_bounds__(NT) k_jacobi(const double *__restrict__ gpart, int nparts, int p,
-                                               double *__restrict__ Yeig,
-                                               double *__restrict__ theta, Params *prm) {
-  extern __shared__ double dyn[];
-  double(*H)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn);
-  double(*V)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn + kMaxP * (kMaxP + 1));
-  __shared__ double cs[kMaxP / 2], sn[kMaxP / 2];
-  __shared__ int pk[kMaxP / 2], pl[kMaxP / 2];
-  __shared__ double redsh[32];
-  __shared__ double lam_s[kMaxP];
-  const int tid = threadIdx.x;
-  // H = sym(sum of partials); V = I
-  for (int idx = tid; idx < p * p; idx += NT) {
-    const int a = idx / p, b = idx % p;
-    double s = 0.0, s2 = 0.0;
-    for (int q = 0; q < nparts; ++q) {
-      s += gpart[(int64_t)q * p * p + a * p + b];
-      s2 += gpart[(int64_t)q * p * p + b * p + a];
-    }
-    H[a][b] = 0.5 * (s + s2);
-    V[a][b] = (a == b) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  const int m = p + (p & 1);  // even number of players; index p (if odd) is a dummy
-  const int half = m / 2;
-  for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int idx = tid; idx < p * p; idx += NT) {
-      const int a = idx / p, b = idx % p;
-      const double h = H[a][b];
-      tot = fma(h, h, tot);
-      if (a != b) off = fma(h, h, off);
-    }
-    off = block_reduce(off, redsh, 0);
-    tot = block_reduce(tot, redsh, 0);
-    if (!(off > 1e-30 * tot)) break;  // off(H) <= 1e-15 ||H||_F (also stops on NaN)
-    for (int round = 0; round < m - 1; ++round) {
-      if (tid < half) {
-        const int i = tid;
-        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (m - 1)); };
-        int k = player(i), l = player(m - 1 - i);
-        if (k > l) { const int t = k; k = l; l = t; }
-        double c = 1.0, s = 0.0;
-        if (l < p) {
-          const double hkl = H[k][l];
-          // rotations below the relative threshold change nothing at FP64
-          // precision and are skipped (cost then scales with the active pairs)
-          if (fabs(hkl) > 1e-17 * sqrt(fabs(H[k][k]) * fabs(H[l][l])) && hkl != 0.0) {
-            const double tau = (H[l][l] - H[k][k]) / (2.0 * hkl);
-            double t;
-            if (fabs(tau) > 1e150) t = 0.5 / tau;
-            else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        cs[i] = c; sn[i] = s; pk[i] = k; pl[i] = l;
-      }
-      __syncthreads();
-      // rows: H <- J^T H
-      for (int idx = tid; idx < half * p; idx += NT) {
-        const int i = idx / p, col = idx % p;
-        const int k = pk[i], l = pl[i];
-        if (l >= p || sn[i] == 0.0) continue;
-        const double c = cs[i], s = sn[i];
-        const double hk = H[k][col], hl = H[l][col];
-        H[k][col] = c * hk - s * hl;
-        H[l][col] = s * hk + c * hl;
-      }
-      __syncthreads();
-      // columns: H <- H J, V <- V J
-      for (int idx = tid; idx < half * p; idx += NT) {
-        const int i = idx / p, row = idx % p;
-        const int k = pk[i], l = pl[i];
-        if (l >= p || sn[i] == 0.0) continue;
-        const double c = cs[i], s = sn[i];
-        const double hk = H[row][k], hl = H[row][l];
-        H[row][k] = c * hk - s * hl;
-        H[row][l] = s * hk + c * hl;
-        const double vk = V[row][k], vl = V[row][l];
-        V[row][k] = c * vk - s * vl;
-        V[row][l] = s * vk + c * vl;
-      }
-      __syncthreads();
-      if (tid < half) {
-        const int k = pk[tid], l = pl[tid];
-        if (l < p && sn[tid] != 0.0) { H[k][l] = 0.0; H[l][k] = 0.0; }
-      }
-      __syncthreads();
-    }
-  }
-  // sort descending (ties by index) and write out
-  if (tid < p) lam_s[tid] = H[tid][tid];
-  __syncthreads();
-  bool bad = false;
-  for (int j = tid; j < p; j += NT) {
-    const double lj = lam_s[j];
-    if (!isfinite(lj)) bad = true;
-    int rank = 0;
-    for (int i = 0; i < p; ++i) {
-      const double li = lam_s[i];
-      if (li > lj || (li == lj && i < j)) ++rank;
-    }
-    theta[rank] = lj;
-    for (int a = 0; a < p; ++a) Yeig[a * p + rank] = V[a][j];
-  }
-  if (bad) atomicOr(&prm->flags, 4);
-}
-
 constexpr size_t kSqBytes = 2 * kMaxP * (kMaxP + 1) * sizeof(double);
 constexpr size_t apply_bytes(int PT) { return (size_t)(PT + RC) * (PT + 1) * sizeof(double); }
 constexpr size_t rotate_bytes(int PT) {
@@ -401,7 +289,6 @@ cudaError_t configure_skinny() {
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
   if (e != cudaSuccess) return e;
   PF_SET(k_chol_inv, kSqBytes)
-  PF_SET(k_jacobi, kSqBytes)
   PF_SET(k_apply_right<16>, apply_bytes(16))
   PF_SET(k_apply_right<32>, apply_bytes(32))
   PF_SET(k_apply_right<64>, apply_bytes(64))
@@ -488,12 +375,6 @@ cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double
       k_apply_right<64><<<nb, NT, apply_bytes(64), s>>>(Y, ldy, Q, ldq, n, p, R, upper, rpb, ws.prm, cond_flag);
       PF_LAUNCHED();
     }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_jacobi(cudaStream_t s, const Workspace &ws, int nparts, int p, double *theta) {
-  k_jacobi<<<1, NT, kSqBytes, s>>>(ws.gpart, nparts, p, ws.Yeig, theta, ws.prm);
-  PF_LAUNCHED();
   return cudaGetLastError();
 }
 

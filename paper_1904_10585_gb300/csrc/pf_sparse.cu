@@ -703,6 +703,8 @@ __global__ void k_export_info(const Params *__restrict__ prm, pf_iter_info *__re
   r.flags = prm->flags;
   r.degree = degree;
   r.precision = precision;
+  r.jacobi_sweeps = prm->sweeps;
+  r.reserved = 0;
   *info = r;
 }
 }  // namespace
@@ -1119,6 +1121,167 @@ cudaError_t launch_maxcut_lp_shadow_fp32(cudaStream_t s, const Workspace &ws, bo
   else if (p <= 32) { PF_EXP(32) }
   else { PF_EXP(64) }
 #undef PF_EXP
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Nearest correlation estimation (Sec. 5.1): gradient method on the dual
+// F(x) = 1/2 ||P_+(G + Diag x)||^2 - 1^T x, grad F = diag(P_+(G + Diag x)) - 1,
+// with P_+ taken from the positive Ritz pairs of the filtered subspace.  The
+// dense FP64 iteration matrix B = G + Diag(x) lives in the problem's Z; only
+// its diagonal changes between iterations.
+// ===========================================================================
+namespace {
+
+// diag(G), off-diagonal |G| row sums, x^0 = 1 - diag(G), diag(B^0) = 1.
+__global__ void __launch_bounds__(NT) k_nce_init(double *Z, int64_t ldz, int n,
+                                                 double *__restrict__ gdiag,
+                                                 double *__restrict__ rsum,
+                                                 double *__restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * WPB;
+  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
+    const double *zr = Z + (int64_t)row * ldz;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32)
+      if (j != row) s += fabs(zr[j]);
+    s = warp_sum(s);
+    if (lane == 0) {
+      const double g = zr[row];
+      gdiag[row] = g;
+      rsum[row] = s;
+      x[row] = 1.0 - g;
+      Z[(int64_t)row * ldz + row] = 1.0;
+    }
+  }
+}
+
+// Gershgorin bounds of B = G + Diag(x): B_ii -/+ rowsum_i (into the interval slot).
+__global__ void __launch_bounds__(NT) k_nce_rows(const double *Z, int64_t ldz, int n,
+                                                 const double *__restrict__ rsum,
+                                                 double *__restrict__ red) {
+  __shared__ double sh[32];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+    const double d = Z[(int64_t)i * ldz + i];
+    lo = fmin(lo, d - rsum[i]);
+    hi = fmax(hi, d + rsum[i]);
+  }
+  lo = block_reduce(lo, sh, 1);
+  hi = block_reduce(hi, sh, 2);
+  if (threadIdx.x == 0) {
+    red[blockIdx.x * kRedWidth + 0] = lo;
+    red[blockIdx.x * kRedWidth + 1] = hi;
+  }
+}
+
+// g = diag(X~) - 1 with X~ = V diag(max(theta,0)) V^T; x <- x - tau g;
+// diag(B) <- diag(G) + x.  Partial sums: sum g^2, sum x (before the step).
+__global__ void __launch_bounds__(NT) k_nce_update(double *Z, int64_t ldz, int n, int p,
+                                                   const double *__restrict__ V, int64_t ldv,
+                                                   const double *__restrict__ theta,
+                                                   const double *__restrict__ gdiag,
+                                                   double *__restrict__ x, double tau,
+                                                   double *__restrict__ red) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * WPB;
+  double sg = 0.0, sx = 0.0;
+  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
+    double dx = 0.0;
+    for (int l = lane; l < p; l += 32) {
+      const double th = theta[l];
+      if (th > 0.0) {
+        const double v = V[(int64_t)row * ldv + l];
+        dx = fma(th * v, v, dx);
+      }
+    }
+    dx = warp_sum(dx);
+    if (lane == 0) {
+      const double g = dx - 1.0;
+      const double xo = x[row];
+      const double xn = xo - tau * g;
+      x[row] = xn;
+      Z[(int64_t)row * ldz + row] = gdiag[row] + xn;
+      sg = fma(g, g, sg);
+      sx += xo;
+    }
+  }
+  sg = block_reduce(sg, sh, 0);
+  sx = block_reduce(sx, sh, 0);
+  if (threadIdx.x == 0) {
+    red[blockIdx.x * kRedWidth + 0] = sg;
+    red[blockIdx.x * kRedWidth + 1] = sx;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_nce_report(const double *__restrict__ red, int nb,
+                                                   const double *__restrict__ theta, int p,
+                                                   Params *prm) {
+  __shared__ double sh[32];
+  double sg = 0.0, sx = 0.0;
+  for (int q = threadIdx.x; q < nb; q += NT) {
+    sg += red[q * kRedWidth + 0];
+    sx += red[q * kRedWidth + 1];
+  }
+  sg = block_reduce(sg, sh, 0);
+  sx = block_reduce(sx, sh, 0);
+  if (threadIdx.x != 0) return;
+  double f = 0.0;
+  int rp = 0;
+  for (int l = 0; l < p; ++l) {
+    const double th = theta[l];
+    if (th > 0.0) {
+      f = fma(th, th, f);
+      ++rp;
+    }
+  }
+  const double gnorm = sqrt(sg);
+  if (!(prm->g0 > 0.0)) prm->g0 = gnorm;
+  prm->obj = 0.5 * f - sx;
+  prm->kkt = prm->g0 > 0.0 ? gnorm / prm->g0 : 0.0;
+  prm->pinf = gnorm;  // ||grad F(x_k)|| (absolute), reported in the pinf slot
+  prm->dinf = 0.0;
+  prm->gap = 0.0;
+  prm->r_plus = rp;
+  prm->theta_max = theta[0];
+  prm->theta_min = theta[p - 1];
+  prm->have_prev = 1;
+}
+
+}  // namespace
+
+cudaError_t launch_nce_init(cudaStream_t s, const Workspace &ws, double *Z, int64_t ldz, int n,
+                            double *x) {
+  k_nce_init<<<red_blocks(n, ws.num_sms), NT, 0, s>>>(Z, ldz, n, ws.gdiag, ws.rsum, x);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nce_interval(cudaStream_t s, const Workspace &ws, const double *Z, int64_t ldz,
+                                int n, const double *theta, int p) {
+  int nb = (n + NT - 1) / NT;
+  if (nb > kMaxRedBlocks) nb = kMaxRedBlocks;
+  k_nce_rows<<<nb, NT, 0, s>>>(Z, ldz, n, ws.rsum, slot(ws, SLOT_INTERVAL));
+  PF_LAUNCHED();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_interval_final<<<1, NT, 0, s>>>(slot(ws, SLOT_INTERVAL), nb, theta, p, ws.prm);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nce_update(cudaStream_t s, const Workspace &ws, double *Z, int64_t ldz, int n,
+                              int p, const double *V, int64_t ldv, const double *theta, double *x,
+                              double tau) {
+  const int nb = red_blocks(n, ws.num_sms);
+  k_nce_update<<<nb, NT, 0, s>>>(Z, ldz, n, p, V, ldv, theta, ws.gdiag, x, tau,
+                                 slot(ws, SLOT_LAMBDA));
+  PF_LAUNCHED();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_nce_report<<<1, NT, 0, s>>>(slot(ws, SLOT_LAMBDA), nb, theta, p, ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
 }

@@ -132,6 +132,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Instruction descriptor: fp32 accumulator, A/B K-major, M = 128, N = NB.
 template <bool TF32, int NB>
 __host__ __device__ constexpr uint32_t make_idesc() {
@@ -304,41 +321,61 @@ __global__ void k_f32_to_f64(const float *__restrict__ src, int64_t total, doubl
 // Low-precision shadow of the max-cut iteration matrix (Eq. (PFAM1)):
 //     Z_lp[i][j] = ( sum_l W[i][l] V[j][l] - t C_ij - [i == j] lam_i ) / s
 // with W = V diag(max(theta, 0)) (fp32, K-padded to KP columns, zero beyond
-// r+).  One CTA per 128 x 128 output tile: TMA loads the 128 x KP tiles of W
-// and V (tf32 operands), tcgen05.mma (kind::tf32, M = N = 128) accumulates in
-// 128 TMEM columns, and the epilogue adds the sparse and diagonal parts,
-// scales and stores bf16 (or fp32) rows.
+// r+).  The write of Z_lp (n^2 elements) bounds the kernel, so each CTA owns
+// one 128-row block and walks a range of 128-column tiles:
+//   warp 0 (one lane): TMA of the W tile once, then V tiles through a
+//                      2-stage ring;
+//   warp 1 (one lane): tcgen05.mma kind::tf32 (M = N = 128, K = KP) into one
+//                      of two 128-column TMEM accumulators;
+//   warps 2-5        : epilogue of the previous tile (TMEM lanes = rows),
+//                      sparse and diagonal parts, scale, bf16/fp32 stores;
+//                      they release the accumulator through an mbarrier.
 // ---------------------------------------------------------------------------
 constexpr int EX_TILE = 128;
+constexpr int EX_THREADS = 192;
+constexpr int EX_VST = 2;
 
 template <int KP, bool F32OUT>
-__global__ void __launch_bounds__(TC_THREADS)
+__global__ void __launch_bounds__(EX_THREADS)
     k_tc_expand(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmV,
-                int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
-                const double *__restrict__ vals, const double *__restrict__ lam, void *Zlp,
-                int64_t ldz, Params *prm) {
-  constexpr int KB = KP / 32;                 // 128-byte k-blocks of tf32
+                int n, int tiles_per_cta, const int32_t *__restrict__ rowptr,
+                const int32_t *__restrict__ colind, const double *__restrict__ vals,
+                const double *__restrict__ lam, void *Zlp, int64_t ldz, Params *prm) {
+  constexpr int KB = KP / 32;                    // 128-byte k-blocks of tf32
   constexpr int TILE_BYTES = EX_TILE * TC_ROWB;  // 16 KB per operand per k-block
+  constexpr int OP_BYTES = KB * TILE_BYTES;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar;
-  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t w_full;
+  __shared__ __align__(8) uint64_t v_full[EX_VST], v_empty[EX_VST];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const uint32_t sW = base, sV = base + KB * TILE_BYTES;
-  const int i0 = blockIdx.y * EX_TILE, j0 = blockIdx.x * EX_TILE;
+  const uint32_t sW = base, sV = base + OP_BYTES;
+  const int T = (n + EX_TILE - 1) / EX_TILE;
+  const int i0 = blockIdx.y * EX_TILE;
+  const int t_begin = blockIdx.x * tiles_per_cta;
+  const int t_end = min(T, t_begin + tiles_per_cta);
+  const int cnt = max(0, t_end - t_begin);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    mbar_init(smem_u32(&full_bar), 1);
-    mbar_init(smem_u32(&acc_bar), 1);
+    mbar_init(smem_u32(&w_full), 1);
+    for (int s = 0; s < EX_VST; ++s) {
+      mbar_init(smem_u32(&v_full[s]), 1);
+      mbar_init(smem_u32(&v_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(128u)
+                 "r"(256u)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -347,103 +384,143 @@ __global__ void __launch_bounds__(TC_THREADS)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    const uint32_t fb = smem_u32(&full_bar);
-    mbar_expect_tx(fb, 2 * KB * TILE_BYTES);
+  if (warp == 0) {
+    if (lane == 0 && cnt > 0) {
+      const uint32_t wb = smem_u32(&w_full);
+      mbar_expect_tx(wb, OP_BYTES);
 #pragma unroll
-    for (int kb = 0; kb < KB; ++kb) {
-      tma_load_2d(sW + kb * TILE_BYTES, &tmW, fb, kb * 32, i0);
-      tma_load_2d(sV + kb * TILE_BYTES, &tmV, fb, kb * 32, j0);
-    }
-  } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(EX_TILE >> 3) << 17) |
-                               ((uint32_t)(EX_TILE >> 4) << 24);
-    if (mbar_wait(smem_u32(&full_bar), 0, &abort_flag)) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kb = 0; kb < KB; ++kb) tma_load_2d(sW + kb * TILE_BYTES, &tmW, wb, kb * 32, i0);
+      for (int t = 0; t < cnt; ++t) {
+        const int s = t % EX_VST;
+        if (t >= EX_VST && !mbar_wait(smem_u32(&v_empty[s]), ((t / EX_VST) - 1) & 1, &abort_flag))
+          break;
+        const uint32_t vb = smem_u32(&v_full[s]);
+        mbar_expect_tx(vb, OP_BYTES);
+        const int j0 = (t_begin + t) * EX_TILE;
 #pragma unroll
-      for (int kb = 0; kb < KB; ++kb) {
-        const uint64_t ad = sw128_desc(sW + kb * TILE_BYTES);
-        const uint64_t bd = sw128_desc(sV + kb * TILE_BYTES);
-#pragma unroll
-        for (int k = 0; k < TC_ROWB / 32; ++k)
-          mma_issue<true>(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+        for (int kb = 0; kb < KB; ++kb)
+          tma_load_2d(sV + s * OP_BYTES + kb * TILE_BYTES, &tmV, vb, kb * 32, j0);
       }
-      mma_commit(smem_u32(&acc_bar));
     }
-  }
-  __syncwarp();
-  const bool have_acc = mbar_wait(smem_u32(&acc_bar), 0, &abort_flag);
-  __syncwarp();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (have_acc) {
+  } else if (warp == 1) {
+    if (lane == 0 && cnt > 0) {
+      constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                                 ((uint32_t)(EX_TILE >> 3) << 17) | ((uint32_t)(EX_TILE >> 4) << 24);
+      bool ok = mbar_wait(smem_u32(&w_full), 0, &abort_flag);
+      for (int t = 0; ok && t < cnt; ++t) {
+        const int s = t % EX_VST, b = t & 1;
+        if (!mbar_wait(smem_u32(&v_full[s]), (t / EX_VST) & 1, &abort_flag)) break;
+        if (t >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), ((t >> 1) - 1) & 1, &abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * EX_TILE);
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) {
+          const uint64_t ad = sw128_desc(sW + kb * TILE_BYTES);
+          const uint64_t bd = sw128_desc(sV + s * OP_BYTES + kb * TILE_BYTES);
+#pragma unroll
+          for (int k = 0; k < TC_ROWB / 32; ++k)
+            mma_issue<true>(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+        }
+        mma_commit(smem_u32(&v_empty[s]));
+        mma_commit(smem_u32(&acc_full[b]));
+      }
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter (warp % 4) = rows of the block
+    const int quarter = warp & 3;
+    const int row = i0 + quarter * 32 + lane;
+    const bool in = row < n;
     const float t = (float)prm->t;
     const float inv_s = (float)(1.0 / prm->lp_scale);
-    const int row = i0 + warp * 32 + lane;
-    const bool in = row < n;
-    // this row's sparse entries with columns in [j0, j0 + 128)
+    const float lrow = in ? (float)lam[row] : 0.f;
     int e = 0, e_end = 0;
-    if (in) {
+    if (in && cnt > 0) {
       int lo = rowptr[row], hi = rowptr[row + 1];
       e_end = hi;
+      const int j_first = t_begin * EX_TILE;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (colind[mid] < j0) lo = mid + 1;
+        if (colind[mid] < j_first) lo = mid + 1;
         else hi = mid;
       }
       e = lo;
     }
-    const float lrow = in ? (float)lam[row] : 0.f;
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int tt = 0; tt < cnt; ++tt) {
+      const int b = tt & 1;
+      const bool have = mbar_wait(smem_u32(&acc_full[b]), (tt >> 1) & 1, &abort_flag);
+      __syncwarp();
+      if (!have) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int j0 = (t_begin + tt) * EX_TILE;
+      const uint32_t taddr = tmem + (uint32_t)(b * EX_TILE) + ((uint32_t)(quarter * 32) << 16);
+      const float ts = t * inv_s, ls = lrow * inv_s;
 #pragma unroll 1
-    for (int c0 = 0; c0 < EX_TILE; c0 += 16) {
-      float v[16];
-      tmem_ld16(taddr + c0, v);
-      if (!in || j0 + c0 >= n) continue;
-      // sparse part on columns j0 + c0 .. j0 + c0 + 15
-      while (e < e_end) {
-        const int col = colind[e];
-        if (col >= j0 + c0 + 16) break;
-        const int q = col - (j0 + c0);
-        const float tc = t * (float)vals[e];
+      for (int c0 = 0; c0 < EX_TILE; c0 += 32) {
+        float v[32];
+        tmem_ld32(taddr + c0, v);
+        if (!in || j0 + c0 >= n) continue;
+        // sparse part (a few entries per row and tile) and the diagonal
+        while (e < e_end) {
+          const int col = colind[e];
+          if (col >= j0 + c0 + 32) break;
+          const int q = col - (j0 + c0);
+          const float tc = ts * (float)vals[e];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] -= (k == q) ? tc : 0.f;
-        ++e;
-      }
-      const int dj = row - (j0 + c0);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] -= (k == dj) ? lrow : 0.f;
-      const int64_t off = (int64_t)row * ldz + j0 + c0;
-      const int valid = min(16, n - (j0 + c0));
-      if (F32OUT) {
-        float *zp = reinterpret_cast<float *>(Zlp) + off;
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (q < valid) zp[q] = v[q] * inv_s;
-      } else {
-        __nv_bfloat16 *zp = reinterpret_cast<__nv_bfloat16 *>(Zlp) + off;
-        if (valid == 16 && ((off & 7) == 0)) {
-          uint32_t w[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q] * inv_s, v[2 * q + 1] * inv_s);
-            w[q] = *reinterpret_cast<const uint32_t *>(&h2);
-          }
-          uint4 *dst = reinterpret_cast<uint4 *>(zp);
-          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (q < valid) zp[q] = __float2bfloat16_rn(v[q] * inv_s);
+          for (int k = 0; k < 32; ++k) v[k] -= (k == q) ? tc : 0.f;
+          ++e;
         }
+        const int dj = row - (j0 + c0);
+        if (dj >= 0 && dj < 32) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) v[k] -= (k == dj) ? ls : 0.f;
+        }
+        const int64_t off = (int64_t)row * ldz + j0 + c0;
+        const int valid = min(32, n - (j0 + c0));
+        if (F32OUT) {
+          float *zp = reinterpret_cast<float *>(Zlp) + off;
+          if (valid == 32 && ((off & 3) == 0)) {
+            float4 *dst = reinterpret_cast<float4 *>(zp);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (q < valid) zp[q] = v[q];
+          }
+        } else {
+          __nv_bfloat16 *zp = reinterpret_cast<__nv_bfloat16 *>(Zlp) + off;
+          if (valid == 32 && ((off & 7) == 0)) {
+            uint32_t w[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+              w[q] = *reinterpret_cast<const uint32_t *>(&h2);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(zp);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (q < valid) zp[q] = __float2bfloat16_rn(v[q]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b]))
+                     : "memory");
       }
     }
   }
-  if (threadIdx.x == 0 && (abort_flag || !have_acc)) atomicOr(&prm->flags, 8);
+  __syncwarp();
+  if (threadIdx.x == 0 && abort_flag) atomicOr(&prm->flags, 8);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
                  : "memory");
   }
 }
@@ -451,7 +528,9 @@ __global__ void __launch_bounds__(TC_THREADS)
 // W = V diag(max(theta,0)) and V in fp32, K-padded to KP (zero beyond r+).
 __global__ void k_expand_prep(const double *__restrict__ V, int64_t ldv,
                               const double *__restrict__ theta, int n, int p, int KP,
-                              float *__restrict__ Wf, float *__restrict__ Vf) {
+                              float *__restrict__ Wf, float *__restrict__ Vf,
+                              const Params *__restrict__ prm) {
+  const double inv_s = 1.0 / prm->lp_scale;  // the shadow's scale folded into W
   const int64_t total = (int64_t)n * KP;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -462,7 +541,7 @@ __global__ void k_expand_prep(const double *__restrict__ V, int64_t ldv,
       const double th = theta[l];
       if (th > 0.0) {
         const double x = V[i * ldv + l];
-        w = (float)(x * th);
+        w = (float)(x * th * inv_s);
         v = (float)x;
       }
     }
@@ -471,7 +550,9 @@ __global__ void k_expand_prep(const double *__restrict__ V, int64_t ldv,
   }
 }
 
-size_t expand_smem_bytes(int KP) { return 1024 + (size_t)2 * (KP / 32) * EX_TILE * TC_ROWB; }
+size_t expand_smem_bytes(int KP) {
+  return 1024 + (size_t)(1 + EX_VST) * (KP / 32) * EX_TILE * TC_ROWB;
+}
 
 size_t tc_smem_bytes(int NB) { return 1024 + (size_t)TC_STAGES * (TC_A_BYTES + NB * TC_ROWB); }
 
@@ -603,18 +684,25 @@ cudaError_t launch_tc_expand(cudaStream_t s, const Workspace &ws, bool f32out, c
   const int KP = p <= 32 ? 32 : 64;
   int64_t blocks = ((int64_t)n * KP + 255) / 256;
   if (blocks > 4 * ws.num_sms) blocks = 4 * ws.num_sms;
-  k_expand_prep<<<(int)blocks, 256, 0, s>>>(V, ldv, theta, n, p, KP, ws.Wf, ws.Vf);
+  k_expand_prep<<<(int)blocks, 256, 0, s>>>(V, ldv, theta, n, p, KP, ws.Wf, ws.Vf, ws.prm);
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap mw, mv;
   if ((e = encode_map(&mw, ws.Wf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
   if ((e = encode_map(&mv, ws.Vf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
-  const dim3 grid((n + EX_TILE - 1) / EX_TILE, (n + EX_TILE - 1) / EX_TILE);
+  // one CTA per (row block, range of column tiles): about two CTAs per SM
+  const int T = (n + EX_TILE - 1) / EX_TILE;
+  int splits = (2 * ws.num_sms) / T;
+  if (splits < 1) splits = 1;
+  if (splits > T) splits = T;
+  const int tiles_per = (T + splits - 1) / splits;
+  splits = (T + tiles_per - 1) / tiles_per;
+  const dim3 grid(splits, T);
   const size_t smem = expand_smem_bytes(KP);
-#define PF_EX_LAUNCH(KPV, F32)                                                                    \
-  k_tc_expand<KPV, F32><<<grid, TC_THREADS, smem, s>>>(mw, mv, n, rowptr, colind, vals, lam, Zlp, \
-                                                       ldz, ws.prm)
+#define PF_EX_LAUNCH(KPV, F32)                                                                  \
+  k_tc_expand<KPV, F32><<<grid, EX_THREADS, smem, s>>>(mw, mv, n, tiles_per, rowptr, colind,   \
+                                                       vals, lam, Zlp, ldz, ws.prm)
   if (KP == 32) {
     if (f32out) PF_EX_LAUNCH(32, true);
     else PF_EX_LAUNCH(32, false);

@@ -130,9 +130,17 @@ class Problem:
 
     def make_struct(self) -> B.pf_problem:
         s = B.pf_problem(kind=self.kind, n=self.n, rowptr=_ptr(self.rowptr),
-                         colind=_ptr(self.colind), nnz=self.colind.numel(), t=self.t, mu=self.mu,
+                         colind=_ptr(self.colind),
+                         nnz=self.colind.numel() if self.colind is not None else 0,
+                         t=self.t, mu=self.mu,
                          U=_ptr(self.U), ldu=_ld(self.U), V=_ptr(self.V), ldv=_ld(self.V),
                          theta=_ptr(self.theta))
+        if self.kind == B.PF_PROBLEM_NCE:
+            s.Z = _ptr(self.Z)
+            s.ldz = _ld(self.Z)
+            s.lam = _ptr(self.lam)
+            self.struct = s
+            return s
         if self.kind == B.PF_PROBLEM_MAXCUT:
             s.vals_f64 = _ptr(self.vals)
             if self.Z is not None:
@@ -176,6 +184,20 @@ def maxcut_problem(rowptr, colind, vals, U0: torch.Tensor, t: float = 0.0, dense
                  lam=torch.empty(n, dtype=torch.float64, device=dev),
                  S=(torch.empty(colind.numel(), dtype=torch.float64, device=dev)
                     if (not dense or lowprec is not None) else None), t=t)
+    pr.make_struct()
+    return pr
+
+
+def nce_problem(G: torch.Tensor, U0: torch.Tensor, tau: float = 1.0) -> Problem:
+    """Nearest correlation estimation for the symmetric G (copied: the copy
+    becomes the iteration matrix G + Diag(x)); lam holds the dual x."""
+    n, p = U0.shape
+    dev = U0.device
+    pr = Problem(kind=B.PF_PROBLEM_NCE, n=n, rowptr=None, colind=None, vals=None,
+                 U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
+                 theta=torch.zeros(p, dtype=torch.float64, device=dev),
+                 Z=G.clone().contiguous(), lam=torch.empty(n, dtype=torch.float64, device=dev),
+                 t=tau)
     pr.make_struct()
     return pr
 

@@ -158,6 +158,13 @@ class MaxCutInstance:
     U0_raw: np.ndarray  # n x p standard Gaussian start block
 
 
+@dataclasses.dataclass
+class NCEInstance:
+    n: int
+    G: np.ndarray       # symmetric test matrix (Sec. 5.1 examples)
+    U0_raw: np.ndarray  # n x p standard Gaussian start block
+
+
 def maxcut_cost_from_edges(n: int, i: np.ndarray, j: np.ndarray, w: np.ndarray) -> CSR:
     """C = -(D - W)/4 for the weighted graph with edges (i<j, w)."""
     deg = np.zeros(n, dtype=np.float64)
@@ -204,6 +211,8 @@ WORKLOADS = {
                                     config_index=1),
     "maxcut_n16384_lowprec": dict(kind="maxcut", n=16384, prob=0.01, p=64, degree=4,
                                   degree_max=8, iters=200, config_index=2),
+    "nce_n4000": dict(kind="nce", n=4000, example="5.7", p=32, degree=3, iters=1000,
+                      config_index=5),
     "completion_n50000": dict(kind="completion", n=50000, rank=20, rate=0.01, p=40, degree=4,
                               iters=100, mu=0.05, t=1.0, config_index=3),
 }
@@ -213,6 +222,10 @@ def make_workload(name: str, **overrides):
     cfg = dict(WORKLOADS[name])
     cfg.update(overrides)
     seed = config_seed(cfg["config_index"])
+    if cfg["kind"] == "nce":
+        rng_u = _streams(seed + 1, 1)[0]
+        return cfg, NCEInstance(cfg["n"], nce_matrix(cfg["n"], cfg["example"], seed),
+                                rng_u.standard_normal((cfg["n"], cfg["p"])))
     if cfg["kind"] == "completion":
         return cfg, completion_instance(cfg["n"], cfg["rank"], cfg["rate"], cfg["p"], seed,
                                         mu=cfg["mu"], t=cfg["t"])
