@@ -426,6 +426,8 @@ def completion_solve(omega, U0_raw, mu: float, t: float, degree: int, iters: int
 # 1 - diag(G) (as in Sec. 5.1); the interval uses reading R4 with the
 # Gershgorin bounds of G + Diag(x) (a dense matrix: the bound is exact but
 # loose); the reported residual is ||grad F(x_k)|| / ||grad F(x_0)||.
+# Reading R11 (acceleration, Sec. 4.3): windows of l + 2 = 5 iterates,
+# lam = 1e-10 tr(U^T U); after a combination the iteration restarts from it.
 
 
 @dataclasses.dataclass
@@ -485,12 +487,37 @@ def nce_step(G: np.ndarray, st: NCEState, degree: int, tau: float = 1.0, exact: 
     return NCEState(x=st.x - tau * g, U=U, theta_prev=theta, g0=g0), info
 
 
-def nce_solve(G, U0_raw, degree: int, iters: int, exact: bool = False, tol: float = 0.0):
+def rna_combination(points, lam_rel: float):
+    """Extrapolation of Sec. 4.3 (regularized nonlinear acceleration): with
+    U = [x_1 - x_0, ..., x_{l+1} - x_l] (l+2 points), the coefficients
+    c = argmin_{1^T c = 1} c^T (U^T U + lam I) c are (U^T U + lam I)^{-1} 1
+    normalised to sum 1, and the new point is sum_{i=0}^{l} c_i x_i.
+    Reading R11: lam = lam_rel * tr(U^T U)."""
+    X = np.stack(points, axis=1)
+    U = X[:, 1:] - X[:, :-1]
+    M = U.T @ U
+    M = M + lam_rel * np.trace(M) * np.eye(M.shape[0])
+    z = np.linalg.solve(M, np.ones(M.shape[0]))
+    c = z / np.sum(z)
+    return X[:, :-1] @ c, c
+
+
+def nce_solve(G, U0_raw, degree: int, iters: int, exact: bool = False, tol: float = 0.0,
+              accel_l: int = 0, accel_lam: float = 1e-10):
+    """Filtered (or exact) gradient method on the NCE dual; with accel_l > 0
+    every l+2 iterates are combined by rna_combination and the iteration
+    restarts from the combination (Sec. 4.3)."""
     st = nce_init(G, U0_raw)
     hist = []
+    window = [st.x.copy()]
     for _ in range(iters):
         st, info = nce_step(G, st, degree, exact=exact)
         hist.append(info)
         if tol > 0 and info.rel <= tol:
             break
+        if accel_l > 0:
+            window.append(st.x.copy())
+            if len(window) == accel_l + 2:
+                st.x, _ = rna_combination(window, accel_lam)
+                window = [st.x.copy()]
     return st, hist

@@ -466,3 +466,38 @@ def test_nce_pf_converges_on_example_5_7_law():
     _, h_pf = o.nce_solve(G, syn.gaussian_block(n, 24, seed=7), 3, 1500, tol=1e-5)
     assert h_pf[-1].rel <= 1e-5 and h_ex[-1].rel <= 1e-5
     assert abs(h_pf[-1].obj - h_ex[-1].obj) <= 1e-7 * abs(h_ex[-1].obj)
+
+
+def test_rna_coefficients_solve_the_constrained_quadratic():
+    """c = argmin_{1^T c = 1} c^T (U^T U + lam I) c (Sec. 4.3): 1^T c = 1 and
+    the KKT condition (U^T U + lam I) c = nu 1; on points of a linear
+    fixed-point iteration x+ = A x + b with l + 1 >= dim, the combination
+    recovers the fixed point (the classical extrapolation property)."""
+    rng = np.random.default_rng(2)
+    pts = [rng.standard_normal(7) for _ in range(5)]
+    x, c = o.rna_combination(pts, 1e-6)
+    assert abs(c.sum() - 1.0) < 1e-14
+    X = np.stack(pts, axis=1)
+    U = X[:, 1:] - X[:, :-1]
+    M = U.T @ U + 1e-6 * np.trace(U.T @ U) * np.eye(4)
+    r = M @ c
+    np.testing.assert_allclose(r, r.mean() * np.ones(4), rtol=1e-9)
+    d = 3
+    A = np.diag([0.9, -0.5, 0.3])
+    bvec = np.array([1.0, 2.0, -1.0])
+    xs = [np.zeros(d)]
+    for _ in range(d + 1):
+        xs.append(A @ xs[-1] + bvec)
+    xf, _ = o.rna_combination(xs, 0.0)
+    np.testing.assert_allclose(xf, np.linalg.solve(np.eye(d) - A, bvec), atol=1e-10)
+
+
+def test_nce_accelerated_reaches_same_optimum_much_faster():
+    n = 120
+    G = syn.nce_matrix(n, "5.7", seed=8)
+    U0 = syn.gaussian_block(n, 24, seed=9)
+    _, h_plain = o.nce_solve(G, U0, 3, 3000, tol=1e-7)
+    _, h_acc = o.nce_solve(G, U0, 3, 3000, tol=1e-7, accel_l=3)
+    assert h_acc[-1].rel <= 1e-7 and h_plain[-1].rel <= 1e-7
+    assert len(h_acc) * 4 < len(h_plain)
+    assert abs(h_acc[-1].obj - h_plain[-1].obj) <= 1e-9 * abs(h_plain[-1].obj)
