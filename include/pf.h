@@ -42,6 +42,7 @@ extern "C" {
 #endif
 
 #define PF_MAX_P 64
+#define PF_MAX_ACCEL 6   /* largest extrapolation window l (Sec. 4.3) */
 
 typedef struct pf_ctx pf_ctx;
 
@@ -133,6 +134,16 @@ typedef struct {
  *  afterwards; lam is the dual vector x (n); no CSR data; t is the gradient
  *  step (t <= 0 selects 1); the report's kkt is ||grad F(x_k)|| /
  *  ||grad F(x_0)|| and obj is F(x_k).
+ *  Extrapolation (Sec. 4.3, regularized nonlinear acceleration): with
+ *  1 <= accel_l <= PF_MAX_ACCEL and hist an (accel_l + 2) x n FP64 device
+ *  buffer (row i holds iterate x_i of the current window, caller-owned,
+ *  contents managed by the library), every accel_l + 1 steps the window
+ *  x_0..x_{l+1} is replaced by x = sum_i c_i x_i, c = (D^T D + lam I)^{-1} 1
+ *  normalised to sum 1, D = [x_1 - x_0, ..., x_{l+1} - x_l], lam =
+ *  accel_lam * tr(D^T D) (accel_lam <= 0 selects 1e-10), and the iteration
+ *  continues from x.  accel_l = 0 (or hist NULL) disables it.  If the small
+ *  system has a non-positive pivot the window restarts from the current
+ *  iterate instead.  Ignored by the other kinds.
  * t: MAXCUT step; if t <= 0 on entry to pf_problem_init it is set to
  *    10 sqrt(n)/||C||_F.  COMPLETION step (t = 1 matches the Lipschitz
  *    constant of P_Omega).
@@ -151,6 +162,9 @@ typedef struct {
   double *lam;
   double *S;
   int64_t iter;          /* host-side counter, advanced by each step */
+  int32_t accel_l;       /* NCE extrapolation window l (0 = off)     */
+  double accel_lam;      /* NCE extrapolation regulariser (relative) */
+  double *hist;          /* NCE (accel_l + 2) x n window of iterates  */
 } pf_problem;
 
 /* Per-step report (host struct).  MAXCUT: obj = <C, X~>, pinf/dinf/gap as in

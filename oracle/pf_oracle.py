@@ -423,9 +423,12 @@ def completion_solve(omega, U0_raw, mu: float, t: float, degree: int, iters: int
 # (Eq. (NCE-gradient)); the gradient method takes x+ = x - tau grad F(x).
 # PFPG replaces P_+ by the projection onto the positive Ritz pairs of the
 # filtered subspace.  Readings: tau = 1 (grad F is 1-Lipschitz); x^0 =
-# 1 - diag(G) (as in Sec. 5.1); the interval uses reading R4 with the
-# Gershgorin bounds of G + Diag(x) (a dense matrix: the bound is exact but
-# loose); the reported residual is ||grad F(x_k)|| / ||grad F(x_0)||.
+# 1 - diag(G) (as in Sec. 5.1); the interval uses reading R4 with the lower
+# end a from a LANCZOS_STEPS-step Lanczos run on G + Diag(x) (Sec. 4.1 names
+# Lanczos for estimating the smallest eigenvalue; a Gershgorin bound of a
+# dense matrix is some sqrt(n) times too loose), a = theta_min - residual
+# bound, refreshed every iteration; the Gershgorin upper bound stays as the
+# upper bound; the reported residual is ||grad F(x_k)|| / ||grad F(x_0)||.
 # Reading R11 (acceleration, Sec. 4.3): windows of l + 2 = 5 iterates,
 # lam = 1e-10 tr(U^T U); after a combination the iteration restarts from it.
 
@@ -449,6 +452,37 @@ class NCEInfo:
     theta: np.ndarray
 
 
+LANCZOS_STEPS = 12
+
+
+def lanczos_lower_estimate(matvec, n: int, k: int = LANCZOS_STEPS):
+    """k steps of the symmetric Lanczos process (no reorthogonalisation) from
+    q_0 = 1/sqrt(n): alpha_j = q_j^T B q_j, beta_j = ||w_j||, with
+    w_j = B q_j - alpha_j q_j - beta_{j-1} q_{j-1} and q_{j+1} = w_j / beta_j.
+    With (theta, s) the smallest eigenpair of the k x k tridiagonal T, some
+    eigenvalue of B lies within beta_{k-1} |s_{k-1}| of theta, and theta >=
+    lambda_min(B) (interlacing).  Returns (theta - beta_{k-1}|s_{k-1}|, theta).
+    A zero beta ends the process early (an invariant subspace: exact)."""
+    q = np.full(n, 1.0 / np.sqrt(n))
+    q_prev = np.zeros(n)
+    beta_prev = 0.0
+    alpha, beta = [], []
+    for _ in range(min(k, n)):
+        w = matvec(q) - beta_prev * q_prev
+        a = float(q @ w)
+        w = w - a * q
+        alpha.append(a)
+        bj = float(np.linalg.norm(w))
+        beta.append(bj)
+        if bj == 0.0:
+            break
+        q_prev, q, beta_prev = q, w / bj, bj
+    m = len(alpha)
+    T = np.diag(alpha) + np.diag(beta[:m - 1], 1) + np.diag(beta[:m - 1], -1)
+    th, S = np.linalg.eigh(T)
+    return float(th[0] - beta[m - 1] * abs(S[m - 1, 0])), float(th[0])
+
+
 def nce_objective(G: np.ndarray, x: np.ndarray) -> float:
     lam = np.linalg.eigvalsh(G + np.diag(x))
     return 0.5 * float(np.sum(np.maximum(lam, 0.0) ** 2)) - float(np.sum(x))
@@ -464,8 +498,8 @@ def nce_step(G: np.ndarray, st: NCEState, degree: int, tau: float = 1.0, exact: 
     """One (polynomial-filtered) gradient step on the NCE dual."""
     B = G + np.diag(st.x)
     off = np.sum(np.abs(B), axis=1) - np.abs(np.diag(B))
-    a = float(np.min(np.diag(B) - off))
     ub = float(np.max(np.diag(B) + off))
+    a, _ = lanczos_lower_estimate(lambda v: B @ v, B.shape[0])
     b = choose_b(a, st.theta_prev, max(ub, 0.0), eta)
     if exact:
         lam, VB = np.linalg.eigh(B)

@@ -60,7 +60,8 @@ class pf_problem(C.Structure):
                 ("theta", C.c_void_p),
                 ("Z", C.c_void_p), ("ldz", C.c_int64),
                 ("Z_lp", C.c_void_p), ("ldz_lp", C.c_int64),
-                ("lam", C.c_void_p), ("S", C.c_void_p), ("iter", C.c_int64)]
+                ("lam", C.c_void_p), ("S", C.c_void_p), ("iter", C.c_int64),
+                ("accel_l", C.c_int32), ("accel_lam", C.c_double), ("hist", C.c_void_p)]
 
 
 class pf_iter_info(C.Structure):

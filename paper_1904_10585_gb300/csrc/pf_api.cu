@@ -255,6 +255,10 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
       return set_err(ctx, PF_ERR_INVALID_ARG, "NCE needs Z (G, ldz >= n) and lam (x)");
     if (ctx->opt.precision != PF_PREC_FP64)
       return set_err(ctx, PF_ERR_UNSUPPORTED, "NCE runs in an FP64 context");
+    if (pr->accel_l < 0 || pr->accel_l > PF_MAX_ACCEL || (pr->accel_l > 0 && !pr->hist))
+      return set_err(ctx, PF_ERR_INVALID_ARG,
+                     "NCE extrapolation needs 0 <= accel_l <= %d and hist ((l+2) x n)",
+                     PF_MAX_ACCEL);
   } else if (pr->kind == PF_PROBLEM_COMPLETION) {
     if (!pr->vals_f32 || !pr->S)
       return set_err(ctx, PF_ERR_INVALID_ARG, "completion needs vals_f32 (M on Omega) and S");
@@ -285,7 +289,7 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_nce_update(s, ws, pr->Z, pr->ldz, n, p, pr->V, pr->ldv, pr->theta, pr->lam,
-                              pr->t > 0.0 ? pr->t : 1.0));
+                              pr->t > 0.0 ? pr->t : 1.0, pr->hist, pr->accel_l, pr->accel_lam));
     return PF_OK;
   }
   // a low-precision context keeps no FP64 dense Z up to date, so it always
@@ -400,7 +404,8 @@ bool same_problem(const pf_problem &a, const pf_problem &b) {
          a.vals_f64 == b.vals_f64 && a.vals_f32 == b.vals_f32 && a.nnz == b.nnz && a.t == b.t &&
          a.mu == b.mu && a.U == b.U && a.ldu == b.ldu && a.V == b.V && a.ldv == b.ldv &&
          a.theta == b.theta && a.Z == b.Z && a.ldz == b.ldz && a.lam == b.lam && a.S == b.S &&
-         a.Z_lp == b.Z_lp && a.ldz_lp == b.ldz_lp;
+         a.Z_lp == b.Z_lp && a.ldz_lp == b.ldz_lp && a.accel_l == b.accel_l &&
+         a.accel_lam == b.accel_lam && a.hist == b.hist;
 }
 
 }  // namespace
@@ -454,7 +459,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   size_t tot = 0;
   const size_t sizes[] = {np, np, np, np, part, (size_t)kMaxGramBlocks * sq,
                           (size_t)kRedSlots * kMaxRedBlocks * kRedWidth, sq, sq, sq, kMaxP, kMaxP,
-                          (size_t)n_max, (size_t)n_max};
+                          (size_t)n_max, (size_t)n_max, (size_t)4 * n_max};
   const int nsz = sizeof(sizes) / sizeof(sizes[0]);
   for (int i = 0; i < nsz; ++i) {
     off[i] = tot;
@@ -506,6 +511,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   ws.resid = (double *)(b + off[11]);
   ws.gdiag = (double *)(b + off[12]);
   ws.rsum = (double *)(b + off[13]);
+  ws.lz = (double *)(b + off[14]);
   ws.prm = (Params *)(b + prm_off);
   ws.info = (pf_iter_info *)(b + info_off);
   ws.ldxt = ldxt;
@@ -604,7 +610,8 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
     if (!(pr->t > 0.0)) pr->t = 1.0;
     PF_CUDA(launch_params_init(s, ws.prm, ctx->opt.eta, pr->t, 0.0, ctx->opt.degree,
                                ctx->opt.precision));
-    PF_CUDA(launch_nce_init(s, ws, pr->Z, pr->ldz, n, pr->lam));
+    PF_CUDA(launch_nce_init(s, ws, pr->Z, pr->ldz, n, pr->lam,
+                            pr->accel_l > 0 ? pr->hist : nullptr));
   }
   if (pr->kind == PF_PROBLEM_MAXCUT) {
     PF_CUDA(launch_cnorm(s, ws, pr->vals_f64, pr->nnz));

@@ -41,7 +41,17 @@ struct Params {
   int degree;
   int precision;
   int sweeps;             // sweeps of the last p x p eigensolve
+  int acc_count;          // NCE extrapolation: iterates held in the window
+  int acc_go;             // NCE extrapolation: the combination below is due
+  double acc_c[PF_MAX_ACCEL + 1];  // its coefficients c_0..c_l
+  // NCE: Lanczos estimate of the smallest eigenvalue (lower end of the interval)
+  double lz_alpha[16], lz_beta[16];
+  double a_lz;            // theta_min - residual bound
+  int lz_m;               // Lanczos steps taken (fewer than kLanczos on breakdown)
 };
+
+// Lanczos steps of the NCE interval estimate (Sec. 4.1)
+constexpr int kLanczos = 12;
 
 // Internal iteration-matrix description.
 struct Op {
@@ -75,6 +85,7 @@ struct Workspace {
   void *Xt[2];            // transposed low-precision operands, p x ldxt
   float *Wf, *Vf;         // fp32 factors of the shadow expansion, n_max x 64
   double *gdiag, *rsum;   // NCE: diag(G) and off-diagonal |G| row sums, n_max each
+  double *lz;             // NCE: Lanczos vectors q (2), B q, w: 4 x n_max
   int64_t ldxt;
 };
 
@@ -175,12 +186,12 @@ cudaError_t launch_maxcut_lp_shadow(cudaStream_t s, const Workspace &ws, bool f3
 cudaError_t launch_copy_block(cudaStream_t s, const Workspace &ws, const double *src, int64_t lds,
                               int n, int p, double *dst, int64_t ldd);
 cudaError_t launch_nce_init(cudaStream_t s, const Workspace &ws, double *Z, int64_t ldz, int n,
-                            double *x);
+                            double *x, double *hist);
 cudaError_t launch_nce_interval(cudaStream_t s, const Workspace &ws, const double *Z, int64_t ldz,
                                 int n, const double *theta, int p);
 cudaError_t launch_nce_update(cudaStream_t s, const Workspace &ws, double *Z, int64_t ldz, int n,
                               int p, const double *V, int64_t ldv, const double *theta, double *x,
-                              double tau);
+                              double tau, double *hist, int accel_l, double accel_lam);
 cudaError_t launch_fill(cudaStream_t s, double *x, int64_t rows, int64_t cols, int64_t ld, double v);
 cudaError_t launch_export_info(cudaStream_t s, const Workspace &ws, int degree, int precision);
 cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,

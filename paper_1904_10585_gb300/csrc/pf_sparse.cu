@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(NT) k_interval_rows(int kind, const int32_t *_
 
 __global__ void __launch_bounds__(NT) k_interval_final(const double *__restrict__ red, int nb,
                                                        const double *__restrict__ theta, int p,
-                                                       Params *prm) {
+                                                       Params *prm, int use_lanczos) {
   __shared__ double sh[32];
   double a = INFINITY, ubs = -INFINITY;
   for (int q = threadIdx.x; q < nb; q += NT) {
@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(NT) k_interval_final(const double *__restrict_
   a = block_reduce(a, sh, 1);
   ubs = block_reduce(ubs, sh, 2);
   if (threadIdx.x != 0) return;
+  if (use_lanczos) a = prm->a_lz;
   const int have = prm->have_prev;
   const double thmax = have ? fmax(theta[0], 0.0) : 0.0;
   double ub = fmax(ubs + thmax, 0.0);
@@ -571,7 +572,7 @@ cudaError_t launch_interval(cudaStream_t s, const Workspace &ws, int kind, const
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_interval_final<<<1, NT, 0, s>>>(slot(ws, SLOT_INTERVAL), nb, theta, p, ws.prm);
+  k_interval_final<<<1, NT, 0, s>>>(slot(ws, SLOT_INTERVAL), nb, theta, p, ws.prm, 0);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
@@ -1138,8 +1139,10 @@ namespace {
 __global__ void __launch_bounds__(NT) k_nce_init(double *Z, int64_t ldz, int n,
                                                  double *__restrict__ gdiag,
                                                  double *__restrict__ rsum,
-                                                 double *__restrict__ x) {
+                                                 double *__restrict__ x,
+                                                 double *__restrict__ hist, Params *prm) {
   const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) prm->acc_count = hist != nullptr ? 1 : 0;
   const int warps = gridDim.x * WPB;
   for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
     const double *zr = Z + (int64_t)row * ldz;
@@ -1152,6 +1155,7 @@ __global__ void __launch_bounds__(NT) k_nce_init(double *Z, int64_t ldz, int n,
       gdiag[row] = g;
       rsum[row] = s;
       x[row] = 1.0 - g;
+      if (hist != nullptr) hist[row] = 1.0 - g;
       Z[(int64_t)row * ldz + row] = 1.0;
     }
   }
@@ -1183,10 +1187,13 @@ __global__ void __launch_bounds__(NT) k_nce_update(double *Z, int64_t ldz, int n
                                                    const double *__restrict__ theta,
                                                    const double *__restrict__ gdiag,
                                                    double *__restrict__ x, double tau,
-                                                   double *__restrict__ red) {
+                                                   double *__restrict__ red,
+                                                   double *__restrict__ hist,
+                                                   const Params *__restrict__ prm) {
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * WPB;
+  double *hrow = hist != nullptr ? hist + (int64_t)prm->acc_count * n : nullptr;
   double sg = 0.0, sx = 0.0;
   for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
     double dx = 0.0;
@@ -1203,6 +1210,7 @@ __global__ void __launch_bounds__(NT) k_nce_update(double *Z, int64_t ldz, int n
       const double xo = x[row];
       const double xn = xo - tau * g;
       x[row] = xn;
+      if (hrow != nullptr) hrow[row] = xn;
       Z[(int64_t)row * ldz + row] = gdiag[row] + xn;
       sg = fma(g, g, sg);
       sx += xo;
@@ -1218,7 +1226,7 @@ __global__ void __launch_bounds__(NT) k_nce_update(double *Z, int64_t ldz, int n
 
 __global__ void __launch_bounds__(NT) k_nce_report(const double *__restrict__ red, int nb,
                                                    const double *__restrict__ theta, int p,
-                                                   Params *prm) {
+                                                   int accel, Params *prm) {
   __shared__ double sh[32];
   double sg = 0.0, sx = 0.0;
   for (int q = threadIdx.x; q < nb; q += NT) {
@@ -1248,40 +1256,382 @@ __global__ void __launch_bounds__(NT) k_nce_report(const double *__restrict__ re
   prm->theta_max = theta[0];
   prm->theta_min = theta[p - 1];
   prm->have_prev = 1;
+  if (accel) prm->acc_count += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos estimate of lambda_min(B), B = G + Diag(x) dense (Sec. 4.1): k
+// steps from q_0 = 1/sqrt(n) without reorthogonalisation.  Step j is two
+// launches:
+//   k_lz_matvec: beta_{j-1} = ||w_{j-1}|| (each block sums the partials in
+//     the same order), q_j = w_{j-1} / beta_{j-1}, y = B q_j, partial q_j^T y;
+//   k_lz_update: alpha_j = q_j^T y, w_j = y - alpha_j q_j - beta_{j-1} q_{j-1},
+//     partial ||w_j||^2.
+// lz rows: 0, 1 = q_j by parity of j; 2 = y; 3 = w.  A zero (or non-finite)
+// beta ends the process (lz_m = steps taken); later launches do nothing.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sum_partials(const double *__restrict__ red, int nb) {
+  double v = 0.0;
+  for (int q = 0; q < nb; ++q) v += red[q * kRedWidth];
+  return v;
+}
+
+__global__ void __launch_bounds__(NT) k_lz_matvec(const double *__restrict__ Z, int64_t ldz, int n,
+                                                  int j, double *lz,
+                                                  const double *__restrict__ wpart, int nbp,
+                                                  double *__restrict__ apart, Params *prm) {
+  __shared__ double sh[32];
+  __shared__ double s_scale;
+  double *qj = lz + (int64_t)(j & 1) * n;
+  double *y = lz + 2 * (int64_t)n;
+  const double *w = lz + 3 * (int64_t)n;
+  if (j > 0 && prm->lz_m < j) return;  // ended earlier
+  if (threadIdx.x == 0) {
+    if (j == 0) {
+      s_scale = 1.0 / sqrt((double)n);
+      if (blockIdx.x == 0) prm->lz_m = kLanczos;
+    } else {
+      const double beta = sqrt(sum_partials(wpart, nbp));
+      if (blockIdx.x == 0) prm->lz_beta[j - 1] = beta;
+      s_scale = (beta > 0.0 && isfinite(beta)) ? 1.0 / beta : 0.0;
+      if (s_scale == 0.0 && blockIdx.x == 0) prm->lz_m = j;
+    }
+  }
+  __syncthreads();
+  const double sc = s_scale;
+  if (sc == 0.0) return;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * WPB;
+  double part = 0.0;
+  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
+    const double *zr = Z + (int64_t)row * ldz;
+    double acc = 0.0;
+    if (j == 0) {
+      for (int c = lane; c < n; c += 32) acc += zr[c];
+    } else {
+      for (int c = lane; c < n; c += 32) acc = fma(zr[c], w[c], acc);
+    }
+    acc = warp_sum(acc) * sc;
+    if (lane == 0) {
+      const double q = j == 0 ? sc : w[row] * sc;
+      qj[row] = q;
+      y[row] = acc;
+      part = fma(q, acc, part);
+    }
+  }
+  part = block_reduce(part, sh, 0);
+  if (threadIdx.x == 0) apart[blockIdx.x * kRedWidth] = part;
+}
+
+__global__ void __launch_bounds__(NT) k_lz_update(int n, int j, double *lz,
+                                                  const double *__restrict__ apart, int nb,
+                                                  double *__restrict__ wpart_out, Params *prm) {
+  __shared__ double sh[32];
+  __shared__ double s_alpha, s_beta;
+  if (prm->lz_m <= j) return;
+  const double *qj = lz + (int64_t)(j & 1) * n;
+  const double *qm = lz + (int64_t)((j + 1) & 1) * n;  // q_{j-1}
+  const double *y = lz + 2 * (int64_t)n;
+  double *w = lz + 3 * (int64_t)n;
+  if (threadIdx.x == 0) {
+    s_alpha = sum_partials(apart, nb);
+    s_beta = j > 0 ? prm->lz_beta[j - 1] : 0.0;
+    if (blockIdx.x == 0) prm->lz_alpha[j] = s_alpha;
+  }
+  __syncthreads();
+  const double al = s_alpha, be = s_beta;
+  double part = 0.0;
+  for (int r = blockIdx.x * NT + threadIdx.x; r < n; r += gridDim.x * NT) {
+    double v = y[r] - al * qj[r];
+    if (j > 0) v -= be * qm[r];
+    w[r] = v;
+    part = fma(v, v, part);
+  }
+  part = block_reduce(part, sh, 0);
+  if (threadIdx.x == 0) wpart_out[blockIdx.x * kRedWidth] = part;
+}
+
+// Smallest eigenvalue theta of the m x m Lanczos tridiagonal by bisection on
+// the Sturm count, its eigenvector by inverse iteration with the shift just
+// below theta (T - sigma I is then positive definite: the LDL^T sweep needs
+// no pivoting), and a = theta - beta_{m-1} |s_{m-1}|.
+__device__ int sturm_below(const double *al, const double *be, int m, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; ++i) {
+    const double b2 = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+    d = (al[i] - x) - (i > 0 ? b2 / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_lz_final(const double *__restrict__ wpart, int nb, Params *prm) {
+  if (threadIdx.x != 0) return;
+  const int m = prm->lz_m;
+  const double *al = prm->lz_alpha;
+  double be[16];
+  for (int i = 0; i + 1 < m; ++i) be[i] = prm->lz_beta[i];
+  const double blast = m == kLanczos ? sqrt(sum_partials(wpart, nb)) : prm->lz_beta[m - 1];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
+    lo = fmin(lo, al[i] - r);
+    hi = fmax(hi, al[i] + r);
+  }
+  double a0 = lo, b0 = hi;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (a0 + b0);
+    if (!(mid > a0 && mid < b0)) break;
+    if (sturm_below(al, be, m, mid) >= 1) b0 = mid;
+    else a0 = mid;
+  }
+  const double theta = b0;
+  double s[16];
+  double res = 0.0;
+  if (m == 1) {
+    res = fabs(blast);
+  } else {
+    const double sigma = theta - 1e-10 * fmax(hi - lo, 1e-300);
+    for (int i = 0; i < m; ++i) s[i] = 1.0;
+    for (int rep = 0; rep < 3; ++rep) {
+      // solve (T - sigma I) z = s by the LDL^T sweep, in place
+      double d[16], l[16];
+      d[0] = al[0] - sigma;
+      for (int i = 1; i < m; ++i) {
+        l[i] = be[i - 1] / d[i - 1];
+        d[i] = (al[i] - sigma) - l[i] * be[i - 1];
+      }
+      for (int i = 1; i < m; ++i) s[i] -= l[i] * s[i - 1];
+      s[m - 1] /= d[m - 1];
+      for (int i = m - 2; i >= 0; --i) s[i] = s[i] / d[i] - l[i + 1] * s[i + 1];
+      double nrm = 0.0;
+      for (int i = 0; i < m; ++i) nrm = fma(s[i], s[i], nrm);
+      nrm = sqrt(nrm);
+      for (int i = 0; i < m; ++i) s[i] /= nrm;
+    }
+    res = fabs(blast) * fabs(s[m - 1]);
+  }
+  prm->a_lz = theta - res;
+}
+
+// ---------------------------------------------------------------------------
+// Extrapolation of Sec. 4.3 over the window x_0..x_{l+1} (rows of hist).
+// All three kernels are launched every step and act only when the window is
+// full, so the step stays one fixed launch sequence (graph-capturable).
+// ---------------------------------------------------------------------------
+
+// Partial sums of D^T D (upper triangle, row-major pair order), D_j =
+// x_{j+1} - x_j, over this block's rows: out[block][pair].
+template <int L1>
+__global__ void __launch_bounds__(NT) k_rna_gram(const double *__restrict__ hist, int n,
+                                                 const Params *__restrict__ prm,
+                                                 double *__restrict__ out) {
+  constexpr int NPAIR = L1 * (L1 + 1) / 2;
+  if (prm->acc_count != L1 + 1) return;
+  __shared__ double sh[32];
+  double acc[NPAIR];
+#pragma unroll
+  for (int q = 0; q < NPAIR; ++q) acc[q] = 0.0;
+  for (int r = blockIdx.x * NT + threadIdx.x; r < n; r += gridDim.x * NT) {
+    double d[L1];
+    double prev = hist[r];
+#pragma unroll
+    for (int j = 0; j < L1; ++j) {
+      const double cur = hist[(int64_t)(j + 1) * n + r];
+      d[j] = cur - prev;
+      prev = cur;
+    }
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < L1; ++i)
+#pragma unroll
+      for (int j = i; j < L1; ++j) {
+        acc[q] = fma(d[i], d[j], acc[q]);
+        ++q;
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < NPAIR; ++q) {
+    const double v = block_reduce(acc[q], sh, 0);
+    if (threadIdx.x == 0) out[blockIdx.x * NPAIR + q] = v;
+  }
+}
+
+// Fixed-order sum of the partials, M = D^T D + lam tr(D^T D) I, Cholesky
+// solve M z = 1, c = z / 1^T z.  acc_go: 1 combine, 2 restart the window from
+// the current iterate (non-positive pivot), 0 nothing due.
+__global__ void k_rna_solve(const double *__restrict__ part, int nb, int l1, double lam_rel,
+                            Params *prm) {
+  __shared__ double pair[(PF_MAX_ACCEL + 1) * (PF_MAX_ACCEL + 2) / 2];
+  const bool due = prm->acc_count == l1 + 1;
+  if (!due) {
+    if (threadIdx.x == 0) prm->acc_go = 0;
+    return;
+  }
+  const int npair = l1 * (l1 + 1) / 2;
+  for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+    double v = 0.0;
+    for (int b = 0; b < nb; ++b) v += part[b * npair + q];
+    pair[q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double M[PF_MAX_ACCEL + 1][PF_MAX_ACCEL + 1];
+  int q = 0;
+  double tr = 0.0;
+  for (int i = 0; i < l1; ++i)
+    for (int j = i; j < l1; ++j) {
+      M[i][j] = M[j][i] = pair[q++];
+      if (i == j) tr += M[i][i];
+    }
+  for (int i = 0; i < l1; ++i) M[i][i] += lam_rel * tr;
+  // Cholesky M = L L^T in place (lower triangle)
+  bool ok = tr > 0.0 && isfinite(tr);
+  for (int j = 0; j < l1 && ok; ++j) {
+    double dj = M[j][j];
+    for (int k = 0; k < j; ++k) dj -= M[j][k] * M[j][k];
+    if (!(dj > 0.0)) { ok = false; break; }
+    const double ljj = sqrt(dj);
+    M[j][j] = ljj;
+    for (int i = j + 1; i < l1; ++i) {
+      double v = M[i][j];
+      for (int k = 0; k < j; ++k) v -= M[i][k] * M[j][k];
+      M[i][j] = v / ljj;
+    }
+  }
+  double z[PF_MAX_ACCEL + 1];
+  double sz = 0.0;
+  if (ok) {
+    for (int i = 0; i < l1; ++i) {  // L w = 1
+      double v = 1.0;
+      for (int k = 0; k < i; ++k) v -= M[i][k] * z[k];
+      z[i] = v / M[i][i];
+    }
+    for (int i = l1 - 1; i >= 0; --i) {  // L^T z = w
+      double v = z[i];
+      for (int k = i + 1; k < l1; ++k) v -= M[k][i] * z[k];
+      z[i] = v / M[i][i];
+    }
+    for (int i = 0; i < l1; ++i) sz += z[i];
+    ok = sz != 0.0 && isfinite(sz);
+  }
+  if (ok)
+    for (int i = 0; i < l1; ++i) prm->acc_c[i] = z[i] / sz;
+  prm->acc_go = ok ? 1 : 2;
+  prm->acc_count = 1;
+}
+
+// x = sum_{i<=l} c_i x_i; diag(B) <- diag(G) + x; the window restarts at x.
+__global__ void __launch_bounds__(NT) k_rna_combine(double *__restrict__ hist, int n, int l1,
+                                                    double *__restrict__ x, double *Z,
+                                                    int64_t ldz,
+                                                    const double *__restrict__ gdiag,
+                                                    const Params *__restrict__ prm) {
+  const int go = prm->acc_go;
+  if (go == 0) return;
+  double c[PF_MAX_ACCEL + 1];
+  for (int i = 0; i < l1; ++i) c[i] = prm->acc_c[i];
+  for (int r = blockIdx.x * NT + threadIdx.x; r < n; r += gridDim.x * NT) {
+    double xn;
+    if (go == 1) {
+      xn = 0.0;
+      for (int i = 0; i < l1; ++i) xn = fma(c[i], hist[(int64_t)i * n + r], xn);
+      x[r] = xn;
+      Z[(int64_t)r * ldz + r] = gdiag[r] + xn;
+    } else {
+      xn = x[r];
+    }
+    hist[r] = xn;
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_nce_init(cudaStream_t s, const Workspace &ws, double *Z, int64_t ldz, int n,
-                            double *x) {
-  k_nce_init<<<red_blocks(n, ws.num_sms), NT, 0, s>>>(Z, ldz, n, ws.gdiag, ws.rsum, x);
+                            double *x, double *hist) {
+  k_nce_init<<<red_blocks(n, ws.num_sms), NT, 0, s>>>(Z, ldz, n, ws.gdiag, ws.rsum, x, hist,
+                                                      ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
 
 cudaError_t launch_nce_interval(cudaStream_t s, const Workspace &ws, const double *Z, int64_t ldz,
                                 int n, const double *theta, int p) {
+  // Lanczos estimate of the lower end a
+  const int nbm = red_blocks(n, ws.num_sms);
+  int nbu = (n + NT - 1) / NT;
+  if (nbu > 2 * ws.num_sms) nbu = 2 * ws.num_sms;
+  double *apart = slot(ws, SLOT_EXPAND);
+  double *wp[2] = {slot(ws, SLOT_SDDMM), slot(ws, SLOT_RESID)};
+  for (int j = 0; j < kLanczos; ++j) {
+    k_lz_matvec<<<nbm, NT, 0, s>>>(Z, ldz, n, j, ws.lz, wp[(j + 1) & 1], nbu, apart, ws.prm);
+    PF_LAUNCHED();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_lz_update<<<nbu, NT, 0, s>>>(n, j, ws.lz, apart, nbm, wp[j & 1], ws.prm);
+    PF_LAUNCHED();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_lz_final<<<1, 32, 0, s>>>(wp[(kLanczos - 1) & 1], nbu, ws.prm);
+  PF_LAUNCHED();
+  cudaError_t e0 = cudaGetLastError();
+  if (e0 != cudaSuccess) return e0;
   int nb = (n + NT - 1) / NT;
   if (nb > kMaxRedBlocks) nb = kMaxRedBlocks;
   k_nce_rows<<<nb, NT, 0, s>>>(Z, ldz, n, ws.rsum, slot(ws, SLOT_INTERVAL));
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_interval_final<<<1, NT, 0, s>>>(slot(ws, SLOT_INTERVAL), nb, theta, p, ws.prm);
+  k_interval_final<<<1, NT, 0, s>>>(slot(ws, SLOT_INTERVAL), nb, theta, p, ws.prm, 1);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
 
 cudaError_t launch_nce_update(cudaStream_t s, const Workspace &ws, double *Z, int64_t ldz, int n,
                               int p, const double *V, int64_t ldv, const double *theta, double *x,
-                              double tau) {
+                              double tau, double *hist, int accel_l, double accel_lam) {
   const int nb = red_blocks(n, ws.num_sms);
+  const bool acc = hist != nullptr && accel_l > 0;
   k_nce_update<<<nb, NT, 0, s>>>(Z, ldz, n, p, V, ldv, theta, ws.gdiag, x, tau,
-                                 slot(ws, SLOT_LAMBDA));
+                                 slot(ws, SLOT_LAMBDA), acc ? hist : nullptr, ws.prm);
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_nce_report<<<1, NT, 0, s>>>(slot(ws, SLOT_LAMBDA), nb, theta, p, ws.prm);
+  k_nce_report<<<1, NT, 0, s>>>(slot(ws, SLOT_LAMBDA), nb, theta, p, acc ? 1 : 0, ws.prm);
+  PF_LAUNCHED();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !acc) return e;
+  // the whole reduction array (every slot) holds the Gram partials: at most
+  // 512 blocks x 28 pairs <= kRedSlots * kMaxRedBlocks * kRedWidth doubles
+  static_assert(512 * (PF_MAX_ACCEL + 1) * (PF_MAX_ACCEL + 2) / 2 <=
+                    kRedSlots * kMaxRedBlocks * kRedWidth,
+                "extrapolation partials exceed the reduction array");
+  const int l1 = accel_l + 1;
+  int gb = (n + NT - 1) / NT;
+  if (gb > 512) gb = 512;
+  if (gb > 2 * ws.num_sms) gb = 2 * ws.num_sms;
+  if (gb < 1) gb = 1;
+  switch (l1) {
+#define PF_RNA(L)                                                         \
+  case L:                                                                 \
+    k_rna_gram<L><<<gb, NT, 0, s>>>(hist, n, ws.prm, ws.red);             \
+    break;
+    PF_RNA(2) PF_RNA(3) PF_RNA(4) PF_RNA(5) PF_RNA(6) PF_RNA(7)
+#undef PF_RNA
+    default: return cudaErrorInvalidValue;
+  }
+  PF_LAUNCHED();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rna_solve<<<1, 32, 0, s>>>(ws.red, gb, l1, accel_lam > 0.0 ? accel_lam : 1e-10, ws.prm);
+  PF_LAUNCHED();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rna_combine<<<red_blocks(n, ws.num_sms), NT, 0, s>>>(hist, n, l1, x, Z, ldz, ws.gdiag,
+                                                          ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
 }

@@ -126,6 +126,9 @@ class Problem:
     S: Optional[torch.Tensor] = None
     t: float = 0.0
     mu: float = 0.0
+    hist: Optional[torch.Tensor] = None
+    accel_l: int = 0
+    accel_lam: float = 0.0
     struct: Optional[B.pf_problem] = None
 
     def make_struct(self) -> B.pf_problem:
@@ -139,6 +142,10 @@ class Problem:
             s.Z = _ptr(self.Z)
             s.ldz = _ld(self.Z)
             s.lam = _ptr(self.lam)
+            if self.hist is not None:
+                s.hist = _ptr(self.hist)
+                s.accel_l = self.accel_l
+                s.accel_lam = self.accel_lam
             self.struct = s
             return s
         if self.kind == B.PF_PROBLEM_MAXCUT:
@@ -188,16 +195,21 @@ def maxcut_problem(rowptr, colind, vals, U0: torch.Tensor, t: float = 0.0, dense
     return pr
 
 
-def nce_problem(G: torch.Tensor, U0: torch.Tensor, tau: float = 1.0) -> Problem:
+def nce_problem(G: torch.Tensor, U0: torch.Tensor, tau: float = 1.0, accel_l: int = 0,
+                accel_lam: float = 1e-10) -> Problem:
     """Nearest correlation estimation for the symmetric G (copied: the copy
-    becomes the iteration matrix G + Diag(x)); lam holds the dual x."""
+    becomes the iteration matrix G + Diag(x)); lam holds the dual x.
+    accel_l > 0 turns on the extrapolation of Sec. 4.3 over windows of
+    accel_l + 2 iterates (regulariser accel_lam * tr(D^T D))."""
     n, p = U0.shape
     dev = U0.device
     pr = Problem(kind=B.PF_PROBLEM_NCE, n=n, rowptr=None, colind=None, vals=None,
                  U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
                  theta=torch.zeros(p, dtype=torch.float64, device=dev),
                  Z=G.clone().contiguous(), lam=torch.empty(n, dtype=torch.float64, device=dev),
-                 t=tau)
+                 t=tau, accel_l=accel_l, accel_lam=accel_lam,
+                 hist=(torch.zeros(accel_l + 2, n, dtype=torch.float64, device=dev)
+                       if accel_l > 0 else None))
     pr.make_struct()
     return pr
 

@@ -501,3 +501,60 @@ def test_nce_accelerated_reaches_same_optimum_much_faster():
     assert h_acc[-1].rel <= 1e-7 and h_plain[-1].rel <= 1e-7
     assert len(h_acc) * 4 < len(h_plain)
     assert abs(h_acc[-1].obj - h_plain[-1].obj) <= 1e-9 * abs(h_plain[-1].obj)
+
+
+def _sym_with_spectrum(lam, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((len(lam), len(lam))))
+    return (Q * lam) @ Q.T
+
+
+def test_lanczos_estimate_brackets_an_eigenvalue_and_interlaces():
+    """Sec. 4.1 Lanczos estimate of lambda_min: the Ritz value theta is >=
+    lambda_min (Cauchy interlacing) and an eigenvalue of B lies in
+    [theta - r, theta + r] with r the residual bound; on a matrix with a
+    separated bottom eigenvalue 12 steps find it to 1e-6."""
+    for seed in range(4):
+        rng = np.random.default_rng(seed)
+        lam = np.sort(rng.uniform(-3, 5, 60))
+        B = _sym_with_spectrum(lam, 10 + seed)
+        lo, th = o.lanczos_lower_estimate(lambda v: B @ v, 60, 12)
+        assert th >= lam[0] - 1e-12
+        r = th - lo
+        assert r >= 0
+        assert np.min(np.abs(lam - th)) <= r + 1e-12
+    lam = np.concatenate([[-10.0], np.linspace(0.0, 1.0, 79)])
+    B = _sym_with_spectrum(lam, 3)
+    lo, th = o.lanczos_lower_estimate(lambda v: B @ v, 80, 12)
+    assert abs(th - (-10.0)) < 1e-6 and lo <= -10.0 + 1e-9
+
+
+def test_lanczos_full_krylov_space_is_exact():
+    """k = n steps from a start vector with components along every
+    eigenvector span the whole space: theta = lambda_min and the residual
+    bound vanishes (to rounding); an invariant start (B = c I) stops after
+    one step with the exact value."""
+    lam = np.array([-2.5, -1.0, 0.25, 0.5, 3.0, 7.0])
+    B = _sym_with_spectrum(lam, 5)
+    lo, th = o.lanczos_lower_estimate(lambda v: B @ v, 6, 6)
+    assert abs(th - lam[0]) < 1e-10 and abs(lo - lam[0]) < 1e-8
+    lo, th = o.lanczos_lower_estimate(lambda v: 3.0 * v, 9, 12)
+    assert lo == th == pytest.approx(3.0, abs=1e-15)
+
+
+def test_lanczos_planted_sign_error_is_caught():
+    """A recurrence with +beta q_{j-1} instead of -beta q_{j-1} no longer
+    produces the Lanczos tridiagonal: its theta misses lambda_min."""
+    lam = np.array([-2.5, -1.0, 0.25, 0.5, 3.0, 7.0])
+    B = _sym_with_spectrum(lam, 5)
+
+    def wrong(n, k):
+        q = np.full(n, 1.0 / np.sqrt(n)); qp = np.zeros(n); bp = 0.0; al = []; be = []
+        for _ in range(k):
+            w = B @ q + bp * qp
+            a = q @ w; w = w - a * q; al.append(a); bj = np.linalg.norm(w); be.append(bj)
+            qp, q, bp = q, w / bj, bj
+        T = np.diag(al) + np.diag(be[:-1], 1) + np.diag(be[:-1], -1)
+        return np.linalg.eigvalsh(T)[0]
+
+    assert abs(wrong(6, 6) - lam[0]) > 1e-3
