@@ -429,8 +429,9 @@ def completion_solve(omega, U0_raw, mu: float, t: float, degree: int, iters: int
 # dense matrix is some sqrt(n) times too loose), a = theta_min - residual
 # bound, refreshed every iteration; the Gershgorin upper bound stays as the
 # upper bound; the reported residual is ||grad F(x_k)|| / ||grad F(x_0)||.
-# Reading R11 (acceleration, Sec. 4.3): windows of l + 2 = 5 iterates,
-# lam = 1e-10 tr(U^T U); after a combination the iteration restarts from it.
+# Reading R11 (acceleration, Sec. 4.3): windows of l + 2 iterates (the NCE
+# workload takes l = 2), lam = 1e-10 tr(U^T U); after a combination the
+# iteration restarts from it.
 
 
 @dataclasses.dataclass

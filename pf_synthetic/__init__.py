@@ -211,8 +211,8 @@ WORKLOADS = {
                                     config_index=1),
     "maxcut_n16384_lowprec": dict(kind="maxcut", n=16384, prob=0.01, p=64, degree=4,
                                   degree_max=8, iters=200, config_index=2),
-    "nce_n4000": dict(kind="nce", n=4000, example="5.7", p=32, degree=3, iters=1000,
-                      accel_l=3, config_index=5),
+    "nce_n4000": dict(kind="nce", n=4000, example="5.7", p=64, degree=3, iters=1000,
+                      accel_l=2, config_index=5),
     "completion_n50000": dict(kind="completion", n=50000, rank=20, rate=0.01, p=40, degree=4,
                               iters=100, mu=0.05, t=1.0, config_index=3),
 }
