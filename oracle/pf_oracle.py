@@ -427,7 +427,10 @@ def completion_solve(omega, U0_raw, mu: float, t: float, degree: int, iters: int
 # end a from a LANCZOS_STEPS-step Lanczos run on G + Diag(x) (Sec. 4.1 names
 # Lanczos for estimating the smallest eigenvalue; a Gershgorin bound of a
 # dense matrix is some sqrt(n) times too loose), a = theta_min - residual
-# bound, refreshed every iteration; the Gershgorin upper bound stays as the
+# bound, with full reorthogonalisation (without it the process loses
+# orthogonality once the dominant Ritz value has converged, which it does in
+# a step or two for these G, and the small end drifts with rounding),
+# refreshed every iteration; the Gershgorin upper bound stays as the
 # upper bound; the reported residual is ||grad F(x_k)|| / ||grad F(x_0)||.
 # Reading R11 (acceleration, Sec. 4.3): windows of l + 2 iterates (the NCE
 # workload takes l = 2), lam = 1e-10 tr(U^T U); after a combination the
@@ -457,27 +460,33 @@ LANCZOS_STEPS = 12
 
 
 def lanczos_lower_estimate(matvec, n: int, k: int = LANCZOS_STEPS):
-    """k steps of the symmetric Lanczos process (no reorthogonalisation) from
-    q_0 = 1/sqrt(n): alpha_j = q_j^T B q_j, beta_j = ||w_j||, with
-    w_j = B q_j - alpha_j q_j - beta_{j-1} q_{j-1} and q_{j+1} = w_j / beta_j.
-    With (theta, s) the smallest eigenpair of the k x k tridiagonal T, some
-    eigenvalue of B lies within beta_{k-1} |s_{k-1}| of theta, and theta >=
-    lambda_min(B) (interlacing).  Returns (theta - beta_{k-1}|s_{k-1}|, theta).
-    A zero beta ends the process early (an invariant subspace: exact)."""
+    """k steps of the symmetric Lanczos process from q_0 = 1/sqrt(n), with
+    full reorthogonalisation (classical Gram-Schmidt against every basis
+    vector, the form ARPACK-style Lanczos codes use):
+        y = B q_j - beta_{j-1} q_{j-1},  c = Q_j^T y,  alpha_j = c_j,
+        w = y - Q_j c,  beta_j = ||w||,  q_{j+1} = w / beta_j,
+    Q_j = [q_0, ..., q_j].  With (theta, s) the smallest eigenpair of the
+    tridiagonal T (alpha on the diagonal, beta beside it), some eigenvalue of
+    B lies within beta_{k-1} |s_{k-1}| of theta, and theta >= lambda_min(B)
+    (interlacing).  Returns (theta - beta_{k-1}|s_{k-1}|, theta).  A zero
+    beta ends the process early (an invariant subspace: exact)."""
+    Q = np.zeros((n, min(k, n)))
     q = np.full(n, 1.0 / np.sqrt(n))
-    q_prev = np.zeros(n)
     beta_prev = 0.0
     alpha, beta = [], []
-    for _ in range(min(k, n)):
-        w = matvec(q) - beta_prev * q_prev
-        a = float(q @ w)
-        w = w - a * q
-        alpha.append(a)
+    for j in range(min(k, n)):
+        Q[:, j] = q
+        y = matvec(q)
+        if j > 0:
+            y = y - beta_prev * Q[:, j - 1]
+        c = Q[:, :j + 1].T @ y
+        alpha.append(float(c[j]))
+        w = y - Q[:, :j + 1] @ c
         bj = float(np.linalg.norm(w))
         beta.append(bj)
         if bj == 0.0:
             break
-        q_prev, q, beta_prev = q, w / bj, bj
+        q, beta_prev = w / bj, bj
     m = len(alpha)
     T = np.diag(alpha) + np.diag(beta[:m - 1], 1) + np.diag(beta[:m - 1], -1)
     th, S = np.linalg.eigh(T)

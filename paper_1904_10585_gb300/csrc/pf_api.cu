@@ -459,7 +459,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   size_t tot = 0;
   const size_t sizes[] = {np, np, np, np, part, (size_t)kMaxGramBlocks * sq,
                           (size_t)kRedSlots * kMaxRedBlocks * kRedWidth, sq, sq, sq, kMaxP, kMaxP,
-                          (size_t)n_max, (size_t)n_max, (size_t)4 * n_max};
+                          (size_t)n_max, (size_t)n_max, (size_t)(kLanczos + 2) * n_max};
   const int nsz = sizeof(sizes) / sizeof(sizes[0]);
   for (int i = 0; i < nsz; ++i) {
     off[i] = tot;

@@ -85,7 +85,7 @@ struct Workspace {
   void *Xt[2];            // transposed low-precision operands, p x ldxt
   float *Wf, *Vf;         // fp32 factors of the shadow expansion, n_max x 64
   double *gdiag, *rsum;   // NCE: diag(G) and off-diagonal |G| row sums, n_max each
-  double *lz;             // NCE: Lanczos vectors q (2), B q, w: 4 x n_max
+  double *lz;             // NCE: Lanczos basis q_0..q_{k-1}, y, w: (kLanczos + 2) x n_max
   int64_t ldxt;
 };
 

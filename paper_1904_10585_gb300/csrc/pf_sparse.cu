@@ -1261,48 +1261,55 @@ __global__ void __launch_bounds__(NT) k_nce_report(const double *__restrict__ re
 
 // ---------------------------------------------------------------------------
 // Lanczos estimate of lambda_min(B), B = G + Diag(x) dense (Sec. 4.1): k
-// steps from q_0 = 1/sqrt(n) without reorthogonalisation.  Step j is two
-// launches:
+// steps from q_0 = 1/sqrt(n) with full reorthogonalisation (classical
+// Gram-Schmidt against every basis vector).  Step j is two launches:
 //   k_lz_matvec: beta_{j-1} = ||w_{j-1}|| (each block sums the partials in
-//     the same order), q_j = w_{j-1} / beta_{j-1}, y = B q_j, partial q_j^T y;
-//   k_lz_update: alpha_j = q_j^T y, w_j = y - alpha_j q_j - beta_{j-1} q_{j-1},
-//     partial ||w_j||^2.
-// lz rows: 0, 1 = q_j by parity of j; 2 = y; 3 = w.  A zero (or non-finite)
-// beta ends the process (lz_m = steps taken); later launches do nothing.
+//     the same order), q_j = w_{j-1} / beta_{j-1}, y = B q_j - beta_{j-1}
+//     q_{j-1}, partials of c_i = q_i^T y for i <= j;
+//   k_lz_update: c = Q_j^T y, alpha_j = c_j, w = y - Q_j c, partial ||w||^2.
+// lz rows: 0..k-1 = q_j; k = y; k+1 = w.  A zero (or non-finite) beta ends
+// the process (lz_m = steps taken); later launches do nothing.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double sum_partials(const double *__restrict__ red, int nb) {
+constexpr int kLzStride = 16;  // partials per block (>= kLanczos)
+static_assert(kLanczos <= kLzStride, "Lanczos partial stride");
+
+__device__ __forceinline__ double sum_partials(const double *__restrict__ red, int nb, int stride) {
   double v = 0.0;
-  for (int q = 0; q < nb; ++q) v += red[q * kRedWidth];
+  for (int q = 0; q < nb; ++q) v += red[q * stride];
   return v;
 }
 
 __global__ void __launch_bounds__(NT) k_lz_matvec(const double *__restrict__ Z, int64_t ldz, int n,
                                                   int j, double *lz,
                                                   const double *__restrict__ wpart, int nbp,
-                                                  double *__restrict__ apart, Params *prm) {
+                                                  double *__restrict__ cpart, Params *prm) {
   __shared__ double sh[32];
-  __shared__ double s_scale;
-  double *qj = lz + (int64_t)(j & 1) * n;
-  double *y = lz + 2 * (int64_t)n;
-  const double *w = lz + 3 * (int64_t)n;
+  __shared__ double s_scale, s_beta;
+  double *Q = lz;
+  double *y = lz + (int64_t)kLanczos * n;
+  const double *w = lz + (int64_t)(kLanczos + 1) * n;
   if (j > 0 && prm->lz_m < j) return;  // ended earlier
   if (threadIdx.x == 0) {
     if (j == 0) {
       s_scale = 1.0 / sqrt((double)n);
+      s_beta = 0.0;
       if (blockIdx.x == 0) prm->lz_m = kLanczos;
     } else {
-      const double beta = sqrt(sum_partials(wpart, nbp));
+      const double beta = sqrt(sum_partials(wpart, nbp, kRedWidth));
       if (blockIdx.x == 0) prm->lz_beta[j - 1] = beta;
+      s_beta = beta;
       s_scale = (beta > 0.0 && isfinite(beta)) ? 1.0 / beta : 0.0;
       if (s_scale == 0.0 && blockIdx.x == 0) prm->lz_m = j;
     }
   }
   __syncthreads();
-  const double sc = s_scale;
+  const double sc = s_scale, be = s_beta;
   if (sc == 0.0) return;
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * WPB;
-  double part = 0.0;
+  double part[kLanczos];
+#pragma unroll
+  for (int i = 0; i < kLanczos; ++i) part[i] = 0.0;
   for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
     const double *zr = Z + (int64_t)row * ldz;
     double acc = 0.0;
@@ -1314,36 +1321,42 @@ __global__ void __launch_bounds__(NT) k_lz_matvec(const double *__restrict__ Z, 
     acc = warp_sum(acc) * sc;
     if (lane == 0) {
       const double q = j == 0 ? sc : w[row] * sc;
-      qj[row] = q;
-      y[row] = acc;
-      part = fma(q, acc, part);
+      Q[(int64_t)j * n + row] = q;
+      double yv = acc;
+      if (j > 0) yv -= be * Q[(int64_t)(j - 1) * n + row];
+      y[row] = yv;
+#pragma unroll
+      for (int i = 0; i < kLanczos; ++i) {
+        if (i < j) part[i] = fma(Q[(int64_t)i * n + row], yv, part[i]);
+        else if (i == j) part[i] = fma(q, yv, part[i]);
+      }
     }
   }
-  part = block_reduce(part, sh, 0);
-  if (threadIdx.x == 0) apart[blockIdx.x * kRedWidth] = part;
+  for (int i = 0; i <= j; ++i) {
+    const double v = block_reduce(part[i], sh, 0);
+    if (threadIdx.x == 0) cpart[blockIdx.x * kLzStride + i] = v;
+  }
 }
 
 __global__ void __launch_bounds__(NT) k_lz_update(int n, int j, double *lz,
-                                                  const double *__restrict__ apart, int nb,
+                                                  const double *__restrict__ cpart, int nb,
                                                   double *__restrict__ wpart_out, Params *prm) {
   __shared__ double sh[32];
-  __shared__ double s_alpha, s_beta;
+  __shared__ double s_c[kLanczos];
   if (prm->lz_m <= j) return;
-  const double *qj = lz + (int64_t)(j & 1) * n;
-  const double *qm = lz + (int64_t)((j + 1) & 1) * n;  // q_{j-1}
-  const double *y = lz + 2 * (int64_t)n;
-  double *w = lz + 3 * (int64_t)n;
-  if (threadIdx.x == 0) {
-    s_alpha = sum_partials(apart, nb);
-    s_beta = j > 0 ? prm->lz_beta[j - 1] : 0.0;
-    if (blockIdx.x == 0) prm->lz_alpha[j] = s_alpha;
+  const double *Q = lz;
+  const double *y = lz + (int64_t)kLanczos * n;
+  double *w = lz + (int64_t)(kLanczos + 1) * n;
+  if (threadIdx.x <= j) {
+    const double c = sum_partials(cpart + threadIdx.x, nb, kLzStride);
+    s_c[threadIdx.x] = c;
+    if (blockIdx.x == 0 && threadIdx.x == j) prm->lz_alpha[j] = c;
   }
   __syncthreads();
-  const double al = s_alpha, be = s_beta;
   double part = 0.0;
   for (int r = blockIdx.x * NT + threadIdx.x; r < n; r += gridDim.x * NT) {
-    double v = y[r] - al * qj[r];
-    if (j > 0) v -= be * qm[r];
+    double v = y[r];
+    for (int i = 0; i <= j; ++i) v -= s_c[i] * Q[(int64_t)i * n + r];
     w[r] = v;
     part = fma(v, v, part);
   }
@@ -1373,7 +1386,8 @@ __global__ void k_lz_final(const double *__restrict__ wpart, int nb, Params *prm
   const double *al = prm->lz_alpha;
   double be[16];
   for (int i = 0; i + 1 < m; ++i) be[i] = prm->lz_beta[i];
-  const double blast = m == kLanczos ? sqrt(sum_partials(wpart, nb)) : prm->lz_beta[m - 1];
+  const double blast =
+      m == kLanczos ? sqrt(sum_partials(wpart, nb, kRedWidth)) : prm->lz_beta[m - 1];
   double lo = INFINITY, hi = -INFINITY;
   for (int i = 0; i < m; ++i) {
     const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
@@ -1563,8 +1577,13 @@ cudaError_t launch_nce_interval(cudaStream_t s, const Workspace &ws, const doubl
   const int nbm = red_blocks(n, ws.num_sms);
   int nbu = (n + NT - 1) / NT;
   if (nbu > 2 * ws.num_sms) nbu = 2 * ws.num_sms;
-  double *apart = slot(ws, SLOT_EXPAND);
-  double *wp[2] = {slot(ws, SLOT_SDDMM), slot(ws, SLOT_RESID)};
+  // c partials (kLzStride per block) from the start of the reduction array,
+  // ||w||^2 partials in the last two slots (no overlap: 4 x 152 x 16 doubles
+  // < 4 slots)
+  double *apart = ws.red;
+  double *wp[2] = {slot(ws, SLOT_RESID), slot(ws, SLOT_MISC)};
+  static_assert((size_t)kMaxRedBlocks * kLzStride <= (size_t)SLOT_RESID * kMaxRedBlocks * kRedWidth,
+                "Lanczos partials overlap");
   for (int j = 0; j < kLanczos; ++j) {
     k_lz_matvec<<<nbm, NT, 0, s>>>(Z, ldz, n, j, ws.lz, wp[(j + 1) & 1], nbu, apart, ws.prm);
     PF_LAUNCHED();

@@ -20,6 +20,7 @@
 //                      (warp w owns TMEM lanes 32w..32w+31 = its rows).
 // Every wait is bounded (about 2 s of %globaltimer); on expiry the CTA sets
 // flags bit 3 in the context parameters, skips the rest and frees its TMEM.
+#include <climits>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -321,31 +322,36 @@ __global__ void k_f32_to_f64(const float *__restrict__ src, int64_t total, doubl
 // Low-precision shadow of the max-cut iteration matrix (Eq. (PFAM1)):
 //     Z_lp[i][j] = ( sum_l W[i][l] V[j][l] - t C_ij - [i == j] lam_i ) / s
 // with W = V diag(max(theta, 0)) (fp32, K-padded to KP columns, zero beyond
-// r+).  The write of Z_lp (n^2 elements) bounds the kernel, so each CTA owns
-// one 128-row block and walks a range of 128-column tiles:
-//   warp 0 (one lane): TMA of the W tile once, then V tiles through a
-//                      2-stage ring;
+// r+).  The write of Z_lp (n^2 elements) bounds the kernel.  The grid is
+// persistent (two CTAs per SM); the 128 x 128 output tiles, numbered row
+// block by row block, are split into equal contiguous ranges, one per CTA:
+//   warp 0 (one lane): TMA of the W tile of the current row block (reloaded
+//                      when the range crosses into the next row block, once
+//                      the MMAs that read the old one have completed), and of
+//                      the V tiles through a 2-stage ring;
 //   warp 1 (one lane): tcgen05.mma kind::tf32 (M = N = 128, K = KP) into one
 //                      of two 128-column TMEM accumulators;
-//   warps 2-5        : epilogue of the previous tile (TMEM lanes = rows),
-//                      sparse and diagonal parts, scale, bf16/fp32 stores;
-//                      they release the accumulator through an mbarrier.
+//   warps 2-9        : epilogue of the previous tile, two warps per TMEM lane
+//                      quarter (rows), each taking 64 of the 128 columns:
+//                      sparse and diagonal parts, bf16/fp32 stores; they
+//                      release the accumulator through an mbarrier.
 // ---------------------------------------------------------------------------
 constexpr int EX_TILE = 128;
-constexpr int EX_THREADS = 192;
+constexpr int EX_EPI_WARPS = 8;
+constexpr int EX_THREADS = 64 + 32 * EX_EPI_WARPS;
 constexpr int EX_VST = 2;
 
 template <int KP, bool F32OUT>
-__global__ void __launch_bounds__(EX_THREADS)
+__global__ void __launch_bounds__(EX_THREADS, 2)
     k_tc_expand(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmV,
-                int n, int tiles_per_cta, const int32_t *__restrict__ rowptr,
+                int n, const int32_t *__restrict__ rowptr,
                 const int32_t *__restrict__ colind, const double *__restrict__ vals,
                 const double *__restrict__ lam, void *Zlp, int64_t ldz, Params *prm) {
   constexpr int KB = KP / 32;                    // 128-byte k-blocks of tf32
   constexpr int TILE_BYTES = EX_TILE * TC_ROWB;  // 16 KB per operand per k-block
   constexpr int OP_BYTES = KB * TILE_BYTES;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t w_full;
+  __shared__ __align__(8) uint64_t w_full, w_empty;
   __shared__ __align__(8) uint64_t v_full[EX_VST], v_empty[EX_VST];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
@@ -354,21 +360,22 @@ __global__ void __launch_bounds__(EX_THREADS)
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t sW = base, sV = base + OP_BYTES;
   const int T = (n + EX_TILE - 1) / EX_TILE;
-  const int i0 = blockIdx.y * EX_TILE;
-  const int t_begin = blockIdx.x * tiles_per_cta;
-  const int t_end = min(T, t_begin + tiles_per_cta);
-  const int cnt = max(0, t_end - t_begin);
+  const int64_t ntiles = (int64_t)T * T;
+  const int64_t g_begin = ntiles * blockIdx.x / gridDim.x;
+  const int64_t g_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int cnt = (int)(g_end - g_begin);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     mbar_init(smem_u32(&w_full), 1);
+    mbar_init(smem_u32(&w_empty), 1);
     for (int s = 0; s < EX_VST; ++s) {
       mbar_init(smem_u32(&v_full[s]), 1);
       mbar_init(smem_u32(&v_empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
-      mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrival per epilogue warp
+      mbar_init(smem_u32(&acc_empty[b]), EX_EPI_WARPS);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -386,28 +393,44 @@ __global__ void __launch_bounds__(EX_THREADS)
 
   if (warp == 0) {
     if (lane == 0 && cnt > 0) {
-      const uint32_t wb = smem_u32(&w_full);
-      mbar_expect_tx(wb, OP_BYTES);
-#pragma unroll
-      for (int kb = 0; kb < KB; ++kb) tma_load_2d(sW + kb * TILE_BYTES, &tmW, wb, kb * 32, i0);
+      int cur_rb = -1, wloads = 0;
       for (int t = 0; t < cnt; ++t) {
+        const int64_t g = g_begin + t;
+        const int rb = (int)(g / T), ct = (int)(g - (int64_t)rb * T);
+        if (rb != cur_rb) {
+          // the MMAs that read the previous W tile have completed
+          if (wloads > 0 && !mbar_wait(smem_u32(&w_empty), (wloads - 1) & 1, &abort_flag)) break;
+          const uint32_t wb = smem_u32(&w_full);
+          mbar_expect_tx(wb, OP_BYTES);
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb)
+            tma_load_2d(sW + kb * TILE_BYTES, &tmW, wb, kb * 32, rb * EX_TILE);
+          ++wloads;
+          cur_rb = rb;
+        }
         const int s = t % EX_VST;
         if (t >= EX_VST && !mbar_wait(smem_u32(&v_empty[s]), ((t / EX_VST) - 1) & 1, &abort_flag))
           break;
         const uint32_t vb = smem_u32(&v_full[s]);
         mbar_expect_tx(vb, OP_BYTES);
-        const int j0 = (t_begin + t) * EX_TILE;
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb)
-          tma_load_2d(sV + s * OP_BYTES + kb * TILE_BYTES, &tmV, vb, kb * 32, j0);
+          tma_load_2d(sV + s * OP_BYTES + kb * TILE_BYTES, &tmV, vb, kb * 32, ct * EX_TILE);
       }
     }
   } else if (warp == 1) {
     if (lane == 0 && cnt > 0) {
       constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
                                  ((uint32_t)(EX_TILE >> 3) << 17) | ((uint32_t)(EX_TILE >> 4) << 24);
-      bool ok = mbar_wait(smem_u32(&w_full), 0, &abort_flag);
-      for (int t = 0; ok && t < cnt; ++t) {
+      int cur_rb = -1, wloads = 0;
+      for (int t = 0; t < cnt; ++t) {
+        const int64_t g = g_begin + t;
+        const int rb = (int)(g / T);
+        if (rb != cur_rb) {
+          if (!mbar_wait(smem_u32(&w_full), wloads & 1, &abort_flag)) break;
+          ++wloads;
+          cur_rb = rb;
+        }
         const int s = t % EX_VST, b = t & 1;
         if (!mbar_wait(smem_u32(&v_full[s]), (t / EX_VST) & 1, &abort_flag)) break;
         if (t >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), ((t >> 1) - 1) & 1, &abort_flag)) break;
@@ -423,59 +446,83 @@ __global__ void __launch_bounds__(EX_THREADS)
         }
         mma_commit(smem_u32(&v_empty[s]));
         mma_commit(smem_u32(&acc_full[b]));
+        const bool last_of_rb = t + 1 == cnt || (int)((g + 1) / T) != rb;
+        if (last_of_rb) mma_commit(smem_u32(&w_empty));
       }
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter (warp % 4) = rows of the block
+    // epilogue warps 2..9: TMEM lane quarter (warp % 4) = rows of the block,
+    // column half (warp - 2) / 4 of every tile
     const int quarter = warp & 3;
-    const int row = i0 + quarter * 32 + lane;
-    const bool in = row < n;
-    const float t = (float)prm->t;
-    const float inv_s = (float)(1.0 / prm->lp_scale);
-    const float lrow = in ? (float)lam[row] : 0.f;
-    int e = 0, e_end = 0;
-    if (in && cnt > 0) {
-      int lo = rowptr[row], hi = rowptr[row + 1];
-      e_end = hi;
-      const int j_first = t_begin * EX_TILE;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (colind[mid] < j_first) lo = mid + 1;
-        else hi = mid;
-      }
-      e = lo;
-    }
+    const int chalf = (warp - 2) >> 2;
+    const float ts = (float)(prm->t / prm->lp_scale);
+    const double inv_s = 1.0 / prm->lp_scale;
+    int cur_rb = -1, row = 0;
+    bool in = false;
+    float ls = 0.f;
+    int e = 0, e_end = 0, ncol = INT_MAX;
+    float nval = 0.f;
     for (int tt = 0; tt < cnt; ++tt) {
+      const int64_t g = g_begin + tt;
+      const int rb = (int)(g / T), ct = (int)(g - (int64_t)rb * T);
+      const int j0 = ct * EX_TILE + chalf * 64;  // first column of this warp's half
+      if (rb != cur_rb) {
+        // new row block: row state and the first sparse entry at or after j0
+        cur_rb = rb;
+        row = rb * EX_TILE + quarter * 32 + lane;
+        in = row < n;
+        ls = in ? (float)(lam[row] * inv_s) : 0.f;
+        ncol = INT_MAX;
+        if (in) {
+          int lo = rowptr[row], hi = rowptr[row + 1];
+          e_end = hi;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (colind[mid] < j0) lo = mid + 1;
+            else hi = mid;
+          }
+          e = lo;
+          if (e < e_end) {
+            ncol = colind[e];
+            nval = ts * (float)vals[e];
+          }
+        }
+      }
       const int b = tt & 1;
       const bool have = mbar_wait(smem_u32(&acc_full[b]), (tt >> 1) & 1, &abort_flag);
       __syncwarp();
       if (!have) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int j0 = (t_begin + tt) * EX_TILE;
-      const uint32_t taddr = tmem + (uint32_t)(b * EX_TILE) + ((uint32_t)(quarter * 32) << 16);
-      const float ts = t * inv_s, ls = lrow * inv_s;
+      const uint32_t taddr = tmem + (uint32_t)(b * EX_TILE + chalf * 64) +
+                             ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-      for (int c0 = 0; c0 < EX_TILE; c0 += 32) {
+      for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
         tmem_ld32(taddr + c0, v);
-        if (!in || j0 + c0 >= n) continue;
-        // sparse part (a few entries per row and tile) and the diagonal
-        while (e < e_end) {
-          const int col = colind[e];
-          if (col >= j0 + c0 + 32) break;
-          const int q = col - (j0 + c0);
-          const float tc = ts * (float)vals[e];
+        const int jc = j0 + c0;
+        if (!in || jc >= n) continue;
+        // sparse entries before this chunk belong to the other column half
+        while (ncol < jc) {
+          ++e;
+          ncol = e < e_end ? colind[e] : INT_MAX;
+          nval = e < e_end ? ts * (float)vals[e] : 0.f;
+        }
+        while (ncol < jc + 32) {
+          const int q = ncol - jc;
+          const float tc = nval;
 #pragma unroll
           for (int k = 0; k < 32; ++k) v[k] -= (k == q) ? tc : 0.f;
           ++e;
+          ncol = e < e_end ? colind[e] : INT_MAX;
+          nval = e < e_end ? ts * (float)vals[e] : 0.f;
         }
-        const int dj = row - (j0 + c0);
+        const int dj = row - jc;
         if (dj >= 0 && dj < 32) {
 #pragma unroll
           for (int k = 0; k < 32; ++k) v[k] -= (k == dj) ? ls : 0.f;
         }
-        const int64_t off = (int64_t)row * ldz + j0 + c0;
-        const int valid = min(32, n - (j0 + c0));
+        const int64_t off = (int64_t)row * ldz + jc;
+        const int valid = min(32, n - jc);
         if (F32OUT) {
           float *zp = reinterpret_cast<float *>(Zlp) + off;
           if (valid == 32 && ((off & 3) == 0)) {
@@ -691,18 +738,14 @@ cudaError_t launch_tc_expand(cudaStream_t s, const Workspace &ws, bool f32out, c
   CUtensorMap mw, mv;
   if ((e = encode_map(&mw, ws.Wf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
   if ((e = encode_map(&mv, ws.Vf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
-  // one CTA per (row block, range of column tiles): about two CTAs per SM
+  // persistent: two CTAs per SM over equal contiguous ranges of the T x T tiles
   const int T = (n + EX_TILE - 1) / EX_TILE;
-  int splits = (2 * ws.num_sms) / T;
-  if (splits < 1) splits = 1;
-  if (splits > T) splits = T;
-  const int tiles_per = (T + splits - 1) / splits;
-  splits = (T + tiles_per - 1) / tiles_per;
-  const dim3 grid(splits, T);
+  const int64_t ntiles = (int64_t)T * T;
+  const int grid = (int)(ntiles < 2 * ws.num_sms ? ntiles : 2 * ws.num_sms);
   const size_t smem = expand_smem_bytes(KP);
 #define PF_EX_LAUNCH(KPV, F32)                                                                  \
-  k_tc_expand<KPV, F32><<<grid, EX_THREADS, smem, s>>>(mw, mv, n, tiles_per, rowptr, colind,   \
-                                                       vals, lam, Zlp, ldz, ws.prm)
+  k_tc_expand<KPV, F32><<<grid, EX_THREADS, smem, s>>>(mw, mv, n, rowptr, colind, vals, lam,  \
+                                                       Zlp, ldz, ws.prm)
   if (KP == 32) {
     if (f32out) PF_EX_LAUNCH(32, true);
     else PF_EX_LAUNCH(32, false);
