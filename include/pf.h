@@ -82,6 +82,16 @@ typedef struct {
   double eta;           /* interval parameter of Sec. 4.1 (0 < eta < 1), e.g. 0.1    */
   int32_t precision;    /* pf_precision of the filter products                       */
   int32_t adaptive;     /* nonzero: raise degree/precision when the KKT stalls        */
+  /* Block width rule (Sec. 4.2), FP64 contexts: with adapt_guard > 0, after
+   * every adapt_every-th step of a problem its active width becomes
+   * min(p, max(p_min, r_+ + adapt_guard)) rounded up to a multiple of 8,
+   * r_+ the positive Ritz count of that step (p above is the maximum and
+   * sizes the workspace).  Shrinking drops trailing Ritz columns (their
+   * Ritz values are <= 0); growing takes the problem's guard columns of the
+   * same index.  0 disables the rule.                                       */
+  int32_t p_min;
+  int32_t adapt_guard;
+  int32_t adapt_every;
 } pf_options;
 
 /*
@@ -165,6 +175,10 @@ typedef struct {
   int32_t accel_l;       /* NCE extrapolation window l (0 = off)     */
   double accel_lam;      /* NCE extrapolation regulariser (relative) */
   double *hist;          /* NCE (accel_l + 2) x n window of iterates  */
+  int32_t p_active;      /* active block width; 0 on entry to pf_problem_init selects p;
+                            maintained by the library under the width rule */
+  const double *guard;   /* n x p random columns for width growth (ldg), read only */
+  int64_t ldg;
 } pf_problem;
 
 /* Per-step report (host struct).  MAXCUT: obj = <C, X~>, pinf/dinf/gap as in

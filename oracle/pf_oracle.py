@@ -200,6 +200,46 @@ def choose_b(a: float, theta_prev: Optional[np.ndarray], ub: float, eta: float =
 
 
 # ---------------------------------------------------------------------------
+# Block width (Sec. 4.2): when all positive eigenpairs are wanted, the number
+# of positive Ritz values of the previous iteration estimates the dimension,
+# and guard vectors are added.  Reading R13: after every `every`-th step the
+# width becomes min(p_max, max(p_min, r_+ + guard)) rounded up to a multiple
+# of `mult`; shrinking keeps the leading columns (the Ritz basis is sorted by
+# decreasing Ritz value, so only columns with non-positive Ritz values are
+# dropped), growing appends the same-index columns of a caller-drawn random
+# block and repeats the smallest previous Ritz value for them (the iterate,
+# held as factors of its positive part, is unchanged either way).
+# ---------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class AdaptiveWidth:
+    guard: int
+    p_min: int
+    p_max: int
+    every: int
+    block: np.ndarray          # n x p_max random columns for growth
+    mult: int = 8
+
+    def width(self, r_plus: int) -> int:
+        want = r_plus + self.guard
+        want = ((want + self.mult - 1) // self.mult) * self.mult
+        return int(min(self.p_max, max(self.p_min, want)))
+
+
+def adapt_width(U: np.ndarray, theta_prev: np.ndarray, r_plus: int, rule: AdaptiveWidth):
+    p = U.shape[1]
+    p_new = rule.width(r_plus)
+    if p_new < p:
+        assert np.all(theta_prev[p_new:] <= 0.0), "would drop a positive Ritz pair"
+        return U[:, :p_new].copy(), theta_prev[:p_new].copy()
+    if p_new > p:
+        U = np.hstack([U, rule.block[:, p:p_new]])
+        theta_prev = np.concatenate([theta_prev, np.full(p_new - p, theta_prev[-1])])
+    return U, theta_prev
+
+
+# ---------------------------------------------------------------------------
 # Max-cut SDP by PFAM / DRS (Sec. 2.3)
 # ---------------------------------------------------------------------------
 
@@ -301,15 +341,18 @@ def maxcut_pfam_step(C: sp.csr_matrix, st: MaxCutState, t: float, degree: int,
 
 
 def maxcut_solve(C: sp.csr_matrix, U0_raw: np.ndarray, degree: int, iters: int,
-                 t: Optional[float] = None, exact: bool = False, tol: float = 0.0):
+                 t: Optional[float] = None, exact: bool = False, tol: float = 0.0,
+                 adapt: Optional[AdaptiveWidth] = None):
     t = maxcut_step_size(C) if t is None else t
     st = maxcut_init(C, U0_raw, t)
     hist = []
-    for _ in range(iters):
+    for k in range(iters):
         st, info = maxcut_pfam_step(C, st, t, degree, exact=exact)
         hist.append(info)
         if tol > 0 and info.kkt <= tol:
             break
+        if adapt is not None and (k + 1) % adapt.every == 0:
+            st.U, st.theta_prev = adapt_width(st.U, st.theta_prev, info.r_plus, adapt)
     return st, hist
 
 
@@ -402,15 +445,18 @@ def completion_pfpg_step(Om: sp.csr_matrix, st: CompletionState, mu: float, t: f
 
 
 def completion_solve(omega, U0_raw, mu: float, t: float, degree: int, iters: int,
-                     exact: bool = False, tol: float = 0.0):
+                     exact: bool = False, tol: float = 0.0,
+                     adapt: Optional[AdaptiveWidth] = None):
     Om = omega_matrix(omega)
     st = completion_init(omega.n, U0_raw)
     hist = []
-    for _ in range(iters):
+    for k in range(iters):
         st, info = completion_pfpg_step(Om, st, mu, t, degree, exact=exact)
         hist.append(info)
         if tol > 0 and info.kkt <= tol:
             break
+        if adapt is not None and (k + 1) % adapt.every == 0:
+            st.U, st.theta_prev = adapt_width(st.U, st.theta_prev, info.r_plus, adapt)
     return st, hist
 
 
@@ -547,18 +593,21 @@ def rna_combination(points, lam_rel: float):
 
 
 def nce_solve(G, U0_raw, degree: int, iters: int, exact: bool = False, tol: float = 0.0,
-              accel_l: int = 0, accel_lam: float = 1e-10):
+              accel_l: int = 0, accel_lam: float = 1e-10,
+              adapt: Optional[AdaptiveWidth] = None):
     """Filtered (or exact) gradient method on the NCE dual; with accel_l > 0
     every l+2 iterates are combined by rna_combination and the iteration
     restarts from the combination (Sec. 4.3)."""
     st = nce_init(G, U0_raw)
     hist = []
     window = [st.x.copy()]
-    for _ in range(iters):
+    for k in range(iters):
         st, info = nce_step(G, st, degree, exact=exact)
         hist.append(info)
         if tol > 0 and info.rel <= tol:
             break
+        if adapt is not None and (k + 1) % adapt.every == 0:
+            st.U, st.theta_prev = adapt_width(st.U, st.theta_prev, info.r_plus, adapt)
         if accel_l > 0:
             window.append(st.x.copy())
             if len(window) == accel_l + 2:

@@ -38,7 +38,8 @@ PF_PROBLEM_NCE = 2
 class pf_options(C.Structure):
     _fields_ = [("p", C.c_int32), ("degree", C.c_int32), ("degree_max", C.c_int32),
                 ("q", C.c_int32), ("eta", C.c_double), ("precision", C.c_int32),
-                ("adaptive", C.c_int32)]
+                ("adaptive", C.c_int32), ("p_min", C.c_int32), ("adapt_guard", C.c_int32),
+                ("adapt_every", C.c_int32)]
 
 
 class pf_operator(C.Structure):
@@ -61,7 +62,8 @@ class pf_problem(C.Structure):
                 ("Z", C.c_void_p), ("ldz", C.c_int64),
                 ("Z_lp", C.c_void_p), ("ldz_lp", C.c_int64),
                 ("lam", C.c_void_p), ("S", C.c_void_p), ("iter", C.c_int64),
-                ("accel_l", C.c_int32), ("accel_lam", C.c_double), ("hist", C.c_void_p)]
+                ("accel_l", C.c_int32), ("accel_lam", C.c_double), ("hist", C.c_void_p),
+                ("p_active", C.c_int32), ("guard", C.c_void_p), ("ldg", C.c_int64)]
 
 
 class pf_iter_info(C.Structure):

@@ -31,6 +31,7 @@ struct pf_ctx {
   pf_problem gkey;
   int gdegree;
   bool glp;
+  int gp;
   bool have_graph;
   // adaptive ladder state (degree and low-precision filter currently used)
   int cur_degree;
@@ -38,6 +39,13 @@ struct pf_ctx {
 };
 
 namespace {
+
+bool width_rule_on(const pf_ctx *ctx) { return ctx->opt.adapt_guard > 0; }
+
+// Active block width of a problem (validated by check_problem).
+int active_width(const pf_ctx *ctx, const pf_problem *pr) {
+  return pr->p_active > 0 ? pr->p_active : ctx->p;
+}
 
 pf_status set_err(pf_ctx *ctx, pf_status s, const char *fmt, ...) {
   if (ctx) {
@@ -131,7 +139,7 @@ pf_status apply(pf_ctx *ctx, const Op &op, const double *X, int64_t ldx, const d
 
 // Q = orth(Y) by CholQR2 (a third pass follows a shifted first pass).
 pf_status cholqr2(pf_ctx *ctx, const double *Y, int64_t ldy, double *U, int64_t ldu, int n) {
-  const int p = ctx->p;
+  const int p = ctx->ws.p;  // active width
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
   int nb = 0;
@@ -150,7 +158,7 @@ pf_status cholqr2(pf_ctx *ctx, const double *Y, int64_t ldy, double *U, int64_t 
 // Low-precision filter (tensor cores): fp32 recurrence, bf16/tf32 operands,
 // then CholQR2 in FP64.
 pf_status filter_core_lp(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
-  const int p = ctx->p;
+  const int p = ctx->ws.p;  // active width
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
   const bool tf32 = ctx->opt.precision == PF_PREC_TF32;
@@ -171,7 +179,7 @@ pf_status filter_core_lp(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int 
 // Low-precision context, low-rank + sparse operator: fp32 products on the
 // CUDA cores, fp32 recurrence, then CholQR2 in FP64.
 pf_status filter_core_lp_sparse(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
-  const int p = ctx->p;
+  const int p = ctx->ws.p;  // active width
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
   const float *Uf32 = nullptr;
@@ -193,7 +201,7 @@ pf_status filter_core_lp_sparse(pf_ctx *ctx, const Op &op, double *U, int64_t ld
 
 // U <- orth(rho(op) U) with the interval already in the device parameters.
 pf_status filter_core(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
-  const int p = ctx->p;
+  const int p = ctx->ws.p;  // active width
   if (op.kind == PF_OP_LOWRANK_SPARSE && ctx->cur_lp)
     return filter_core_lp_sparse(ctx, op, U, ldu, degree);
   if (op.kind == PF_OP_DENSE && op.A_lp != nullptr && ctx->opt.precision != PF_PREC_FP64)
@@ -211,7 +219,7 @@ pf_status filter_core(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int deg
 
 pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, double *V, int64_t ldv,
                   double *theta, double *resid) {
-  const int p = ctx->p;
+  const int p = ctx->ws.p;  // active width
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
   PF_TRY(apply(ctx, op, Q, ldq, nullptr, 0, ws.W, p, MODE_PLAIN));
@@ -229,6 +237,16 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
   if (pr->n < p || pr->n > ctx->n_max)
     return set_err(ctx, PF_ERR_INVALID_ARG, "problem n=%lld outside [p=%d, n_max=%lld]",
                    (long long)pr->n, p, (long long)ctx->n_max);
+  if (pr->p_active < 0 || pr->p_active > p)
+    return set_err(ctx, PF_ERR_INVALID_ARG, "p_active=%d outside [0, p=%d]", pr->p_active, p);
+  if (width_rule_on(ctx)) {
+    if (ctx->opt.precision != PF_PREC_FP64)
+      return set_err(ctx, PF_ERR_UNSUPPORTED, "the block width rule runs in an FP64 context");
+    if (ctx->opt.p_min < 1 || ctx->opt.p_min > p || ctx->opt.adapt_every < 1)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "width rule needs 1 <= p_min <= p, adapt_every >= 1");
+    if (!pr->guard || pr->ldg < p)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "width rule needs guard columns (ldg >= p)");
+  }
   if (pr->kind != PF_PROBLEM_NCE &&
       (!pr->rowptr || !pr->colind || pr->nnz < 0 || pr->nnz > INT32_MAX))
     return set_err(ctx, PF_ERR_INVALID_ARG, "problem needs a CSR matrix (rowptr, colind, nnz)");
@@ -272,7 +290,7 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
 
 // One PFAM / PFPG step, enqueued only (graph-capturable).
 pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
-  const int p = ctx->p;
+  const int p = ctx->ws.p;  // active width
   const int n = (int)pr->n;
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
@@ -405,14 +423,27 @@ bool same_problem(const pf_problem &a, const pf_problem &b) {
          a.mu == b.mu && a.U == b.U && a.ldu == b.ldu && a.V == b.V && a.ldv == b.ldv &&
          a.theta == b.theta && a.Z == b.Z && a.ldz == b.ldz && a.lam == b.lam && a.S == b.S &&
          a.Z_lp == b.Z_lp && a.ldz_lp == b.ldz_lp && a.accel_l == b.accel_l &&
-         a.accel_lam == b.accel_lam && a.hist == b.hist;
+         a.accel_lam == b.accel_lam && a.hist == b.hist && a.p_active == b.p_active &&
+         a.guard == b.guard && a.ldg == b.ldg;
 }
+
+bool graph_matches(const pf_ctx *ctx, const pf_problem &pr) {
+  return ctx->have_graph && same_problem(ctx->gkey, pr) && ctx->gdegree == ctx->cur_degree &&
+         ctx->glp == ctx->cur_lp && ctx->gp == ctx->ws.p;
+}
+
+
 
 }  // namespace
 
 extern "C" {
 
 static pf_status capture_step(pf_ctx *ctx, pf_problem *pr);
+// Width rule of Sec. 4.2 after the step that advanced pr->iter to a multiple
+// of adapt_every: r_+ of that step plus the guard vectors, rounded up to a
+// multiple of 8, clamped to [p_min, p].  Synchronises the stream (r_+ is
+// read on the host).
+static pf_status apply_width_rule(pf_ctx *ctx, pf_problem *pr);
 
 pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx **out) {
   if (!out) return PF_ERR_INVALID_ARG;
@@ -550,6 +581,7 @@ pf_status pf_destroy(pf_ctx *ctx) {
 pf_status pf_filter(pf_ctx *ctx, const pf_operator *op, double a, double b, int32_t degree,
                     double *U, int64_t ldu) {
   if (!ctx) return PF_ERR_INVALID_ARG;
+  ctx->ws.p = ctx->p;
   Op o;
   PF_TRY(make_op(ctx, op, &o));
   if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
@@ -563,6 +595,7 @@ pf_status pf_filter(pf_ctx *ctx, const pf_operator *op, double a, double b, int3
 pf_status pf_rayleigh_ritz(pf_ctx *ctx, const pf_operator *op, const double *Q, int64_t ldq,
                            double *V, int64_t ldv, double *theta, double *resid) {
   if (!ctx) return PF_ERR_INVALID_ARG;
+  ctx->ws.p = ctx->p;
   Op o;
   PF_TRY(make_op(ctx, op, &o));
   if (!Q || ldq < ctx->p || !V || ldv < ctx->p || !theta)
@@ -573,6 +606,7 @@ pf_status pf_rayleigh_ritz(pf_ctx *ctx, const pf_operator *op, const double *Q, 
 pf_status pf_apply(pf_ctx *ctx, const pf_operator *op, const double *X, int64_t ldx, double *Y,
                    int64_t ldy) {
   if (!ctx) return PF_ERR_INVALID_ARG;
+  ctx->ws.p = ctx->p;
   Op o;
   PF_TRY(make_op(ctx, op, &o));
   if (!X || !Y || X == Y || ldx < ctx->p || ldy < ctx->p)
@@ -598,6 +632,8 @@ int64_t pf_kernel_launch_count(void) { return g_launches.load(std::memory_order_
 pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
+  if (pr->p_active == 0) pr->p_active = ctx->p;
+  ctx->ws.p = ctx->p;  // the fills below cover every column
   const int n = (int)pr->n, p = ctx->p;
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
@@ -637,6 +673,7 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
   PF_CUDA(cudaStreamSynchronize(s));
   PF_CUDA(cudaGetLastError());
   pr->iter = 0;
+  ctx->ws.p = pr->p_active;
   ctx->cur_degree = ctx->opt.degree;
   ctx->cur_lp = ctx->opt.precision != PF_PREC_FP64;
   return PF_OK;
@@ -645,6 +682,7 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
 pf_status pf_prox_step(pf_ctx *ctx, pf_problem *pr, pf_iter_info *info) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
+  ctx->ws.p = active_width(ctx, pr);
   PF_TRY(step_core(ctx, pr));
   pr->iter += 1;
   if (info) {
@@ -655,6 +693,24 @@ pf_status pf_prox_step(pf_ctx *ctx, pf_problem *pr, pf_iter_info *info) {
     if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
     if (h.flags & 4) return set_err(ctx, PF_ERR_NAN, "non-finite Ritz value");
   }
+  if (width_rule_on(ctx) && pr->iter % ctx->opt.adapt_every == 0)
+    PF_TRY(apply_width_rule(ctx, pr));
+  return PF_OK;
+}
+
+static pf_status apply_width_rule(pf_ctx *ctx, pf_problem *pr) {
+  Params h;
+  PF_TRY(read_params(ctx, &h));
+  const int p_old = active_width(ctx, pr);
+  int want = h.r_plus + ctx->opt.adapt_guard;
+  want = ((want + 7) / 8) * 8;
+  if (want < ctx->opt.p_min) want = ctx->opt.p_min;
+  if (want > ctx->p) want = ctx->p;
+  if (want > p_old)
+    PF_CUDA(launch_grow_block(ctx->stream, ctx->ws, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta,
+                              (int)pr->n, p_old, want, pr->guard, pr->ldg));
+  pr->p_active = want;
+  ctx->ws.p = want;
   return PF_OK;
 }
 
@@ -670,11 +726,14 @@ pf_status pf_enqueue_steps(pf_ctx *ctx, pf_problem *pr, int64_t n_steps) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
   if (n_steps < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "n_steps must be >= 0");
+  if (width_rule_on(ctx))
+    return set_err(ctx, PF_ERR_UNSUPPORTED, "the block width rule needs host decisions "
+                                            "(pf_prox_step / pf_solve)");
+  ctx->ws.p = active_width(ctx, pr);
   const bool use_graph = ctx->stream != nullptr;
   for (int64_t k = 0; k < n_steps; ++k) {
     if (use_graph) {
-      if (!(ctx->have_graph && same_problem(ctx->gkey, *pr) && ctx->gdegree == ctx->cur_degree &&
-            ctx->glp == ctx->cur_lp))
+      if (!graph_matches(ctx, *pr))
         PF_TRY(capture_step(ctx, pr));
       PF_CUDA(cudaGraphLaunch(ctx->gexec, ctx->stream));
     } else {
@@ -716,6 +775,7 @@ static pf_status capture_step(pf_ctx *ctx, pf_problem *pr) {
   ctx->gkey = *pr;
   ctx->gdegree = ctx->cur_degree;
   ctx->glp = ctx->cur_lp;
+  ctx->gp = ctx->ws.p;
   ctx->have_graph = true;
   return PF_OK;
 }
@@ -737,10 +797,10 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
   Params h = {};
   int64_t it = 0;
   bool converged = false;
+  ctx->ws.p = active_width(ctx, pr);
   for (; it < max_iter;) {
     if (use_graph) {
-      if (!(ctx->have_graph && same_problem(ctx->gkey, *pr) && ctx->gdegree == ctx->cur_degree &&
-            ctx->glp == ctx->cur_lp))
+      if (!graph_matches(ctx, *pr))
         PF_TRY(capture_step(ctx, pr));
       PF_CUDA(cudaGraphLaunch(ctx->gexec, ctx->stream));
     } else {
@@ -748,7 +808,8 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
     }
     ++it;
     pr->iter += 1;
-    if (check && (it % check_every == 0 || it == max_iter)) {
+    const bool rule_now = width_rule_on(ctx) && pr->iter % ctx->opt.adapt_every == 0;
+    if (check && (it % check_every == 0 || it == max_iter || rule_now)) {
       PF_TRY(read_params(ctx, &h));
       if (tol > 0.0 && h.kkt <= tol) {
         converged = true;
@@ -773,6 +834,7 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
         }
       }
     }
+    if (rule_now) PF_TRY(apply_width_rule(ctx, pr));
   }
   PF_TRY(read_params(ctx, &h));
   if (out) {

@@ -193,6 +193,9 @@ cudaError_t launch_nce_update(cudaStream_t s, const Workspace &ws, double *Z, in
                               int p, const double *V, int64_t ldv, const double *theta, double *x,
                               double tau, double *hist, int accel_l, double accel_lam);
 cudaError_t launch_fill(cudaStream_t s, double *x, int64_t rows, int64_t cols, int64_t ld, double v);
+cudaError_t launch_grow_block(cudaStream_t s, const Workspace &ws, double *U, int64_t ldu,
+                              double *V, int64_t ldv, double *theta, int n, int p_old, int p_new,
+                              const double *guard, int64_t ldg);
 cudaError_t launch_export_info(cudaStream_t s, const Workspace &ws, int degree, int precision);
 cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,
                                int degree, int precision);

@@ -577,6 +577,35 @@ cudaError_t launch_interval(cudaStream_t s, const Workspace &ws, int kind, const
   return cudaGetLastError();
 }
 
+// Width growth (Sec. 4.2): columns [p_old, p_new) of U take the guard
+// columns of the same index, those of V become zero (the iterate, held by its
+// positive Ritz pairs, is unchanged), theta repeats its smallest value.
+__global__ void k_grow_block(double *U, int64_t ldu, double *V, int64_t ldv, double *theta, int n,
+                             int p_old, int p_new, const double *__restrict__ guard, int64_t ldg) {
+  const int w = p_new - p_old;
+  const int64_t total = (int64_t)n * w;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / w;
+    const int j = p_old + (int)(idx - i * w);
+    U[i * ldu + j] = guard[i * ldg + j];
+    V[i * ldv + j] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < w) theta[p_old + threadIdx.x] = theta[p_old - 1];
+}
+
+cudaError_t launch_grow_block(cudaStream_t s, const Workspace &ws, double *U, int64_t ldu,
+                              double *V, int64_t ldv, double *theta, int n, int p_old, int p_new,
+                              const double *guard, int64_t ldg) {
+  if (p_old < 1 || p_new <= p_old || p_new > kMaxP) return cudaErrorInvalidValue;
+  int64_t blocks = ((int64_t)n * (p_new - p_old) + 255) / 256;
+  if (blocks > 4 * ws.num_sms) blocks = 4 * ws.num_sms;
+  if (blocks < 1) blocks = 1;
+  k_grow_block<<<(int)blocks, 256, 0, s>>>(U, ldu, V, ldv, theta, n, p_old, p_new, guard, ldg);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill(cudaStream_t s, double *x, int64_t rows, int64_t cols, int64_t ld, double v) {
   int64_t blocks = (rows * cols + 255) / 256;
   if (blocks > 4096) blocks = 4096;

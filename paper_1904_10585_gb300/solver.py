@@ -32,10 +32,16 @@ class Context:
 
     def __init__(self, p: int, n_max: int, degree: int, eta: float = 0.1,
                  precision: int = B.PF_PREC_FP64, stream: Optional[torch.cuda.Stream] = None,
-                 degree_max: int = 0, adaptive: int = 0):
+                 degree_max: int = 0, adaptive: int = 0, p_min: int = 0, adapt_guard: int = 0,
+                 adapt_every: int = 10):
+        """p is the (maximum) block width; adapt_guard > 0 turns on the block
+        width rule of Sec. 4.2 (width r_+ + adapt_guard, rounded up to a
+        multiple of 8, in [p_min, p], after every adapt_every-th step)."""
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.opt = B.pf_options(p=p, degree=degree, degree_max=degree_max or degree, q=1,
-                                eta=eta, precision=precision, adaptive=adaptive)
+                                eta=eta, precision=precision, adaptive=adaptive,
+                                p_min=p_min or min(8, p), adapt_guard=adapt_guard,
+                                adapt_every=adapt_every)
         self.p = p
         self.n_max = n_max
         self.handle = B.pf_create(self.opt, n_max, self.stream.cuda_stream)
@@ -129,6 +135,8 @@ class Problem:
     hist: Optional[torch.Tensor] = None
     accel_l: int = 0
     accel_lam: float = 0.0
+    guard: Optional[torch.Tensor] = None   # n x p random columns for width growth
+    p_active: int = 0                      # start width (0: the context's p)
     struct: Optional[B.pf_problem] = None
 
     def make_struct(self) -> B.pf_problem:
@@ -137,7 +145,10 @@ class Problem:
                          nnz=self.colind.numel() if self.colind is not None else 0,
                          t=self.t, mu=self.mu,
                          U=_ptr(self.U), ldu=_ld(self.U), V=_ptr(self.V), ldv=_ld(self.V),
-                         theta=_ptr(self.theta))
+                         theta=_ptr(self.theta), p_active=self.p_active)
+        if self.guard is not None:
+            s.guard = _ptr(self.guard)
+            s.ldg = _ld(self.guard)
         if self.kind == B.PF_PROBLEM_NCE:
             s.Z = _ptr(self.Z)
             s.ldz = _ld(self.Z)
@@ -164,6 +175,16 @@ class Problem:
             s.S = _ptr(self.S)
         self.struct = s
         return s
+
+
+def with_width_rule(pr: Problem, guard: torch.Tensor, p_start: int) -> Problem:
+    """Attach guard columns (n x p device block, the context's p) and the
+    start width for the block width rule; the problem's U must be n x p with
+    the start block in its first p_start columns."""
+    pr.guard = guard
+    pr.p_active = p_start
+    pr.make_struct()
+    return pr
 
 
 def maxcut_problem(rowptr, colind, vals, U0: torch.Tensor, t: float = 0.0, dense: bool = True,

@@ -558,3 +558,55 @@ def test_lanczos_planted_sign_error_is_caught():
         return np.linalg.eigvalsh(T)[0]
 
     assert abs(wrong(6, 6) - lam[0]) > 1e-3
+
+
+def test_adaptive_width_rule_and_resize():
+    """Sec. 4.2 width rule (reading R13): r_+ + guard rounded up to a multiple
+    of 8 and clamped; growth appends the guard block's columns of the same
+    index and repeats the smallest Ritz value; shrinking drops only
+    columns with non-positive Ritz values."""
+    n = 30
+    block = np.arange(n * 24, dtype=float).reshape(n, 24)
+    rule = o.AdaptiveWidth(guard=4, p_min=8, p_max=24, every=5, block=block)
+    assert [rule.width(r) for r in (0, 3, 4, 5, 12, 13, 30)] == [8, 8, 8, 16, 16, 24, 24]
+    U = np.ones((n, 8))
+    th = np.array([5.0, 4.0, 3.0, 2.0, 1.0, 0.5, 0.25, 0.125])
+    U2, th2 = o.adapt_width(U, th, 8, rule)
+    assert U2.shape == (n, 16) and np.array_equal(U2[:, 8:], block[:, 8:16])
+    assert np.array_equal(U2[:, :8], U) and np.all(th2[8:] == 0.125)
+    th3 = np.concatenate([[3.0, 2.0], -np.arange(1.0, 15.0)])
+    U3, th3b = o.adapt_width(U2, th3, 2, rule)
+    assert U3.shape == (n, 8) and np.array_equal(U3, U2[:, :8]) and np.array_equal(th3b, th3[:8])
+    with pytest.raises(AssertionError):
+        o.adapt_width(U2, np.ones(16), 2, rule)
+
+
+def test_adaptive_width_nce_grows_from_a_saturated_block():
+    """Example 5.7 at n = 120 keeps about a dozen positive eigenvalues: a
+    start block of 8 is saturated.  With the width rule it grows and
+    reaches the optimum of a fixed 32-wide block (same objective, same
+    positive count), ending at ceil8(r_+ + guard)."""
+    n = 120
+    G = syn.nce_matrix(n, "5.7", seed=8)
+    full = syn.gaussian_block(n, 32, seed=9)
+    _, h_fix = o.nce_solve(G, full, 3, 3000, tol=1e-7, accel_l=2)
+    rule = o.AdaptiveWidth(guard=4, p_min=8, p_max=32, every=5, block=full)
+    st, h_ad = o.nce_solve(G, full[:, :8], 3, 3000, tol=1e-7, accel_l=2, adapt=rule)
+    assert h_fix[-1].rel <= 1e-7 and h_ad[-1].rel <= 1e-7
+    assert abs(h_ad[-1].obj - h_fix[-1].obj) <= 1e-9 * abs(h_fix[-1].obj)
+    assert h_ad[-1].r_plus == h_fix[-1].r_plus
+    assert h_ad[0].r_plus == 8 and st.U.shape[1] in (rule.width(h_ad[-2].r_plus), rule.width(h_ad[-1].r_plus))
+
+
+def test_adaptive_width_completion_shrinks_to_the_solution_rank():
+    """Rank-2 completion (mu = 0.1) started 24 wide: the positive count falls
+    to 2, the block shrinks to 8 (2 + 4 guards), and the solve reaches the
+    optimum of the fixed 24-wide solve (objective to 1e-9)."""
+    n, r, mu = 80, 2, 0.1
+    inst = syn.completion_instance(n, r, 0.5, 24, seed=13, mu=mu)
+    rule = o.AdaptiveWidth(guard=4, p_min=4, p_max=24, every=10, block=inst.U0_raw)
+    st, hist = o.completion_solve(inst.omega, inst.U0_raw, mu, 1.0, 3, 300, adapt=rule, tol=1e-9)
+    _, hist_fix = o.completion_solve(inst.omega, inst.U0_raw, mu, 1.0, 3, 300, tol=1e-9)
+    assert st.U.shape[1] == 8
+    assert hist[-1].r_plus == r and hist[-1].kkt <= 1e-9 and hist_fix[-1].kkt <= 1e-9
+    assert abs(hist[-1].obj - hist_fix[-1].obj) <= 1e-9 * abs(hist_fix[-1].obj)
