@@ -460,8 +460,32 @@ __global__ void __launch_bounds__(EX_THREADS, 2)
     int cur_rb = -1, row = 0;
     bool in = false;
     float ls = 0.f;
-    int e = 0, e_end = 0, ncol = INT_MAX;
-    float nval = 0.f;
+    // the row's next four sparse entries (column, t C / s), prefetched so that
+    // consuming one issues the load of the entry three places later
+    int e = 0, e_end = 0;
+    int rc[4];
+    float rv[4];
+    auto fetch = [&](int idx, int &c, float &v) {
+      if (idx < e_end) {
+        c = colind[idx];
+        v = ts * (float)vals[idx];
+      } else {
+        c = INT_MAX;
+        v = 0.f;
+      }
+    };
+    auto advance = [&]() {
+      rc[0] = rc[1]; rv[0] = rv[1];
+      rc[1] = rc[2]; rv[1] = rv[2];
+      rc[2] = rc[3]; rv[2] = rv[3];
+      ++e;
+      fetch(e + 3, rc[3], rv[3]);
+    };
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      rc[q] = INT_MAX;
+      rv[q] = 0.f;
+    }
     for (int tt = 0; tt < cnt; ++tt) {
       const int64_t g = g_begin + tt;
       const int rb = (int)(g / T), ct = (int)(g - (int64_t)rb * T);
@@ -472,7 +496,8 @@ __global__ void __launch_bounds__(EX_THREADS, 2)
         row = rb * EX_TILE + quarter * 32 + lane;
         in = row < n;
         ls = in ? (float)(lam[row] * inv_s) : 0.f;
-        ncol = INT_MAX;
+        e_end = 0;
+        e = 0;
         if (in) {
           int lo = rowptr[row], hi = rowptr[row + 1];
           e_end = hi;
@@ -482,11 +507,9 @@ __global__ void __launch_bounds__(EX_THREADS, 2)
             else hi = mid;
           }
           e = lo;
-          if (e < e_end) {
-            ncol = colind[e];
-            nval = ts * (float)vals[e];
-          }
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fetch(e + q, rc[q], rv[q]);
       }
       const int b = tt & 1;
       const bool have = mbar_wait(smem_u32(&acc_full[b]), (tt >> 1) & 1, &abort_flag);
@@ -502,19 +525,13 @@ __global__ void __launch_bounds__(EX_THREADS, 2)
         const int jc = j0 + c0;
         if (!in || jc >= n) continue;
         // sparse entries before this chunk belong to the other column half
-        while (ncol < jc) {
-          ++e;
-          ncol = e < e_end ? colind[e] : INT_MAX;
-          nval = e < e_end ? ts * (float)vals[e] : 0.f;
-        }
-        while (ncol < jc + 32) {
-          const int q = ncol - jc;
-          const float tc = nval;
+        while (rc[0] < jc) advance();
+        while (rc[0] < jc + 32) {
+          const int q = rc[0] - jc;
+          const float tc = rv[0];
 #pragma unroll
           for (int k = 0; k < 32; ++k) v[k] -= (k == q) ? tc : 0.f;
-          ++e;
-          ncol = e < e_end ? colind[e] : INT_MAX;
-          nval = e < e_end ? ts * (float)vals[e] : 0.f;
+          advance();
         }
         const int dj = row - jc;
         if (dj >= 0 && dj < 32) {
