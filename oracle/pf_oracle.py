@@ -614,3 +614,119 @@ def nce_solve(G, U0_raw, degree: int, iters: int, exact: bool = False, tol: floa
                 st.x, _ = rna_combination(window, accel_lam)
                 window = [st.x.copy()]
     return st, hist
+
+
+# ---------------------------------------------------------------------------
+# Nuclear-norm matrix completion by SVT and its polynomial-filtered form
+# PFSVT (Sec. 5.2.1, Eq. (svt))
+# ---------------------------------------------------------------------------
+#
+# min ||X||_* + 1/(2 mu) ||X||_F^2 s.t. P_Omega(X) = P_Omega(M) is solved on
+# its dual F(x) = 1/2 ||shrink_mu(A*(x))||_F^2 - b^T x (Eq. (ANM-dual)) by the
+# SVT iteration W = shrink_mu(A*(x)), x <- x + tau (b - A(W)), a gradient step
+# on F.  A*(x) is the sparse matrix Y with the values x on Omega.  PFSVT takes
+# the singular pairs of Y from a subspace filtered on Y^T Y (Sec. 5.2.1:
+# extraction from A^T A), then a Rayleigh-Ritz step on the projected Gram
+# matrix: B = Y Q, B^T B = Wr diag(theta) Wr^T, sigma = sqrt(theta), right
+# vectors Q Wr, left vectors B Wr / sigma.
+# Readings (R14): square M (the paper's tests have m = n); x starts at
+# tau P_Omega(M), the exact result of the first iteration from x = 0 (W = 0
+# there); the interval on Y^T Y >= 0 is a = 0 with reading R4 for b and the
+# bound ||Y||_1 ||Y||_inf >= sigma_max^2 as upper bound; mu = 5 n and
+# tau = 1.2 / SR as in the SVT reference the paper cites; the reported
+# residual is ||P_Omega(W - M)||_F / ||P_Omega(M)||_F, the stopping rule of
+# that reference; the block carried forward is the Ritz basis Q Wr.
+
+
+def shrink(X: np.ndarray, mu: float) -> np.ndarray:
+    """Singular value soft-thresholding U diag((sigma - mu)_+) V^T (dense)."""
+    Ud, s, Vt = np.linalg.svd(X, full_matrices=False)
+    return (Ud * np.maximum(s - mu, 0.0)) @ Vt
+
+
+@dataclasses.dataclass
+class SVTState:
+    x: np.ndarray                       # dual variable on Omega (row-major entry order)
+    U: np.ndarray                       # n x p warm-start block (right singular subspace)
+    theta_prev: Optional[np.ndarray]
+
+
+@dataclasses.dataclass
+class SVTInfo:
+    a: float
+    b: float
+    obj: float                          # F(x) at the step's x
+    rel: float                          # ||P_Omega(W - M)|| / ||P_Omega(M)||
+    svp: int                            # singular values above mu
+    theta: np.ndarray                   # Ritz values of Y^T Y (sigma^2), descending
+
+
+def svt_pattern(omega) -> sp.csr_matrix:
+    return sp.csr_matrix((np.ones(omega.nnz), omega.colind, omega.rowptr),
+                         shape=(omega.n, omega.n))
+
+
+def svt_init(omega, U0_raw: np.ndarray, tau: float) -> SVTState:
+    return SVTState(x=tau * omega.vals.astype(np.float64), U=np.array(U0_raw, dtype=np.float64),
+                    theta_prev=None)
+
+
+def svt_step(omega, st: SVTState, mu: float, tau: float, degree: int, exact: bool = False,
+             eta: float = ETA):
+    n = omega.n
+    m_vals = omega.vals.astype(np.float64)
+    Y = sp.csr_matrix((st.x, omega.colind, omega.rowptr), shape=(n, n))
+    absY = abs(Y)
+    ub = float(np.max(np.asarray(absY.sum(axis=0)))) * float(np.max(np.asarray(absY.sum(axis=1))))
+    a = 0.0
+    b = choose_b(a, st.theta_prev, ub, eta)
+    rows = omega.row_of_entries()
+    if exact:
+        Ud, s, Vt = np.linalg.svd(Y.toarray())
+        theta = s ** 2
+        Vr, Lr = Vt.T, Ud * s
+        U_next = st.U
+    else:
+        Q = orth(cheb_filter(lambda Z: Y.T @ (Y @ Z), st.U, a, b, degree))
+        Bm = Y @ Q
+        H = Bm.T @ Bm
+        H = 0.5 * (H + H.T)
+        lam, Wr = np.linalg.eigh(H)
+        order = np.argsort(-lam, kind="stable")
+        theta, Wr = lam[order], Wr[:, order]
+        Vr, Lr = Q @ Wr, Bm @ Wr
+        U_next = Vr
+    sigma = np.sqrt(np.maximum(theta, 0.0))
+    keep = sigma > mu
+    scale = np.zeros_like(sigma)
+    scale[keep] = (sigma[keep] - mu) / sigma[keep]
+    w = np.einsum("el,el->e", Lr[rows][:, keep] * scale[keep], Vr[omega.colind][:, keep])
+    resid = m_vals - w
+    rel = float(np.linalg.norm(resid) / np.linalg.norm(m_vals))
+    obj = 0.5 * float(np.sum((sigma[keep] - mu) ** 2)) - float(m_vals @ st.x)
+    info = SVTInfo(a, b, obj, rel, int(keep.sum()), theta)
+    return SVTState(x=st.x + tau * resid, U=U_next, theta_prev=theta), info
+
+
+def svt_factors(omega, st: SVTState, mu: float, tau: float, degree: int):
+    """Factors (L, s, R) of the primal iterate W = L diag(s) R^T that the
+    next step would form (for recovery checks)."""
+    n = omega.n
+    Y = sp.csr_matrix((st.x, omega.colind, omega.rowptr), shape=(n, n))
+    Ud, s, Vt = np.linalg.svd(Y.toarray())
+    keep = s > mu
+    return Ud[:, keep], s[keep] - mu, Vt[keep].T
+
+
+def svt_solve(omega, U0_raw, mu: float, tau: float, degree: int, iters: int,
+              exact: bool = False, tol: float = 0.0, adapt: Optional[AdaptiveWidth] = None):
+    st = svt_init(omega, U0_raw, tau)
+    hist = []
+    for k in range(iters):
+        st, info = svt_step(omega, st, mu, tau, degree, exact=exact)
+        hist.append(info)
+        if tol > 0 and info.rel <= tol:
+            break
+        if adapt is not None and (k + 1) % adapt.every == 0:
+            st.U, st.theta_prev = adapt_width(st.U, st.theta_prev, info.svp, adapt)
+    return st, hist

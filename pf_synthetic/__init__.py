@@ -18,6 +18,12 @@ Workload laws:
   probability ``prob``, no self loops, weights +-1 with equal probability,
   and cost matrix ``C = -L/4`` with ``L = D - W`` the weighted Laplacian,
   stored as a CSR matrix that includes the diagonal.
+* Matrix completion for SVT (Example "MC" of Sec. 5.2): ``M = M_L M_R^T``
+  with standard Gaussian ``n x r`` factors; every entry is observed
+  independently with probability ``SR`` (Bernoulli sampling standing in for
+  a uniform draw of exactly ``SR n^2`` pairs).  The pattern is stored twice:
+  row-major CSR, and the CSR of the transpose with the permutation that maps
+  its entries to the row-major ones (an input format, like CSR itself).
 * Start block: an ``n x p`` standard Gaussian matrix.  Orthonormalising it
   is the method's job, not the generator's.
 
@@ -148,6 +154,48 @@ def completion_instance(n: int, rank: int, rate: float, p: int, seed: int,
     omega = _symmetric_csr(n, i, j, vals.astype(np.float32))
     U0 = r_u.standard_normal((n, p))
     return CompletionInstance(n, rank, G, omega, U0, float(mu), float(t))
+
+
+@dataclasses.dataclass
+class SVTInstance:
+    n: int
+    rank: int
+    ML: np.ndarray          # n x r
+    MR: np.ndarray          # n x r
+    omega: CSR              # observed entries of M (float64 values), row-major
+    t_rowptr: np.ndarray    # CSR of the transpose of the pattern
+    t_colind: np.ndarray
+    t_perm: np.ndarray      # int32: entry e of the transpose is entry t_perm[e] of omega
+    U0_raw: np.ndarray      # n x p standard Gaussian start block
+
+
+def svt_instance(n: int, rank: int, sr: float, p: int, seed: int) -> SVTInstance:
+    r_pat, r_l, r_r, r_u = _streams(seed, 4)
+    ML = r_l.standard_normal((n, rank))
+    MR = r_r.standard_normal((n, rank))
+    rows, cols = [], []
+    for i0 in range(0, n, 1024):
+        i1 = min(n, i0 + 1024)
+        mask = r_pat.random((i1 - i0, n)) < sr
+        ii, jj = np.nonzero(mask)
+        rows.append((ii + i0).astype(np.int64))
+        cols.append(jj.astype(np.int64))
+    i = np.concatenate(rows)
+    j = np.concatenate(cols)
+    vals = np.empty(i.shape[0], dtype=np.float64)
+    step = 1 << 20
+    for s0 in range(0, i.shape[0], step):
+        vals[s0:s0 + step] = np.einsum("ij,ij->i", ML[i[s0:s0 + step]], MR[j[s0:s0 + step]])
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, i + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int32)
+    omega = CSR(n, rowptr, j.astype(np.int32), vals)
+    order = np.lexsort((i, j))                    # by column, then row
+    t_rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(t_rowptr, j + 1, 1)
+    t_rowptr = np.cumsum(t_rowptr).astype(np.int32)
+    return SVTInstance(n, rank, ML, MR, omega, t_rowptr, i[order].astype(np.int32),
+                       order.astype(np.int32), r_u.standard_normal((n, p)))
 
 
 @dataclasses.dataclass

@@ -610,3 +610,79 @@ def test_adaptive_width_completion_shrinks_to_the_solution_rank():
     assert st.U.shape[1] == 8
     assert hist[-1].r_plus == r and hist[-1].kkt <= 1e-9 and hist_fix[-1].kkt <= 1e-9
     assert abs(hist[-1].obj - hist_fix[-1].obj) <= 1e-9 * abs(hist_fix[-1].obj)
+
+
+def _svt_F(omega, x, mu):
+    n = omega.n
+    Y = sp.csr_matrix((x, omega.colind, omega.rowptr), shape=(n, n)).toarray()
+    s = np.linalg.svd(Y, compute_uv=False)
+    return 0.5 * float(np.sum(np.maximum(s - mu, 0.0) ** 2)) - float(omega.vals @ x)
+
+
+def test_svt_step_is_a_gradient_step_on_the_dual():
+    """Eq. (ANM-dual): F(x) = 1/2||shrink_mu(A*(x))||^2 - b^T x has gradient
+    A(shrink_mu(A*(x))) - b, so the SVT update x + tau (b - A(W)) is
+    x - tau grad F.  Checked against central differences of F computed
+    from singular values alone (no shrink code involved)."""
+    n = 24
+    I = syn.svt_instance(n, 2, 0.5, n, seed=4)
+    rng = np.random.default_rng(1)
+    x = 3.0 * I.omega.vals * (1 + 0.1 * rng.standard_normal(I.omega.nnz))
+    mu, tau = 0.8, 0.7
+    st = o.SVTState(x=x.copy(), U=I.U0_raw, theta_prev=None)
+    st2, info = o.svt_step(I.omega, st, mu, tau, 1, exact=True)
+    grad = -(st2.x - x) / tau
+    for k in range(3):
+        d = rng.standard_normal(I.omega.nnz)
+        eps = 1e-6
+        fd = (_svt_F(I.omega, x + eps * d, mu) - _svt_F(I.omega, x - eps * d, mu)) / (2 * eps)
+        assert abs(fd - grad @ d) <= 1e-5 * max(1.0, abs(fd))
+    assert abs(info.obj - _svt_F(I.omega, x, mu)) <= 1e-10 * abs(info.obj)
+
+
+def test_shrink_is_the_nuclear_norm_prox():
+    """shrink_mu(X) minimises mu||W||_* + 1/2||W - X||^2: its value is below
+    that of random perturbations, and on a diagonal matrix it soft-thresholds
+    the absolute diagonal."""
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((7, 7)) * 3
+    mu = 2.0
+    W = o.shrink(X, mu)
+    f = lambda V: mu * np.linalg.svd(V, compute_uv=False).sum() + 0.5 * np.sum((V - X) ** 2)  # noqa: E731
+    for _ in range(20):
+        assert f(W) <= f(W + 1e-3 * rng.standard_normal((7, 7))) + 1e-12
+    D = np.diag([5.0, -3.0, 1.0, -0.5])
+    np.testing.assert_allclose(o.shrink(D, 2.0), np.diag([3.0, -1.0, 0.0, 0.0]), atol=1e-14)
+
+
+def test_pfsvt_full_block_is_exact_svt():
+    """p = n: the filtered block spans everything, so one PFSVT step equals
+    the exact SVT step (Sec. 5.2.1)."""
+    n = 30
+    I = syn.svt_instance(n, 2, 0.4, n, seed=6)
+    mu, tau = 5.0, 1.2 / 0.4
+    st = o.svt_init(I.omega, I.U0_raw, tau)
+    for _ in range(3):
+        st, _ = o.svt_step(I.omega, st, mu, tau, 1, exact=True)
+    a, ia = o.svt_step(I.omega, st, mu, tau, 1, exact=True)
+    b, ib = o.svt_step(I.omega, st, mu, tau, 1)
+    np.testing.assert_allclose(b.x, a.x, rtol=0, atol=1e-9 * np.abs(a.x).max())
+    assert ia.svp == ib.svp and abs(ia.rel - ib.rel) < 1e-10
+
+
+def test_svt_and_pfsvt_recover_a_low_rank_matrix():
+    """Example MC (rank 2, n = 100, SR = 0.5, mu = 5n, tau = 1.2/SR): SVT
+    reaches the 1e-4 residual with the right rank and mse near 1e-4, and
+    PFSVT with degree 1 takes the same number of iterations (Table 5.x
+    reports iter/svp/mse equal across SVT and PFSVT)."""
+    n, r, sr = 100, 2, 0.5
+    I = syn.svt_instance(n, r, sr, 8, seed=3)
+    mu, tau = 5 * n, 1.2 / sr
+    st_e, h_e = o.svt_solve(I.omega, I.U0_raw, mu, tau, 1, 500, exact=True, tol=1e-4)
+    st_p, h_p = o.svt_solve(I.omega, I.U0_raw, mu, tau, 1, 500, tol=1e-4)
+    assert h_e[-1].rel <= 1e-4 and h_p[-1].rel <= 1e-4
+    assert h_e[-1].svp == h_p[-1].svp == r
+    assert abs(len(h_e) - len(h_p)) <= 2
+    M = I.ML @ I.MR.T
+    L, s, R = o.svt_factors(I.omega, st_p, mu, tau, 1)
+    assert np.linalg.norm((L * s) @ R.T - M) / np.linalg.norm(M) < 1e-3
