@@ -146,6 +146,8 @@ class WorkloadSpec:
     def nnz(self):
         if self.kind == "nce":
             return self.n * self.n
+        if self.kind == "svt":
+            return self.inst.omega.nnz
         return self.inst.C.nnz if self.kind == "maxcut" else self.inst.omega.nnz
 
     def oracle_sample(self, iters_sample):
@@ -156,6 +158,9 @@ class WorkloadSpec:
         if self.kind == "nce":
             o.nce_solve(self.inst.G, self.inst.U0_raw[:, :self.p], self.d, iters_sample,
                         accel_l=self.cfg.get("accel_l", 0))
+        elif self.kind == "svt":
+            o.svt_solve(self.inst.omega, self.inst.U0_raw[:, :self.p], *self.svt_params(),
+                        self.d, iters_sample)
         elif self.kind == "maxcut":
             inst = self.inst
             C = sp.csr_matrix((inst.C.vals, inst.C.colind, inst.C.rowptr), shape=(inst.n, inst.n))
@@ -170,18 +175,32 @@ class WorkloadSpec:
                 st, _ = o.completion_pfpg_step(Om, st, self.cfg["mu"], self.cfg["t"], self.d)
         return time.perf_counter() - t0
 
+    def svt_params(self):
+        """(mu, tau) of the SVT reference: mu = 5 n, tau = 1.2 / SR."""
+        return 5.0 * self.n, 1.2 / self.cfg["sr"]
+
     def tol(self):
         return 1e-7 if self.kind == "nce" else TOL
 
     def sample_iters(self):
         return min(self.iters, {"maxcut_n4096": 15, "maxcut_n4096_structured": 15,
-                                "completion_n400": 100, "nce_n4000": 10}.get(self.name, 1))
+                                "completion_n400": 100, "nce_n4000": 10,
+                                "svt_n5000": 20}.get(self.name, 1))
 
     def config(self):
         c = self.cfg
         d = {"workload": self.name, "n": c["n"], "p": c["p"], "degree": c["degree"],
              "max_iters": c["iters"], "tol_kkt": TOL}
-        if self.kind == "nce":
+        if self.kind == "svt":
+            mu, tau = self.svt_params()
+            d["problem"] = ("nuclear-norm matrix completion, PFSVT (Sec. 5.2.1): filter on Y^T Y "
+                            "by two CSR SpMMs per product, FP64")
+            d["matrix"] = (f"Example MC: M = M_L M_R^T rank {c['rank']}, Bernoulli sampling "
+                           f"SR {c['sr']}, mu = 5n = {mu:g}, tau = 1.2/SR = {tau:g}")
+            d["tol"] = "relative residual ||P_Omega(X - M)|| / ||P_Omega(M)|| 1e-4"
+            d["nnz"] = int(self.nnz())
+            bytes_z = self.nnz() * 16
+        elif self.kind == "nce":
             d["problem"] = ("nearest correlation estimation, PFPG on the dual (dense FP64 "
                             "G + Diag(x))")
             d["matrix"] = f"Example {c['example']} law (off-diagonal uniform, unit diagonal)"
@@ -252,6 +271,11 @@ class Workload(WorkloadSpec):
         self.U0 = torch.from_numpy(np.ascontiguousarray(self.inst.U0_raw[:, :self.p])).to(dev)
         if self.kind == "nce":
             self.G = torch.from_numpy(self.inst.G).to(dev)
+        elif self.kind == "svt":
+            self.rp, self.ci, self.cv = S.csr_to_device(self.inst.omega, dev, torch.float64)
+            self.tr = torch.from_numpy(self.inst.t_rowptr).to(dev)
+            self.tc = torch.from_numpy(self.inst.t_colind).to(dev)
+            self.tp = torch.from_numpy(self.inst.t_perm).to(dev)
         elif self.kind == "maxcut":
             self.rp, self.ci, self.cv = S.csr_to_device(self.inst.C, dev, torch.float64)
         else:
@@ -262,11 +286,15 @@ class Workload(WorkloadSpec):
         in the end-to-end measurement), start block last."""
         if self.kind == "nce":
             return [self.G, self.U0]
+        if self.kind == "svt":
+            return [self.rp, self.ci, self.cv, self.tr, self.tc, self.tp, self.U0]
         return [self.rp, self.ci, self.cv, self.U0]
 
     def problem_from(self, tensors):
         if self.kind == "nce":
             return self.S.nce_problem(tensors[0], tensors[1], accel_l=self.cfg.get("accel_l", 0))
+        if self.kind == "svt":
+            return self.S.svt_problem(*tensors, *self.svt_params())
         return self.problem(*tensors)
 
     def precision(self):
@@ -277,6 +305,9 @@ class Workload(WorkloadSpec):
         if self.kind == "nce":
             return S.nce_problem(self.G, self.U0 if U0 is None else U0,
                                  accel_l=self.cfg.get("accel_l", 0))
+        if self.kind == "svt":
+            return S.svt_problem(self.rp, self.ci, self.cv, self.tr, self.tc, self.tp,
+                                 self.U0 if U0 is None else U0, *self.svt_params())
         rp = self.rp if rp is None else rp
         ci = self.ci if ci is None else ci
         cv = self.cv if cv is None else cv
@@ -291,6 +322,12 @@ class Workload(WorkloadSpec):
         """(operator, description, bound, work per launch, unit) of the dominant kernel."""
         import torch
         S, B, n, p = self.S, self.B, self.n, self.p
+        if self.kind == "svt":
+            # Y X with Y = A*(x): the plain CSR product of the filter and the
+            # Ritz step (the transposed product k_svt_spmm does the same work)
+            op = S.lowrank_sparse_operator(n, None, None, self.rp, self.ci, pr.S, 1.0, 0.0)
+            nnz = self.ci.numel()
+            return (op, "k_lrsp_apply (Y X, CSR SpMM, FP64)", "alu", 2.0 * nnz * p, "TFLOP/s")
         if self.kind == "nce":
             return (S.dense_operator(pr.Z),
                     "k_gemm_f64_splitk + k_combine (Y = (G + Diag x) X, dense FP64 filter product)",

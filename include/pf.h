@@ -69,7 +69,8 @@ typedef enum { PF_PREC_FP64 = 0, PF_PREC_TF32 = 1, PF_PREC_BF16 = 2 } pf_precisi
 typedef enum {
   PF_PROBLEM_MAXCUT = 0,       /* max-cut SDP by PFAM (Sec. 2.3)                          */
   PF_PROBLEM_COMPLETION = 1,   /* PSD matrix completion by PFPG (Sec. 2.2)                */
-  PF_PROBLEM_NCE = 2           /* nearest correlation estimation, PFPG on the dual (Sec. 5.1) */
+  PF_PROBLEM_NCE = 2,          /* nearest correlation estimation, PFPG on the dual (Sec. 5.1) */
+  PF_PROBLEM_SVT = 3           /* nuclear-norm matrix completion, PFSVT (Sec. 5.2.1)        */
 } pf_problem_kind;
 
 /* Solver options (Sec. 2.2-2.3 and Sec. 4: degree d, q, eta, block width p). */
@@ -154,6 +155,17 @@ typedef struct {
  *  continues from x.  accel_l = 0 (or hist NULL) disables it.  If the small
  *  system has a non-positive pivot the window restarts from the current
  *  iterate instead.  Ignored by the other kinds.
+ * SVT (min ||X||_* + 1/(2 mu)||X||_F^2 s.t. P_Omega(X) = P_Omega(M), by the
+ *  SVT iteration W = shrink_mu(A*(x)), x <- x + t (b - A(W)) with the
+ *  singular pairs of Y = A*(x) from a subspace filtered on Y^T Y):
+ *  rowptr/colind/vals_f64 hold M on Omega (row-major CSR of the n x n
+ *  matrix), t_rowptr/t_colind/t_perm the CSR of the transposed pattern and
+ *  the map from its entries to the row-major ones; t is the step, mu the
+ *  threshold; S (nnz) holds the dual x, set to t P_Omega(M) by
+ *  pf_problem_init (the first iteration from x = 0); theta holds the Ritz
+ *  values of Y^T Y (sigma^2) and V the right singular vectors.  The report's
+ *  kkt is ||P_Omega(W - M)||_F / ||P_Omega(M)||_F, obj the dual F(x), r_plus
+ *  the number of singular values above mu, pinf ||P_Omega(W - M)||_F.
  * t: MAXCUT step; if t <= 0 on entry to pf_problem_init it is set to
  *    10 sqrt(n)/||C||_F.  COMPLETION step (t = 1 matches the Lipschitz
  *    constant of P_Omega).
@@ -179,6 +191,7 @@ typedef struct {
                             maintained by the library under the width rule */
   const double *guard;   /* n x p random columns for width growth (ldg), read only */
   int64_t ldg;
+  const int32_t *t_rowptr; const int32_t *t_colind; const int32_t *t_perm;  /* SVT */
 } pf_problem;
 
 /* Per-step report (host struct).  MAXCUT: obj = <C, X~>, pinf/dinf/gap as in

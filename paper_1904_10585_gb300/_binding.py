@@ -33,6 +33,7 @@ PF_PREC_BF16 = 2
 PF_PROBLEM_MAXCUT = 0
 PF_PROBLEM_COMPLETION = 1
 PF_PROBLEM_NCE = 2
+PF_PROBLEM_SVT = 3
 
 
 class pf_options(C.Structure):
@@ -63,7 +64,8 @@ class pf_problem(C.Structure):
                 ("Z_lp", C.c_void_p), ("ldz_lp", C.c_int64),
                 ("lam", C.c_void_p), ("S", C.c_void_p), ("iter", C.c_int64),
                 ("accel_l", C.c_int32), ("accel_lam", C.c_double), ("hist", C.c_void_p),
-                ("p_active", C.c_int32), ("guard", C.c_void_p), ("ldg", C.c_int64)]
+                ("p_active", C.c_int32), ("guard", C.c_void_p), ("ldg", C.c_int64),
+                ("t_rowptr", C.c_void_p), ("t_colind", C.c_void_p), ("t_perm", C.c_void_p)]
 
 
 class pf_iter_info(C.Structure):

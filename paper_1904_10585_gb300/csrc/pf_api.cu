@@ -277,6 +277,14 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
       return set_err(ctx, PF_ERR_INVALID_ARG,
                      "NCE extrapolation needs 0 <= accel_l <= %d and hist ((l+2) x n)",
                      PF_MAX_ACCEL);
+  } else if (pr->kind == PF_PROBLEM_SVT) {
+    if (!pr->vals_f64 || !pr->S || !pr->t_rowptr || !pr->t_colind || !pr->t_perm)
+      return set_err(ctx, PF_ERR_INVALID_ARG,
+                     "SVT needs vals_f64 (M on Omega), S (x) and the transposed pattern");
+    if (!(pr->t > 0.0) || !(pr->mu > 0.0))
+      return set_err(ctx, PF_ERR_INVALID_ARG, "SVT needs t > 0 and mu > 0");
+    if (ctx->opt.precision != PF_PREC_FP64)
+      return set_err(ctx, PF_ERR_UNSUPPORTED, "SVT runs in an FP64 context");
   } else if (pr->kind == PF_PROBLEM_COMPLETION) {
     if (!pr->vals_f32 || !pr->S)
       return set_err(ctx, PF_ERR_INVALID_ARG, "completion needs vals_f32 (M on Omega) and S");
@@ -296,6 +304,46 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
   const Workspace &ws = ctx->ws;
   const int degree = ctx->cur_degree;
   const bool lp = ctx->cur_lp;
+  if (pr->kind == PF_PROBLEM_SVT) {
+    // interval on Y^T Y, Y = A*(x) (values x in S)
+    PF_CUDA(launch_svt_interval(s, ws, pr->rowptr, pr->t_rowptr, pr->t_perm, pr->S, n,
+                                pr->theta));
+    // filter: each product Y^T (Y X) is two SpMMs, the recurrence in the second;
+    // Y X is the plain CSR product of the low-rank + sparse kernel (r = 0)
+    Op oy = {};
+    oy.kind = PF_OP_LOWRANK_SPARSE;
+    oy.n = n;
+    oy.rowptr = pr->rowptr;
+    oy.colind = pr->colind;
+    oy.vals = pr->S;
+    oy.sscale = 1.0;
+    oy.shift = 0.0;
+    double *const *Yb = ws.Y;
+    for (int j = 0; j < degree; ++j) {
+      const double *cur = j == 0 ? pr->U : Yb[(j - 1) & 1];
+      const int64_t ldc = j == 0 ? pr->ldu : p;
+      const double *prev = j == 1 ? pr->U : Yb[j & 1];
+      const int64_t ldprev = j == 1 ? pr->ldu : p;
+      PF_CUDA(launch_lowrank_sparse_apply(s, ws, oy, cur, ldc, nullptr, 0, ws.W, p, MODE_PLAIN));
+      PF_CUDA(launch_svt_spmm(s, ws, pr->t_rowptr, pr->t_colind, pr->S, pr->t_perm, n, ws.W, p,
+                              cur, ldc, j == 0 ? nullptr : prev, ldprev, Yb[j & 1], p,
+                              j == 0 ? MODE_FIRST : MODE_RECUR));
+    }
+    PF_TRY(cholqr2(ctx, Yb[(degree - 1) & 1], p, pr->U, pr->ldu, n));
+    // Rayleigh-Ritz on the projected Gram matrix: B = Y Q, B^T B = Wr theta Wr^T
+    PF_CUDA(launch_lowrank_sparse_apply(s, ws, oy, pr->U, pr->ldu, nullptr, 0, ws.W, p,
+                                        MODE_PLAIN));
+    int nb = 0;
+    PF_CUDA(launch_gram(s, ws, ws.W, p, ws.W, p, n, p, p, 0, &nb));
+    PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, pr->theta));
+    PF_CUDA(launch_apply_right(s, ws, pr->U, pr->ldu, pr->V, pr->ldv, n, p, ws.Yeig, 0, 0));
+    PF_CUDA(launch_apply_right(s, ws, ws.W, p, Yb[0], p, n, p, ws.Yeig, 0, 0));
+    // shrink, sampled residual, dual update and report
+    PF_CUDA(launch_svt_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, Yb[0], p, pr->V,
+                              pr->ldv, pr->theta, pr->mu, pr->t, pr->S));
+    PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
+    return PF_OK;
+  }
   if (pr->kind == PF_PROBLEM_NCE) {
     PF_CUDA(launch_nce_interval(s, ws, pr->Z, pr->ldz, n, pr->theta, p));
     Op op = {};
@@ -424,7 +472,8 @@ bool same_problem(const pf_problem &a, const pf_problem &b) {
          a.theta == b.theta && a.Z == b.Z && a.ldz == b.ldz && a.lam == b.lam && a.S == b.S &&
          a.Z_lp == b.Z_lp && a.ldz_lp == b.ldz_lp && a.accel_l == b.accel_l &&
          a.accel_lam == b.accel_lam && a.hist == b.hist && a.p_active == b.p_active &&
-         a.guard == b.guard && a.ldg == b.ldg;
+         a.guard == b.guard && a.ldg == b.ldg && a.t_rowptr == b.t_rowptr &&
+         a.t_colind == b.t_colind && a.t_perm == b.t_perm;
 }
 
 bool graph_matches(const pf_ctx *ctx, const pf_problem &pr) {
@@ -642,6 +691,11 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
                              ctx->opt.precision));
   PF_CUDA(launch_fill(s, pr->V, n, p, pr->ldv, 0.0));
   PF_CUDA(launch_fill(s, pr->theta, 1, p, p, 0.0));
+  if (pr->kind == PF_PROBLEM_SVT) {
+    PF_CUDA(launch_params_init(s, ws.prm, ctx->opt.eta, pr->t, pr->mu, ctx->opt.degree,
+                               ctx->opt.precision));
+    PF_CUDA(launch_svt_init(s, ws, pr->vals_f64, pr->nnz, pr->t, pr->S));
+  }
   if (pr->kind == PF_PROBLEM_NCE) {
     if (!(pr->t > 0.0)) pr->t = 1.0;
     PF_CUDA(launch_params_init(s, ws.prm, ctx->opt.eta, pr->t, 0.0, ctx->opt.degree,

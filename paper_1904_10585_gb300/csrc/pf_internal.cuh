@@ -193,6 +193,21 @@ cudaError_t launch_nce_update(cudaStream_t s, const Workspace &ws, double *Z, in
                               int p, const double *V, int64_t ldv, const double *theta, double *x,
                               double tau, double *hist, int accel_l, double accel_lam);
 cudaError_t launch_fill(cudaStream_t s, double *x, int64_t rows, int64_t cols, int64_t ld, double v);
+// PFSVT (pf_svt.cu)
+cudaError_t launch_svt_spmm(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                            const int32_t *colind, const double *vals, const int32_t *perm, int n,
+                            const double *X, int64_t ldx, const double *Xr, int64_t ldr,
+                            const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn,
+                            int mode);
+cudaError_t launch_svt_interval(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                const int32_t *t_rowptr, const int32_t *t_perm, const double *x,
+                                int n, const double *theta);
+cudaError_t launch_svt_update(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                              const int32_t *colind, const double *mvals, int n, const double *L,
+                              int64_t ldl, const double *R, int64_t ldr, const double *theta,
+                              double mu, double tau, double *x);
+cudaError_t launch_svt_init(cudaStream_t s, const Workspace &ws, const double *mvals, int64_t nnz,
+                            double tau, double *x);
 cudaError_t launch_grow_block(cudaStream_t s, const Workspace &ws, double *U, int64_t ldu,
                               double *V, int64_t ldv, double *theta, int n, int p_old, int p_new,
                               const double *guard, int64_t ldg);

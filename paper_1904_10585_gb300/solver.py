@@ -135,6 +135,7 @@ class Problem:
     hist: Optional[torch.Tensor] = None
     accel_l: int = 0
     accel_lam: float = 0.0
+    t_pattern: Optional[tuple] = None      # SVT: transposed pattern (rowptr, colind, perm)
     guard: Optional[torch.Tensor] = None   # n x p random columns for width growth
     p_active: int = 0                      # start width (0: the context's p)
     struct: Optional[B.pf_problem] = None
@@ -157,6 +158,13 @@ class Problem:
                 s.hist = _ptr(self.hist)
                 s.accel_l = self.accel_l
                 s.accel_lam = self.accel_lam
+            self.struct = s
+            return s
+        if self.kind == B.PF_PROBLEM_SVT:
+            s.vals_f64 = _ptr(self.vals)
+            s.S = _ptr(self.S)
+            tr, tc, tp = self.t_pattern
+            s.t_rowptr, s.t_colind, s.t_perm = _ptr(tr), _ptr(tc), _ptr(tp)
             self.struct = s
             return s
         if self.kind == B.PF_PROBLEM_MAXCUT:
@@ -231,6 +239,21 @@ def nce_problem(G: torch.Tensor, U0: torch.Tensor, tau: float = 1.0, accel_l: in
                  t=tau, accel_l=accel_l, accel_lam=accel_lam,
                  hist=(torch.zeros(accel_l + 2, n, dtype=torch.float64, device=dev)
                        if accel_l > 0 else None))
+    pr.make_struct()
+    return pr
+
+
+def svt_problem(rowptr, colind, mvals_f64, t_rowptr, t_colind, t_perm, U0: torch.Tensor,
+                mu: float, tau: float) -> Problem:
+    """Nuclear-norm matrix completion by PFSVT: M on Omega (row-major CSR,
+    float64 values) with the transposed pattern; S holds the dual x."""
+    n, p = U0.shape
+    dev = U0.device
+    pr = Problem(kind=B.PF_PROBLEM_SVT, n=n, rowptr=rowptr, colind=colind, vals=mvals_f64,
+                 U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
+                 theta=torch.zeros(p, dtype=torch.float64, device=dev),
+                 S=torch.empty(colind.numel(), dtype=torch.float64, device=dev), t=tau, mu=mu)
+    pr.t_pattern = (t_rowptr, t_colind, t_perm)
     pr.make_struct()
     return pr
 

@@ -263,6 +263,8 @@ WORKLOADS = {
                       accel_l=2, config_index=5),
     "completion_n50000": dict(kind="completion", n=50000, rank=20, rate=0.01, p=40, degree=4,
                               iters=100, mu=0.05, t=1.0, config_index=3),
+    "svt_n5000": dict(kind="svt", n=5000, rank=10, sr=0.1, p=32, degree=1, iters=500,
+                      config_index=6),
 }
 
 
@@ -274,6 +276,8 @@ def make_workload(name: str, **overrides):
         rng_u = _streams(seed + 1, 1)[0]
         return cfg, NCEInstance(cfg["n"], nce_matrix(cfg["n"], cfg["example"], seed),
                                 rng_u.standard_normal((cfg["n"], cfg["p"])))
+    if cfg["kind"] == "svt":
+        return cfg, svt_instance(cfg["n"], cfg["rank"], cfg["sr"], cfg["p"], seed)
     if cfg["kind"] == "completion":
         return cfg, completion_instance(cfg["n"], cfg["rank"], cfg["rate"], cfg["p"], seed,
                                         mu=cfg["mu"], t=cfg["t"])
