@@ -1376,10 +1376,17 @@ __global__ void __launch_bounds__(NT) k_lz_update(int n, int j, double *lz,
   const double *Q = lz;
   const double *y = lz + (int64_t)kLanczos * n;
   double *w = lz + (int64_t)(kLanczos + 1) * n;
-  if (threadIdx.x <= j) {
-    const double c = sum_partials(cpart + threadIdx.x, nb, kLzStride);
-    s_c[threadIdx.x] = c;
-    if (blockIdx.x == 0 && threadIdx.x == j) prm->lz_alpha[j] = c;
+  // c_i: 16 lanes (a half-warp) per coefficient, strided partial sums and a
+  // fixed shuffle tree
+  if (threadIdx.x < 16 * (j + 1)) {
+    const int i = threadIdx.x >> 4, sub = threadIdx.x & 15;
+    double c = 0.0;
+    for (int b = sub; b < nb; b += 16) c += cpart[b * kLzStride + i];
+    for (int off = 8; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffu << (threadIdx.x & 16), c, off);
+    if (sub == 0) {
+      s_c[i] = c;
+      if (blockIdx.x == 0 && i == j) prm->lz_alpha[j] = c;
+    }
   }
   __syncthreads();
   double part = 0.0;
@@ -1410,26 +1417,52 @@ __device__ int sturm_below(const double *al, const double *be, int m, double x) 
 }
 
 __global__ void k_lz_final(const double *__restrict__ wpart, int nb, Params *prm) {
-  if (threadIdx.x != 0) return;
+  // one warp: the Sturm counts of a multisection round run on all lanes
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
   const int m = prm->lz_m;
-  const double *al = prm->lz_alpha;
-  double be[16];
+  double al[16], be[16];
+  for (int i = 0; i < m; ++i) al[i] = prm->lz_alpha[i];
   for (int i = 0; i + 1 < m; ++i) be[i] = prm->lz_beta[i];
-  const double blast =
-      m == kLanczos ? sqrt(sum_partials(wpart, nb, kRedWidth)) : prm->lz_beta[m - 1];
+  double blast;
+  if (m == kLanczos) {
+    double v = 0.0;
+    for (int q = lane; q < nb; q += 32) v += wpart[q * kRedWidth];
+    blast = sqrt(warp_sum(v));
+  } else {
+    blast = prm->lz_beta[m - 1];
+  }
   double lo = INFINITY, hi = -INFINITY;
   for (int i = 0; i < m; ++i) {
     const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
     lo = fmin(lo, al[i] - r);
     hi = fmax(hi, al[i] + r);
   }
+  // multisection for the smallest eigenvalue: the interval [a0, b0] keeps
+  // count(a0) = 0 and count(b0) >= 1; each round evaluates 32 interior points
   double a0 = lo, b0 = hi;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (a0 + b0);
-    if (!(mid > a0 && mid < b0)) break;
-    if (sturm_below(al, be, m, mid) >= 1) b0 = mid;
-    else a0 = mid;
+  for (int round = 0; round < 24; ++round) {
+    const double x = a0 + (b0 - a0) * ((double)(lane + 1) / 33.0);
+    const bool inside = x > a0 && x < b0;
+    const bool hit = inside && sturm_below(al, be, m, x) >= 1;
+    const unsigned hmask = __ballot_sync(0xffffffffu, hit);
+    const unsigned imask = __ballot_sync(0xffffffffu, inside);
+    if (imask == 0u) break;
+    double na = a0, nb2 = b0;
+    if (hmask != 0u) {
+      const int k = __ffs(hmask) - 1;
+      nb2 = __shfl_sync(0xffffffffu, x, k);
+      // largest inside point below lane k (its count is 0)
+      const unsigned below = imask & ((1u << k) - 1u);
+      if (below != 0u) na = __shfl_sync(0xffffffffu, x, 31 - __clz(below));
+    } else {
+      na = __shfl_sync(0xffffffffu, x, 31 - __clz(imask));
+    }
+    if (na == a0 && nb2 == b0) break;
+    a0 = na;
+    b0 = nb2;
   }
+  if (lane != 0) return;
   const double theta = b0;
   double s[16];
   double res = 0.0;
