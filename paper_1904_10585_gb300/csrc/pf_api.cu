@@ -143,12 +143,13 @@ pf_status cholqr2(pf_ctx *ctx, const double *Y, int64_t ldy, double *U, int64_t 
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
   int nb = 0;
-  PF_CUDA(launch_gram(s, ws, Y, ldy, Y, ldy, n, p, p, 0, &nb));
+  // symmetric Grams: the Cholesky factorisation reads the upper triangle only
+  PF_CUDA(launch_gram(s, ws, Y, ldy, Y, ldy, n, p, p, 0, &nb, true));
   PF_CUDA(launch_chol_inv(s, ws, nb, n, p, 0));
   PF_CUDA(launch_apply_right(s, ws, Y, ldy, U, ldu, n, p, ws.Rinv, 1, 0));
   for (int pass = 1; pass <= 2; ++pass) {
     const int cond = pass == 2 ? 1 : 0;
-    PF_CUDA(launch_gram(s, ws, U, ldu, U, ldu, n, p, p, cond, &nb));
+    PF_CUDA(launch_gram(s, ws, U, ldu, U, ldu, n, p, p, cond, &nb, true));
     PF_CUDA(launch_chol_inv(s, ws, nb, n, p, pass));
     PF_CUDA(launch_apply_right(s, ws, U, ldu, U, ldu, n, p, ws.Rinv, 1, cond));
   }
@@ -227,7 +228,10 @@ pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, doubl
   PF_CUDA(launch_gram(s, ws, Q, ldq, ws.W, p, op.n, p, p, 0, &nb));
   // launch_gram leaves the reduced H = Q^T W in the first Gram slot
   PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, theta));
-  PF_CUDA(launch_rotate_resid(s, ws, Q, ldq, ws.W, p, op.n, p, theta, V, ldv, resid));
+  if (resid != nullptr)
+    PF_CUDA(launch_rotate_resid(s, ws, Q, ldq, ws.W, p, op.n, p, theta, V, ldv, resid));
+  else  // Ritz vectors only (the solver steps do not use the residual norms)
+    PF_CUDA(launch_apply_right(s, ws, Q, ldq, V, ldv, op.n, p, ws.Yeig, 0, 0));
   return PF_OK;
 }
 
@@ -352,7 +356,7 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
     op.A = pr->Z;
     op.lda = pr->ldz;
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
-    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_nce_update(s, ws, pr->Z, pr->ldz, n, p, pr->V, pr->ldv, pr->theta, pr->lam,
                               pr->t > 0.0 ? pr->t : 1.0, pr->hist, pr->accel_l, pr->accel_lam));
@@ -393,7 +397,7 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
     } else {
       PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     }
-    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_maxcut_struct_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V,
                                         pr->ldv, pr->theta, pr->lam));
@@ -410,7 +414,7 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
     op.A = pr->Z;
     op.lda = pr->ldz;
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
-    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_maxcut_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv,
                                  pr->theta, pr->Z, pr->ldz, pr->lam));
@@ -434,7 +438,7 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
     op.sscale = -pr->t;
     op.shift = -pr->t * pr->mu;
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
-    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, ws.resid));
+    PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_completion_kkt(s, ws, pr->V, pr->ldv, pr->theta, n, p));
   }

@@ -116,7 +116,7 @@ cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, con
                                         int64_t ldp, double *Ynext, int64_t ldn, int mode);
 cudaError_t launch_gram(cudaStream_t s, const Workspace &ws, const double *X, int64_t ldx,
                         const double *Y, int64_t ldy, int n, int px, int py, int cond_flag,
-                        int *nblocks_out);
+                        int *nblocks_out, bool sym = false);
 cudaError_t launch_chol_inv(cudaStream_t s, const Workspace &ws, int nparts, int n, int p, int pass);
 cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double *Y, int64_t ldy,
                                double *Q, int64_t ldq, int n, int p, const double *R, int upper,

@@ -17,7 +17,10 @@ namespace {
 constexpr int NT = 256;
 constexpr int RC = 32;  // rows staged per step
 
-template <int PT>
+// SYM (X = Y, so X^T Y is symmetric): warps skip the column groups that lie
+// entirely below the diagonal of their rows and leave zeros there; the
+// consumers (the Cholesky factorisation) read the upper triangle only.
+template <int PT, bool SYM>
 __global__ void __launch_bounds__(NT) k_gram(const double *__restrict__ X, int64_t ldx,
                                              const double *__restrict__ Y, int64_t ldy, int n,
                                              int px, int py, int rows_per_block,
@@ -50,9 +53,12 @@ __global__ void __launch_bounds__(NT) k_gram(const double *__restrict__ X, int64
 #pragma unroll
       for (int j = 0; j < TN; ++j) b[j] = Ys[r][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+      for (int j = 0; j < TN; ++j) {
+        // rows of this warp: [2 w TM, 2 w TM + 2 TM); columns of group j: [16 j, 16 j + 16)
+        if (SYM && 2 * (tid >> 5) * TM > 16 * j + 15) continue;
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int i = 0; i < TM; ++i) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
     }
     __syncthreads();
   }
@@ -312,28 +318,32 @@ static void row_split(int n, int max_blocks, int min_rows, int *nb, int *rpb) {
 
 cudaError_t launch_gram(cudaStream_t s, const Workspace &ws, const double *X, int64_t ldx,
                         const double *Y, int64_t ldy, int n, int px, int py, int cond_flag,
-                        int *nblocks_out) {
+                        int *nblocks_out, bool sym) {
   int nb, rpb;
   row_split(n, kMaxGramBlocks, 64, &nb, &rpb);
   const int pm = px > py ? px : py;
   if (pm <= 16)
     {
-      k_gram<16><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      if (sym) k_gram<16, true><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      else k_gram<16, false><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
       PF_LAUNCHED();
     }
   else if (pm <= 32)
     {
-      k_gram<32><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      if (sym) k_gram<32, true><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      else k_gram<32, false><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
       PF_LAUNCHED();
     }
   else if (pm <= 48)
     {
-      k_gram<48><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      if (sym) k_gram<48, true><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      else k_gram<48, false><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
       PF_LAUNCHED();
     }
   else
     {
-      k_gram<64><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      if (sym) k_gram<64, true><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
+      else k_gram<64, false><<<nb, NT, 0, s>>>(X, ldx, Y, ldy, n, px, py, rpb, ws.gpart, ws.prm, cond_flag);
       PF_LAUNCHED();
     }
   cudaError_t e = cudaGetLastError();

@@ -784,20 +784,27 @@ __global__ void __launch_bounds__(NT) k_maxcut_sparse_part(const int32_t *__rest
 // lam_new = 2 diag(X~) - diag(Z) - t diag(C) - 1 with
 // diag(Z) = diag(X~prev) - t diag(C) - lam_prev, i.e.
 // lam_new = 2 dX - dXprev + lam_prev - 1; plus the KKT partial sums and
-// <C, X~> over C's pattern.
+// <C, X~> = sum_i sum_l theta+_l V_il (C V)_il.  C is symmetric, so each row
+// takes its diagonal entry once and the entries right of it twice; the
+// product C V of those entries runs like the SpMM (half-warps alternate
+// entries, lanes cover 16 columns each, whole rows of V per entry).
+template <int JG>
 __global__ void __launch_bounds__(NT) k_maxcut_struct_update(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const double *__restrict__ vals, int n, int p, const double *__restrict__ V, int64_t ldv,
     const double *__restrict__ theta, const double *__restrict__ Vp, int64_t ldvp,
     const double *__restrict__ thp, double *__restrict__ lam, double *__restrict__ red) {
-  __shared__ double wv[WPB][kMaxP];
   __shared__ double sh[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
   const int warps = gridDim.x * WPB;
-  int rp = 0;
-  for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
+  double thpos[JG];
+#pragma unroll
+  for (int g = 0; g < JG; ++g) {
+    const int j = hl + 16 * g;
+    thpos[g] = (j < p && theta[j] > 0.0) ? theta[j] : 0.0;
+  }
   double s_pinf = 0.0, s_lam = 0.0, s_cross = 0.0, s_d2 = 0.0, s_cx = 0.0;
-  for (int row = blockIdx.x * WPB + w; row < n; row += warps) {
+  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
     double dx = 0.0, dxp = 0.0;
     for (int l = lane; l < p; l += 32) {
       const double th = theta[l], tp = thp[l];
@@ -805,20 +812,44 @@ __global__ void __launch_bounds__(NT) k_maxcut_struct_update(
       const double vp = Vp[(int64_t)row * ldvp + l];
       if (th > 0.0) dx = fma(th * v, v, dx);
       if (tp > 0.0) dxp = fma(tp * vp, vp, dxp);
-      wv[w][l] = th > 0.0 ? th * v : 0.0;
     }
     dx = warp_sum(dx);
     dxp = warp_sum(dxp);
-    __syncwarp();
+    // first entry at or right of the diagonal (columns sorted)
+    int lo = rowptr[row], hi = rowptr[row + 1];
+    const int e1 = hi;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (colind[mid] < row) lo = mid + 1;
+      else hi = mid;
+    }
+    double acc[JG];
+#pragma unroll
+    for (int g = 0; g < JG; ++g) acc[g] = 0.0;
+    for (int base = lo; base < e1; base += 32) {
+      const int my = base + lane;
+      const int mcol = my < e1 ? colind[my] : 0;
+      const double mv = my < e1 ? (mcol == row ? vals[my] : 2.0 * vals[my]) : 0.0;
+      const int cnt = min(32, e1 - base);
+      for (int k = 0; k < cnt; k += 2) {
+        const int kk = k + half;  // half 0: even entries, half 1: odd entries
+        const int col = __shfl_sync(0xffffffffu, mcol, kk);
+        const double v = __shfl_sync(0xffffffffu, mv, kk);
+        const double *vr = V + (int64_t)col * ldv;
+#pragma unroll
+        for (int g = 0; g < JG; ++g) {
+          const int j = hl + 16 * g;
+          if (j < p) acc[g] = fma(v, vr[j], acc[g]);
+        }
+      }
+    }
     double cx = 0.0;
-    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
-      const int col = colind[e];
-      double x = 0.0;
-      for (int l = 0; l < rp; ++l) x = fma(wv[w][l], V[(int64_t)col * ldv + l], x);
-      cx = fma(vals[e], x, cx);
+#pragma unroll
+    for (int g = 0; g < JG; ++g) {
+      const int j = hl + 16 * g;
+      if (j < p) cx = fma(thpos[g] * V[(int64_t)row * ldv + j], acc[g], cx);
     }
     cx = warp_sum(cx);
-    __syncwarp();
     if (lane == 0) {
       const double lp = lam[row];
       const double ln = 2.0 * dx - dxp + lp - 1.0;
@@ -1089,8 +1120,14 @@ cudaError_t launch_maxcut_struct_update(cudaStream_t s, const Workspace &ws, con
                                         double *lam) {
   const int nb = red_blocks(n, ws.num_sms);
   double *red = slot(ws, SLOT_LAMBDA);  // 2 * kRedWidth doubles per block: spans LAMBDA + EXPAND
-  k_maxcut_struct_update<<<nb, NT, 0, s>>>(rowptr, colind, vals, n, p, V, ldv, theta, ws.Vprev, p,
-                                           ws.thprev, lam, red);
+#define PF_SU(JGV)                                                                           \
+  k_maxcut_struct_update<JGV><<<nb, NT, 0, s>>>(rowptr, colind, vals, n, p, V, ldv, theta,      \
+                                                ws.Vprev, p, ws.thprev, lam, red)
+  if (p <= 16) { PF_SU(1); }
+  else if (p <= 32) { PF_SU(2); }
+  else if (p <= 48) { PF_SU(3); }
+  else { PF_SU(4); }
+#undef PF_SU
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
