@@ -25,6 +25,33 @@ namespace pf {
 
 namespace {
 
+// 1/x and 1/sqrt(x) in FP64 by Newton-Raphson refinement of a single-precision
+// seed (y <- y + y (1 - x y) for 1/x, y <- y + (y/2)(1 - x y^2) for 1/sqrt(x));
+// each step doubles the correct bits (24 -> 48 -> full precision).  On GB300
+// the FP64 pipe is 1/64 of FP32, and these short FMA chains replace the much
+// longer IEEE divide and square-root sequences on the rotation-angle path.
+__device__ __forceinline__ double nr_rcp(double x) {
+  int e;
+  const double m = frexp(x, &e);  // x = m 2^e, 0.5 <= |m| < 1
+  double y = (double)__frcp_rn((float)m);
+  y = fma(y, fma(-m, y, 1.0), y);
+  y = fma(y, fma(-m, y, 1.0), y);
+  return ldexp(y, -e);
+}
+
+__device__ __forceinline__ double nr_rsqrt(double x) {  // x > 0
+  int e;
+  double m = frexp(x, &e);
+  if (e & 1) {
+    m *= 2.0;
+    e -= 1;
+  }
+  double y = (double)rsqrtf((float)m);
+  y = fma(0.5 * y, fma(-m * y, y, 1.0), y);
+  y = fma(0.5 * y, fma(-m * y, y, 1.0), y);
+  return ldexp(y, -e / 2);
+}
+
 constexpr int JC = 8;      // CTAs per cluster
 constexpr int JNT = 256;   // threads per CTA
 constexpr int JLD = kMaxP + 1;
@@ -84,12 +111,19 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
         double c = 1.0, s = 0.0;
         if (l < p) {
           const double hkl = H[k * JLD + l];
-          if (fabs(hkl) > 1e-17 * sqrt(fabs(H[k * JLD + k]) * fabs(H[l * JLD + l])) && hkl != 0.0) {
-            const double tau = (H[l * JLD + l] - H[k * JLD + k]) / (2.0 * hkl);
+          const double hkk = H[k * JLD + k], hll = H[l * JLD + l];
+          if (fabs(hkl) > 0.5e-17 * (fabs(hkk) + fabs(hll)) && hkl != 0.0) {
+            // t = tan of the angle that annihilates h_kl: the smaller root of
+            // t^2 + 2 tau t - 1 = 0, tau = (h_ll - h_kk) / (2 h_kl)
+            const double tau = (hll - hkk) * (0.5 * nr_rcp(hkl));
             double t;
-            if (fabs(tau) > 1e150) t = 0.5 / tau;
-            else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+            if (fabs(tau) > 1e150) {
+              t = 0.5 * nr_rcp(tau);
+            } else {
+              const double q = fma(tau, tau, 1.0);
+              t = (tau >= 0.0 ? 1.0 : -1.0) * nr_rcp(fabs(tau) + q * nr_rsqrt(q));
+            }
+            c = nr_rsqrt(fma(t, t, 1.0));
             s = t * c;
           }
         }

@@ -90,47 +90,81 @@ __global__ void k_gram_reduce(double *__restrict__ gpart, int nparts, int m) {
 //         s = 11 (n p + p (p+1)) u tr(G) and set flags bit 0;
 // pass 1: plain; pass 2: only runs when flags bit 0 is set.
 // A failure with no retry left sets flags bit 1 and writes R^{-1} = I.
+// Only the upper triangle of G is read.  Right-looking factorisation with one
+// barrier per column: in step k every thread scales row k of R by 1/r_kk and
+// updates the trailing upper triangle from the unscaled row; thread 0 updates
+// A[k+1][k+1] first and takes the next pivot (square root and reciprocal)
+// while the other warps finish the update.  The inverse reuses the pivot
+// reciprocals: four lanes per column share each back-substitution sum.
 __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpart, int nparts,
                                                  int n, int p, int pass, double *__restrict__ Rinv,
                                                  Params *prm) {
   if (pass == 2 && !(prm->flags & 1)) return;
   extern __shared__ double dyn[];
-  double(*G)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn);
+  double(*A)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn);
   double(*R)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn + kMaxP * (kMaxP + 1));
+  __shared__ double dinv[kMaxP];
+  __shared__ double diag0[kMaxP];
   __shared__ int fail;
-  __shared__ double trace_s;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  // the partials were reduced in place: nparts is 1 on every call path
   for (int idx = tid; idx < p * p; idx += NT) {
-    double s = 0.0;
-    for (int q = 0; q < nparts; ++q) s += gpart[(int64_t)q * p * p + idx];
-    G[idx / p][idx % p] = s;
+    const int a = idx / p, b = idx % p;
+    if (a <= b) {
+      double s = 0.0;
+      for (int q = 0; q < nparts; ++q) s += gpart[(int64_t)q * p * p + idx];
+      A[a][b] = s;
+      if (a == b) diag0[a] = s;
+    }
   }
   __syncthreads();
   double sh = 0.0;
   bool ok = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
-    for (int idx = tid; idx < p * p; idx += NT) {
-      const int a = idx / p, b = idx % p;
-      R[a][b] = G[a][b] + (a == b ? sh : 0.0);
-    }
-    if (tid == 0) fail = 0;
-    __syncthreads();
-    for (int k = 0; k < p; ++k) {
-      if (tid == 0) {
-        const double piv = R[k][k];
-        const double ref = G[k][k] + sh;
-        if (!(piv > 1e-13 * ref) || !isfinite(piv)) fail = 1;
-        else R[k][k] = sqrt(piv);
+    if (attempt == 1) {
+      // shifted retry from the original Gram matrix
+      for (int idx = tid; idx < p * p; idx += NT) {
+        const int a = idx / p, b = idx % p;
+        if (a <= b) {
+          double g = 0.0;
+          for (int q = 0; q < nparts; ++q) g += gpart[(int64_t)q * p * p + idx];
+          A[a][b] = g + (a == b ? sh : 0.0);
+        }
       }
       __syncthreads();
-      if (fail) break;
-      const double rkk = R[k][k];
-      for (int j = k + 1 + tid; j < p; j += NT) R[k][j] /= rkk;
-      __syncthreads();
-      const int m = p - k - 1;
-      for (int idx = tid; idx < m * m; idx += NT) {
-        const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-        R[i][j] -= R[k][i] * R[k][j];
+    }
+    if (tid == 0) {
+      fail = 0;
+      const double piv = A[0][0];
+      if (!(piv > 1e-13 * (diag0[0] + sh)) || !isfinite(piv)) {
+        fail = 1;
+      } else {
+        const double d = sqrt(piv);
+        R[0][0] = d;
+        dinv[0] = 1.0 / d;
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < p && !fail; ++k) {
+      const double iv = dinv[k], iv2 = iv * iv;
+      // row k of R
+      for (int j = k + 1 + tid; j < p; j += NT) R[k][j] = A[k][j] * iv;
+      // trailing upper triangle; row k+1 first on warp 0 so that thread 0
+      // can take the next pivot early
+      for (int i = k + 1 + warp; i < p; i += NW) {
+        const double aki = A[k][i] * iv2;
+        for (int j = i + lane; j < p; j += 32) A[i][j] = fma(-aki, A[k][j], A[i][j]);
+        if (tid == 0 && i == k + 1) {
+          const double piv = A[i][i];
+          if (!(piv > 1e-13 * (diag0[i] + sh)) || !isfinite(piv)) {
+            fail = 1;
+          } else {
+            const double d = sqrt(piv);
+            R[i][i] = d;
+            dinv[i] = 1.0 / d;
+          }
+        }
       }
       __syncthreads();
     }
@@ -139,34 +173,41 @@ __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpar
       break;
     }
     if (pass != 0) break;
-    // shifted retry
-    if (tid == 0) {
-      double tr = 0.0;
-      for (int k = 0; k < p; ++k) tr += G[k][k];
-      trace_s = tr;
-      atomicOr(&prm->flags, 1);
-    }
     __syncthreads();
-    sh = 11.0 * ((double)n * p + (double)p * (p + 1)) * 1.1102230246251565e-16 * trace_s;
-    __syncthreads();
+    if (tid == 0) atomicOr(&prm->flags, 1);
+    double tr = 0.0;
+    for (int k = 0; k < p; ++k) tr += diag0[k];
+    sh = 11.0 * ((double)n * p + (double)p * (p + 1)) * 1.1102230246251565e-16 * tr;
   }
   if (!ok) {
     if (tid == 0) atomicOr(&prm->flags, 2);
     for (int idx = tid; idx < p * p; idx += NT) Rinv[idx] = (idx / p == idx % p) ? 1.0 : 0.0;
     return;
   }
-  // inverse of the upper-triangular R, column j by thread j (into G)
-  for (int j = tid; j < p; j += NT) {
-    for (int i = j + 1; i < p; ++i) G[i][j] = 0.0;
-    G[j][j] = 1.0 / R[j][j];
-    for (int i = j - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= j; ++k) s = fma(R[i][k], G[k][j], s);
-      G[i][j] = -s / R[i][i];
+  // inverse of the upper-triangular R into A: column j on four lanes q, each
+  // summing the k = i+1+q, i+5+q, ... terms; back-substitution from the diagonal
+  {
+    const int q = lane & 3;
+    const int j = warp * 8 + (lane >> 2);  // 8 columns per warp, 64 columns
+    const int jmax = warp * 8 + 7;
+    if (j < p && q == 0) A[j][j] = dinv[j];
+    __syncwarp();
+    for (int i = (jmax < p ? jmax : p - 1) - 1; i >= 0; --i) {
+      double sacc = 0.0;
+      const bool act = j < p && i < j;
+      if (act)
+        for (int k = i + 1 + q; k <= j; k += 4) sacc = fma(R[i][k], A[k][j], sacc);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+      if (act && q == 0) A[i][j] = -sacc * dinv[i];
+      __syncwarp();
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < p * p; idx += NT) Rinv[idx] = G[idx / p][idx % p];
+  for (int idx = tid; idx < p * p; idx += NT) {
+    const int a = idx / p, b = idx % p;
+    Rinv[idx] = a <= b ? A[a][b] : 0.0;
+  }
 }
 
 // Q = Y R (R p x p; `upper` skips the zero lower part).  In place allowed.
