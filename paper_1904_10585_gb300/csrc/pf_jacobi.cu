@@ -25,31 +25,46 @@ namespace pf {
 
 namespace {
 
-// 1/x and 1/sqrt(x) in FP64 by Newton-Raphson refinement of a single-precision
-// seed (y <- y + y (1 - x y) for 1/x, y <- y + (y/2)(1 - x y^2) for 1/sqrt(x));
-// each step doubles the correct bits (24 -> 48 -> full precision).  On GB300
-// the FP64 pipe is 1/64 of FP32, and these short FMA chains replace the much
-// longer IEEE divide and square-root sequences on the rotation-angle path.
-__device__ __forceinline__ double nr_rcp(double x) {
-  int e;
-  const double m = frexp(x, &e);  // x = m 2^e, 0.5 <= |m| < 1
-  double y = (double)__frcp_rn((float)m);
-  y = fma(y, fma(-m, y, 1.0), y);
-  y = fma(y, fma(-m, y, 1.0), y);
-  return ldexp(y, -e);
-}
-
-__device__ __forceinline__ double nr_rsqrt(double x) {  // x > 0
-  int e;
-  double m = frexp(x, &e);
-  if (e & 1) {
-    m *= 2.0;
-    e -= 1;
+// Rotation of the pair (k, l): the tangent t comes from single-precision
+// arithmetic (|t| <= 1, the smaller root of t^2 + 2 tau t - 1 = 0 with
+// tau = (h_ll - h_kk) / (2 h_kl)); c = 1/sqrt(1 + t^2) is then formed in FP64
+// from the exact double t by Newton-Raphson refinement of a single-precision
+// seed (y <- y + (y/2)(1 - q y^2), twice: 24 -> 48 -> full precision), so
+// (c, s = t c) is orthonormal to FP64 rounding.  The rotation annihilates
+// h_kl only to single precision, so the updated 2 x 2 block keeps its
+// computed off-diagonal entries; the sweeps still converge (each rotation
+// shrinks |h_kl| by ~1e-7 on top of the quadratic coupling).  On GB300 the
+// FP64 pipe is 1/64 of FP32, and a timing probe put the FP64 divide/sqrt
+// chain of the exact angle at ~2 of the 5.3 us of each rotation round.
+__device__ __forceinline__ void rotation(double hkk, double hll, double hkl, double &c,
+                                         double &s) {
+  c = 1.0;
+  s = 0.0;
+  if (!(fabs(hkl) > 0.5e-17 * (fabs(hkk) + fabs(hll))) || hkl == 0.0) return;
+  const double d = hll - hkk;
+  const float h32 = (float)hkl, d32 = (float)d;
+  float t32;
+  if (fabsf(h32) >= 1e-30f && isfinite(h32) && isfinite(d32)) {
+    const float tau = d32 / (2.0f * h32);
+    if (fabsf(tau) > 1e18f) t32 = 0.5f / tau;
+    else t32 = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+  } else {
+    // outside the single-precision range: the exact FP64 angle
+    const double tau = d / (2.0 * hkl);
+    double t;
+    if (fabs(tau) > 1e150) t = 0.5 / tau;
+    else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    c = 1.0 / sqrt(1.0 + t * t);
+    s = t * c;
+    return;
   }
-  double y = (double)rsqrtf((float)m);
-  y = fma(0.5 * y, fma(-m * y, y, 1.0), y);
-  y = fma(0.5 * y, fma(-m * y, y, 1.0), y);
-  return ldexp(y, -e / 2);
+  const double t = (double)t32;
+  const double q = fma(t, t, 1.0);  // in [1, 2]
+  double y = (double)rsqrtf((float)q);
+  y = fma(0.5 * y, fma(-q * y, y, 1.0), y);
+  y = fma(0.5 * y, fma(-q * y, y, 1.0), y);
+  c = y;
+  s = t * y;
 }
 
 constexpr int JC = 8;      // CTAs per cluster
@@ -109,24 +124,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
         int k = player(i), l = player(m - 1 - i);
         if (k > l) { const int tt = k; k = l; l = tt; }
         double c = 1.0, s = 0.0;
-        if (l < p) {
-          const double hkl = H[k * JLD + l];
-          const double hkk = H[k * JLD + k], hll = H[l * JLD + l];
-          if (fabs(hkl) > 0.5e-17 * (fabs(hkk) + fabs(hll)) && hkl != 0.0) {
-            // t = tan of the angle that annihilates h_kl: the smaller root of
-            // t^2 + 2 tau t - 1 = 0, tau = (h_ll - h_kk) / (2 h_kl)
-            const double tau = (hll - hkk) * (0.5 * nr_rcp(hkl));
-            double t;
-            if (fabs(tau) > 1e150) {
-              t = 0.5 * nr_rcp(tau);
-            } else {
-              const double q = fma(tau, tau, 1.0);
-              t = (tau >= 0.0 ? 1.0 : -1.0) * nr_rcp(fabs(tau) + q * nr_rsqrt(q));
-            }
-            c = nr_rsqrt(fma(t, t, 1.0));
-            s = t * c;
-          }
-        }
+        if (l < p) rotation(H[k * JLD + k], H[l * JLD + l], H[k * JLD + l], c, s);
         cs[i] = c; sn[i] = s; pk[i] = k; pl[i] = l;
       }
       __syncthreads();
@@ -155,9 +153,9 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
         const double m00 = cj * a - sj * b, m01 = sj * a + cj * b;
         const double m10 = cj * c - sj * d, m11 = sj * c + cj * d;
         // H' block = J_i^T M
-        double h00 = ci * m00 - si * m10, h01 = ci * m01 - si * m11;
-        double h10 = si * m00 + ci * m10, h11 = si * m01 + ci * m11;
-        if (i == j && si != 0.0) { h01 = 0.0; h10 = 0.0; }
+        const double h00 = ci * m00 - si * m10, h11 = si * m01 + ci * m11;
+        double h01 = ci * m01 - si * m11, h10 = si * m00 + ci * m10;
+        if (i == j) h01 = h10 = 0.5 * (h01 + h10);  // the rotated pair block stays symmetric
         for (int q = 0; q < JC; ++q) {
           double *dst = cluster.map_shared_rank(Hn, q);
           dst[ki * JLD + kj] = h00;
