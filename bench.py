@@ -146,7 +146,7 @@ class WorkloadSpec:
     def nnz(self):
         if self.kind == "nce":
             return self.n * self.n
-        if self.kind == "svt":
+        if self.kind in ("svt", "nnls"):
             return self.inst.omega.nnz
         return self.inst.C.nnz if self.kind == "maxcut" else self.inst.omega.nnz
 
@@ -161,6 +161,9 @@ class WorkloadSpec:
         elif self.kind == "svt":
             o.svt_solve(self.inst.omega, self.inst.U0_raw[:, :self.p], *self.svt_params(),
                         self.d, iters_sample)
+        elif self.kind == "nnls":
+            o.nnls_solve(self.inst.omega, self.inst.U0_raw[:, :self.p], self.d, iters_sample,
+                         mu_bar_rel=self.cfg["mu_bar_rel"], cap=self.p - 8)
         elif self.kind == "maxcut":
             inst = self.inst
             C = sp.csr_matrix((inst.C.vals, inst.C.colind, inst.C.rowptr), shape=(inst.n, inst.n))
@@ -185,13 +188,22 @@ class WorkloadSpec:
     def sample_iters(self):
         return min(self.iters, {"maxcut_n4096": 15, "maxcut_n4096_structured": 15,
                                 "completion_n400": 100, "nce_n4000": 10,
-                                "svt_n5000": 20}.get(self.name, 1))
+                                "svt_n5000": 20, "nnls_n10000": 15}.get(self.name, 1))
 
     def config(self):
         c = self.cfg
         d = {"workload": self.name, "n": c["n"], "p": c["p"], "degree": c["degree"],
              "max_iters": c["iters"], "tol_kkt": TOL}
-        if self.kind == "svt":
+        if self.kind == "nnls":
+            d["problem"] = ("nuclear-norm regularised least squares, PFNNLS (Sec. 5.2.2): "
+                            "accelerated proximal gradient, filter on G^T G, FP64")
+            d["matrix"] = (f"Example MC: M = M_L M_R^T rank {c['rank']}, Bernoulli sampling "
+                           f"SR {c['sr']}, continuation to mu_bar = {c['mu_bar_rel']} mu_0, "
+                           f"rank cap p - 8")
+            d["tol"] = "relative change ||X_k+1 - X_k|| / max(1, ||X_k+1||) 1e-4 at mu_bar"
+            d["nnz"] = int(self.nnz())
+            bytes_z = self.nnz() * 16
+        elif self.kind == "svt":
             mu, tau = self.svt_params()
             d["problem"] = ("nuclear-norm matrix completion, PFSVT (Sec. 5.2.1): filter on Y^T Y "
                             "by two CSR SpMMs per product, FP64")
@@ -271,7 +283,7 @@ class Workload(WorkloadSpec):
         self.U0 = torch.from_numpy(np.ascontiguousarray(self.inst.U0_raw[:, :self.p])).to(dev)
         if self.kind == "nce":
             self.G = torch.from_numpy(self.inst.G).to(dev)
-        elif self.kind == "svt":
+        elif self.kind in ("svt", "nnls"):
             self.rp, self.ci, self.cv = S.csr_to_device(self.inst.omega, dev, torch.float64)
             self.tr = torch.from_numpy(self.inst.t_rowptr).to(dev)
             self.tc = torch.from_numpy(self.inst.t_colind).to(dev)
@@ -286,7 +298,7 @@ class Workload(WorkloadSpec):
         in the end-to-end measurement), start block last."""
         if self.kind == "nce":
             return [self.G, self.U0]
-        if self.kind == "svt":
+        if self.kind in ("svt", "nnls"):
             return [self.rp, self.ci, self.cv, self.tr, self.tc, self.tp, self.U0]
         return [self.rp, self.ci, self.cv, self.U0]
 
@@ -295,6 +307,8 @@ class Workload(WorkloadSpec):
             return self.S.nce_problem(tensors[0], tensors[1], accel_l=self.cfg.get("accel_l", 0))
         if self.kind == "svt":
             return self.S.svt_problem(*tensors, *self.svt_params())
+        if self.kind == "nnls":
+            return self.S.nnls_problem(*tensors, mu_bar_rel=self.cfg["mu_bar_rel"])
         return self.problem(*tensors)
 
     def precision(self):
@@ -308,6 +322,10 @@ class Workload(WorkloadSpec):
         if self.kind == "svt":
             return S.svt_problem(self.rp, self.ci, self.cv, self.tr, self.tc, self.tp,
                                  self.U0 if U0 is None else U0, *self.svt_params())
+        if self.kind == "nnls":
+            return S.nnls_problem(self.rp, self.ci, self.cv, self.tr, self.tc, self.tp,
+                                  self.U0 if U0 is None else U0,
+                                  mu_bar_rel=self.cfg["mu_bar_rel"])
         rp = self.rp if rp is None else rp
         ci = self.ci if ci is None else ci
         cv = self.cv if cv is None else cv
@@ -322,6 +340,16 @@ class Workload(WorkloadSpec):
         """(operator, description, bound, work per launch, unit) of the dominant kernel."""
         import torch
         S, B, n, p = self.S, self.B, self.n, self.p
+        if self.kind == "nnls":
+            # G X: CSR SpMM of the residual plus the rank-2p low-rank part
+            # (the same kernel and work as the step's products)
+            ones = torch.ones(2 * p, dtype=torch.float64, device=pr.fac.device)
+            self._keep = ones
+            op = S.lowrank_sparse_operator(n, pr.fac[:, :2 * p], ones, self.rp, self.ci, pr.S,
+                                           -1.0, 0.0)
+            nnz = self.ci.numel()
+            return (op, "k_lrsp_apply (G X: CSR SpMM + rank-2p low-rank, FP64) + k_gram", "alu",
+                    2.0 * nnz * p + 8.0 * n * p * p, "TFLOP/s")
         if self.kind == "svt":
             # Y X with Y = A*(x): the plain CSR product of the filter and the
             # Ritz step (the transposed product k_svt_spmm does the same work)

@@ -70,7 +70,8 @@ typedef enum {
   PF_PROBLEM_MAXCUT = 0,       /* max-cut SDP by PFAM (Sec. 2.3)                          */
   PF_PROBLEM_COMPLETION = 1,   /* PSD matrix completion by PFPG (Sec. 2.2)                */
   PF_PROBLEM_NCE = 2,          /* nearest correlation estimation, PFPG on the dual (Sec. 5.1) */
-  PF_PROBLEM_SVT = 3           /* nuclear-norm matrix completion, PFSVT (Sec. 5.2.1)        */
+  PF_PROBLEM_SVT = 3,          /* nuclear-norm matrix completion, PFSVT (Sec. 5.2.1)        */
+  PF_PROBLEM_NNLS = 4          /* nuclear-norm regularised least squares, PFNNLS (Sec. 5.2.2) */
 } pf_problem_kind;
 
 /* Solver options (Sec. 2.2-2.3 and Sec. 4: degree d, q, eta, block width p). */
@@ -166,6 +167,18 @@ typedef struct {
  *  values of Y^T Y (sigma^2) and V the right singular vectors.  The report's
  *  kkt is ||P_Omega(W - M)||_F / ||P_Omega(M)||_F, obj the dual F(x), r_plus
  *  the number of singular values above mu, pinf ||P_Omega(W - M)||_F.
+ * NNLS (min mu ||X||_* + 1/2 ||P_Omega(X) - P_Omega(M)||_F^2 by accelerated
+ *  proximal gradient with continuation mu_{k+1} = max(0.7 mu_k, mu_bar); the
+ *  singular pairs of G = (1+beta) X^k - beta X^{k-1} - A*(A(Y) - b) come from
+ *  a subspace filtered on G^T G): the data fields as for SVT; t = mu_0
+ *  (t <= 0 selects 0.1 sqrt(||P_Omega M||_1 ||P_Omega M||_inf)); mu is
+ *  mu_bar / mu_0; S (nnz) holds the residual A(Y) - b; fac (n x 4p, ldfac >=
+ *  4p) holds [L | Lp | R | Rp], the orthonormal factors of X^k = L diag(s)
+ *  R^T and of X^{k-1}; fsv (2p) holds [s | sp]; at most rank_cap pairs are
+ *  kept (0 selects p - 8); p <= 32.  The report's kkt is
+ *  ||X^{k+1} - X^k||_F / max(1, ||X^{k+1}||_F) once mu has reached mu_bar
+ *  (at least 1 before), obj is mu ||X^k||_* + 1/2 ||A(X^k) - b||^2, r_plus
+ *  the rank of X^{k+1}, dinf the step's mu.
  * t: MAXCUT step; if t <= 0 on entry to pf_problem_init it is set to
  *    10 sqrt(n)/||C||_F.  COMPLETION step (t = 1 matches the Lipschitz
  *    constant of P_Omega).
@@ -191,7 +204,8 @@ typedef struct {
                             maintained by the library under the width rule */
   const double *guard;   /* n x p random columns for width growth (ldg), read only */
   int64_t ldg;
-  const int32_t *t_rowptr; const int32_t *t_colind; const int32_t *t_perm;  /* SVT */
+  const int32_t *t_rowptr; const int32_t *t_colind; const int32_t *t_perm;  /* SVT, NNLS */
+  double *fac; int64_t ldfac; double *fsv; int32_t rank_cap;                /* NNLS */
 } pf_problem;
 
 /* Per-step report (host struct).  MAXCUT: obj = <C, X~>, pinf/dinf/gap as in

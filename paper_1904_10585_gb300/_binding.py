@@ -34,6 +34,7 @@ PF_PROBLEM_MAXCUT = 0
 PF_PROBLEM_COMPLETION = 1
 PF_PROBLEM_NCE = 2
 PF_PROBLEM_SVT = 3
+PF_PROBLEM_NNLS = 4
 
 
 class pf_options(C.Structure):
@@ -65,7 +66,9 @@ class pf_problem(C.Structure):
                 ("lam", C.c_void_p), ("S", C.c_void_p), ("iter", C.c_int64),
                 ("accel_l", C.c_int32), ("accel_lam", C.c_double), ("hist", C.c_void_p),
                 ("p_active", C.c_int32), ("guard", C.c_void_p), ("ldg", C.c_int64),
-                ("t_rowptr", C.c_void_p), ("t_colind", C.c_void_p), ("t_perm", C.c_void_p)]
+                ("t_rowptr", C.c_void_p), ("t_colind", C.c_void_p), ("t_perm", C.c_void_p),
+                ("fac", C.c_void_p), ("ldfac", C.c_int64), ("fsv", C.c_void_p),
+                ("rank_cap", C.c_int32)]
 
 
 class pf_iter_info(C.Structure):

@@ -281,6 +281,17 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
       return set_err(ctx, PF_ERR_INVALID_ARG,
                      "NCE extrapolation needs 0 <= accel_l <= %d and hist ((l+2) x n)",
                      PF_MAX_ACCEL);
+  } else if (pr->kind == PF_PROBLEM_NNLS) {
+    if (!pr->vals_f64 || !pr->S || !pr->t_rowptr || !pr->t_colind || !pr->t_perm || !pr->fac ||
+        pr->ldfac < 4 * p || !pr->fsv)
+      return set_err(ctx, PF_ERR_INVALID_ARG,
+                     "NNLS needs vals_f64, S, the transposed pattern, fac (ldfac >= 4p) and fsv");
+    if (!(pr->mu > 0.0) || !(pr->mu <= 1.0) || pr->rank_cap < 0 || pr->rank_cap > p)
+      return set_err(ctx, PF_ERR_INVALID_ARG, "NNLS needs 0 < mu <= 1 and 0 <= rank_cap <= p");
+    if (p > kMaxP / 2)
+      return set_err(ctx, PF_ERR_UNSUPPORTED, "NNLS runs with p <= %d", kMaxP / 2);
+    if (ctx->opt.precision != PF_PREC_FP64 || width_rule_on(ctx))
+      return set_err(ctx, PF_ERR_UNSUPPORTED, "NNLS runs in an FP64 context without the width rule");
   } else if (pr->kind == PF_PROBLEM_SVT) {
     if (!pr->vals_f64 || !pr->S || !pr->t_rowptr || !pr->t_colind || !pr->t_perm)
       return set_err(ctx, PF_ERR_INVALID_ARG,
@@ -308,6 +319,54 @@ pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
   const Workspace &ws = ctx->ws;
   const int degree = ctx->cur_degree;
   const bool lp = ctx->cur_lp;
+  if (pr->kind == PF_PROBLEM_NNLS) {
+    // G = (1+beta) X - beta Xp - A*(r): coefficients, residual r (in S), interval
+    PF_CUDA(launch_nnls_residual(s, ws, pr->rowptr, pr->colind, pr->t_rowptr, pr->t_perm,
+                                 pr->vals_f64, n, pr->fac, pr->ldfac, pr->fsv, pr->S, pr->theta));
+    Op og = {};  // G Z = [L | Lp] diag(coef) [R | Rp]^T Z - R_sp Z
+    og.kind = PF_OP_LOWRANK_SPARSE;
+    og.n = n;
+    og.Uf = pr->fac;
+    og.lduf = pr->ldfac;
+    og.Vf = pr->fac + 2 * p;
+    og.ldvf = pr->ldfac;
+    og.lam = ws.resid;
+    og.r = 2 * p;
+    og.rowptr = pr->rowptr;
+    og.colind = pr->colind;
+    og.vals = pr->S;
+    og.sscale = -1.0;
+    Op ot = og;  // G^T Z = [R | Rp] diag(coef) [L | Lp]^T Z - R_sp^T Z
+    ot.Uf = pr->fac + 2 * p;
+    ot.Vf = pr->fac;
+    ot.rowptr = pr->t_rowptr;
+    ot.colind = pr->t_colind;
+    ot.perm = pr->t_perm;
+    double *const *Yb = ws.Y;
+    for (int j = 0; j < degree; ++j) {
+      const double *cur = j == 0 ? pr->U : Yb[(j - 1) & 1];
+      const int64_t ldc = j == 0 ? pr->ldu : p;
+      const double *prev = j == 1 ? pr->U : Yb[j & 1];
+      const int64_t ldprev = j == 1 ? pr->ldu : p;
+      PF_CUDA(launch_lowrank_sparse_apply(s, ws, og, cur, ldc, nullptr, 0, ws.W, p, MODE_PLAIN));
+      PF_CUDA(launch_lowrank_sparse_apply(s, ws, ot, ws.W, p, j == 0 ? nullptr : prev, ldprev,
+                                          Yb[j & 1], p, j == 0 ? MODE_FIRST : MODE_RECUR, cur,
+                                          ldc));
+    }
+    PF_TRY(cholqr2(ctx, Yb[(degree - 1) & 1], p, pr->U, pr->ldu, n));
+    PF_CUDA(launch_lowrank_sparse_apply(s, ws, og, pr->U, pr->ldu, nullptr, 0, ws.W, p,
+                                        MODE_PLAIN));
+    int nb = 0;
+    PF_CUDA(launch_gram(s, ws, ws.W, p, ws.W, p, n, p, p, 0, &nb));
+    PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, pr->theta));
+    PF_CUDA(launch_apply_right(s, ws, pr->U, pr->ldu, pr->V, pr->ldv, n, p, ws.Yeig, 0, 0));
+    PF_CUDA(launch_apply_right(s, ws, ws.W, p, Yb[0], p, n, p, ws.Yeig, 0, 0));
+    const int cap = pr->rank_cap > 0 ? pr->rank_cap : (p > 8 ? p - 8 : 1);
+    PF_CUDA(launch_nnls_update(s, ws, n, pr->fac, pr->ldfac, pr->fsv, Yb[0], pr->V, pr->ldv,
+                               pr->theta, cap));
+    PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
+    return PF_OK;
+  }
   if (pr->kind == PF_PROBLEM_SVT) {
     // interval on Y^T Y, Y = A*(x) (values x in S)
     PF_CUDA(launch_svt_interval(s, ws, pr->rowptr, pr->t_rowptr, pr->t_perm, pr->S, n,
@@ -477,7 +536,8 @@ bool same_problem(const pf_problem &a, const pf_problem &b) {
          a.Z_lp == b.Z_lp && a.ldz_lp == b.ldz_lp && a.accel_l == b.accel_l &&
          a.accel_lam == b.accel_lam && a.hist == b.hist && a.p_active == b.p_active &&
          a.guard == b.guard && a.ldg == b.ldg && a.t_rowptr == b.t_rowptr &&
-         a.t_colind == b.t_colind && a.t_perm == b.t_perm;
+         a.t_colind == b.t_colind && a.t_perm == b.t_perm && a.fac == b.fac &&
+         a.ldfac == b.ldfac && a.fsv == b.fsv && a.rank_cap == b.rank_cap;
 }
 
 bool graph_matches(const pf_ctx *ctx, const pf_problem &pr) {
@@ -699,6 +759,11 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
     PF_CUDA(launch_params_init(s, ws.prm, ctx->opt.eta, pr->t, pr->mu, ctx->opt.degree,
                                ctx->opt.precision));
     PF_CUDA(launch_svt_init(s, ws, pr->vals_f64, pr->nnz, pr->t, pr->S));
+  }
+  if (pr->kind == PF_PROBLEM_NNLS) {
+    PF_CUDA(launch_fill(s, pr->fac, n, 4 * p, pr->ldfac, 0.0));
+    PF_CUDA(launch_nnls_init(s, ws, pr->rowptr, pr->t_rowptr, pr->t_perm, pr->vals_f64, n, pr->t,
+                             pr->mu, pr->fsv));
   }
   if (pr->kind == PF_PROBLEM_NCE) {
     if (!(pr->t > 0.0)) pr->t = 1.0;

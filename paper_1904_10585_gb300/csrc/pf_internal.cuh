@@ -48,6 +48,8 @@ struct Params {
   double lz_alpha[16], lz_beta[16];
   double a_lz;            // theta_min - residual bound
   int lz_m;               // Lanczos steps taken (fewer than kLanczos on breakdown)
+  // NNLS (accelerated proximal gradient): momentum scalars and continuation
+  double nn_t, nn_tp, nn_beta, nn_mu, nn_mubar;
 };
 
 // Lanczos steps of the NCE interval estimate (Sec. 4.1)
@@ -62,6 +64,11 @@ struct Op {
   const double *Uf; int64_t lduf; const double *lam; int r; int clamp;
   const int32_t *rowptr; const int32_t *colind; const double *vals;
   double sscale, shift;
+  // non-symmetric low-rank part Uf diag(lam) Vf^T (Vf = nullptr: Vf = Uf), and
+  // a sparse part read through a value permutation (vals[perm[e]], the
+  // transposed pattern of a non-symmetric matrix); both optional
+  const double *Vf; int64_t ldvf;
+  const int32_t *perm;
 };
 
 struct Workspace {
@@ -113,7 +120,8 @@ cudaError_t launch_dense_apply(cudaStream_t s, const Workspace &ws, const Op &op
                                int64_t ldn, int mode);
 cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, const Op &op,
                                         const double *X, int64_t ldx, const double *Yprev,
-                                        int64_t ldp, double *Ynext, int64_t ldn, int mode);
+                                        int64_t ldp, double *Ynext, int64_t ldn, int mode,
+                                        const double *Xr = nullptr, int64_t ldr = 0);
 cudaError_t launch_gram(cudaStream_t s, const Workspace &ws, const double *X, int64_t ldx,
                         const double *Y, int64_t ldy, int n, int px, int py, int cond_flag,
                         int *nblocks_out, bool sym = false);
@@ -208,6 +216,18 @@ cudaError_t launch_svt_update(cudaStream_t s, const Workspace &ws, const int32_t
                               double mu, double tau, double *x);
 cudaError_t launch_svt_init(cudaStream_t s, const Workspace &ws, const double *mvals, int64_t nnz,
                             double tau, double *x);
+// PFNNLS (pf_svt.cu); fac = [L | Lp | R | Rp] (n x 4p, ldfac), fsv = [s | sp]
+cudaError_t launch_nnls_init(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                             const int32_t *t_rowptr, const int32_t *t_perm, const double *mvals,
+                             int n, double mu0, double mubar_rel, double *fsv);
+cudaError_t launch_nnls_residual(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                 const int32_t *colind, const int32_t *t_rowptr,
+                                 const int32_t *t_perm, const double *mvals, int n,
+                                 const double *fac, int64_t ldfac, const double *fsv, double *r,
+                                 const double *theta);
+cudaError_t launch_nnls_update(cudaStream_t s, const Workspace &ws, int n, double *fac,
+                               int64_t ldfac, double *fsv, const double *BY, const double *V,
+                               int64_t ldv, const double *theta, int cap);
 cudaError_t launch_grow_block(cudaStream_t s, const Workspace &ws, double *U, int64_t ldu,
                               double *V, int64_t ldv, double *theta, int n, int p_old, int p_new,
                               const double *guard, int64_t ldg);

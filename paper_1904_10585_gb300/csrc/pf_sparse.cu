@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
     const double *__restrict__ svals, int n, int p, const double *__restrict__ Uf, int64_t lduf,
     int r, const double *__restrict__ T, double sscale, double shift, const double *X, int64_t ldx,
     const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn, const Params *__restrict__ prm,
-    int mode) {
+    int mode, const int32_t *__restrict__ perm, const double *Xr, int64_t ldr) {
   __shared__ double Ts[kMaxP * kMaxP];
   for (int idx = threadIdx.x; idx < r * p; idx += NT) Ts[idx] = T[idx];
   __syncthreads();
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
       for (int base = e0; base < e1; base += 32) {
         const int my = base + lane;
         const int mcol = my < e1 ? colind[my] : 0;
-        const double mv = my < e1 ? svals[my] : 0.0;
+        const double mv = my < e1 ? svals[perm != nullptr ? perm[my] : my] : 0.0;
         const int cnt = min(32, e1 - base);
         for (int k = 0; k < cnt; k += 2) {
           const int kk = k + half;  // half 0: even entries, half 1: odd entries
@@ -63,6 +63,9 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
         }
       }
     }
+    // the block of the shift and recurrence terms (the input unless given)
+    const double *Xb = Xr != nullptr ? Xr : X;
+    const int64_t ldb = Xr != nullptr ? ldr : ldx;
     // low-rank part, terms l = half, half + 2, ...
     const double *ur = Uf + (int64_t)row * lduf;
     for (int l = half; l < r; l += 2) {
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
       for (int g = 0; g < JG; ++g) {
         const int j = hl + 16 * g;
         if (j >= p) continue;
-        const double xij = X[(int64_t)row * ldx + j];
+        const double xij = Xb[(int64_t)row * ldb + j];
         const double o = lr[g] + sscale * acc[g] + shift * xij;
         double y;
         if (mode == MODE_PLAIN) y = o;
@@ -532,12 +535,15 @@ int red_blocks(int n, int num_sms) {
 
 cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, const Op &op,
                                         const double *X, int64_t ldx, const double *Yprev,
-                                        int64_t ldp, double *Ynext, int64_t ldn, int mode) {
+                                        int64_t ldp, double *Ynext, int64_t ldn, int mode,
+                                        const double *Xr, int64_t ldr) {
   const int n = op.n, p = ws.p;
   int r = op.r;
   if (r > 0 && op.Uf != nullptr) {
     int nb = 0;
-    cudaError_t e = launch_gram(s, ws, op.Uf, op.lduf, X, ldx, n, r, p, 0, &nb);
+    const double *Rf = op.Vf != nullptr ? op.Vf : op.Uf;
+    const int64_t ldrf = op.Vf != nullptr ? op.ldvf : op.lduf;
+    cudaError_t e = launch_gram(s, ws, Rf, ldrf, X, ldx, n, r, p, 0, &nb);
     if (e != cudaSuccess) return e;
     e = launch_lowrank_coef(s, ws, nb, op.lam, r, p, op.clamp);
     if (e != cudaSuccess) return e;
@@ -549,7 +555,7 @@ cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, con
 #define PF_LRSP(JGV)                                                                            \
   k_lrsp_apply<JGV><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf, op.lduf, r, \
                                           ws.T, op.sscale, op.shift, X, ldx, Yprev, ldp, Ynext,   \
-                                          ldn, ws.prm, mode)
+                                          ldn, ws.prm, mode, op.perm, Xr, ldr)
   if (p <= 16) { PF_LRSP(1); }
   else if (p <= 32) { PF_LRSP(2); }
   else if (p <= 48) { PF_LRSP(3); }

@@ -135,7 +135,10 @@ class Problem:
     hist: Optional[torch.Tensor] = None
     accel_l: int = 0
     accel_lam: float = 0.0
-    t_pattern: Optional[tuple] = None      # SVT: transposed pattern (rowptr, colind, perm)
+    t_pattern: Optional[tuple] = None      # SVT, NNLS: transposed pattern (rowptr, colind, perm)
+    fac: Optional[torch.Tensor] = None     # NNLS: [L | Lp | R | Rp], n x 4p
+    fsv: Optional[torch.Tensor] = None     # NNLS: [s | sp]
+    rank_cap: int = 0
     guard: Optional[torch.Tensor] = None   # n x p random columns for width growth
     p_active: int = 0                      # start width (0: the context's p)
     struct: Optional[B.pf_problem] = None
@@ -160,11 +163,14 @@ class Problem:
                 s.accel_lam = self.accel_lam
             self.struct = s
             return s
-        if self.kind == B.PF_PROBLEM_SVT:
+        if self.kind in (B.PF_PROBLEM_SVT, B.PF_PROBLEM_NNLS):
             s.vals_f64 = _ptr(self.vals)
             s.S = _ptr(self.S)
             tr, tc, tp = self.t_pattern
             s.t_rowptr, s.t_colind, s.t_perm = _ptr(tr), _ptr(tc), _ptr(tp)
+            if self.kind == B.PF_PROBLEM_NNLS:
+                s.fac, s.ldfac, s.fsv = _ptr(self.fac), _ld(self.fac), _ptr(self.fsv)
+                s.rank_cap = self.rank_cap
             self.struct = s
             return s
         if self.kind == B.PF_PROBLEM_MAXCUT:
@@ -254,6 +260,25 @@ def svt_problem(rowptr, colind, mvals_f64, t_rowptr, t_colind, t_perm, U0: torch
                  theta=torch.zeros(p, dtype=torch.float64, device=dev),
                  S=torch.empty(colind.numel(), dtype=torch.float64, device=dev), t=tau, mu=mu)
     pr.t_pattern = (t_rowptr, t_colind, t_perm)
+    pr.make_struct()
+    return pr
+
+
+def nnls_problem(rowptr, colind, mvals_f64, t_rowptr, t_colind, t_perm, U0: torch.Tensor,
+                 mu_bar_rel: float = 1e-2, mu0: float = 0.0, rank_cap: int = 0) -> Problem:
+    """Nuclear-norm regularised least squares by PFNNLS (accelerated proximal
+    gradient with continuation to mu_bar = mu_bar_rel mu_0)."""
+    n, p = U0.shape
+    dev = U0.device
+    pr = Problem(kind=B.PF_PROBLEM_NNLS, n=n, rowptr=rowptr, colind=colind, vals=mvals_f64,
+                 U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
+                 theta=torch.zeros(p, dtype=torch.float64, device=dev),
+                 S=torch.empty(colind.numel(), dtype=torch.float64, device=dev), t=mu0,
+                 mu=mu_bar_rel)
+    pr.t_pattern = (t_rowptr, t_colind, t_perm)
+    pr.fac = torch.zeros(n, 4 * p, dtype=torch.float64, device=dev)
+    pr.fsv = torch.zeros(2 * p, dtype=torch.float64, device=dev)
+    pr.rank_cap = rank_cap
     pr.make_struct()
     return pr
 

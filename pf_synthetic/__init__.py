@@ -265,6 +265,8 @@ WORKLOADS = {
                               iters=100, mu=0.05, t=1.0, config_index=3),
     "svt_n5000": dict(kind="svt", n=5000, rank=10, sr=0.1, p=32, degree=1, iters=500,
                       config_index=6),
+    "nnls_n10000": dict(kind="nnls", n=10000, rank=10, sr=0.05, p=32, degree=1, iters=300,
+                        mu_bar_rel=1e-2, config_index=7),
 }
 
 
@@ -276,7 +278,7 @@ def make_workload(name: str, **overrides):
         rng_u = _streams(seed + 1, 1)[0]
         return cfg, NCEInstance(cfg["n"], nce_matrix(cfg["n"], cfg["example"], seed),
                                 rng_u.standard_normal((cfg["n"], cfg["p"])))
-    if cfg["kind"] == "svt":
+    if cfg["kind"] in ("svt", "nnls"):
         return cfg, svt_instance(cfg["n"], cfg["rank"], cfg["sr"], cfg["p"], seed)
     if cfg["kind"] == "completion":
         return cfg, completion_instance(cfg["n"], cfg["rank"], cfg["rate"], cfg["p"], seed,

@@ -686,3 +686,56 @@ def test_svt_and_pfsvt_recover_a_low_rank_matrix():
     M = I.ML @ I.MR.T
     L, s, R = o.svt_factors(I.omega, st_p, mu, tau, 1)
     assert np.linalg.norm((L * s) @ R.T - M) / np.linalg.norm(M) < 1e-3
+
+
+def test_nnls_converges_to_the_prox_gradient_fixed_point():
+    """With mu held fixed (no continuation) accelerated proximal gradient
+    converges to the minimiser of mu||X||_* + 1/2||P_Omega(X) - b||^2, the
+    fixed point X = shrink_mu(X - A*(A(X) - b)) (Sec. 5.2.2); the gradient and
+    the prox are recomputed here densely from the definitions."""
+    n = 40
+    I = syn.svt_instance(n, 2, 0.5, n, seed=5)
+    mu = 0.5
+    st, hist = o.nnls_solve(I.omega, I.U0_raw, 1, 3000, exact=True, tol=1e-12, mu0=mu,
+                            mu_bar_rel=1.0)
+    X = (st.L * st.s) @ st.R.T
+    mask = np.zeros((n, n))
+    rows = I.omega.row_of_entries()
+    mask[rows, I.omega.colind] = 1.0
+    Md = np.zeros((n, n))
+    Md[rows, I.omega.colind] = I.omega.vals
+    G = X - (mask * X - Md)
+    assert np.linalg.norm(o.shrink(G, mu) - X) <= 1e-8 * np.linalg.norm(X)
+    # and it beats nearby points on the objective
+    f = lambda Z: mu * np.linalg.svd(Z, compute_uv=False).sum() + 0.5 * np.sum((mask * Z - Md) ** 2)  # noqa: E731
+    rng = np.random.default_rng(0)
+    for _ in range(10):
+        assert f(X) <= f(X + 1e-4 * rng.standard_normal((n, n))) + 1e-12
+
+
+def test_pfnnls_full_block_is_exact_nnls():
+    n = 30
+    I = syn.svt_instance(n, 2, 0.5, n, seed=6)
+    _, h_e = o.nnls_solve(I.omega, I.U0_raw, 1, 12, exact=True, mu_bar_rel=1e-2)
+    _, h_p = o.nnls_solve(I.omega, I.U0_raw, 1, 12, mu_bar_rel=1e-2)
+    for a, b in zip(h_e, h_p):
+        assert a.svp == b.svp and abs(a.obj - b.obj) <= 1e-9 * abs(a.obj)
+        assert abs(a.rel - b.rel) <= 1e-8 * max(a.rel, 1e-3)
+
+
+def test_pfnnls_capped_matches_capped_nnls_and_recovers():
+    """Reading R15 (at most p - 8 pairs): exact NNLS and PFNNLS (degree 1)
+    reach the 1e-4 change with the same rank and nearly the same iterate, and
+    recover the rank-5 matrix (Tables 5.x report equal iter/svp/mse)."""
+    n, r, sr, p = 400, 5, 0.2, 16
+    I = syn.svt_instance(n, r, sr, p, seed=4)
+    M = I.ML @ I.MR.T
+    out = []
+    for exact in (True, False):
+        st, h = o.nnls_solve(I.omega, I.U0_raw, 1, 300, exact=exact, tol=1e-4, mu_bar_rel=1e-2,
+                             cap=p - 8)
+        out.append((len(h), h[-1].svp, (st.L * st.s) @ st.R.T))
+    assert out[0][1] == out[1][1] == r and abs(out[0][0] - out[1][0]) <= 5
+    for _, _, X in out:
+        assert np.linalg.norm(X - M) / np.linalg.norm(M) < 1e-2
+    assert np.linalg.norm(out[0][2] - out[1][2]) / np.linalg.norm(out[0][2]) < 1e-3
