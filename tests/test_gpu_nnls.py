@@ -35,7 +35,8 @@ def test_pfnnls_matches_oracle(n, r, sr, p, d, iters):
         h_g = [S.prox_step(ctx, pr) for _ in range(iters)]
         ctx.stream.synchronize()
     for k, (a, b) in enumerate(zip(h_g, h_o)):
-        assert abs(a.b - b.b) <= 1e-8 * abs(b.b), (k, a.b, b.b)
+        # b follows the smallest Ritz value, accurate to rounding relative to the largest
+        assert abs(a.b - b.b) <= 1e-8 * max(abs(b.b), b.theta[0]), (k, a.b, b.b)
         assert abs(a.dinf - b.mu) <= 1e-12 * b.mu, (k, a.dinf, b.mu)
         assert a.r_plus == b.svp, k
         assert abs(a.pinf - b.rel) <= 1e-8 * max(b.rel, 1e-3), (k, a.pinf, b.rel)
