@@ -81,3 +81,21 @@ def test_status_strings_need_no_gpu(lib_path):
     # argument validation happens before any CUDA call
     assert pkg.raw_call("pf_create", None, 10, None, None) == pkg.PF_ERR_INVALID_ARG
     assert pkg.raw_call("pf_destroy", None) == pkg.PF_ERR_INVALID_ARG
+
+
+def test_enum_values_match_header():
+    """Every PF_* enumerator of the header has the same value in the binding."""
+    import paper_1904_10585_gb300._binding as B
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    found = 0
+    for body in re.findall(r"typedef enum\s*\{(.*?)\}", text, flags=re.S):
+        value = -1
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            m = re.match(r"(PF_\w+)\s*(?:=\s*(-?\d+))?", item)
+            value = int(m.group(2)) if m.group(2) is not None else value + 1
+            assert getattr(B, m.group(1)) == value, m.group(1)
+            found += 1
+    assert found >= 19
