@@ -45,7 +45,10 @@ FP64_CUBLAS_MEASURED = 1.09    # torch float64 matmul 16384x16384x64 on this poo
 HBM_PEAK_GBS = 6773.2          # measured STREAM-style copy on the GB300s
 # dram bytes per launch of the dominant kernel from the committed ncu captures
 # (None until a capture of the current kernel exists)
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {
+    # profiles/k_gemm_f64_splitk_maxcut_n4096.md: 135.29 MB read + 7.19 MB written per launch
+    "maxcut_n4096": 142.48e6,
+}
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
