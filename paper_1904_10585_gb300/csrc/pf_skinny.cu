@@ -75,14 +75,26 @@ __global__ void __launch_bounds__(NT) k_gram(const double *__restrict__ X, int64
 }
 
 // In-place fixed-order reduction of the Gram partials into partial 0:
-// out[idx] = sum_q part[q][idx], one thread per output element.
-__global__ void k_gram_reduce(double *__restrict__ gpart, int nparts, int m) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m) return;
-  double s = gpart[idx];
-#pragma unroll 8
-  for (int q = 1; q < nparts; ++q) s += gpart[(int64_t)q * m + idx];
-  gpart[idx] = s;
+// out[idx] = sum_q part[q][idx].  A block covers 32 outputs with 8 threads
+// each: thread q sums partials q, q + 8, q + 16, ... in order, then the 8
+// sub-sums are added in a fixed tree (deterministic, 8x the parallelism of
+// one thread per output).
+constexpr int GR_OUT = 32, GR_SUB = 8;
+__global__ void __launch_bounds__(GR_OUT * GR_SUB) k_gram_reduce(double *__restrict__ gpart,
+                                                                 int nparts, int m) {
+  __shared__ double sub[GR_SUB][GR_OUT];
+  const int o = threadIdx.x & (GR_OUT - 1), q0 = threadIdx.x / GR_OUT;
+  const int idx = blockIdx.x * GR_OUT + o;
+  double s = 0.0;
+  if (idx < m)
+    for (int q = q0; q < nparts; q += GR_SUB) s += gpart[(int64_t)q * m + idx];
+  sub[q0][o] = s;
+  __syncthreads();
+  if (q0 == 0 && idx < m) {
+    const double a = (sub[0][o] + sub[1][o]) + (sub[2][o] + sub[3][o]);
+    const double b = (sub[4][o] + sub[5][o]) + (sub[6][o] + sub[7][o]);
+    gpart[idx] = a + b;
+  }
 }
 
 // Sum Gram partials, Cholesky G = R^T R (upper R), write R^{-1}.
@@ -392,7 +404,7 @@ cudaError_t launch_gram(cudaStream_t s, const Workspace &ws, const double *X, in
   // reduce the partials in place so that consumers read one matrix
   if (nb > 1) {
     const int m = px * py;
-    k_gram_reduce<<<(m + 255) / 256, 256, 0, s>>>(ws.gpart, nb, m);
+    k_gram_reduce<<<(m + GR_OUT - 1) / GR_OUT, GR_OUT * GR_SUB, 0, s>>>(ws.gpart, nb, m);
     PF_LAUNCHED();
     e = cudaGetLastError();
   }
