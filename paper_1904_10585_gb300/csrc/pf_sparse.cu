@@ -423,56 +423,29 @@ __global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ re
 // ---------------------------------------------------------------------------
 // PSD completion: S = P_Omega(X - M) with X = V diag(max(theta,0)) V^T.
 // ---------------------------------------------------------------------------
-// Half-warps take alternate entries of a row; the 16 lanes of a half cover
-// the factor columns (l = lane + 16 g), so each entry reads its row of V
-// with coalesced loads and the dot product ends in a 16-lane reduction.
-template <int JG>
 __global__ void __launch_bounds__(NT) k_completion_residual(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const float *__restrict__ mvals, int n, int p, const double *__restrict__ V, int64_t ldv,
     const double *__restrict__ theta, double *__restrict__ S, double *__restrict__ red) {
+  __shared__ double wv[WPB][kMaxP];
   __shared__ double sh[32];
-  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int warps = gridDim.x * WPB;
-  double thp[JG];
-#pragma unroll
-  for (int g = 0; g < JG; ++g) {
-    const int l = hl + 16 * g;
-    thp[g] = (l < p && theta[l] > 0.0) ? theta[l] : 0.0;
-  }
+  int rp = 0;
+  for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
   double ssq = 0.0;
-  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
-    double a[JG];
-#pragma unroll
-    for (int g = 0; g < JG; ++g) {
-      const int l = hl + 16 * g;
-      a[g] = l < p ? V[(int64_t)row * ldv + l] * thp[g] : 0.0;
+  for (int row = blockIdx.x * WPB + w; row < n; row += warps) {
+    for (int l = lane; l < rp; l += 32) wv[w][l] = V[(int64_t)row * ldv + l] * theta[l];
+    __syncwarp();
+    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+      const int col = colind[e];
+      double x = 0.0;
+      for (int l = 0; l < rp; ++l) x = fma(wv[w][l], V[(int64_t)col * ldv + l], x);
+      const double s = x - (double)mvals[e];
+      S[e] = s;
+      ssq = fma(s, s, ssq);
     }
-    const int e0 = rowptr[row], e1 = rowptr[row + 1];
-    for (int base = e0; base < e1; base += 32) {
-      const int my = base + lane;
-      const int mcol = my < e1 ? colind[my] : 0;
-      const int cnt = min(32, e1 - base);
-      for (int k = 0; k < cnt; k += 2) {
-        const int kk = k + half;
-        const int col = __shfl_sync(0xffffffffu, mcol, kk);
-        const double *vr = V + (int64_t)col * ldv;
-        double x = 0.0;
-#pragma unroll
-        for (int g = 0; g < JG; ++g) {
-          const int l = hl + 16 * g;
-          if (l < p) x = fma(a[g], vr[l], x);
-        }
-#pragma unroll
-        for (int off = 8; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        if (hl == 0 && kk < cnt) {
-          const int e = base + kk;
-          const double sv = x - (double)mvals[e];
-          S[e] = sv;
-          ssq = fma(sv, sv, ssq);
-        }
-      }
-    }
+    __syncwarp();
   }
   ssq = block_reduce(ssq, sh, 0);
   if (threadIdx.x == 0) red[blockIdx.x * kRedWidth] = ssq;
@@ -720,14 +693,8 @@ cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, cons
                                        const double *V, int64_t ldv, const double *theta,
                                        double *S) {
   const int nb = red_blocks(n, ws.num_sms);
-#define PF_CR(JGV)                                                                           \
-  k_completion_residual<JGV><<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, V, ldv, theta, S, \
-                                               slot(ws, SLOT_SDDMM))
-  if (p <= 16) { PF_CR(1); }
-  else if (p <= 32) { PF_CR(2); }
-  else if (p <= 48) { PF_CR(3); }
-  else { PF_CR(4); }
-#undef PF_CR
+  k_completion_residual<<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, V, ldv, theta, S,
+                                          slot(ws, SLOT_SDDMM));
   PF_LAUNCHED();
   return cudaGetLastError();
 }

@@ -134,63 +134,42 @@ __global__ void __launch_bounds__(NT) k_svt_interval_final(const double *__restr
 
 // w_e = sum_l L[i][l] s_l R[j][l], s_l = (sigma_l - mu)_+ / sigma_l with
 // sigma_l = sqrt(theta_l); r_e = m_e - w_e; x_e += tau r_e.  Partial sums:
-// sum r^2, sum m x (before the update), sum m^2.  Half-warps take alternate
-// entries; the 16 lanes of a half cover the factor columns (coalesced rows of
-// R) and reduce the dot product among themselves.
-template <int JG>
+// sum r^2, sum m x (before the update), sum m^2.
 __global__ void __launch_bounds__(NT) k_svt_update(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const double *__restrict__ mvals, int n, int p, const double *__restrict__ L, int64_t ldl,
     const double *__restrict__ R, int64_t ldr, const double *__restrict__ theta, double mu,
     double tau, double *__restrict__ x, double *__restrict__ red) {
+  __shared__ double sl[kMaxP];
+  __shared__ double wv[WPB][kMaxP];
   __shared__ double sh[32];
-  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int warps = gridDim.x * WPB;
-  double sl[JG];
-#pragma unroll
-  for (int g = 0; g < JG; ++g) {
-    const int l = hl + 16 * g;
-    const double th = l < p ? theta[l] : 0.0;
-    const double sg = th > 0.0 ? sqrt(th) : 0.0;
-    sl[g] = sg > mu ? (sg - mu) / sg : 0.0;
+  // singular values above mu lead (theta is sorted descending)
+  int keep = 0;
+  for (int l = 0; l < p; ++l) keep += (theta[l] > 0.0 && sqrt(theta[l]) > mu) ? 1 : 0;
+  for (int l = threadIdx.x; l < p; l += NT) {
+    const double sg = theta[l] > 0.0 ? sqrt(theta[l]) : 0.0;
+    sl[l] = sg > mu ? (sg - mu) / sg : 0.0;
   }
+  __syncthreads();
   double rr = 0.0, mx = 0.0, mm = 0.0;
-  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
-    double a[JG];
-#pragma unroll
-    for (int g = 0; g < JG; ++g) {
-      const int l = hl + 16 * g;
-      a[g] = (l < p && sl[g] != 0.0) ? L[(int64_t)row * ldl + l] * sl[g] : 0.0;
+  for (int row = blockIdx.x * WPB + w; row < n; row += warps) {
+    for (int l = lane; l < keep; l += 32) wv[w][l] = L[(int64_t)row * ldl + l] * sl[l];
+    __syncwarp();
+    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+      const int col = colind[e];
+      double wsum = 0.0;
+      for (int l = 0; l < keep; ++l) wsum = fma(wv[w][l], R[(int64_t)col * ldr + l], wsum);
+      const double m = mvals[e];
+      const double r = m - wsum;
+      const double xo = x[e];
+      x[e] = fma(tau, r, xo);
+      rr = fma(r, r, rr);
+      mx = fma(m, xo, mx);
+      mm = fma(m, m, mm);
     }
-    const int e0 = rowptr[row], e1 = rowptr[row + 1];
-    for (int base = e0; base < e1; base += 32) {
-      const int my = base + lane;
-      const int mcol = my < e1 ? colind[my] : 0;
-      const int cnt = min(32, e1 - base);
-      for (int k = 0; k < cnt; k += 2) {
-        const int kk = k + half;
-        const int col = __shfl_sync(0xffffffffu, mcol, kk);
-        const double *rr_ = R + (int64_t)col * ldr;
-        double w = 0.0;
-#pragma unroll
-        for (int g = 0; g < JG; ++g) {
-          const int l = hl + 16 * g;
-          if (l < p) w = fma(a[g], rr_[l], w);
-        }
-#pragma unroll
-        for (int off = 8; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
-        if (hl == 0 && kk < cnt) {
-          const int e = base + kk;
-          const double m = mvals[e];
-          const double r = m - w;
-          const double xo = x[e];
-          x[e] = fma(tau, r, xo);
-          rr = fma(r, r, rr);
-          mx = fma(m, xo, mx);
-          mm = fma(m, m, mm);
-        }
-      }
-    }
+    __syncwarp();
   }
   rr = block_reduce(rr, sh, 0);
   mx = block_reduce(mx, sh, 0);
@@ -266,66 +245,37 @@ __global__ void k_nnls_coef(const double *__restrict__ fsv, int p, double *__res
 }
 
 // r_e = A(Y) - b on Omega with Y = (1 + beta) X - beta Xp; partial sum of
-// (x_e - m_e)^2 (the objective's data term at X).  Half-warps take alternate
-// entries, lanes cover the factor columns (coalesced rows of R and Rp).
-template <int JG>
+// (x_e - m_e)^2 (the objective's data term at X).
 __global__ void __launch_bounds__(NT) k_nnls_resid(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const double *__restrict__ mvals, int n, int p, const double *__restrict__ fac, int64_t ldf,
     const double *__restrict__ fsv, const Params *__restrict__ prm, double *__restrict__ r,
     double *__restrict__ red) {
+  __shared__ double wl[WPB][kMaxP / 2], wp[WPB][kMaxP / 2];
   __shared__ double sh[32];
-  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int warps = gridDim.x * WPB;
   const double beta = prm->nn_beta;
-  double sc[JG], sp[JG];
-#pragma unroll
-  for (int g = 0; g < JG; ++g) {
-    const int l = hl + 16 * g;
-    sc[g] = l < p ? fsv[l] : 0.0;
-    sp[g] = l < p ? fsv[p + l] : 0.0;
-  }
   double dd = 0.0;
-  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
+  for (int row = blockIdx.x * WPB + w; row < n; row += warps) {
     const double *fr = fac + (int64_t)row * ldf;
-    double al[JG], ap[JG];
-#pragma unroll
-    for (int g = 0; g < JG; ++g) {
-      const int l = hl + 16 * g;
-      al[g] = l < p ? fr[l] * sc[g] : 0.0;
-      ap[g] = l < p ? fr[p + l] * sp[g] : 0.0;
+    for (int l = lane; l < p; l += 32) {
+      wl[w][l] = fr[l] * fsv[l];
+      wp[w][l] = fr[p + l] * fsv[p + l];
     }
-    const int e0 = rowptr[row], e1 = rowptr[row + 1];
-    for (int base = e0; base < e1; base += 32) {
-      const int my = base + lane;
-      const int mcol = my < e1 ? colind[my] : 0;
-      const int cnt = min(32, e1 - base);
-      for (int k = 0; k < cnt; k += 2) {
-        const int kk = k + half;
-        const int col = __shfl_sync(0xffffffffu, mcol, kk);
-        const double *fc = fac + (int64_t)col * ldf;
-        double xn = 0.0, xp = 0.0;
-#pragma unroll
-        for (int g = 0; g < JG; ++g) {
-          const int l = hl + 16 * g;
-          if (l < p) {
-            xn = fma(al[g], fc[2 * p + l], xn);
-            xp = fma(ap[g], fc[3 * p + l], xp);
-          }
-        }
-#pragma unroll
-        for (int off = 8; off > 0; off >>= 1) {
-          xn += __shfl_xor_sync(0xffffffffu, xn, off);
-          xp += __shfl_xor_sync(0xffffffffu, xp, off);
-        }
-        if (hl == 0 && kk < cnt) {
-          const int e = base + kk;
-          const double m = mvals[e];
-          r[e] = (1.0 + beta) * xn - beta * xp - m;
-          dd = fma(xn - m, xn - m, dd);
-        }
+    __syncwarp();
+    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+      const double *fc = fac + (int64_t)colind[e] * ldf;
+      double xn = 0.0, xp = 0.0;
+      for (int l = 0; l < p; ++l) {
+        xn = fma(wl[w][l], fc[2 * p + l], xn);
+        xp = fma(wp[w][l], fc[3 * p + l], xp);
       }
+      const double m = mvals[e];
+      r[e] = (1.0 + beta) * xn - beta * xp - m;
+      dd = fma(xn - m, xn - m, dd);
     }
+    __syncwarp();
   }
   dd = block_reduce(dd, sh, 0);
   if (threadIdx.x == 0) red[blockIdx.x * kRedWidth] = dd;
@@ -519,14 +469,8 @@ cudaError_t launch_svt_update(cudaStream_t s, const Workspace &ws, const int32_t
                               double mu, double tau, double *x) {
   const int nb = row_blocks(n, ws.num_sms);
   double *slot = red_slot(ws, SLOT_SDDMM);
-#define PF_SU(JGV)                                                                          \
-  k_svt_update<JGV><<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, ws.p, L, ldl, R, ldr, theta, mu, \
-                                      tau, x, slot)
-  if (ws.p <= 16) { PF_SU(1); }
-  else if (ws.p <= 32) { PF_SU(2); }
-  else if (ws.p <= 48) { PF_SU(3); }
-  else { PF_SU(4); }
-#undef PF_SU
+  k_svt_update<<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, ws.p, L, ldl, R, ldr, theta, mu, tau,
+                                 x, slot);
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -561,12 +505,8 @@ cudaError_t launch_nnls_residual(cudaStream_t s, const Workspace &ws, const int3
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nb = row_blocks(n, ws.num_sms);
-  if (p <= 16)
-    k_nnls_resid<1><<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, fac, ldfac, fsv, ws.prm, r,
-                                      red_slot(ws, SLOT_SDDMM));
-  else
-    k_nnls_resid<2><<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, fac, ldfac, fsv, ws.prm, r,
-                                      red_slot(ws, SLOT_SDDMM));
+  k_nnls_resid<<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, fac, ldfac, fsv, ws.prm, r,
+                                 red_slot(ws, SLOT_SDDMM));
   PF_LAUNCHED();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
