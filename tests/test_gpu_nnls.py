@@ -39,7 +39,9 @@ def test_pfnnls_matches_oracle(n, r, sr, p, d, iters):
         assert abs(a.b - b.b) <= 1e-8 * max(abs(b.b), b.theta[0]), (k, a.b, b.b)
         assert abs(a.dinf - b.mu) <= 1e-12 * b.mu, (k, a.dinf, b.mu)
         assert a.r_plus == b.svp, k
-        assert abs(a.pinf - b.rel) <= 1e-8 * max(b.rel, 1e-3), (k, a.pinf, b.rel)
+        # the change norm comes from ||Xn||^2 + ||X||^2 - 2<Xn, X> (factor Grams):
+        # the cancellation leaves it an absolute accuracy of about 1e-12 / rel
+        assert abs(a.pinf - b.rel) <= 1e-9, (k, a.pinf, b.rel)
         assert abs(a.obj - b.obj) <= 1e-8 * abs(b.obj), (k, a.obj, b.obj)
 
 
