@@ -217,7 +217,11 @@ typedef struct {
   double theta_max, theta_min;
   int32_t r_plus;            /* number of positive Ritz values               */
   int32_t flags;             /* bit 0: shifted CholQR pass used; bit 1: Cholesky
-                                breakdown; bit 2: non-finite Ritz value        */
+                                breakdown; bit 2: non-finite Ritz value; bit 3:
+                                a bounded device wait ran out; bit 4: the block
+                                is saturated, r_plus >= p - 2 on each of the
+                                last 20 steps (p too small for the solution
+                                rank, Sec. 4.2)                                 */
   int32_t degree;            /* degree used by the step                      */
   int32_t precision;         /* precision used by the step                   */
   int32_t jacobi_sweeps;     /* sweeps of the p x p eigensolve of the step   */

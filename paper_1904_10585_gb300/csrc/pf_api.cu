@@ -311,8 +311,17 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
   return PF_OK;
 }
 
-// One PFAM / PFPG step, enqueued only (graph-capturable).
+pf_status step_body(pf_ctx *ctx, const pf_problem *pr);
+
+// One step of the problem's method, enqueued only (graph-capturable), then
+// the saturation count of the block.
 pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
+  PF_TRY(step_body(ctx, pr));
+  PF_CUDA(launch_step_end(ctx->stream, ctx->ws));
+  return PF_OK;
+}
+
+pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
   const int p = ctx->ws.p;  // active width
   const int n = (int)pr->n;
   cudaStream_t s = ctx->stream;

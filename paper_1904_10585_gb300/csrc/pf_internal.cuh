@@ -41,6 +41,7 @@ struct Params {
   int degree;
   int precision;
   int sweeps;             // sweeps of the last p x p eigensolve
+  int sat_run;            // consecutive steps with r_plus >= p - 2
   int acc_count;          // NCE extrapolation: iterates held in the window
   int acc_go;             // NCE extrapolation: the combination below is due
   double acc_c[PF_MAX_ACCEL + 1];  // its coefficients c_0..c_l
@@ -232,6 +233,7 @@ cudaError_t launch_grow_block(cudaStream_t s, const Workspace &ws, double *U, in
                               double *V, int64_t ldv, double *theta, int n, int p_old, int p_new,
                               const double *guard, int64_t ldg);
 cudaError_t launch_export_info(cudaStream_t s, const Workspace &ws, int degree, int precision);
+cudaError_t launch_step_end(cudaStream_t s, const Workspace &ws);
 cudaError_t launch_params_init(cudaStream_t s, Params *prm, double eta, double t, double mu,
                                int degree, int precision);
 

@@ -67,16 +67,26 @@ __device__ __forceinline__ void rotation(double hkk, double hll, double hkl, dou
   s = t * y;
 }
 
-constexpr int JC = 8;      // CTAs per cluster
+constexpr int JC = 8;      // CTAs per cluster (p > 32)
 constexpr int JNT = 256;   // threads per CTA
 constexpr int JLD = kMaxP + 1;
-constexpr int JROWS = (kMaxP + JC - 1) / JC;  // eigenvector rows per CTA
 
-__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
-    k_jacobi_cluster(const double *__restrict__ Hin, int p, double *__restrict__ Yeig,
-                     double *__restrict__ theta, Params *prm) {
+// The sweep loop, on NC CTAs: NC = 8 (a thread-block cluster, distributed
+// shared memory, one cluster barrier per round) or NC = 1 (one CTA holds
+// everything and a block barrier orders the rounds; at p <= 32 the FP64 work
+// of a round is small enough that one SM beats the cluster's barrier and
+// broadcast cost).
+template <int NC>
+__device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int p,
+                                            double *__restrict__ Yeig,
+                                            double *__restrict__ theta, Params *prm) {
+  constexpr int JROWS = (kMaxP + NC - 1) / NC;  // eigenvector rows per CTA
   cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
+  const int rank = NC > 1 ? (int)cluster.block_rank() : 0;
+  auto sync_all = [&]() {
+    if constexpr (NC > 1) cluster.sync();
+    else __syncthreads();
+  };
   extern __shared__ double dyn[];
   double *Hb[2] = {dyn, dyn + kMaxP * JLD};
   double *Vloc = dyn + 2 * kMaxP * JLD;  // JROWS x JLD
@@ -87,7 +97,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
   const int tid = threadIdx.x;
   const int m = p + (p & 1);          // players (index p is a dummy when p is odd)
   const int half = m / 2;
-  const int ppc = (half + JC - 1) / JC;
+  const int ppc = (half + NC - 1) / NC;
   const int pair0 = rank * ppc, pair1 = min(half, pair0 + ppc);
   const int row0 = rank * JROWS, row1 = min(p, row0 + JROWS);
 
@@ -100,7 +110,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
     const int r = idx / p, b = idx % p;
     Vloc[r * JLD + b] = (row0 + r == b) ? 1.0 : 0.0;
   }
-  cluster.sync();  // every CTA has started before any remote store
+  sync_all();  // every CTA has started before any remote store
   int cur = 0;
   int sweeps_done = 0;
   for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
@@ -156,15 +166,15 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
         const double h00 = ci * m00 - si * m10, h11 = si * m01 + ci * m11;
         double h01 = ci * m01 - si * m11, h10 = si * m00 + ci * m10;
         if (i == j) h01 = h10 = 0.5 * (h01 + h10);  // the rotated pair block stays symmetric
-        for (int q = 0; q < JC; ++q) {
-          double *dst = cluster.map_shared_rank(Hn, q);
+        for (int q = 0; q < NC; ++q) {
+          double *dst = NC > 1 ? cluster.map_shared_rank(Hn, q) : Hn;
           dst[ki * JLD + kj] = h00;
           if (rj) dst[ki * JLD + lj] = h01;
           if (ri) dst[li * JLD + kj] = h10;
           if (ri && rj) dst[li * JLD + lj] = h11;
         }
       }
-      cluster.sync();
+      sync_all();
       cur ^= 1;
     }
     sweeps_done = sweep + 1;
@@ -187,21 +197,40 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
   }
   if (bad && rank == 0) atomicOr(&prm->flags, 4);
   if (rank == 0 && tid == 0) prm->sweeps = sweeps_done;
-  cluster.sync();  // no CTA leaves while its shared memory may still be written
+  sync_all();  // no CTA leaves while its shared memory may still be written
 }
 
-constexpr size_t kJacobiBytes = (size_t)(2 * kMaxP * JLD + JROWS * JLD) * sizeof(double);
+__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
+    k_jacobi_cluster(const double *__restrict__ Hin, int p, double *__restrict__ Yeig,
+                     double *__restrict__ theta, Params *prm) {
+  jacobi_body<JC>(Hin, p, Yeig, theta, prm);
+}
+
+__global__ void __launch_bounds__(JNT)
+    k_jacobi_block(const double *__restrict__ Hin, int p, double *__restrict__ Yeig,
+                   double *__restrict__ theta, Params *prm) {
+  jacobi_body<1>(Hin, p, Yeig, theta, prm);
+}
+
+constexpr size_t jacobi_bytes(int nc) {
+  return (size_t)(2 * kMaxP * JLD + ((kMaxP + nc - 1) / nc) * JLD) * sizeof(double);
+}
 
 }  // namespace
 
 cudaError_t configure_jacobi() {
-  return cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kJacobiBytes);
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_cluster,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)jacobi_bytes(JC));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_jacobi_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)jacobi_bytes(1));
 }
 
 cudaError_t launch_jacobi_cluster(cudaStream_t s, const Workspace &ws, const double *H, int p,
                                   double *theta) {
-  k_jacobi_cluster<<<JC, JNT, kJacobiBytes, s>>>(H, p, ws.Yeig, theta, ws.prm);
+  if (p <= 32) k_jacobi_block<<<1, JNT, jacobi_bytes(1), s>>>(H, p, ws.Yeig, theta, ws.prm);
+  else k_jacobi_cluster<<<JC, JNT, jacobi_bytes(JC), s>>>(H, p, ws.Yeig, theta, ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
 }

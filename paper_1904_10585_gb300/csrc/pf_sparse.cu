@@ -745,6 +745,23 @@ __global__ void k_export_info(const Params *__restrict__ prm, pf_iter_info *__re
 }
 }  // namespace
 
+namespace {
+// End of a step: count consecutive steps whose positive Ritz count fills the
+// block (r_plus >= p - 2) and flag saturation after 20 (flags bit 4).
+__global__ void k_step_end(Params *prm, int p) {
+  if (threadIdx.x != 0) return;
+  const int run = prm->r_plus >= p - 2 ? prm->sat_run + 1 : 0;
+  prm->sat_run = run;
+  if (run >= 20) prm->flags |= 16;
+}
+}  // namespace
+
+cudaError_t launch_step_end(cudaStream_t s, const Workspace &ws) {
+  k_step_end<<<1, 32, 0, s>>>(ws.prm, ws.p);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_export_info(cudaStream_t s, const Workspace &ws, int degree, int precision) {
   k_export_info<<<1, 32, 0, s>>>(ws.prm, ws.info, degree, precision);
   PF_LAUNCHED();
