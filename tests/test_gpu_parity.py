@@ -190,6 +190,11 @@ def test_maxcut_pfam_parity(pf, n, prob, p, d, iters):
         assert abs(a.b - b.b) <= 1e-9 * max(1.0, abs(b.b))
         assert a.r_plus == b.r_plus
         assert abs(a.kkt - b.kkt) <= 1e-7 * max(1e-3, b.kkt), (k, a.kkt, b.kkt)
+    # saturation flag (bit 4): r_+ >= p - 2 on each of the last 20 steps
+    run = 0
+    for k, b in enumerate(h_o):
+        run = run + 1 if b.r_plus >= p - 2 else 0
+        assert bool(h_g[k].flags & 16) == (run >= 20), (k, run, h_g[k].flags)
     th = pr.theta.cpu().numpy()
     assert np.max(np.abs(th - h_o[-1].theta)) <= 1e-9 * np.max(np.abs(h_o[-1].theta))
     Zg = pr.Z.cpu().numpy()
