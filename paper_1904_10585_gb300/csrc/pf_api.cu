@@ -227,7 +227,7 @@ pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, doubl
   int nb = 0;
   PF_CUDA(launch_gram(s, ws, Q, ldq, ws.W, p, op.n, p, p, 0, &nb));
   // launch_gram leaves the reduced H = Q^T W in the first Gram slot
-  PF_CUDA(launch_eigensolve(s, ws, ws.gpart, p, theta));
+  PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, theta));
   if (resid != nullptr)
     PF_CUDA(launch_rotate_resid(s, ws, Q, ldq, ws.W, p, op.n, p, theta, V, ldv, resid));
   else  // Ritz vectors only (the solver steps do not use the residual norms)
@@ -367,7 +367,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
                                         MODE_PLAIN));
     int nb = 0;
     PF_CUDA(launch_gram(s, ws, ws.W, p, ws.W, p, n, p, p, 0, &nb));
-    PF_CUDA(launch_eigensolve(s, ws, ws.gpart, p, pr->theta));
+    PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, pr->theta));
     PF_CUDA(launch_apply_right(s, ws, pr->U, pr->ldu, pr->V, pr->ldv, n, p, ws.Yeig, 0, 0));
     PF_CUDA(launch_apply_right(s, ws, ws.W, p, Yb[0], p, n, p, ws.Yeig, 0, 0));
     const int cap = pr->rank_cap > 0 ? pr->rank_cap : (p > 8 ? p - 8 : 1);
@@ -407,7 +407,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
                                         MODE_PLAIN));
     int nb = 0;
     PF_CUDA(launch_gram(s, ws, ws.W, p, ws.W, p, n, p, p, 0, &nb));
-    PF_CUDA(launch_eigensolve(s, ws, ws.gpart, p, pr->theta));
+    PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, pr->theta));
     PF_CUDA(launch_apply_right(s, ws, pr->U, pr->ldu, pr->V, pr->ldv, n, p, ws.Yeig, 0, 0));
     PF_CUDA(launch_apply_right(s, ws, ws.W, p, Yb[0], p, n, p, ws.Yeig, 0, 0));
     // shrink, sampled residual, dual update and report
@@ -593,7 +593,6 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   if (e == cudaSuccess) e = configure_skinny();
   if (e == cudaSuccess) e = configure_sparse();
   if (e == cudaSuccess) e = configure_jacobi();
-  if (e == cudaSuccess) e = configure_eig();
   if (e == cudaSuccess && lp) e = configure_tc();
   if (e != cudaSuccess) {
     delete ctx;

@@ -130,10 +130,6 @@ cudaError_t launch_chol_inv(cudaStream_t s, const Workspace &ws, int nparts, int
 cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double *Y, int64_t ldy,
                                double *Q, int64_t ldq, int n, int p, const double *R, int upper,
                                int cond_flag);
-cudaError_t configure_eig();
-// p x p eigensolve: FP32 Jacobi + FP64 refinement (pf_eig.cu)
-cudaError_t launch_eigensolve(cudaStream_t s, const Workspace &ws, const double *H, int p,
-                              double *theta);
 cudaError_t launch_jacobi_cluster(cudaStream_t s, const Workspace &ws, const double *H, int p,
                                   double *theta);
 cudaError_t launch_rotate_resid(cudaStream_t s, const Workspace &ws, const double *Q, int64_t ldq,
