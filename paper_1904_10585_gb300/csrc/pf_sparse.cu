@@ -17,18 +17,21 @@ constexpr int WPB = NT / 32;  // warps per block
 // Low-rank + sparse operator with the Chebyshev epilogue:
 //   op(X)_i = sum_l Uf_il T_l. + sscale * sum_e S_e X_{col_e} + shift X_i
 //   Ynext   = alpha (op(X) - c X) - beta Yprev   (mode as in the dense path)
-// One warp per row.  The two half-warps take alternate entries of the row
-// (and alternate terms of the low-rank sum); lane h of a half covers columns
-// h, h + 16, ... (JG groups of 16), so every lane does useful FP64 work for
-// any p.  The halves are combined by one shuffle in a fixed order.
+// One warp per row.  The warp splits into NQ = 32 / LW lane groups that take
+// every NQ-th entry of the row (and every NQ-th term of the low-rank sum);
+// lane h of a group covers columns h, h + LW, ... (JG groups of LW).  LW = 16
+// or 8 is chosen so that LW * JG is p or just above it (p = 40: 8 lanes x 5),
+// which keeps the FP64 lanes busy.  The groups are combined by shuffles in a
+// fixed order.
 // ---------------------------------------------------------------------------
-template <int JG>
+template <int LW, int JG>
 __global__ void __launch_bounds__(NT) k_lrsp_apply(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const double *__restrict__ svals, int n, int p, const double *__restrict__ Uf, int64_t lduf,
     int r, const double *__restrict__ T, double sscale, double shift, const double *X, int64_t ldx,
     const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn, const Params *__restrict__ prm,
     int mode, const int32_t *__restrict__ perm, const double *Xr, int64_t ldr) {
+  constexpr int NQ = 32 / LW;
   __shared__ double Ts[kMaxP * kMaxP];
   for (int idx = threadIdx.x; idx < r * p; idx += NT) Ts[idx] = T[idx];
   __syncthreads();
@@ -37,7 +40,7 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
     c = prm->c;
     alpha = (mode == MODE_FIRST ? 1.0 : 2.0) / prm->e;
   }
-  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const int lane = threadIdx.x & 31, gq = lane / LW, gl = lane % LW;
   const int warps = gridDim.x * WPB;
   for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
     double acc[JG], lr[JG];
@@ -50,14 +53,16 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
         const int mcol = my < e1 ? colind[my] : 0;
         const double mv = my < e1 ? svals[perm != nullptr ? perm[my] : my] : 0.0;
         const int cnt = min(32, e1 - base);
-        for (int k = 0; k < cnt; k += 2) {
-          const int kk = k + half;  // half 0: even entries, half 1: odd entries
+        for (int k = 0; k < cnt; k += NQ) {
+          // group q takes entries q, q + NQ, ...; past the chunk's end
+          // (kk >= cnt, always < 32 here) the source lane holds col 0, value 0
+          const int kk = k + gq;
           const int col = __shfl_sync(0xffffffffu, mcol, kk);
           const double v = __shfl_sync(0xffffffffu, mv, kk);
           const double *xr = X + (int64_t)col * ldx;
 #pragma unroll
           for (int g = 0; g < JG; ++g) {
-            const int j = hl + 16 * g;
+            const int j = gl + LW * g;
             if (j < p) acc[g] = fma(v, xr[j], acc[g]);
           }
         }
@@ -66,25 +71,28 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
     // the block of the shift and recurrence terms (the input unless given)
     const double *Xb = Xr != nullptr ? Xr : X;
     const int64_t ldb = Xr != nullptr ? ldr : ldx;
-    // low-rank part, terms l = half, half + 2, ...
+    // low-rank part, terms l = gq, gq + NQ, ...
     const double *ur = Uf + (int64_t)row * lduf;
-    for (int l = half; l < r; l += 2) {
+    for (int l = gq; l < r; l += NQ) {
       const double u = ur[l];
 #pragma unroll
       for (int g = 0; g < JG; ++g) {
-        const int j = hl + 16 * g;
+        const int j = gl + LW * g;
         if (j < p) lr[g] = fma(u, Ts[l * p + j], lr[g]);
       }
     }
 #pragma unroll
     for (int g = 0; g < JG; ++g) {
-      acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], 16);
-      lr[g] += __shfl_xor_sync(0xffffffffu, lr[g], 16);
+#pragma unroll
+      for (int off = LW; off < 32; off <<= 1) {
+        acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], off);
+        lr[g] += __shfl_xor_sync(0xffffffffu, lr[g], off);
+      }
     }
-    if (half == 0) {
+    if (gq == 0) {
 #pragma unroll
       for (int g = 0; g < JG; ++g) {
-        const int j = hl + 16 * g;
+        const int j = gl + LW * g;
         if (j >= p) continue;
         const double xij = Xb[(int64_t)row * ldb + j];
         const double o = lr[g] + sscale * acc[g] + shift * xij;
@@ -552,14 +560,19 @@ cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, con
   }
   int blocks = (n + WPB - 1) / WPB;
   if (blocks > 8 * ws.num_sms) blocks = 8 * ws.num_sms;
-#define PF_LRSP(JGV)                                                                            \
-  k_lrsp_apply<JGV><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf, op.lduf, r, \
-                                          ws.T, op.sscale, op.shift, X, ldx, Yprev, ldp, Ynext,   \
-                                          ldn, ws.prm, mode, op.perm, Xr, ldr)
-  if (p <= 16) { PF_LRSP(1); }
-  else if (p <= 32) { PF_LRSP(2); }
-  else if (p <= 48) { PF_LRSP(3); }
-  else { PF_LRSP(4); }
+#define PF_LRSP(LWV, JGV)                                                                     \
+  k_lrsp_apply<LWV, JGV><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf,      \
+                                               op.lduf, r, ws.T, op.sscale, op.shift, X, ldx,  \
+                                               Yprev, ldp, Ynext, ldn, ws.prm, mode, op.perm,  \
+                                               Xr, ldr)
+  // 8-lane groups where 8 x ceil(p/8) < 16 x ceil(p/16) (p = 24, 40: no idle lanes)
+  if (p <= 8) { PF_LRSP(8, 1); }
+  else if (p <= 16) { PF_LRSP(16, 1); }
+  else if (p <= 24) { PF_LRSP(8, 3); }
+  else if (p <= 32) { PF_LRSP(16, 2); }
+  else if (p <= 40) { PF_LRSP(8, 5); }
+  else if (p <= 48) { PF_LRSP(16, 3); }
+  else { PF_LRSP(16, 4); }
 #undef PF_LRSP
   PF_LAUNCHED();
   return cudaGetLastError();

@@ -121,7 +121,7 @@ def test_dense_rr_recovers_known_spectrum(pf):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("n,p,r,d", [(400, 16, 5, 3), (333, 40, 12, 4), (100, 64, 64, 2),
-                                     (70, 8, 0, 3)])
+                                     (70, 8, 0, 3), (211, 44, 9, 3), (97, 20, 3, 2), (45, 5, 2, 2)])
 def test_lowrank_sparse_filter_and_rr_parity(pf, n, p, r, d):
     pkg, S = pf
     inst = syn.completion_instance(n, 4, 0.2, p, seed=n + r)
