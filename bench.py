@@ -45,10 +45,9 @@ FP64_CUBLAS_MEASURED = 1.09    # torch float64 matmul 16384x16384x64 on this poo
 HBM_PEAK_GBS = 6773.2          # measured STREAM-style copy on the GB300s
 # dram bytes per launch of the dominant kernel from the committed ncu captures
 # (None until a capture of the current kernel exists)
-NCU_TRAFFIC_BYTES = {
-    # profiles/k_gemm_f64_splitk_maxcut_n4096.md: 135.29 MB read + 7.19 MB written per launch
-    "maxcut_n4096": 142.48e6,
-}
+NCU_TRAFFIC_BYTES = {}
+SLICED_NOTE = ("bf16 digit planes x7 of Z and X on tcgen05 (TMA, TMEM), level sums exact in fp32, "
+               "int64 fold, FP64 recurrence epilogue: an FP64-accurate product")
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -145,6 +144,12 @@ class WorkloadSpec:
         self.kind = c["kind"]
         self.lowprec = "bf16" if name.endswith("lowprec") else None
         self.structured = name.endswith("structured")
+        self.sliced = True   # dense FP64 products as bf16 digit planes on the tensor cores
+
+    def dense_f64(self):
+        """The step applies a dense FP64 iteration matrix."""
+        return self.kind == "nce" or (self.kind == "maxcut" and not self.lowprec
+                                      and not self.structured)
 
     def nnz(self):
         if self.kind == "nce":
@@ -224,6 +229,7 @@ class WorkloadSpec:
                 d["extrapolation"] = (f"Sec. 4.3 over windows of {c['accel_l'] + 2} iterates, "
                                       "lambda 1e-10 tr(D^T D)")
             bytes_z = self.n * self.n * 8
+            d["dense_product"] = SLICED_NOTE if self.sliced else "FP64 FMAs on the CUDA cores"
         elif self.kind == "maxcut":
             if self.structured:
                 d["problem"] = ("max-cut SDP (PFAM, structured FP64 iteration matrix "
@@ -233,6 +239,7 @@ class WorkloadSpec:
                                 "structured FP64 Rayleigh-Ritz)")
             else:
                 d["problem"] = "max-cut SDP (PFAM, dense FP64 iteration matrix)"
+                d["dense_product"] = SLICED_NOTE if self.sliced else "FP64 FMAs on the CUDA cores"
             d["graph"] = f"Erdos-Renyi p={c['prob']}, weights +-1"
             bytes_z = (self.nnz() * 16 if self.structured
                        else self.n * self.n * (2 if self.lowprec else 8))
@@ -359,6 +366,13 @@ class Workload(WorkloadSpec):
             op = S.lowrank_sparse_operator(n, None, None, self.rp, self.ci, pr.S, 1.0, 0.0)
             nnz = self.ci.numel()
             return (op, "k_lrsp_apply (Y X, CSR SpMM, FP64)", "alu", 2.0 * nnz * p, "TFLOP/s")
+        if self.dense_f64() and self.sliced:
+            # digit planes of Z read once, the block's planes read and the next
+            # block's written, X / Yprev read and Ynext written in FP64
+            return (S.dense_operator(pr.Z),
+                    "k_oz_product (Y = Z X from bf16 digit planes x7 on tcgen05, recurrence "
+                    "epilogue)", "hbm",
+                    14.0 * n * n + 28.0 * n * p + 24.0 * n * p, "GB/s")
         if self.kind == "nce":
             return (S.dense_operator(pr.Z),
                     "k_gemm_f64_splitk + k_combine (Y = (G + Diag x) X, dense FP64 filter product)",
@@ -408,7 +422,9 @@ def run_ours(args):
     W = Workload(args.workload, dev, S, pkg)
     n, p, d, iters = W.n, W.p, W.d, W.iters
     stream = torch.cuda.Stream(device=dev)
-    ctx = S.Context(p=p, n_max=n, degree=d, stream=stream, precision=W.precision())
+    W.sliced = args.dense_product == "sliced"
+    ctx = S.Context(p=p, n_max=n, degree=d, stream=stream, precision=W.precision(),
+                    dense_product=pkg.PF_DENSE_SLICED if W.sliced else pkg.PF_DENSE_FP64)
     pr = W.problem()
 
     def solve_once(problem):
@@ -487,7 +503,7 @@ def run_ours(args):
         stream.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    if W.lowprec:
+    if W.lowprec or (W.sliced and W.dense_f64()):
         # the tensor-core product alone: a degree-5 filter minus a degree-1
         # filter on the same block is exactly four product launches (the
         # operand preparation and CholQR2 cancel)
@@ -565,7 +581,9 @@ def run_ours(args):
         "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16+f64" if W.lowprec else "f64", "data": "synthetic",
+        "dtype": ("bf16+f64" if W.lowprec else
+                  "bf16x7->f64" if (W.sliced and W.dense_f64()) else "f64"),
+        "data": "synthetic",
         "config": W.config(),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
@@ -705,6 +723,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(syn.WORKLOADS) + ["serving_mix"])
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dense-product", default="sliced", choices=["sliced", "fp64"],
+                    help="dense FP64 products: bf16 digit planes on the tensor cores (FP64-"
+                         "accurate) or FP64 FMAs on the CUDA cores")
     ap.add_argument("--profile", action="store_true",
                     help="short run for profiler captures (init + 1 + --profile-iters "
                          "iterations, no timing)")

@@ -66,6 +66,15 @@ typedef enum {
 
 typedef enum { PF_PREC_FP64 = 0, PF_PREC_TF32 = 1, PF_PREC_BF16 = 2 } pf_precision;
 
+/* Arithmetic of the FP64 dense product A X (PF_OP_DENSE on the FP64 path). */
+typedef enum {
+  PF_DENSE_SLICED = 0,  /* error-free bf16 digit planes of A and X on the tensor cores
+                         * (tcgen05), level sums exact in fp32, folded in int64: an
+                         * FP64-accurate product (per entry within a few units of
+                         * 2^-53 max|A_i.| max|X_.j| per term of the sum) -- default */
+  PF_DENSE_FP64 = 1     /* FP64 fused multiply-adds on the CUDA cores            */
+} pf_dense_product;
+
 typedef enum {
   PF_PROBLEM_MAXCUT = 0,       /* max-cut SDP by PFAM (Sec. 2.3)                          */
   PF_PROBLEM_COMPLETION = 1,   /* PSD matrix completion by PFPG (Sec. 2.2)                */
@@ -94,6 +103,11 @@ typedef struct {
   int32_t p_min;
   int32_t adapt_guard;
   int32_t adapt_every;
+  /* pf_dense_product of the FP64 dense products.  The sliced product keeps
+   * digit planes of A (7 bf16 copies, 14 bytes per entry of an
+   * n_max x n_max matrix) in device memory allocated by the context on the
+   * first dense call outside a stream capture, and freed by pf_destroy.  */
+  int32_t dense_product;
 } pf_options;
 
 /*

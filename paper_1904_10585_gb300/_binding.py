@@ -30,6 +30,10 @@ PF_OP_LOWRANK_SPARSE = 1
 PF_PREC_FP64 = 0
 PF_PREC_TF32 = 1
 PF_PREC_BF16 = 2
+
+PF_DENSE_SLICED = 0
+PF_DENSE_FP64 = 1
+
 PF_PROBLEM_MAXCUT = 0
 PF_PROBLEM_COMPLETION = 1
 PF_PROBLEM_NCE = 2
@@ -41,7 +45,7 @@ class pf_options(C.Structure):
     _fields_ = [("p", C.c_int32), ("degree", C.c_int32), ("degree_max", C.c_int32),
                 ("q", C.c_int32), ("eta", C.c_double), ("precision", C.c_int32),
                 ("adaptive", C.c_int32), ("p_min", C.c_int32), ("adapt_guard", C.c_int32),
-                ("adapt_every", C.c_int32)]
+                ("adapt_every", C.c_int32), ("dense_product", C.c_int32)]
 
 
 class pf_operator(C.Structure):

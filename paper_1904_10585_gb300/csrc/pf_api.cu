@@ -36,6 +36,8 @@ struct pf_ctx {
   // adaptive ladder state (degree and low-precision filter currently used)
   int cur_degree;
   bool cur_lp;
+  // digit planes of the sliced dense product (allocated on first use)
+  void *oz_base;
 };
 
 namespace {
@@ -45,6 +47,20 @@ bool width_rule_on(const pf_ctx *ctx) { return ctx->opt.adapt_guard > 0; }
 // Active block width of a problem (validated by check_problem).
 int active_width(const pf_ctx *ctx, const pf_problem *pr) {
   return pr->p_active > 0 ? pr->p_active : ctx->p;
+}
+
+// The FP64 dense product of this operator runs on the tensor cores as bf16
+// digit planes (pf_oz.cu).
+bool sliced(const pf_ctx *ctx, const Op &op) {
+  return op.kind == PF_OP_DENSE && op.A != nullptr &&
+         ctx->opt.dense_product == PF_DENSE_SLICED;
+}
+
+// Problems whose steps apply a dense FP64 iteration matrix.
+bool dense_f64_problem(const pf_ctx *ctx, const pf_problem *pr) {
+  return pr->kind == PF_PROBLEM_NCE ||
+         (pr->kind == PF_PROBLEM_MAXCUT && pr->Z != nullptr &&
+          ctx->opt.precision == PF_PREC_FP64);
 }
 
 pf_status set_err(pf_ctx *ctx, pf_status s, const char *fmt, ...) {
@@ -72,6 +88,59 @@ pf_status set_err(pf_ctx *ctx, pf_status s, const char *fmt, ...) {
   } while (0)
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Digit-plane buffers of the sliced dense product, sized for n_max and the
+// context's p; allocated once, outside any stream capture.
+pf_status ensure_oz(pf_ctx *ctx) {
+  if (ctx->oz_base != nullptr || ctx->opt.dense_product != PF_DENSE_SLICED) return PF_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  PF_CUDA(cudaStreamIsCapturing(ctx->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return set_err(ctx, PF_ERR_UNSUPPORTED,
+                   "the sliced dense product allocates its digit planes on the first dense call, "
+                   "which must not be inside a stream capture");
+  const int64_t nz = ((ctx->n_max + 127) / 128) * 128;
+  const int64_t chunks = nz / 128;
+  int smax = kOzMaxSplits;
+  const int need = (int)((chunks + kOzMaxChunks - 1) / kOzMaxChunks);
+  if (need > smax) smax = need;
+  const size_t sizes[] = {(size_t)kOzSlices * nz * nz * 2,                 // zs
+                          (size_t)nz * sizeof(int),                        // ez
+                          (size_t)kOzSlices * kMaxP * nz * 2,              // xs[0]
+                          (size_t)kOzSlices * kMaxP * nz * 2,              // xs[1]
+                          (size_t)chunks * kMaxP * sizeof(int),            // ex[0]
+                          (size_t)chunks * kMaxP * sizeof(int),            // ex[1]
+                          (size_t)smax * ctx->n_max * ctx->p * sizeof(double),  // part
+                          (size_t)chunks * sizeof(int)};                   // cnt
+  size_t off[8], tot = 0;
+  for (int i = 0; i < 8; ++i) {
+    off[i] = tot;
+    tot += align_up(sizes[i]);
+  }
+  void *base = nullptr;
+  if (cudaMalloc(&base, tot) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, PF_ERR_OOM, "digit planes of the sliced dense product (%zu bytes)", tot);
+  }
+  if (cudaMemsetAsync(base, 0, tot, ctx->stream) != cudaSuccess) {
+    cudaFree(base);
+    return set_err(ctx, PF_ERR_CUDA, "clearing the digit planes failed");
+  }
+  char *b = (char *)base;
+  OzBuffers &oz = ctx->ws.oz;
+  oz.zs = b + off[0];
+  oz.ez = (int *)(b + off[1]);
+  oz.xs[0] = b + off[2];
+  oz.xs[1] = b + off[3];
+  oz.ex[0] = (int *)(b + off[4]);
+  oz.ex[1] = (int *)(b + off[5]);
+  oz.part = (double *)(b + off[6]);
+  oz.cnt = (int *)(b + off[7]);
+  oz.ldk = nz;
+  oz.slice_rows = nz;
+  ctx->oz_base = base;
+  return PF_OK;
+}
 
 pf_status make_op(pf_ctx *ctx, const pf_operator *op, Op *out) {
   if (!op) return set_err(ctx, PF_ERR_INVALID_ARG, "operator is NULL");
@@ -208,6 +277,24 @@ pf_status filter_core(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int deg
   if (op.kind == PF_OP_DENSE && op.A_lp != nullptr && ctx->opt.precision != PF_PREC_FP64)
     return filter_core_lp(ctx, op, U, ldu, degree);
   double *const *Y = ctx->ws.Y;
+  if (sliced(ctx, op)) {
+    // digit planes of A (unless current), of U, then one tensor-core product
+    // per degree, each cutting its output into the planes of the next
+    cudaStream_t s = ctx->stream;
+    const Workspace &ws = ctx->ws;
+    if (!op.zs_ready) PF_CUDA(launch_oz_zslice(s, ws, op.A, op.lda, op.n));
+    PF_CUDA(launch_oz_xslice(s, ws, U, ldu, op.n, 0));
+    for (int j = 0; j < degree; ++j) {
+      const double *cur = j == 0 ? U : Y[(j - 1) & 1];
+      const int64_t ldc = j == 0 ? ldu : p;
+      const double *prev = j == 0 ? nullptr : (j == 1 ? U : Y[j & 1]);
+      const int64_t ldprev = j == 1 ? ldu : p;
+      PF_CUDA(launch_oz_product(s, ws, op.n, j & 1, cur, ldc, prev, ldprev, Y[j & 1], p,
+                                j + 1 < degree ? ((j + 1) & 1) : -1,
+                                j == 0 ? MODE_FIRST : MODE_RECUR));
+    }
+    return cholqr2(ctx, Y[(degree - 1) & 1], p, U, ldu, op.n);
+  }
   PF_TRY(apply(ctx, op, U, ldu, nullptr, 0, Y[0], p, MODE_FIRST));
   for (int j = 1; j < degree; ++j) {
     const double *cur = Y[(j - 1) & 1];
@@ -223,7 +310,13 @@ pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, doubl
   const int p = ctx->ws.p;  // active width
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
-  PF_TRY(apply(ctx, op, Q, ldq, nullptr, 0, ws.W, p, MODE_PLAIN));
+  if (sliced(ctx, op)) {
+    if (!op.zs_ready) PF_CUDA(launch_oz_zslice(s, ws, op.A, op.lda, op.n));
+    PF_CUDA(launch_oz_xslice(s, ws, Q, ldq, op.n, 0));
+    PF_CUDA(launch_oz_product(s, ws, op.n, 0, Q, ldq, nullptr, 0, ws.W, p, -1, MODE_PLAIN));
+  } else {
+    PF_TRY(apply(ctx, op, Q, ldq, nullptr, 0, ws.W, p, MODE_PLAIN));
+  }
   int nb = 0;
   PF_CUDA(launch_gram(s, ws, Q, ldq, ws.W, p, op.n, p, p, 0, &nb));
   // launch_gram leaves the reduced H = Q^T W in the first Gram slot
@@ -423,6 +516,10 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     op.n = n;
     op.A = pr->Z;
     op.lda = pr->ldz;
+    if (sliced(ctx, op)) {  // one set of digit planes serves the filter and Rayleigh-Ritz
+      PF_CUDA(launch_oz_zslice(s, ws, pr->Z, pr->ldz, n));
+      op.zs_ready = 1;
+    }
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
@@ -481,6 +578,10 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     op.n = n;
     op.A = pr->Z;
     op.lda = pr->ldz;
+    if (sliced(ctx, op)) {  // one set of digit planes serves the filter and Rayleigh-Ritz
+      PF_CUDA(launch_oz_zslice(s, ws, pr->Z, pr->ldz, n));
+      op.zs_ready = 1;
+    }
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
@@ -577,6 +678,9 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   if (opt->precision != PF_PREC_FP64 && opt->precision != PF_PREC_BF16 &&
       opt->precision != PF_PREC_TF32)
     return PF_ERR_INVALID_ARG;
+  if (opt->dense_product != PF_DENSE_SLICED && opt->dense_product != PF_DENSE_FP64)
+    return PF_ERR_INVALID_ARG;
+  const bool oz = opt->dense_product == PF_DENSE_SLICED;
   const bool lp = opt->precision != PF_PREC_FP64;
   pf_ctx *ctx = new (std::nothrow) pf_ctx();
   if (!ctx) return PF_ERR_OOM;
@@ -593,7 +697,8 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   if (e == cudaSuccess) e = configure_skinny();
   if (e == cudaSuccess) e = configure_sparse();
   if (e == cudaSuccess) e = configure_jacobi();
-  if (e == cudaSuccess && lp) e = configure_tc();
+  if (e == cudaSuccess && (lp || oz)) e = configure_tc();
+  if (e == cudaSuccess && oz) e = configure_oz();
   if (e != cudaSuccess) {
     delete ctx;
     return PF_ERR_CUDA;
@@ -696,6 +801,7 @@ pf_status pf_destroy(pf_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->have_graph) cudaGraphExecDestroy(ctx->gexec);
   cudaFree(ctx->base);
+  if (ctx->oz_base) cudaFree(ctx->oz_base);
   delete ctx;
   return PF_OK;
 }
@@ -710,6 +816,7 @@ pf_status pf_filter(pf_ctx *ctx, const pf_operator *op, double a, double b, int3
     return set_err(ctx, PF_ERR_INVALID_ARG, "interval needs finite a < b");
   if (degree < 1 || degree > 64) return set_err(ctx, PF_ERR_INVALID_ARG, "degree must be 1..64");
   if (!U || ldu < ctx->p) return set_err(ctx, PF_ERR_INVALID_ARG, "U needs ldu >= p");
+  if (sliced(ctx, o)) PF_TRY(ensure_oz(ctx));
   PF_CUDA(launch_set_interval(ctx->stream, ctx->ws.prm, a, b));
   return filter_core(ctx, o, U, ldu, degree);
 }
@@ -722,6 +829,7 @@ pf_status pf_rayleigh_ritz(pf_ctx *ctx, const pf_operator *op, const double *Q, 
   PF_TRY(make_op(ctx, op, &o));
   if (!Q || ldq < ctx->p || !V || ldv < ctx->p || !theta)
     return set_err(ctx, PF_ERR_INVALID_ARG, "rayleigh_ritz needs Q, V (ld >= p) and theta");
+  if (sliced(ctx, o)) PF_TRY(ensure_oz(ctx));
   return rr_core(ctx, o, Q, ldq, V, ldv, theta, resid);
 }
 
@@ -746,6 +854,15 @@ pf_status pf_apply(pf_ctx *ctx, const pf_operator *op, const double *X, int64_t 
       return set_err(ctx, PF_ERR_INVALID_ARG, "low-precision apply needs ldy == p");
     return PF_OK;
   }
+  if (sliced(ctx, o)) {
+    PF_TRY(ensure_oz(ctx));
+    const Workspace &ws = ctx->ws;
+    PF_CUDA(launch_oz_zslice(ctx->stream, ws, o.A, o.lda, o.n));
+    PF_CUDA(launch_oz_xslice(ctx->stream, ws, X, ldx, o.n, 0));
+    PF_CUDA(launch_oz_product(ctx->stream, ws, o.n, 0, X, ldx, nullptr, 0, Y, ldy, -1,
+                              MODE_PLAIN));
+    return PF_OK;
+  }
   return apply(ctx, o, X, ldx, nullptr, 0, Y, ldy, MODE_PLAIN);
 }
 
@@ -754,6 +871,7 @@ int64_t pf_kernel_launch_count(void) { return g_launches.load(std::memory_order_
 pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
+  if (dense_f64_problem(ctx, pr)) PF_TRY(ensure_oz(ctx));
   if (pr->p_active == 0) pr->p_active = ctx->p;
   ctx->ws.p = ctx->p;  // the fills below cover every column
   const int n = (int)pr->n, p = ctx->p;
@@ -814,6 +932,7 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
 pf_status pf_prox_step(pf_ctx *ctx, pf_problem *pr, pf_iter_info *info) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
+  if (dense_f64_problem(ctx, pr)) PF_TRY(ensure_oz(ctx));
   ctx->ws.p = active_width(ctx, pr);
   PF_TRY(step_core(ctx, pr));
   pr->iter += 1;
@@ -857,6 +976,7 @@ pf_status pf_get_info(pf_ctx *ctx, pf_iter_info *info) {
 pf_status pf_enqueue_steps(pf_ctx *ctx, pf_problem *pr, int64_t n_steps) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
+  if (dense_f64_problem(ctx, pr)) PF_TRY(ensure_oz(ctx));
   if (n_steps < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "n_steps must be >= 0");
   if (width_rule_on(ctx))
     return set_err(ctx, PF_ERR_UNSUPPORTED, "the block width rule needs host decisions "
@@ -916,6 +1036,7 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
                    pf_result *out) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
+  if (dense_f64_problem(ctx, pr)) PF_TRY(ensure_oz(ctx));
   if (max_iter < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (check_every < 1) check_every = 1;
   const bool use_graph = ctx->stream != nullptr;

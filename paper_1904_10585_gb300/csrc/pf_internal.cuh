@@ -16,6 +16,11 @@ constexpr int kRedWidth = 4;        // doubles per block in a reduction slot
 constexpr int kMaxRedBlocks = 1024; // max blocks of a row reduction
 constexpr int kMaxGramBlocks = 256; // max blocks of a Gram (X^T Y) reduction
 constexpr int kMaxSplitK = 16;      // max K-splits of the dense FP64 product
+// sliced tensor-core product (pf_oz.cu)
+constexpr int kOzSlices = 7;        // bf16 digit planes per FP64 operand
+constexpr int kOzExpBad = 4096;     // exponent marking a row / chunk with Inf or NaN
+constexpr int kOzMaxChunks = 32;    // 128-wide K chunks per split (int64 headroom)
+constexpr int kOzMaxSplits = 8;     // K splits when the row blocks leave SMs idle
 
 enum RedSlot { SLOT_INTERVAL = 0, SLOT_LAMBDA = 1, SLOT_EXPAND = 2, SLOT_SDDMM = 3, SLOT_RESID = 4,
                SLOT_MISC = 5 };
@@ -70,10 +75,25 @@ struct Op {
   // transposed pattern of a non-symmetric matrix); both optional
   const double *Vf; int64_t ldvf;
   const int32_t *perm;
+  // dense, sliced product: the digit planes of A are already current
+  int zs_ready;
+};
+
+// Digit planes of the sliced dense product (allocated on first use).
+struct OzBuffers {
+  void *zs;               // bf16 planes of A: kOzSlices x slice_rows x ldk
+  int *ez;                // row exponents of A, slice_rows
+  void *xs[2];            // bf16 planes of the block: kOzSlices x kMaxP x ldk each
+  int *ex[2];             // chunk x column exponents, (slice_rows / 128) x kMaxP each
+  double *part;           // split partials, max splits x n_max x p
+  int *cnt;               // per row block arrival tickets (zero between launches)
+  int64_t ldk;            // row pitch of the planes (n_max rounded up to 128)
+  int64_t slice_rows;     // rows per A plane (n_max rounded up to 128)
 };
 
 struct Workspace {
   int n_max, p, num_sms;
+  OzBuffers oz;
   double *Y[2];           // filter recurrence buffers, n_max x p
   double *W;              // op(Q), n_max x p
   double *Vprev;          // previous Ritz vectors (completion), n_max x p
@@ -108,6 +128,9 @@ cudaError_t configure_skinny();
 cudaError_t configure_tc();
 cudaError_t configure_sparse();
 cudaError_t configure_jacobi();
+cudaError_t configure_oz();
+// K splits of the sliced product for size n
+int oz_splits(int n, int num_sms);
 // K splits of the dense FP64 product for size n (returns S, sets the chunk).
 int dense_splits(int n, int num_sms, int *kchunk);
 
@@ -137,6 +160,18 @@ cudaError_t launch_rotate_resid(cudaStream_t s, const Workspace &ws, const doubl
                                 double *V, int64_t ldv, double *resid_out);
 cudaError_t launch_lowrank_coef(cudaStream_t s, const Workspace &ws, int nparts, const double *lam,
                                 int r, int p, int clamp);
+
+// FP64-accurate sliced dense product on the tensor cores (pf_oz.cu): the
+// digit planes of A (once per A), of the block X into xs[which], and the
+// product Ynext = alpha (A X - c X) - beta Yprev reading xs[which], writing
+// the next block's planes into xs[next] unless next < 0
+cudaError_t launch_oz_zslice(cudaStream_t s, const Workspace &ws, const double *A, int64_t lda,
+                             int n);
+cudaError_t launch_oz_xslice(cudaStream_t s, const Workspace &ws, const double *X, int64_t ldx,
+                             int n, int which);
+cudaError_t launch_oz_product(cudaStream_t s, const Workspace &ws, int n, int which,
+                              const double *X, int64_t ldx, const double *Yprev, int64_t ldp,
+                              double *Ynext, int64_t ldn, int next, int mode);
 
 // tensor-core (tcgen05) low-precision filter product and its conversions
 cudaError_t launch_tc_product(cudaStream_t s, const Workspace &ws, bool tf32, const void *A_lp,

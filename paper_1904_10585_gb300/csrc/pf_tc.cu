@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include "pf_internal.cuh"
+#include "pf_sm100.cuh"
 
 namespace pf {
 
@@ -36,119 +37,6 @@ constexpr int TC_THREADS = 128;
 constexpr int TC_STAGES = 6;
 constexpr int TC_ROWB = 128;                       // bytes of K per tile row (one swizzle row)
 constexpr int TC_A_BYTES = TC_BM * TC_ROWB;        // 16 KB per stage
-constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;  // bounded waits
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on a barrier phase; false on timeout or when another thread
-// of the CTA has already given up.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > TC_TIMEOUT_NS) {
-      *abort_flag = 1;
-      return false;
-    }
-  }
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
-      : "memory");
-}
-// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row
-// groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
-  return d;
-}
-template <bool TF32>
-__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accum) {
-  if (TF32) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-  }
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Instruction descriptor: fp32 accumulator, A/B K-major, M = 128, N = NB.
 template <bool TF32, int NB>
@@ -662,17 +550,15 @@ cudaError_t configure_tc() {
   return cudaSuccess;
 }
 
-// 2-D row-major tensor map: rows x cols elements, leading dimension ld
-// elements, box = box_rows x (128 bytes of columns), 128-byte swizzle.
-static cudaError_t encode_map(CUtensorMap *m, const void *ptr, bool tf32, int64_t rows,
-                              int64_t cols, int64_t ld, int box_rows) {
+cudaError_t encode_tile_map(CUtensorMap *m, const void *ptr, bool f32, int64_t rows, int64_t cols,
+                            int64_t ld, int box_rows) {
   if (g_encode == nullptr) return cudaErrorNotSupported;
-  const int esz = tf32 ? 4 : 2;
+  const int esz = f32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
   cuuint32_t box[2] = {(cuuint32_t)(TC_ROWB / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+  CUresult r = g_encode(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                         2, const_cast<void *>(ptr), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -688,9 +574,9 @@ cudaError_t launch_tc_product(cudaStream_t s, const Workspace &ws, bool tf32, co
   const int p = ws.p;
   const int NB = tc_nb(p);
   CUtensorMap ma, mb;
-  cudaError_t e = encode_map(&ma, A_lp, tf32, n, n, lda_lp, TC_BM);
+  cudaError_t e = encode_tile_map(&ma, A_lp, tf32, n, n, lda_lp, TC_BM);
   if (e != cudaSuccess) return e;
-  e = encode_map(&mb, Xt, tf32, p, n, ws.ldxt, NB);
+  e = encode_tile_map(&mb, Xt, tf32, p, n, ws.ldxt, NB);
   if (e != cudaSuccess) return e;
   const int kel = TC_ROWB / (tf32 ? 4 : 2);
   const int num_kb = (n + kel - 1) / kel;
@@ -753,8 +639,8 @@ cudaError_t launch_tc_expand(cudaStream_t s, const Workspace &ws, bool f32out, c
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap mw, mv;
-  if ((e = encode_map(&mw, ws.Wf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
-  if ((e = encode_map(&mv, ws.Vf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
+  if ((e = encode_tile_map(&mw, ws.Wf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
+  if ((e = encode_tile_map(&mv, ws.Vf, true, n, KP, KP, EX_TILE)) != cudaSuccess) return e;
   // persistent: two CTAs per SM over equal contiguous ranges of the T x T tiles
   const int T = (n + EX_TILE - 1) / EX_TILE;
   const int64_t ntiles = (int64_t)T * T;

@@ -33,15 +33,18 @@ class Context:
     def __init__(self, p: int, n_max: int, degree: int, eta: float = 0.1,
                  precision: int = B.PF_PREC_FP64, stream: Optional[torch.cuda.Stream] = None,
                  degree_max: int = 0, adaptive: int = 0, p_min: int = 0, adapt_guard: int = 0,
-                 adapt_every: int = 10):
+                 adapt_every: int = 10, dense_product: int = B.PF_DENSE_SLICED):
         """p is the (maximum) block width; adapt_guard > 0 turns on the block
         width rule of Sec. 4.2 (width r_+ + adapt_guard, rounded up to a
-        multiple of 8, in [p_min, p], after every adapt_every-th step)."""
+        multiple of 8, in [p_min, p], after every adapt_every-th step).
+        dense_product selects the arithmetic of FP64 dense products: bf16
+        digit planes on the tensor cores (PF_DENSE_SLICED, FP64-accurate) or
+        FP64 FMAs on the CUDA cores (PF_DENSE_FP64)."""
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.opt = B.pf_options(p=p, degree=degree, degree_max=degree_max or degree, q=1,
                                 eta=eta, precision=precision, adaptive=adaptive,
                                 p_min=p_min or min(8, p), adapt_guard=adapt_guard,
-                                adapt_every=adapt_every)
+                                adapt_every=adapt_every, dense_product=dense_product)
         self.p = p
         self.n_max = n_max
         self.handle = B.pf_create(self.opt, n_max, self.stream.cuda_stream)

@@ -70,15 +70,20 @@ def spectrum_matrix(n, p, seed, gap=1.0):
 # pf_filter / pf_rayleigh_ritz on a dense operator
 # ---------------------------------------------------------------------------
 
+# dense products: bf16 digit planes on the tensor cores (default) and FP64 FMAs
+DENSE = [0, 1]
+
+
+@pytest.mark.parametrize("dp", DENSE)
 @pytest.mark.parametrize("n,p,d", [(300, 16, 3), (300, 32, 4), (257, 40, 2), (200, 64, 5),
                                    (130, 5, 1), (33, 33, 3), (17, 16, 2), (2, 1, 4), (150, 31, 8)])
-def test_dense_filter_parity(pf, n, p, d):
+def test_dense_filter_parity(pf, n, p, d, dp):
     pkg, S = pf
     B, Q, lam = spectrum_matrix(n, min(p, n - 1) if n > p else p, seed=n + p)
     U0 = syn.gaussian_block(n, p, seed=7)
     a, b = -3.2, 1.3
     ref = o.orth(o.cheb_filter(lambda X: B @ X, U0, a, b, d))
-    with S.Context(p=p, n_max=n, degree=d) as ctx:
+    with S.Context(p=p, n_max=n, degree=d, dense_product=dp) as ctx:
         Bd = t64(B)
         U = t64(U0)
         S.filter_(ctx, S.dense_operator(Bd), a, b, d, U)
@@ -88,13 +93,14 @@ def test_dense_filter_parity(pf, n, p, d):
     assert np.abs(Ug.T @ Ug - np.eye(p)).max() < 1e-13
 
 
+@pytest.mark.parametrize("dp", DENSE)
 @pytest.mark.parametrize("n,p", [(300, 16), (300, 32), (257, 40), (200, 64), (65, 7), (17, 16)])
-def test_dense_rayleigh_ritz_parity(pf, n, p):
+def test_dense_rayleigh_ritz_parity(pf, n, p, dp):
     pkg, S = pf
     B, Q, lam = spectrum_matrix(n, p, seed=3 * n + p)
     U0 = o.orth(o.cheb_filter(lambda X: B @ X, syn.gaussian_block(n, p, seed=2), -3.1, 1.5, 3))
     rr = o.rayleigh_ritz(lambda X: B @ X, U0)
-    with S.Context(p=p, n_max=n, degree=3) as ctx:
+    with S.Context(p=p, n_max=n, degree=3, dense_product=dp) as ctx:
         V, th, res = S.rayleigh_ritz(ctx, S.dense_operator(t64(B)), t64(U0))
         torch.cuda.synchronize()
     assert_ritz_parity(th.cpu().numpy(), V.cpu().numpy(), rr.theta, rr.V)
@@ -158,9 +164,10 @@ def _csr(c):
     return sp.csr_matrix((c.vals.astype(np.float64), c.colind, c.rowptr), shape=(c.n, c.n))
 
 
-def run_maxcut_gpu(S, inst, p, d, iters, use_solve=False):
+def run_maxcut_gpu(S, inst, p, d, iters, use_solve=False, dp=0):
     rp, ci, vals = S.csr_to_device(inst.C, DEV, torch.float64)
-    with S.Context(p=p, n_max=inst.n, degree=d, stream=torch.cuda.Stream()) as ctx:
+    with S.Context(p=p, n_max=inst.n, degree=d, stream=torch.cuda.Stream(),
+                   dense_product=dp) as ctx:
         pr = S.maxcut_problem(rp, ci, vals, t64(inst.U0_raw[:, :p]))
         S.problem_init(ctx, pr)
         hist = []
@@ -174,14 +181,15 @@ def run_maxcut_gpu(S, inst, p, d, iters, use_solve=False):
         return pr, hist
 
 
+@pytest.mark.parametrize("dp", DENSE)
 @pytest.mark.parametrize("n,prob,p,d,iters", [(520, 0.04, 32, 4, 40), (300, 0.05, 16, 3, 30),
                                               (130, 0.1, 40, 4, 25)])
-def test_maxcut_pfam_parity(pf, n, prob, p, d, iters):
+def test_maxcut_pfam_parity(pf, n, prob, p, d, iters, dp):
     pkg, S = pf
     inst = syn.maxcut_instance(n, prob, p, seed=n)
     C = _csr(inst.C)
     st, h_o = o.maxcut_solve(C, inst.U0_raw[:, :p], d, iters)
-    pr, h_g = run_maxcut_gpu(S, inst, p, d, iters)
+    pr, h_g = run_maxcut_gpu(S, inst, p, d, iters, dp=dp)
     t = o.maxcut_step_size(C)
     assert abs(pr.t - t) <= 1e-14 * t
     for k, (a, b) in enumerate(zip(h_g, h_o)):

@@ -1,0 +1,128 @@
+"""The arithmetic of the sliced dense product, checked exactly on the CPU.
+
+The tensor-core product cuts FP64 entries into balanced base-256 digits: for
+a row (or 128-row chunk) with exponent e (every |x| < 2^e), round(x 2^(55-e))
+= sum_s d_s 2^(8(6-s)) with d_0 in [-128, 128] and d_1..d_6 in [-128, 127],
+so x ~ 2^(e-7) sum_s d_s 2^(-8s).  These tests restate that decomposition
+with Python integers and fractions (no floating point) and check the facts the
+kernel relies on: digit ranges (8 significant bits: exact in bf16), the
+rounding error 2^(e-56), the bound 7 * 128 * 2^14 < 2^24 on a chunk's level
+sums (exact fp32 accumulation), and the product error bound that the GPU test
+asserts, n 2^-50 max|A_i.| max|X_.j|.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+
+KS = 7
+FRAC = 8 * (KS - 1) + 7  # 55
+
+
+def exponent(values):
+    """e with |x| < 2^e for all x (from the largest exponent field)."""
+    m = max(abs(v) for v in values)
+    if m == 0.0:
+        return -1021
+    return math.frexp(m)[1]  # m = f 2^e, 0.5 <= f < 1
+
+
+def digits(x, e):
+    v = round(Fraction(x) * 2 ** (FRAC - e))
+    d = [0] * KS
+    for s in range(KS - 1, 0, -1):
+        lo = v & 0xFF
+        dd = (lo ^ 0x80) - 0x80
+        d[s] = dd
+        v = (v - dd) >> 8
+    d[0] = v
+    return d
+
+
+def value(d, e):
+    return sum(Fraction(d[s]) * Fraction(2) ** (e - 7 - 8 * s) for s in range(KS))
+
+
+def test_digit_ranges_and_rounding_error():
+    rng = np.random.default_rng(0)
+    for trial in range(200):
+        row = rng.standard_normal(16) * 2.0 ** rng.integers(-40, 40)
+        if trial % 7 == 0:
+            row[3] = -np.abs(row).max()  # extreme entry, negative
+        e = exponent(row)
+        for x in row:
+            d = digits(float(x), e)
+            assert -128 <= d[0] <= 128
+            assert all(-128 <= ds <= 127 for ds in d[1:])
+            # every digit has at most 8 significant bits (exact in bf16)
+            assert all(abs(ds) < 2 ** 8 + 1 for ds in d)
+            err = abs(value(d, e) - Fraction(float(x)))
+            assert err <= Fraction(2) ** (e - 56)
+
+
+def test_extreme_digit_plus_128():
+    """An entry just below 2^e rounds its first digit up to 128."""
+    e = 3
+    x = math.ldexp(1.0, e) * (1 - 2.0 ** -53)
+    d = digits(x, e)   # x 2^(55-e) = 2^55 - 4: digits 128, 0, ..., 0, -4
+    assert d[0] == 128 and d[1:] == [0] * (KS - 2) + [-4]
+    assert value(d, e) == Fraction(x)
+
+
+def test_level_sums_fit_fp32():
+    """Worst case of a level sum over one 128-wide chunk: 7 pairs of digits at
+    magnitude 128: every partial sum is an integer below 2^24."""
+    worst = 7 * 128 * 128 * 128
+    assert worst < 2 ** 24
+
+
+def sliced_product_exact(A, X):
+    """The kernel's arithmetic with exact integers: per-row exponents of A,
+    per-(chunk, column) exponents of X, level sums of pairs s + t <= 6 over
+    128-wide chunks, the int64 fold at resolution 2^-36 (levels 5, 6 rounded
+    half up), the shift to the column's largest exponent, the sum over chunks."""
+    n, p = X.shape
+    eA = [exponent(A[i]) for i in range(n)]
+    chunks = [(c0, min(n, c0 + 128)) for c0 in range(0, n, 128)]
+    eX = [[exponent(X[c0:c1, j]) for j in range(p)] for (c0, c1) in chunks]
+    dA = [[digits(float(A[i, k]), eA[i]) for k in range(n)] for i in range(n)]
+    dX = [[None] * p for _ in range(n)]
+    for ci, (c0, c1) in enumerate(chunks):
+        for k in range(c0, c1):
+            for j in range(p):
+                dX[k][j] = digits(float(X[k, j]), eX[ci][j])
+    Y = np.zeros((n, p), dtype=object)
+    for i in range(n):
+        for j in range(p):
+            emax = max(eX[ci][j] for ci in range(len(chunks)))
+            acc = 0
+            for ci, (c0, c1) in enumerate(chunks):
+                L = [0] * KS
+                for k in range(c0, c1):
+                    for s in range(KS):
+                        for t in range(KS - s):
+                            L[s + t] += dA[i][k][s] * dX[k][j][t]
+                assert all(abs(v) < 2 ** 24 for v in L)
+                v = 0
+                for lvl in range(KS):
+                    sh = 36 - 8 * lvl
+                    v += L[lvl] << sh if sh >= 0 else (L[lvl] + (1 << (-sh - 1))) >> (-sh)
+                d = emax - eX[ci][j]
+                acc += v if d == 0 else (v + (1 << (d - 1))) >> d
+            Y[i, j] = Fraction(acc) * Fraction(2) ** (eA[i] + emax - 14 - 36)
+    return Y
+
+
+def test_sliced_product_error_bound_exact_arithmetic():
+    rng = np.random.default_rng(1)
+    n, p = 140, 2   # two chunks (128 + 12)
+    A = rng.standard_normal((n, n)) * np.exp2(rng.uniform(-10, 10, n))[:, None]
+    X = rng.standard_normal((n, p)) * np.exp2(rng.uniform(-10, 10, p))[None, :]
+    X[:128, 1] *= 2.0 ** -20  # the two chunks of column 1 get different exponents
+    Y = sliced_product_exact(A, X)
+    for i in range(0, n, 7):
+        for j in range(p):
+            exact = sum(Fraction(float(A[i, k])) * Fraction(float(X[k, j])) for k in range(n))
+            bound = Fraction(n) * Fraction(2) ** -50 * Fraction(float(np.abs(A[i]).max())) * \
+                Fraction(float(np.abs(X[:, j]).max()))
+            assert abs(Y[i, j] - exact) <= bound
