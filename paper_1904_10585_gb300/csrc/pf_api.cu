@@ -36,8 +36,11 @@ struct pf_ctx {
   // adaptive ladder state (degree and low-precision filter currently used)
   int cur_degree;
   bool cur_lp;
-  // digit planes of the sliced dense product (allocated on first use)
+  // digit planes of the sliced dense product (allocated on first use) and
+  // the matrix (pointer, n) they currently hold, nullptr when unknown
   void *oz_base;
+  const void *oz_owner;
+  int64_t oz_owner_n;
 };
 
 namespace {
@@ -54,6 +57,13 @@ int active_width(const pf_ctx *ctx, const pf_problem *pr) {
 bool sliced(const pf_ctx *ctx, const Op &op) {
   return op.kind == PF_OP_DENSE && op.A != nullptr &&
          ctx->opt.dense_product == PF_DENSE_SLICED;
+}
+
+// Dense max-cut whose update runs on the tensor cores and leaves the digit
+// planes of the new Z for the next step.
+bool sliced_maxcut(const pf_ctx *ctx, const pf_problem *pr) {
+  return pr->kind == PF_PROBLEM_MAXCUT && pr->Z != nullptr &&
+         ctx->opt.precision == PF_PREC_FP64 && ctx->opt.dense_product == PF_DENSE_SLICED;
 }
 
 // Problems whose steps apply a dense FP64 iteration matrix.
@@ -105,15 +115,22 @@ pf_status ensure_oz(pf_ctx *ctx) {
   const int need = (int)((chunks + kOzMaxChunks - 1) / kOzMaxChunks);
   if (need > smax) smax = need;
   const size_t sizes[] = {(size_t)kOzSlices * nz * nz * 2,                 // zs
-                          (size_t)nz * sizeof(int),                        // ez
+                          (size_t)nz * chunks * sizeof(int),               // ez
                           (size_t)kOzSlices * kMaxP * nz * 2,              // xs[0]
                           (size_t)kOzSlices * kMaxP * nz * 2,              // xs[1]
                           (size_t)chunks * kMaxP * sizeof(int),            // ex[0]
                           (size_t)chunks * kMaxP * sizeof(int),            // ex[1]
                           (size_t)smax * ctx->n_max * ctx->p * sizeof(double),  // part
-                          (size_t)chunks * sizeof(int)};                   // cnt
-  size_t off[8], tot = 0;
-  for (int i = 0; i < 8; ++i) {
+                          (size_t)chunks * 2 * sizeof(int),                // cnt
+                          (size_t)kOzSlices * nz * 64 * 2,                 // wp
+                          (size_t)kOzSlices * nz * 64 * 2,                 // vp
+                          (size_t)nz * sizeof(int),                        // ew
+                          (size_t)nz * sizeof(int),                        // ev
+                          (size_t)nz * sizeof(double),                     // xdiag
+                          (size_t)chunks * sizeof(double)};                // mchunk
+  constexpr int nbuf = 14;
+  size_t off[nbuf], tot = 0;
+  for (int i = 0; i < nbuf; ++i) {
     off[i] = tot;
     tot += align_up(sizes[i]);
   }
@@ -136,10 +153,41 @@ pf_status ensure_oz(pf_ctx *ctx) {
   oz.ex[1] = (int *)(b + off[5]);
   oz.part = (double *)(b + off[6]);
   oz.cnt = (int *)(b + off[7]);
+  oz.wp = b + off[8];
+  oz.vp = b + off[9];
+  oz.ew = (int *)(b + off[10]);
+  oz.ev = (int *)(b + off[11]);
+  oz.xdiag = (double *)(b + off[12]);
+  oz.mchunk = (double *)(b + off[13]);
   oz.ldk = nz;
   oz.slice_rows = nz;
   ctx->oz_base = base;
   return PF_OK;
+}
+
+// Before steps of a problem: the digit-plane buffers, and for a sliced dense
+// max-cut the planes of its current Z (sliced here, outside any capture,
+// unless they already hold it).
+pf_status oz_prepare_problem(pf_ctx *ctx, const pf_problem *pr) {
+  if (!dense_f64_problem(ctx, pr)) return PF_OK;
+  PF_TRY(ensure_oz(ctx));
+  if (sliced_maxcut(ctx, pr) && (ctx->oz_owner != pr->Z || ctx->oz_owner_n != pr->n)) {
+    PF_CUDA(launch_oz_zslice(ctx->stream, ctx->ws, pr->Z, pr->ldz, (int)pr->n));
+    ctx->oz_owner = pr->Z;
+    ctx->oz_owner_n = pr->n;
+  }
+  return PF_OK;
+}
+
+// After steps: the planes hold the problem's Z only for the sliced max-cut.
+void oz_after_steps(pf_ctx *ctx, const pf_problem *pr) {
+  if (!dense_f64_problem(ctx, pr)) return;
+  if (sliced_maxcut(ctx, pr)) {
+    ctx->oz_owner = pr->Z;
+    ctx->oz_owner_n = pr->n;
+  } else {
+    ctx->oz_owner = nullptr;
+  }
 }
 
 pf_status make_op(pf_ctx *ctx, const pf_operator *op, Op *out) {
@@ -578,15 +626,14 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     op.n = n;
     op.A = pr->Z;
     op.lda = pr->ldz;
-    if (sliced(ctx, op)) {  // one set of digit planes serves the filter and Rayleigh-Ritz
-      PF_CUDA(launch_oz_zslice(s, ws, pr->Z, pr->ldz, n));
-      op.zs_ready = 1;
-    }
+    // the digit planes of Z are current: written by the previous step's
+    // update, or by the host before the first step (pf_prox_step / pf_solve)
+    op.zs_ready = sliced(ctx, op) ? 1 : 0;
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_maxcut_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv,
-                                 pr->theta, pr->Z, pr->ldz, pr->lam));
+                                 pr->theta, pr->Z, pr->ldz, pr->lam, sliced(ctx, op)));
   } else {
     PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
     PF_CUDA(launch_completion_residual(s, ws, pr->rowptr, pr->colind, pr->vals_f32, n, p, ws.Vprev,
@@ -818,7 +865,13 @@ pf_status pf_filter(pf_ctx *ctx, const pf_operator *op, double a, double b, int3
   if (!U || ldu < ctx->p) return set_err(ctx, PF_ERR_INVALID_ARG, "U needs ldu >= p");
   if (sliced(ctx, o)) PF_TRY(ensure_oz(ctx));
   PF_CUDA(launch_set_interval(ctx->stream, ctx->ws.prm, a, b));
-  return filter_core(ctx, o, U, ldu, degree);
+  if (sliced(ctx, o)) ctx->oz_owner = nullptr;
+  PF_TRY(filter_core(ctx, o, U, ldu, degree));
+  if (sliced(ctx, o)) {
+    ctx->oz_owner = o.A;
+    ctx->oz_owner_n = o.n;
+  }
+  return PF_OK;
 }
 
 pf_status pf_rayleigh_ritz(pf_ctx *ctx, const pf_operator *op, const double *Q, int64_t ldq,
@@ -829,8 +882,16 @@ pf_status pf_rayleigh_ritz(pf_ctx *ctx, const pf_operator *op, const double *Q, 
   PF_TRY(make_op(ctx, op, &o));
   if (!Q || ldq < ctx->p || !V || ldv < ctx->p || !theta)
     return set_err(ctx, PF_ERR_INVALID_ARG, "rayleigh_ritz needs Q, V (ld >= p) and theta");
-  if (sliced(ctx, o)) PF_TRY(ensure_oz(ctx));
-  return rr_core(ctx, o, Q, ldq, V, ldv, theta, resid);
+  if (sliced(ctx, o)) {
+    PF_TRY(ensure_oz(ctx));
+    ctx->oz_owner = nullptr;
+  }
+  PF_TRY(rr_core(ctx, o, Q, ldq, V, ldv, theta, resid));
+  if (sliced(ctx, o)) {
+    ctx->oz_owner = o.A;
+    ctx->oz_owner_n = o.n;
+  }
+  return PF_OK;
 }
 
 pf_status pf_apply(pf_ctx *ctx, const pf_operator *op, const double *X, int64_t ldx, double *Y,
@@ -857,7 +918,10 @@ pf_status pf_apply(pf_ctx *ctx, const pf_operator *op, const double *X, int64_t 
   if (sliced(ctx, o)) {
     PF_TRY(ensure_oz(ctx));
     const Workspace &ws = ctx->ws;
+    ctx->oz_owner = nullptr;
     PF_CUDA(launch_oz_zslice(ctx->stream, ws, o.A, o.lda, o.n));
+    ctx->oz_owner = o.A;
+    ctx->oz_owner_n = o.n;
     PF_CUDA(launch_oz_xslice(ctx->stream, ws, X, ldx, o.n, 0));
     PF_CUDA(launch_oz_product(ctx->stream, ws, o.n, 0, X, ldx, nullptr, 0, Y, ldy, -1,
                               MODE_PLAIN));
@@ -871,7 +935,10 @@ int64_t pf_kernel_launch_count(void) { return g_launches.load(std::memory_order_
 pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
-  if (dense_f64_problem(ctx, pr)) PF_TRY(ensure_oz(ctx));
+  if (dense_f64_problem(ctx, pr)) {
+    PF_TRY(ensure_oz(ctx));
+    ctx->oz_owner = nullptr;  // Z is set anew below
+  }
   if (pr->p_active == 0) pr->p_active = ctx->p;
   ctx->ws.p = ctx->p;  // the fills below cover every column
   const int n = (int)pr->n, p = ctx->p;
@@ -932,9 +999,11 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
 pf_status pf_prox_step(pf_ctx *ctx, pf_problem *pr, pf_iter_info *info) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
-  if (dense_f64_problem(ctx, pr)) PF_TRY(ensure_oz(ctx));
+  PF_TRY(oz_prepare_problem(ctx, pr));
   ctx->ws.p = active_width(ctx, pr);
+  ctx->oz_owner = nullptr;
   PF_TRY(step_core(ctx, pr));
+  oz_after_steps(ctx, pr);
   pr->iter += 1;
   if (info) {
     Params h;
@@ -976,12 +1045,13 @@ pf_status pf_get_info(pf_ctx *ctx, pf_iter_info *info) {
 pf_status pf_enqueue_steps(pf_ctx *ctx, pf_problem *pr, int64_t n_steps) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
-  if (dense_f64_problem(ctx, pr)) PF_TRY(ensure_oz(ctx));
   if (n_steps < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "n_steps must be >= 0");
+  PF_TRY(oz_prepare_problem(ctx, pr));
   if (width_rule_on(ctx))
     return set_err(ctx, PF_ERR_UNSUPPORTED, "the block width rule needs host decisions "
                                             "(pf_prox_step / pf_solve)");
   ctx->ws.p = active_width(ctx, pr);
+  ctx->oz_owner = nullptr;
   const bool use_graph = ctx->stream != nullptr;
   for (int64_t k = 0; k < n_steps; ++k) {
     if (use_graph) {
@@ -993,6 +1063,7 @@ pf_status pf_enqueue_steps(pf_ctx *ctx, pf_problem *pr, int64_t n_steps) {
     }
     pr->iter += 1;
   }
+  oz_after_steps(ctx, pr);
   return PF_OK;
 }
 
@@ -1036,7 +1107,7 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
                    pf_result *out) {
   if (!ctx) return PF_ERR_INVALID_ARG;
   PF_TRY(check_problem(ctx, pr));
-  if (dense_f64_problem(ctx, pr)) PF_TRY(ensure_oz(ctx));
+  PF_TRY(oz_prepare_problem(ctx, pr));
   if (max_iter < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (check_every < 1) check_every = 1;
   const bool use_graph = ctx->stream != nullptr;
@@ -1051,6 +1122,7 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
   int64_t it = 0;
   bool converged = false;
   ctx->ws.p = active_width(ctx, pr);
+  ctx->oz_owner = nullptr;  // until the steps below have been enqueued without error
   for (; it < max_iter;) {
     if (use_graph) {
       if (!graph_matches(ctx, *pr))
@@ -1089,6 +1161,7 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
     }
     if (rule_now) PF_TRY(apply_width_rule(ctx, pr));
   }
+  oz_after_steps(ctx, pr);
   PF_TRY(read_params(ctx, &h));
   if (out) {
     out->iters = it;

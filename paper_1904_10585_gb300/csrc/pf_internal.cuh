@@ -82,13 +82,20 @@ struct Op {
 // Digit planes of the sliced dense product (allocated on first use).
 struct OzBuffers {
   void *zs;               // bf16 planes of A: kOzSlices x slice_rows x ldk
-  int *ez;                // row exponents of A, slice_rows
+  int *ez;                // exponents of A per row and 128-column chunk, slice_rows x (slice_rows / 128)
   void *xs[2];            // bf16 planes of the block: kOzSlices x kMaxP x ldk each
   int *ex[2];             // chunk x column exponents, (slice_rows / 128) x kMaxP each
   double *part;           // split partials, max splits x n_max x p
-  int *cnt;               // per row block arrival tickets (zero between launches)
+  int *cnt;               // arrival tickets per row block and column half (zero between launches)
   int64_t ldk;            // row pitch of the planes (n_max rounded up to 128)
   int64_t slice_rows;     // rows per A plane (n_max rounded up to 128)
+  // max-cut expansion on the tensor cores: digit planes of the rows of
+  // W = V diag(theta+) and V (kOzSlices x slice_rows x 64 bf16 each), their
+  // row exponents, diag(X~) and per 128-row chunk max sqrt(diag(X~))
+  void *wp, *vp;
+  int *ew, *ev;
+  double *xdiag;
+  double *mchunk;
 };
 
 struct Workspace {
@@ -129,8 +136,8 @@ cudaError_t configure_tc();
 cudaError_t configure_sparse();
 cudaError_t configure_jacobi();
 cudaError_t configure_oz();
-// K splits of the sliced product for size n
-int oz_splits(int n, int num_sms);
+// K splits of the sliced product for size n and block width p
+int oz_splits(int n, int p, int num_sms);
 // K splits of the dense FP64 product for size n (returns S, sets the chunk).
 int dense_splits(int n, int num_sms, int *kchunk);
 
@@ -200,10 +207,16 @@ cudaError_t launch_maxcut_init(cudaStream_t s, const Workspace &ws, const int32_
                                const int32_t *colind, const double *vals, int n, double t,
                                double *Z, int64_t ldz, double *lam);
 cudaError_t launch_cnorm(cudaStream_t s, const Workspace &ws, const double *vals, int64_t nnz);
+// sliced: the expansion runs on the tensor cores (pf_oz.cu) and also writes
+// the digit planes of the new Z for the next step's products
 cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
                                  const int32_t *colind, const double *vals, int n, int p,
                                  const double *V, int64_t ldv, const double *theta, double *Z,
-                                 int64_t ldz, double *lam);
+                                 int64_t ldz, double *lam, bool sliced = false);
+cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                             const int32_t *colind, const double *vals, int n, int p,
+                             const double *V, int64_t ldv, const double *theta, const double *lam,
+                             double *Z, int64_t ldz, double *red, int *nblocks);
 cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
                                        const int32_t *colind, const float *mvals, int n, int p,
                                        const double *V, int64_t ldv, const double *theta,

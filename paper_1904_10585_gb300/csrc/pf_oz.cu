@@ -7,35 +7,42 @@
 // FP64 iteration matrix A (n x n) and block X (n x p):
 //     Ynext = alpha (A X - c X) - beta Yprev.
 //
-// Slices.  Row i of A gets the exponent eA_i with |A_ij| < 2^eA_i; each entry
-// is rounded to the integer round(A_ij 2^(55 - eA_i)) (|.| <= 2^55), whose
-// balanced base-256 digits a_0..a_6 (a_0 in [-128, 128], the rest in
-// [-128, 127]) give A_ij ~ 2^(eA_i - 7) sum_s a_s 2^(-8s), error <= 2^(eA_i - 56).
-// X is cut the same way per (128-row chunk c, column j) with exponent eX_cj.
+// Slices.  Row i of A gets, per 128-column chunk c, the exponent eA_ic with
+// |A_ij| < 2^eA_ic on the chunk; each entry is rounded to the integer
+// round(A_ij 2^(55 - eA_ic)) (|.| <= 2^55), whose balanced base-256 digits
+// a_0..a_6 (a_0 in [-128, 128], the rest in [-128, 127]) give
+// A_ij ~ 2^(eA_ic - 7) sum_s a_s 2^(-8s), error <= 2^(eA_ic - 56).  X is cut
+// the same way per (128-row chunk c, column j) with exponent eX_cj.
 // Every digit is an integer of at most 8 significant bits, exact in bf16.
+// The planes of A are stored tile by tile (oz_zs_index), so that every TMA
+// box of the product is one contiguous 16 KB read.
 //
 // Products.  For a chunk c of 128 values of k, the level sums
 //     L_l = sum_{s + t = l} sum_{k in c} a_s(i,k) x_t(k,j),   l = 0..6,
 // are integers with |L_l| <= 7 * 128 * 2^14 < 2^24, so the tensor cores'
 // fp32 accumulation of the (exact) bf16 products is exact.  Pairs with
-// s + t >= 7 are dropped: each weighs <= 2^(eA_i + eX_cj - 56).  The chunk's
-// value 2^(eA_i + eX_cj - 14) sum_l L_l 2^(-8l) is folded into one int64 of
-// resolution 2^(eA_i + eX_cj - 50) (levels 5 and 6 rounded), shifted to the
-// largest exponent of column j in the split, and summed over the split's
-// chunks in int64 (exact).  Per output entry the error is a few units of
-// 2^(eA_i + max_c eX_cj - 53) per term of the sum, the order of an FP64 dot
-// product's rounding bound.
+// s + t >= 7 are dropped: each weighs <= 2^(eA_ic + eX_cj - 56).  The chunk's
+// value 2^(eA_ic + eX_cj - 14) sum_l L_l 2^(-8l) is folded into one int64 of
+// resolution 2^(eA_ic + eX_cj - 50) (levels 5 and 6 rounded), shifted to the
+// largest exponents of row i and column j over the split's chunks, and summed
+// over those chunks in int64 (exact).  Per output entry the error is a few
+// units of 2^(max_c eA_ic + max_c eX_cj - 53) per term of the sum, the order
+// of an FP64 dot product's rounding bound.
 //
 // Tensor-core mapping (per CTA: one 128-row block of A, one K split):
 //   warp 0, one lane : TMA producer.  Per 64-wide K tile: the 7 digit planes
 //                      of X (one stage, 7 x NB rows) and, one stage each,
 //                      the 7 digit planes of the A tile (128 x 64 bf16).
 //   warp 1, one lane : MMA issuer.  A-plane s times the stacked X planes
-//                      0..6-s in one tcgen05.mma of N = (7 - s) NB (split in
-//                      runs of N <= 256), accumulating into TMEM columns
-//                      [s NB, 7 NB): level l lives at columns l NB.  Two
-//                      accumulator sets (one for NB > 32) alternate per chunk.
-//   warps 2..        : epilogue.  Per chunk: tcgen05.ld of the 7 levels,
+//                      0..6-s in one tcgen05.mma of N = (7 - s) NB,
+//                      accumulating into TMEM columns [s NB, 7 NB): level l
+//                      lives at columns l NB.  Two accumulator sets alternate
+//                      per chunk.  NB is 16 or 32; a block wider than 32
+//                      columns is split over two CTAs per row block (grid z),
+//                      each reading the A planes, so that 2 x 7 x NB TMEM
+//                      columns always fit.
+//   warps 2..        : epilogue, NB / 2 warps, 8 columns per thread (several
+//                      warps per lane quarter).  Per chunk: tcgen05.ld of the 7 levels,
 //                      fold to int64, release the accumulator set.  At the
 //                      end: the split's FP64 partial; the last CTA of a row
 //                      block (atomic ticket, no waiting) sums the partials in
@@ -65,13 +72,17 @@ constexpr int OZ_FOLD = 36;              // binary point of the int64 fold (leve
 
 template <int NB>
 struct OzCfg {
-  static constexpr int EPI = NB <= 32 ? 4 : 8;   // epilogue warps (two per lane quarter above 32)
+  static_assert(NB == 16 || NB == 32, "columns per CTA");
+  // epilogue: 8 columns per thread, so that each TMEM lane quarter has NB / 8
+  // warps and every SM sub-partition several of them (the per-chunk fold is
+  // a latency-bound integer chain)
+  static constexpr int CW = 8;
+  static constexpr int EPI = 4 * (NB / CW);      // epilogue warps
   static constexpr int THREADS = 64 + 32 * EPI;
-  static constexpr int CW = NB / (EPI / 4);      // columns per epilogue thread
   static constexpr int LEVEL_COLS = kOzSlices * NB;
-  static constexpr int NBUF = 2 * LEVEL_COLS <= 512 ? 2 : 1;
+  static constexpr int NBUF = 2;
   static constexpr uint32_t TMEM_COLS = NBUF * LEVEL_COLS <= 256 ? 256u : 512u;
-  static constexpr int SA = NB <= 32 ? 8 : 6;    // A stages
+  static constexpr int SA = 8;                   // A stages
   static constexpr int B_BYTES = kOzSlices * NB * 128;
   static constexpr int MAXRUN = 256 / NB;        // X planes per MMA (N <= 256)
   static constexpr size_t SMEM = 1024 + (size_t)SA * OZ_A_BYTES + (size_t)OZ_SB * B_BYTES;
@@ -126,38 +137,59 @@ __device__ __forceinline__ uint32_t oz_idesc(int N) {
          ((uint32_t)(OZ_BM >> 4) << 24);
 }
 
+// Digit planes of A are stored tile by tile: plane s, 128-row block, 64-wide
+// K tile, then the 128 x 64 tile row-major (128 bytes per row), so that one
+// TMA box of the product is 16 KB of contiguous memory.  rb_n = row blocks
+// per plane, kt_n = K tiles per row (the buffer's capacity, not n).
+__host__ __device__ __forceinline__ int64_t oz_zs_index(int s, int row, int col, int rb_n,
+                                                         int kt_n) {
+  return ((((int64_t)s * rb_n + (row >> 7)) * kt_n + (col >> 6)) * OZ_BM + (row & 127)) * OZ_BK +
+         (col & 63);
+}
+
 __device__ __forceinline__ void epi_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
 // ---------------------------------------------------------------------------
-// A (n x n FP64) -> digit planes zs[s][i][k] (bf16, plane stride slice_rows
-// rows of ldk) and row exponents ez[i].  One warp per row.
+// A (n x n FP64) -> digit planes of A (bf16, tile-contiguous, oz_zs_index)
+// and exponents ez[i * nzc + c] of each row and 128-column chunk.  One warp
+// per row, four entries per lane and chunk.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_oz_zslice(const double *__restrict__ A, int64_t lda,
                                                    int n, __nv_bfloat16 *__restrict__ zs,
-                                                   int64_t ldk, int64_t slice_rows,
+                                                   int rb_n, int kt_n, int nzc,
                                                    int *__restrict__ ez) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= n) return;
   const double *ar = A + (int64_t)row * lda;
-  unsigned f = 0;
-  for (int k = lane; k < n; k += 32) f = max(f, oz_exfield(ar[k]));
-  f = __reduce_max_sync(0xffffffffu, f);
-  const int e = oz_exponent(f);
-  if (lane == 0) ez[row] = e;
-  __nv_bfloat16 *zr = zs + (int64_t)row * ldk;
-  for (int k = lane; k < n; k += 32) {
-    int d[kOzSlices];
-    if (e != kOzExpBad) {
-      oz_digits(ar[k], e, d);
-    } else {
+  for (int c0 = 0; c0 < n; c0 += OZ_BM) {
+    double v[4];
+    unsigned f = 0;
 #pragma unroll
-      for (int s = 0; s < kOzSlices; ++s) d[s] = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int k = c0 + 32 * q + lane;
+      v[q] = k < n ? ar[k] : 0.0;
+      f = max(f, oz_exfield(v[q]));
     }
+    f = __reduce_max_sync(0xffffffffu, f);
+    const int e = oz_exponent(f);
+    if (lane == 0) ez[(int64_t)row * nzc + c0 / OZ_BM] = e;
 #pragma unroll
-    for (int s = 0; s < kOzSlices; ++s) zr[s * slice_rows * ldk + k] = oz_bf16(d[s]);
+    for (int q = 0; q < 4; ++q) {
+      const int k = c0 + 32 * q + lane;
+      if (k >= n) continue;
+      int d[kOzSlices];
+      if (e != kOzExpBad) {
+        oz_digits(v[q], e, d);
+      } else {
+#pragma unroll
+        for (int s = 0; s < kOzSlices; ++s) d[s] = 0;
+      }
+#pragma unroll
+      for (int s = 0; s < kOzSlices; ++s) zs[oz_zs_index(s, row, k, rb_n, kt_n)] = oz_bf16(d[s]);
+    }
   }
 }
 
@@ -207,7 +239,8 @@ __global__ void __launch_bounds__(128) k_oz_xslice(const double *__restrict__ X,
 template <int NB>
 __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n,
-    int p, int slice_rows, int nsplit, const int *__restrict__ ez, const int *__restrict__ ex,
+    int p, int nbt, int rb_n, int kt_n, int nzc, int nsplit, const int *__restrict__ ez,
+    const int *__restrict__ ex,
     double *__restrict__ part, int *__restrict__ cnt, const double *X, int64_t ldx,
     const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn,
     __nv_bfloat16 *__restrict__ xs_next, int *__restrict__ ex_next, int64_t ldk, Params *prm,
@@ -227,6 +260,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb = blockIdx.x, split = blockIdx.y;
+  const int jh = blockIdx.z * NB;  // first column of this CTA (planes hold nbt rows each)
   const int nchunks = (n + OZ_BM - 1) / OZ_BM;
   const int c0 = (int)((int64_t)split * nchunks / nsplit);
   const int c1 = (int)((int64_t)(split + 1) * nchunks / nsplit);
@@ -236,7 +270,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
 
   for (int j = threadIdx.x; j < NB; j += blockDim.x) {
     int m = INT_MIN;
-    for (int c = c0; c < c1; ++c) m = max(m, ex[c * kMaxP + j]);
+    for (int c = c0; c < c1; ++c) m = max(m, ex[c * kMaxP + jh + j]);
     exmax[j] = m;
   }
   if (threadIdx.x == 0) {
@@ -268,7 +302,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
   __syncthreads();
   for (int idx = threadIdx.x; idx < (c1 - c0) * NB; idx += blockDim.x) {
     const int c = idx / NB, j = idx - c * NB;
-    dsh[c][j] = exmax[j] - ex[(c0 + c) * kMaxP + j];
+    dsh[c][j] = exmax[j] - ex[(c0 + c) * kMaxP + jh + j];
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -293,7 +327,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
           mbar_expect_tx(fb, C::B_BYTES);
 #pragma unroll
           for (int t = 0; t < KS; ++t)
-            tma_load_2d(sB + sb * C::B_BYTES + t * NB * 128, &tmB, fb, kx, t * NB);
+            tma_load_2d(sB + sb * C::B_BYTES + t * NB * 128, &tmB, fb, kx, t * nbt + jh);
           ++ib;
           for (int s = 0; s < KS; ++s) {
             const int sa = ia % C::SA;
@@ -304,7 +338,8 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
             }
             const uint32_t fa = smem_u32(&a_full[sa]);
             mbar_expect_tx(fa, OZ_A_BYTES);
-            tma_load_2d(sA + sa * OZ_A_BYTES, &tmA, fa, kx, s * slice_rows + rb * OZ_BM);
+            tma_load_2d(sA + sa * OZ_A_BYTES, &tmA, fa, 0,
+                        (int)((((int64_t)s * rb_n + rb) * kt_n + 2 * c + h) * OZ_BM));
             ++ia;
           }
         }
@@ -375,17 +410,32 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
     constexpr int CW = C::CW;
     const int ew = warp - 2;
     const int q = warp & 3;           // TMEM lane quarter this warp may read
-    const int col0 = (ew >> 2) * CW;  // its columns
+    const int col0 = (ew >> 2) * CW;  // its columns (of this CTA's NB)
+    const int gc0 = jh + col0;        // the same, in the block
     const int rl = q * 32 + lane;
     const int row = rb * OZ_BM + rl;
+    const bool in = row < n;
+    // the row's exponents over the split's chunks
+    const int *ezr = ez + (int64_t)(in ? row : 0) * nzc;
+    int ea = INT_MIN;
+#pragma unroll 4
+    for (int c = c0; c < c1; ++c) ea = max(ea, ezr[c]);
     long long acc[CW];
 #pragma unroll
     for (int j = 0; j < CW; ++j) acc[j] = 0;
     int cc = 0;
+    int ez_next = ezr[c0];
     for (int c = c0; c < c1; ++c, ++cc) {
       const int buf = cc % C::NBUF;
-      if (!mbar_wait(smem_u32(&acc_full[buf]), (cc / C::NBUF) & 1, &abort_flag)) break;
+      // the row's exponent of this chunk, and the next one's load in flight
+      const int da = ea - ez_next;
+      if (c + 1 < c1) ez_next = ezr[c + 1];
+      // one lane waits on the accumulator, the warp follows it
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(smem_u32(&acc_full[buf]), (cc / C::NBUF) & 1, &abort_flag);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
       __syncwarp();
+      if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t taddr =
           tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * C::LEVEL_COLS + col0);
@@ -405,7 +455,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
             if (s >= 0) v += (long long)li << s;
             else v += (long long)((li + (1 << (-s - 1))) >> (-s));
           }
-          acc[g + i] += oz_rshift(v, dsh[cc][col0 + g + i]);
+          acc[g + i] += oz_rshift(v, da + dsh[cc][col0 + g + i]);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -413,9 +463,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
     }
 
-    // this split's values: acc 2^(eA_i + exmax_j - 14 - OZ_FOLD)
-    const bool in = row < n;
-    const int ea = in ? ez[row] : 0;
+    // this split's values: acc 2^(max_c eA_ic + exmax_j - 14 - OZ_FOLD)
     double y[CW];
 #pragma unroll
     for (int j = 0; j < CW; ++j) {
@@ -430,11 +478,12 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
         double *pr = part + ((int64_t)split * n + row) * p;
 #pragma unroll
         for (int j = 0; j < CW; ++j)
-          if (col0 + j < p) pr[col0 + j] = y[j];
+          if (gc0 + j < p) pr[gc0 + j] = y[j];
       }
       __threadfence();
       epi_sync(32 * C::EPI);
-      if (ew == 0 && lane == 0) is_last = atomicAdd(&cnt[rb], 1) == nsplit - 1;
+      if (ew == 0 && lane == 0)
+        is_last = atomicAdd(&cnt[rb * gridDim.z + blockIdx.z], 1) == nsplit - 1;
       epi_sync(32 * C::EPI);
       last = is_last != 0;
       if (last) {
@@ -446,10 +495,10 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
             const double *pr = part + ((int64_t)sp * n + row) * p;
 #pragma unroll
             for (int j = 0; j < CW; ++j)
-              if (col0 + j < p) y[j] += __ldcg(pr + col0 + j);
+              if (gc0 + j < p) y[j] += __ldcg(pr + gc0 + j);
           }
         }
-        if (ew == 0 && lane == 0) cnt[rb] = 0;  // ready for the next launch
+        if (ew == 0 && lane == 0) cnt[rb * gridDim.z + blockIdx.z] = 0;  // for the next launch
       }
     }
     if (last) {
@@ -461,7 +510,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
       if (in) {
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
-          const int jj = col0 + j;
+          const int jj = gc0 + j;
           if (jj >= p) continue;
           double v = y[j];
           if (mode != MODE_PLAIN) {
@@ -476,16 +525,16 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
         // digit planes of the new block's rows for the next product
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
-          const unsigned f = (in && col0 + j < p) ? oz_exfield(y[j]) : 0u;
+          const unsigned f = (in && gc0 + j < p) ? oz_exfield(y[j]) : 0u;
           const unsigned m = __reduce_max_sync(0xffffffffu, f);
           if (lane == 0) qmax[q][col0 + j] = m;
         }
         epi_sync(32 * C::EPI);
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
-          const int jj = col0 + j;
+          const int lj = col0 + j, jj = gc0 + j;
           const int e =
-              oz_exponent(max(max(qmax[0][jj], qmax[1][jj]), max(qmax[2][jj], qmax[3][jj])));
+              oz_exponent(max(max(qmax[0][lj], qmax[1][lj]), max(qmax[2][lj], qmax[3][lj])));
           if (rl == 0) ex_next[rb * kMaxP + jj] = e;
           int d[KS];
           if (in && jj < p && e != kOzExpBad) {
@@ -496,7 +545,8 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
           }
           if (in) {
 #pragma unroll
-            for (int s = 0; s < KS; ++s) xs_next[(int64_t)(s * NB + jj) * ldk + row] = oz_bf16(d[s]);
+            for (int s = 0; s < KS; ++s)
+              xs_next[(int64_t)(s * nbt + jj) * ldk + row] = oz_bf16(d[s]);
           }
         }
       }
@@ -513,13 +563,393 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
   }
 }
 
+// ===========================================================================
+// Max-cut DRS update (Eq. (PFAM1), prox of G with the minus sign) with the
+// rank-r+ expansion X~ = W V^T, W = V diag(max(theta, 0)), on the tensor
+// cores, producing the new Z = X~ - tC - Diag(lam) in FP64 together with its
+// digit planes for the next step's products:
+//   k_oz_lr_prep : digit planes of the rows of W and V (K = 64, zero beyond
+//                  p and for theta_l <= 0), their row exponents, and per
+//                  128-row chunk the largest sqrt(X~_jj);
+//   k_oz_expand  : persistent over 128 x 64 output tiles (row block by row
+//                  block).  One MMA round per tile (K = 64, one exact chunk:
+//                  |level sums| <= 7 * 64 * 2^14), the 7 levels in 448 TMEM
+//                  columns; the epilogue folds them, scales to FP64, applies
+//                  -tC and -lam on the diagonal, accumulates
+//                  ||Z_old - Z||^2 and <C, X~>, stores Z and its digit planes.
+// The exponent of a (row i, 128-column chunk c) of the new Z comes from a
+// bound known before the product: X~ is PSD, so |X~_ij| <= sqrt(X~_ii X~_jj),
+// and |Z_ij| <= sqrt(X~_ii) max_{j in c} sqrt(X~_jj) + t max_{j in c} |C_ij|
+// + [i in c] |lam_i| (times 1 + 2^-20 for rounding).  A loose bound costs
+// accuracy bits of the planes, never correctness.
+// ===========================================================================
+// epilogue warps: 2 per TMEM lane quarter, 32 columns each (10 warps in all,
+// so that every SM sub-partition's 16K registers hold its warps at ~160
+// registers a thread)
+constexpr int XP_EPI = 8;
+constexpr int XP_THREADS = 64 + 32 * XP_EPI;
+constexpr int XP_CW = 32;                     // columns per epilogue thread
+constexpr int XP_TN = 64;                     // output columns per tile
+constexpr int XP_W_BYTES = kOzSlices * OZ_A_BYTES;         // 7 W planes of a row block
+constexpr int XP_V_BYTES = kOzSlices * XP_TN * 128;        // 7 V planes of a column tile
+constexpr size_t XP_SMEM = 1024 + (size_t)XP_W_BYTES + XP_V_BYTES;
+
+__global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
+    const double *__restrict__ V, int64_t ldv, const double *__restrict__ theta, int n, int p,
+    const double *__restrict__ xdiag, __nv_bfloat16 *__restrict__ wp,
+    __nv_bfloat16 *__restrict__ vp, int64_t plane_rows, int *__restrict__ ew,
+    int *__restrict__ ev, double *__restrict__ mchunk) {
+  __shared__ double th[kMaxP];
+  __shared__ double sq[4];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int row = blockIdx.x * OZ_BM + t;
+  const bool in = row < n;
+  if (t < kMaxP) th[t] = (t < p && theta[t] > 0.0) ? theta[t] : 0.0;
+  double r = in ? sqrt(fmax(xdiag[row], 0.0)) : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+  if (lane == 0) sq[w] = r;
+  __syncthreads();
+  if (t == 0) mchunk[blockIdx.x] = fmax(fmax(sq[0], sq[1]), fmax(sq[2], sq[3]));
+  if (!in) return;
+  const double *vr = V + (int64_t)row * ldv;
+  unsigned fw = 0, fv = 0;
+  for (int l = 0; l < p; ++l) {
+    if (th[l] > 0.0) {
+      fw = max(fw, oz_exfield(vr[l] * th[l]));
+      fv = max(fv, oz_exfield(vr[l]));
+    }
+  }
+  const int e_w = oz_exponent(fw), e_v = oz_exponent(fv);
+  ew[row] = e_w;
+  ev[row] = e_v;
+  for (int l0 = 0; l0 < 64; l0 += 8) {
+    uint32_t pw[kOzSlices][4], pv[kOzSlices][4];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int l = l0 + h;
+      int dw[kOzSlices], dv[kOzSlices];
+      const bool on = l < p && th[l] > 0.0;
+      if (on && e_w != kOzExpBad) oz_digits(vr[l] * th[l], e_w, dw);
+      else
+#pragma unroll
+        for (int s2 = 0; s2 < kOzSlices; ++s2) dw[s2] = 0;
+      if (on && e_v != kOzExpBad) oz_digits(vr[l], e_v, dv);
+      else
+#pragma unroll
+        for (int s2 = 0; s2 < kOzSlices; ++s2) dv[s2] = 0;
+#pragma unroll
+      for (int s2 = 0; s2 < kOzSlices; ++s2) {
+        const uint32_t bw = __bfloat16_as_ushort(oz_bf16(dw[s2]));
+        const uint32_t bv = __bfloat16_as_ushort(oz_bf16(dv[s2]));
+        if (h & 1) {
+          pw[s2][h >> 1] |= bw << 16;
+          pv[s2][h >> 1] |= bv << 16;
+        } else {
+          pw[s2][h >> 1] = bw;
+          pv[s2][h >> 1] = bv;
+        }
+      }
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < kOzSlices; ++s2) {
+      const int64_t off = ((int64_t)s2 * plane_rows + row) * 64 + l0;
+      *reinterpret_cast<uint4 *>(wp + off) = make_uint4(pw[s2][0], pw[s2][1], pw[s2][2], pw[s2][3]);
+      *reinterpret_cast<uint4 *>(vp + off) = make_uint4(pv[s2][0], pv[s2][1], pv[s2][2], pv[s2][3]);
+    }
+  }
+}
+
+// (double)v 2^k with the scaling done on the exponent field when it stays
+// normal (ldexp otherwise)
+__device__ __forceinline__ double oz_scale(long long v, int k) {
+  if (v == 0) return 0.0;
+  const double d = (double)v;
+  const long long bits = __double_as_longlong(d);
+  const int ex = (int)((bits >> 52) & 0x7FF) + k;
+  if (ex > 0 && ex < 0x7FF) return __longlong_as_double(bits + ((long long)k << 52));
+  return ldexp(d, k);
+}
+
+__global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
+    const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmV, int n,
+    int plane_rows, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
+    const double *__restrict__ cvals, const double *__restrict__ lam,
+    const double *__restrict__ xdiag, const double *__restrict__ mchunk,
+    const int *__restrict__ ew, const int *__restrict__ ev, double *__restrict__ Z, int64_t ldz,
+    __nv_bfloat16 *__restrict__ zs, int rb_n, int kt_n, int *__restrict__ ez,
+    int nzc, const Params *__restrict__ prm, Params *__restrict__ prm_flags,
+    double *__restrict__ red) {
+  constexpr int KS = kOzSlices;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t w_full, w_empty, v_full, v_empty, acc_full, acc_empty,
+      mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ double rsum[XP_EPI][2];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = (n + OZ_BM - 1) / OZ_BM, TCN = (n + XP_TN - 1) / XP_TN;
+  const int64_t T = (int64_t)R * TCN;
+  const int64_t t0 = T * blockIdx.x / gridDim.x, t1 = T * (blockIdx.x + 1) / gridDim.x;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t sW = base, sV = base + XP_W_BYTES;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(smem_u32(&w_full), 1);
+    mbar_init(smem_u32(&w_empty), 1);
+    mbar_init(smem_u32(&v_full), 1);
+    mbar_init(smem_u32(&v_empty), 1);
+    mbar_init(smem_u32(&acc_full), 1);
+    mbar_init(smem_u32(&acc_empty), XP_EPI);
+    mbar_init(smem_u32(&mma_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmW) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmV) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int cur = -1, nw = 0, nv = 0;
+      bool ok = true;
+      for (int64_t t = t0; t < t1 && ok; ++t) {
+        const int rb = (int)(t / TCN), ct = (int)(t - (int64_t)rb * TCN);
+        if (rb != cur) {
+          if (nw > 0 && !mbar_wait(smem_u32(&w_empty), (nw - 1) & 1, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(smem_u32(&w_full), XP_W_BYTES);
+#pragma unroll
+          for (int s2 = 0; s2 < KS; ++s2)
+            tma_load_2d(sW + s2 * OZ_A_BYTES, &tmW, smem_u32(&w_full), 0,
+                        s2 * plane_rows + rb * OZ_BM);
+          ++nw;
+          cur = rb;
+        }
+        if (nv > 0 && !mbar_wait(smem_u32(&v_empty), (nv - 1) & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(smem_u32(&v_full), XP_V_BYTES);
+#pragma unroll
+        for (int s2 = 0; s2 < KS; ++s2)
+          tma_load_2d(sV + s2 * XP_TN * 128, &tmV, smem_u32(&v_full), 0,
+                      s2 * plane_rows + ct * XP_TN);
+        ++nv;
+      }
+      if (nw > 0) mbar_drain(smem_u32(&w_full), (nw - 1) & 1);
+      if (nv > 0) mbar_drain(smem_u32(&v_full), (nv - 1) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      int cur = -1, nw = 0, nt = 0;
+      for (int64_t t = t0; t < t1; ++t, ++nt) {
+        const int rb = (int)(t / TCN);
+        if (rb != cur) {
+          if (!mbar_wait(smem_u32(&w_full), nw & 1, &abort_flag)) break;
+          ++nw;
+          cur = rb;
+        }
+        if (!mbar_wait(smem_u32(&v_full), nt & 1, &abort_flag)) break;
+        if (nt > 0 && !mbar_wait(smem_u32(&acc_empty), (nt - 1) & 1, &abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int s2 = 0; s2 < KS; ++s2) {
+          const uint64_t ad = sw128_desc(sW + s2 * OZ_A_BYTES);
+          for (int r0 = 0; r0 < KS - s2; r0 += 4) {  // N = 64 x planes <= 256
+            const int ns = min(4, KS - s2 - r0);
+            const uint32_t idesc = oz_idesc(ns * XP_TN);
+            const uint64_t bd = sw128_desc(sV + r0 * XP_TN * 128);
+            const uint32_t d = tmem + (uint32_t)((s2 + r0) * XP_TN);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              mma_issue<false>(d, ad + 2 * k, bd + 2 * k, idesc, (s2 | k) != 0 ? 1u : 0u);
+          }
+        }
+        mma_commit(smem_u32(&v_empty));
+        mma_commit(smem_u32(&acc_full));
+        const bool last_of_block = t + 1 >= t1 || (int)((t + 1) / TCN) != rb;
+        if (last_of_block) mma_commit(smem_u32(&w_empty));
+      }
+      mma_commit(smem_u32(&mma_done));
+      mbar_drain(smem_u32(&mma_done), 0);
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int ew_ = warp - 2;
+    const int q = warp & 3;
+    const int col0 = (ew_ >> 2) * XP_CW;  // columns of the 64-wide tile
+    const double tt = prm->t;
+    double dsum = 0.0, cx = 0.0;
+    int nt = 0;
+    for (int64_t t = t0; t < t1; ++t, ++nt) {
+      const int rb = (int)(t / TCN), ct = (int)(t - (int64_t)rb * TCN);
+      const int row = rb * OZ_BM + q * 32 + lane;
+      const bool in = row < n;
+      const int j0 = ct * XP_TN + col0;      // first column of this thread
+      const int c = (ct * XP_TN) / OZ_BM;    // 128-column chunk
+      // exponent of (row, chunk) from the bound; the CSR cursor at column j0
+      int ez_rc = 0, ewr = 0;
+      int e_lo = 0, e_hi = 0;
+      double lam_r = 0.0;
+      if (in) {
+        ewr = ew[row];
+        lam_r = lam[row];
+        const int cb = c * OZ_BM, ce = min(n, cb + OZ_BM);
+        int lo = rowptr[row], hi = rowptr[row + 1];
+        e_hi = hi;
+        while (lo < hi) {  // first entry with column >= cb
+          const int mid = (lo + hi) >> 1;
+          if (colind[mid] < cb) lo = mid + 1;
+          else hi = mid;
+        }
+        double cmax = 0.0;
+        e_lo = e_hi;
+        for (int e = lo; e < e_hi; ++e) {
+          const int col = colind[e];
+          if (col >= ce) break;
+          cmax = fmax(cmax, fabs(cvals[e]));
+          if (col >= j0 && e_lo == e_hi) e_lo = e;
+        }
+        const double bound =
+            (sqrt(fmax(xdiag[row], 0.0)) * mchunk[c] + tt * cmax +
+             ((row >= cb && row < ce) ? fabs(lam_r) : 0.0)) *
+            (1.0 + 0x1p-20);
+        ez_rc = oz_exponent(oz_exfield(bound));
+        if (col0 == 0 && (ct * XP_TN) % OZ_BM == 0) ez[(int64_t)row * nzc + c] = ez_rc;
+      }
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(smem_u32(&acc_full), nt & 1, &abort_flag);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
+      int e = e_lo;
+#pragma unroll
+      for (int g = 0; g < XP_CW; g += 8) {
+        // the group's old Z and V exponents: independent loads, in flight
+        // while TMEM is read and the levels are folded
+        double zo[8];
+        int evv[8];
+        const double *zrow = Z + (int64_t)(in ? row : 0) * ldz;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int col = j0 + g + i;
+          const bool ok2 = in && col < n;
+          zo[i] = ok2 ? zrow[col] : 0.0;
+          evv[i] = ok2 ? ev[col] : 0;
+        }
+        uint32_t L[KS][8];
+#pragma unroll
+        for (int l = 0; l < KS; ++l) tmem_ld8(taddr + l * XP_TN + g, L[l]);
+        tmem_wait_ld();
+        uint32_t pk[KS][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int col = j0 + g + i;
+          long long v = 0;
+#pragma unroll
+          for (int l = 0; l < KS; ++l) {
+            const int li = __float2int_rn(__uint_as_float(L[l][i]));
+            const int sh = OZ_FOLD - 8 * l;
+            if (sh >= 0) v += (long long)li << sh;
+            else v += (long long)((li + (1 << (-sh - 1))) >> (-sh));
+          }
+          int d[KS];
+#pragma unroll
+          for (int s2 = 0; s2 < KS; ++s2) d[s2] = 0;
+          if (in && col < n) {
+            const int evc = evv[i];
+            double xt = (ewr == kOzExpBad || evc == kOzExpBad)
+                            ? __longlong_as_double(0x7FF8000000000000ll)
+                            : oz_scale(v, ewr + evc - 14 - OZ_FOLD);
+            double z = xt;
+            if (e < e_hi && colind[e] == col) {
+              const double cij = cvals[e];
+              z = fma(-tt, cij, z);
+              cx = fma(cij, xt, cx);
+              ++e;
+            }
+            if (col == row) z -= lam_r;
+            const double dz = zo[i] - z;
+            dsum = fma(dz, dz, dsum);
+            Z[(int64_t)row * ldz + col] = z;
+            if (ez_rc != kOzExpBad) oz_digits(z, ez_rc, d);
+          }
+#pragma unroll
+          for (int s2 = 0; s2 < KS; ++s2) {
+            const uint32_t b = __bfloat16_as_ushort(oz_bf16(d[s2]));
+            if (i & 1) pk[s2][i >> 1] |= b << 16;
+            else pk[s2][i >> 1] = b;
+          }
+        }
+        if (in) {
+#pragma unroll
+          for (int s2 = 0; s2 < KS; ++s2)
+            *reinterpret_cast<uint4 *>(zs + oz_zs_index(s2, row, j0 + g, rb_n, kt_n)) =
+                make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty));
+    }
+    // per-CTA sums in a fixed order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+      cx += __shfl_xor_sync(0xffffffffu, cx, o);
+    }
+    if (lane == 0) {
+      rsum[ew_][0] = dsum;
+      rsum[ew_][1] = cx;
+    }
+    epi_sync(32 * XP_EPI);
+    if (ew_ == 0 && lane == 0) {
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < XP_EPI; ++k) {
+        a += rsum[k][0];
+        b += rsum[k][1];
+      }
+      red[blockIdx.x * kRedWidth + 0] = a;
+      red[blockIdx.x * kRedWidth + 1] = b;
+    }
+  }
+
+  if (threadIdx.x == 0 && abort_flag) atomicOr(&prm_flags->flags, 8);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
 template <int NB>
 cudaError_t oz_set_attr() {
   return cudaFuncSetAttribute(k_oz_product<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)OzCfg<NB>::SMEM);
 }
 
-int oz_nb(int p) { return p <= 16 ? 16 : p <= 32 ? 32 : p <= 48 ? 48 : 64; }
+// columns per CTA, column halves (grid z) and rows per digit plane of X
+int oz_nb(int p) { return p <= 16 ? 16 : 32; }
+int oz_halves(int p) { return p <= 32 ? 1 : 2; }
+int oz_nbt(int p) { return oz_halves(p) == 1 ? oz_nb(p) : 64; }
 
 }  // namespace
 
@@ -527,13 +957,13 @@ cudaError_t configure_oz() {
   cudaError_t e;
   if ((e = oz_set_attr<16>()) != cudaSuccess) return e;
   if ((e = oz_set_attr<32>()) != cudaSuccess) return e;
-  if ((e = oz_set_attr<48>()) != cudaSuccess) return e;
-  return oz_set_attr<64>();
+  return cudaFuncSetAttribute(k_oz_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)XP_SMEM);
 }
 
-int oz_splits(int n, int num_sms) {
+int oz_splits(int n, int p, int num_sms) {
   const int R = (n + OZ_BM - 1) / OZ_BM;
-  int S = num_sms / R;
+  int S = num_sms / (R * oz_halves(p));
   if (S > kOzMaxSplits) S = kOzMaxSplits;
   if (S > R) S = R;
   const int need = (R + kOzMaxChunks - 1) / kOzMaxChunks;  // int64 headroom of the fold
@@ -544,8 +974,10 @@ int oz_splits(int n, int num_sms) {
 cudaError_t launch_oz_zslice(cudaStream_t s, const Workspace &ws, const double *A, int64_t lda,
                              int n) {
   if (ws.oz.zs == nullptr || n > ws.oz.slice_rows) return cudaErrorInvalidValue;
-  k_oz_zslice<<<(n + 7) / 8, 256, 0, s>>>(A, lda, n, (__nv_bfloat16 *)ws.oz.zs, ws.oz.ldk,
-                                          ws.oz.slice_rows, ws.oz.ez);
+  k_oz_zslice<<<(n + 7) / 8, 256, 0, s>>>(A, lda, n, (__nv_bfloat16 *)ws.oz.zs,
+                                          (int)(ws.oz.slice_rows / OZ_BM),
+                                          (int)(ws.oz.ldk / OZ_BK),
+                                          (int)(ws.oz.slice_rows / OZ_BM), ws.oz.ez);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
@@ -555,7 +987,7 @@ cudaError_t launch_oz_xslice(cudaStream_t s, const Workspace &ws, const double *
   if (ws.oz.xs[which] == nullptr || n > ws.oz.ldk) return cudaErrorInvalidValue;
   const int p = ws.p;
   k_oz_xslice<<<(n + OZ_BM - 1) / OZ_BM, OZ_BM, 0, s>>>(
-      X, ldx, n, p, oz_nb(p), (__nv_bfloat16 *)ws.oz.xs[which], ws.oz.ldk, ws.oz.ex[which]);
+      X, ldx, n, p, oz_nbt(p), (__nv_bfloat16 *)ws.oz.xs[which], ws.oz.ldk, ws.oz.ex[which]);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
@@ -565,29 +997,60 @@ cudaError_t launch_oz_product(cudaStream_t s, const Workspace &ws, int n, int wh
                               double *Ynext, int64_t ldn, int next, int mode) {
   if (ws.oz.zs == nullptr || n > ws.oz.slice_rows) return cudaErrorInvalidValue;
   const int p = ws.p;
-  const int NB = oz_nb(p);
+  const int NB = oz_nb(p), H = oz_halves(p), nbt = oz_nbt(p);
   CUtensorMap ma, mb;
-  cudaError_t e = encode_tile_map(&ma, ws.oz.zs, false, (int64_t)kOzSlices * ws.oz.slice_rows, n,
-                                  ws.oz.ldk, OZ_BM);
+  // the tile-contiguous planes seen as rows of 64 bf16 (one 16 KB box per tile)
+  cudaError_t e = encode_tile_map(&ma, ws.oz.zs, false,
+                                  (int64_t)kOzSlices * ws.oz.slice_rows * (ws.oz.ldk / OZ_BK),
+                                  OZ_BK, OZ_BK, OZ_BM);
   if (e != cudaSuccess) return e;
-  e = encode_tile_map(&mb, ws.oz.xs[which], false, (int64_t)kOzSlices * NB, n, ws.oz.ldk, NB);
+  e = encode_tile_map(&mb, ws.oz.xs[which], false, (int64_t)kOzSlices * nbt, n, ws.oz.ldk, NB);
   if (e != cudaSuccess) return e;
-  const int S = oz_splits(n, ws.num_sms);
-  const dim3 grid((n + OZ_BM - 1) / OZ_BM, S);
+  const int S = oz_splits(n, p, ws.num_sms);
+  const dim3 grid((n + OZ_BM - 1) / OZ_BM, S, H);
   __nv_bfloat16 *xn = next >= 0 ? (__nv_bfloat16 *)ws.oz.xs[next] : nullptr;
   int *exn = next >= 0 ? ws.oz.ex[next] : nullptr;
 #define PF_OZ(NBV)                                                                              \
   k_oz_product<NBV><<<grid, OzCfg<NBV>::THREADS, OzCfg<NBV>::SMEM, s>>>(                       \
-      ma, mb, n, p, (int)ws.oz.slice_rows, S, ws.oz.ez, ws.oz.ex[which], ws.oz.part, ws.oz.cnt, \
+      ma, mb, n, p, nbt, (int)(ws.oz.slice_rows / OZ_BM), (int)(ws.oz.ldk / OZ_BK),          \
+      (int)(ws.oz.slice_rows / OZ_BM), S, ws.oz.ez,                                           \
+      ws.oz.ex[which], ws.oz.part, ws.oz.cnt,                                                 \
       X, ldx, Yprev, ldp, Ynext, ldn, xn, exn, ws.oz.ldk, ws.prm, mode)
-  switch (NB) {
-    case 16: PF_OZ(16); break;
-    case 32: PF_OZ(32); break;
-    case 48: PF_OZ(48); break;
-    default: PF_OZ(64); break;
-  }
+  if (NB == 16) PF_OZ(16);
+  else PF_OZ(32);
 #undef PF_OZ
   PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                             const int32_t *colind, const double *vals, int n, int p,
+                             const double *V, int64_t ldv, const double *theta, const double *lam,
+                             double *Z, int64_t ldz, double *red, int *nblocks) {
+  const OzBuffers &oz = ws.oz;
+  if (oz.zs == nullptr || oz.wp == nullptr || n > oz.slice_rows) return cudaErrorInvalidValue;
+  const int R = (n + OZ_BM - 1) / OZ_BM;
+  k_oz_lr_prep<<<R, OZ_BM, 0, s>>>(V, ldv, theta, n, p, oz.xdiag, (__nv_bfloat16 *)oz.wp,
+                                   (__nv_bfloat16 *)oz.vp, oz.slice_rows, oz.ew, oz.ev,
+                                   oz.mchunk);
+  PF_LAUNCHED();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mw, mv;
+  if ((e = encode_tile_map(&mw, oz.wp, false, (int64_t)kOzSlices * oz.slice_rows, 64, 64,
+                           OZ_BM)) != cudaSuccess)
+    return e;
+  if ((e = encode_tile_map(&mv, oz.vp, false, (int64_t)kOzSlices * oz.slice_rows, 64, 64,
+                           XP_TN)) != cudaSuccess)
+    return e;
+  const int64_t T = (int64_t)R * ((n + XP_TN - 1) / XP_TN);
+  const int grid = (int)(T < ws.num_sms ? T : ws.num_sms);
+  k_oz_expand<<<grid, XP_THREADS, XP_SMEM, s>>>(
+      mw, mv, n, (int)oz.slice_rows, rowptr, colind, vals, lam, oz.xdiag, oz.mchunk, oz.ew,
+      oz.ev, Z, ldz, (__nv_bfloat16 *)oz.zs, (int)(oz.slice_rows / OZ_BM),
+      (int)(oz.ldk / OZ_BK), oz.ez, (int)(oz.slice_rows / OZ_BM), ws.prm, ws.prm, red);
+  PF_LAUNCHED();
+  *nblocks = grid;
   return cudaGetLastError();
 }
 

@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(NT) k_maxcut_lambda(const int32_t *__restrict_
                                                       const double *__restrict__ Z, int64_t ldz,
                                                       double *__restrict__ lam,
                                                       const Params *__restrict__ prm,
-                                                      double *__restrict__ red) {
+                                                      double *__restrict__ red,
+                                                      double *__restrict__ xdiag) {
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * WPB;
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(NT) k_maxcut_lambda(const int32_t *__restrict_
     const double l_new = 2.0 * dx - Z[(int64_t)row * ldz + row] - t * cii - 1.0;
     if (lane == 0) {
       lam[row] = l_new;
+      if (xdiag != nullptr) xdiag[row] = dx;
       spinf = fma(dx - 1.0, dx - 1.0, spinf);
       slam += l_new;
     }
@@ -665,13 +667,24 @@ cudaError_t launch_cnorm(cudaStream_t s, const Workspace &ws, const double *vals
 cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
                                  const int32_t *colind, const double *vals, int n, int p,
                                  const double *V, int64_t ldv, const double *theta, double *Z,
-                                 int64_t ldz, double *lam) {
+                                 int64_t ldz, double *lam, bool sliced) {
   const int nb1 = red_blocks(n, ws.num_sms);
   k_maxcut_lambda<<<nb1, NT, 0, s>>>(rowptr, colind, vals, n, p, V, ldv, theta, Z, ldz, lam,
-                                     ws.prm, slot(ws, SLOT_LAMBDA));
+                                     ws.prm, slot(ws, SLOT_LAMBDA),
+                                     sliced ? ws.oz.xdiag : nullptr);
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (sliced) {
+    int nbx = 0;
+    e = launch_oz_expand(s, ws, rowptr, colind, vals, n, p, V, ldv, theta, lam, Z, ldz,
+                         slot(ws, SLOT_EXPAND), &nbx);
+    if (e != cudaSuccess) return e;
+    k_maxcut_kkt<<<1, NT, 0, s>>>(slot(ws, SLOT_LAMBDA), nb1, slot(ws, SLOT_EXPAND), nbx, theta,
+                                  n, p, ws.prm);
+    PF_LAUNCHED();
+    return cudaGetLastError();
+  }
   const int64_t tiles1 = (n + EB - 1) / EB;
   int64_t nb2 = tiles1 * (tiles1 + 1) / 2;
   if (nb2 > kMaxRedBlocks) nb2 = kMaxRedBlocks;

@@ -1,7 +1,8 @@
 """The arithmetic of the sliced dense product, checked exactly on the CPU.
 
 The tensor-core product cuts FP64 entries into balanced base-256 digits: for
-a row (or 128-row chunk) with exponent e (every |x| < 2^e), round(x 2^(55-e))
+a 128-wide chunk of a row of A (or of a column of X) with exponent e (every
+|x| < 2^e), round(x 2^(55-e))
 = sum_s d_s 2^(8(6-s)) with d_0 in [-128, 128] and d_1..d_6 in [-128, 127],
 so x ~ 2^(e-7) sum_s d_s 2^(-8s).  These tests restate that decomposition
 with Python integers and fractions (no floating point) and check the facts the
@@ -77,15 +78,16 @@ def test_level_sums_fit_fp32():
 
 
 def sliced_product_exact(A, X):
-    """The kernel's arithmetic with exact integers: per-row exponents of A,
-    per-(chunk, column) exponents of X, level sums of pairs s + t <= 6 over
-    128-wide chunks, the int64 fold at resolution 2^-36 (levels 5, 6 rounded
-    half up), the shift to the column's largest exponent, the sum over chunks."""
+    """The kernel's arithmetic with exact integers: exponents of A per (row,
+    128-column chunk) and of X per (128-row chunk, column), level sums of pairs
+    s + t <= 6 over each chunk, the int64 fold at resolution 2^-36 (levels 5, 6
+    rounded half up), the shift to the row's and column's largest exponents,
+    the sum over chunks."""
     n, p = X.shape
-    eA = [exponent(A[i]) for i in range(n)]
     chunks = [(c0, min(n, c0 + 128)) for c0 in range(0, n, 128)]
+    eA = [[exponent(A[i, c0:c1]) for (c0, c1) in chunks] for i in range(n)]
     eX = [[exponent(X[c0:c1, j]) for j in range(p)] for (c0, c1) in chunks]
-    dA = [[digits(float(A[i, k]), eA[i]) for k in range(n)] for i in range(n)]
+    dA = [[digits(float(A[i, k]), eA[i][k // 128]) for k in range(n)] for i in range(n)]
     dX = [[None] * p for _ in range(n)]
     for ci, (c0, c1) in enumerate(chunks):
         for k in range(c0, c1):
@@ -93,6 +95,7 @@ def sliced_product_exact(A, X):
                 dX[k][j] = digits(float(X[k, j]), eX[ci][j])
     Y = np.zeros((n, p), dtype=object)
     for i in range(n):
+        amax = max(eA[i])
         for j in range(p):
             emax = max(eX[ci][j] for ci in range(len(chunks)))
             acc = 0
@@ -107,9 +110,9 @@ def sliced_product_exact(A, X):
                 for lvl in range(KS):
                     sh = 36 - 8 * lvl
                     v += L[lvl] << sh if sh >= 0 else (L[lvl] + (1 << (-sh - 1))) >> (-sh)
-                d = emax - eX[ci][j]
+                d = (amax - eA[i][ci]) + (emax - eX[ci][j])
                 acc += v if d == 0 else (v + (1 << (d - 1))) >> d
-            Y[i, j] = Fraction(acc) * Fraction(2) ** (eA[i] + emax - 14 - 36)
+            Y[i, j] = Fraction(acc) * Fraction(2) ** (amax + emax - 14 - 36)
     return Y
 
 
@@ -119,6 +122,7 @@ def test_sliced_product_error_bound_exact_arithmetic():
     A = rng.standard_normal((n, n)) * np.exp2(rng.uniform(-10, 10, n))[:, None]
     X = rng.standard_normal((n, p)) * np.exp2(rng.uniform(-10, 10, p))[None, :]
     X[:128, 1] *= 2.0 ** -20  # the two chunks of column 1 get different exponents
+    A[::3, 128:] *= 2.0 ** 9   # and so do the two column chunks of every third row
     Y = sliced_product_exact(A, X)
     for i in range(0, n, 7):
         for j in range(p):
