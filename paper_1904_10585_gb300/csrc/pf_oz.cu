@@ -131,6 +131,17 @@ __device__ __forceinline__ long long oz_rshift(long long v, int s) {
   return (v + (1ll << (s - 1))) >> s;
 }
 
+// (double)v 2^k with the scaling done on the exponent field when it stays
+// normal (ldexp otherwise)
+__device__ __forceinline__ double oz_scale(long long v, int k) {
+  if (v == 0) return 0.0;
+  const double d = (double)v;
+  const long long bits = __double_as_longlong(d);
+  const int ex = (int)((bits >> 52) & 0x7FF) + k;
+  if (ex > 0 && ex < 0x7FF) return __longlong_as_double(bits + ((long long)k << 52));
+  return ldexp(d, k);
+}
+
 // Instruction descriptor: fp32 accumulator, bf16 A and B (K-major), M = 128.
 __device__ __forceinline__ uint32_t oz_idesc(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -240,11 +251,7 @@ template <int NB>
 __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n,
     int p, int nbt, int rb_n, int kt_n, int nzc, int nsplit, const int *__restrict__ ez,
-    const int *__restrict__ ex,
-    double *__restrict__ part, int *__restrict__ cnt, const double *X, int64_t ldx,
-    const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn,
-    __nv_bfloat16 *__restrict__ xs_next, int *__restrict__ ex_next, int64_t ldk, Params *prm,
-    int mode) {
+    const int *__restrict__ ex, double *__restrict__ part, Params *prm) {
   using C = OzCfg<NB>;
   constexpr int KS = kOzSlices;
   extern __shared__ uint8_t smem_raw[];
@@ -253,10 +260,8 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
-  __shared__ int is_last;
   __shared__ int dsh[kOzMaxChunks][NB];  // per chunk and column: shift to the split's exponent
   __shared__ int exmax[NB];
-  __shared__ unsigned qmax[4][NB];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb = blockIdx.x, split = blockIdx.y;
@@ -463,92 +468,17 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
     }
 
-    // this split's values: acc 2^(max_c eA_ic + exmax_j - 14 - OZ_FOLD)
-    double y[CW];
+    // this split's values, acc 2^(max_c eA_ic + exmax_j - 14 - OZ_FOLD), to
+    // the partials (summed with the recurrence by k_oz_finish)
+    if (in) {
+      double *pr = part + ((int64_t)split * n + row) * p;
 #pragma unroll
-    for (int j = 0; j < CW; ++j) {
-      const int e2 = exmax[col0 + j];
-      y[j] = (ea == kOzExpBad || e2 == kOzExpBad)
-                 ? __longlong_as_double(0x7FF8000000000000ll)
-                 : ldexp((double)acc[j], ea + e2 - 14 - OZ_FOLD);
-    }
-    bool last = true;
-    if (nsplit > 1) {
-      if (in) {
-        double *pr = part + ((int64_t)split * n + row) * p;
-#pragma unroll
-        for (int j = 0; j < CW; ++j)
-          if (gc0 + j < p) pr[gc0 + j] = y[j];
-      }
-      __threadfence();
-      epi_sync(32 * C::EPI);
-      if (ew == 0 && lane == 0)
-        is_last = atomicAdd(&cnt[rb * gridDim.z + blockIdx.z], 1) == nsplit - 1;
-      epi_sync(32 * C::EPI);
-      last = is_last != 0;
-      if (last) {
-        __threadfence();
-        if (in) {
-#pragma unroll
-          for (int j = 0; j < CW; ++j) y[j] = 0.0;
-          for (int sp = 0; sp < nsplit; ++sp) {
-            const double *pr = part + ((int64_t)sp * n + row) * p;
-#pragma unroll
-            for (int j = 0; j < CW; ++j)
-              if (gc0 + j < p) y[j] += __ldcg(pr + gc0 + j);
-          }
-        }
-        if (ew == 0 && lane == 0) cnt[rb * gridDim.z + blockIdx.z] = 0;  // for the next launch
-      }
-    }
-    if (last) {
-      double cval = 0.0, alpha = 1.0;
-      if (mode != MODE_PLAIN) {
-        cval = prm->c;
-        alpha = (mode == MODE_FIRST ? 1.0 : 2.0) / prm->e;
-      }
-      if (in) {
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          const int jj = gc0 + j;
-          if (jj >= p) continue;
-          double v = y[j];
-          if (mode != MODE_PLAIN) {
-            v = alpha * (v - cval * X[(int64_t)row * ldx + jj]);
-            if (mode == MODE_RECUR) v -= Yprev[(int64_t)row * ldp + jj];
-          }
-          Ynext[(int64_t)row * ldn + jj] = v;
-          y[j] = v;
-        }
-      }
-      if (xs_next != nullptr) {
-        // digit planes of the new block's rows for the next product
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          const unsigned f = (in && gc0 + j < p) ? oz_exfield(y[j]) : 0u;
-          const unsigned m = __reduce_max_sync(0xffffffffu, f);
-          if (lane == 0) qmax[q][col0 + j] = m;
-        }
-        epi_sync(32 * C::EPI);
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          const int lj = col0 + j, jj = gc0 + j;
-          const int e =
-              oz_exponent(max(max(qmax[0][lj], qmax[1][lj]), max(qmax[2][lj], qmax[3][lj])));
-          if (rl == 0) ex_next[rb * kMaxP + jj] = e;
-          int d[KS];
-          if (in && jj < p && e != kOzExpBad) {
-            oz_digits(y[j], e, d);
-          } else {
-#pragma unroll
-            for (int s = 0; s < KS; ++s) d[s] = 0;
-          }
-          if (in) {
-#pragma unroll
-            for (int s = 0; s < KS; ++s)
-              xs_next[(int64_t)(s * nbt + jj) * ldk + row] = oz_bf16(d[s]);
-          }
-        }
+      for (int j = 0; j < CW; ++j) {
+        const int e2 = exmax[col0 + j];
+        const double y = (ea == kOzExpBad || e2 == kOzExpBad)
+                             ? __longlong_as_double(0x7FF8000000000000ll)
+                             : oz_scale(acc[j], ea + e2 - 14 - OZ_FOLD);
+        if (gc0 + j < p) pr[gc0 + j] = y;
       }
     }
   }
@@ -658,17 +588,6 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
       *reinterpret_cast<uint4 *>(vp + off) = make_uint4(pv[s2][0], pv[s2][1], pv[s2][2], pv[s2][3]);
     }
   }
-}
-
-// (double)v 2^k with the scaling done on the exponent field when it stays
-// normal (ldexp otherwise)
-__device__ __forceinline__ double oz_scale(long long v, int k) {
-  if (v == 0) return 0.0;
-  const double d = (double)v;
-  const long long bits = __double_as_longlong(d);
-  const int ex = (int)((bits >> 52) & 0x7FF) + k;
-  if (ex > 0 && ex < 0x7FF) return __longlong_as_double(bits + ((long long)k << 52));
-  return ldexp(d, k);
 }
 
 __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
@@ -940,6 +859,78 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
   }
 }
 
+// ---------------------------------------------------------------------------
+// The sum of the K splits in split order, the recurrence, and the digit
+// planes of the new block for the next product.  Grid (128-row blocks,
+// 8-column groups), thread = row: the FP64 work of the combine spreads over
+// many SMs instead of one CTA per row block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(OZ_BM) k_oz_finish(
+    const double *__restrict__ part, int nsplit, int n, int p, const double *X, int64_t ldx,
+    const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn,
+    __nv_bfloat16 *__restrict__ xs_next, int *__restrict__ ex_next, int64_t ldk, int nbt,
+    const Params *__restrict__ prm, int mode) {
+  __shared__ unsigned qmax[4][8];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int rb = blockIdx.x, j0 = blockIdx.y * 8;
+  const int row = rb * OZ_BM + t;
+  const bool in = row < n;
+  double cval = 0.0, alpha = 1.0;
+  if (mode != MODE_PLAIN) {
+    cval = prm->c;
+    alpha = (mode == MODE_FIRST ? 1.0 : 2.0) / prm->e;
+  }
+  double y[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) y[j] = 0.0;
+  if (in) {
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const double *pr = part + ((int64_t)sp * n + row) * p + j0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j0 + j < p) y[j] += __ldcg(pr + j);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int jj = j0 + j;
+      if (jj >= p) continue;
+      double v = y[j];
+      if (mode != MODE_PLAIN) {
+        v = alpha * (v - cval * X[(int64_t)row * ldx + jj]);
+        if (mode == MODE_RECUR) v -= Yprev[(int64_t)row * ldp + jj];
+      }
+      Ynext[(int64_t)row * ldn + jj] = v;
+      y[j] = v;
+    }
+  }
+  if (xs_next == nullptr) return;  // uniform over the grid
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const unsigned f = (in && j0 + j < p) ? oz_exfield(y[j]) : 0u;
+    const unsigned mx = __reduce_max_sync(0xffffffffu, f);
+    if (lane == 0) qmax[w][j] = mx;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int jj = j0 + j;
+    const int e = oz_exponent(max(max(qmax[0][j], qmax[1][j]), max(qmax[2][j], qmax[3][j])));
+    if (t == 0 && jj < nbt) ex_next[rb * kMaxP + jj] = e;
+    int d[kOzSlices];
+    if (in && jj < p && e != kOzExpBad) {
+      oz_digits(y[j], e, d);
+    } else {
+#pragma unroll
+      for (int s2 = 0; s2 < kOzSlices; ++s2) d[s2] = 0;
+    }
+    if (in && jj < nbt) {
+#pragma unroll
+      for (int s2 = 0; s2 < kOzSlices; ++s2)
+        xs_next[(int64_t)(s2 * nbt + jj) * ldk + row] = oz_bf16(d[s2]);
+    }
+  }
+}
+
 template <int NB>
 cudaError_t oz_set_attr() {
   return cudaFuncSetAttribute(k_oz_product<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1007,18 +998,22 @@ cudaError_t launch_oz_product(cudaStream_t s, const Workspace &ws, int n, int wh
   e = encode_tile_map(&mb, ws.oz.xs[which], false, (int64_t)kOzSlices * nbt, n, ws.oz.ldk, NB);
   if (e != cudaSuccess) return e;
   const int S = oz_splits(n, p, ws.num_sms);
-  const dim3 grid((n + OZ_BM - 1) / OZ_BM, S, H);
-  __nv_bfloat16 *xn = next >= 0 ? (__nv_bfloat16 *)ws.oz.xs[next] : nullptr;
-  int *exn = next >= 0 ? ws.oz.ex[next] : nullptr;
+  const int R = (n + OZ_BM - 1) / OZ_BM;
+  const dim3 grid(R, S, H);
 #define PF_OZ(NBV)                                                                              \
   k_oz_product<NBV><<<grid, OzCfg<NBV>::THREADS, OzCfg<NBV>::SMEM, s>>>(                       \
       ma, mb, n, p, nbt, (int)(ws.oz.slice_rows / OZ_BM), (int)(ws.oz.ldk / OZ_BK),          \
-      (int)(ws.oz.slice_rows / OZ_BM), S, ws.oz.ez,                                           \
-      ws.oz.ex[which], ws.oz.part, ws.oz.cnt,                                                 \
-      X, ldx, Yprev, ldp, Ynext, ldn, xn, exn, ws.oz.ldk, ws.prm, mode)
+      (int)(ws.oz.slice_rows / OZ_BM), S, ws.oz.ez, ws.oz.ex[which], ws.oz.part, ws.prm)
   if (NB == 16) PF_OZ(16);
   else PF_OZ(32);
 #undef PF_OZ
+  PF_LAUNCHED();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  __nv_bfloat16 *xn = next >= 0 ? (__nv_bfloat16 *)ws.oz.xs[next] : nullptr;
+  int *exn = next >= 0 ? ws.oz.ex[next] : nullptr;
+  k_oz_finish<<<dim3(R, (nbt + 7) / 8), OZ_BM, 0, s>>>(ws.oz.part, S, n, p, X, ldx, Yprev, ldp,
+                                                      Ynext, ldn, xn, exn, ws.oz.ldk, nbt,
+                                                      ws.prm, mode);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
