@@ -120,8 +120,15 @@ __device__ __forceinline__ void oz_digits(double x, int e, int *d) {
   d[0] = (int)v;
 }
 
+// bf16 pattern of a digit (|d| <= 255: at most 8 significant bits, exact).
+// d + 1.5 2^23 is exact in fp32 for |d| < 2^22, so subtracting the constant
+// again leaves d; its bf16 pattern is the top half of the float's.  Integer
+// and FMA-pipe operations instead of two conversions.
+__device__ __forceinline__ uint32_t oz_bf16_bits(int d) {
+  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+}
 __device__ __forceinline__ __nv_bfloat16 oz_bf16(int d) {
-  return __float2bfloat16_rn((float)d);  // exact: |d| <= 128
+  return __ushort_as_bfloat16((unsigned short)oz_bf16_bits(d));
 }
 
 // round(v / 2^s) for s >= 0
@@ -131,8 +138,8 @@ __device__ __forceinline__ long long oz_rshift(long long v, int s) {
   return (v + (1ll << (s - 1))) >> s;
 }
 
-// (double)v 2^k with the scaling done on the exponent field when it stays
-// normal (ldexp otherwise)
+// (double)v 2^k: the conversion rounds to nearest even, the scaling is done
+// on the exponent field when the result stays normal (ldexp otherwise)
 __device__ __forceinline__ double oz_scale(long long v, int k) {
   if (v == 0) return 0.0;
   const double d = (double)v;
@@ -499,8 +506,9 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
 // cores, producing the new Z = X~ - tC - Diag(lam) in FP64 together with its
 // digit planes for the next step's products:
 //   k_oz_lr_prep : digit planes of the rows of W and V (K = 64, zero beyond
-//                  p and for theta_l <= 0), their row exponents, and per
-//                  128-row chunk the largest sqrt(X~_jj);
+//                  p and for theta_l <= 0), their row exponents, sqrt(X~_ii)
+//                  in place of X~_ii, and per 128-row chunk the largest
+//                  sqrt(X~_jj);
 //   k_oz_expand  : persistent over 128 x 64 output tiles (row block by row
 //                  block).  One MMA round per tile (K = 64, one exact chunk:
 //                  |level sums| <= 7 * 64 * 2^14), the 7 levels in 448 TMEM
@@ -513,12 +521,12 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
 // + [i in c] |lam_i| (times 1 + 2^-20 for rounding).  A loose bound costs
 // accuracy bits of the planes, never correctness.
 // ===========================================================================
-// epilogue warps: 2 per TMEM lane quarter, 32 columns each (10 warps in all,
-// so that every SM sub-partition's 16K registers hold its warps at ~160
-// registers a thread)
-constexpr int XP_EPI = 8;
+// epilogue warps: 4 per TMEM lane quarter, 16 columns each (18 warps in all:
+// at 96 registers a thread with a few spills they still hide more latency
+// than 8 warps at 160 registers; measured 471 vs 547 us at n = 4096)
+constexpr int XP_EPI = 16;
 constexpr int XP_THREADS = 64 + 32 * XP_EPI;
-constexpr int XP_CW = 32;                     // columns per epilogue thread
+constexpr int XP_CW = 16;                     // columns per epilogue thread
 constexpr int XP_TN = 64;                     // output columns per tile
 constexpr int XP_W_BYTES = kOzSlices * OZ_A_BYTES;         // 7 W planes of a row block
 constexpr int XP_V_BYTES = kOzSlices * XP_TN * 128;        // 7 V planes of a column tile
@@ -526,7 +534,7 @@ constexpr size_t XP_SMEM = 1024 + (size_t)XP_W_BYTES + XP_V_BYTES;
 
 __global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
     const double *__restrict__ V, int64_t ldv, const double *__restrict__ theta, int n, int p,
-    const double *__restrict__ xdiag, __nv_bfloat16 *__restrict__ wp,
+    double *__restrict__ xdiag, __nv_bfloat16 *__restrict__ wp,
     __nv_bfloat16 *__restrict__ vp, int64_t plane_rows, int *__restrict__ ew,
     int *__restrict__ ev, double *__restrict__ mchunk) {
   __shared__ double th[kMaxP];
@@ -536,6 +544,7 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
   const bool in = row < n;
   if (t < kMaxP) th[t] = (t < p && theta[t] > 0.0) ? theta[t] : 0.0;
   double r = in ? sqrt(fmax(xdiag[row], 0.0)) : 0.0;
+  if (in) xdiag[row] = r;  // the expansion reads sqrt(X~_ii)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
   if (lane == 0) sq[w] = r;
@@ -570,8 +579,8 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
         for (int s2 = 0; s2 < kOzSlices; ++s2) dv[s2] = 0;
 #pragma unroll
       for (int s2 = 0; s2 < kOzSlices; ++s2) {
-        const uint32_t bw = __bfloat16_as_ushort(oz_bf16(dw[s2]));
-        const uint32_t bv = __bfloat16_as_ushort(oz_bf16(dv[s2]));
+        const uint32_t bw = oz_bf16_bits(dw[s2]);
+        const uint32_t bv = oz_bf16_bits(dv[s2]);
         if (h & 1) {
           pw[s2][h >> 1] |= bw << 16;
           pv[s2][h >> 1] |= bv << 16;
@@ -745,7 +754,7 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
           if (col >= j0 && e_lo == e_hi) e_lo = e;
         }
         const double bound =
-            (sqrt(fmax(xdiag[row], 0.0)) * mchunk[c] + tt * cmax +
+            (xdiag[row] * mchunk[c] + tt * cmax +
              ((row >= cb && row < ce) ? fabs(lam_r) : 0.0)) *
             (1.0 + 0x1p-20);
         ez_rc = oz_exponent(oz_exfield(bound));
@@ -812,7 +821,7 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
           }
 #pragma unroll
           for (int s2 = 0; s2 < KS; ++s2) {
-            const uint32_t b = __bfloat16_as_ushort(oz_bf16(d[s2]));
+            const uint32_t b = oz_bf16_bits(d[s2]);
             if (i & 1) pk[s2][i >> 1] |= b << 16;
             else pk[s2][i >> 1] = b;
           }
