@@ -45,7 +45,10 @@ FP64_CUBLAS_MEASURED = 1.09    # torch float64 matmul 16384x16384x64 on this poo
 HBM_PEAK_GBS = 6773.2          # measured STREAM-style copy on the GB300s
 # dram bytes per launch of the dominant kernel from the committed ncu captures
 # (None until a capture of the current kernel exists)
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {
+    # profiles/k_oz_product_maxcut_n4096.md: 237.30 MB read + 3.62 MB written per launch
+    "maxcut_n4096": 240.92e6,
+}
 SLICED_NOTE = ("bf16 digit planes x7 of Z and X on tcgen05 (TMA, TMEM), level sums exact in fp32, "
                "int64 fold, FP64 recurrence epilogue: an FP64-accurate product")
 
@@ -620,7 +623,7 @@ def run_serving(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    import paper_1904_10585_gb300 as pkg  # noqa: F401
+    import paper_1904_10585_gb300 as pkg
     from paper_1904_10585_gb300 import serving as SV
     from paper_1904_10585_gb300 import solver as S
 
@@ -657,35 +660,40 @@ def run_serving(args):
     sp50, sp99 = SV.latency_percentiles(res_sat)
     srv.close()
 
-    # plain baseline: one request at a time, FP64 path
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.synchronize(dev)
-    tp0 = time.perf_counter()
-    plain_kkt = []
-    ctxs = {}
-    for r in reqs:
-        key = r.kind
-        if key not in ctxs:
-            ctxs[key] = S.Context(p=p, n_max=(mc_n[1] if key == "maxcut" else cp_n[1]),
-                                  degree=degree, stream=stream)
-        ctx = ctxs[key]
-        with torch.cuda.stream(stream):
-            rp = r.pinned["rowptr"].to(dev, non_blocking=True)
-            ci = r.pinned["colind"].to(dev, non_blocking=True)
-            vv = r.pinned["vals"].to(dev, non_blocking=True)
-            U0 = r.pinned["U0"].to(dev, non_blocking=True)
-            if r.kind == "maxcut":
-                pr = S.maxcut_problem(rp, ci, vv, U0)
-            else:
-                pr = S.completion_problem(rp, ci, vv, U0, mu=r.mu, t=r.t)
-            S.problem_init(ctx, pr)
-            out = S.solve(ctx, pr, r.max_iter, TOL, 10)
-            V = pr.V.to("cpu")
-        plain_kkt.append(out.kkt)
-    stream.synchronize()
-    plain_s = time.perf_counter() - tp0
-    for c in ctxs.values():
-        c.close()
+    # plain baselines: one request at a time, FP64 path -- with FP64 FMAs
+    # (the plain method) and with the FP64-accurate sliced tensor-core products
+    def one_at_a_time(dense_product):
+        stream = torch.cuda.Stream(device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctxs = {}
+        for r in reqs:
+            key = r.kind
+            if key not in ctxs:
+                ctxs[key] = S.Context(p=p, n_max=(mc_n[1] if key == "maxcut" else cp_n[1]),
+                                      degree=degree, stream=stream,
+                                      dense_product=dense_product)
+            ctx = ctxs[key]
+            with torch.cuda.stream(stream):
+                rp = r.pinned["rowptr"].to(dev, non_blocking=True)
+                ci = r.pinned["colind"].to(dev, non_blocking=True)
+                vv = r.pinned["vals"].to(dev, non_blocking=True)
+                U0 = r.pinned["U0"].to(dev, non_blocking=True)
+                if r.kind == "maxcut":
+                    pr = S.maxcut_problem(rp, ci, vv, U0)
+                else:
+                    pr = S.completion_problem(rp, ci, vv, U0, mu=r.mu, t=r.t)
+                S.problem_init(ctx, pr)
+                S.solve(ctx, pr, r.max_iter, TOL, 10)
+                pr.V.to("cpu")
+        stream.synchronize()
+        secs = time.perf_counter() - t0
+        for c in ctxs.values():
+            c.close()
+        return secs
+
+    plain_s = one_at_a_time(pkg.PF_DENSE_FP64)
+    sliced_s = one_at_a_time(pkg.PF_DENSE_SLICED)
     plain_rate = N / plain_s
     kkts = np.array([r.kkt for r in res_sat])
     line = {
@@ -701,7 +709,12 @@ def run_serving(args):
         "latency_s": {"poisson_0.8x_p50": p50, "poisson_0.8x_p99": p99,
                       "saturation_p50": sp50, "saturation_p99": sp99},
         "plain_one_at_a_time_fp64": {"value": plain_rate, "seconds": plain_s,
+                                     "dense_product": "FP64 FMAs on the CUDA cores",
                                      "speedup_of_serving": sat_rate / plain_rate},
+        "one_at_a_time_fp64_sliced": {"value": N / sliced_s, "seconds": sliced_s,
+                                      "dense_product": "FP64-accurate bf16 digit planes on "
+                                                       "tcgen05",
+                                      "speedup_of_serving": sat_rate * sliced_s / N},
         "kkt_reached_fraction": float(np.mean(kkts <= TOL)),
         "clocks": clocks,
     }

@@ -10,6 +10,8 @@
 //   * CTA c computes the new rows of H' = J^T H J for its share of the
 //     rotation pairs (2 x 2 blocks J_i^T H_ij J_j) and stores them into the
 //     next buffer of every CTA of the cluster (distributed shared memory);
+//     the one-CTA variant (p <= 32) computes the upper block triangle only
+//     and mirrors it;
 //   * CTA c owns a slice of rows of the eigenvector matrix and applies all
 //     rotations to it locally;
 //   * one cluster barrier per round orders the exchange.
@@ -162,9 +164,10 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
         vr[k] = cs[i] * vk - sn[i] * vl;
         vr[l] = sn[i] * vk + cs[i] * vl;
       }
-      // new rows of H for the pairs of this CTA: block (i, j) = J_i^T H_ij J_j.
-      // One CTA computes the upper block triangle only and mirrors it (H
-      // stays exactly symmetric; a third less FP64 work per round).
+      // new blocks of H: block (i, j) = J_i^T H_ij J_j.  One CTA computes the
+      // upper block triangle and mirrors it (H stays exactly symmetric; a
+      // third less FP64 work per round); the cluster's CTAs compute the block
+      // rows of their pairs, so that their broadcasts stay row-contiguous
       const int nb = NC == 1 ? half * (half + 1) / 2 : (pair1 - pair0) * half;
       for (int idx = tid; idx < nb; idx += JNT) {
         const int i = NC == 1 ? (int)tri_i[idx] : pair0 + idx / half;
@@ -189,12 +192,12 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
           if (rj) dst[ki * JLD + lj] = h01;
           if (ri) dst[li * JLD + kj] = h10;
           if (ri && rj) dst[li * JLD + lj] = h11;
-        }
-        if (NC == 1 && i != j) {  // the mirrored block (j, i)
-          Hn[kj * JLD + ki] = h00;
-          if (rj) Hn[lj * JLD + ki] = h01;
-          if (ri) Hn[kj * JLD + li] = h10;
-          if (ri && rj) Hn[lj * JLD + li] = h11;
+          if (NC == 1 && i != j) {  // the mirrored block (j, i)
+            dst[kj * JLD + ki] = h00;
+            if (rj) dst[lj * JLD + ki] = h01;
+            if (ri) dst[kj * JLD + li] = h10;
+            if (ri && rj) dst[lj * JLD + li] = h11;
+          }
         }
       }
       sync_all();
