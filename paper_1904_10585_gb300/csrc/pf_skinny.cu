@@ -152,9 +152,9 @@ __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpar
       if (!(piv > 1e-13 * (diag0[0] + sh)) || !isfinite(piv)) {
         fail = 1;
       } else {
-        const double d = sqrt(piv);
-        R[0][0] = d;
-        dinv[0] = 1.0 / d;
+        const double r = rsqrt(piv);  // one long-latency call per pivot
+        R[0][0] = piv * r;
+        dinv[0] = r;
       }
     }
     __syncthreads();
@@ -172,9 +172,9 @@ __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpar
           if (!(piv > 1e-13 * (diag0[i] + sh)) || !isfinite(piv)) {
             fail = 1;
           } else {
-            const double d = sqrt(piv);
-            R[i][i] = d;
-            dinv[i] = 1.0 / d;
+            const double r = rsqrt(piv);
+            R[i][i] = piv * r;
+            dinv[i] = r;
           }
         }
       }
@@ -247,13 +247,25 @@ __global__ void __launch_bounds__(NT) k_apply_right(const double *Y, int64_t ldy
       Ys[r][c] = (gr < r1 && c < p) ? Y[(int64_t)gr * ldy + c] : 0.0;
     }
     __syncthreads();
-    for (int e = tid; e < RC * PT; e += NT) {
-      const int r = e / PT, c = e % PT, gr = rb + r;
-      if (gr >= r1 || c >= p) continue;
+    // thread = column c and rows rg, rg + G, ...: U independent FMA chains
+    // sharing each load of R (a warp reads one row of Ys: a broadcast)
+    constexpr int G = NT / PT, U = RC / G;
+    const int c = tid % PT, rg = tid / PT;
+    if (c < p) {
       const int kend = upper ? c + 1 : p;
-      double s = 0.0;
-      for (int k = 0; k < kend; ++k) s = fma(Ys[r][k], Rs[k][c], s);
-      Q[(int64_t)gr * ldq + c] = s;
+      double acc[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] = 0.0;
+      for (int k = 0; k < kend; ++k) {
+        const double rk = Rs[k][c];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = fma(Ys[rg + G * u][k], rk, acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int gr = rb + rg + G * u;
+        if (gr < r1) Q[(int64_t)gr * ldq + c] = acc[u];
+      }
     }
   }
 }
@@ -422,7 +434,7 @@ cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double
                                double *Q, int64_t ldq, int n, int p, const double *R, int upper,
                                int cond_flag) {
   int nb, rpb;
-  row_split(n, 4 * ws.num_sms, 64, &nb, &rpb);
+  row_split(n, 4 * ws.num_sms, RC, &nb, &rpb);
   if (p <= 16)
     {
       k_apply_right<16><<<nb, NT, apply_bytes(16), s>>>(Y, ldy, Q, ldq, n, p, R, upper, rpb, ws.prm, cond_flag);
