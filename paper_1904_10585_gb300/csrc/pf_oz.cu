@@ -527,6 +527,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
 constexpr int XP_EPI = 16;
 constexpr int XP_THREADS = 64 + 32 * XP_EPI;
 constexpr int XP_CW = 16;                     // columns per epilogue thread
+constexpr int XP_G = 8;                       // columns folded together (TMEM load width)
 constexpr int XP_TN = 64;                     // output columns per tile
 constexpr int XP_W_BYTES = kOzSlices * OZ_A_BYTES;         // 7 W planes of a row block
 constexpr int XP_V_BYTES = kOzSlices * XP_TN * 128;        // 7 V planes of a column tile
@@ -769,26 +770,29 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
       int e = e_lo;
 #pragma unroll
-      for (int g = 0; g < XP_CW; g += 8) {
+      for (int g = 0; g < XP_CW; g += XP_G) {
         // the group's old Z and V exponents: independent loads, in flight
         // while TMEM is read and the levels are folded
-        double zo[8];
-        int evv[8];
+        double zo[XP_G];
+        int evv[XP_G];
         const double *zrow = Z + (int64_t)(in ? row : 0) * ldz;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < XP_G; ++i) {
           const int col = j0 + g + i;
           const bool ok2 = in && col < n;
           zo[i] = ok2 ? zrow[col] : 0.0;
           evv[i] = ok2 ? ev[col] : 0;
         }
-        uint32_t L[KS][8];
+        uint32_t L[KS][XP_G];
 #pragma unroll
-        for (int l = 0; l < KS; ++l) tmem_ld8(taddr + l * XP_TN + g, L[l]);
+        for (int l = 0; l < KS; ++l) {
+          if constexpr (XP_G == 8) tmem_ld8(taddr + l * XP_TN + g, L[l]);
+          else tmem_ld4(taddr + l * XP_TN + g, L[l]);
+        }
         tmem_wait_ld();
-        uint32_t pk[KS][4];
+        uint32_t pk[KS][XP_G / 2];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < XP_G; ++i) {
           const int col = j0 + g + i;
           long long v = 0;
 #pragma unroll
@@ -828,9 +832,14 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
         }
         if (in) {
 #pragma unroll
-          for (int s2 = 0; s2 < KS; ++s2)
-            *reinterpret_cast<uint4 *>(zs + oz_zs_index(s2, row, j0 + g, rb_n, kt_n)) =
-                make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+          for (int s2 = 0; s2 < KS; ++s2) {
+            __nv_bfloat16 *dst = zs + oz_zs_index(s2, row, j0 + g, rb_n, kt_n);
+            if constexpr (XP_G == 8)
+              *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2],
+                                                           pk[s2][3]);
+            else
+              *reinterpret_cast<uint2 *>(dst) = make_uint2(pk[s2][0], pk[s2][1]);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
