@@ -70,7 +70,8 @@ __device__ __forceinline__ void rotation(double hkk, double hll, double hkl, dou
 }
 
 constexpr int JC = 8;      // CTAs per cluster (p > 32)
-constexpr int JNT = 256;   // threads per CTA
+constexpr int JNT = 256;   // threads per CTA of the cluster version
+constexpr int JNB = 256;   // threads of the one-CTA version
 constexpr int JLD = kMaxP + 1;
 
 // The sweep loop, on NC CTAs: NC = 8 (a thread-block cluster, distributed
@@ -78,7 +79,7 @@ constexpr int JLD = kMaxP + 1;
 // everything and a block barrier orders the rounds; at p <= 32 the FP64 work
 // of a round is small enough that one SM beats the cluster's barrier and
 // broadcast cost).
-template <int NC>
+template <int NC, int NTH>
 __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int p,
                                             double *__restrict__ Yeig,
                                             double *__restrict__ theta, Params *prm) {
@@ -94,6 +95,7 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
   double *Vloc = dyn + 2 * kMaxP * JLD;  // JROWS x JLD
   __shared__ double cs[kMaxP / 2], sn[kMaxP / 2];
   __shared__ int pk[kMaxP / 2], pl[kMaxP / 2];
+  __shared__ int act[kMaxP / 2];  // the pair rotates (an integer test, off the FP64 pipe)
   __shared__ double redsh[32];
   __shared__ double lam_s[kMaxP];
   // one CTA: the blocks (i, j >= i) of the upper block triangle, in order
@@ -118,11 +120,11 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     }
   }
   // H = sym(reduced Gram matrix); local eigenvector rows = rows of I
-  for (int idx = tid; idx < p * p; idx += JNT) {
+  for (int idx = tid; idx < p * p; idx += NTH) {
     const int a = idx / p, b = idx % p;
     Hb[0][a * JLD + b] = 0.5 * (Hin[a * p + b] + Hin[b * p + a]);
   }
-  for (int idx = tid; idx < JROWS * p; idx += JNT) {
+  for (int idx = tid; idx < JROWS * p; idx += NTH) {
     const int r = idx / p, b = idx % p;
     Vloc[r * JLD + b] = (row0 + r == b) ? 1.0 : 0.0;
   }
@@ -132,7 +134,7 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
   for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
     const double *H = Hb[cur];
     double off = 0.0, tot = 0.0;
-    for (int idx = tid; idx < p * p; idx += JNT) {
+    for (int idx = tid; idx < p * p; idx += NTH) {
       const int a = idx / p, b = idx % p;
       const double h = H[a * JLD + b];
       tot = fma(h, h, tot);
@@ -152,13 +154,14 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
         double c = 1.0, s = 0.0;
         if (l < p) rotation(H[k * JLD + k], H[l * JLD + l], H[k * JLD + l], c, s);
         cs[i] = c; sn[i] = s; pk[i] = k; pl[i] = l;
+        act[i] = (l < p && s != 0.0) ? 1 : 0;
       }
       __syncthreads();
       // local eigenvector rows: V <- V J
-      for (int idx = tid; idx < (row1 - row0) * half; idx += JNT) {
+      for (int idx = tid; idx < (row1 - row0) * half; idx += NTH) {
         const int r = idx / half, i = idx % half;
+        if (!act[i]) continue;
         const int k = pk[i], l = pl[i];
-        if (l >= p || sn[i] == 0.0) continue;
         double *vr = Vloc + r * JLD;
         const double vk = vr[k], vl = vr[l];
         vr[k] = cs[i] * vk - sn[i] * vl;
@@ -169,7 +172,7 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
       // third less FP64 work per round); the cluster's CTAs compute the block
       // rows of their pairs, so that their broadcasts stay row-contiguous
       const int nb = NC == 1 ? half * (half + 1) / 2 : (pair1 - pair0) * half;
-      for (int idx = tid; idx < nb; idx += JNT) {
+      for (int idx = tid; idx < nb; idx += NTH) {
         const int i = NC == 1 ? (int)tri_i[idx] : pair0 + idx / half;
         const int j = NC == 1 ? (int)tri_j[idx] : idx % half;
         const int ki = pk[i], li = pl[i], kj = pk[j], lj = pl[j];
@@ -210,7 +213,7 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
   if (tid < p) lam_s[tid] = H[tid * JLD + tid];
   __syncthreads();
   bool bad = false;
-  for (int j = tid; j < p; j += JNT) {
+  for (int j = tid; j < p; j += NTH) {
     const double lj = lam_s[j];
     if (!isfinite(lj)) bad = true;
     int rk = 0;
@@ -229,13 +232,13 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
 __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JNT)
     k_jacobi_cluster(const double *__restrict__ Hin, int p, double *__restrict__ Yeig,
                      double *__restrict__ theta, Params *prm) {
-  jacobi_body<JC>(Hin, p, Yeig, theta, prm);
+  jacobi_body<JC, JNT>(Hin, p, Yeig, theta, prm);
 }
 
-__global__ void __launch_bounds__(JNT)
+__global__ void __launch_bounds__(JNB)
     k_jacobi_block(const double *__restrict__ Hin, int p, double *__restrict__ Yeig,
                    double *__restrict__ theta, Params *prm) {
-  jacobi_body<1>(Hin, p, Yeig, theta, prm);
+  jacobi_body<1, JNB>(Hin, p, Yeig, theta, prm);
 }
 
 constexpr size_t jacobi_bytes(int nc) {
@@ -255,7 +258,7 @@ cudaError_t configure_jacobi() {
 
 cudaError_t launch_jacobi_cluster(cudaStream_t s, const Workspace &ws, const double *H, int p,
                                   double *theta) {
-  if (p <= 32) k_jacobi_block<<<1, JNT, jacobi_bytes(1), s>>>(H, p, ws.Yeig, theta, ws.prm);
+  if (p <= 32) k_jacobi_block<<<1, JNB, jacobi_bytes(1), s>>>(H, p, ws.Yeig, theta, ws.prm);
   else k_jacobi_cluster<<<JC, JNT, jacobi_bytes(JC), s>>>(H, p, ws.Yeig, theta, ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
