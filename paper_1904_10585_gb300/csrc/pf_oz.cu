@@ -533,30 +533,24 @@ constexpr int XP_W_BYTES = kOzSlices * OZ_A_BYTES;         // 7 W planes of a ro
 constexpr int XP_V_BYTES = kOzSlices * XP_TN * 128;        // 7 V planes of a column tile
 constexpr size_t XP_SMEM = 1024 + (size_t)XP_W_BYTES + XP_V_BYTES;
 
-// One CTA per 128-row chunk, 8 threads per row (one 8-column group each).
-__global__ void __launch_bounds__(OZ_BM * 8) k_oz_lr_prep(
+__global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
     const double *__restrict__ V, int64_t ldv, const double *__restrict__ theta, int n, int p,
     double *__restrict__ xdiag, __nv_bfloat16 *__restrict__ wp,
     __nv_bfloat16 *__restrict__ vp, int64_t plane_rows, int *__restrict__ ew,
     int *__restrict__ ev, double *__restrict__ mchunk) {
   __shared__ double th[kMaxP];
-  __shared__ double sq[32];
+  __shared__ double sq[4];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int rl = t >> 3, grp = t & 7;
-  const int row = blockIdx.x * OZ_BM + rl;
+  const int row = blockIdx.x * OZ_BM + t;
   const bool in = row < n;
   if (t < kMaxP) th[t] = (t < p && theta[t] > 0.0) ? theta[t] : 0.0;
   double r = in ? sqrt(fmax(xdiag[row], 0.0)) : 0.0;
+  if (in) xdiag[row] = r;  // the expansion reads sqrt(X~_ii)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
   if (lane == 0) sq[w] = r;
   __syncthreads();
-  if (in && grp == 0) xdiag[row] = sqrt(fmax(xdiag[row], 0.0));  // the expansion reads sqrt(X~_ii)
-  if (t == 0) {
-    double m = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, sq[k]);
-    mchunk[blockIdx.x] = m;
-  }
+  if (t == 0) mchunk[blockIdx.x] = fmax(fmax(sq[0], sq[1]), fmax(sq[2], sq[3]));
   if (!in) return;
   const double *vr = V + (int64_t)row * ldv;
   unsigned fw = 0, fv = 0;
@@ -567,43 +561,42 @@ __global__ void __launch_bounds__(OZ_BM * 8) k_oz_lr_prep(
     }
   }
   const int e_w = oz_exponent(fw), e_v = oz_exponent(fv);
-  if (grp == 0) {
-    ew[row] = e_w;
-    ev[row] = e_v;
-  }
-  const int l0 = grp * 8;
-  uint32_t pw[kOzSlices][4], pv[kOzSlices][4];
+  ew[row] = e_w;
+  ev[row] = e_v;
+  for (int l0 = 0; l0 < 64; l0 += 8) {
+    uint32_t pw[kOzSlices][4], pv[kOzSlices][4];
 #pragma unroll
-  for (int h = 0; h < 8; ++h) {
-    const int l = l0 + h;
-    int dw[kOzSlices], dv[kOzSlices];
-    const bool on = l < p && th[l] > 0.0;
-    if (on && e_w != kOzExpBad) oz_digits(vr[l] * th[l], e_w, dw);
-    else
+    for (int h = 0; h < 8; ++h) {
+      const int l = l0 + h;
+      int dw[kOzSlices], dv[kOzSlices];
+      const bool on = l < p && th[l] > 0.0;
+      if (on && e_w != kOzExpBad) oz_digits(vr[l] * th[l], e_w, dw);
+      else
 #pragma unroll
-      for (int s2 = 0; s2 < kOzSlices; ++s2) dw[s2] = 0;
-    if (on && e_v != kOzExpBad) oz_digits(vr[l], e_v, dv);
-    else
+        for (int s2 = 0; s2 < kOzSlices; ++s2) dw[s2] = 0;
+      if (on && e_v != kOzExpBad) oz_digits(vr[l], e_v, dv);
+      else
 #pragma unroll
-      for (int s2 = 0; s2 < kOzSlices; ++s2) dv[s2] = 0;
+        for (int s2 = 0; s2 < kOzSlices; ++s2) dv[s2] = 0;
 #pragma unroll
-    for (int s2 = 0; s2 < kOzSlices; ++s2) {
-      const uint32_t bw = oz_bf16_bits(dw[s2]);
-      const uint32_t bv = oz_bf16_bits(dv[s2]);
-      if (h & 1) {
-        pw[s2][h >> 1] |= bw << 16;
-        pv[s2][h >> 1] |= bv << 16;
-      } else {
-        pw[s2][h >> 1] = bw;
-        pv[s2][h >> 1] = bv;
+      for (int s2 = 0; s2 < kOzSlices; ++s2) {
+        const uint32_t bw = oz_bf16_bits(dw[s2]);
+        const uint32_t bv = oz_bf16_bits(dv[s2]);
+        if (h & 1) {
+          pw[s2][h >> 1] |= bw << 16;
+          pv[s2][h >> 1] |= bv << 16;
+        } else {
+          pw[s2][h >> 1] = bw;
+          pv[s2][h >> 1] = bv;
+        }
       }
     }
-  }
 #pragma unroll
-  for (int s2 = 0; s2 < kOzSlices; ++s2) {
-    const int64_t off = ((int64_t)s2 * plane_rows + row) * 64 + l0;
-    *reinterpret_cast<uint4 *>(wp + off) = make_uint4(pw[s2][0], pw[s2][1], pw[s2][2], pw[s2][3]);
-    *reinterpret_cast<uint4 *>(vp + off) = make_uint4(pv[s2][0], pv[s2][1], pv[s2][2], pv[s2][3]);
+    for (int s2 = 0; s2 < kOzSlices; ++s2) {
+      const int64_t off = ((int64_t)s2 * plane_rows + row) * 64 + l0;
+      *reinterpret_cast<uint4 *>(wp + off) = make_uint4(pw[s2][0], pw[s2][1], pw[s2][2], pw[s2][3]);
+      *reinterpret_cast<uint4 *>(vp + off) = make_uint4(pv[s2][0], pv[s2][1], pv[s2][2], pv[s2][3]);
+    }
   }
 }
 
@@ -1050,7 +1043,7 @@ cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t 
   const OzBuffers &oz = ws.oz;
   if (oz.zs == nullptr || oz.wp == nullptr || n > oz.slice_rows) return cudaErrorInvalidValue;
   const int R = (n + OZ_BM - 1) / OZ_BM;
-  k_oz_lr_prep<<<R, OZ_BM * 8, 0, s>>>(V, ldv, theta, n, p, oz.xdiag, (__nv_bfloat16 *)oz.wp,
+  k_oz_lr_prep<<<R, OZ_BM, 0, s>>>(V, ldv, theta, n, p, oz.xdiag, (__nv_bfloat16 *)oz.wp,
                                    (__nv_bfloat16 *)oz.vp, oz.slice_rows, oz.ew, oz.ev,
                                    oz.mchunk);
   PF_LAUNCHED();
