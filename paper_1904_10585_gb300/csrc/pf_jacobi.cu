@@ -7,15 +7,20 @@
 //   * each CTA keeps a full replica of H (double-buffered in shared memory)
 //     and computes all p/2 rotation angles of the round redundantly (the
 //     replicas are bitwise identical, so every CTA takes the same branches);
+//     the one-CTA variant (p <= 32) updates a single copy of H in place: the
+//     p/2 disjoint pairs split H into 2 x 2 blocks that are read and written
+//     by one thread each, and blocks whose two pairs do not rotate are skipped;
 //   * CTA c computes the new rows of H' = J^T H J for its share of the
 //     rotation pairs (2 x 2 blocks J_i^T H_ij J_j) and stores them into the
 //     next buffer of every CTA of the cluster (distributed shared memory);
 //     the one-CTA variant (p <= 32) computes the upper block triangle only
 //     and mirrors it;
 //   * CTA c owns a slice of rows of the eigenvector matrix and applies all
-//     rotations to it locally;
+//     rotations to it locally; the rotations of round r are applied to it
+//     while the angles of round r + 1 are formed (two rotation sets in
+//     shared memory), which keeps the FP64 pipe busy during the angle chain;
 //   * one cluster barrier per round orders the exchange.
-// The sweep loop stops when off(H) <= 1e-15 ||H||_F (or after 40 sweeps);
+// The sweep loop stops when off(H) <= kOffStop ||H||_F (or after 40 sweeps);
 // eigenvalues are sorted descending (ties by index).
 #include <cooperative_groups.h>
 
@@ -69,6 +74,9 @@ __device__ __forceinline__ void rotation(double hkk, double hll, double hkl, dou
   s = t * y;
 }
 
+// Convergence: off(H)^2 <= kOffStop^2 ||H||_F^2 at the start of a sweep.
+constexpr double kOffStop2 = 1e-30;
+
 constexpr int JC = 8;      // CTAs per cluster (p > 32)
 constexpr int JNT = 256;   // threads per CTA of the cluster version
 constexpr int JNB = 256;   // threads of the one-CTA version
@@ -90,12 +98,15 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     if constexpr (NC > 1) cluster.sync();
     else __syncthreads();
   };
+  constexpr int NHB = NC > 1 ? 2 : 1;  // copies of H (one CTA: in place)
   extern __shared__ double dyn[];
-  double *Hb[2] = {dyn, dyn + kMaxP * JLD};
-  double *Vloc = dyn + 2 * kMaxP * JLD;  // JROWS x JLD
-  __shared__ double cs[kMaxP / 2], sn[kMaxP / 2];
-  __shared__ int pk[kMaxP / 2], pl[kMaxP / 2];
-  __shared__ int act[kMaxP / 2];  // the pair rotates (an integer test, off the FP64 pipe)
+  double *Hb[2] = {dyn, dyn + (NHB - 1) * kMaxP * JLD};
+  double *Vloc = dyn + NHB * kMaxP * JLD;  // JROWS x JLD
+  // two rotation sets: the current round's and the previous round's, whose
+  // eigenvector update runs during the current round's angle phase
+  __shared__ double cs[2][kMaxP / 2], sn[2][kMaxP / 2];
+  __shared__ int pk[2][kMaxP / 2], pl[2][kMaxP / 2];
+  __shared__ int act[2][kMaxP / 2];  // the pair rotates (an integer test, off the FP64 pipe)
   __shared__ double redsh[32];
   __shared__ double lam_s[kMaxP];
   // one CTA: the blocks (i, j >= i) of the upper block triangle, in order
@@ -129,8 +140,22 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     Vloc[r * JLD + b] = (row0 + r == b) ? 1.0 : 0.0;
   }
   sync_all();  // every CTA has started before any remote store
+  // local eigenvector rows: V <- V J for rotation set b
+  auto rotate_v = [&](int b) {
+    for (int idx = tid; idx < (row1 - row0) * half; idx += NTH) {
+      const int r = idx / half, i = idx % half;
+      if (!act[b][i]) continue;
+      const int k = pk[b][i], l = pl[b][i];
+      double *vr = Vloc + r * JLD;
+      const double vk = vr[k], vl = vr[l];
+      vr[k] = cs[b][i] * vk - sn[b][i] * vl;
+      vr[l] = sn[b][i] * vk + cs[b][i] * vl;
+    }
+  };
   int cur = 0;
   int sweeps_done = 0;
+  int set = 0;           // rotation set of the current round
+  bool pending = false;  // the other set still has to be applied to V
   for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
     const double *H = Hb[cur];
     double off = 0.0, tot = 0.0;
@@ -142,10 +167,11 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     }
     off = block_reduce(off, redsh, 0);
     tot = block_reduce(tot, redsh, 0);
-    if (!(off > 1e-30 * tot)) break;  // identical decision in every CTA
+    if (!(off > kOffStop2 * tot)) break;  // identical decision in every CTA
     for (int round = 0; round < m - 1; ++round) {
       H = Hb[cur];
       double *Hn = Hb[cur ^ 1];
+      const int b = set;
       if (tid < half) {
         const int i = tid;
         auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (m - 1)); };
@@ -153,30 +179,23 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
         if (k > l) { const int tt = k; k = l; l = tt; }
         double c = 1.0, s = 0.0;
         if (l < p) rotation(H[k * JLD + k], H[l * JLD + l], H[k * JLD + l], c, s);
-        cs[i] = c; sn[i] = s; pk[i] = k; pl[i] = l;
-        act[i] = (l < p && s != 0.0) ? 1 : 0;
+        cs[b][i] = c; sn[b][i] = s; pk[b][i] = k; pl[b][i] = l;
+        act[b][i] = (l < p && s != 0.0) ? 1 : 0;
       }
+      if (pending) rotate_v(b ^ 1);
       __syncthreads();
-      // local eigenvector rows: V <- V J
-      for (int idx = tid; idx < (row1 - row0) * half; idx += NTH) {
-        const int r = idx / half, i = idx % half;
-        if (!act[i]) continue;
-        const int k = pk[i], l = pl[i];
-        double *vr = Vloc + r * JLD;
-        const double vk = vr[k], vl = vr[l];
-        vr[k] = cs[i] * vk - sn[i] * vl;
-        vr[l] = sn[i] * vk + cs[i] * vl;
-      }
       // new blocks of H: block (i, j) = J_i^T H_ij J_j.  One CTA computes the
-      // upper block triangle and mirrors it (H stays exactly symmetric; a
-      // third less FP64 work per round); the cluster's CTAs compute the block
-      // rows of their pairs, so that their broadcasts stay row-contiguous
+      // upper block triangle in place and mirrors it (H stays exactly
+      // symmetric; a third less FP64 work per round); the cluster's CTAs
+      // compute the block rows of their pairs, so that their broadcasts stay
+      // row-contiguous
       const int nb = NC == 1 ? half * (half + 1) / 2 : (pair1 - pair0) * half;
       for (int idx = tid; idx < nb; idx += NTH) {
         const int i = NC == 1 ? (int)tri_i[idx] : pair0 + idx / half;
         const int j = NC == 1 ? (int)tri_j[idx] : idx % half;
-        const int ki = pk[i], li = pl[i], kj = pk[j], lj = pl[j];
-        const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+        if (NC == 1 && !act[b][i] && !act[b][j]) continue;  // identity block, kept in place
+        const int ki = pk[b][i], li = pl[b][i], kj = pk[b][j], lj = pl[b][j];
+        const double ci = cs[b][i], si = sn[b][i], cj = cs[b][j], sj = sn[b][j];
         const bool ri = li < p, rj = lj < p;  // false: the partner is the dummy
         const double a = H[ki * JLD + kj];
         const double b = rj ? H[ki * JLD + lj] : 0.0;
@@ -204,9 +223,15 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
         }
       }
       sync_all();
-      cur ^= 1;
+      if (NHB > 1) cur ^= 1;
+      set ^= 1;
+      pending = true;
     }
     sweeps_done = sweep + 1;
+  }
+  if (pending) {
+    rotate_v(set ^ 1);
+    __syncthreads();
   }
   // eigenvalues, descending (ties by index); every CTA computes the ranks
   const double *H = Hb[cur];
@@ -242,7 +267,8 @@ __global__ void __launch_bounds__(JNB)
 }
 
 constexpr size_t jacobi_bytes(int nc) {
-  return (size_t)(2 * kMaxP * JLD + ((kMaxP + nc - 1) / nc) * JLD) * sizeof(double);
+  return (size_t)((nc > 1 ? 2 : 1) * kMaxP * JLD + ((kMaxP + nc - 1) / nc) * JLD) *
+         sizeof(double);
 }
 
 }  // namespace
