@@ -97,9 +97,9 @@ __device__ __forceinline__ int oz_exponent(unsigned f) {
   return f == 0x7FFu ? kOzExpBad : (int)(f > 1u ? f : 1u) - 1022;
 }
 
-// Balanced base-256 digits of round(x 2^(OZ_FRAC - e)) for |x| < 2^e:
-// x ~ 2^(e - 7) sum_s d[s] 2^(-8s).  Integer arithmetic only.
-__device__ __forceinline__ void oz_digits(double x, int e, int *d) {
+// round(x 2^(OZ_FRAC - e)) for |x| < 2^e (|result| <= 2^55).  Integer
+// arithmetic only.
+__device__ __forceinline__ long long oz_fixed(double x, int e) {
   const long long bits = __double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   long long m = bits & 0xFFFFFFFFFFFFFll;
@@ -110,25 +110,37 @@ __device__ __forceinline__ void oz_digits(double x, int e, int *d) {
   if (sh >= 0) v = m << sh;
   else if (sh > -60) v = (m + (1ll << (-sh - 1))) >> (-sh);
   else v = 0;
-  if (bits < 0) v = -v;
-#pragma unroll
-  for (int s = kOzSlices - 1; s > 0; --s) {
-    const int dd = ((int)(v & 0xFF) ^ 0x80) - 0x80;  // low byte as a value in [-128, 127]
-    d[s] = dd;
-    v = (v - dd) >> 8;
-  }
-  d[0] = (int)v;
+  return bits < 0 ? -v : v;
 }
 
-// bf16 pattern of a digit (|d| <= 255: at most 8 significant bits, exact).
-// d + 1.5 2^23 is exact in fp32 for |d| < 2^22, so subtracting the constant
-// again leaves d; its bf16 pattern is the top half of the float's.  Integer
-// and FMA-pipe operations instead of two conversions.
-__device__ __forceinline__ uint32_t oz_bf16_bits(int d) {
-  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+// The 7 balanced base-256 digits of v (|v| <= 2^55), v = sum_s d[s] 256^(6-s)
+// with d[1..6] in [-128, 127] and d[0] in [-128, 128], as the fp32 bit
+// patterns of the digits; each is exact in bf16 (at most 8 significant bits),
+// so its high half is the digit's bf16 pattern and its low half is zero.
+// Adding 128 (1 + 256 + ... + 256^6) makes the digits, plus 128, the bytes
+// of u (the top one, up to 256, is u >> 48): no carry runs from one digit to
+// the next.  A byte permute drops byte k into the mantissa of 1.5 2^23, and
+// one exact fp32 subtraction of 1.5 2^23 + 128 leaves the digit.
+__device__ __forceinline__ void oz_digit_bits(long long v, uint32_t *f) {
+  const unsigned long long u = (unsigned long long)v + 0x0080808080808080ull;
+  const uint32_t lo = (uint32_t)u, hi = (uint32_t)(u >> 32);
+  constexpr uint32_t kM = 0x4B400000u;  // 1.5 2^23
+  constexpr float kB = 12583040.0f;     // 1.5 2^23 + 128
+  f[6] = __float_as_uint(__uint_as_float(__byte_perm(lo, kM, 0x7650)) - kB);
+  f[5] = __float_as_uint(__uint_as_float(__byte_perm(lo, kM, 0x7651)) - kB);
+  f[4] = __float_as_uint(__uint_as_float(__byte_perm(lo, kM, 0x7652)) - kB);
+  f[3] = __float_as_uint(__uint_as_float(__byte_perm(lo, kM, 0x7653)) - kB);
+  f[2] = __float_as_uint(__uint_as_float(__byte_perm(hi, kM, 0x7650)) - kB);
+  f[1] = __float_as_uint(__uint_as_float(__byte_perm(hi, kM, 0x7651)) - kB);
+  f[0] = __float_as_uint(__uint_as_float(kM + (hi >> 16)) - kB);
 }
-__device__ __forceinline__ __nv_bfloat16 oz_bf16(int d) {
-  return __ushort_as_bfloat16((unsigned short)oz_bf16_bits(d));
+
+// Two digit patterns of oz_digit_bits as one word of bf16: lo in the low half
+__device__ __forceinline__ uint32_t oz_pack2(uint32_t lo, uint32_t hi) {
+  return __byte_perm(lo, hi, 0x7632);
+}
+__device__ __forceinline__ __nv_bfloat16 oz_bf16_of(uint32_t f) {
+  return __ushort_as_bfloat16((unsigned short)(f >> 16));
 }
 
 // round(v / 2^s) for s >= 0
@@ -198,15 +210,10 @@ __global__ void __launch_bounds__(256) k_oz_zslice(const double *__restrict__ A,
     for (int q = 0; q < 4; ++q) {
       const int k = c0 + 32 * q + lane;
       if (k >= n) continue;
-      int d[kOzSlices];
-      if (e != kOzExpBad) {
-        oz_digits(v[q], e, d);
-      } else {
+      uint32_t d[kOzSlices];
+      oz_digit_bits(e != kOzExpBad ? oz_fixed(v[q], e) : 0ll, d);
 #pragma unroll
-        for (int s = 0; s < kOzSlices; ++s) d[s] = 0;
-      }
-#pragma unroll
-      for (int s = 0; s < kOzSlices; ++s) zs[oz_zs_index(s, row, k, rb_n, kt_n)] = oz_bf16(d[s]);
+      for (int s = 0; s < kOzSlices; ++s) zs[oz_zs_index(s, row, k, rb_n, kt_n)] = oz_bf16_of(d[s]);
     }
   }
 }
@@ -236,16 +243,12 @@ __global__ void __launch_bounds__(128) k_oz_xslice(const double *__restrict__ X,
     const unsigned m = max(max(qmax[0][j], qmax[1][j]), max(qmax[2][j], qmax[3][j]));
     const int e = oz_exponent(m);
     if (t == 0) ex[blockIdx.x * kMaxP + j] = e;
-    int d[kOzSlices];
-    if (in && j < p && e != kOzExpBad) {
-      oz_digits(xr[j], e, d);
-    } else {
-#pragma unroll
-      for (int s = 0; s < kOzSlices; ++s) d[s] = 0;
-    }
+    uint32_t d[kOzSlices];
+    oz_digit_bits((in && j < p && e != kOzExpBad) ? oz_fixed(xr[j], e) : 0ll, d);
     if (in) {
 #pragma unroll
-      for (int s = 0; s < kOzSlices; ++s) xs[(int64_t)(s * NB + j) * ldk + row] = oz_bf16(d[s]);
+      for (int s = 0; s < kOzSlices; ++s)
+        xs[(int64_t)(s * NB + j) * ldk + row] = oz_bf16_of(d[s]);
     }
   }
 }
@@ -568,26 +571,18 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
       const int l = l0 + h;
-      int dw[kOzSlices], dv[kOzSlices];
+      uint32_t dw[kOzSlices], dv[kOzSlices];
       const bool on = l < p && th[l] > 0.0;
-      if (on && e_w != kOzExpBad) oz_digits(vr[l] * th[l], e_w, dw);
-      else
-#pragma unroll
-        for (int s2 = 0; s2 < kOzSlices; ++s2) dw[s2] = 0;
-      if (on && e_v != kOzExpBad) oz_digits(vr[l], e_v, dv);
-      else
-#pragma unroll
-        for (int s2 = 0; s2 < kOzSlices; ++s2) dv[s2] = 0;
+      oz_digit_bits((on && e_w != kOzExpBad) ? oz_fixed(vr[l] * th[l], e_w) : 0ll, dw);
+      oz_digit_bits((on && e_v != kOzExpBad) ? oz_fixed(vr[l], e_v) : 0ll, dv);
 #pragma unroll
       for (int s2 = 0; s2 < kOzSlices; ++s2) {
-        const uint32_t bw = oz_bf16_bits(dw[s2]);
-        const uint32_t bv = oz_bf16_bits(dv[s2]);
         if (h & 1) {
-          pw[s2][h >> 1] |= bw << 16;
-          pv[s2][h >> 1] |= bv << 16;
+          pw[s2][h >> 1] = oz_pack2(pw[s2][h >> 1], dw[s2]);
+          pv[s2][h >> 1] = oz_pack2(pv[s2][h >> 1], dv[s2]);
         } else {
-          pw[s2][h >> 1] = bw;
-          pv[s2][h >> 1] = bv;
+          pw[s2][h >> 1] = dw[s2];
+          pv[s2][h >> 1] = dv[s2];
         }
       }
     }
@@ -769,6 +764,7 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
       int e = e_lo;
+      int ncol = e < e_hi ? colind[e] : INT_MAX;  // column of the next entry of C
 #pragma unroll
       for (int g = 0; g < XP_CW; g += XP_G) {
         // the group's old Z and V exponents: independent loads, in flight
@@ -802,33 +798,31 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
             if (sh >= 0) v += (long long)li << sh;
             else v += (long long)((li + (1 << (-sh - 1))) >> (-sh));
           }
-          int d[KS];
-#pragma unroll
-          for (int s2 = 0; s2 < KS; ++s2) d[s2] = 0;
+          long long zf = 0;  // round(Z_ij 2^(OZ_FRAC - e)) for the planes
           if (in && col < n) {
             const int evc = evv[i];
             double xt = (ewr == kOzExpBad || evc == kOzExpBad)
                             ? __longlong_as_double(0x7FF8000000000000ll)
                             : oz_scale(v, ewr + evc - 14 - OZ_FOLD);
             double z = xt;
-            if (e < e_hi && colind[e] == col) {
+            if (ncol == col) {
               const double cij = cvals[e];
               z = fma(-tt, cij, z);
               cx = fma(cij, xt, cx);
               ++e;
+              ncol = e < e_hi ? colind[e] : INT_MAX;
             }
             if (col == row) z -= lam_r;
             const double dz = zo[i] - z;
             dsum = fma(dz, dz, dsum);
             Z[(int64_t)row * ldz + col] = z;
-            if (ez_rc != kOzExpBad) oz_digits(z, ez_rc, d);
+            if (ez_rc != kOzExpBad) zf = oz_fixed(z, ez_rc);
           }
+          uint32_t d[KS];
+          oz_digit_bits(zf, d);
 #pragma unroll
-          for (int s2 = 0; s2 < KS; ++s2) {
-            const uint32_t b = oz_bf16_bits(d[s2]);
-            if (i & 1) pk[s2][i >> 1] |= b << 16;
-            else pk[s2][i >> 1] = b;
-          }
+          for (int s2 = 0; s2 < KS; ++s2)
+            pk[s2][i >> 1] = (i & 1) ? oz_pack2(pk[s2][i >> 1], d[s2]) : d[s2];
         }
         if (in) {
 #pragma unroll
@@ -934,17 +928,12 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_finish(
     const int jj = j0 + j;
     const int e = oz_exponent(max(max(qmax[0][j], qmax[1][j]), max(qmax[2][j], qmax[3][j])));
     if (t == 0 && jj < nbt) ex_next[rb * kMaxP + jj] = e;
-    int d[kOzSlices];
-    if (in && jj < p && e != kOzExpBad) {
-      oz_digits(y[j], e, d);
-    } else {
-#pragma unroll
-      for (int s2 = 0; s2 < kOzSlices; ++s2) d[s2] = 0;
-    }
+    uint32_t d[kOzSlices];
+    oz_digit_bits((in && jj < p && e != kOzExpBad) ? oz_fixed(y[j], e) : 0ll, d);
     if (in && jj < nbt) {
 #pragma unroll
       for (int s2 = 0; s2 < kOzSlices; ++s2)
-        xs_next[(int64_t)(s2 * nbt + jj) * ldk + row] = oz_bf16(d[s2]);
+        xs_next[(int64_t)(s2 * nbt + jj) * ldk + row] = oz_bf16_of(d[s2]);
     }
   }
 }
