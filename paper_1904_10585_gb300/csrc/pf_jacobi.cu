@@ -10,6 +10,12 @@
 //     the one-CTA variant (p <= 32) updates a single copy of H in place: the
 //     p/2 disjoint pairs split H into 2 x 2 blocks that are read and written
 //     by one thread each, and blocks whose two pairs do not rotate are skipped;
+//   * on one CTA, the thread that forms the angle of a pair also rotates the
+//     pair's own 2 x 2 diagonal block, so the block phase holds only the
+//     off-diagonal blocks (at p = 32: 120 instead of 136, four warps, one per
+//     SM sub-partition); in the cluster, where every CTA forms all angles, the
+//     diagonal blocks stay in the block phase (a longer angle chain in every
+//     CTA measured slower at p = 64);
 //   * CTA c computes the new rows of H' = J^T H J for its share of the
 //     rotation pairs (2 x 2 blocks J_i^T H_ij J_j) and stores them into the
 //     next buffer of every CTA of the cluster (distributed shared memory);
@@ -17,8 +23,8 @@
 //     and mirrors it;
 //   * CTA c owns a slice of rows of the eigenvector matrix and applies all
 //     rotations to it locally; the rotations of round r are applied to it
-//     while the angles of round r + 1 are formed (two rotation sets in
-//     shared memory), which keeps the FP64 pipe busy during the angle chain;
+//     while warp 0 forms the angles of round r + 1 (two rotation sets in
+//     shared memory; on one CTA by warps 1.. only);
 //   * one cluster barrier per round orders the exchange.
 // The sweep loop stops when off(H) <= kOffStop ||H||_F (or after 40 sweeps);
 // eigenvalues are sorted descending (ties by index).
@@ -109,9 +115,9 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
   __shared__ int act[2][kMaxP / 2];  // the pair rotates (an integer test, off the FP64 pipe)
   __shared__ double redsh[32];
   __shared__ double lam_s[kMaxP];
-  // one CTA: the blocks (i, j >= i) of the upper block triangle, in order
-  __shared__ unsigned char tri_i[NC == 1 ? (kMaxP / 2) * (kMaxP / 2 + 1) / 2 : 1];
-  __shared__ unsigned char tri_j[NC == 1 ? (kMaxP / 2) * (kMaxP / 2 + 1) / 2 : 1];
+  // one CTA: the blocks (i, j > i) of the strict upper block triangle, in order
+  __shared__ unsigned char tri_i[NC == 1 ? (kMaxP / 2) * (kMaxP / 2 - 1) / 2 : 1];
+  __shared__ unsigned char tri_j[NC == 1 ? (kMaxP / 2) * (kMaxP / 2 - 1) / 2 : 1];
   const int tid = threadIdx.x;
   const int m = p + (p & 1);          // players (index p is a dummy when p is odd)
   const int half = m / 2;
@@ -123,7 +129,7 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     if (tid == 0) {
       int k = 0;
       for (int i = 0; i < half; ++i)
-        for (int j = i; j < half; ++j) {
+        for (int j = i + 1; j < half; ++j) {
           tri_i[k] = (unsigned char)i;
           tri_j[k] = (unsigned char)j;
           ++k;
@@ -140,9 +146,10 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     Vloc[r * JLD + b] = (row0 + r == b) ? 1.0 : 0.0;
   }
   sync_all();  // every CTA has started before any remote store
-  // local eigenvector rows: V <- V J for rotation set b
-  auto rotate_v = [&](int b) {
-    for (int idx = tid; idx < (row1 - row0) * half; idx += NTH) {
+  // local eigenvector rows: V <- V J for rotation set b, by threads t0.. of
+  // the CTA
+  auto rotate_v = [&](int b, int t0) {
+    for (int idx = tid - t0; idx < (row1 - row0) * half; idx += NTH - t0) {
       const int r = idx / half, i = idx % half;
       if (!act[b][i]) continue;
       const int k = pk[b][i], l = pl[b][i];
@@ -177,23 +184,48 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
         auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (m - 1)); };
         int k = player(i), l = player(m - 1 - i);
         if (k > l) { const int tt = k; k = l; l = tt; }
+        const bool real = l < p;  // false: the partner is the dummy
+        const double hkk = H[k * JLD + k];
+        const double hkl = real ? H[k * JLD + l] : 0.0, hlk = real ? H[l * JLD + k] : 0.0;
+        const double hll = real ? H[l * JLD + l] : 0.0;
         double c = 1.0, s = 0.0;
-        if (l < p) rotation(H[k * JLD + k], H[l * JLD + l], H[k * JLD + l], c, s);
+        if (real) rotation(hkk, hll, hkl, c, s);
         cs[b][i] = c; sn[b][i] = s; pk[b][i] = k; pl[b][i] = l;
-        act[b][i] = (l < p && s != 0.0) ? 1 : 0;
+        act[b][i] = (real && s != 0.0) ? 1 : 0;
+        // one CTA: the pair's diagonal block J^T B J (symmetrised), skipped
+        // when J = I
+        if (NC == 1 && s != 0.0) {
+          const double m00 = c * hkk - s * hkl, m01 = s * hkk + c * hkl;
+          const double m10 = c * hlk - s * hll, m11 = s * hlk + c * hll;
+          const double h00 = c * m00 - s * m10, h11 = s * m01 + c * m11;
+          const double h01 = 0.5 * ((c * m01 - s * m11) + (s * m00 + c * m10));
+          Hn[k * JLD + k] = h00;
+          if (real) {
+            Hn[k * JLD + l] = h01;
+            Hn[l * JLD + k] = h01;
+            Hn[l * JLD + l] = h11;
+          }
+        }
       }
-      if (pending) rotate_v(b ^ 1);
+      constexpr int VT0 = NC == 1 ? 32 : 0;  // first thread of the V update
+      if (pending && tid >= VT0) rotate_v(b ^ 1, VT0);
       __syncthreads();
-      // new blocks of H: block (i, j) = J_i^T H_ij J_j.  One CTA computes the
-      // upper block triangle in place and mirrors it (H stays exactly
-      // symmetric; a third less FP64 work per round); the cluster's CTAs
-      // compute the block rows of their pairs, so that their broadcasts stay
-      // row-contiguous
-      const int nb = NC == 1 ? half * (half + 1) / 2 : (pair1 - pair0) * half;
+      // blocks (i, j) = J_i^T H_ij J_j.  One CTA computes the strict upper
+      // block triangle in place and mirrors it (H stays exactly symmetric;
+      // less than half the FP64 work of the full square); the cluster's CTAs
+      // compute the block rows of their pairs, diagonal blocks included, so
+      // that their broadcasts stay row-contiguous
+      const int nb = NC == 1 ? half * (half - 1) / 2 : (pair1 - pair0) * half;
       for (int idx = tid; idx < nb; idx += NTH) {
-        const int i = NC == 1 ? (int)tri_i[idx] : pair0 + idx / half;
-        const int j = NC == 1 ? (int)tri_j[idx] : idx % half;
-        if (NC == 1 && !act[b][i] && !act[b][j]) continue;  // identity block, kept in place
+        int i, j;
+        if constexpr (NC == 1) {
+          i = tri_i[idx];
+          j = tri_j[idx];
+          if (!act[b][i] && !act[b][j]) continue;  // identity block, kept in place
+        } else {
+          i = pair0 + idx / half;
+          j = idx % half;
+        }
         const int ki = pk[b][i], li = pl[b][i], kj = pk[b][j], lj = pl[b][j];
         const double ci = cs[b][i], si = sn[b][i], cj = cs[b][j], sj = sn[b][j];
         const bool ri = li < p, rj = lj < p;  // false: the partner is the dummy
@@ -207,14 +239,14 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
         // H' block = J_i^T M
         const double h00 = ci * m00 - si * m10, h11 = si * m01 + ci * m11;
         double h01 = ci * m01 - si * m11, h10 = si * m00 + ci * m10;
-        if (i == j) h01 = h10 = 0.5 * (h01 + h10);  // the rotated pair block stays symmetric
+        if (NC > 1 && i == j) h01 = h10 = 0.5 * (h01 + h10);  // the rotated pair block stays symmetric
         for (int q = 0; q < NC; ++q) {
           double *dst = NC > 1 ? cluster.map_shared_rank(Hn, q) : Hn;
           dst[ki * JLD + kj] = h00;
           if (rj) dst[ki * JLD + lj] = h01;
           if (ri) dst[li * JLD + kj] = h10;
           if (ri && rj) dst[li * JLD + lj] = h11;
-          if (NC == 1 && i != j) {  // the mirrored block (j, i)
+          if (NC == 1) {  // the mirrored block (j, i), j > i
             dst[kj * JLD + ki] = h00;
             if (rj) dst[lj * JLD + ki] = h01;
             if (ri) dst[kj * JLD + li] = h10;
@@ -230,7 +262,7 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     sweeps_done = sweep + 1;
   }
   if (pending) {
-    rotate_v(set ^ 1);
+    rotate_v(set ^ 1, 0);
     __syncthreads();
   }
   // eigenvalues, descending (ties by index); every CTA computes the ranks

@@ -181,6 +181,24 @@ __device__ __forceinline__ void epi_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
+// 32-byte global vector access (p 32-byte aligned): a full sector per lane
+__device__ __forceinline__ void ld_v4_f64(const double *p, double *v) {
+  asm("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];"
+      : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+      : "l"(p)
+      : "memory");
+}
+__device__ __forceinline__ void st_v8_b32(void *p, const uint32_t *a, const uint32_t *b) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a[0]),
+               "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3])
+               : "memory");
+}
+__device__ __forceinline__ void st_v4_f64(double *p, const double *v) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
+               "d"(v[2]), "d"(v[3])
+               : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // A (n x n FP64) -> digit planes of A (bf16, tile-contiguous, oz_zs_index)
 // and exponents ez[i * nzc + c] of each row and 128-column chunk.  One warp
@@ -601,7 +619,7 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
     const double *__restrict__ cvals, const double *__restrict__ lam,
     const double *__restrict__ xdiag, const double *__restrict__ mchunk,
     const int *__restrict__ ew, const int *__restrict__ ev, double *__restrict__ Z, int64_t ldz,
-    __nv_bfloat16 *__restrict__ zs, int rb_n, int kt_n, int *__restrict__ ez,
+    int zvec, __nv_bfloat16 *__restrict__ zs, int rb_n, int kt_n, int *__restrict__ ez,
     int nzc, const Params *__restrict__ prm, Params *__restrict__ prm_flags,
     double *__restrict__ red) {
   constexpr int KS = kOzSlices;
@@ -765,42 +783,66 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
       int e = e_lo;
       int ncol = e < e_hi ? colind[e] : INT_MAX;  // column of the next entry of C
+      static_assert(XP_G == 8 && XP_CW == 2 * XP_G, "two 8-column groups per thread");
+      static_assert(OZ_FOLD == 36 && KS == 7, "the fold below is written out for 7 levels");
+      // the first group's plane words, stored with the second group's: 32
+      // bytes (a full sector) of each plane row per store
+      uint32_t pk0[KS][XP_G / 2];
 #pragma unroll
       for (int g = 0; g < XP_CW; g += XP_G) {
-        // the group's old Z and V exponents: independent loads, in flight
-        // while TMEM is read and the levels are folded
+        // the group's old Z: independent loads, in flight while TMEM is read
+        // and the levels are folded.  Whole groups of an aligned Z move as
+        // two 32-byte vectors (a full sector per access: each lane of the
+        // warp holds another row)
         double zo[XP_G];
-        int evv[XP_G];
-        const double *zrow = Z + (int64_t)(in ? row : 0) * ldz;
-#pragma unroll
-        for (int i = 0; i < XP_G; ++i) {
-          const int col = j0 + g + i;
-          const bool ok2 = in && col < n;
-          zo[i] = ok2 ? zrow[col] : 0.0;
-          evv[i] = ok2 ? ev[col] : 0;
+        double *zrow = Z + (int64_t)(in ? row : 0) * ldz;
+        const bool vec = zvec && j0 + g + XP_G <= n;  // the same for the whole warp
+        if (vec && in) {
+          ld_v4_f64(zrow + j0 + g, zo);
+          ld_v4_f64(zrow + j0 + g + 4, zo + 4);
         }
-        uint32_t L[KS][XP_G];
+        if (!vec) {
 #pragma unroll
-        for (int l = 0; l < KS; ++l) {
-          if constexpr (XP_G == 8) tmem_ld8(taddr + l * XP_TN + g, L[l]);
-          else tmem_ld4(taddr + l * XP_TN + g, L[l]);
+          for (int i = 0; i < XP_G; ++i) {
+            const int col = j0 + g + i;
+            zo[i] = (in && col < n) ? zrow[col] : 0.0;
+          }
         }
-        tmem_wait_ld();
+        // v = sum_l L_l 2^(36 - 8l), levels 5 and 6 rounded together, folded
+        // in pairs of levels as they leave TMEM.  With K <= 64,
+        // |L_l| <= (l + 1) 2^20, so L_0 2^8 + L_1, L_2 2^8 + L_3 and
+        // L_5 2^8 + L_6 stay inside int32
+        int hi[XP_G], mid[XP_G], lo[XP_G];
+        {
+          uint32_t A[XP_G], B[XP_G], C[XP_G];
+          auto f2i = [](uint32_t u) { return __float2int_rn(__uint_as_float(u)); };
+          tmem_ld8(taddr + 0 * XP_TN + g, A);
+          tmem_ld8(taddr + 1 * XP_TN + g, B);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < XP_G; ++i) hi[i] = f2i(A[i]) * 256 + f2i(B[i]);
+          tmem_ld8(taddr + 2 * XP_TN + g, A);
+          tmem_ld8(taddr + 3 * XP_TN + g, B);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < XP_G; ++i) mid[i] = f2i(A[i]) * 256 + f2i(B[i]);
+          tmem_ld8(taddr + 4 * XP_TN + g, A);
+          tmem_ld8(taddr + 5 * XP_TN + g, B);
+          tmem_ld8(taddr + 6 * XP_TN + g, C);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < XP_G; ++i)
+            lo[i] = f2i(A[i]) * 16 + ((f2i(B[i]) * 256 + f2i(C[i]) + 2048) >> 12);
+        }
         uint32_t pk[KS][XP_G / 2];
 #pragma unroll
         for (int i = 0; i < XP_G; ++i) {
           const int col = j0 + g + i;
-          long long v = 0;
-#pragma unroll
-          for (int l = 0; l < KS; ++l) {
-            const int li = __float2int_rn(__uint_as_float(L[l][i]));
-            const int sh = OZ_FOLD - 8 * l;
-            if (sh >= 0) v += (long long)li << sh;
-            else v += (long long)((li + (1 << (-sh - 1))) >> (-sh));
-          }
+          const long long v = (long long)lo[i] + (long long)mid[i] * 4096 +
+                              (long long)hi[i] * 268435456;
           long long zf = 0;  // round(Z_ij 2^(OZ_FRAC - e)) for the planes
           if (in && col < n) {
-            const int evc = evv[i];
+            const int evc = ev[col];
             double xt = (ewr == kOzExpBad || evc == kOzExpBad)
                             ? __longlong_as_double(0x7FF8000000000000ll)
                             : oz_scale(v, ewr + evc - 14 - OZ_FOLD);
@@ -815,7 +857,8 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
             if (col == row) z -= lam_r;
             const double dz = zo[i] - z;
             dsum = fma(dz, dz, dsum);
-            Z[(int64_t)row * ldz + col] = z;
+            zo[i] = z;  // the new value, stored with the group
+            if (!vec) zrow[col] = z;
             if (ez_rc != kOzExpBad) zf = oz_fixed(z, ez_rc);
           }
           uint32_t d[KS];
@@ -824,16 +867,21 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
           for (int s2 = 0; s2 < KS; ++s2)
             pk[s2][i >> 1] = (i & 1) ? oz_pack2(pk[s2][i >> 1], d[s2]) : d[s2];
         }
-        if (in) {
+        if (vec && in) {
+          st_v4_f64(zrow + j0 + g, zo);
+          st_v4_f64(zrow + j0 + g + 4, zo + 4);
+        }
+        if (g == 0) {
 #pragma unroll
-          for (int s2 = 0; s2 < KS; ++s2) {
-            __nv_bfloat16 *dst = zs + oz_zs_index(s2, row, j0 + g, rb_n, kt_n);
-            if constexpr (XP_G == 8)
-              *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2],
-                                                           pk[s2][3]);
-            else
-              *reinterpret_cast<uint2 *>(dst) = make_uint2(pk[s2][0], pk[s2][1]);
-          }
+          for (int s2 = 0; s2 < KS; ++s2)
+#pragma unroll
+            for (int w2 = 0; w2 < XP_G / 2; ++w2) pk0[s2][w2] = pk[s2][w2];
+        } else if (in) {
+          // columns j0 .. j0 + 15 of each plane row: 32 bytes at a 32-byte
+          // boundary (j0 is a multiple of 16, plane rows are 128 bytes)
+#pragma unroll
+          for (int s2 = 0; s2 < KS; ++s2)
+            st_v8_b32(zs + oz_zs_index(s2, row, j0, rb_n, kt_n), pk0[s2], pk[s2]);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1047,9 +1095,11 @@ cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t 
     return e;
   const int64_t T = (int64_t)R * ((n + XP_TN - 1) / XP_TN);
   const int grid = (int)(T < ws.num_sms ? T : ws.num_sms);
+  // 32-byte vector access to Z: 32-byte aligned rows
+  const int zvec = ((reinterpret_cast<uintptr_t>(Z) & 31) == 0 && (ldz & 3) == 0) ? 1 : 0;
   k_oz_expand<<<grid, XP_THREADS, XP_SMEM, s>>>(
       mw, mv, n, (int)oz.slice_rows, rowptr, colind, vals, lam, oz.xdiag, oz.mchunk, oz.ew,
-      oz.ev, Z, ldz, (__nv_bfloat16 *)oz.zs, (int)(oz.slice_rows / OZ_BM),
+      oz.ev, Z, ldz, zvec, (__nv_bfloat16 *)oz.zs, (int)(oz.slice_rows / OZ_BM),
       (int)(oz.ldk / OZ_BK), oz.ez, (int)(oz.slice_rows / OZ_BM), ws.prm, ws.prm, red);
   PF_LAUNCHED();
   *nblocks = grid;
