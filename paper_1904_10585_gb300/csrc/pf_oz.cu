@@ -500,13 +500,21 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
     // the partials (summed with the recurrence by k_oz_finish)
     if (in) {
       double *pr = part + ((int64_t)split * n + row) * p;
+      double y[CW];
 #pragma unroll
       for (int j = 0; j < CW; ++j) {
         const int e2 = exmax[col0 + j];
-        const double y = (ea == kOzExpBad || e2 == kOzExpBad)
-                             ? __longlong_as_double(0x7FF8000000000000ll)
-                             : oz_scale(acc[j], ea + e2 - 14 - OZ_FOLD);
-        if (gc0 + j < p) pr[gc0 + j] = y;
+        y[j] = (ea == kOzExpBad || e2 == kOzExpBad)
+                   ? __longlong_as_double(0x7FF8000000000000ll)
+                   : oz_scale(acc[j], ea + e2 - 14 - OZ_FOLD);
+      }
+      if ((p & 3) == 0 && gc0 + CW <= p) {  // 32-byte aligned: whole sectors
+#pragma unroll
+        for (int j = 0; j < CW; j += 4) st_v4_f64(pr + gc0 + j, y + j);
+      } else {
+#pragma unroll
+        for (int j = 0; j < CW; ++j)
+          if (gc0 + j < p) pr[gc0 + j] = y[j];
       }
     }
   }
@@ -584,31 +592,26 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
   const int e_w = oz_exponent(fw), e_v = oz_exponent(fv);
   ew[row] = e_w;
   ev[row] = e_v;
-  for (int l0 = 0; l0 < 64; l0 += 8) {
-    uint32_t pw[kOzSlices][4], pv[kOzSlices][4];
+  // digit planes of the rows of W (q = 0) and V (q = 1), 16 columns at a
+  // time: 32 bytes (a full sector) of each plane row per store
+  for (int q = 0; q < 2; ++q) {
+    const int e_q = q == 0 ? e_w : e_v;
+    __nv_bfloat16 *dst = q == 0 ? wp : vp;
+    for (int l0 = 0; l0 < 64; l0 += 16) {
+      uint32_t pk[kOzSlices][8];
 #pragma unroll
-    for (int h = 0; h < 8; ++h) {
-      const int l = l0 + h;
-      uint32_t dw[kOzSlices], dv[kOzSlices];
-      const bool on = l < p && th[l] > 0.0;
-      oz_digit_bits((on && e_w != kOzExpBad) ? oz_fixed(vr[l] * th[l], e_w) : 0ll, dw);
-      oz_digit_bits((on && e_v != kOzExpBad) ? oz_fixed(vr[l], e_v) : 0ll, dv);
+      for (int h = 0; h < 16; ++h) {
+        const int l = l0 + h;
+        const bool on = l < p && th[l] > 0.0 && e_q != kOzExpBad;
+        uint32_t d[kOzSlices];
+        oz_digit_bits(on ? oz_fixed(q == 0 ? vr[l] * th[l] : vr[l], e_q) : 0ll, d);
 #pragma unroll
-      for (int s2 = 0; s2 < kOzSlices; ++s2) {
-        if (h & 1) {
-          pw[s2][h >> 1] = oz_pack2(pw[s2][h >> 1], dw[s2]);
-          pv[s2][h >> 1] = oz_pack2(pv[s2][h >> 1], dv[s2]);
-        } else {
-          pw[s2][h >> 1] = dw[s2];
-          pv[s2][h >> 1] = dv[s2];
-        }
+        for (int s2 = 0; s2 < kOzSlices; ++s2)
+          pk[s2][h >> 1] = (h & 1) ? oz_pack2(pk[s2][h >> 1], d[s2]) : d[s2];
       }
-    }
 #pragma unroll
-    for (int s2 = 0; s2 < kOzSlices; ++s2) {
-      const int64_t off = ((int64_t)s2 * plane_rows + row) * 64 + l0;
-      *reinterpret_cast<uint4 *>(wp + off) = make_uint4(pw[s2][0], pw[s2][1], pw[s2][2], pw[s2][3]);
-      *reinterpret_cast<uint4 *>(vp + off) = make_uint4(pv[s2][0], pv[s2][1], pv[s2][2], pv[s2][3]);
+      for (int s2 = 0; s2 < kOzSlices; ++s2)
+        st_v8_b32(dst + ((int64_t)s2 * plane_rows + row) * 64 + l0, pk[s2], pk[s2] + 4);
     }
   }
 }
@@ -929,7 +932,7 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_finish(
     const double *__restrict__ part, int nsplit, int n, int p, const double *X, int64_t ldx,
     const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn,
     __nv_bfloat16 *__restrict__ xs_next, int *__restrict__ ex_next, int64_t ldk, int nbt,
-    const Params *__restrict__ prm, int mode) {
+    const Params *__restrict__ prm, int mode, int vmask) {
   __shared__ unsigned qmax[4][8];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int rb = blockIdx.x, j0 = blockIdx.y * 8;
@@ -943,24 +946,59 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_finish(
   double y[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) y[j] = 0.0;
+  // a whole group of 8 columns moves as two 32-byte vectors per row where
+  // the array allows it (vmask bits: partials, X, Y_prev, Y_next)
+  const bool full = j0 + 8 <= p;
   if (in) {
     for (int sp = 0; sp < nsplit; ++sp) {
       const double *pr = part + ((int64_t)sp * n + row) * p + j0;
+      if (full && (vmask & 1)) {
+        double a[8];
+        ld_v4_f64(pr, a);
+        ld_v4_f64(pr + 4, a + 4);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) y[j] += a[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j0 + j < p) y[j] += __ldcg(pr + j);
+      }
+    }
+    if (mode != MODE_PLAIN) {
+      double xv[8], yp[8];
+      const double *xr = X + (int64_t)row * ldx + j0;
+      const double *pr = Yprev + (int64_t)row * ldp + j0;
+      if (full && (vmask & 2)) {
+        ld_v4_f64(xr, xv);
+        ld_v4_f64(xr + 4, xv + 4);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xv[j] = j0 + j < p ? xr[j] : 0.0;
+      }
+      if (mode == MODE_RECUR) {
+        if (full && (vmask & 4)) {
+          ld_v4_f64(pr, yp);
+          ld_v4_f64(pr + 4, yp + 4);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) yp[j] = j0 + j < p ? pr[j] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        double v = alpha * (y[j] - cval * xv[j]);
+        if (mode == MODE_RECUR) v -= yp[j];
+        y[j] = v;
+      }
+    }
+    double *yn = Ynext + (int64_t)row * ldn + j0;
+    if (full && (vmask & 8)) {
+      st_v4_f64(yn, y);
+      st_v4_f64(yn + 4, y + 4);
+    } else {
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        if (j0 + j < p) y[j] += __ldcg(pr + j);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int jj = j0 + j;
-      if (jj >= p) continue;
-      double v = y[j];
-      if (mode != MODE_PLAIN) {
-        v = alpha * (v - cval * X[(int64_t)row * ldx + jj]);
-        if (mode == MODE_RECUR) v -= Yprev[(int64_t)row * ldp + jj];
-      }
-      Ynext[(int64_t)row * ldn + jj] = v;
-      y[j] = v;
+        if (j0 + j < p) yn[j] = y[j];
     }
   }
   if (xs_next == nullptr) return;  // uniform over the grid
@@ -1066,9 +1104,14 @@ cudaError_t launch_oz_product(cudaStream_t s, const Workspace &ws, int n, int wh
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   __nv_bfloat16 *xn = next >= 0 ? (__nv_bfloat16 *)ws.oz.xs[next] : nullptr;
   int *exn = next >= 0 ? ws.oz.ex[next] : nullptr;
+  auto vec_ok = [](const double *a, int64_t ld) {
+    return a != nullptr && (reinterpret_cast<uintptr_t>(a) & 31) == 0 && (ld & 3) == 0;
+  };
+  const int vmask = ((p & 3) == 0 ? 1 : 0) | (vec_ok(X, ldx) ? 2 : 0) |
+                    (vec_ok(Yprev, ldp) ? 4 : 0) | (vec_ok(Ynext, ldn) ? 8 : 0);
   k_oz_finish<<<dim3(R, (nbt + 7) / 8), OZ_BM, 0, s>>>(ws.oz.part, S, n, p, X, ldx, Yprev, ldp,
                                                       Ynext, ldn, xn, exn, ws.oz.ldk, nbt,
-                                                      ws.prm, mode);
+                                                      ws.prm, mode, vmask);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
