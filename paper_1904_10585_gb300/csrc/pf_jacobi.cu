@@ -24,7 +24,8 @@
 //   * CTA c owns a slice of rows of the eigenvector matrix and applies all
 //     rotations to it locally; the rotations of round r are applied to it
 //     while warp 0 forms the angles of round r + 1 (two rotation sets in
-//     shared memory; on one CTA by warps 1.. only);
+//     shared memory; on one CTA by the warps that do not share warp 0's SM
+//     sub-partition);
 //   * one cluster barrier per round orders the exchange.
 // The sweep loop stops when off(H) <= kOffStop ||H||_F (or after 40 sweeps);
 // eigenvalues are sorted descending (ties by index).
@@ -146,10 +147,9 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     Vloc[r * JLD + b] = (row0 + r == b) ? 1.0 : 0.0;
   }
   sync_all();  // every CTA has started before any remote store
-  // local eigenvector rows: V <- V J for rotation set b, by threads t0.. of
-  // the CTA
-  auto rotate_v = [&](int b, int t0) {
-    for (int idx = tid - t0; idx < (row1 - row0) * half; idx += NTH - t0) {
+  // local eigenvector rows: V <- V J for rotation set b, item idx0, stride
+  auto rotate_v = [&](int b, int idx0, int stride) {
+    for (int idx = idx0; idx < (row1 - row0) * half; idx += stride) {
       const int r = idx / half, i = idx % half;
       if (!act[b][i]) continue;
       const int k = pk[b][i], l = pl[b][i];
@@ -207,8 +207,17 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
           }
         }
       }
-      constexpr int VT0 = NC == 1 ? 32 : 0;  // first thread of the V update
-      if (pending && tid >= VT0) rotate_v(b ^ 1, VT0);
+      if (pending) {
+        if constexpr (NC == 1) {
+          // warps 1-3 and 5-7: warp 4 shares the FP64 pipe of warp 0's
+          // angle chain and diagonal blocks (warp w runs on SM
+          // sub-partition w mod 4)
+          const int w = tid >> 5;
+          if ((w & 3) != 0) rotate_v(b ^ 1, (w - 1 - (w >> 2)) * 32 + (tid & 31), NTH - 64);
+        } else {
+          rotate_v(b ^ 1, tid, NTH);
+        }
+      }
       __syncthreads();
       // blocks (i, j) = J_i^T H_ij J_j.  One CTA computes the strict upper
       // block triangle in place and mirrors it (H stays exactly symmetric;
@@ -262,7 +271,7 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
     sweeps_done = sweep + 1;
   }
   if (pending) {
-    rotate_v(set ^ 1, 0);
+    rotate_v(set ^ 1, tid, NTH);
     __syncthreads();
   }
   // eigenvalues, descending (ties by index); every CTA computes the ranks

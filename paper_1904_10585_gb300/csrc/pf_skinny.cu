@@ -108,14 +108,40 @@ __global__ void __launch_bounds__(GR_OUT * GR_SUB) k_gram_reduce(double *__restr
 // A[k+1][k+1] first and takes the next pivot (square root and reciprocal)
 // while the other warps finish the update.  The inverse reuses the pivot
 // reciprocals: four lanes per column share each back-substitution sum.
+// 1/x for a positive, finite pivot x by Newton-Raphson, y <- y + y (1 - x y),
+// from a single-precision seed: the top 23 bits of the mantissa of x as a
+// float in [1, 2), its hardware reciprocal (rcp.approx, relative error
+// below 2^-22 with the truncation), and the exponent of x applied by integer
+// arithmetic.  Each step squares the relative error (2^-44, then rounding),
+// so the chain from one Cholesky pivot to the next holds four dependent FP64
+// operations instead of a square root and a division.  Exponents near the
+// ends of the range take the plain division.
+__device__ __forceinline__ double rcp_pivot(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex < 64 || ex > 1982) return 1.0 / x;
+  const float m = __int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF));
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));  // in (0.5, 1]
+  const long long rb = (long long)__float_as_uint(r);
+  const long long de = ((rb >> 23) & 0xFF) - 127 + 1023 - (ex - 1023);
+  double y = __longlong_as_double((de << 52) | ((rb & 0x7FFFFF) << 29));
+  y = fma(y, fma(-x, y, 1.0), y);
+  y = fma(y, fma(-x, y, 1.0), y);
+  return y;
+}
+
 __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpart, int nparts,
                                                  int n, int p, int pass, double *__restrict__ Rinv,
                                                  Params *prm) {
   if (pass == 2 && !(prm->flags & 1)) return;
   extern __shared__ double dyn[];
+  // A: the Gram matrix, reduced in place to the pivots (upper triangle);
+  // U: the strict upper part of the unit upper factor G = U^T D U,
+  // overwritten by that of -U^{-1}
   double(*A)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn);
-  double(*R)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn + kMaxP * (kMaxP + 1));
-  __shared__ double dinv[kMaxP];
+  double(*U)[kMaxP + 1] = reinterpret_cast<double(*)[kMaxP + 1]>(dyn + kMaxP * (kMaxP + 1));
+  __shared__ double dpiv[kMaxP], rpiv[kMaxP];
   __shared__ double diag0[kMaxP];
   __shared__ int fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -131,6 +157,17 @@ __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpar
     }
   }
   __syncthreads();
+  // pivot k: accepted when it is finite and above 1e-13 of the (shifted)
+  // diagonal; its reciprocal then comes from rcp_pivot
+  auto take_pivot = [&](int k, double sh) {
+    const double piv = A[k][k];
+    if (!(piv > 1e-13 * (diag0[k] + sh)) || !isfinite(piv)) {
+      fail = 1;
+    } else {
+      dpiv[k] = piv;
+      rpiv[k] = rcp_pivot(piv);
+    }
+  };
   double sh = 0.0;
   bool ok = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -148,35 +185,24 @@ __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpar
     }
     if (tid == 0) {
       fail = 0;
-      const double piv = A[0][0];
-      if (!(piv > 1e-13 * (diag0[0] + sh)) || !isfinite(piv)) {
-        fail = 1;
-      } else {
-        const double r = rsqrt(piv);  // one long-latency call per pivot
-        R[0][0] = piv * r;
-        dinv[0] = r;
-      }
+      take_pivot(0, sh);
     }
     __syncthreads();
+    // G = U^T D U without square roots: row k of U is row k of the reduced
+    // matrix times 1/d_k, and the trailing triangle loses A_ki A_kj / d_k.
+    // The chain from one pivot to the next is one multiply, one FMA and
+    // rcp_pivot (no square root, no division).  (Spreading the trailing
+    // triangle element by element over all warps measured slower: the step
+    // is bound by that chain and the barrier, not by FP64 throughput.)
     for (int k = 0; k < p && !fail; ++k) {
-      const double iv = dinv[k], iv2 = iv * iv;
-      // row k of R
-      for (int j = k + 1 + tid; j < p; j += NT) R[k][j] = A[k][j] * iv;
+      const double rk = rpiv[k];
+      for (int j = k + 1 + tid; j < p; j += NT) U[k][j] = A[k][j] * rk;
       // trailing upper triangle; row k+1 first on warp 0 so that thread 0
       // can take the next pivot early
       for (int i = k + 1 + warp; i < p; i += NW) {
-        const double aki = A[k][i] * iv2;
+        const double aki = A[k][i] * rk;
         for (int j = i + lane; j < p; j += 32) A[i][j] = fma(-aki, A[k][j], A[i][j]);
-        if (tid == 0 && i == k + 1) {
-          const double piv = A[i][i];
-          if (!(piv > 1e-13 * (diag0[i] + sh)) || !isfinite(piv)) {
-            fail = 1;
-          } else {
-            const double r = rsqrt(piv);
-            R[i][i] = piv * r;
-            dinv[i] = r;
-          }
-        }
+        if (tid == 0 && i == k + 1) take_pivot(i, sh);
       }
       __syncthreads();
     }
@@ -196,29 +222,25 @@ __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpar
     for (int idx = tid; idx < p * p; idx += NT) Rinv[idx] = (idx / p == idx % p) ? 1.0 : 0.0;
     return;
   }
-  // inverse of the upper-triangular R into A: column j on four lanes q, each
-  // summing the k = i+1+q, i+5+q, ... terms; back-substitution from the diagonal
-  {
-    const int q = lane & 3;
-    const int j = warp * 8 + (lane >> 2);  // 8 columns per warp, 64 columns
-    const int jmax = warp * 8 + 7;
-    if (j < p && q == 0) A[j][j] = dinv[j];
-    __syncwarp();
-    for (int i = (jmax < p ? jmax : p - 1) - 1; i >= 0; --i) {
-      double sacc = 0.0;
-      const bool act = j < p && i < j;
-      if (act)
-        for (int k = i + 1 + q; k <= j; k += 4) sacc = fma(R[i][k], A[k][j], sacc);
-      sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
-      sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
-      if (act && q == 0) A[i][j] = -sacc * dinv[i];
-      __syncwarp();
+  // Y = -U^{-1} (strict upper part) in place, right-looking from the last
+  // row: Y_mc = U_mc - sum_{m<j<c} U_mj Y_jc.  At the step for row j, row j
+  // is final and column j still holds U; the step reads column j and row j
+  // and writes only columns c > j of rows m < j, so it needs no barrier
+  // inside
+  for (int j = p - 2; j >= 1; --j) {
+    const int w = p - 1 - j;
+    for (int idx = tid; idx < j * w; idx += NT) {
+      const int m = idx / w, c = j + 1 + idx % w;
+      U[m][c] = fma(-U[m][j], U[j][c], U[m][c]);
     }
+    __syncthreads();
   }
+  // R = D^{1/2} U, so R^{-1} = U^{-1} D^{-1/2}: column b scaled by d_b^{-1/2}
+  if (tid < p) rpiv[tid] = rsqrt(dpiv[tid]);
   __syncthreads();
   for (int idx = tid; idx < p * p; idx += NT) {
     const int a = idx / p, b = idx % p;
-    Rinv[idx] = a <= b ? A[a][b] : 0.0;
+    Rinv[idx] = a < b ? -U[a][b] * rpiv[b] : (a == b ? rpiv[b] : 0.0);
   }
 }
 
@@ -385,7 +407,7 @@ cudaError_t launch_gram(cudaStream_t s, const Workspace &ws, const double *X, in
                         const double *Y, int64_t ldy, int n, int px, int py, int cond_flag,
                         int *nblocks_out, bool sym) {
   int nb, rpb;
-  row_split(n, kMaxGramBlocks, 64, &nb, &rpb);
+  row_split(n, kMaxGramBlocks, RC, &nb, &rpb);  // all SMs: the FP64 rate of one SM is small
   const int pm = px > py ? px : py;
   if (pm <= 16)
     {
