@@ -306,6 +306,29 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 // Deterministic block reduction (fixed tree).  `sh` holds >= 32 doubles.
 // op: 0 sum, 1 min, 2 max.  Result valid in all threads.
+// 1/x for a positive, finite x by Newton-Raphson, y <- y + y (1 - x y),
+// from a single-precision seed: the top 23 bits of the mantissa of x as a
+// float in [1, 2), its hardware reciprocal (rcp.approx, relative error
+// below 2^-22 with the truncation), and the exponent of x applied by integer
+// arithmetic.  Each step squares the relative error (2^-44, then rounding),
+// so the result takes four dependent FP64 operations after the seed (a
+// Cholesky pivot chain, a Jacobi rotation).  Exponents near the ends of
+// the range take the plain division.
+__device__ __forceinline__ double rcp_newton(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex < 64 || ex > 1982) return 1.0 / x;
+  const float m = __int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF));
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));  // in (0.5, 1]
+  const long long rb = (long long)__float_as_uint(r);
+  const long long de = ((rb >> 23) & 0xFF) - 127 + 1023 - (ex - 1023);
+  double y = __longlong_as_double((de << 52) | ((rb & 0x7FFFFF) << 29));
+  y = fma(y, fma(-x, y, 1.0), y);
+  y = fma(y, fma(-x, y, 1.0), y);
+  return y;
+}
+
 __device__ __forceinline__ double block_reduce(double v, double *sh, int op) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   v = op == 0 ? warp_sum(v) : (op == 1 ? warp_min(v) : warp_max(v));

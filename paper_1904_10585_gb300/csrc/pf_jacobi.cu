@@ -10,12 +10,12 @@
 //     the one-CTA variant (p <= 32) updates a single copy of H in place: the
 //     p/2 disjoint pairs split H into 2 x 2 blocks that are read and written
 //     by one thread each, and blocks whose two pairs do not rotate are skipped;
-//   * on one CTA, the thread that forms the angle of a pair also rotates the
-//     pair's own 2 x 2 diagonal block, so the block phase holds only the
-//     off-diagonal blocks (at p = 32: 120 instead of 136, four warps, one per
-//     SM sub-partition); in the cluster, where every CTA forms all angles, the
-//     diagonal blocks stay in the block phase (a longer angle chain in every
-//     CTA measured slower at p = 64);
+//   * on one CTA, the four lanes that form the angle of a pair also rotate
+//     the pair's own 2 x 2 diagonal block (one entry each), so the block
+//     phase holds only the off-diagonal blocks (at p = 32: 120 instead of
+//     136, four warps, one per SM sub-partition); in the cluster, where every
+//     CTA forms all angles, the diagonal blocks stay in the block phase (a
+//     longer angle chain in every CTA measured slower at p = 64);
 //   * CTA c computes the new rows of H' = J^T H J for its share of the
 //     rotation pairs (2 x 2 blocks J_i^T H_ij J_j) and stores them into the
 //     next buffer of every CTA of the cluster (distributed shared memory);
@@ -23,9 +23,8 @@
 //     and mirrors it;
 //   * CTA c owns a slice of rows of the eigenvector matrix and applies all
 //     rotations to it locally; the rotations of round r are applied to it
-//     while warp 0 forms the angles of round r + 1 (two rotation sets in
-//     shared memory; on one CTA by the warps that do not share warp 0's SM
-//     sub-partition);
+//     while the angles of round r + 1 are formed (two rotation sets in
+//     shared memory; on one CTA by warps 2..7);
 //   * one cluster barrier per round orders the exchange.
 // The sweep loop stops when off(H) <= kOffStop ||H||_F (or after 40 sweeps);
 // eigenvalues are sorted descending (ties by index).
@@ -41,15 +40,18 @@ namespace {
 
 // Rotation of the pair (k, l): the tangent t comes from single-precision
 // arithmetic (|t| <= 1, the smaller root of t^2 + 2 tau t - 1 = 0 with
-// tau = (h_ll - h_kk) / (2 h_kl)); c = 1/sqrt(1 + t^2) is then formed in FP64
-// from the exact double t by Newton-Raphson refinement of a single-precision
-// seed (y <- y + (y/2)(1 - q y^2), twice: 24 -> 48 -> full precision), so
-// (c, s = t c) is orthonormal to FP64 rounding.  The rotation annihilates
-// h_kl only to single precision, so the updated 2 x 2 block keeps its
-// computed off-diagonal entries; the sweeps still converge (each rotation
-// shrinks |h_kl| by ~1e-7 on top of the quadratic coupling).  On GB300 the
-// FP64 pipe is 1/64 of FP32, and a timing probe put the FP64 divide/sqrt
-// chain of the exact angle at ~2 of the 5.3 us of each rotation round.
+// tau = (h_ll - h_kk) / (2 h_kl)), and so does u = tan(theta / 2) =
+// t / (1 + sqrt(1 + t^2)).  The rotation is then the rational one,
+// c = (1 - u^2) / (1 + u^2), s = 2u / (1 + u^2), formed in FP64 from the
+// exact single-precision u (u^2 is exact in FP64) with one Newton
+// reciprocal: c^2 + s^2 = 1 to FP64 rounding, and the FP64 chain after the
+// single-precision part is a multiply, an add, the reciprocal's four
+// operations and a multiply (a reciprocal square root by Newton's method
+// needs six).  The rotation annihilates h_kl only to single precision, so
+// the updated 2 x 2 block keeps its computed off-diagonal entries; the
+// sweeps still converge (each rotation shrinks |h_kl| by ~1e-7 on top of the
+// quadratic coupling).  On GB300 the FP64 pipe is 1/64 of FP32, and dependent
+// FP64 operations set the length of every rotation round.
 __device__ __forceinline__ void rotation(double hkk, double hll, double hkl, double &c,
                                          double &s) {
   c = 1.0;
@@ -57,28 +59,26 @@ __device__ __forceinline__ void rotation(double hkk, double hll, double hkl, dou
   if (!(fabs(hkl) > 0.5e-17 * (fabs(hkk) + fabs(hll))) || hkl == 0.0) return;
   const double d = hll - hkk;
   const float h32 = (float)hkl, d32 = (float)d;
-  float t32;
   if (fabsf(h32) >= 1e-30f && isfinite(h32) && isfinite(d32)) {
     const float tau = d32 / (2.0f * h32);
+    float t32;
     if (fabsf(tau) > 1e18f) t32 = 0.5f / tau;
     else t32 = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-  } else {
-    // outside the single-precision range: the exact FP64 angle
-    const double tau = d / (2.0 * hkl);
-    double t;
-    if (fabs(tau) > 1e150) t = 0.5 / tau;
-    else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-    c = 1.0 / sqrt(1.0 + t * t);
-    s = t * c;
+    const float u32 = t32 / (1.0f + sqrtf(fmaf(t32, t32, 1.0f)));  // |u| <= tan(pi/8)
+    const double u = (double)u32;
+    const double u2 = u * u;  // exact
+    const double r = rcp_newton(1.0 + u2);
+    c = (1.0 - u2) * r;
+    s = (2.0 * u) * r;
     return;
   }
-  const double t = (double)t32;
-  const double q = fma(t, t, 1.0);  // in [1, 2]
-  double y = (double)rsqrtf((float)q);
-  y = fma(0.5 * y, fma(-q * y, y, 1.0), y);
-  y = fma(0.5 * y, fma(-q * y, y, 1.0), y);
-  c = y;
-  s = t * y;
+  // outside the single-precision range: the exact FP64 angle
+  const double tau = d / (2.0 * hkl);
+  double t;
+  if (fabs(tau) > 1e150) t = 0.5 / tau;
+  else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
 }
 
 // Convergence: off(H)^2 <= kOffStop^2 ||H||_F^2 at the start of a sweep.
@@ -179,8 +179,13 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
       H = Hb[cur];
       double *Hn = Hb[cur ^ 1];
       const int b = set;
-      if (tid < half) {
-        const int i = tid;
+      // angle phase: one CTA gives each pair four lanes (threads 4i..4i+3),
+      // which form the same rotation and one entry each of the pair's
+      // rotated diagonal block; the cluster forms the angles on lanes 0..
+      // of warp 0 and rotates the diagonal blocks in the block phase
+      constexpr int LPP = NC == 1 ? 4 : 1;  // lanes per pair
+      if (tid < LPP * half) {
+        const int i = tid / LPP, lq = tid % LPP;
         auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (m - 1)); };
         int k = player(i), l = player(m - 1 - i);
         if (k > l) { const int tt = k; k = l; l = tt; }
@@ -190,30 +195,38 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
         const double hll = real ? H[l * JLD + l] : 0.0;
         double c = 1.0, s = 0.0;
         if (real) rotation(hkk, hll, hkl, c, s);
-        cs[b][i] = c; sn[b][i] = s; pk[b][i] = k; pl[b][i] = l;
-        act[b][i] = (real && s != 0.0) ? 1 : 0;
-        // one CTA: the pair's diagonal block J^T B J (symmetrised), skipped
-        // when J = I
-        if (NC == 1 && s != 0.0) {
-          const double m00 = c * hkk - s * hkl, m01 = s * hkk + c * hkl;
-          const double m10 = c * hlk - s * hll, m11 = s * hlk + c * hll;
-          const double h00 = c * m00 - s * m10, h11 = s * m01 + c * m11;
-          const double h01 = 0.5 * ((c * m01 - s * m11) + (s * m00 + c * m10));
-          Hn[k * JLD + k] = h00;
-          if (real) {
-            Hn[k * JLD + l] = h01;
-            Hn[l * JLD + k] = h01;
-            Hn[l * JLD + l] = h11;
+        if (lq == 0) {
+          cs[b][i] = c; sn[b][i] = s; pk[b][i] = k; pl[b][i] = l;
+          act[b][i] = (real && s != 0.0) ? 1 : 0;
+        }
+        if constexpr (NC == 1) {
+          // the pair's diagonal block J^T B J with B = [a b; b' d]:
+          // M = B J has m00 = c a - s b, m01 = s a + c b, m10 = c b' - s d,
+          // m11 = s b' + c d; lane 0 forms h00 = c m00 - s m10, lane 1
+          // h11 = s m01 + c m11, lane 2 h01 = c m01 - s m11, lane 3
+          // h10 = s m00 + c m10 (one instruction stream for all four
+          // lanes), and lanes 2, 3 store the symmetrised (h01 + h10) / 2.
+          // Skipped when J = I
+          const bool sw = lq == 1 || lq == 2;  // lanes using (m01, m11)
+          const double al = sw ? s : c, be = sw ? c : -s;
+          const double x = fma(al, hkk, be * hkl), y = fma(al, hlk, be * hll);
+          const bool so = lq == 1 || lq == 3;  // outputs s x + c y
+          const double h = fma(so ? s : c, x, (so ? c : -s) * y);
+          // the lanes of this warp in the angle phase: whole groups of four
+          const int nact = min(32, LPP * half - (tid & ~31));
+          const unsigned gmask = nact >= 32 ? 0xffffffffu : ((1u << nact) - 1u);
+          const double hx = __shfl_xor_sync(gmask, h, 1);
+          if (s != 0.0) {
+            if (lq == 0) Hn[k * JLD + k] = h;
+            else if (lq == 1) Hn[l * JLD + l] = h;
+            else Hn[lq == 2 ? k * JLD + l : l * JLD + k] = 0.5 * (h + hx);
           }
         }
       }
       if (pending) {
         if constexpr (NC == 1) {
-          // warps 1-3 and 5-7: warp 4 shares the FP64 pipe of warp 0's
-          // angle chain and diagonal blocks (warp w runs on SM
-          // sub-partition w mod 4)
-          const int w = tid >> 5;
-          if ((w & 3) != 0) rotate_v(b ^ 1, (w - 1 - (w >> 2)) * 32 + (tid & 31), NTH - 64);
+          // warps 2-7 (warps 0 and 1 hold the angles and diagonal blocks)
+          if (tid >= 64) rotate_v(b ^ 1, tid - 64, NTH - 64);
         } else {
           rotate_v(b ^ 1, tid, NTH);
         }

@@ -108,29 +108,6 @@ __global__ void __launch_bounds__(GR_OUT * GR_SUB) k_gram_reduce(double *__restr
 // A[k+1][k+1] first and takes the next pivot (square root and reciprocal)
 // while the other warps finish the update.  The inverse reuses the pivot
 // reciprocals: four lanes per column share each back-substitution sum.
-// 1/x for a positive, finite pivot x by Newton-Raphson, y <- y + y (1 - x y),
-// from a single-precision seed: the top 23 bits of the mantissa of x as a
-// float in [1, 2), its hardware reciprocal (rcp.approx, relative error
-// below 2^-22 with the truncation), and the exponent of x applied by integer
-// arithmetic.  Each step squares the relative error (2^-44, then rounding),
-// so the chain from one Cholesky pivot to the next holds four dependent FP64
-// operations instead of a square root and a division.  Exponents near the
-// ends of the range take the plain division.
-__device__ __forceinline__ double rcp_pivot(double x) {
-  const long long b = __double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex < 64 || ex > 1982) return 1.0 / x;
-  const float m = __int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF));
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));  // in (0.5, 1]
-  const long long rb = (long long)__float_as_uint(r);
-  const long long de = ((rb >> 23) & 0xFF) - 127 + 1023 - (ex - 1023);
-  double y = __longlong_as_double((de << 52) | ((rb & 0x7FFFFF) << 29));
-  y = fma(y, fma(-x, y, 1.0), y);
-  y = fma(y, fma(-x, y, 1.0), y);
-  return y;
-}
-
 __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpart, int nparts,
                                                  int n, int p, int pass, double *__restrict__ Rinv,
                                                  Params *prm) {
@@ -158,14 +135,14 @@ __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpar
   }
   __syncthreads();
   // pivot k: accepted when it is finite and above 1e-13 of the (shifted)
-  // diagonal; its reciprocal then comes from rcp_pivot
+  // diagonal; its reciprocal then comes from rcp_newton
   auto take_pivot = [&](int k, double sh) {
     const double piv = A[k][k];
     if (!(piv > 1e-13 * (diag0[k] + sh)) || !isfinite(piv)) {
       fail = 1;
     } else {
       dpiv[k] = piv;
-      rpiv[k] = rcp_pivot(piv);
+      rpiv[k] = rcp_newton(piv);
     }
   };
   double sh = 0.0;
@@ -191,7 +168,7 @@ __global__ void __launch_bounds__(NT) k_chol_inv(const double *__restrict__ gpar
     // G = U^T D U without square roots: row k of U is row k of the reduced
     // matrix times 1/d_k, and the trailing triangle loses A_ki A_kj / d_k.
     // The chain from one pivot to the next is one multiply, one FMA and
-    // rcp_pivot (no square root, no division).  (Spreading the trailing
+    // rcp_newton (no square root, no division).  (Spreading the trailing
     // triangle element by element over all warps measured slower: the step
     // is bound by that chain and the barrier, not by FP64 throughput.)
     for (int k = 0; k < p && !fail; ++k) {
