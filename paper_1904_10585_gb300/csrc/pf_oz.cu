@@ -151,11 +151,24 @@ __device__ __forceinline__ long long oz_rshift(long long v, int s) {
 }
 
 // (double)v 2^k: the conversion rounds to nearest even, the scaling is done
-// on the exponent field when the result stays normal (ldexp otherwise)
+// on the exponent field when the result stays normal (ldexp otherwise).  The
+// conversion is built with integer operations from the binary64 format: |v|
+// normalised by its leading-zero count, its top 53 bits rounded to nearest
+// even on the 11 bits below, the exponent set from the shift (a rounding
+// carry into bit 53 moves into the exponent by the addition).  GB300 runs
+// the int64 -> FP64 conversion instruction on its slow FP64 pipe.
 __device__ __forceinline__ double oz_scale(long long v, int k) {
   if (v == 0) return 0.0;
-  const double d = (double)v;
-  const long long bits = __double_as_longlong(d);
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  const unsigned long long m = a << lz;  // bit 63 set
+  unsigned long long r = m >> 11;         // 53 bits
+  const unsigned rem = (unsigned)(m & 0x7FF);
+  r += (rem > 0x400u || (rem == 0x400u && (r & 1ull))) ? 1ull : 0ull;
+  const long long bits =
+      (long long)((((unsigned long long)(63 - lz + 1022)) << 52) + r) |
+      (v < 0 ? (long long)0x8000000000000000ull : 0ll);
+  const double d = __longlong_as_double(bits);
   const int ex = (int)((bits >> 52) & 0x7FF) + k;
   if (ex > 0 && ex < 0x7FF) return __longlong_as_double(bits + ((long long)k << 52));
   return ldexp(d, k);
@@ -239,34 +252,46 @@ __global__ void __launch_bounds__(256) k_oz_zslice(const double *__restrict__ A,
 // ---------------------------------------------------------------------------
 // X (n x p FP64) -> digit planes xs[t][j][k] (bf16, plane t of NB rows j,
 // ldk) and exponents ex[c * kMaxP + j] of each 128-row chunk c and column j
-// (columns p..NB-1 are zero).  One CTA of 128 threads per chunk, thread =
-// row.
-// ---------------------------------------------------------------------------
+// (columns p..NB-1 are zero).  Grid (128-row chunks, groups of 8 columns),
+// thread = row: each thread reads the 8 entries of its row in the group
+// (two 32-byte vectors where X allows), so that the grid covers the SMs and
+// each row segment leaves HBM in whole sectors.
 __global__ void __launch_bounds__(128) k_oz_xslice(const double *__restrict__ X, int64_t ldx,
                                                    int n, int p, int NB,
                                                    __nv_bfloat16 *__restrict__ xs, int64_t ldk,
-                                                   int *__restrict__ ex) {
-  __shared__ unsigned qmax[4][kMaxP];
+                                                   int *__restrict__ ex, int xvec) {
+  __shared__ unsigned qmax[4][8];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int row = blockIdx.x * OZ_BM + t;
+  const int row = blockIdx.x * OZ_BM + t, j0 = blockIdx.y * 8;
   const bool in = row < n;
-  const double *xr = X + (int64_t)row * ldx;
-  for (int j = 0; j < NB; ++j) {
-    const unsigned f = (in && j < p) ? oz_exfield(xr[j]) : 0u;
+  const double *xr = X + (int64_t)(in ? row : 0) * ldx + j0;
+  double v[8];
+  if (in && xvec && j0 + 8 <= p) {
+    ld_v4_f64(xr, v);
+    ld_v4_f64(xr + 4, v + 4);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = (in && j0 + j < p) ? xr[j] : 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const unsigned f = (in && j0 + j < p) ? oz_exfield(v[j]) : 0u;
     const unsigned m = __reduce_max_sync(0xffffffffu, f);
     if (lane == 0) qmax[w][j] = m;
   }
   __syncthreads();
-  for (int j = 0; j < NB; ++j) {
-    const unsigned m = max(max(qmax[0][j], qmax[1][j]), max(qmax[2][j], qmax[3][j]));
-    const int e = oz_exponent(m);
-    if (t == 0) ex[blockIdx.x * kMaxP + j] = e;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int jj = j0 + j;
+    if (jj >= NB) break;
+    const int e = oz_exponent(max(max(qmax[0][j], qmax[1][j]), max(qmax[2][j], qmax[3][j])));
+    if (t == 0) ex[blockIdx.x * kMaxP + jj] = e;
     uint32_t d[kOzSlices];
-    oz_digit_bits((in && j < p && e != kOzExpBad) ? oz_fixed(xr[j], e) : 0ll, d);
+    oz_digit_bits((in && jj < p && e != kOzExpBad) ? oz_fixed(v[j], e) : 0ll, d);
     if (in) {
 #pragma unroll
-      for (int s = 0; s < kOzSlices; ++s)
-        xs[(int64_t)(s * NB + j) * ldk + row] = oz_bf16_of(d[s]);
+      for (int s2 = 0; s2 < kOzSlices; ++s2)
+        xs[(int64_t)(s2 * NB + jj) * ldk + row] = oz_bf16_of(d[s2]);
     }
   }
 }
@@ -622,7 +647,8 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
     const double *__restrict__ cvals, const double *__restrict__ lam,
     const double *__restrict__ xdiag, const double *__restrict__ mchunk,
     const int *__restrict__ ew, const int *__restrict__ ev, double *__restrict__ Z, int64_t ldz,
-    int zvec, __nv_bfloat16 *__restrict__ zs, int rb_n, int kt_n, int *__restrict__ ez,
+    int zvec, int small_k, __nv_bfloat16 *__restrict__ zs, int rb_n, int kt_n,
+    int *__restrict__ ez,
     int nzc, const Params *__restrict__ prm, Params *__restrict__ prm_flags,
     double *__restrict__ red) {
   constexpr int KS = kOzSlices;
@@ -818,7 +844,13 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
         int hi[XP_G], mid[XP_G], lo[XP_G];
         {
           uint32_t A[XP_G], B[XP_G], C[XP_G];
-          auto f2i = [](uint32_t u) { return __float2int_rn(__uint_as_float(u)); };
+          // exact integers in fp32; with p <= 32, |L_l| <= 7 32 2^14 < 2^22, and
+          // adding 1.5 2^23 leaves L_l in the low mantissa bits (an FMA-pipe
+          // add instead of a conversion)
+          auto f2i = [small_k](uint32_t u) {
+            return small_k ? __float_as_int(__uint_as_float(u) + 12582912.0f) - 0x4B400000
+                           : __float2int_rn(__uint_as_float(u));
+          };
           tmem_ld8(taddr + 0 * XP_TN + g, A);
           tmem_ld8(taddr + 1 * XP_TN + g, B);
           tmem_wait_ld();
@@ -1070,8 +1102,10 @@ cudaError_t launch_oz_xslice(cudaStream_t s, const Workspace &ws, const double *
                              int n, int which) {
   if (ws.oz.xs[which] == nullptr || n > ws.oz.ldk) return cudaErrorInvalidValue;
   const int p = ws.p;
-  k_oz_xslice<<<(n + OZ_BM - 1) / OZ_BM, OZ_BM, 0, s>>>(
-      X, ldx, n, p, oz_nbt(p), (__nv_bfloat16 *)ws.oz.xs[which], ws.oz.ldk, ws.oz.ex[which]);
+  const int nb = oz_nbt(p);
+  const int xvec = ((reinterpret_cast<uintptr_t>(X) & 31) == 0 && (ldx & 3) == 0) ? 1 : 0;
+  k_oz_xslice<<<dim3((n + OZ_BM - 1) / OZ_BM, (nb + 7) / 8), OZ_BM, 0, s>>>(
+      X, ldx, n, p, nb, (__nv_bfloat16 *)ws.oz.xs[which], ws.oz.ldk, ws.oz.ex[which], xvec);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
@@ -1142,7 +1176,8 @@ cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t 
   const int zvec = ((reinterpret_cast<uintptr_t>(Z) & 31) == 0 && (ldz & 3) == 0) ? 1 : 0;
   k_oz_expand<<<grid, XP_THREADS, XP_SMEM, s>>>(
       mw, mv, n, (int)oz.slice_rows, rowptr, colind, vals, lam, oz.xdiag, oz.mchunk, oz.ew,
-      oz.ev, Z, ldz, zvec, (__nv_bfloat16 *)oz.zs, (int)(oz.slice_rows / OZ_BM),
+      oz.ev, Z, ldz, zvec, p <= 32 ? 1 : 0, (__nv_bfloat16 *)oz.zs,
+      (int)(oz.slice_rows / OZ_BM),
       (int)(oz.ldk / OZ_BK), oz.ez, (int)(oz.slice_rows / OZ_BM), ws.prm, ws.prm, red);
   PF_LAUNCHED();
   *nblocks = grid;
