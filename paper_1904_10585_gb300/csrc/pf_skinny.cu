@@ -246,24 +246,32 @@ __global__ void __launch_bounds__(NT) k_apply_right(const double *Y, int64_t ldy
       Ys[r][c] = (gr < r1 && c < p) ? Y[(int64_t)gr * ldy + c] : 0.0;
     }
     __syncthreads();
-    // thread = column c and rows rg, rg + G, ...: U independent FMA chains
-    // sharing each load of R (a warp reads one row of Ys: a broadcast)
-    constexpr int G = NT / PT, U = RC / G;
-    const int c = tid % PT, rg = tid / PT;
-    if (c < p) {
-      const int kend = upper ? c + 1 : p;
+    // warp w takes the CPW adjacent columns w CPW .. and lane l the column
+    // w CPW + l mod CPW for rows l / CPW + RG u (U independent FMA chains
+    // sharing each load of R).  With the upper-triangular R a warp's loop
+    // ends at its own columns (k <= c), so the triangle halves the FP64 work
+    // of the warps; a store instruction writes CPW adjacent entries of RG
+    // rows (whole 32-byte sectors at CPW = 4)
+    constexpr int NWARP = NT / 32, CPW = PT / NWARP, RG = 32 / CPW, U = RC / RG;
+    static_assert(PT % NWARP == 0 && 32 % CPW == 0 && RC % RG == 0, "apply_right tiling");
+    const int w = tid >> 5, lane = tid & 31;
+    const int c = w * CPW + lane % CPW, rg = lane / CPW;
+    const int kend = upper ? min(p, w * CPW + CPW) : p;  // the same for the whole warp
+    if (w * CPW < p) {
       double acc[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) acc[u] = 0.0;
       for (int k = 0; k < kend; ++k) {
-        const double rk = Rs[k][c];
+        const double rk = Rs[k][c];  // zero below the diagonal and beyond p
 #pragma unroll
-        for (int u = 0; u < U; ++u) acc[u] = fma(Ys[rg + G * u][k], rk, acc[u]);
+        for (int u = 0; u < U; ++u) acc[u] = fma(Ys[rg + RG * u][k], rk, acc[u]);
       }
+      if (c < p) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int gr = rb + rg + G * u;
-        if (gr < r1) Q[(int64_t)gr * ldq + c] = acc[u];
+        for (int u = 0; u < U; ++u) {
+          const int gr = rb + rg + RG * u;
+          if (gr < r1) Q[(int64_t)gr * ldq + c] = acc[u];
+        }
       }
     }
   }
