@@ -47,7 +47,7 @@ HBM_PEAK_GBS = 6773.2          # measured STREAM-style copy on this machine's GB300
 # (None until a capture of the current kernel exists)
 NCU_TRAFFIC_BYTES = {
     # profiles/k_oz_product_maxcut_n4096.md: 237.30 MB read + 3.62 MB written per launch
-    "maxcut_n4096": 240.92e6,
+    "maxcut_n4096": 240.36e6,
 }
 SLICED_NOTE = ("bf16 digit planes x7 of Z and X on tcgen05 (TMA, TMEM), level sums exact in fp32, "
                "int64 fold, FP64 recurrence epilogue: an FP64-accurate product")

@@ -66,6 +66,16 @@ bool sliced_maxcut(const pf_ctx *ctx, const pf_problem *pr) {
          ctx->opt.precision == PF_PREC_FP64 && ctx->opt.dense_product == PF_DENSE_SLICED;
 }
 
+// Problems whose digit planes stay with the problem between steps: the
+// sliced dense max-cut (its expansion writes the planes of the next Z) and
+// the sliced NCE (its steps change only the diagonal of Z, whose chunks each
+// step slices again).
+bool planes_kept(const pf_ctx *ctx, const pf_problem *pr) {
+  return sliced_maxcut(ctx, pr) ||
+         (pr->kind == PF_PROBLEM_NCE && ctx->opt.dense_product == PF_DENSE_SLICED &&
+          ctx->opt.precision == PF_PREC_FP64);
+}
+
 // Problems whose steps apply a dense FP64 iteration matrix.
 bool dense_f64_problem(const pf_ctx *ctx, const pf_problem *pr) {
   return pr->kind == PF_PROBLEM_NCE ||
@@ -166,12 +176,12 @@ pf_status ensure_oz(pf_ctx *ctx) {
 }
 
 // Before steps of a problem: the digit-plane buffers, and for a sliced dense
-// max-cut the planes of its current Z (sliced here, outside any capture,
-// unless they already hold it).
+// max-cut or NCE the planes of its current Z (sliced here, outside any
+// capture, unless they already hold it).
 pf_status oz_prepare_problem(pf_ctx *ctx, const pf_problem *pr) {
   if (!dense_f64_problem(ctx, pr)) return PF_OK;
   PF_TRY(ensure_oz(ctx));
-  if (sliced_maxcut(ctx, pr) && (ctx->oz_owner != pr->Z || ctx->oz_owner_n != pr->n)) {
+  if (planes_kept(ctx, pr) && (ctx->oz_owner != pr->Z || ctx->oz_owner_n != pr->n)) {
     PF_CUDA(launch_oz_zslice(ctx->stream, ctx->ws, pr->Z, pr->ldz, (int)pr->n));
     ctx->oz_owner = pr->Z;
     ctx->oz_owner_n = pr->n;
@@ -179,10 +189,11 @@ pf_status oz_prepare_problem(pf_ctx *ctx, const pf_problem *pr) {
   return PF_OK;
 }
 
-// After steps: the planes hold the problem's Z only for the sliced max-cut.
+// After steps: the planes hold the problem's Z only for the sliced max-cut
+// and NCE.
 void oz_after_steps(pf_ctx *ctx, const pf_problem *pr) {
   if (!dense_f64_problem(ctx, pr)) return;
-  if (sliced_maxcut(ctx, pr)) {
+  if (planes_kept(ctx, pr)) {
     ctx->oz_owner = pr->Z;
     ctx->oz_owner_n = pr->n;
   } else {
@@ -564,8 +575,12 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     op.n = n;
     op.A = pr->Z;
     op.lda = pr->ldz;
-    if (sliced(ctx, op)) {  // one set of digit planes serves the filter and Rayleigh-Ritz
-      PF_CUDA(launch_oz_zslice(s, ws, pr->Z, pr->ldz, n));
+    if (sliced(ctx, op)) {
+      // one set of digit planes serves the filter and Rayleigh-Ritz; they
+      // hold Z as sliced before the steps (oz_prepare_problem) or by the
+      // previous step, which changed only the diagonal of Z: the chunks
+      // holding a diagonal entry are sliced again
+      PF_CUDA(launch_oz_zslice_diag(s, ws, pr->Z, pr->ldz, n));
       op.zs_ready = 1;
     }
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));

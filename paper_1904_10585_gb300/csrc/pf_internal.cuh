@@ -174,6 +174,8 @@ cudaError_t launch_lowrank_coef(cudaStream_t s, const Workspace &ws, int nparts,
 // the next block's planes into xs[next] unless next < 0
 cudaError_t launch_oz_zslice(cudaStream_t s, const Workspace &ws, const double *A, int64_t lda,
                              int n);
+cudaError_t launch_oz_zslice_diag(cudaStream_t s, const Workspace &ws, const double *A, int64_t lda,
+                             int n);
 cudaError_t launch_oz_xslice(cudaStream_t s, const Workspace &ws, const double *X, int64_t ldx,
                              int n, int which);
 cudaError_t launch_oz_product(cudaStream_t s, const Workspace &ws, int n, int which,

@@ -84,7 +84,8 @@ __device__ __forceinline__ void rotation(double hkk, double hll, double hkl, dou
 // Convergence: off(H)^2 <= kOffStop^2 ||H||_F^2 at the start of a sweep.
 constexpr double kOffStop2 = 1e-30;
 
-constexpr int JC = 8;      // CTAs per cluster (p > 32)
+constexpr int JC = 8;      // CTAs per cluster
+constexpr int kJacobiOneCta = 32;  // largest p on one CTA (the cluster above; at p = 64 one CTA took 2.4-3.7 ms per call against the cluster's 1.3 ms)
 constexpr int JNT = 256;   // threads per CTA of the cluster version
 constexpr int JNB = 256;   // threads of the one-CTA version
 constexpr int JLD = kMaxP + 1;
@@ -225,8 +226,10 @@ __device__ __forceinline__ void jacobi_body(const double *__restrict__ Hin, int 
       }
       if (pending) {
         if constexpr (NC == 1) {
-          // warps 2-7 (warps 0 and 1 hold the angles and diagonal blocks)
-          if (tid >= 64) rotate_v(b ^ 1, tid - 64, NTH - 64);
+          // the warps after those of the angle phase (LPP half lanes: warps
+          // 0-1 at p = 32, 0-3 at p = 64)
+          const int va = ((LPP * half + 31) / 32) * 32;
+          if (tid >= va) rotate_v(b ^ 1, tid - va, NTH - va);
         } else {
           rotate_v(b ^ 1, tid, NTH);
         }
@@ -338,7 +341,7 @@ cudaError_t configure_jacobi() {
 
 cudaError_t launch_jacobi_cluster(cudaStream_t s, const Workspace &ws, const double *H, int p,
                                   double *theta) {
-  if (p <= 32) k_jacobi_block<<<1, JNB, jacobi_bytes(1), s>>>(H, p, ws.Yeig, theta, ws.prm);
+  if (p <= kJacobiOneCta) k_jacobi_block<<<1, JNB, jacobi_bytes(1), s>>>(H, p, ws.Yeig, theta, ws.prm);
   else k_jacobi_cluster<<<JC, JNT, jacobi_bytes(JC), s>>>(H, p, ws.Yeig, theta, ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();

@@ -217,6 +217,34 @@ __device__ __forceinline__ void st_v4_f64(double *p, const double *v) {
 // and exponents ez[i * nzc + c] of each row and 128-column chunk.  One warp
 // per row, four entries per lane and chunk.
 // ---------------------------------------------------------------------------
+// One 128-column chunk of one row: its exponent and its 7 digit-plane
+// segments, by one warp (four entries per lane).
+__device__ __forceinline__ void oz_slice_chunk(const double *__restrict__ ar, int n, int row,
+                                               int c0, int lane, __nv_bfloat16 *__restrict__ zs,
+                                               int rb_n, int kt_n, int nzc,
+                                               int *__restrict__ ez) {
+  double v[4];
+  unsigned f = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = c0 + 32 * q + lane;
+    v[q] = k < n ? ar[k] : 0.0;
+    f = max(f, oz_exfield(v[q]));
+  }
+  f = __reduce_max_sync(0xffffffffu, f);
+  const int e = oz_exponent(f);
+  if (lane == 0) ez[(int64_t)row * nzc + c0 / OZ_BM] = e;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = c0 + 32 * q + lane;
+    if (k >= n) continue;
+    uint32_t d[kOzSlices];
+    oz_digit_bits(e != kOzExpBad ? oz_fixed(v[q], e) : 0ll, d);
+#pragma unroll
+    for (int s = 0; s < kOzSlices; ++s) zs[oz_zs_index(s, row, k, rb_n, kt_n)] = oz_bf16_of(d[s]);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_oz_zslice(const double *__restrict__ A, int64_t lda,
                                                    int n, __nv_bfloat16 *__restrict__ zs,
                                                    int rb_n, int kt_n, int nzc,
@@ -225,28 +253,21 @@ __global__ void __launch_bounds__(256) k_oz_zslice(const double *__restrict__ A,
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= n) return;
   const double *ar = A + (int64_t)row * lda;
-  for (int c0 = 0; c0 < n; c0 += OZ_BM) {
-    double v[4];
-    unsigned f = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = c0 + 32 * q + lane;
-      v[q] = k < n ? ar[k] : 0.0;
-      f = max(f, oz_exfield(v[q]));
-    }
-    f = __reduce_max_sync(0xffffffffu, f);
-    const int e = oz_exponent(f);
-    if (lane == 0) ez[(int64_t)row * nzc + c0 / OZ_BM] = e;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = c0 + 32 * q + lane;
-      if (k >= n) continue;
-      uint32_t d[kOzSlices];
-      oz_digit_bits(e != kOzExpBad ? oz_fixed(v[q], e) : 0ll, d);
-#pragma unroll
-      for (int s = 0; s < kOzSlices; ++s) zs[oz_zs_index(s, row, k, rb_n, kt_n)] = oz_bf16_of(d[s]);
-    }
-  }
+  for (int c0 = 0; c0 < n; c0 += OZ_BM) oz_slice_chunk(ar, n, row, c0, lane, zs, rb_n, kt_n, nzc, ez);
+}
+
+// The same for only the chunk that holds each row's diagonal entry: the
+// planes of a matrix whose other entries have not changed since it was
+// sliced (the nearest-correlation iteration matrix G + Diag(x)).
+__global__ void __launch_bounds__(256) k_oz_zslice_diag(const double *__restrict__ A,
+                                                        int64_t lda, int n,
+                                                        __nv_bfloat16 *__restrict__ zs, int rb_n,
+                                                        int kt_n, int nzc, int *__restrict__ ez) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= n) return;
+  oz_slice_chunk(A + (int64_t)row * lda, n, row, (row / OZ_BM) * OZ_BM, lane, zs, rb_n, kt_n,
+                 nzc, ez);
 }
 
 // ---------------------------------------------------------------------------
@@ -1094,6 +1115,17 @@ cudaError_t launch_oz_zslice(cudaStream_t s, const Workspace &ws, const double *
                                           (int)(ws.oz.slice_rows / OZ_BM),
                                           (int)(ws.oz.ldk / OZ_BK),
                                           (int)(ws.oz.slice_rows / OZ_BM), ws.oz.ez);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_zslice_diag(cudaStream_t s, const Workspace &ws, const double *A,
+                                  int64_t lda, int n) {
+  if (ws.oz.zs == nullptr || n > ws.oz.slice_rows) return cudaErrorInvalidValue;
+  k_oz_zslice_diag<<<(n + 7) / 8, 256, 0, s>>>(A, lda, n, (__nv_bfloat16 *)ws.oz.zs,
+                                               (int)(ws.oz.slice_rows / OZ_BM),
+                                               (int)(ws.oz.ldk / OZ_BK),
+                                               (int)(ws.oz.slice_rows / OZ_BM), ws.oz.ez);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
