@@ -98,3 +98,43 @@ def test_nce_lanczos_breakdown_on_invariant_start():
     assert info.b == h_o[0].b
     assert info.r_plus == 4
     assert abs(info.obj - 2.0) <= 1e-12
+
+
+def test_nce_planes_shared_context_matches_fresh_context():
+    """The digit planes of G + Diag(x) stay with the NCE problem between
+    steps, and each step re-slices only the chunks holding the diagonal.  A
+    product with another dense matrix on the same context (pf_apply) takes
+    the planes over; the next NCE steps must slice Z again in full.  The
+    interleaved run equals, bitwise, a run on a fresh context, and the
+    product equals A X within the sliced product's bound."""
+    from paper_1904_10585_gb300 import solver as S
+    n, p, d = 257, 32, 3
+    G = syn.nce_matrix(n, "5.7", seed=3)
+    U0 = syn.gaussian_block(n, p, seed=4)
+    A = syn.gaussian_block(n, n, seed=5)
+    X = syn.gaussian_block(n, p, seed=6)
+
+    def run(interleave):
+        with S.Context(p=p, n_max=n, degree=d, stream=torch.cuda.Stream()) as ctx:
+            pr = S.nce_problem(torch.from_numpy(G).to(DEV), torch.from_numpy(U0).to(DEV))
+            S.problem_init(ctx, pr)
+            hist, Ys = [], []
+            for k in range(12):
+                hist.append(S.prox_step(ctx, pr))
+                if interleave and k in (3, 7):
+                    Y = torch.empty(n, p, dtype=torch.float64, device=DEV)
+                    S.apply(ctx, S.dense_operator(torch.from_numpy(A).to(DEV)),
+                            torch.from_numpy(X).to(DEV), Y)
+                    Ys.append(Y)
+            ctx.stream.synchronize()
+            return hist, pr.lam.cpu().numpy(), [Y.cpu().numpy() for Y in Ys]
+
+    h1, x1, Ys = run(True)
+    h2, x2, _ = run(False)
+    assert [a.obj for a in h1] == [b.obj for b in h2]
+    assert np.array_equal(x1, x2)
+    ref = A.astype(np.longdouble) @ X.astype(np.longdouble)
+    bound = n * 2.0 ** -50 * np.abs(A).max(axis=1)[:, None] * np.abs(X).max(axis=0)[None, :]
+    for Y in Ys:
+        err = np.abs(Y.astype(np.longdouble) - ref).astype(np.float64)
+        assert np.all(err <= bound), float(np.max(err / bound))
