@@ -318,12 +318,15 @@ pf_status pf_report_async(pf_ctx *ctx, pf_iter_info *info);
  * sums live in one fixed device array inside the library of
  * 2 Mi doubles (16 MiB), which every GPU that loads the library keeps until
  * the process exits; calls need n * p <= 2,097,152 (PF_ERR_INVALID_ARG
- * otherwise).  The first call on each device looks up that array's device
- * address (with the device current) and should come before any stream
- * capture.  All calls share the array: calls whose kernels can overlap on a
- * GPU (different streams without ordering) race and must be serialised by
- * the caller.  Nothing in the array needs to start at zero (every partial
- * sum a call reads it has written itself).  Errors: PF_ERR_INVALID_ARG,
+ * otherwise).  Every call looks up that array's device address for the
+ * current device (so the address stays right after cudaDeviceReset); the
+ * first call on each device may load the library's device code and should
+ * come before any stream capture.  All calls share the array: calls whose
+ * kernels can overlap on a GPU (different streams without ordering) race and
+ * must be serialised by the caller.  Nothing in the array needs to start at
+ * zero (every partial sum a call reads it has written itself).  A CUDA error
+ * already pending when the call starts is left in place and reported as
+ * PF_ERR_CUDA with nothing launched.  Errors: PF_ERR_INVALID_ARG,
  * PF_ERR_CUDA, PF_ERR_UNSUPPORTED (device index >= 64). */
 pf_status pf_apply_dense_noalloc(const double *A, int64_t lda, const double *X, int64_t ldx,
                                  double *Y, int64_t ldy, int64_t n, int32_t p, void *stream);

@@ -224,29 +224,29 @@ constexpr int kStaticMaxDevices = 64;
 static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
 std::mutex g_static_mutex;
-double *g_static_addr[kStaticMaxDevices] = {};
 int g_static_sms[kStaticMaxDevices] = {};
 
-// Device address of the scratch array (and SM count) for the current
-// device, looked up once per device.  In host code the array's name only
-// stands in for the device copy, so the address must come from
-// cudaGetSymbolAddress with the device current.
+// Device address of the scratch array (and SM count) for the current device.
+// In host code the array's name only stands in for the device copy, so the
+// address comes from cudaGetSymbolAddress with the device current.  It is
+// looked up on every call (a host-side lookup, no device work), so a new
+// context after cudaDeviceReset gets the array's new address; only the SM
+// count, a property of the device, is remembered.
 pf_status static_scratch_for_current_device(double **addr, int *sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PF_ERR_CUDA;
   if (dev < 0 || dev >= kStaticMaxDevices) return PF_ERR_UNSUPPORTED;
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr)
+    return PF_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (g_static_addr[dev] == nullptr) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr)
-      return PF_ERR_CUDA;
+  if (g_static_sms[dev] == 0) {
     int count = 0;
     if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return PF_ERR_CUDA;
-    g_static_addr[dev] = (double *)p;
     g_static_sms[dev] = count;
   }
-  *addr = g_static_addr[dev];
+  *addr = (double *)p;
   *sms = g_static_sms[dev];
   return PF_OK;
 }
@@ -262,6 +262,9 @@ extern "C" pf_status pf_apply_dense_noalloc(const double *A, int64_t lda, const 
       lda < n || ldx < p || ldy < p)
     return PF_ERR_INVALID_ARG;
   if (n * (int64_t)p > kStaticScratchDoubles) return PF_ERR_INVALID_ARG;
+  // an error left pending by someone else's earlier launch belongs to its
+  // owner: report it without clearing it, and launch nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return PF_ERR_CUDA;
   double *scratch = nullptr;
   int sms = 0;
   const pf_status st = static_scratch_for_current_device(&scratch, &sms);

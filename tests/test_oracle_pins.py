@@ -338,6 +338,98 @@ def test_completion_kkt_factor_formula_matches_dense():
 
 
 # --------------------------------------------------------------------------
+# Interval rule of Sec. 4.1 (reading R4) and the max-cut step (reading R6),
+# against values computed by hand from the printed formulas
+# --------------------------------------------------------------------------
+
+def test_choose_b_r_largest_rule_hand_values():
+    """b = (1 - eta) lambda_r_prev + eta a with lambda_r_prev the smallest of
+    the previous Ritz values: a = -4, previous values {5, 2, 1}, eta = 0.1
+    gives 0.9 * 1 + 0.1 * (-4) = 0.5; eta = 0.2 gives 0.8 - 0.8 = 0."""
+    th = np.array([5.0, 2.0, 1.0])
+    assert o.choose_b(-4.0, th, ub=100.0, eta=0.1) == pytest.approx(0.5, abs=1e-15)
+    assert o.choose_b(-4.0, th, ub=100.0, eta=0.2) == pytest.approx(0.0, abs=1e-15)
+    # the estimate is the smallest previous value wherever it sits in the array
+    assert o.choose_b(-4.0, np.array([1.0, 5.0, 2.0]), ub=100.0) == pytest.approx(0.5, abs=1e-15)
+    # the upper Gershgorin bound plays no part once Ritz values exist
+    assert o.choose_b(-4.0, th, ub=-1e9) == o.choose_b(-4.0, th, ub=1e9)
+
+
+def test_choose_b_first_step_hand_values():
+    """No previous Ritz values: the all-positive rule b = eta a for a < 0
+    (a = -4: b = -0.4); for a >= 0 the interval keeps (1 - eta) of the way to
+    the upper bound (a = 2, ub = 12: b = 2 + 0.9 * 10 = 11)."""
+    assert o.choose_b(-4.0, None, ub=12.0) == pytest.approx(-0.4, abs=1e-15)
+    assert o.choose_b(-4.0, None, ub=12.0, eta=0.2) == pytest.approx(-0.8, abs=1e-15)
+    assert o.choose_b(2.0, None, ub=12.0) == pytest.approx(11.0, abs=1e-14)
+    assert o.choose_b(0.0, None, ub=12.0) == pytest.approx(10.8, abs=1e-14)
+
+
+def test_choose_b_gap_guard_hand_values():
+    """b - a is kept >= 1e-3 max(1, |a|): a = -4 with a previous smallest Ritz
+    value of -4 gives b = -4 -> -4 + 0.004; a = -0.5 with -0.5 gives
+    -0.5 + 0.001; a gap already wide enough is left alone."""
+    assert o.choose_b(-4.0, np.array([-4.0]), ub=0.0) == pytest.approx(-3.996, abs=1e-15)
+    assert o.choose_b(-0.5, np.array([-0.5]), ub=0.0) == pytest.approx(-0.499, abs=1e-15)
+    # -3.9 is 0.09 above a = -4 after the rule (0.9 * -3.9 + 0.1 * -4 = -3.91)
+    assert o.choose_b(-4.0, np.array([-3.9]), ub=0.0) == pytest.approx(-3.91, abs=1e-14)
+
+
+def test_maxcut_step_size_hand_value():
+    """t = 10 sqrt(n)/||C||_F with C = -L/4.  Path 1-2-3 with weights +1
+    and -1: D = diag(1, 0, -1), L = D - W has six entries of magnitude 1 and
+    a zero middle diagonal, so ||C||_F = sqrt(6)/4 and
+    t = 10 sqrt(3) * 4/sqrt(6) = 20 sqrt(2)."""
+    L = np.array([[1.0, -1.0, 0.0], [-1.0, 0.0, 1.0], [0.0, 1.0, -1.0]])
+    C = sp.csr_matrix(-L / 4.0)
+    assert o.maxcut_step_size(C) == pytest.approx(20.0 * math.sqrt(2.0), rel=1e-15)
+    # one edge of weight 1 on four vertices (two isolated): ||C||_F = 1/2,
+    # t = 10 * 2 / (1/2) = 40
+    C4 = sp.csr_matrix(([-0.25, 0.25, 0.25, -0.25], ([0, 0, 1, 1], [0, 1, 0, 1])), shape=(4, 4))
+    assert o.maxcut_step_size(C4) == pytest.approx(40.0, rel=1e-15)
+    # the synthetic generator's cost matrix: ||C||_F from its definition
+    inst = syn.maxcut_instance(60, 0.2, 4, seed=5)
+    Cs = sp.csr_matrix((inst.C.vals, inst.C.colind, inst.C.rowptr), shape=(60, 60))
+    ref = 10.0 * math.sqrt(60) / math.sqrt(float(np.sum(inst.C.vals.astype(np.float64) ** 2)))
+    assert o.maxcut_step_size(Cs) == pytest.approx(ref, rel=1e-14)
+
+
+@pytest.mark.parametrize("mutation", ["swap_eta", "theta_max", "first_step_sign", "no_guard"])
+def test_planted_interval_mistakes_are_caught(monkeypatch, mutation):
+    def bad(a, theta_prev, ub, eta=o.ETA):
+        if theta_prev is None:
+            if mutation == "first_step_sign":
+                b = -eta * a if a < 0 else a + (1.0 - eta) * (ub - a)
+            else:
+                b = eta * a if a < 0 else a + (1.0 - eta) * (ub - a)
+        elif mutation == "swap_eta":
+            b = eta * float(np.min(theta_prev)) + (1.0 - eta) * a
+        elif mutation == "theta_max":
+            b = (1.0 - eta) * float(np.max(theta_prev)) + eta * a
+        else:
+            b = (1.0 - eta) * float(np.min(theta_prev)) + eta * a
+        if mutation != "no_guard":
+            gap = 1e-3 * max(1.0, abs(a))
+            if b - a < gap:
+                b = a + gap
+        return b
+    monkeypatch.setattr(o, "choose_b", bad)
+    with pytest.raises(AssertionError):
+        test_choose_b_r_largest_rule_hand_values()
+        test_choose_b_first_step_hand_values()
+        test_choose_b_gap_guard_hand_values()
+
+
+def test_planted_step_size_mistakes_are_caught(monkeypatch):
+    for bad in (lambda C: 10.0 * C.shape[0] / float(sp.linalg.norm(C, "fro")),
+                lambda C: math.sqrt(C.shape[0]) / float(sp.linalg.norm(C, "fro")),
+                lambda C: 10.0 * math.sqrt(C.shape[0]) / float(sp.linalg.norm(C, "fro")) ** 2):
+        monkeypatch.setattr(o, "maxcut_step_size", bad)
+        with pytest.raises(AssertionError):
+            test_maxcut_step_size_hand_value()
+
+
+# --------------------------------------------------------------------------
 # Planted mistakes: each must be caught by a pin above
 # --------------------------------------------------------------------------
 
