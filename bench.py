@@ -2,13 +2,16 @@
 
 One step = one whole solve of the workload through the hot path (interval,
 Chebyshev filter, CholQR2, Rayleigh-Ritz, prox/DRS update, KKT report) from a
-fresh initial state:  default workload ``maxcut_n4096``, the max-cut SDP of an
-Erdos-Renyi graph (n = 4096, edge probability 0.01, weights +-1) solved by
-PFAM with a dense FP64 iteration matrix, p = 32, degree 4, up to 200
-iterations or relative KKT <= 1e-4 (checked every 10 iterations).
+fresh initial state, run until the relative KKT residual is <= 1e-4 (checked
+every 10 iterations; a cap of ``max_iters`` iterations bounds it).  Default
+workload ``maxcut_n4096``: the max-cut SDP of an Erdos-Renyi graph (n = 4096,
+edge probability 0.01, weights +-1) solved by PFAM with a dense FP64
+iteration matrix, p = 32, degree 4.
 
-Metric: solves/s (whole job), with p50/p99 solve latency; the dominant
-kernel (the dense FP64 filter product) is reported against its roofline.
+Metric: solves/s at KKT 1e-4 (whole job), with p50/p99 solve latency; the
+filter's dense product is reported against its roofline (the metric's
+"filter GB/s vs roofline"), and the device time of every phase of the step
+is measured with CUDA events over one traced solve.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -43,12 +46,16 @@ CHECK_EVERY = 10
 FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 nominal (no measured FP64 peak is provided)
 FP64_CUBLAS_MEASURED = 1.09    # torch float64 matmul 16384x16384x64 on this pool (context)
 HBM_PEAK_GBS = 6773.2          # measured STREAM-style copy on the GB300s
-# dram bytes per launch of the dominant kernel from the committed ncu captures
-# (None until a capture of the current kernel exists)
+# DRAM bytes (read + written) per launch of the roofline kernel, from an ncu
+# capture of the current kernel (None where no capture of it exists):
+# k_oz_product<32> at n = 4096, p = 32 read 237.30 MB and wrote 3.62 MB
 NCU_TRAFFIC_BYTES = {
-    # profiles/k_oz_product_maxcut_n4096.md: 237.30 MB read + 3.62 MB written per launch
     "maxcut_n4096": 240.36e6,
 }
+# Iterations the default workload's solve takes to reach KKT 1e-4 on the GPU;
+# the oracle follows the same trajectory (parity of every iteration), so the
+# reference arm scales its sampled iterations to this count.
+ITERS_TO_TOL = {"maxcut_n4096": 2740}
 SLICED_NOTE = ("bf16 digit planes x7 of Z and X on tcgen05 (TMA, TMEM), level sums exact in fp32, "
                "int64 fold, FP64 recurrence epilogue: an FP64-accurate product")
 
@@ -128,6 +135,24 @@ def max_over_ranks(values, pg, device=None):
     return [float(x) for x in t]
 
 
+def cpu_model() -> str:
+    """Model name of the host CPU (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -144,6 +169,9 @@ class WorkloadSpec:
         self.cfg, self.inst = syn.make_workload(name)
         c = self.cfg
         self.n, self.p, self.d, self.iters = c["n"], c["p"], c["degree"], c["iters"]
+        # solves run to the tolerance, capped at max_iters (the configured
+        # iteration count where no cap is given)
+        self.max_iters = c.get("max_iters", c["iters"])
         self.kind = c["kind"]
         self.lowprec = "bf16" if name.endswith("lowprec") else None
         self.structured = name.endswith("structured")
@@ -204,7 +232,11 @@ class WorkloadSpec:
     def config(self):
         c = self.cfg
         d = {"workload": self.name, "n": c["n"], "p": c["p"], "degree": c["degree"],
-             "max_iters": c["iters"], "tol_kkt": TOL}
+             "tol_kkt": self.tol(), "max_iters": self.max_iters,
+             "configured_iters": c["iters"],
+             "stopping": (f"each solve runs until its KKT residual is <= {self.tol():g} "
+                          f"(checked every {CHECK_EVERY} iterations), at most "
+                          f"{self.max_iters} iterations")}
         if self.kind == "nnls":
             d["problem"] = ("nuclear-norm regularised least squares, PFNNLS (Sec. 5.2.2): "
                             "accelerated proximal gradient, filter on G^T G, FP64")
@@ -263,13 +295,14 @@ def run_reference(args):
         return 0
     W = WorkloadSpec(args.workload)
     iters_sample = 2 if W.name == "maxcut_n4096" else max(1, W.sample_iters() // 10)
+    iters_solve = ITERS_TO_TOL.get(W.name, W.iters)
     for _ in range(args.warmup):
         W.oracle_sample(iters_sample)
     times = [W.oracle_sample(iters_sample) for _ in range(args.steps)]
-    per_solve = [tt * W.iters / iters_sample for tt in times]
+    per_solve = [tt * iters_solve / iters_sample for tt in times]
     value = len(per_solve) / sum(per_solve)
-    sample = (f"initial state + {iters_sample} of {W.iters} iterations per step, scaled to one "
-              f"{W.iters}-iteration solve")
+    sample = (f"initial state + {iters_sample} iterations per step, scaled to one "
+              f"{iters_solve}-iteration solve (the iterations to KKT {W.tol():g})")
     line = {
         "impl": "reference", "metric": "solves/s", "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -277,7 +310,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": W.config(),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": host_cores(),
-                         "kind": "oracle", "sample": sample},
+                         "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -370,12 +403,13 @@ class Workload(WorkloadSpec):
             nnz = self.ci.numel()
             return (op, "k_lrsp_apply (Y X, CSR SpMM, FP64)", "alu", 2.0 * nnz * p, "TFLOP/s")
         if self.dense_f64() and self.sliced:
-            # digit planes of Z read once, the block's planes read and the next
-            # block's written, X / Yprev read and Ynext written in FP64
+            # the method's bytes: the FP64 iteration matrix read once, X and
+            # Y_prev read and Y_next written in FP64 (the digit planes the
+            # kernel moves instead are its representation, reported beside)
             return (S.dense_operator(pr.Z),
-                    "k_oz_product (Y = Z X from bf16 digit planes x7 on tcgen05, recurrence "
-                    "epilogue)", "hbm",
-                    14.0 * n * n + 28.0 * n * p + 24.0 * n * p, "GB/s")
+                    "k_oz_product + k_oz_finish (Y = Z X from bf16 digit planes x7 on tcgen05, "
+                    "recurrence epilogue)", "hbm",
+                    8.0 * n * n + 24.0 * n * p, "GB/s")
         if self.kind == "nce":
             return (S.dense_operator(pr.Z),
                     "k_gemm_f64_splitk + k_combine (Y = (G + Diag x) X, dense FP64 filter product)",
@@ -435,7 +469,7 @@ def run_ours(args):
         if W.kind == "nce":
             problem.Z.copy_(W.G)        # the iteration matrix starts from G again
         S.problem_init(ctx, problem)
-        return S.solve(ctx, problem, iters, W.tol(), CHECK_EVERY)
+        return S.solve(ctx, problem, W.max_iters, W.tol(), CHECK_EVERY)
 
     # launch counting (non-graph calls): init + one step
     with torch.cuda.stream(stream):
@@ -486,8 +520,36 @@ def run_ours(args):
     iters_run = [int(r.iters) for r in results]
     gpu_launches = sum(init_launches + it * step_launches for it in iters_run)
 
-    # dominant kernel, timed with CUDA events on the library stream over R
-    # launches of the same operator on the state left by the timed solves.
+    # device time per phase over one whole solve, stepped outside the graph
+    # with the library's phase events (the same kernels the graph replays)
+    phase_ms = {k: 0.0 for k in pkg.PHASE_NAMES}
+    traced_iters = 0
+    pkg.pf_set_tracing(ctx.handle, True)
+    with torch.cuda.stream(stream):
+        pr.U.copy_(W.U0)
+        if W.kind == "nce":
+            pr.Z.copy_(W.G)
+        S.problem_init(ctx, pr)
+        cap = min(W.max_iters, int(np.max(iters_run)))
+        for k in range(cap):
+            info = S.prox_step(ctx, pr, want_info=(k + 1) % CHECK_EVERY == 0)
+            for name, v in pkg.pf_phase_times(ctx.handle).items():
+                phase_ms[name] += v
+            traced_iters += 1
+            if info is not None and info.kkt <= W.tol():
+                break
+    pkg.pf_set_tracing(ctx.handle, False)
+    phase_total = sum(phase_ms.values())
+    phases = {"iterations": traced_iters,
+              "ms_per_iteration": {k: v / max(1, traced_iters) for k, v in phase_ms.items()},
+              "share": {k: (v / phase_total if phase_total > 0 else 0.0)
+                        for k, v in phase_ms.items()},
+              "how": "CUDA events at the phase boundaries of one solve stepped outside the "
+                     "graph (pf_set_tracing / pf_phase_times)"}
+    dominant_phase = max(phase_ms, key=phase_ms.get)
+
+    # the filter's product, timed with CUDA events on the library stream over
+    # R launches of the same operator on the state left by the solves above
     R = 20
     op, kname, bound, work, unit = W.kernel_op(pr)
     X = pr.U.clone()
@@ -545,7 +607,7 @@ def run_ours(args):
         if W.kind == "nce":
             pe.Z.copy_(d_in[0])
         S.problem_init(ctx, pe)
-        S.solve(ctx, pe, iters, W.tol(), CHECK_EVERY)
+        S.solve(ctx, pe, W.max_iters, W.tol(), CHECK_EVERY)
         h_V.copy_(pe.V, non_blocking=True)
         h_th.copy_(pe.theta, non_blocking=True)
         stream.synchronize()
@@ -574,7 +636,7 @@ def run_ours(args):
         secs = W.oracle_sample(iters_sample)
         it_solve = float(np.mean(iters_run))
         cpu = {"value": 1.0 / (secs * it_solve / iters_sample), "unit": "solves/s",
-               "cores": host_cores(), "kind": "oracle",
+               "cores": host_cores(), "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"initial state + {iters_sample} iterations of the same workload "
                          f"({secs:.1f} s), scaled to one {it_solve:.0f}-iteration solve (the "
                          f"iterations the timed GPU solves ran)"}
@@ -597,13 +659,22 @@ def run_ours(args):
         "roofline": {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
                      "traffic": NCU_TRAFFIC_BYTES.get(args.workload),
-                     "work_per_launch": work, "avg_launch_ms": apply_ms, "peak_source": peak_src},
+                     "work_per_launch": work, "avg_launch_ms": apply_ms, "peak_source": peak_src,
+                     "note": ("the metric's filter product; work = the method's algorithmic "
+                              "bytes (FP64 iteration matrix and blocks)")},
+        "phases": phases,
+        "dominant_phase": dominant_phase,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "gpu_launches": gpu_launches,
         "launches_per_iteration": step_launches,
     }
+    if W.sliced and W.dense_f64():
+        # what the sliced product moves: 7 bf16 digit planes of Z (14 bytes an
+        # entry), the planes of X read and of the next block written, and the
+        # FP64 blocks
+        line["roofline"]["representation_bytes_per_launch"] = 14.0 * n * n + 52.0 * n * p
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

@@ -331,6 +331,46 @@ pf_status pf_report_async(pf_ctx *ctx, pf_iter_info *info);
 pf_status pf_apply_dense_noalloc(const double *A, int64_t lda, const double *X, int64_t ldx,
                                  double *Y, int64_t ldy, int64_t n, int32_t p, void *stream);
 
+/* Phases of a step, in the paper's terms: the interval [a, b] (Sec. 4.1),
+ * the Chebyshev filter products (Sec. 2.1, Eq. (cheb)), orth by CholQR2
+ * (Eq. (subspace-update)), the Rayleigh-Ritz product and projected matrix
+ * (Sec. 2.2, Eq. (RR)), the p x p eigensolve with the Ritz vectors, and the
+ * update (prox / DRS step, reconstruction and KKT report; for completion also
+ * the sampled residual that starts a step). */
+#define PF_NUM_PHASES 6
+typedef enum {
+  PF_PHASE_INTERVAL = 0,
+  PF_PHASE_FILTER = 1,
+  PF_PHASE_ORTH = 2,
+  PF_PHASE_RR = 3,
+  PF_PHASE_EIG = 4,
+  PF_PHASE_UPDATE = 5
+} pf_phase;
+
+/* Phase tracing (instrumentation with no counterpart in the paper).  Every
+ * call that enqueues a step, a filter or a Rayleigh-Ritz projection opens an
+ * NVTX range named "pf:<phase>" per phase (host-side, always on; visible to
+ * Nsight tools).  With tracing on (on != 0; creates CUDA events, allocates no
+ * device memory), such calls enqueued outside a stream capture also record an
+ * event at each phase boundary; pf_phase_times then waits for the most recent
+ * traced call and writes the device time of each phase to ms (host,
+ * PF_NUM_PHASES doubles, milliseconds; zeros when nothing was traced).  Steps
+ * replayed from pf_solve's CUDA graph are not traced. */
+pf_status pf_set_tracing(pf_ctx *ctx, int32_t on);
+pf_status pf_phase_times(pf_ctx *ctx, double *ms);
+
+/* Limit, in nanoseconds of the GPU's global timer, of each bounded wait in
+ * the tensor-core pipelines (TMA and MMA stages); 2 s by default.  A wait that
+ * runs out makes its kernel stop its pipeline, let the copies and MMAs it has
+ * already issued land (with a separate fixed limit), free its tensor memory,
+ * and set flags bit 3 of the step report, which pf_prox_step / pf_solve
+ * return as PF_ERR_DEVICE_TIMEOUT; the results of that step are then invalid
+ * but the context stays usable.  0 gives up on the first wait that is not
+ * already satisfied (for tests of that path).  Applies to the current device,
+ * is synchronous, and must not be called while this library's kernels run
+ * or during a stream capture.  No counterpart in the paper. */
+pf_status pf_set_wait_limit(uint64_t ns);
+
 /* Number of kernels this library has enqueued in this process (host-side
  * count; a replayed CUDA graph adds nothing).  Instrumentation with no
  * counterpart in the paper: it lets a caller count the GPU launches of a

@@ -116,6 +116,9 @@ def _load():
         "pf_get_info": (C.c_int, [P, C.POINTER(pf_iter_info)]),
         "pf_enqueue_steps": (C.c_int, [P, C.POINTER(pf_problem), C.c_int64]),
         "pf_report_async": (C.c_int, [P, P]),
+        "pf_set_tracing": (C.c_int, [P, C.c_int32]),
+        "pf_phase_times": (C.c_int, [P, C.POINTER(C.c_double)]),
+        "pf_set_wait_limit": (C.c_int, [C.c_uint64]),
         "pf_status_string": (C.c_char_p, [C.c_int]),
         "pf_last_error": (C.c_char_p, [P]),
     }
@@ -130,8 +133,18 @@ _lib = _load()
 EXPORTED = ("pf_create", "pf_destroy", "pf_filter", "pf_rayleigh_ritz", "pf_apply",
             "pf_problem_init", "pf_prox_step", "pf_solve", "pf_get_info", "pf_enqueue_steps",
             "pf_report_async",
-            "pf_kernel_launch_count", "pf_apply_dense_noalloc", "pf_status_string",
-            "pf_last_error")
+            "pf_kernel_launch_count", "pf_apply_dense_noalloc", "pf_set_tracing",
+            "pf_phase_times", "pf_set_wait_limit", "pf_status_string", "pf_last_error")
+
+# pf_phase (include/pf.h)
+PF_NUM_PHASES = 6
+PF_PHASE_INTERVAL = 0
+PF_PHASE_FILTER = 1
+PF_PHASE_ORTH = 2
+PF_PHASE_RR = 3
+PF_PHASE_EIG = 4
+PF_PHASE_UPDATE = 5
+PHASE_NAMES = ("interval", "filter", "orth", "rayleigh_ritz", "eigensolve", "update")
 
 
 class PFError(RuntimeError):
@@ -226,6 +239,21 @@ def pf_get_info(ctx) -> pf_iter_info:
     info = pf_iter_info()
     _check(_lib.pf_get_info(ctx, C.byref(info)), ctx)
     return info
+
+
+def pf_set_tracing(ctx, on: bool) -> None:
+    _check(_lib.pf_set_tracing(ctx, 1 if on else 0), ctx)
+
+
+def pf_phase_times(ctx) -> dict:
+    """Device milliseconds per phase of the most recent traced call."""
+    ms = (C.c_double * PF_NUM_PHASES)()
+    _check(_lib.pf_phase_times(ctx, ms), ctx)
+    return {name: float(ms[i]) for i, name in enumerate(PHASE_NAMES)}
+
+
+def pf_set_wait_limit(ns: int) -> None:
+    _check(_lib.pf_set_wait_limit(int(ns)))
 
 
 def raw_call(name: str, *args) -> int:

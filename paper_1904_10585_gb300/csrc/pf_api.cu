@@ -9,6 +9,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pf_internal.cuh"
 
 using namespace pf;
@@ -16,6 +18,9 @@ using namespace pf;
 namespace pf {
 std::atomic<int64_t> g_launches{0};
 }
+
+// phase boundaries kept per traced call (a step marks at most about 8)
+constexpr int kTraceMarks = 32;
 
 struct pf_ctx {
   pf_options opt;
@@ -41,6 +46,13 @@ struct pf_ctx {
   void *oz_base;
   const void *oz_owner;
   int64_t oz_owner_n;
+  // phase tracing (pf_set_tracing): an event at each phase boundary of the
+  // most recent call enqueued outside a stream capture
+  bool trace;
+  bool nvtx_open;
+  int nmarks;
+  int tmark[kTraceMarks];
+  cudaEvent_t tev[kTraceMarks + 1];
 };
 
 namespace {
@@ -108,6 +120,49 @@ pf_status set_err(pf_ctx *ctx, pf_status s, const char *fmt, ...) {
   } while (0)
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------------------
+// Phase tracing: an NVTX range per phase of a call (always), and, when
+// tracing is on and the stream is not being captured, a timing event at each
+// phase boundary (pf_phase_times turns them into milliseconds per phase).
+// ---------------------------------------------------------------------------
+const char *const kPhaseName[PF_NUM_PHASES] = {"pf:interval", "pf:filter", "pf:orth",
+                                               "pf:rayleigh_ritz", "pf:eigensolve", "pf:update"};
+
+bool capturing(const pf_ctx *ctx) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &st) != cudaSuccess) return true;
+  return st != cudaStreamCaptureStatusNone;
+}
+
+void trace_begin(pf_ctx *ctx) {
+  if (ctx->nvtx_open) {
+    nvtxRangePop();
+    ctx->nvtx_open = false;
+  }
+  if (ctx->trace && !capturing(ctx)) ctx->nmarks = 0;
+}
+
+void phase(pf_ctx *ctx, int ph) {
+  if (ctx->nvtx_open) nvtxRangePop();
+  nvtxRangePushA(kPhaseName[ph]);
+  ctx->nvtx_open = true;
+  if (ctx->trace && ctx->nmarks < kTraceMarks && !capturing(ctx)) {
+    if (cudaEventRecord(ctx->tev[ctx->nmarks], ctx->stream) == cudaSuccess)
+      ctx->tmark[ctx->nmarks++] = ph;
+  }
+}
+
+void trace_end(pf_ctx *ctx) {
+  if (ctx->nvtx_open) {
+    nvtxRangePop();
+    ctx->nvtx_open = false;
+  }
+  if (ctx->trace && ctx->nmarks > 0 && !capturing(ctx) &&
+      cudaEventRecord(ctx->tev[ctx->nmarks], ctx->stream) != cudaSuccess)
+    ctx->nmarks = 0;
+}
+
 
 // Digit-plane buffers of the sliced dense product, sized for n_max and the
 // context's p; allocated once, outside any stream capture.
@@ -267,6 +322,7 @@ pf_status apply(pf_ctx *ctx, const Op &op, const double *X, int64_t ldx, const d
 
 // Q = orth(Y) by CholQR2 (a third pass follows a shifted first pass).
 pf_status cholqr2(pf_ctx *ctx, const double *Y, int64_t ldy, double *U, int64_t ldu, int n) {
+  phase(ctx, PF_PHASE_ORTH);
   const int p = ctx->ws.p;  // active width
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
@@ -330,6 +386,7 @@ pf_status filter_core_lp_sparse(pf_ctx *ctx, const Op &op, double *U, int64_t ld
 
 // U <- orth(rho(op) U) with the interval already in the device parameters.
 pf_status filter_core(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
+  phase(ctx, PF_PHASE_FILTER);
   const int p = ctx->ws.p;  // active width
   if (op.kind == PF_OP_LOWRANK_SPARSE && ctx->cur_lp)
     return filter_core_lp_sparse(ctx, op, U, ldu, degree);
@@ -366,6 +423,7 @@ pf_status filter_core(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int deg
 
 pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, double *V, int64_t ldv,
                   double *theta, double *resid) {
+  phase(ctx, PF_PHASE_RR);
   const int p = ctx->ws.p;  // active width
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
@@ -379,6 +437,7 @@ pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, doubl
   int nb = 0;
   PF_CUDA(launch_gram(s, ws, Q, ldq, ws.W, p, op.n, p, p, 0, &nb));
   // launch_gram leaves the reduced H = Q^T W in the first Gram slot
+  phase(ctx, PF_PHASE_EIG);
   PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, theta));
   if (resid != nullptr)
     PF_CUDA(launch_rotate_resid(s, ws, Q, ldq, ws.W, p, op.n, p, theta, V, ldv, resid));
@@ -468,8 +527,10 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr);
 // One step of the problem's method, enqueued only (graph-capturable), then
 // the saturation count of the block.
 pf_status step_core(pf_ctx *ctx, const pf_problem *pr) {
+  trace_begin(ctx);
   PF_TRY(step_body(ctx, pr));
   PF_CUDA(launch_step_end(ctx->stream, ctx->ws));
+  trace_end(ctx);
   return PF_OK;
 }
 
@@ -482,6 +543,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
   const bool lp = ctx->cur_lp;
   if (pr->kind == PF_PROBLEM_NNLS) {
     // G = (1+beta) X - beta Xp - A*(r): coefficients, residual r (in S), interval
+    phase(ctx, PF_PHASE_UPDATE);
     PF_CUDA(launch_nnls_residual(s, ws, pr->rowptr, pr->colind, pr->t_rowptr, pr->t_perm,
                                  pr->vals_f64, n, pr->fac, pr->ldfac, pr->fsv, pr->S, pr->theta));
     Op og = {};  // G Z = [L | Lp] diag(coef) [R | Rp]^T Z - R_sp Z
@@ -504,6 +566,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     ot.colind = pr->t_colind;
     ot.perm = pr->t_perm;
     double *const *Yb = ws.Y;
+    phase(ctx, PF_PHASE_FILTER);
     for (int j = 0; j < degree; ++j) {
       const double *cur = j == 0 ? pr->U : Yb[(j - 1) & 1];
       const int64_t ldc = j == 0 ? pr->ldu : p;
@@ -515,13 +578,16 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
                                           ldc));
     }
     PF_TRY(cholqr2(ctx, Yb[(degree - 1) & 1], p, pr->U, pr->ldu, n));
+    phase(ctx, PF_PHASE_RR);
     PF_CUDA(launch_lowrank_sparse_apply(s, ws, og, pr->U, pr->ldu, nullptr, 0, ws.W, p,
                                         MODE_PLAIN));
     int nb = 0;
     PF_CUDA(launch_gram(s, ws, ws.W, p, ws.W, p, n, p, p, 0, &nb));
+    phase(ctx, PF_PHASE_EIG);
     PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, pr->theta));
     PF_CUDA(launch_apply_right(s, ws, pr->U, pr->ldu, pr->V, pr->ldv, n, p, ws.Yeig, 0, 0));
     PF_CUDA(launch_apply_right(s, ws, ws.W, p, Yb[0], p, n, p, ws.Yeig, 0, 0));
+    phase(ctx, PF_PHASE_UPDATE);
     const int cap = pr->rank_cap > 0 ? pr->rank_cap : (p > 8 ? p - 8 : 1);
     PF_CUDA(launch_nnls_update(s, ws, n, pr->fac, pr->ldfac, pr->fsv, Yb[0], pr->V, pr->ldv,
                                pr->theta, cap));
@@ -530,6 +596,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
   }
   if (pr->kind == PF_PROBLEM_SVT) {
     // interval on Y^T Y, Y = A*(x) (values x in S)
+    phase(ctx, PF_PHASE_INTERVAL);
     PF_CUDA(launch_svt_interval(s, ws, pr->rowptr, pr->t_rowptr, pr->t_perm, pr->S, n,
                                 pr->theta));
     // filter: each product Y^T (Y X) is two SpMMs, the recurrence in the second;
@@ -543,6 +610,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     oy.sscale = 1.0;
     oy.shift = 0.0;
     double *const *Yb = ws.Y;
+    phase(ctx, PF_PHASE_FILTER);
     for (int j = 0; j < degree; ++j) {
       const double *cur = j == 0 ? pr->U : Yb[(j - 1) & 1];
       const int64_t ldc = j == 0 ? pr->ldu : p;
@@ -555,13 +623,16 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     }
     PF_TRY(cholqr2(ctx, Yb[(degree - 1) & 1], p, pr->U, pr->ldu, n));
     // Rayleigh-Ritz on the projected Gram matrix: B = Y Q, B^T B = Wr theta Wr^T
+    phase(ctx, PF_PHASE_RR);
     PF_CUDA(launch_lowrank_sparse_apply(s, ws, oy, pr->U, pr->ldu, nullptr, 0, ws.W, p,
                                         MODE_PLAIN));
     int nb = 0;
     PF_CUDA(launch_gram(s, ws, ws.W, p, ws.W, p, n, p, p, 0, &nb));
+    phase(ctx, PF_PHASE_EIG);
     PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, pr->theta));
     PF_CUDA(launch_apply_right(s, ws, pr->U, pr->ldu, pr->V, pr->ldv, n, p, ws.Yeig, 0, 0));
     PF_CUDA(launch_apply_right(s, ws, ws.W, p, Yb[0], p, n, p, ws.Yeig, 0, 0));
+    phase(ctx, PF_PHASE_UPDATE);
     // shrink, sampled residual, dual update and report
     PF_CUDA(launch_svt_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, Yb[0], p, pr->V,
                               pr->ldv, pr->theta, pr->mu, pr->t, pr->S));
@@ -569,6 +640,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     return PF_OK;
   }
   if (pr->kind == PF_PROBLEM_NCE) {
+    phase(ctx, PF_PHASE_INTERVAL);
     PF_CUDA(launch_nce_interval(s, ws, pr->Z, pr->ldz, n, pr->theta, p));
     Op op = {};
     op.kind = PF_OP_DENSE;
@@ -585,6 +657,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     }
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
+    phase(ctx, PF_PHASE_UPDATE);
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_nce_update(s, ws, pr->Z, pr->ldz, n, p, pr->V, pr->ldv, pr->theta, pr->lam,
                               pr->t > 0.0 ? pr->t : 1.0, pr->hist, pr->accel_l, pr->accel_lam));
@@ -596,6 +669,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
   if (pr->kind == PF_PROBLEM_MAXCUT && structured) {
     // structured Z = X~prev - tC - Diag(lam) for the Rayleigh-Ritz step (and
     // for the filter unless a low-precision dense shadow is used)
+    phase(ctx, PF_PHASE_INTERVAL);
     PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
     PF_CUDA(launch_maxcut_sparse_part(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, pr->lam,
                                       pr->S));
@@ -626,6 +700,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
       PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     }
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
+    phase(ctx, PF_PHASE_UPDATE);
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_maxcut_struct_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V,
                                         pr->ldv, pr->theta, pr->lam));
@@ -634,6 +709,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
                                       pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv, pr->theta,
                                       pr->lam, pr->Z_lp, pr->ldz_lp));
   } else if (pr->kind == PF_PROBLEM_MAXCUT) {
+    phase(ctx, PF_PHASE_INTERVAL);
     PF_CUDA(launch_interval(s, ws, PF_PROBLEM_MAXCUT, pr->rowptr, pr->colind, pr->vals_f64, n,
                             pr->lam, pr->theta, p));
     Op op = {};
@@ -646,13 +722,16 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     op.zs_ready = sliced(ctx, op) ? 1 : 0;
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
+    phase(ctx, PF_PHASE_UPDATE);
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_maxcut_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv,
                                  pr->theta, pr->Z, pr->ldz, pr->lam, sliced(ctx, op)));
   } else {
+    phase(ctx, PF_PHASE_UPDATE);  // the sampled residual: the gradient of the prox step
     PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
     PF_CUDA(launch_completion_residual(s, ws, pr->rowptr, pr->colind, pr->vals_f32, n, p, ws.Vprev,
                                        p, ws.thprev, pr->S));
+    phase(ctx, PF_PHASE_INTERVAL);
     PF_CUDA(launch_interval(s, ws, PF_PROBLEM_COMPLETION, pr->rowptr, pr->colind, pr->S, n, nullptr,
                             ws.thprev, p));
     Op op = {};
@@ -670,6 +749,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     op.shift = -pr->t * pr->mu;
     PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     PF_TRY(rr_core(ctx, op, pr->U, pr->ldu, pr->V, pr->ldv, pr->theta, nullptr));
+    phase(ctx, PF_PHASE_UPDATE);
     PF_CUDA(launch_copy_block(s, ws, pr->V, pr->ldv, n, p, pr->U, pr->ldu));
     PF_CUDA(launch_completion_kkt(s, ws, pr->V, pr->ldv, pr->theta, n, p));
   }
@@ -768,8 +848,11 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   const int p = opt->p;
   const size_t np = (size_t)n_max * p;
   // largest split-K partial buffer over all n <= n_max
-  size_t part = 0;
-  for (int n = p; n <= n_max; ++n) {
+  // (beyond 2^20 rows every split count is 1: a single split already has
+  // more row blocks than 8 per SM)
+  size_t part = np;
+  const int64_t n_scan = n_max < ((int64_t)1 << 20) ? n_max : ((int64_t)1 << 20);
+  for (int n = p; n <= n_scan; ++n) {
     int kc = 0;
     const size_t v = (size_t)dense_splits(n, sms, &kc) * n * p;
     if (v > part) part = v;
@@ -864,7 +947,48 @@ pf_status pf_destroy(pf_ctx *ctx) {
   if (ctx->have_graph) cudaGraphExecDestroy(ctx->gexec);
   cudaFree(ctx->base);
   if (ctx->oz_base) cudaFree(ctx->oz_base);
+  if (ctx->trace)
+    for (int i = 0; i <= kTraceMarks; ++i) cudaEventDestroy(ctx->tev[i]);
   delete ctx;
+  return PF_OK;
+}
+
+pf_status pf_set_tracing(pf_ctx *ctx, int32_t on) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  if (on && !ctx->trace) {
+    for (int i = 0; i <= kTraceMarks; ++i) {
+      if (cudaEventCreate(&ctx->tev[i]) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->tev[j]);
+        return set_err(ctx, PF_ERR_CUDA, "cudaEventCreate failed");
+      }
+    }
+    ctx->trace = true;
+    ctx->nmarks = 0;
+  } else if (!on && ctx->trace) {
+    PF_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i <= kTraceMarks; ++i) cudaEventDestroy(ctx->tev[i]);
+    ctx->trace = false;
+    ctx->nmarks = 0;
+  }
+  return PF_OK;
+}
+
+pf_status pf_phase_times(pf_ctx *ctx, double *ms) {
+  if (!ctx || !ms) return PF_ERR_INVALID_ARG;
+  for (int k = 0; k < PF_NUM_PHASES; ++k) ms[k] = 0.0;
+  if (!ctx->trace || ctx->nmarks == 0) return PF_OK;
+  PF_CUDA(cudaEventSynchronize(ctx->tev[ctx->nmarks]));
+  for (int i = 0; i < ctx->nmarks; ++i) {
+    float t = 0.0f;
+    PF_CUDA(cudaEventElapsedTime(&t, ctx->tev[i], ctx->tev[i + 1]));
+    ms[ctx->tmark[i]] += (double)t;
+  }
+  return PF_OK;
+}
+
+pf_status pf_set_wait_limit(uint64_t ns) {
+  if (set_wait_limit_oz(ns) != cudaSuccess || set_wait_limit_tc(ns) != cudaSuccess)
+    return PF_ERR_CUDA;
   return PF_OK;
 }
 
@@ -881,7 +1005,9 @@ pf_status pf_filter(pf_ctx *ctx, const pf_operator *op, double a, double b, int3
   if (sliced(ctx, o)) PF_TRY(ensure_oz(ctx));
   PF_CUDA(launch_set_interval(ctx->stream, ctx->ws.prm, a, b));
   if (sliced(ctx, o)) ctx->oz_owner = nullptr;
+  trace_begin(ctx);
   PF_TRY(filter_core(ctx, o, U, ldu, degree));
+  trace_end(ctx);
   if (sliced(ctx, o)) {
     ctx->oz_owner = o.A;
     ctx->oz_owner_n = o.n;
@@ -901,7 +1027,9 @@ pf_status pf_rayleigh_ritz(pf_ctx *ctx, const pf_operator *op, const double *Q, 
     PF_TRY(ensure_oz(ctx));
     ctx->oz_owner = nullptr;
   }
+  trace_begin(ctx);
   PF_TRY(rr_core(ctx, o, Q, ldq, V, ldv, theta, resid));
+  trace_end(ctx);
   if (sliced(ctx, o)) {
     ctx->oz_owner = o.A;
     ctx->oz_owner_n = o.n;
@@ -1025,8 +1153,8 @@ pf_status pf_prox_step(pf_ctx *ctx, pf_problem *pr, pf_iter_info *info) {
     PF_TRY(read_params(ctx, &h));
     params_to_info(h, info, ctx);
     if (h.flags & 8) return set_err(ctx, PF_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
-    if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
     if (h.flags & 4) return set_err(ctx, PF_ERR_NAN, "non-finite Ritz value");
+    if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
   }
   if (width_rule_on(ctx) && pr->iter % ctx->opt.adapt_every == 0)
     PF_TRY(apply_width_rule(ctx, pr));
@@ -1185,8 +1313,8 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
     params_to_info(h, &out->last, ctx);
   }
   if (h.flags & 8) return set_err(ctx, PF_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
-  if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
   if (h.flags & 4) return set_err(ctx, PF_ERR_NAN, "non-finite Ritz value");
+  if (h.flags & 2) return set_err(ctx, PF_ERR_CHOL_BREAKDOWN, "CholQR2 broke down");
   if (tol > 0.0 && !converged && max_iter > 0)
     return set_err(ctx, PF_ERR_NOT_CONVERGED, "kkt %.3e above tol %.3e after %lld steps", h.kkt,
                    tol, (long long)it);

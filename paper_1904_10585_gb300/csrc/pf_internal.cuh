@@ -136,6 +136,9 @@ cudaError_t configure_tc();
 cudaError_t configure_sparse();
 cudaError_t configure_jacobi();
 cudaError_t configure_oz();
+// limits of the bounded tensor-core pipeline waits (per translation unit)
+cudaError_t set_wait_limit_oz(uint64_t ns);
+cudaError_t set_wait_limit_tc(uint64_t ns);
 // K splits of the sliced product for size n and block width p
 int oz_splits(int n, int p, int num_sms);
 // K splits of the dense FP64 product for size n (returns S, sets the chunk).

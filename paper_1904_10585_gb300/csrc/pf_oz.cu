@@ -1090,6 +1090,9 @@ int oz_nbt(int p) { return oz_halves(p) == 1 ? oz_nb(p) : 64; }
 
 }  // namespace
 
+// Limit of the bounded pipeline waits of this file's kernels (current device).
+cudaError_t set_wait_limit_oz(uint64_t ns) { return set_wait_limit_here(ns); }
+
 cudaError_t configure_oz() {
   cudaError_t e;
   if ((e = oz_set_attr<16>()) != cudaSuccess) return e;

@@ -5,12 +5,23 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace pf {
 namespace {
 
-constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;  // bounded waits (about 2 s)
+// Limit of the bounded pipeline waits (mbar_wait), in ns of the global
+// timer: a device variable of this translation unit, 2 s unless
+// set_wait_limit_here() changes it.  The drains that let issued copies and
+// MMAs land before a CTA exits keep their own fixed limit.
+__device__ uint64_t tc_wait_limit_ns = 2000000000ull;
+constexpr uint64_t TC_DRAIN_NS = 2000000000ull;
+
+// Host side: set this translation unit's wait limit on the current device.
+inline cudaError_t set_wait_limit_here(uint64_t ns) {
+  return cudaMemcpyToSymbol(tc_wait_limit_ns, &ns, sizeof(ns));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -43,10 +54,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
+  const uint64_t limit = tc_wait_limit_ns;
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (gtimer() - t0 > TC_TIMEOUT_NS) {
+    if (gtimer() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -147,7 +159,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
   const uint64_t t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (gtimer() - t0 > TC_TIMEOUT_NS) return;
+    if (gtimer() - t0 > TC_DRAIN_NS) return;
   }
 }
 

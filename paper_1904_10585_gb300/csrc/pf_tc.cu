@@ -518,6 +518,9 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 }  // namespace
 
+// Limit of the bounded pipeline waits of this file's kernels (current device).
+cudaError_t set_wait_limit_tc(uint64_t ns) { return set_wait_limit_here(ns); }
+
 cudaError_t configure_tc() {
   if (g_encode == nullptr) {
     cudaDriverEntryPointQueryResult q;

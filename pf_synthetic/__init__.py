@@ -250,19 +250,21 @@ def gaussian_block(n: int, p: int, seed: int) -> np.ndarray:
 
 
 # Named workloads (sizes of the configurations the benchmark and tests use).
+# ``iters`` is the configured iteration count (fixed-count parity runs);
+# ``max_iters``, where given, caps a solve that runs to its tolerance.
 WORKLOADS = {
     "completion_n400": dict(kind="completion", n=400, rank=8, rate=0.20, p=16, degree=3,
-                            iters=100, mu=0.05, t=1.0, config_index=0),
+                            iters=100, max_iters=3000, mu=0.05, t=1.0, config_index=0),
     "maxcut_n4096": dict(kind="maxcut", n=4096, prob=0.01, p=32, degree=4, iters=200,
-                         config_index=1),
+                         max_iters=6000, config_index=1),
     "maxcut_n4096_structured": dict(kind="maxcut", n=4096, prob=0.01, p=32, degree=4, iters=200,
-                                    config_index=1),
+                                    max_iters=6000, config_index=1),
     "maxcut_n16384_lowprec": dict(kind="maxcut", n=16384, prob=0.01, p=64, degree=4,
                                   degree_max=8, iters=200, config_index=2),
     "nce_n4000": dict(kind="nce", n=4000, example="5.7", p=64, degree=3, iters=1000,
                       accel_l=2, config_index=5),
     "completion_n50000": dict(kind="completion", n=50000, rank=20, rate=0.01, p=40, degree=4,
-                              iters=100, mu=0.05, t=1.0, config_index=3),
+                              iters=100, max_iters=3000, mu=0.05, t=1.0, config_index=3),
     "svt_n5000": dict(kind="svt", n=5000, rank=10, sr=0.1, p=32, degree=1, iters=500,
                       config_index=6),
     "nnls_n10000": dict(kind="nnls", n=10000, rank=10, sr=0.05, p=32, degree=1, iters=300,
