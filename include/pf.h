@@ -151,6 +151,13 @@ typedef struct {
  *        Z / s (n x n, ldz_lp elements, 16-byte aligned row pitch) that the
  *        tensor-core filter reads; the Rayleigh-Ritz step then uses the
  *        structured FP64 operator, so Z may be NULL.
+ *  Z_tf32  MAXCUT with a bf16 context (optional): an fp32 n x n buffer
+ *        (ldz_tf32 elements, 16-byte aligned row pitch).  When given,
+ *        pf_solve's adaptive ladder (options.adaptive) has three rungs: the
+ *        bf16 filter, raised in degree up to degree_max while the KKT
+ *        residual stalls; then the tf32 filter on the fp32 shadow Z / s kept
+ *        in this buffer; then the FP64 structured filter.  Without it the
+ *        ladder goes from bf16 to FP64.
  *  lam   MAXCUT only: n-vector lambda of the last DRS update.
  *  S     nnz FP64 workspace: COMPLETION P_Omega(X - M); structured MAXCUT
  *        the sparse part -tC - Diag(lam).
@@ -220,6 +227,7 @@ typedef struct {
   int64_t ldg;
   const int32_t *t_rowptr; const int32_t *t_colind; const int32_t *t_perm;  /* SVT, NNLS */
   double *fac; int64_t ldfac; double *fsv; int32_t rank_cap;                /* NNLS */
+  void *Z_tf32; int64_t ldz_tf32;  /* MAXCUT, bf16 context, optional: fp32 shadow for the tf32 rung */
 } pf_problem;
 
 /* Per-step report (host struct).  MAXCUT: obj = <C, X~>, pinf/dinf/gap as in

@@ -72,7 +72,7 @@ class pf_problem(C.Structure):
                 ("p_active", C.c_int32), ("guard", C.c_void_p), ("ldg", C.c_int64),
                 ("t_rowptr", C.c_void_p), ("t_colind", C.c_void_p), ("t_perm", C.c_void_p),
                 ("fac", C.c_void_p), ("ldfac", C.c_int64), ("fsv", C.c_void_p),
-                ("rank_cap", C.c_int32)]
+                ("rank_cap", C.c_int32), ("Z_tf32", C.c_void_p), ("ldz_tf32", C.c_int64)]
 
 
 class pf_iter_info(C.Structure):

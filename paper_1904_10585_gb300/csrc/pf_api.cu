@@ -35,12 +35,17 @@ struct pf_ctx {
   cudaGraphExec_t gexec;
   pf_problem gkey;
   int gdegree;
-  bool glp;
+  int gprec;
   int gp;
   bool have_graph;
-  // adaptive ladder state (degree and low-precision filter currently used)
+  // adaptive ladder state: degree and filter precision (pf_precision)
+  // currently used
   int cur_degree;
-  bool cur_lp;
+  int cur_prec;
+  // KKT residuals at the last (up to 5) checks of the ladder; kept across
+  // pf_solve calls so that a solve run in pieces climbs the same ladder
+  double ladder_hist[5];
+  int ladder_n;
   // digit planes of the sliced dense product (allocated on first use) and
   // the matrix (pointer, n) they currently hold, nullptr when unknown
   void *oz_base;
@@ -58,6 +63,9 @@ struct pf_ctx {
 namespace {
 
 bool width_rule_on(const pf_ctx *ctx) { return ctx->opt.adapt_guard > 0; }
+
+// The filter currently runs on a low-precision shadow (bf16 or tf32).
+bool cur_lp(const pf_ctx *ctx) { return ctx->cur_prec != PF_PREC_FP64; }
 
 // Active block width of a problem (validated by check_problem).
 int active_width(const pf_ctx *ctx, const pf_problem *pr) {
@@ -342,11 +350,11 @@ pf_status cholqr2(pf_ctx *ctx, const double *Y, int64_t ldy, double *U, int64_t 
 
 // Low-precision filter (tensor cores): fp32 recurrence, bf16/tf32 operands,
 // then CholQR2 in FP64.
-pf_status filter_core_lp(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
+pf_status filter_core_lp(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree,
+                         bool tf32) {
   const int p = ctx->ws.p;  // active width
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
-  const bool tf32 = ctx->opt.precision == PF_PREC_TF32;
   if (op.lp_scale > 0.0) PF_CUDA(launch_set_scale(s, ws.prm, op.lp_scale));
   PF_CUDA(launch_prep_lp(s, ws, tf32, U, ldu, op.n, ws.U32, ws.Xt[0]));
   for (int j = 0; j < degree; ++j) {
@@ -388,10 +396,10 @@ pf_status filter_core_lp_sparse(pf_ctx *ctx, const Op &op, double *U, int64_t ld
 pf_status filter_core(pf_ctx *ctx, const Op &op, double *U, int64_t ldu, int degree) {
   phase(ctx, PF_PHASE_FILTER);
   const int p = ctx->ws.p;  // active width
-  if (op.kind == PF_OP_LOWRANK_SPARSE && ctx->cur_lp)
+  if (op.kind == PF_OP_LOWRANK_SPARSE && cur_lp(ctx))
     return filter_core_lp_sparse(ctx, op, U, ldu, degree);
   if (op.kind == PF_OP_DENSE && op.A_lp != nullptr && ctx->opt.precision != PF_PREC_FP64)
-    return filter_core_lp(ctx, op, U, ldu, degree);
+    return filter_core_lp(ctx, op, U, ldu, degree, ctx->opt.precision == PF_PREC_TF32);
   double *const *Y = ctx->ws.Y;
   if (sliced(ctx, op)) {
     // digit planes of A (unless current), of U, then one tensor-core product
@@ -479,6 +487,12 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
                        "low-precision max-cut needs Z_lp (16-byte aligned, ldz_lp >= n, 16-byte "
                        "row pitch)");
     }
+    if (pr->Z_tf32 != nullptr &&
+        (ctx->opt.precision != PF_PREC_BF16 || pr->ldz_tf32 < pr->n ||
+         (pr->ldz_tf32 * 4) % 16 != 0 || ((uintptr_t)pr->Z_tf32 & 15) != 0))
+      return set_err(ctx, PF_ERR_INVALID_ARG,
+                     "Z_tf32 (the tf32 rung's shadow) needs a bf16 context, 16-byte alignment, "
+                     "ldz_tf32 >= n and a 16-byte row pitch");
     if (pr->Z != nullptr && pr->ldz < pr->n)
       return set_err(ctx, PF_ERR_INVALID_ARG, "max-cut Z needs ldz >= n");
     if ((lp || pr->Z == nullptr) && !pr->S)
@@ -540,7 +554,12 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
   cudaStream_t s = ctx->stream;
   const Workspace &ws = ctx->ws;
   const int degree = ctx->cur_degree;
-  const bool lp = ctx->cur_lp;
+  const bool lp = cur_lp(ctx);
+  // the tf32 rung of a bf16 context's ladder reads the problem's fp32 shadow
+  const bool tf32_now = ctx->cur_prec == PF_PREC_TF32;
+  void *const zlp_now = (tf32_now && ctx->opt.precision == PF_PREC_BF16) ? pr->Z_tf32 : pr->Z_lp;
+  const int64_t ldzlp_now =
+      (tf32_now && ctx->opt.precision == PF_PREC_BF16) ? pr->ldz_tf32 : pr->ldz_lp;
   if (pr->kind == PF_PROBLEM_NNLS) {
     // G = (1+beta) X - beta Xp - A*(r): coefficients, residual r (in S), interval
     phase(ctx, PF_PHASE_UPDATE);
@@ -692,10 +711,10 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
       Op dop = {};
       dop.kind = PF_OP_DENSE;
       dop.n = n;
-      dop.A_lp = pr->Z_lp;
-      dop.lda_lp = pr->ldz_lp;
+      dop.A_lp = zlp_now;
+      dop.lda_lp = ldzlp_now;
       dop.lp_scale = 0.0;  // the scale the shadow was written with is on the device
-      PF_TRY(filter_core_lp(ctx, dop, pr->U, pr->ldu, degree));
+      PF_TRY(filter_core_lp(ctx, dop, pr->U, pr->ldu, degree, tf32_now));
     } else {
       PF_TRY(filter_core(ctx, op, pr->U, pr->ldu, degree));
     }
@@ -705,11 +724,14 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     PF_CUDA(launch_maxcut_struct_update(s, ws, pr->rowptr, pr->colind, pr->vals_f64, n, p, pr->V,
                                         pr->ldv, pr->theta, pr->lam));
     if (lp)
-      PF_CUDA(launch_maxcut_lp_shadow(s, ws, ctx->opt.precision == PF_PREC_TF32, pr->rowptr,
-                                      pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv, pr->theta,
-                                      pr->lam, pr->Z_lp, pr->ldz_lp));
+      PF_CUDA(launch_maxcut_lp_shadow(s, ws, tf32_now, pr->rowptr, pr->colind, pr->vals_f64, n,
+                                      p, pr->V, pr->ldv, pr->theta, pr->lam, zlp_now, ldzlp_now));
   } else if (pr->kind == PF_PROBLEM_MAXCUT) {
     phase(ctx, PF_PHASE_INTERVAL);
+    // the sliced update takes the dual residual from the factors of the
+    // previous and the new X~: keep the previous Ritz pairs
+    if (ctx->opt.dense_product == PF_DENSE_SLICED)
+      PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
     PF_CUDA(launch_interval(s, ws, PF_PROBLEM_MAXCUT, pr->rowptr, pr->colind, pr->vals_f64, n,
                             pr->lam, pr->theta, p));
     Op op = {};
@@ -771,7 +793,7 @@ void params_to_info(const Params &h, pf_iter_info *info, const pf_ctx *ctx = nul
   info->jacobi_sweeps = h.sweeps;
   info->reserved = 0;
   info->degree = ctx ? ctx->cur_degree : h.degree;
-  info->precision = ctx ? (ctx->cur_lp ? ctx->opt.precision : (int)PF_PREC_FP64) : h.precision;
+  info->precision = ctx ? ctx->cur_prec : h.precision;
 }
 
 pf_status read_params(pf_ctx *ctx, Params *h) {
@@ -789,12 +811,13 @@ bool same_problem(const pf_problem &a, const pf_problem &b) {
          a.accel_lam == b.accel_lam && a.hist == b.hist && a.p_active == b.p_active &&
          a.guard == b.guard && a.ldg == b.ldg && a.t_rowptr == b.t_rowptr &&
          a.t_colind == b.t_colind && a.t_perm == b.t_perm && a.fac == b.fac &&
-         a.ldfac == b.ldfac && a.fsv == b.fsv && a.rank_cap == b.rank_cap;
+         a.ldfac == b.ldfac && a.fsv == b.fsv && a.rank_cap == b.rank_cap &&
+         a.Z_tf32 == b.Z_tf32 && a.ldz_tf32 == b.ldz_tf32;
 }
 
 bool graph_matches(const pf_ctx *ctx, const pf_problem &pr) {
   return ctx->have_graph && same_problem(ctx->gkey, pr) && ctx->gdegree == ctx->cur_degree &&
-         ctx->glp == ctx->cur_lp && ctx->gp == ctx->ws.p;
+         ctx->gprec == ctx->cur_prec && ctx->gp == ctx->ws.p;
 }
 
 
@@ -831,7 +854,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   ctx->p = opt->p;
   ctx->stream = (cudaStream_t)stream;
   ctx->cur_degree = opt->degree;
-  ctx->cur_lp = opt->precision != PF_PREC_FP64;
+  ctx->cur_prec = opt->precision;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   int sms = 0;
@@ -1135,7 +1158,8 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
   pr->iter = 0;
   ctx->ws.p = pr->p_active;
   ctx->cur_degree = ctx->opt.degree;
-  ctx->cur_lp = ctx->opt.precision != PF_PREC_FP64;
+  ctx->cur_prec = ctx->opt.precision;
+  ctx->ladder_n = 0;
   return PF_OK;
 }
 
@@ -1213,7 +1237,7 @@ pf_status pf_enqueue_steps(pf_ctx *ctx, pf_problem *pr, int64_t n_steps) {
 pf_status pf_report_async(pf_ctx *ctx, pf_iter_info *info) {
   if (!ctx || !info) return PF_ERR_INVALID_ARG;
   PF_CUDA(launch_export_info(ctx->stream, ctx->ws, ctx->cur_degree,
-                             ctx->cur_lp ? ctx->opt.precision : (int)PF_PREC_FP64));
+                             ctx->cur_prec));
   PF_CUDA(cudaMemcpyAsync(info, ctx->ws.info, sizeof(pf_iter_info), cudaMemcpyDeviceToHost,
                           ctx->stream));
   return PF_OK;
@@ -1240,7 +1264,7 @@ static pf_status capture_step(pf_ctx *ctx, pf_problem *pr) {
   ctx->gexec = ge;
   ctx->gkey = *pr;
   ctx->gdegree = ctx->cur_degree;
-  ctx->glp = ctx->cur_lp;
+  ctx->gprec = ctx->cur_prec;
   ctx->gp = ctx->ws.p;
   ctx->have_graph = true;
   return PF_OK;
@@ -1259,8 +1283,8 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
   // the low-precision filter for the FP64 one
   const bool adaptive = ctx->opt.adaptive != 0;
   const bool check = tol > 0.0 || adaptive;
-  double hist[5] = {0, 0, 0, 0, 0};
-  int nhist = 0;
+  double *hist = ctx->ladder_hist;
+  int &nhist = ctx->ladder_n;
   Params h = {};
   int64_t it = 0;
   bool converged = false;
@@ -1295,8 +1319,17 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
           if (ctx->cur_degree < dmax) {
             ctx->cur_degree += 1;
             nhist = 0;
-          } else if (ctx->cur_lp) {
-            ctx->cur_lp = false;
+          } else if (ctx->cur_prec == PF_PREC_BF16 && pr->kind == PF_PROBLEM_MAXCUT &&
+                     pr->Z_tf32 != nullptr) {
+            // tf32 rung: the fp32 shadow of the current iteration matrix,
+            // written now from the state the bf16 steps left
+            ctx->cur_prec = PF_PREC_TF32;
+            nhist = 0;
+            PF_CUDA(launch_maxcut_lp_shadow(ctx->stream, ctx->ws, true, pr->rowptr, pr->colind,
+                                            pr->vals_f64, (int)pr->n, ctx->ws.p, pr->V, pr->ldv,
+                                            pr->theta, pr->lam, pr->Z_tf32, pr->ldz_tf32));
+          } else if (cur_lp(ctx)) {
+            ctx->cur_prec = PF_PREC_FP64;
             nhist = 0;
           }
         }

@@ -588,8 +588,9 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
 //                  block).  One MMA round per tile (K = 64, one exact chunk:
 //                  |level sums| <= 7 * 64 * 2^14), the 7 levels in 448 TMEM
 //                  columns; the epilogue folds them, scales to FP64, applies
-//                  -tC and -lam on the diagonal, accumulates
-//                  ||Z_old - Z||^2 and <C, X~>, stores Z and its digit planes.
+//                  -tC and -lam on the diagonal, accumulates <C, X~>,
+//                  stores Z and its digit planes (the old Z is not read: the
+//                  dual residual ||Z_old - Z|| comes from the factors).
 // The exponent of a (row i, 128-column chunk c) of the new Z comes from a
 // bound known before the product: X~ is PSD, so |X~_ij| <= sqrt(X~_ii X~_jj),
 // and |Z_ij| <= sqrt(X~_ii) max_{j in c} sqrt(X~_jj) + t max_{j in c} |C_ij|
@@ -840,24 +841,13 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
       uint32_t pk0[KS][XP_G / 2];
 #pragma unroll
       for (int g = 0; g < XP_CW; g += XP_G) {
-        // the group's old Z: independent loads, in flight while TMEM is read
-        // and the levels are folded.  Whole groups of an aligned Z move as
-        // two 32-byte vectors (a full sector per access: each lane of the
-        // warp holds another row)
+        // the group's new Z values, stored together: whole groups of an
+        // aligned Z leave as two 32-byte vectors (a full sector per access:
+        // each lane of the warp holds another row).  The old Z is not read:
+        // the dual residual comes from the factors (k_maxcut_kkt)
         double zo[XP_G];
         double *zrow = Z + (int64_t)(in ? row : 0) * ldz;
         const bool vec = zvec && j0 + g + XP_G <= n;  // the same for the whole warp
-        if (vec && in) {
-          ld_v4_f64(zrow + j0 + g, zo);
-          ld_v4_f64(zrow + j0 + g + 4, zo + 4);
-        }
-        if (!vec) {
-#pragma unroll
-          for (int i = 0; i < XP_G; ++i) {
-            const int col = j0 + g + i;
-            zo[i] = (in && col < n) ? zrow[col] : 0.0;
-          }
-        }
         // v = sum_l L_l 2^(36 - 8l), levels 5 and 6 rounded together, folded
         // in pairs of levels as they leave TMEM.  With K <= 64,
         // |L_l| <= (l + 1) 2^20, so L_0 2^8 + L_1, L_2 2^8 + L_3 and
@@ -911,8 +901,6 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
               ncol = e < e_hi ? colind[e] : INT_MAX;
             }
             if (col == row) z -= lam_r;
-            const double dz = zo[i] - z;
-            dsum = fma(dz, dz, dsum);
             zo[i] = z;  // the new value, stored with the group
             if (!vec) zrow[col] = z;
             if (ez_rc != kOzExpBad) zf = oz_fixed(z, ez_rc);

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NT) k_maxcut_lambda(const int32_t *__restrict_
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * WPB;
   const double t = prm->t;
-  double spinf = 0.0, slam = 0.0;
+  double spinf = 0.0, slam = 0.0, sdl2 = 0.0, sxl = 0.0;
   for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
     double dx = 0.0;
     for (int l = lane; l < p; l += 32) {
@@ -259,19 +259,32 @@ __global__ void __launch_bounds__(NT) k_maxcut_lambda(const int32_t *__restrict_
     for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32)
       if (colind[e] == row) cii += vals[e];
     cii = warp_sum(cii);
-    const double l_new = 2.0 * dx - Z[(int64_t)row * ldz + row] - t * cii - 1.0;
+    const double zii = Z[(int64_t)row * ldz + row];
+    const double l_new = 2.0 * dx - zii - t * cii - 1.0;
     if (lane == 0) {
+      // Z_k = X~_{k-1} - tC - Diag(lam_k), so X~_{k-1,ii} = Z_ii + t C_ii + lam_k,i; the
+      // diagonal terms of ||Z_k - Z_{k+1}||^2 = ||X~_{k-1} - X~_k - Diag(dl)||^2,
+      // dl = lam_k - lam_{k+1}
+      const double l_old = lam[row];
+      const double dl = l_old - l_new;
+      const double dxx = (zii + t * cii + l_old) - dx;
       lam[row] = l_new;
       if (xdiag != nullptr) xdiag[row] = dx;
       spinf = fma(dx - 1.0, dx - 1.0, spinf);
       slam += l_new;
+      sdl2 = fma(dl, dl, sdl2);
+      sxl = fma(dxx, dl, sxl);
     }
   }
   spinf = block_reduce(spinf, sh, 0);
   slam = block_reduce(slam, sh, 0);
+  sdl2 = block_reduce(sdl2, sh, 0);
+  sxl = block_reduce(sxl, sh, 0);
   if (threadIdx.x == 0) {
     red[blockIdx.x * kRedWidth + 0] = spinf;
     red[blockIdx.x * kRedWidth + 1] = slam;
+    red[blockIdx.x * kRedWidth + 2] = sdl2;
+    red[blockIdx.x * kRedWidth + 3] = sxl;
   }
 }
 
@@ -392,25 +405,56 @@ __global__ void __launch_bounds__(NT) k_maxcut_expand(const int32_t *__restrict_
   }
 }
 
+// Max-cut report.  dsum = ||Z_k - Z_{k+1}||_F^2 comes either from the
+// expansion's entrywise sums (red_exp[0]) or, when G = Vprev^T V is given,
+// from the factors: ||X~_{k-1} - X~_k||^2 = sum thp^2 + sum th^2
+// - 2 sum_ab thp_a th_b G_ab^2 (positive parts; both bases orthonormal), plus
+// the diagonal terms ||dl||^2 - 2 <diag(X~_{k-1} - X~_k), dl> from
+// k_maxcut_lambda.  The factor form cancels terms of size ||X~||^2, so it
+// carries a relative error of about u ||X~||^2 / ||Z_k - Z_{k+1}||^2.
 __global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ red_lam, int nb_lam,
                                                    const double *__restrict__ red_exp, int nb_exp,
                                                    const double *__restrict__ theta, int n, int p,
-                                                   Params *prm) {
+                                                   Params *prm, const double *__restrict__ gram,
+                                                   const double *__restrict__ thp) {
   __shared__ double sh[32];
-  double spinf = 0.0, slam = 0.0, dsum = 0.0, cx = 0.0;
+  double spinf = 0.0, slam = 0.0, dsum = 0.0, cx = 0.0, sdl2 = 0.0, sxl = 0.0, cross = 0.0;
   for (int q = threadIdx.x; q < nb_lam; q += NT) {
     spinf += red_lam[q * kRedWidth + 0];
     slam += red_lam[q * kRedWidth + 1];
+    sdl2 += red_lam[q * kRedWidth + 2];
+    sxl += red_lam[q * kRedWidth + 3];
   }
   for (int q = threadIdx.x; q < nb_exp; q += NT) {
     dsum += red_exp[q * kRedWidth + 0];
     cx += red_exp[q * kRedWidth + 1];
   }
+  if (gram != nullptr) {
+    for (int idx = threadIdx.x; idx < p * p; idx += NT) {
+      const int a = idx / p, b = idx % p;
+      const double wa = fmax(thp[a], 0.0), wb = fmax(theta[b], 0.0);
+      if (wa == 0.0 || wb == 0.0) continue;
+      const double m = gram[idx];
+      cross = fma(wa * wb, m * m, cross);
+    }
+  }
   spinf = block_reduce(spinf, sh, 0);
   slam = block_reduce(slam, sh, 0);
   dsum = block_reduce(dsum, sh, 0);
   cx = block_reduce(cx, sh, 0);
+  sdl2 = block_reduce(sdl2, sh, 0);
+  sxl = block_reduce(sxl, sh, 0);
+  cross = block_reduce(cross, sh, 0);
   if (threadIdx.x != 0) return;
+  if (gram != nullptr) {
+    double n1 = 0.0, n2 = 0.0;
+    for (int l = 0; l < p; ++l) {
+      const double wa = fmax(thp[l], 0.0), wb = fmax(theta[l], 0.0);
+      n1 = fma(wa, wa, n1);
+      n2 = fma(wb, wb, n2);
+    }
+    dsum = fmax(0.0, (n1 + n2 - 2.0 * cross) + sdl2 - 2.0 * sxl);
+  }
   const double t = prm->t;
   const double pinf = sqrt(spinf) / (1.0 + sqrt((double)n));
   const double dinf = sqrt(dsum) / (t * (1.0 + prm->Cnorm));
@@ -676,12 +720,18 @@ cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int3
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (sliced) {
+    // the dual residual from the factors (the previous Ritz pairs were saved
+    // to Vprev / thprev at the start of the step), so the expansion writes Z
+    // without reading the old one
+    int ng = 0;
+    e = launch_gram(s, ws, ws.Vprev, p, V, ldv, n, p, p, 0, &ng);
+    if (e != cudaSuccess) return e;
     int nbx = 0;
     e = launch_oz_expand(s, ws, rowptr, colind, vals, n, p, V, ldv, theta, lam, Z, ldz,
                          slot(ws, SLOT_EXPAND), &nbx);
     if (e != cudaSuccess) return e;
     k_maxcut_kkt<<<1, NT, 0, s>>>(slot(ws, SLOT_LAMBDA), nb1, slot(ws, SLOT_EXPAND), nbx, theta,
-                                  n, p, ws.prm);
+                                  n, p, ws.prm, ws.gpart, ws.thprev);
     PF_LAUNCHED();
     return cudaGetLastError();
   }
@@ -709,7 +759,7 @@ cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int3
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_maxcut_kkt<<<1, NT, 0, s>>>(slot(ws, SLOT_LAMBDA), nb1, slot(ws, SLOT_EXPAND), (int)nb2, theta,
-                                n, p, ws.prm);
+                                n, p, ws.prm, nullptr, nullptr);
   PF_LAUNCHED();
   return cudaGetLastError();
 }

