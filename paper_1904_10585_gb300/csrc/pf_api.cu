@@ -51,6 +51,10 @@ struct pf_ctx {
   void *oz_base;
   const void *oz_owner;
   int64_t oz_owner_n;
+  // the sliced dense max-cut problem (its lam) whose interval row bounds the
+  // interval slot holds, nullptr when unknown: each step of that problem
+  // leaves them for the next step
+  const void *ivl_owner;
   // phase tracing (pf_set_tracing): an event at each phase boundary of the
   // most recent call enqueued outside a stream capture
   bool trace;
@@ -200,8 +204,10 @@ pf_status ensure_oz(pf_ctx *ctx) {
                           (size_t)nz * sizeof(int),                        // ew
                           (size_t)nz * sizeof(int),                        // ev
                           (size_t)nz * sizeof(double),                     // xdiag
-                          (size_t)chunks * sizeof(double)};                // mchunk
-  constexpr int nbuf = 14;
+                          (size_t)chunks * sizeof(double),                 // mchunk
+                          (size_t)nz * sizeof(double),                     // cdiag
+                          (size_t)nz * sizeof(double)};                    // crsum
+  constexpr int nbuf = 16;
   size_t off[nbuf], tot = 0;
   for (int i = 0; i < nbuf; ++i) {
     off[i] = tot;
@@ -232,6 +238,8 @@ pf_status ensure_oz(pf_ctx *ctx) {
   oz.ev = (int *)(b + off[11]);
   oz.xdiag = (double *)(b + off[12]);
   oz.mchunk = (double *)(b + off[13]);
+  oz.cdiag = (double *)(b + off[14]);
+  oz.crsum = (double *)(b + off[15]);
   oz.ldk = nz;
   oz.slice_rows = nz;
   ctx->oz_base = base;
@@ -242,12 +250,23 @@ pf_status ensure_oz(pf_ctx *ctx) {
 // max-cut or NCE the planes of its current Z (sliced here, outside any
 // capture, unless they already hold it).
 pf_status oz_prepare_problem(pf_ctx *ctx, const pf_problem *pr) {
+  const bool ivl_kept = sliced_maxcut(ctx, pr) && pr->Z != nullptr;
+  if (!ivl_kept) ctx->ivl_owner = nullptr;
   if (!dense_f64_problem(ctx, pr)) return PF_OK;
   PF_TRY(ensure_oz(ctx));
   if (planes_kept(ctx, pr) && (ctx->oz_owner != pr->Z || ctx->oz_owner_n != pr->n)) {
     PF_CUDA(launch_oz_zslice(ctx->stream, ctx->ws, pr->Z, pr->ldz, (int)pr->n));
     ctx->oz_owner = pr->Z;
     ctx->oz_owner_n = pr->n;
+  }
+  if (ivl_kept && ctx->ivl_owner != pr->lam) {
+    // C's diagonal and row sums, and the first step's interval row bounds;
+    // from then on every step leaves the next step's bounds
+    PF_CUDA(launch_maxcut_cdata(ctx->stream, ctx->ws, pr->rowptr, pr->colind, pr->vals_f64,
+                                (int)pr->n));
+    PF_CUDA(launch_interval_rows(ctx->stream, ctx->ws, pr->rowptr, pr->colind, pr->vals_f64,
+                                 (int)pr->n, pr->lam));
+    ctx->ivl_owner = pr->lam;
   }
   return PF_OK;
 }
@@ -728,12 +747,18 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
                                       p, pr->V, pr->ldv, pr->theta, pr->lam, zlp_now, ldzlp_now));
   } else if (pr->kind == PF_PROBLEM_MAXCUT) {
     phase(ctx, PF_PHASE_INTERVAL);
-    // the sliced update takes the dual residual from the factors of the
-    // previous and the new X~: keep the previous Ritz pairs
-    if (ctx->opt.dense_product == PF_DENSE_SLICED)
+    if (ctx->opt.dense_product == PF_DENSE_SLICED) {
+      // the sliced update takes the dual residual from the factors of the
+      // previous and the new X~: keep the previous Ritz pairs.  The row
+      // bounds of the interval were left by the previous step's update (or
+      // by oz_prepare_problem); the chunk maxima of the expansion's bound
+      // start at zero
       PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
-    PF_CUDA(launch_interval(s, ws, PF_PROBLEM_MAXCUT, pr->rowptr, pr->colind, pr->vals_f64, n,
-                            pr->lam, pr->theta, p));
+      PF_CUDA(launch_interval_final(s, ws, n, pr->theta, p, ws.oz.mchunk, (n + 127) / 128));
+    } else {
+      PF_CUDA(launch_interval(s, ws, PF_PROBLEM_MAXCUT, pr->rowptr, pr->colind, pr->vals_f64, n,
+                              pr->lam, pr->theta, p));
+    }
     Op op = {};
     op.kind = PF_OP_DENSE;
     op.n = n;
@@ -1105,6 +1130,7 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
     PF_TRY(ensure_oz(ctx));
     ctx->oz_owner = nullptr;  // Z is set anew below
   }
+  ctx->ivl_owner = nullptr;  // so is lam
   if (pr->p_active == 0) pr->p_active = ctx->p;
   ctx->ws.p = ctx->p;  // the fills below cover every column
   const int n = (int)pr->n, p = ctx->p;

@@ -96,6 +96,9 @@ struct OzBuffers {
   int *ew, *ev;
   double *xdiag;
   double *mchunk;
+  // max-cut: C_ii and the off-diagonal |C| row sums of the problem whose
+  // steps run (for the update's next-interval bounds)
+  double *cdiag, *crsum;
 };
 
 struct Workspace {
@@ -205,6 +208,22 @@ cudaError_t launch_f32_to_f64(cudaStream_t s, const Workspace &ws, const float *
                               double *dst);
 
 // problem-level kernels
+// Gershgorin row bounds of the max-cut sparse part -tC - Diag(lam) into the
+// interval slot (red_blocks(n) partials), and the interval of the step from
+// them (choose_b of Sec. 4.1); the latter also zeroes `zero` (nzero doubles).
+cudaError_t launch_interval_rows(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                 const int32_t *colind, const double *vals, int n,
+                                 const double *lam);
+cudaError_t launch_interval_final(cudaStream_t s, const Workspace &ws, int n, const double *theta,
+                                  int p, double *zero, int nzero);
+// C_ii and the off-diagonal |C| row sums into ws.oz.cdiag / crsum.
+cudaError_t launch_maxcut_cdata(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                const int32_t *colind, const double *vals, int n);
+// The sliced max-cut update's row pass (k_oz_maxcut_rows), nb blocks.
+cudaError_t launch_oz_maxcut_rows(cudaStream_t s, const Workspace &ws, int n, int p,
+                                  const double *V, int64_t ldv, const double *theta,
+                                  const double *Z, int64_t ldz, double *lam, int nb,
+                                  double *red_lam, double *red_ivl);
 cudaError_t launch_interval(cudaStream_t s, const Workspace &ws, int kind, const int32_t *rowptr,
                             const int32_t *colind, const double *vals, int n, const double *lam,
                             const double *theta, int p);

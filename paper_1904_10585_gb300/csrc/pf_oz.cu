@@ -580,10 +580,11 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
 // rank-r+ expansion X~ = W V^T, W = V diag(max(theta, 0)), on the tensor
 // cores, producing the new Z = X~ - tC - Diag(lam) in FP64 together with its
 // digit planes for the next step's products:
-//   k_oz_lr_prep : digit planes of the rows of W and V (K = 64, zero beyond
-//                  p and for theta_l <= 0), their row exponents, sqrt(X~_ii)
-//                  in place of X~_ii, and per 128-row chunk the largest
-//                  sqrt(X~_jj);
+//   k_oz_maxcut_rows : lam of the DRS update, the report's row sums, the
+//                  next interval's row bounds, and the digit planes of the
+//                  rows of W and V (K = 64, zero beyond p and for
+//                  theta_l <= 0) with their row exponents, sqrt(X~_ii) and
+//                  per 128-row chunk the largest sqrt(X~_jj);
 //   k_oz_expand  : persistent over 128 x 64 output tiles (row block by row
 //                  block).  One MMA round per tile (K = 64, one exact chunk:
 //                  |level sums| <= 7 * 64 * 2^14), the 7 levels in 448 TMEM
@@ -609,57 +610,104 @@ constexpr int XP_W_BYTES = kOzSlices * OZ_A_BYTES;         // 7 W planes of a ro
 constexpr int XP_V_BYTES = kOzSlices * XP_TN * 128;        // 7 V planes of a column tile
 constexpr size_t XP_SMEM = 1024 + (size_t)XP_W_BYTES + XP_V_BYTES;
 
-__global__ void __launch_bounds__(OZ_BM) k_oz_lr_prep(
-    const double *__restrict__ V, int64_t ldv, const double *__restrict__ theta, int n, int p,
-    double *__restrict__ xdiag, __nv_bfloat16 *__restrict__ wp,
+// One warp per row of the sliced max-cut update (Eq. (PFAM1)), from the
+// Ritz pairs (V, theta) of the step:
+//   X~_ii = sum_l theta+_l V_il^2 and lam'_i = 2 X~_ii - Z_ii - t C_ii - 1
+//   (lam' replaces lam; Z_ii is the current iteration matrix's diagonal);
+//   the report's partial sums per block: ||diag X~ - 1||^2, sum lam', and the
+//   diagonal terms of ||Z_k - Z_{k+1}||^2 (Z_k = X~_{k-1} - tC - Diag(lam),
+//   so X~_{k-1,ii} = Z_ii + t C_ii + lam_i);
+//   the Gershgorin bounds of the next step's sparse part -tC - Diag(lam')
+//   (Sec. 4.1, reading R4; C_ii and the off-diagonal |C| row sums come
+//   precomputed);
+//   sqrt(X~_ii) and, per 128-row chunk, its maximum (for the expansion's
+//   exponent bound; the chunk maxima are zeroed at the start of the step);
+//   the digit planes of the rows of W = V diag(theta+) and V (K = 64, zero
+//   beyond p and where theta_l <= 0) with their row exponents.
+// Each warp accumulates its rows' sums in a fixed order; the block adds its
+// eight warps in order (no atomics on sums: the result is reproducible).
+__global__ void __launch_bounds__(256) k_oz_maxcut_rows(
+    int n, int p, const double *__restrict__ V, int64_t ldv, const double *__restrict__ theta,
+    const double *__restrict__ Z, int64_t ldz, double *__restrict__ lam,
+    const double *__restrict__ cdiag, const double *__restrict__ crsum,
+    const Params *__restrict__ prm, double *__restrict__ xdiag,
+    unsigned long long *__restrict__ mchunk_bits, __nv_bfloat16 *__restrict__ wp,
     __nv_bfloat16 *__restrict__ vp, int64_t plane_rows, int *__restrict__ ew,
-    int *__restrict__ ev, double *__restrict__ mchunk) {
+    int *__restrict__ ev, double *__restrict__ red_lam, double *__restrict__ red_ivl) {
   __shared__ double th[kMaxP];
-  __shared__ double sq[4];
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int row = blockIdx.x * OZ_BM + t;
-  const bool in = row < n;
-  if (t < kMaxP) th[t] = (t < p && theta[t] > 0.0) ? theta[t] : 0.0;
-  double r = in ? sqrt(fmax(xdiag[row], 0.0)) : 0.0;
-  if (in) xdiag[row] = r;  // the expansion reads sqrt(X~_ii)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-  if (lane == 0) sq[w] = r;
+  __shared__ double acc[8][6];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < kMaxP)
+    th[threadIdx.x] = (threadIdx.x < p && theta[threadIdx.x] > 0.0) ? theta[threadIdx.x] : 0.0;
   __syncthreads();
-  if (t == 0) mchunk[blockIdx.x] = fmax(fmax(sq[0], sq[1]), fmax(sq[2], sq[3]));
-  if (!in) return;
-  const double *vr = V + (int64_t)row * ldv;
-  unsigned fw = 0, fv = 0;
-  for (int l = 0; l < p; ++l) {
-    if (th[l] > 0.0) {
-      fw = max(fw, oz_exfield(vr[l] * th[l]));
-      fv = max(fv, oz_exfield(vr[l]));
-    }
-  }
-  const int e_w = oz_exponent(fw), e_v = oz_exponent(fv);
-  ew[row] = e_w;
-  ev[row] = e_v;
-  // digit planes of the rows of W (q = 0) and V (q = 1), 16 columns at a
-  // time: 32 bytes (a full sector) of each plane row per store
-  for (int q = 0; q < 2; ++q) {
-    const int e_q = q == 0 ? e_w : e_v;
-    __nv_bfloat16 *dst = q == 0 ? wp : vp;
-    for (int l0 = 0; l0 < 64; l0 += 16) {
-      uint32_t pk[kOzSlices][8];
+  const double t = prm->t;
+  const double t0 = th[lane], t1 = th[lane + 32];
+  const bool on0 = t0 > 0.0, on1 = t1 > 0.0;  // implies column < p
+  double spinf = 0.0, slam = 0.0, sdl2 = 0.0, sxl = 0.0, lo = INFINITY, hi = -INFINITY;
+  const int warps = gridDim.x * 8;
+  for (int row = blockIdx.x * 8 + w; row < n; row += warps) {
+    const double *vr = V + (int64_t)row * ldv;
+    const double v0 = lane < p ? vr[lane] : 0.0;
+    const double v1 = lane + 32 < p ? vr[lane + 32] : 0.0;
+    const double w0 = v0 * t0, w1 = v1 * t1;
+    const double dx = warp_sum(fma(w1, v1, w0 * v0));
+    unsigned fw = max(on0 ? oz_exfield(w0) : 0u, on1 ? oz_exfield(w1) : 0u);
+    unsigned fv = max(on0 ? oz_exfield(v0) : 0u, on1 ? oz_exfield(v1) : 0u);
+    fw = __reduce_max_sync(0xffffffffu, fw);
+    fv = __reduce_max_sync(0xffffffffu, fv);
+    const int e_w = oz_exponent(fw), e_v = oz_exponent(fv);
 #pragma unroll
-      for (int h = 0; h < 16; ++h) {
-        const int l = l0 + h;
-        const bool on = l < p && th[l] > 0.0 && e_q != kOzExpBad;
+    for (int q = 0; q < 2; ++q) {
+      const int e_q = q == 0 ? e_w : e_v;
+      __nv_bfloat16 *dst = (q == 0 ? wp : vp) + (int64_t)row * 64 + lane;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const double x = q == 0 ? (h ? w1 : w0) : (h ? v1 : v0);
+        const bool on = (h ? on1 : on0) && e_q != kOzExpBad;
         uint32_t d[kOzSlices];
-        oz_digit_bits(on ? oz_fixed(q == 0 ? vr[l] * th[l] : vr[l], e_q) : 0ll, d);
+        oz_digit_bits(on ? oz_fixed(x, e_q) : 0ll, d);
 #pragma unroll
         for (int s2 = 0; s2 < kOzSlices; ++s2)
-          pk[s2][h >> 1] = (h & 1) ? oz_pack2(pk[s2][h >> 1], d[s2]) : d[s2];
+          dst[(int64_t)s2 * plane_rows * 64 + 32 * h] = oz_bf16_of(d[s2]);
       }
-#pragma unroll
-      for (int s2 = 0; s2 < kOzSlices; ++s2)
-        st_v8_b32(dst + ((int64_t)s2 * plane_rows + row) * 64 + l0, pk[s2], pk[s2] + 4);
     }
+    if (lane == 0) {
+      ew[row] = e_w;
+      ev[row] = e_v;
+      const double zii = Z[(int64_t)row * ldz + row];
+      const double cii = cdiag[row];
+      const double l_old = lam[row];
+      const double l_new = 2.0 * dx - zii - t * cii - 1.0;
+      const double dl = l_old - l_new;
+      const double dxx = (zii + t * cii + l_old) - dx;
+      lam[row] = l_new;
+      const double r = sqrt(fmax(dx, 0.0));
+      xdiag[row] = r;
+      atomicMax(mchunk_bits + row / OZ_BM, (unsigned long long)__double_as_longlong(r));
+      spinf = fma(dx - 1.0, dx - 1.0, spinf);
+      slam += l_new;
+      sdl2 = fma(dl, dl, sdl2);
+      sxl = fma(dxx, dl, sxl);
+      const double dg = -t * cii - l_new, o = t * crsum[row];
+      lo = fmin(lo, dg - o);
+      hi = fmax(hi, dg + o);
+    }
+  }
+  if (lane == 0) {
+    acc[w][0] = spinf;
+    acc[w][1] = slam;
+    acc[w][2] = sdl2;
+    acc[w][3] = sxl;
+    acc[w][4] = lo;
+    acc[w][5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    double v = acc[0][k];
+    for (int q = 1; q < 8; ++q) v = k == 4 ? fmin(v, acc[q][k]) : (k == 5 ? fmax(v, acc[q][k]) : v + acc[q][k]);
+    if (k < 4) red_lam[blockIdx.x * kRedWidth + k] = v;
+    else red_ivl[blockIdx.x * kRedWidth + (k - 4)] = v;
   }
 }
 
@@ -1180,12 +1228,7 @@ cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t 
   const OzBuffers &oz = ws.oz;
   if (oz.zs == nullptr || oz.wp == nullptr || n > oz.slice_rows) return cudaErrorInvalidValue;
   const int R = (n + OZ_BM - 1) / OZ_BM;
-  k_oz_lr_prep<<<R, OZ_BM, 0, s>>>(V, ldv, theta, n, p, oz.xdiag, (__nv_bfloat16 *)oz.wp,
-                                   (__nv_bfloat16 *)oz.vp, oz.slice_rows, oz.ew, oz.ev,
-                                   oz.mchunk);
-  PF_LAUNCHED();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   CUtensorMap mw, mv;
   if ((e = encode_tile_map(&mw, oz.wp, false, (int64_t)kOzSlices * oz.slice_rows, 64, 64,
                            OZ_BM)) != cudaSuccess)
@@ -1204,6 +1247,20 @@ cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t 
       (int)(oz.ldk / OZ_BK), oz.ez, (int)(oz.slice_rows / OZ_BM), ws.prm, ws.prm, red);
   PF_LAUNCHED();
   *nblocks = grid;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_maxcut_rows(cudaStream_t s, const Workspace &ws, int n, int p,
+                                  const double *V, int64_t ldv, const double *theta,
+                                  const double *Z, int64_t ldz, double *lam, int nb,
+                                  double *red_lam, double *red_ivl) {
+  const OzBuffers &oz = ws.oz;
+  if (oz.wp == nullptr || n > oz.slice_rows) return cudaErrorInvalidValue;
+  k_oz_maxcut_rows<<<nb, 256, 0, s>>>(n, p, V, ldv, theta, Z, ldz, lam, oz.cdiag, oz.crsum,
+                                      ws.prm, oz.xdiag, (unsigned long long *)oz.mchunk,
+                                      (__nv_bfloat16 *)oz.wp, (__nv_bfloat16 *)oz.vp,
+                                      oz.slice_rows, oz.ew, oz.ev, red_lam, red_ivl);
+  PF_LAUNCHED();
   return cudaGetLastError();
 }
 

@@ -145,10 +145,38 @@ __global__ void __launch_bounds__(NT) k_interval_rows(int kind, const int32_t *_
   }
 }
 
+// C_ii and the off-diagonal |C| row sums (one warp per row; the same sums
+// in the same order as k_interval_rows).
+__global__ void __launch_bounds__(NT) k_maxcut_cdata(const int32_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ colind,
+                                                     const double *__restrict__ vals, int n,
+                                                     double *__restrict__ cdiag,
+                                                     double *__restrict__ crsum) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * WPB;
+  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
+    double dg = 0.0, off = 0.0;
+    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+      const double v = vals[e];
+      if (colind[e] == row) dg += v;
+      else off += fabs(v);
+    }
+    dg = warp_sum(dg);
+    off = warp_sum(off);
+    if (lane == 0) {
+      cdiag[row] = dg;
+      crsum[row] = off;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(NT) k_interval_final(const double *__restrict__ red, int nb,
                                                        const double *__restrict__ theta, int p,
-                                                       Params *prm, int use_lanczos) {
+                                                       Params *prm, int use_lanczos,
+                                                       double *__restrict__ zero = nullptr,
+                                                       int nzero = 0) {
   __shared__ double sh[32];
+  for (int i = threadIdx.x; i < nzero; i += NT) zero[i] = 0.0;
   double a = INFINITY, ubs = -INFINITY;
   for (int q = threadIdx.x; q < nb; q += NT) {
     a = fmin(a, red[q * kRedWidth + 0]);
@@ -417,44 +445,59 @@ __global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ re
                                                    const double *__restrict__ theta, int n, int p,
                                                    Params *prm, const double *__restrict__ gram,
                                                    const double *__restrict__ thp) {
-  __shared__ double sh[32];
-  double spinf = 0.0, slam = 0.0, dsum = 0.0, cx = 0.0, sdl2 = 0.0, sxl = 0.0, cross = 0.0;
-  for (int q = threadIdx.x; q < nb_lam; q += NT) {
-    spinf += red_lam[q * kRedWidth + 0];
-    slam += red_lam[q * kRedWidth + 1];
-    sdl2 += red_lam[q * kRedWidth + 2];
-    sxl += red_lam[q * kRedWidth + 3];
+  // eight sums reduced together (one pass through shared memory, in a fixed
+  // order): spinf, slam, sdl2, sxl, dsum, cx, cross, and n1 + n2 split as
+  // two values below
+  constexpr int K = 9;
+  __shared__ double sh[NT / 32][K];
+  __shared__ int rp_s;
+  double v[K] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int q = tid; q < nb_lam; q += NT) {
+    v[0] += red_lam[q * kRedWidth + 0];
+    v[1] += red_lam[q * kRedWidth + 1];
+    v[2] += red_lam[q * kRedWidth + 2];
+    v[3] += red_lam[q * kRedWidth + 3];
   }
-  for (int q = threadIdx.x; q < nb_exp; q += NT) {
-    dsum += red_exp[q * kRedWidth + 0];
-    cx += red_exp[q * kRedWidth + 1];
+  for (int q = tid; q < nb_exp; q += NT) {
+    v[4] += red_exp[q * kRedWidth + 0];
+    v[5] += red_exp[q * kRedWidth + 1];
   }
   if (gram != nullptr) {
-    for (int idx = threadIdx.x; idx < p * p; idx += NT) {
+    for (int idx = tid; idx < p * p; idx += NT) {
       const int a = idx / p, b = idx % p;
       const double wa = fmax(thp[a], 0.0), wb = fmax(theta[b], 0.0);
       if (wa == 0.0 || wb == 0.0) continue;
       const double m = gram[idx];
-      cross = fma(wa * wb, m * m, cross);
+      v[6] = fma(wa * wb, m * m, v[6]);
+    }
+    if (tid < p) {
+      const double wa = fmax(thp[tid], 0.0), wb = fmax(theta[tid], 0.0);
+      v[7] = wa * wa;
+      v[8] = wb * wb;
     }
   }
-  spinf = block_reduce(spinf, sh, 0);
-  slam = block_reduce(slam, sh, 0);
-  dsum = block_reduce(dsum, sh, 0);
-  cx = block_reduce(cx, sh, 0);
-  sdl2 = block_reduce(sdl2, sh, 0);
-  sxl = block_reduce(sxl, sh, 0);
-  cross = block_reduce(cross, sh, 0);
-  if (threadIdx.x != 0) return;
-  if (gram != nullptr) {
-    double n1 = 0.0, n2 = 0.0;
-    for (int l = 0; l < p; ++l) {
-      const double wa = fmax(thp[l], 0.0), wb = fmax(theta[l], 0.0);
-      n1 = fma(wa, wa, n1);
-      n2 = fma(wb, wb, n2);
-    }
-    dsum = fmax(0.0, (n1 + n2 - 2.0 * cross) + sdl2 - 2.0 * sxl);
+  if (tid == 0) {
+    int rp = 0;
+    for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
+    rp_s = rp;
   }
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
+  __syncthreads();
+  if (tid != 0) return;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double a = sh[0][k];
+    for (int w = 1; w < NT / 32; ++w) a += sh[w][k];
+    v[k] = a;
+  }
+  const double spinf = v[0], slam = v[1], sdl2 = v[2], sxl = v[3], cx = v[5], cross = v[6];
+  double dsum = v[4];
+  if (gram != nullptr) dsum = fmax(0.0, (v[7] + v[8] - 2.0 * cross) + sdl2 - 2.0 * sxl);
   const double t = prm->t;
   const double pinf = sqrt(spinf) / (1.0 + sqrt((double)n));
   const double dinf = sqrt(dsum) / (t * (1.0 + prm->Cnorm));
@@ -466,9 +509,7 @@ __global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ re
   prm->dinf = dinf;
   prm->gap = gap;
   prm->kkt = fmax(pinf, fmax(dinf, gap));
-  int rp = 0;
-  for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
-  prm->r_plus = rp;
+  prm->r_plus = rp_s;
   prm->theta_max = theta[0];
   prm->theta_min = theta[p - 1];
   prm->have_prev = 1;
@@ -642,6 +683,31 @@ cudaError_t launch_interval(cudaStream_t s, const Workspace &ws, int kind, const
   return cudaGetLastError();
 }
 
+cudaError_t launch_interval_rows(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                 const int32_t *colind, const double *vals, int n,
+                                 const double *lam) {
+  k_interval_rows<<<red_blocks(n, ws.num_sms), NT, 0, s>>>(PF_PROBLEM_MAXCUT, rowptr, colind, vals,
+                                                           n, lam, ws.prm, slot(ws, SLOT_INTERVAL));
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interval_final(cudaStream_t s, const Workspace &ws, int n, const double *theta,
+                                  int p, double *zero, int nzero) {
+  k_interval_final<<<1, NT, 0, s>>>(slot(ws, SLOT_INTERVAL), red_blocks(n, ws.num_sms), theta, p,
+                                    ws.prm, 0, zero, nzero);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxcut_cdata(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                const int32_t *colind, const double *vals, int n) {
+  k_maxcut_cdata<<<red_blocks(n, ws.num_sms), NT, 0, s>>>(rowptr, colind, vals, n, ws.oz.cdiag,
+                                                          ws.oz.crsum);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
 // Width growth (Sec. 4.2): columns [p_old, p_new) of U take the guard
 // columns of the same index, those of V become zero (the iterate, held by its
 // positive Ritz pairs, is unchanged), theta repeats its smallest value.
@@ -713,13 +779,13 @@ cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int3
                                  const double *V, int64_t ldv, const double *theta, double *Z,
                                  int64_t ldz, double *lam, bool sliced) {
   const int nb1 = red_blocks(n, ws.num_sms);
-  k_maxcut_lambda<<<nb1, NT, 0, s>>>(rowptr, colind, vals, n, p, V, ldv, theta, Z, ldz, lam,
-                                     ws.prm, slot(ws, SLOT_LAMBDA),
-                                     sliced ? ws.oz.xdiag : nullptr);
-  PF_LAUNCHED();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   if (sliced) {
+    // lam, the report's row sums, the next step's interval bounds and the
+    // digit planes of W and V in one pass over the rows
+    e = launch_oz_maxcut_rows(s, ws, n, p, V, ldv, theta, Z, ldz, lam, nb1,
+                              slot(ws, SLOT_LAMBDA), slot(ws, SLOT_INTERVAL));
+    if (e != cudaSuccess) return e;
     // the dual residual from the factors (the previous Ritz pairs were saved
     // to Vprev / thprev at the start of the step), so the expansion writes Z
     // without reading the old one
@@ -735,6 +801,11 @@ cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int3
     PF_LAUNCHED();
     return cudaGetLastError();
   }
+  k_maxcut_lambda<<<nb1, NT, 0, s>>>(rowptr, colind, vals, n, p, V, ldv, theta, Z, ldz, lam,
+                                     ws.prm, slot(ws, SLOT_LAMBDA), nullptr);
+  PF_LAUNCHED();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int64_t tiles1 = (n + EB - 1) / EB;
   int64_t nb2 = tiles1 * (tiles1 + 1) / 2;
   if (nb2 > kMaxRedBlocks) nb2 = kMaxRedBlocks;
