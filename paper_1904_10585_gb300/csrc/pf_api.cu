@@ -906,11 +906,12 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
     if (v > part) part = v;
   }
   const size_t sq = (size_t)kMaxP * kMaxP;
-  size_t off[16];
+  size_t off[20];
   size_t tot = 0;
   const size_t sizes[] = {np, np, np, np, part, (size_t)kMaxGramBlocks * sq,
                           (size_t)kRedSlots * kMaxRedBlocks * kRedWidth, sq, sq, sq, kMaxP, kMaxP,
-                          (size_t)n_max, (size_t)n_max, (size_t)(kLanczos + 2) * n_max};
+                          (size_t)n_max, (size_t)n_max, (size_t)(kLanczos + 2) * n_max,
+                          np /* Xs: n_max x p float pairs, 8 bytes each */};
   const int nsz = sizeof(sizes) / sizeof(sizes[0]);
   for (int i = 0; i < nsz; ++i) {
     off[i] = tot;
@@ -963,6 +964,7 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   ws.gdiag = (double *)(b + off[12]);
   ws.rsum = (double *)(b + off[13]);
   ws.lz = (double *)(b + off[14]);
+  ws.Xs = (float2 *)(b + off[15]);
   ws.prm = (Params *)(b + prm_off);
   ws.info = (pf_iter_info *)(b + info_off);
   ws.ldxt = ldxt;

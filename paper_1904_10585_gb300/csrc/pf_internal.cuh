@@ -107,6 +107,7 @@ struct Workspace {
   double *Y[2];           // filter recurrence buffers, n_max x p
   double *W;              // op(Q), n_max x p
   double *Vprev;          // previous Ritz vectors (completion), n_max x p
+  float2 *Xs;             // the sparse product's input block as float pairs, n_max x p
   double *part;           // split-K partials, kMaxSplitK x n_max x p
   double *gpart;          // Gram partials, kMaxGramBlocks x p x p
   double *red;            // reduction partials, kRedSlots x kMaxRedBlocks x kRedWidth
@@ -351,6 +352,73 @@ __device__ __forceinline__ double rcp_newton(double x) {
   y = fma(y, fma(-x, y, 1.0), y);
   y = fma(y, fma(-x, y, 1.0), y);
   return y;
+}
+
+// ---------------------------------------------------------------------------
+// FP64-accurate sums of products on the FP32 pipe (GB300 runs FP64 at 1/64
+// of FP32).  A double x is carried as an unevaluated pair of floats
+// x = x1 + x2 (+ at most 2^-49 |x|): x1 = fl32(x), x2 = fl32(x - x1).
+// Products of pairs are accumulated by the Dot2 scheme of Ogita, Rump and
+// Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005):
+// TwoProduct of the leading parts (exact through an FMA), TwoSum of the
+// running sum (Knuth), and the product errors with the first-order terms
+// x1 y2 + x2 y1 summed in plain fp32.  The result carries a relative error of
+// about 2^-47 of sum |x_k y_k| (an FP64 dot product of m terms: m 2^-53).
+// ---------------------------------------------------------------------------
+// The pair of x, with integer operations for 2^-60 <= |x| < 2^60 (the
+// conversion instructions from FP64 run on the slow FP64 pipe).
+__device__ __forceinline__ float2 df_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex < 1023 - 60 || ex >= 1023 + 60) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+  }
+  // x = m 2^(ex - 1075), m of 53 bits; x1 keeps the top 24 bits (rounded to
+  // nearest, ties to even), x2 = the rest (|rem| <= 2^28), rounded to 24 bits
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned hi = (unsigned)(m >> 29);
+  int rem = (int)(m & 0x1FFFFFFFull);
+  if (rem > (1 << 28) || (rem == (1 << 28) && (hi & 1u))) {
+    hi += 1u;
+    rem -= 1 << 29;
+  }
+  int e32 = ex - 896;  // float exponent field of hi 2^(ex - 1046), hi in [2^23, 2^24)
+  if (hi == (1u << 24)) {
+    hi >>= 1;
+    e32 += 1;
+  }
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const float x1 = __uint_as_float(sgn | ((unsigned)e32 << 23) | (hi & 0x7FFFFFu));
+  float x2 = 0.0f;
+  if (rem != 0) {
+    const float r = __int2float_rn(rem);  // |rem| <= 2^28: rounded to 24 bits
+    x2 = __uint_as_float((__float_as_uint(r) + ((unsigned)(ex - 1075) << 23)) ^ sgn);
+  }
+  return make_float2(x1, x2);
+}
+// Exact float -> double with integer operations (zero, subnormals and
+// non-finite values by the conversion).
+__device__ __forceinline__ double df_widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e8 = (u >> 23) & 0xFFu;
+  if (e8 == 0u || e8 == 0xFFu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e8 + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+// (a1, a2) += (s1 + s2)(x1 + x2)
+__device__ __forceinline__ void df_fma(float s1, float s2, float x1, float x2, float &a1,
+                                       float &a2) {
+  const float pp = __fmul_rn(s1, x1);
+  const float pe = __fmaf_rn(s1, x1, -pp);                        // s1 x1 = pp + pe
+  const float q = __fmaf_rn(s1, x2, __fmaf_rn(s2, x1, pe));
+  const float t = __fadd_rn(a1, pp);                              // a1 + pp = t + te
+  const float bp = __fsub_rn(t, a1);
+  const float te = __fadd_rn(__fsub_rn(a1, __fsub_rn(t, bp)), __fsub_rn(pp, bp));
+  a1 = t;
+  a2 = __fadd_rn(a2, __fadd_rn(te, q));
 }
 
 __device__ __forceinline__ double block_reduce(double v, double *sh, int op) {

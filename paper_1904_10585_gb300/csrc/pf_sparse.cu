@@ -24,13 +24,25 @@ constexpr int WPB = NT / 32;  // warps per block
 // which keeps the FP64 lanes busy.  The groups are combined by shuffles in a
 // fixed order.
 // ---------------------------------------------------------------------------
+// The block X (n x p, ldx) as float pairs (df_split), row-major with ld p.
+__global__ void k_split_pairs(const double *__restrict__ X, int64_t ldx, int n, int p,
+                              float2 *__restrict__ Xs) {
+  const int64_t total = (int64_t)n * p;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / p, j = idx - i * p;
+    Xs[idx] = df_split(X[i * ldx + j]);
+  }
+}
+
 template <int LW, int JG>
 __global__ void __launch_bounds__(NT) k_lrsp_apply(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const double *__restrict__ svals, int n, int p, const double *__restrict__ Uf, int64_t lduf,
     int r, const double *__restrict__ T, double sscale, double shift, const double *X, int64_t ldx,
     const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn, const Params *__restrict__ prm,
-    int mode, const int32_t *__restrict__ perm, const double *Xr, int64_t ldr) {
+    int mode, const int32_t *__restrict__ perm, const double *Xr, int64_t ldr,
+    const float2 *__restrict__ Xs) {
   constexpr int NQ = 32 / LW;
   __shared__ double Ts[kMaxP * kMaxP];
   for (int idx = threadIdx.x; idx < r * p; idx += NT) Ts[idx] = T[idx];
@@ -47,26 +59,37 @@ __global__ void __launch_bounds__(NT) k_lrsp_apply(
 #pragma unroll
     for (int g = 0; g < JG; ++g) acc[g] = lr[g] = 0.0;
     if (svals != nullptr) {
+      // the sparse sum on the FP32 pipe: entry values and the block (Xs, the
+      // pairs of X) as float pairs, accumulated by the Dot2 scheme
+      float a1[JG], a2[JG];
+#pragma unroll
+      for (int g = 0; g < JG; ++g) a1[g] = a2[g] = 0.0f;
       const int e0 = rowptr[row], e1 = rowptr[row + 1];
       for (int base = e0; base < e1; base += 32) {
         const int my = base + lane;
         const int mcol = my < e1 ? colind[my] : 0;
-        const double mv = my < e1 ? svals[perm != nullptr ? perm[my] : my] : 0.0;
+        const float2 mv = df_split(my < e1 ? svals[perm != nullptr ? perm[my] : my] : 0.0);
         const int cnt = min(32, e1 - base);
         for (int k = 0; k < cnt; k += NQ) {
           // group q takes entries q, q + NQ, ...; past the chunk's end
           // (kk >= cnt, always < 32 here) the source lane holds col 0, value 0
           const int kk = k + gq;
           const int col = __shfl_sync(0xffffffffu, mcol, kk);
-          const double v = __shfl_sync(0xffffffffu, mv, kk);
-          const double *xr = X + (int64_t)col * ldx;
+          const float v1 = __shfl_sync(0xffffffffu, mv.x, kk);
+          const float v2 = __shfl_sync(0xffffffffu, mv.y, kk);
+          const float2 *xr = Xs + (int64_t)col * p;
 #pragma unroll
           for (int g = 0; g < JG; ++g) {
             const int j = gl + LW * g;
-            if (j < p) acc[g] = fma(v, xr[j], acc[g]);
+            if (j < p) {
+              const float2 x = xr[j];
+              df_fma(v1, v2, x.x, x.y, a1[g], a2[g]);
+            }
           }
         }
       }
+#pragma unroll
+      for (int g = 0; g < JG; ++g) acc[g] = df_widen(a1[g]) + df_widen(a2[g]);
     }
     // the block of the shift and recurrence terms (the input unless given)
     const double *Xb = Xr != nullptr ? Xr : X;
@@ -634,6 +657,15 @@ cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, con
                                         const double *Xr, int64_t ldr) {
   const int n = op.n, p = ws.p;
   int r = op.r;
+  if (op.vals != nullptr) {
+    // the block as float pairs for the sparse sum (rows gathered by column)
+    int64_t nb = ((int64_t)n * p + 255) / 256;
+    if (nb > 8 * ws.num_sms) nb = 8 * ws.num_sms;
+    k_split_pairs<<<(int)nb, 256, 0, s>>>(X, ldx, n, p, ws.Xs);
+    PF_LAUNCHED();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (r > 0 && op.Uf != nullptr) {
     int nb = 0;
     const double *Rf = op.Vf != nullptr ? op.Vf : op.Uf;
@@ -651,7 +683,7 @@ cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, con
   k_lrsp_apply<LWV, JGV><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf,      \
                                                op.lduf, r, ws.T, op.sscale, op.shift, X, ldx,  \
                                                Yprev, ldp, Ynext, ldn, ws.prm, mode, op.perm,  \
-                                               Xr, ldr)
+                                               Xr, ldr, ws.Xs)
   // 8-lane groups where 8 x ceil(p/8) < 16 x ceil(p/16) (p = 24, 40: no idle lanes)
   if (p <= 8) { PF_LRSP(8, 1); }
   else if (p <= 16) { PF_LRSP(16, 1); }

@@ -5,9 +5,10 @@ from oracle/ only).
 
 For each precision the solve must end with an FP64-evaluated relative KKT
 residual <= 1e-4 and an objective within 1e-6 of f* (relative).  A KKT
-residual of 1e-4 alone does not fix the objective to 1e-6 (at the 1e-4
-crossing a DRS iterate can still be a few 1e-6 away), so the solves run to
-1e-5 and the report gives the error at both points.
+residual of 1e-4 alone does not fix the objective to 1e-6 (on the max-cut
+workload below the oracle's own iterate is 1.8e-6 away at the 1e-4 crossing
+and 4.5e-7 at 1e-5), so the max-cut solves run to 3e-6 and the completion
+solve to 1e-7, and the report gives the error at both points.
 
 Max-cut SDP, n = 2048, Erdos-Renyi p = 0.01 with +-1 weights, p = 64,
 degree 4 (the adaptive ladder may raise it to 8): the bf16 and the tf32
@@ -30,7 +31,7 @@ HERE = os.path.join(os.path.dirname(__file__), "golden")
 DEV = "cuda:0"
 KKT_GATE = 1e-4
 OBJ_GATE = 1e-6
-SOLVE_TOL = 1e-5
+SOLVE_TOL = 3e-6
 
 
 def _golden(name):
