@@ -778,9 +778,9 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
     PF_CUDA(launch_completion_residual(s, ws, pr->rowptr, pr->colind, pr->vals_f32, n, p, ws.Vprev,
                                        p, ws.thprev, pr->S));
+    // the residual kernel left the Gershgorin row bounds of -tS - t mu I
     phase(ctx, PF_PHASE_INTERVAL);
-    PF_CUDA(launch_interval(s, ws, PF_PROBLEM_COMPLETION, pr->rowptr, pr->colind, pr->S, n, nullptr,
-                            ws.thprev, p));
+    PF_CUDA(launch_interval_final(s, ws, n, ws.thprev, p, nullptr, 0));
     Op op = {};
     op.kind = PF_OP_LOWRANK_SPARSE;
     op.n = n;

@@ -28,8 +28,10 @@ __global__ void __launch_bounds__(NT) k_gram(const double *__restrict__ X, int64
                                              int cond_flag) {
   if (cond_flag && !(prm->flags & 1)) return;
   constexpr int TM = PT / 16, TN = PT / 16;
-  __shared__ double Xs[RC][PT + 1];
-  __shared__ double Ys[RC][PT + 1];
+  // rows staged as float pairs (df_split); each staged chunk of RC rows is
+  // summed on the FP32 pipe by the Dot2 scheme and added to FP64 accumulators
+  __shared__ float2 Xs[RC][PT + 1];
+  __shared__ float2 Ys[RC][PT + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   double acc[TM][TN];
 #pragma unroll
@@ -41,13 +43,18 @@ __global__ void __launch_bounds__(NT) k_gram(const double *__restrict__ X, int64
   for (int rb = r0; rb < r1; rb += RC) {
     for (int e = tid; e < RC * PT; e += NT) {
       const int r = e / PT, c = e % PT, gr = rb + r;
-      Xs[r][c] = (gr < r1 && c < px) ? X[(int64_t)gr * ldx + c] : 0.0;
-      Ys[r][c] = (gr < r1 && c < py) ? Y[(int64_t)gr * ldy + c] : 0.0;
+      Xs[r][c] = df_split((gr < r1 && c < px) ? X[(int64_t)gr * ldx + c] : 0.0);
+      Ys[r][c] = df_split((gr < r1 && c < py) ? Y[(int64_t)gr * ldy + c] : 0.0);
     }
     __syncthreads();
+    float s1[TM][TN], s2[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) s1[i][j] = s2[i][j] = 0.0f;
 #pragma unroll 4
     for (int r = 0; r < RC; ++r) {
-      double a[TM], b[TN];
+      float2 a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = Xs[r][ty * TM + i];
 #pragma unroll
@@ -57,9 +64,13 @@ __global__ void __launch_bounds__(NT) k_gram(const double *__restrict__ X, int64
         // rows of this warp: [2 w TM, 2 w TM + 2 TM); columns of group j: [16 j, 16 j + 16)
         if (SYM && 2 * (tid >> 5) * TM > 16 * j + 15) continue;
 #pragma unroll
-        for (int i = 0; i < TM; ++i) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int i = 0; i < TM; ++i) df_fma(a[i].x, a[i].y, b[j].x, b[j].y, s1[i][j], s2[i][j]);
       }
     }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] += df_widen(s1[i][j]) + df_widen(s2[i][j]);
     __syncthreads();
   }
   double *out = gpart + (int64_t)blockIdx.x * px * py;
@@ -229,13 +240,15 @@ __global__ void __launch_bounds__(NT) k_apply_right(const double *Y, int64_t ldy
                                                     int rows_per_block, const Params *prm,
                                                     int cond_flag) {
   if (cond_flag && !(prm->flags & 1)) return;
+  // R and the staged rows of Y as float pairs (df_split); each output is a
+  // dot product of at most p terms summed by the Dot2 scheme on the FP32 pipe
   extern __shared__ double dyn[];
-  double(*Rs)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(dyn);
-  double(*Ys)[PT + 1] = reinterpret_cast<double(*)[PT + 1]>(dyn + PT * (PT + 1));
+  float2(*Rs)[PT + 1] = reinterpret_cast<float2(*)[PT + 1]>(dyn);
+  float2(*Ys)[PT + 1] = reinterpret_cast<float2(*)[PT + 1]>(dyn + PT * (PT + 1));
   const int tid = threadIdx.x;
   for (int idx = tid; idx < PT * PT; idx += NT) {
     const int a = idx / PT, b = idx % PT;
-    Rs[a][b] = (a < p && b < p) ? R[a * p + b] : 0.0;
+    Rs[a][b] = df_split((a < p && b < p) ? R[a * p + b] : 0.0);
   }
   const int r0 = blockIdx.x * rows_per_block;
   const int r1 = min(n, r0 + rows_per_block);
@@ -243,7 +256,7 @@ __global__ void __launch_bounds__(NT) k_apply_right(const double *Y, int64_t ldy
     __syncthreads();
     for (int e = tid; e < RC * PT; e += NT) {
       const int r = e / PT, c = e % PT, gr = rb + r;
-      Ys[r][c] = (gr < r1 && c < p) ? Y[(int64_t)gr * ldy + c] : 0.0;
+      Ys[r][c] = df_split((gr < r1 && c < p) ? Y[(int64_t)gr * ldy + c] : 0.0);
     }
     __syncthreads();
     // warp w takes the CPW adjacent columns w CPW .. and lane l the column
@@ -258,19 +271,22 @@ __global__ void __launch_bounds__(NT) k_apply_right(const double *Y, int64_t ldy
     const int c = w * CPW + lane % CPW, rg = lane / CPW;
     const int kend = upper ? min(p, w * CPW + CPW) : p;  // the same for the whole warp
     if (w * CPW < p) {
-      double acc[U];
+      float a1[U], a2[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) acc[u] = 0.0;
+      for (int u = 0; u < U; ++u) a1[u] = a2[u] = 0.0f;
       for (int k = 0; k < kend; ++k) {
-        const double rk = Rs[k][c];  // zero below the diagonal and beyond p
+        const float2 rk = Rs[k][c];  // zero below the diagonal and beyond p
 #pragma unroll
-        for (int u = 0; u < U; ++u) acc[u] = fma(Ys[rg + RG * u][k], rk, acc[u]);
+        for (int u = 0; u < U; ++u) {
+          const float2 y = Ys[rg + RG * u][k];
+          df_fma(y.x, y.y, rk.x, rk.y, a1[u], a2[u]);
+        }
       }
       if (c < p) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int gr = rb + rg + RG * u;
-          if (gr < r1) Q[(int64_t)gr * ldq + c] = acc[u];
+          if (gr < r1) Q[(int64_t)gr * ldq + c] = df_widen(a1[u]) + df_widen(a2[u]);
         }
       }
     }

@@ -541,32 +541,88 @@ __global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ re
 // ---------------------------------------------------------------------------
 // PSD completion: S = P_Omega(X - M) with X = V diag(max(theta,0)) V^T.
 // ---------------------------------------------------------------------------
+// S = P_Omega(X - M) with X = V diag(max(theta, 0)) V^T (one warp per row,
+// a lane per entry), its squared norm, and the Gershgorin row bounds of the
+// step's sparse part -tS - t mu I (Sec. 4.1, reading R4) for the interval.
+// Each entry's r_+-term dot product runs on the FP32 pipe by the Dot2 scheme
+// (the row's W = V theta+ and the pairs Vs of V as float pairs), so does
+// s = x - M (M is exact in fp32) and the |S| row sums; S is stored in FP64.
 __global__ void __launch_bounds__(NT) k_completion_residual(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const float *__restrict__ mvals, int n, int p, const double *__restrict__ V, int64_t ldv,
-    const double *__restrict__ theta, double *__restrict__ S, double *__restrict__ red) {
-  __shared__ double wv[WPB][kMaxP];
+    const double *__restrict__ theta, const float2 *__restrict__ Vs, double *__restrict__ S,
+    double *__restrict__ red, double *__restrict__ red_ivl, const Params *__restrict__ prm) {
+  __shared__ float2 wv[WPB][kMaxP];
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int warps = gridDim.x * WPB;
   int rp = 0;
   for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
-  double ssq = 0.0;
+  const double t = prm->t, mu = prm->mu;
+  float q1 = 0.0f, q2 = 0.0f;  // sum of s^2
+  double lo = INFINITY, hi = -INFINITY;
   for (int row = blockIdx.x * WPB + w; row < n; row += warps) {
-    for (int l = lane; l < rp; l += 32) wv[w][l] = V[(int64_t)row * ldv + l] * theta[l];
+    for (int l = lane; l < rp; l += 32) wv[w][l] = df_split(V[(int64_t)row * ldv + l] * theta[l]);
     __syncwarp();
+    float o1 = 0.0f, o2 = 0.0f;  // sum of |S_ij|, j != i
+    double dg = 0.0;
     for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
       const int col = colind[e];
-      double x = 0.0;
-      for (int l = 0; l < rp; ++l) x = fma(wv[w][l], V[(int64_t)col * ldv + l], x);
-      const double s = x - (double)mvals[e];
-      S[e] = s;
-      ssq = fma(s, s, ssq);
+      const float2 *vc = Vs + (int64_t)col * p;
+      float a1 = 0.0f, a2 = 0.0f;
+      for (int l = 0; l < rp; ++l) {
+        const float2 x = vc[l];
+        df_fma(wv[w][l].x, wv[w][l].y, x.x, x.y, a1, a2);
+      }
+      // s = (a1 + a2) - M by TwoSum of a1 and -M
+      const float m = -mvals[e];
+      const float s1 = __fadd_rn(a1, m);
+      const float bp = __fsub_rn(s1, a1);
+      const float s2 = __fadd_rn(a2, __fadd_rn(__fsub_rn(a1, __fsub_rn(s1, bp)), __fsub_rn(m, bp)));
+      const double sv = df_widen(s1) + df_widen(s2);
+      S[e] = sv;
+      df_fma(s1, s2, s1, s2, q1, q2);
+      if (col == row) {
+        dg += sv;
+      } else {
+        // |s| as a pair (s1 = 0 leaves s = s2)
+        const float u1 = s1 != 0.0f ? fabsf(s1) : fabsf(s2);
+        const float u2 = s1 != 0.0f ? (s1 < 0.0f ? -s2 : s2) : 0.0f;
+        const float tt = __fadd_rn(o1, u1);
+        const float b2 = __fsub_rn(tt, o1);
+        o2 = __fadd_rn(o2, __fadd_rn(__fadd_rn(__fsub_rn(o1, __fsub_rn(tt, b2)),
+                                               __fsub_rn(u1, b2)), u2));
+        o1 = tt;
+      }
+    }
+    // the row's sums over the warp (pairs by TwoSum, the diagonal is in one lane)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float b1 = __shfl_xor_sync(0xffffffffu, o1, off);
+      const float c2 = __shfl_xor_sync(0xffffffffu, o2, off);
+      const float tt = __fadd_rn(o1, b1);
+      const float bb = __fsub_rn(tt, o1);
+      o2 = __fadd_rn(__fadd_rn(o2, c2), __fadd_rn(__fsub_rn(o1, __fsub_rn(tt, bb)), __fsub_rn(b1, bb)));
+      o1 = tt;
+    }
+    const unsigned has = __ballot_sync(0xffffffffu, dg != 0.0);
+    dg = has ? __shfl_sync(0xffffffffu, dg, __ffs(has) - 1) : 0.0;
+    if (lane == 0) {
+      const double d = -t * dg - t * mu, o = t * (df_widen(o1) + df_widen(o2));
+      lo = fmin(lo, d - o);
+      hi = fmax(hi, d + o);
     }
     __syncwarp();
   }
+  double ssq = df_widen(q1) + df_widen(q2);
   ssq = block_reduce(ssq, sh, 0);
-  if (threadIdx.x == 0) red[blockIdx.x * kRedWidth] = ssq;
+  lo = block_reduce(lo, sh, 1);
+  hi = block_reduce(hi, sh, 2);
+  if (threadIdx.x == 0) {
+    red[blockIdx.x * kRedWidth] = ssq;
+    red_ivl[blockIdx.x * kRedWidth + 0] = lo;
+    red_ivl[blockIdx.x * kRedWidth + 1] = hi;
+  }
 }
 
 __global__ void k_save_prev(const double *__restrict__ V, int64_t ldv, const double *theta, int n,
@@ -871,9 +927,16 @@ cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, cons
                                        const int32_t *colind, const float *mvals, int n, int p,
                                        const double *V, int64_t ldv, const double *theta,
                                        double *S) {
+  // V as float pairs (the rows the entries gather), then the entries
+  int64_t ns = ((int64_t)n * p + 255) / 256;
+  if (ns > 8 * ws.num_sms) ns = 8 * ws.num_sms;
+  k_split_pairs<<<(int)ns, 256, 0, s>>>(V, ldv, n, p, ws.Xs);
+  PF_LAUNCHED();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int nb = red_blocks(n, ws.num_sms);
-  k_completion_residual<<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, V, ldv, theta, S,
-                                          slot(ws, SLOT_SDDMM));
+  k_completion_residual<<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, V, ldv, theta, ws.Xs, S,
+                                          slot(ws, SLOT_SDDMM), slot(ws, SLOT_INTERVAL), ws.prm);
   PF_LAUNCHED();
   return cudaGetLastError();
 }

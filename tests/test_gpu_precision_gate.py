@@ -56,14 +56,27 @@ def _trace_solve(S, ctx, pr, tol, max_iter, every=10):
     return trace
 
 
+PREC_NAME = {0: "fp64", 1: "tf32", 2: "bf16"}
+
+
 def _report(name, trace, f_star):
     first = next((t for t in trace if t[1] <= KKT_GATE), None)
     it, kkt, obj, prec, deg = trace[-1]
     err = abs(obj - f_star) / abs(f_star)
     err_gate = abs(first[2] - f_star) / abs(f_star) if first else float("nan")
+    # the ladder's rungs: (precision, degree) and the iterations each ran
+    rungs, prev, start = [], None, 0
+    for t in trace:
+        key = (PREC_NAME.get(t[3], t[3]), t[4])
+        if key != prev:
+            if prev is not None:
+                rungs.append(f"{prev[0]}/d{prev[1]} {start}-{t[0] - 10}")
+            prev, start = key, t[0] - 10
+    rungs.append(f"{prev[0]}/d{prev[1]} {start}-{it}")
     print(f"\n{name}: {it} iterations, kkt {kkt:.2e}, obj {obj:.12g}, f* {f_star:.12g}, "
-          f"relative error {err:.2e} (at the KKT 1e-4 crossing, iteration "
-          f"{first[0] if first else None}: {err_gate:.2e}); final precision {prec}, degree {deg}")
+          f"relative error {err:.2e}; at the KKT 1e-4 crossing (iteration "
+          f"{first[0] if first else None}, {PREC_NAME.get(first[3]) if first else None}): "
+          f"{err_gate:.2e}; rungs: {', '.join(rungs)}")
     return kkt, err
 
 
