@@ -92,7 +92,7 @@ typedef struct {
                         /* this build accepts; Eqs. (pfpg2)/(PFAM2) allow 1..3)       */
   double eta;           /* interval parameter of Sec. 4.1 (0 < eta < 1), e.g. 0.1    */
   int32_t precision;    /* pf_precision of the filter products                       */
-  int32_t adaptive;     /* nonzero: raise degree/precision when the KKT stalls        */
+  int32_t adaptive;     /* nonzero: raise precision, then degree, when the KKT stalls  */
   /* Block width rule (Sec. 4.2), FP64 contexts: with adapt_guard > 0, after
    * every adapt_every-th step of a problem its active width becomes
    * min(p, max(p_min, r_+ + adapt_guard)) rounded up to a multiple of 8,
@@ -295,7 +295,8 @@ pf_status pf_prox_step(pf_ctx *ctx, pf_problem *prob, pf_iter_info *info);
 
 /* Iterate pf_prox_step until kkt <= tol (checked every check_every steps,
  * tol <= 0 disables the test) or max_iter steps.  The step is captured once
- * in a CUDA graph and replayed.  out (host) receives the final report.
+ * in a CUDA graph and replayed.  An adaptive context feeds every check to
+ * the ladder (pf_ladder_update).  out (host) receives the final report.
  * Returns PF_ERR_NOT_CONVERGED if tol > 0 was not reached. */
 pf_status pf_solve(pf_ctx *ctx, pf_problem *prob, int64_t max_iter, double tol,
                    int32_t check_every, pf_result *out);
@@ -305,9 +306,21 @@ pf_status pf_get_info(pf_ctx *ctx, pf_iter_info *info);
 
 /* Enqueue n_steps iterations of pf_prox_step (replays of the step's CUDA
  * graph when the stream is not the legacy default stream) and return without
- * synchronising.  The adaptive ladder is not applied.  Used by request loops
- * that keep several solves in flight on different streams. */
+ * synchronising.  The adaptive ladder is applied only through
+ * pf_ladder_update.  Used by request loops that keep several solves in
+ * flight on different streams. */
 pf_status pf_enqueue_steps(pf_ctx *ctx, pf_problem *prob, int64_t n_steps);
+
+/* Feed the KKT residual of a check (e.g. from a pf_report_async report) to
+ * the adaptive ladder of an adaptive context (options.adaptive != 0; a no-op
+ * otherwise), as pf_solve does at each of its checks.  The ladder has
+ * stalled when the best of the last 5 checks is not 5% below the best of the
+ * 5 checks before; a stall moves a low-precision filter up one precision
+ * (bf16 -> tf32 when the problem carries Z_tf32 -> FP64), and in FP64 raises
+ * the degree by one up to degree_max.  The ladder's state belongs to the
+ * context and restarts at pf_problem_init.  May enqueue the tf32 shadow's
+ * fill on the context's stream. */
+pf_status pf_ladder_update(pf_ctx *ctx, pf_problem *prob, double kkt);
 
 /* Enqueue a copy of the latest step report into `info` (host memory owned
  * by the caller; page-locked memory keeps the copy asynchronous).  The

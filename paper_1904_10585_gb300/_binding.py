@@ -116,6 +116,7 @@ def _load():
         "pf_get_info": (C.c_int, [P, C.POINTER(pf_iter_info)]),
         "pf_enqueue_steps": (C.c_int, [P, C.POINTER(pf_problem), C.c_int64]),
         "pf_report_async": (C.c_int, [P, P]),
+        "pf_ladder_update": (C.c_int, [P, C.POINTER(pf_problem), C.c_double]),
         "pf_set_tracing": (C.c_int, [P, C.c_int32]),
         "pf_phase_times": (C.c_int, [P, C.POINTER(C.c_double)]),
         "pf_set_wait_limit": (C.c_int, [C.c_uint64]),
@@ -133,7 +134,8 @@ _lib = _load()
 EXPORTED = ("pf_create", "pf_destroy", "pf_filter", "pf_rayleigh_ritz", "pf_apply",
             "pf_problem_init", "pf_prox_step", "pf_solve", "pf_get_info", "pf_enqueue_steps",
             "pf_report_async",
-            "pf_kernel_launch_count", "pf_apply_dense_noalloc", "pf_set_tracing",
+            "pf_kernel_launch_count", "pf_apply_dense_noalloc", "pf_ladder_update",
+            "pf_set_tracing",
             "pf_phase_times", "pf_set_wait_limit", "pf_status_string", "pf_last_error")
 
 # pf_phase (include/pf.h)
@@ -239,6 +241,10 @@ def pf_get_info(ctx) -> pf_iter_info:
     info = pf_iter_info()
     _check(_lib.pf_get_info(ctx, C.byref(info)), ctx)
     return info
+
+
+def pf_ladder_update(ctx, prob: pf_problem, kkt: float) -> None:
+    _check(_lib.pf_ladder_update(ctx, C.byref(prob), float(kkt)), ctx)
 
 
 def pf_set_tracing(ctx, on: bool) -> None:

@@ -42,9 +42,9 @@ struct pf_ctx {
   // currently used
   int cur_degree;
   int cur_prec;
-  // KKT residuals at the last (up to 5) checks of the ladder; kept across
-  // pf_solve calls so that a solve run in pieces climbs the same ladder
-  double ladder_hist[5];
+  // KKT residuals at the last (up to kLadderWin) checks of the ladder; kept
+  // across calls so that a solve run in pieces climbs the same ladder
+  double ladder_hist[10];
   int ladder_n;
   // digit planes of the sliced dense product (allocated on first use) and
   // the matrix (pointer, n) they currently hold, nullptr when unknown
@@ -847,6 +847,50 @@ bool graph_matches(const pf_ctx *ctx, const pf_problem &pr) {
 
 
 
+// The adaptive ladder (spec precision pattern; readings in the design
+// notes): a KKT residual read at a check joins the history; the solve has
+// stalled when the best of the last 5 checks is not 5% below the best of the
+// 5 checks before (the KKT residual of DRS is not monotone, and comparing
+// single checks fires on its plateaus).  A stall moves a low-precision filter
+// up one precision (bf16 -> tf32 when the problem carries the fp32 shadow ->
+// FP64): a filter's precision sets a floor on the KKT residual that a higher
+// degree does not remove.  In FP64 a stall raises the degree by one, up to
+// degree_max.  Each move clears the history.
+pf_status ladder_feed(pf_ctx *ctx, const pf_problem *pr, double kkt) {
+  constexpr int W = 5;
+  double *hist = ctx->ladder_hist;
+  int &nh = ctx->ladder_n;
+  if (nh == 2 * W) {
+    for (int i = 0; i < 2 * W - 1; ++i) hist[i] = hist[i + 1];
+    nh = 2 * W - 1;
+  }
+  hist[nh++] = kkt;
+  if (nh < 2 * W) return PF_OK;
+  double before = hist[0], recent = hist[W];
+  for (int i = 1; i < W; ++i) {
+    before = fmin(before, hist[i]);
+    recent = fmin(recent, hist[W + i]);
+  }
+  if (recent < 0.95 * before) return PF_OK;
+  const int dmax = ctx->opt.degree_max > ctx->opt.degree ? ctx->opt.degree_max : ctx->opt.degree;
+  if (ctx->cur_prec == PF_PREC_BF16 && pr->kind == PF_PROBLEM_MAXCUT && pr->Z_tf32 != nullptr) {
+    // tf32 rung: the fp32 shadow of the current iteration matrix, written
+    // now from the state the bf16 steps left
+    ctx->cur_prec = PF_PREC_TF32;
+    PF_CUDA(launch_maxcut_lp_shadow(ctx->stream, ctx->ws, true, pr->rowptr, pr->colind,
+                                    pr->vals_f64, (int)pr->n, ctx->ws.p, pr->V, pr->ldv,
+                                    pr->theta, pr->lam, pr->Z_tf32, pr->ldz_tf32));
+  } else if (cur_lp(ctx)) {
+    ctx->cur_prec = PF_PREC_FP64;
+  } else if (ctx->cur_degree < dmax) {
+    ctx->cur_degree += 1;
+  } else {
+    return PF_OK;
+  }
+  nh = 0;
+  return PF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1034,6 +1078,14 @@ pf_status pf_phase_times(pf_ctx *ctx, double *ms) {
     ms[ctx->tmark[i]] += (double)t;
   }
   return PF_OK;
+}
+
+pf_status pf_ladder_update(pf_ctx *ctx, pf_problem *pr, double kkt) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  PF_TRY(check_problem(ctx, pr));
+  if (ctx->opt.adaptive == 0) return PF_OK;
+  if (!std::isfinite(kkt)) return set_err(ctx, PF_ERR_INVALID_ARG, "kkt must be finite");
+  return ladder_feed(ctx, pr, kkt);
 }
 
 pf_status pf_set_wait_limit(uint64_t ns) {
@@ -1306,13 +1358,9 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
   if (max_iter < 0) return set_err(ctx, PF_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (check_every < 1) check_every = 1;
   const bool use_graph = ctx->stream != nullptr;
-  // adaptive ladder: KKT history at the checks; a stall (< 5% decrease over
-  // the last 5 checks) raises the degree by one up to degree_max, then drops
-  // the low-precision filter for the FP64 one
+  // adaptive ladder (ladder_feed) at every check
   const bool adaptive = ctx->opt.adaptive != 0;
   const bool check = tol > 0.0 || adaptive;
-  double *hist = ctx->ladder_hist;
-  int &nhist = ctx->ladder_n;
   Params h = {};
   int64_t it = 0;
   bool converged = false;
@@ -1335,33 +1383,7 @@ pf_status pf_solve(pf_ctx *ctx, pf_problem *pr, int64_t max_iter, double tol, in
         converged = true;
         break;
       }
-      if (adaptive) {
-        if (nhist == 5) {
-          for (int i = 0; i < 4; ++i) hist[i] = hist[i + 1];
-          nhist = 4;
-        }
-        hist[nhist++] = h.kkt;
-        if (nhist == 5 && !(hist[4] < 0.95 * hist[0])) {
-          const int dmax = ctx->opt.degree_max > ctx->opt.degree ? ctx->opt.degree_max
-                                                                 : ctx->opt.degree;
-          if (ctx->cur_degree < dmax) {
-            ctx->cur_degree += 1;
-            nhist = 0;
-          } else if (ctx->cur_prec == PF_PREC_BF16 && pr->kind == PF_PROBLEM_MAXCUT &&
-                     pr->Z_tf32 != nullptr) {
-            // tf32 rung: the fp32 shadow of the current iteration matrix,
-            // written now from the state the bf16 steps left
-            ctx->cur_prec = PF_PREC_TF32;
-            nhist = 0;
-            PF_CUDA(launch_maxcut_lp_shadow(ctx->stream, ctx->ws, true, pr->rowptr, pr->colind,
-                                            pr->vals_f64, (int)pr->n, ctx->ws.p, pr->V, pr->ldv,
-                                            pr->theta, pr->lam, pr->Z_tf32, pr->ldz_tf32));
-          } else if (cur_lp(ctx)) {
-            ctx->cur_prec = PF_PREC_FP64;
-            nhist = 0;
-          }
-        }
-      }
+      if (adaptive) PF_TRY(ladder_feed(ctx, pr, h.kkt));
     }
     if (rule_now) PF_TRY(apply_width_rule(ctx, pr));
   }

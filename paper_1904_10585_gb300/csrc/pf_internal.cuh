@@ -369,6 +369,7 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // conversion instructions from FP64 run on the slow FP64 pipe).
 __device__ __forceinline__ float2 df_split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  if ((b << 1) == 0ull) return make_float2(0.0f, 0.0f);  // +-0 (padding, zero entries)
   const int ex = (int)((b >> 52) & 0x7FF);
   if (ex < 1023 - 60 || ex >= 1023 + 60) {
     const float h = __double2float_rn(x);
@@ -407,6 +408,14 @@ __device__ __forceinline__ double df_widen(float f) {
                                ((unsigned long long)(e8 + 896u) << 52) |
                                ((unsigned long long)(u & 0x7FFFFFu) << 29);
   return __longlong_as_double((long long)d);
+}
+// (a1, a2) += (b1, b2)
+__device__ __forceinline__ void df_add(float b1, float b2, float &a1, float &a2) {
+  const float t = __fadd_rn(a1, b1);
+  const float bp = __fsub_rn(t, a1);
+  const float te = __fadd_rn(__fsub_rn(a1, __fsub_rn(t, bp)), __fsub_rn(b1, bp));
+  a1 = t;
+  a2 = __fadd_rn(a2, __fadd_rn(te, b2));
 }
 // (a1, a2) += (s1 + s2)(x1 + x2)
 __device__ __forceinline__ void df_fma(float s1, float s2, float x1, float x2, float &a1,

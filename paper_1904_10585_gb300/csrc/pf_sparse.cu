@@ -566,14 +566,28 @@ __global__ void __launch_bounds__(NT) k_completion_residual(
     __syncwarp();
     float o1 = 0.0f, o2 = 0.0f;  // sum of |S_ij|, j != i
     double dg = 0.0;
-    for (int e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
-      const int col = colind[e];
+    // four lanes per entry (terms l = gl, gl + 4, ...: each row of Vs is read
+    // as contiguous 32-byte pieces), eight entries per step
+    const int gq = lane >> 2, gl = lane & 3;
+    const int e1 = rowptr[row + 1];
+    for (int base = rowptr[row]; base < e1; base += 8) {
+      const int e = base + gq;
+      const bool valid = e < e1;
+      const int col = valid ? colind[e] : 0;
       const float2 *vc = Vs + (int64_t)col * p;
       float a1 = 0.0f, a2 = 0.0f;
-      for (int l = 0; l < rp; ++l) {
-        const float2 x = vc[l];
-        df_fma(wv[w][l].x, wv[w][l].y, x.x, x.y, a1, a2);
+      if (valid)
+        for (int l = gl; l < rp; l += 4) {
+          const float2 x = vc[l];
+          df_fma(wv[w][l].x, wv[w][l].y, x.x, x.y, a1, a2);
+        }
+#pragma unroll
+      for (int off = 2; off > 0; off >>= 1) {
+        const float b1 = __shfl_xor_sync(0xffffffffu, a1, off);
+        const float b2 = __shfl_xor_sync(0xffffffffu, a2, off);
+        df_add(b1, b2, a1, a2);
       }
+      if (!valid || gl != 0) continue;
       // s = (a1 + a2) - M by TwoSum of a1 and -M
       const float m = -mvals[e];
       const float s1 = __fadd_rn(a1, m);

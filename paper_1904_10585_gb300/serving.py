@@ -70,11 +70,16 @@ class Result:
 
 
 class _Slot:
-    def __init__(self, kind: str, p: int, n_max: int, degree: int, precision: int, dev):
+    def __init__(self, kind: str, p: int, n_max: int, degree: int, precision: int, dev,
+                 degree_max: int = 0):
         self.kind, self.p, self.n_max, self.precision = kind, p, n_max, precision
         self.stream = torch.cuda.Stream(device=dev)
+        # a low-precision slot climbs the adaptive ladder (to FP64 when its
+        # filter's precision floor stalls the KKT residual)
+        adaptive = 1 if precision != B.PF_PREC_FP64 else 0
         self.ctx = S.Context(p=p, n_max=n_max, degree=degree, precision=precision,
-                             stream=self.stream)
+                             stream=self.stream, adaptive=adaptive,
+                             degree_max=degree_max or degree)
         self.info_buf = torch.empty(ctypes.sizeof(B.pf_iter_info), dtype=torch.uint8).pin_memory()
         self.info = B.pf_iter_info.from_address(self.info_buf.data_ptr())
         self.event = torch.cuda.Event()
@@ -162,8 +167,10 @@ class Server:
         slot.steps = 0
         self._advance(slot)
 
-    def _advance(self, slot: _Slot):
+    def _advance(self, slot: _Slot, kkt: Optional[float] = None):
         r = slot.req
+        if kkt is not None and math.isfinite(kkt):
+            B.pf_ladder_update(slot.ctx.handle, slot.prob.struct, kkt)
         k = min(self.chunk, r.max_iter - slot.steps)
         B.pf_enqueue_steps(slot.ctx.handle, slot.prob.struct, k)
         slot.steps += k
@@ -226,7 +233,7 @@ class Server:
                 if done:
                     results.append(self._retire(slot, time.perf_counter() - t0))
                 else:
-                    self._advance(slot)
+                    self._advance(slot, float(info.kkt))
             if not progressed:
                 time.sleep(20e-6)
         return results

@@ -99,25 +99,33 @@ def test_lowprec_shadow_matches_state(S, lowprec, p, n):
     assert err <= tol, err
 
 
-def test_adaptive_ladder_raises_degree_then_drops_to_fp64(S):
+def test_adaptive_ladder_raises_precision_then_degree(S):
     """pf_solve with the adaptive ladder: once the FP64-evaluated KKT stops
     decreasing (here: a small solve run far past its accuracy floor), the
-    degree rises to degree_max and then the bf16 filter is replaced by the
-    FP64 one.  The solve itself stays correct (objective close to the plain
-    FP64 solve)."""
+    bf16 filter is replaced by the FP64 one first (a filter's precision floor
+    is not lifted by a higher degree), and only then does the degree rise to
+    degree_max.  The ladder's state carries across pf_solve calls, so the
+    solve is run in pieces of 10 steps to record the order.  The solve itself
+    stays correct (objective close to the plain FP64 solve)."""
     import paper_1904_10585_gb300 as B
     n, p = 200, 16
     inst = syn.maxcut_instance(n, 0.1, p, seed=21)
     rp, ci, cv = S.csr_to_device(inst.C, DEV, torch.float64)
     U0 = torch.from_numpy(np.ascontiguousarray(inst.U0_raw[:, :p])).to(DEV)
+    rungs = []
     with S.Context(p=p, n_max=n, degree=2, degree_max=3, precision=B.PF_PREC_BF16, adaptive=1,
                    stream=torch.cuda.Stream()) as ctx:
         pr = S.maxcut_problem(rp, ci, cv, U0, dense=False, lowprec="bf16")
         S.problem_init(ctx, pr)
-        res = S.solve(ctx, pr, 1500, 0.0, 10)
+        for _ in range(1000):
+            res = S.solve(ctx, pr, 10, 0.0, 10)
+            key = (res.last.precision, res.last.degree)
+            if not rungs or rungs[-1] != key:
+                rungs.append(key)
+            if key == (B.PF_PREC_FP64, 3):
+                break
         ctx.stream.synchronize()
-    assert res.last.degree == 3
-    assert res.last.precision == B.PF_PREC_FP64
+    assert rungs == [(B.PF_PREC_BF16, 2), (B.PF_PREC_FP64, 2), (B.PF_PREC_FP64, 3)], rungs
     _, h64 = _run(S, inst, p, 3, 1500, dense=False)
     assert abs(res.obj - h64[-1].obj) <= 1e-4 * abs(h64[-1].obj)
 
