@@ -48,15 +48,17 @@ FP64_CUBLAS_MEASURED = 1.09    # torch float64 matmul 16384x16384x64 on this poo
 HBM_PEAK_GBS = 6773.2          # measured STREAM-style copy on the GB300s
 # DRAM bytes (read + written) per launch of the roofline kernel, from an ncu
 # capture of the current kernel (None where no capture of it exists):
-# k_oz_product<32> at n = 4096, p = 32 read 237.30 MB and wrote 3.62 MB
+# k_oz_product<32> at n = 4096, p = 32 read 120.02 MB and wrote 3.57 MB
+# (7.4 bytes an entry of the iteration matrix)
 NCU_TRAFFIC_BYTES = {
-    "maxcut_n4096": 240.36e6,
+    "maxcut_n4096": 123.58e6,
 }
 # Iterations the default workload's solve takes to reach KKT 1e-4 on the GPU;
 # the oracle follows the same trajectory (parity of every iteration), so the
 # reference arm scales its sampled iterations to this count.
 ITERS_TO_TOL = {"maxcut_n4096": 2740}
-SLICED_NOTE = ("bf16 digit planes x7 of Z and X on tcgen05 (TMA, TMEM), level sums exact in fp32, "
+SLICED_NOTE = ("7 int8 digit planes of Z (bytes in HBM, widened to fp16 in shared memory) and 7 "
+               "fp16 planes of X on tcgen05 (TMA, TMEM), level sums exact in fp32, "
                "int64 fold, FP64 recurrence epilogue: an FP64-accurate product")
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -175,7 +177,7 @@ class WorkloadSpec:
         self.kind = c["kind"]
         self.lowprec = "bf16" if name.endswith("lowprec") else None
         self.structured = name.endswith("structured")
-        self.sliced = True   # dense FP64 products as bf16 digit planes on the tensor cores
+        self.sliced = True   # dense FP64 products as int8 digit planes on the tensor cores
 
     def dense_f64(self):
         """The step applies a dense FP64 iteration matrix."""
@@ -407,7 +409,7 @@ class Workload(WorkloadSpec):
             # Y_prev read and Y_next written in FP64 (the digit planes the
             # kernel moves instead are its representation, reported beside)
             return (S.dense_operator(pr.Z),
-                    "k_oz_product + k_oz_finish (Y = Z X from bf16 digit planes x7 on tcgen05, "
+                    "k_oz_product + k_oz_finish (Y = Z X from int8 digit planes x7 on tcgen05, "
                     "recurrence epilogue)", "hbm",
                     8.0 * n * n + 24.0 * n * p, "GB/s")
         if self.kind == "nce":
@@ -647,7 +649,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": ("bf16+f64" if W.lowprec else
-                  "bf16x7->f64" if (W.sliced and W.dense_f64()) else "f64"),
+                  "f16x7->f64" if (W.sliced and W.dense_f64()) else "f64"),
         "data": "synthetic",
         "config": W.config(),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -671,10 +673,10 @@ def run_ours(args):
         "launches_per_iteration": step_launches,
     }
     if W.sliced and W.dense_f64():
-        # what the sliced product moves: 7 bf16 digit planes of Z (14 bytes an
-        # entry), the planes of X read and of the next block written, and the
-        # FP64 blocks
-        line["roofline"]["representation_bytes_per_launch"] = 14.0 * n * n + 52.0 * n * p
+        # what the sliced product moves: 7 int8 digit planes of Z (7 bytes an
+        # entry), the fp16 planes of X read and of the next block written, and
+        # the FP64 blocks
+        line["roofline"]["representation_bytes_per_launch"] = 7.0 * n * n + 52.0 * n * p
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -784,7 +786,7 @@ def run_serving(args):
                                      "dense_product": "FP64 FMAs on the CUDA cores",
                                      "speedup_of_serving": sat_rate / plain_rate},
         "one_at_a_time_fp64_sliced": {"value": N / sliced_s, "seconds": sliced_s,
-                                      "dense_product": "FP64-accurate bf16 digit planes on "
+                                      "dense_product": "FP64-accurate int8 digit planes on "
                                                        "tcgen05",
                                       "speedup_of_serving": sat_rate * sliced_s / N},
         "kkt_reached_fraction": float(np.mean(kkts <= TOL)),
@@ -809,7 +811,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dense-product", default="sliced", choices=["sliced", "fp64"],
-                    help="dense FP64 products: bf16 digit planes on the tensor cores (FP64-"
+                    help="dense FP64 products: int8 digit planes on the tensor cores (FP64-"
                          "accurate) or FP64 FMAs on the CUDA cores")
     ap.add_argument("--profile", action="store_true",
                     help="short run for profiler captures (init + 1 + --profile-iters "

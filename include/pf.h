@@ -68,8 +68,9 @@ typedef enum { PF_PREC_FP64 = 0, PF_PREC_TF32 = 1, PF_PREC_BF16 = 2 } pf_precisi
 
 /* Arithmetic of the FP64 dense product A X (PF_OP_DENSE on the FP64 path). */
 typedef enum {
-  PF_DENSE_SLICED = 0,  /* error-free bf16 digit planes of A and X on the tensor cores
-                         * (tcgen05), level sums exact in fp32, folded in int64: an
+  PF_DENSE_SLICED = 0,  /* error-free 8-bit digit planes of A (stored as bytes) and X
+                         * (fp16), fp16 MMAs on the tensor cores (tcgen05), level
+                         * sums exact in fp32, folded in int64: an
                          * FP64-accurate product (per entry within a few units of
                          * 2^-53 max|A_i.| max|X_.j| per term of the sum) -- default */
   PF_DENSE_FP64 = 1     /* FP64 fused multiply-adds on the CUDA cores            */

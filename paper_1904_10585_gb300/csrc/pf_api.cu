@@ -191,7 +191,7 @@ pf_status ensure_oz(pf_ctx *ctx) {
   int smax = kOzMaxSplits;
   const int need = (int)((chunks + kOzMaxChunks - 1) / kOzMaxChunks);
   if (need > smax) smax = need;
-  const size_t sizes[] = {(size_t)kOzSlices * nz * nz * 2,                 // zs
+  const size_t sizes[] = {(size_t)kOzSlices * nz * nz,                     // zs (one byte a digit)
                           (size_t)nz * chunks * sizeof(int),               // ez
                           (size_t)kOzSlices * kMaxP * nz * 2,              // xs[0]
                           (size_t)kOzSlices * kMaxP * nz * 2,              // xs[1]

@@ -17,7 +17,7 @@ constexpr int kMaxRedBlocks = 1024; // max blocks of a row reduction
 constexpr int kMaxGramBlocks = 256; // max blocks of a Gram (X^T Y) reduction
 constexpr int kMaxSplitK = 16;      // max K-splits of the dense FP64 product
 // sliced tensor-core product (pf_oz.cu)
-constexpr int kOzSlices = 7;        // bf16 digit planes per FP64 operand
+constexpr int kOzSlices = 7;        // 8-bit digit planes per FP64 operand
 constexpr int kOzExpBad = 4096;     // exponent marking a row / chunk with Inf or NaN
 constexpr int kOzMaxChunks = 32;    // 128-wide K chunks per split (int64 headroom)
 constexpr int kOzMaxSplits = 8;     // K splits when the row blocks leave SMs idle
@@ -81,9 +81,9 @@ struct Op {
 
 // Digit planes of the sliced dense product (allocated on first use).
 struct OzBuffers {
-  void *zs;               // bf16 planes of A: kOzSlices x slice_rows x ldk
+  void *zs;               // byte planes of A (digit + 128): kOzSlices x slice_rows x ldk
   int *ez;                // exponents of A per row and 128-column chunk, slice_rows x (slice_rows / 128)
-  void *xs[2];            // bf16 planes of the block: kOzSlices x kMaxP x ldk each
+  void *xs[2];            // fp16 planes of the block: kOzSlices x kMaxP x ldk each
   int *ex[2];             // chunk x column exponents, (slice_rows / 128) x kMaxP each
   double *part;           // split partials, max splits x n_max x p
   int *cnt;               // arrival tickets per row block and column half (zero between launches)

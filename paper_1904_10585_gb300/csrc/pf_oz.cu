@@ -1,6 +1,7 @@
 // FP64-accurate dense filter product on the 5th-generation tensor cores by
 // error-free slicing: the splitting idea of Ozaki, Ogita, Oishi and Rump
-// (Numer. Algorithms 59, 2012) with bf16 slices and fp32 accumulation.
+// (Numer. Algorithms 59, 2012) with 8-bit digit slices (stored as bytes,
+// multiplied as fp16) and fp32 accumulation.
 //
 // One Chebyshev step (Sec. 2.1, Eq. (cheb), by the three-term recurrence in
 // the mapped variable (A - cI)/e of Eq. (cheb-linear-map)) with the dense
@@ -13,9 +14,12 @@
 // a_0..a_6 (a_0 in [-128, 128], the rest in [-128, 127]) give
 // A_ij ~ 2^(eA_ic - 7) sum_s a_s 2^(-8s), error <= 2^(eA_ic - 56).  X is cut
 // the same way per (128-row chunk c, column j) with exponent eX_cj.
-// Every digit is an integer of at most 8 significant bits, exact in bf16.
-// The planes of A are stored tile by tile (oz_zs_index), so that every TMA
-// box of the product is one contiguous 16 KB read.
+// Every digit is an integer of at most 8 significant bits, exact in fp16 and
+// bf16.  The exponent of A has a margin (oz_exponent_margin: |A_ij| <
+// 2^eA_ic (1 - 2^-7)) that keeps a_0 inside [-128, 127], so the planes of A
+// are stored as bytes a_s + 128 (7 bytes per entry, against 8 for the FP64
+// matrix itself), tile by tile (oz_zs_index): every tile the product reads
+// is one contiguous 8 KB block.  The planes of X are fp16.
 //
 // Products.  For a chunk c of 128 values of k, the level sums
 //     L_l = sum_{s + t = l} sum_{k in c} a_s(i,k) x_t(k,j),   l = 0..6,
@@ -30,9 +34,12 @@
 // of an FP64 dot product's rounding bound.
 //
 // Tensor-core mapping (per CTA: one 128-row block of A, one K split):
-//   warp 0, one lane : TMA producer.  Per 64-wide K tile: the 7 digit planes
-//                      of X (one stage, 7 x NB rows) and, one stage each,
-//                      the 7 digit planes of the A tile (128 x 64 bf16).
+//   warp 0, one lane : producer.  Per 64-wide K tile: the 7 digit planes of
+//                      X (TMA, one stage, 7 x NB rows) and, one stage each,
+//                      the 7 stored byte tiles of A (bulk copies of 8 KB).
+//   widening warps   : each byte tile becomes the fp16 operand tile (128 x 64
+//                      fp16, K-major, 128-byte swizzle) in shared memory: a
+//                      byte permute and one f16x2 subtraction per two digits.
 //   warp 1, one lane : MMA issuer.  A-plane s times the stacked X planes
 //                      0..6-s in one tcgen05.mma of N = (7 - s) NB,
 //                      accumulating into TMEM columns [s NB, 7 NB): level l
@@ -55,6 +62,7 @@
 #include <climits>
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "pf_internal.cuh"
 #include "pf_sm100.cuh"
@@ -65,7 +73,8 @@ namespace {
 
 constexpr int OZ_BM = 128;               // rows per tile and K per chunk
 constexpr int OZ_BK = 64;                // K per TMA tile (128 bytes of bf16)
-constexpr int OZ_A_BYTES = OZ_BM * 128;  // one A digit-plane tile
+constexpr int OZ_A_BYTES = OZ_BM * 128;  // one A digit-plane tile as the fp16 MMA operand
+constexpr int OZ_S_BYTES = OZ_BM * OZ_BK;  // the same tile as stored: one byte per digit
 constexpr int OZ_SB = 2;                 // stages of the X planes
 constexpr int OZ_FRAC = 8 * (kOzSlices - 1) + 7;  // fractional bits of the rounded entry
 constexpr int OZ_FOLD = 36;              // binary point of the int64 fold (level 0)
@@ -73,19 +82,36 @@ constexpr int OZ_FOLD = 36;              // binary point of the int64 fold (leve
 template <int NB>
 struct OzCfg {
   static_assert(NB == 16 || NB == 32, "columns per CTA");
-  // epilogue: 8 columns per thread, so that each TMEM lane quarter has NB / 8
-  // warps and every SM sub-partition several of them (the per-chunk fold is
-  // a latency-bound integer chain)
-  static constexpr int CW = 8;
+  // epilogue: 16 columns per thread (NB / 16 warps per TMEM lane quarter);
+  // its per-chunk fold is small next to the widening of the A planes, which
+  // runs on CONV warps, each widening whole tiles (tile ia on warp ia % CONV),
+  // so that several tiles are in flight
+  static constexpr int CW = 16;
   static constexpr int EPI = 4 * (NB / CW);      // epilogue warps
-  static constexpr int THREADS = 64 + 32 * EPI;
+#ifndef PF_OZ_CONV
+#define PF_OZ_CONV 6
+#endif
+  static constexpr int CONV = PF_OZ_CONV;        // warps widening the A planes
+  static constexpr int THREADS = 64 + 32 * EPI + 32 * CONV;
   static constexpr int LEVEL_COLS = kOzSlices * NB;
   static constexpr int NBUF = 2;
   static constexpr uint32_t TMEM_COLS = NBUF * LEVEL_COLS <= 256 ? 256u : 512u;
-  static constexpr int SA = 8;                   // A stages
+#ifndef PF_OZ_SA
+#define PF_OZ_SA 6
+#endif
+#ifndef PF_OZ_SS
+#define PF_OZ_SS 6
+#endif
+  static constexpr int SA = PF_OZ_SA;            // A operand stages (fp16, 16 KB)
+  static constexpr int SS = PF_OZ_SS;            // A byte-plane stages (8 KB)
   static constexpr int B_BYTES = kOzSlices * NB * 128;
   static constexpr int MAXRUN = 256 / NB;        // X planes per MMA (N <= 256)
-  static constexpr size_t SMEM = 1024 + (size_t)SA * OZ_A_BYTES + (size_t)OZ_SB * B_BYTES;
+  static constexpr size_t SMEM = 1024 + (size_t)SA * OZ_A_BYTES + (size_t)OZ_SB * B_BYTES +
+                                 (size_t)SS * OZ_S_BYTES;
+  // a stage belongs to one widening warp (tile ia to warp ia % CONV): the
+  // warp's parity waits on it then come in phase order
+  static_assert(SA % CONV == 0 && SS % CONV == 0, "stages per widening warp");
+  static_assert(SMEM + 8192 <= 232448, "shared memory per CTA");
 };
 
 // Biased exponent field of |x|.
@@ -95,6 +121,40 @@ __device__ __forceinline__ unsigned oz_exfield(double x) {
 // Exponent e with |x| < 2^e for every x whose exponent field is <= f.
 __device__ __forceinline__ int oz_exponent(unsigned f) {
   return f == 0x7FFu ? kOzExpBad : (int)(f > 1u ? f : 1u) - 1022;
+}
+
+// Exponent of a chunk of A whose largest |x| has the high word `hw` (the
+// sign-less top 32 bits of its binary64 pattern): |x| < 2^e (1 - 2^-7) for
+// every x of the chunk, one more than oz_exponent when the largest mantissa
+// is within 2^-6 of the next power of two.  The margin keeps the leading
+// digit inside [-128, 127], so every digit of A fits one byte.
+__device__ __forceinline__ int oz_exponent_margin(unsigned hw) {
+  const int e = oz_exponent(hw >> 20);
+  if (e == kOzExpBad) return e;
+  return ((hw >> 14) & 0x3Fu) == 0x3Fu ? e + 1 : e;
+}
+__device__ __forceinline__ unsigned oz_highword(double x) {
+  return (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7FFFFFFFu;
+}
+// The 7 balanced base-256 digits of v (|v| <= 2^55 (1 - 2^-7)) as bytes
+// d_s + 128: byte 6 - s of v + 128 (1 + 256 + ... + 256^6) (no carry runs
+// between digits, each digit plus 128 lies in [0, 255]).
+__device__ __forceinline__ unsigned long long oz_digit_word(long long v) {
+  return (unsigned long long)v + 0x0080808080808080ull;
+}
+// Plane s's bytes of four digit words as one 32-bit word (column i in byte i).
+__device__ __forceinline__ uint32_t oz_plane_bytes4(const unsigned long long *u, int s) {
+  const int k = 6 - s;  // byte of the word holding plane s
+  const uint32_t a0 = (uint32_t)(u[0] >> (k < 4 ? 0 : 32)), a1 = (uint32_t)(u[1] >> (k < 4 ? 0 : 32));
+  const uint32_t a2 = (uint32_t)(u[2] >> (k < 4 ? 0 : 32)), a3 = (uint32_t)(u[3] >> (k < 4 ? 0 : 32));
+  const unsigned kk = (unsigned)(k & 3);
+  const uint32_t lo = __byte_perm(a0, a1, kk | ((kk + 4) << 4));
+  const uint32_t hi = __byte_perm(a2, a3, kk | ((kk + 4) << 4));
+  return __byte_perm(lo, hi, 0x5410);
+}
+// fp16 pattern of a digit given as its exact fp32 pattern (oz_digit_bits).
+__device__ __forceinline__ unsigned short oz_f16_of(uint32_t f) {
+  return __half_as_ushort(__float2half_rn(__uint_as_float(f)));
 }
 
 // round(x 2^(OZ_FRAC - e)) for |x| < 2^e (|result| <= 2^55).  Integer
@@ -175,6 +235,19 @@ __device__ __forceinline__ double oz_scale(long long v, int k) {
 }
 
 // Instruction descriptor: fp32 accumulator, bf16 A and B (K-major), M = 128.
+// The same with fp16 A and B (the product's widened byte planes and X planes).
+__device__ __forceinline__ uint32_t oz_idesc_f16(int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+}
+// Four stored digit bytes (d + 128) -> two fp16x2 words (d exactly).
+__device__ __forceinline__ void oz_widen4(uint32_t w, uint32_t &lo, uint32_t &hi) {
+  constexpr uint32_t k1024 = 0x64646464u;   // bytes 0x64: exponent of 1024 in each half
+  constexpr uint32_t k1152 = 0x64806480u;   // 1024 + 128 in both halves
+  lo = __byte_perm(w, k1024, 0x4140);
+  hi = __byte_perm(w, k1024, 0x4342);
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(lo) : "r"(lo), "r"(k1152));
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(hi) : "r"(hi), "r"(k1152));
+}
 __device__ __forceinline__ uint32_t oz_idesc(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(OZ_BM >> 4) << 24);
@@ -206,6 +279,12 @@ __device__ __forceinline__ void st_v8_b32(void *p, const uint32_t *a, const uint
                "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3])
                : "memory");
 }
+__device__ __forceinline__ void st_v4_b32(void *p, uint32_t a, uint32_t b, uint32_t c,
+                                          uint32_t d) {
+  asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
 __device__ __forceinline__ void st_v4_f64(double *p, const double *v) {
   asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
                "d"(v[2]), "d"(v[3])
@@ -213,40 +292,41 @@ __device__ __forceinline__ void st_v4_f64(double *p, const double *v) {
 }
 
 // ---------------------------------------------------------------------------
-// A (n x n FP64) -> digit planes of A (bf16, tile-contiguous, oz_zs_index)
-// and exponents ez[i * nzc + c] of each row and 128-column chunk.  One warp
-// per row, four entries per lane and chunk.
+// A (n x n FP64) -> digit planes of A (one byte per digit, d + 128,
+// tile-contiguous, oz_zs_index) and exponents ez[i * nzc + c] of each row
+// and 128-column chunk (oz_exponent_margin).  One warp per row, four entries
+// per lane and chunk.
 // ---------------------------------------------------------------------------
 // One 128-column chunk of one row: its exponent and its 7 digit-plane
 // segments, by one warp (four entries per lane).
 __device__ __forceinline__ void oz_slice_chunk(const double *__restrict__ ar, int n, int row,
-                                               int c0, int lane, __nv_bfloat16 *__restrict__ zs,
+                                               int c0, int lane, uint8_t *__restrict__ zs,
                                                int rb_n, int kt_n, int nzc,
                                                int *__restrict__ ez) {
   double v[4];
-  unsigned f = 0;
+  unsigned hw = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int k = c0 + 32 * q + lane;
     v[q] = k < n ? ar[k] : 0.0;
-    f = max(f, oz_exfield(v[q]));
+    hw = max(hw, oz_highword(v[q]));
   }
-  f = __reduce_max_sync(0xffffffffu, f);
-  const int e = oz_exponent(f);
+  hw = __reduce_max_sync(0xffffffffu, hw);
+  const int e = oz_exponent_margin(hw);
   if (lane == 0) ez[(int64_t)row * nzc + c0 / OZ_BM] = e;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int k = c0 + 32 * q + lane;
     if (k >= n) continue;
-    uint32_t d[kOzSlices];
-    oz_digit_bits(e != kOzExpBad ? oz_fixed(v[q], e) : 0ll, d);
+    const unsigned long long u = oz_digit_word(e != kOzExpBad ? oz_fixed(v[q], e) : 0ll);
 #pragma unroll
-    for (int s = 0; s < kOzSlices; ++s) zs[oz_zs_index(s, row, k, rb_n, kt_n)] = oz_bf16_of(d[s]);
+    for (int s = 0; s < kOzSlices; ++s)
+      zs[oz_zs_index(s, row, k, rb_n, kt_n)] = (uint8_t)(u >> (8 * (6 - s)));
   }
 }
 
 __global__ void __launch_bounds__(256) k_oz_zslice(const double *__restrict__ A, int64_t lda,
-                                                   int n, __nv_bfloat16 *__restrict__ zs,
+                                                   int n, uint8_t *__restrict__ zs,
                                                    int rb_n, int kt_n, int nzc,
                                                    int *__restrict__ ez) {
   const int lane = threadIdx.x & 31;
@@ -261,7 +341,7 @@ __global__ void __launch_bounds__(256) k_oz_zslice(const double *__restrict__ A,
 // sliced (the nearest-correlation iteration matrix G + Diag(x)).
 __global__ void __launch_bounds__(256) k_oz_zslice_diag(const double *__restrict__ A,
                                                         int64_t lda, int n,
-                                                        __nv_bfloat16 *__restrict__ zs, int rb_n,
+                                                        uint8_t *__restrict__ zs, int rb_n,
                                                         int kt_n, int nzc, int *__restrict__ ez) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -271,7 +351,7 @@ __global__ void __launch_bounds__(256) k_oz_zslice_diag(const double *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// X (n x p FP64) -> digit planes xs[t][j][k] (bf16, plane t of NB rows j,
+// X (n x p FP64) -> digit planes xs[t][j][k] (fp16, plane t of NB rows j,
 // ldk) and exponents ex[c * kMaxP + j] of each 128-row chunk c and column j
 // (columns p..NB-1 are zero).  Grid (128-row chunks, groups of 8 columns),
 // thread = row: each thread reads the 8 entries of its row in the group
@@ -279,7 +359,7 @@ __global__ void __launch_bounds__(256) k_oz_zslice_diag(const double *__restrict
 // each row segment leaves HBM in whole sectors.
 __global__ void __launch_bounds__(128) k_oz_xslice(const double *__restrict__ X, int64_t ldx,
                                                    int n, int p, int NB,
-                                                   __nv_bfloat16 *__restrict__ xs, int64_t ldk,
+                                                   __half *__restrict__ xs, int64_t ldk,
                                                    int *__restrict__ ex, int xvec) {
   __shared__ unsigned qmax[4][8];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -312,7 +392,7 @@ __global__ void __launch_bounds__(128) k_oz_xslice(const double *__restrict__ X,
     if (in) {
 #pragma unroll
       for (int s2 = 0; s2 < kOzSlices; ++s2)
-        xs[(int64_t)(s2 * NB + jj) * ldk + row] = oz_bf16_of(d[s2]);
+        xs[(int64_t)(s2 * NB + jj) * ldk + row] = __ushort_as_half(oz_f16_of(d[s2]));
     }
   }
 }
@@ -323,13 +403,14 @@ __global__ void __launch_bounds__(128) k_oz_xslice(const double *__restrict__ X,
 // ---------------------------------------------------------------------------
 template <int NB>
 __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n,
+    const uint8_t *__restrict__ zs, const __grid_constant__ CUtensorMap tmB, int n,
     int p, int nbt, int rb_n, int kt_n, int nzc, int nsplit, const int *__restrict__ ez,
     const int *__restrict__ ex, double *__restrict__ part, Params *prm) {
   using C = OzCfg<NB>;
   constexpr int KS = kOzSlices;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t a_full[C::SA], a_empty[C::SA];
+  __shared__ __align__(8) uint64_t s_full[C::SS], s_empty[C::SS];
   __shared__ __align__(8) uint64_t b_full[OZ_SB], b_empty[OZ_SB];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
@@ -344,8 +425,10 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
   const int c0 = (int)((int64_t)split * nchunks / nsplit);
   const int c1 = (int)((int64_t)(split + 1) * nchunks / nsplit);
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const uint32_t sA = base;
-  const uint32_t sB = base + C::SA * OZ_A_BYTES;
+  const uint32_t sA = base;                            // fp16 operand ring
+  const uint32_t sB = base + C::SA * OZ_A_BYTES;       // X planes
+  const uint32_t sS = sB + OZ_SB * C::B_BYTES;         // byte planes of A as stored
+  uint8_t *const gbase = smem_raw + (base - smem_u32(smem_raw));  // generic view of base
 
   for (int j = threadIdx.x; j < NB; j += blockDim.x) {
     int m = INT_MIN;
@@ -355,8 +438,12 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < C::SA; ++s) {
-      mbar_init(smem_u32(&a_full[s]), 1);
+      mbar_init(smem_u32(&a_full[s]), 32);  // the 32 threads of the widening warp
       mbar_init(smem_u32(&a_empty[s]), 1);
+    }
+    for (int s = 0; s < C::SS; ++s) {
+      mbar_init(smem_u32(&s_full[s]), 1);
+      mbar_init(smem_u32(&s_empty[s]), 32);
     }
     for (int s = 0; s < OZ_SB; ++s) {
       mbar_init(smem_u32(&b_full[s]), 1);
@@ -368,7 +455,6 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
     }
     mbar_init(smem_u32(&mma_done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
   }
   if (warp == 0) {
@@ -391,7 +477,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      int ia = 0, ib = 0;
+      int is = 0, ib = 0;
       bool ok = true;
       for (int c = c0; c < c1 && ok; ++c) {
         for (int h = 0; h < 2 && ok; ++h) {
@@ -409,24 +495,25 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
             tma_load_2d(sB + sb * C::B_BYTES + t * NB * 128, &tmB, fb, kx, t * nbt + jh);
           ++ib;
           for (int s = 0; s < KS; ++s) {
-            const int sa = ia % C::SA;
-            if (ia >= C::SA &&
-                !mbar_wait(smem_u32(&a_empty[sa]), ((ia / C::SA) - 1) & 1, &abort_flag)) {
+            // the A tile of plane s as stored (8 KB of bytes, contiguous)
+            const int ss = is % C::SS;
+            if (is >= C::SS &&
+                !mbar_wait(smem_u32(&s_empty[ss]), ((is / C::SS) - 1) & 1, &abort_flag)) {
               ok = false;
               break;
             }
-            const uint32_t fa = smem_u32(&a_full[sa]);
-            mbar_expect_tx(fa, OZ_A_BYTES);
-            tma_load_2d(sA + sa * OZ_A_BYTES, &tmA, fa, 0,
-                        (int)((((int64_t)s * rb_n + rb) * kt_n + 2 * c + h) * OZ_BM));
-            ++ia;
+            const uint32_t fs = smem_u32(&s_full[ss]);
+            mbar_expect_tx(fs, OZ_S_BYTES);
+            const int64_t tile = ((int64_t)s * rb_n + rb) * kt_n + 2 * c + h;
+            bulk_load(sS + ss * OZ_S_BYTES, zs + tile * OZ_S_BYTES, OZ_S_BYTES, fs);
+            ++is;
           }
         }
       }
       // let every issued copy land before shared memory is released
-      for (int s = 0; s < C::SA && s < ia; ++s) {
-        const int last = s + ((ia - 1 - s) / C::SA) * C::SA;
-        mbar_drain(smem_u32(&a_full[s]), (last / C::SA) & 1);
+      for (int s = 0; s < C::SS && s < is; ++s) {
+        const int last = s + ((is - 1 - s) / C::SS) * C::SS;
+        mbar_drain(smem_u32(&s_full[s]), (last / C::SS) & 1);
       }
       for (int s = 0; s < OZ_SB && s < ib; ++s) {
         const int last = s + ((ib - 1 - s) / OZ_SB) * OZ_SB;
@@ -464,7 +551,7 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
             const uint64_t ad = sw128_desc(sA + sa * OZ_A_BYTES);
             for (int r0 = 0; r0 < KS - s; r0 += C::MAXRUN) {
               const int ns = min(C::MAXRUN, KS - s - r0);
-              const uint32_t idesc = oz_idesc(ns * NB);
+              const uint32_t idesc = oz_idesc_f16(ns * NB);
               const uint64_t bd = sw128_desc(bbase + r0 * NB * 128);
               const uint32_t d = dbase + (uint32_t)((s + r0) * NB);
 #pragma unroll
@@ -483,6 +570,46 @@ __global__ void __launch_bounds__(OzCfg<NB>::THREADS, 1) k_oz_product(
       // completion of every MMA issued above, before TMEM is freed
       mma_commit(smem_u32(&mma_done));
       mbar_drain(smem_u32(&mma_done), 0);
+    }
+  } else if (warp >= 2 + C::EPI) {
+    // ---------------- widening of the A planes ----------------
+    // Each stored tile (128 rows x 64 bytes, the digits plus 128) becomes the
+    // fp16 MMA operand (128 rows x 128 bytes, K-major, 128-byte swizzle: the
+    // 16-byte chunk c of row r sits at chunk c ^ (r mod 8)).  Two bytes at a
+    // time: a byte permute puts them into the mantissas of 1024 + b in two
+    // fp16 halves, and one f16x2 subtraction of 1152 leaves b - 128 (exact).
+    // Warp cw widens the tiles ia = cw, cw + CONV, ...; each lane the same
+    // sixteen 16-byte pieces of every tile (piece q = lane + 32 i: row q / 4,
+    // bytes 16 (q % 4) of the stored row).
+    constexpr int NP = OZ_BM * 4 / 32;  // pieces per lane and tile
+    const int cw = warp - 2 - C::EPI;
+    const int total = (c1 - c0) * 2 * KS;
+    for (int ia = cw; ia < total; ia += C::CONV) {
+      const int ss = ia % C::SS, sa = ia % C::SA;
+      if (!mbar_wait(smem_u32(&s_full[ss]), (ia / C::SS) & 1, &abort_flag)) break;
+      if (ia >= C::SA &&
+          !mbar_wait(smem_u32(&a_empty[sa]), ((ia / C::SA) - 1) & 1, &abort_flag))
+        break;
+      const uint8_t *src = gbase + (sS - base) + ss * OZ_S_BYTES;
+      uint8_t *dst = gbase + sa * OZ_A_BYTES;
+#pragma unroll 4
+      for (int i = 0; i < NP; ++i) {
+        const int q = lane + 32 * i, r = q >> 2, g = q & 3;
+        const uint4 w = *reinterpret_cast<const uint4 *>(src + r * OZ_BK + g * 16);
+        uint32_t o[8];
+        oz_widen4(w.x, o[0], o[1]);
+        oz_widen4(w.y, o[2], o[3]);
+        oz_widen4(w.z, o[4], o[5]);
+        oz_widen4(w.w, o[6], o[7]);
+        uint8_t *row = dst + (r >> 3) * 1024 + (r & 7) * 128;
+        *reinterpret_cast<uint4 *>(row + (((2 * g) ^ (r & 7)) << 4)) =
+            make_uint4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<uint4 *>(row + (((2 * g + 1) ^ (r & 7)) << 4)) =
+            make_uint4(o[4], o[5], o[6], o[7]);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(smem_u32(&s_empty[ss]));
+      mbar_arrive(smem_u32(&a_full[sa]));
     }
   } else {
     // ---------------- epilogue ----------------
@@ -717,7 +844,7 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
     const double *__restrict__ cvals, const double *__restrict__ lam,
     const double *__restrict__ xdiag, const double *__restrict__ mchunk,
     const int *__restrict__ ew, const int *__restrict__ ev, double *__restrict__ Z, int64_t ldz,
-    int zvec, int small_k, __nv_bfloat16 *__restrict__ zs, int rb_n, int kt_n,
+    int zvec, int small_k, uint8_t *__restrict__ zs, int rb_n, int kt_n,
     int *__restrict__ ez,
     int nzc, const Params *__restrict__ prm, Params *__restrict__ prm_flags,
     double *__restrict__ red) {
@@ -866,10 +993,12 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
           cmax = fmax(cmax, fabs(cvals[e]));
           if (col >= j0 && e_lo == e_hi) e_lo = e;
         }
+        // the factor 1 + 2^-6 covers rounding and keeps |Z_ij| < 2^e (1 - 2^-7),
+        // so that the leading digit fits its byte (oz_exponent_margin)
         const double bound =
             (xdiag[row] * mchunk[c] + tt * cmax +
              ((row >= cb && row < ce) ? fabs(lam_r) : 0.0)) *
-            (1.0 + 0x1p-20);
+            (1.0 + 0x1p-6);
         ez_rc = oz_exponent(oz_exfield(bound));
         if (col0 == 0 && (ct * XP_TN) % OZ_BM == 0) ez[(int64_t)row * nzc + c] = ez_rc;
       }
@@ -884,9 +1013,9 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
       int ncol = e < e_hi ? colind[e] : INT_MAX;  // column of the next entry of C
       static_assert(XP_G == 8 && XP_CW == 2 * XP_G, "two 8-column groups per thread");
       static_assert(OZ_FOLD == 36 && KS == 7, "the fold below is written out for 7 levels");
-      // the first group's plane words, stored with the second group's: 32
-      // bytes (a full sector) of each plane row per store
-      uint32_t pk0[KS][XP_G / 2];
+      // the first group's plane bytes, stored with the second group's: 16
+      // bytes of each plane row per store (columns j0 .. j0 + 15)
+      uint32_t pk0[KS][XP_G / 4];
 #pragma unroll
       for (int g = 0; g < XP_CW; g += XP_G) {
         // the group's new Z values, stored together: whole groups of an
@@ -928,7 +1057,8 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
           for (int i = 0; i < XP_G; ++i)
             lo[i] = f2i(A[i]) * 16 + ((f2i(B[i]) * 256 + f2i(C[i]) + 2048) >> 12);
         }
-        uint32_t pk[KS][XP_G / 2];
+        uint32_t pk[KS][XP_G / 4];
+        unsigned long long uw[XP_G];  // digit words (oz_digit_word) of the group
 #pragma unroll
         for (int i = 0; i < XP_G; ++i) {
           const int col = j0 + g + i;
@@ -953,11 +1083,12 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
             if (!vec) zrow[col] = z;
             if (ez_rc != kOzExpBad) zf = oz_fixed(z, ez_rc);
           }
-          uint32_t d[KS];
-          oz_digit_bits(zf, d);
+          uw[i] = oz_digit_word(zf);
+        }
 #pragma unroll
-          for (int s2 = 0; s2 < KS; ++s2)
-            pk[s2][i >> 1] = (i & 1) ? oz_pack2(pk[s2][i >> 1], d[s2]) : d[s2];
+        for (int s2 = 0; s2 < KS; ++s2) {
+          pk[s2][0] = oz_plane_bytes4(uw, s2);
+          pk[s2][1] = oz_plane_bytes4(uw + 4, s2);
         }
         if (vec && in) {
           st_v4_f64(zrow + j0 + g, zo);
@@ -967,13 +1098,14 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
 #pragma unroll
           for (int s2 = 0; s2 < KS; ++s2)
 #pragma unroll
-            for (int w2 = 0; w2 < XP_G / 2; ++w2) pk0[s2][w2] = pk[s2][w2];
+            for (int w2 = 0; w2 < XP_G / 4; ++w2) pk0[s2][w2] = pk[s2][w2];
         } else if (in) {
-          // columns j0 .. j0 + 15 of each plane row: 32 bytes at a 32-byte
-          // boundary (j0 is a multiple of 16, plane rows are 128 bytes)
+          // columns j0 .. j0 + 15 of each plane row: 16 bytes at a 16-byte
+          // boundary (j0 is a multiple of 16, plane rows are 64 bytes)
 #pragma unroll
           for (int s2 = 0; s2 < KS; ++s2)
-            st_v8_b32(zs + oz_zs_index(s2, row, j0, rb_n, kt_n), pk0[s2], pk[s2]);
+            st_v4_b32(zs + oz_zs_index(s2, row, j0, rb_n, kt_n), pk0[s2][0], pk0[s2][1],
+                      pk[s2][0], pk[s2][1]);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1020,7 +1152,7 @@ __global__ void __launch_bounds__(XP_THREADS, 1) k_oz_expand(
 __global__ void __launch_bounds__(OZ_BM) k_oz_finish(
     const double *__restrict__ part, int nsplit, int n, int p, const double *X, int64_t ldx,
     const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn,
-    __nv_bfloat16 *__restrict__ xs_next, int *__restrict__ ex_next, int64_t ldk, int nbt,
+    __half *__restrict__ xs_next, int *__restrict__ ex_next, int64_t ldk, int nbt,
     const Params *__restrict__ prm, int mode, int vmask) {
   __shared__ unsigned qmax[4][8];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -1108,7 +1240,7 @@ __global__ void __launch_bounds__(OZ_BM) k_oz_finish(
     if (in && jj < nbt) {
 #pragma unroll
       for (int s2 = 0; s2 < kOzSlices; ++s2)
-        xs_next[(int64_t)(s2 * nbt + jj) * ldk + row] = oz_bf16_of(d[s2]);
+        xs_next[(int64_t)(s2 * nbt + jj) * ldk + row] = __ushort_as_half(oz_f16_of(d[s2]));
     }
   }
 }
@@ -1150,7 +1282,7 @@ int oz_splits(int n, int p, int num_sms) {
 cudaError_t launch_oz_zslice(cudaStream_t s, const Workspace &ws, const double *A, int64_t lda,
                              int n) {
   if (ws.oz.zs == nullptr || n > ws.oz.slice_rows) return cudaErrorInvalidValue;
-  k_oz_zslice<<<(n + 7) / 8, 256, 0, s>>>(A, lda, n, (__nv_bfloat16 *)ws.oz.zs,
+  k_oz_zslice<<<(n + 7) / 8, 256, 0, s>>>(A, lda, n, (uint8_t *)ws.oz.zs,
                                           (int)(ws.oz.slice_rows / OZ_BM),
                                           (int)(ws.oz.ldk / OZ_BK),
                                           (int)(ws.oz.slice_rows / OZ_BM), ws.oz.ez);
@@ -1161,7 +1293,7 @@ cudaError_t launch_oz_zslice(cudaStream_t s, const Workspace &ws, const double *
 cudaError_t launch_oz_zslice_diag(cudaStream_t s, const Workspace &ws, const double *A,
                                   int64_t lda, int n) {
   if (ws.oz.zs == nullptr || n > ws.oz.slice_rows) return cudaErrorInvalidValue;
-  k_oz_zslice_diag<<<(n + 7) / 8, 256, 0, s>>>(A, lda, n, (__nv_bfloat16 *)ws.oz.zs,
+  k_oz_zslice_diag<<<(n + 7) / 8, 256, 0, s>>>(A, lda, n, (uint8_t *)ws.oz.zs,
                                                (int)(ws.oz.slice_rows / OZ_BM),
                                                (int)(ws.oz.ldk / OZ_BK),
                                                (int)(ws.oz.slice_rows / OZ_BM), ws.oz.ez);
@@ -1176,7 +1308,7 @@ cudaError_t launch_oz_xslice(cudaStream_t s, const Workspace &ws, const double *
   const int nb = oz_nbt(p);
   const int xvec = ((reinterpret_cast<uintptr_t>(X) & 31) == 0 && (ldx & 3) == 0) ? 1 : 0;
   k_oz_xslice<<<dim3((n + OZ_BM - 1) / OZ_BM, (nb + 7) / 8), OZ_BM, 0, s>>>(
-      X, ldx, n, p, nb, (__nv_bfloat16 *)ws.oz.xs[which], ws.oz.ldk, ws.oz.ex[which], xvec);
+      X, ldx, n, p, nb, (__half *)ws.oz.xs[which], ws.oz.ldk, ws.oz.ex[which], xvec);
   PF_LAUNCHED();
   return cudaGetLastError();
 }
@@ -1187,27 +1319,25 @@ cudaError_t launch_oz_product(cudaStream_t s, const Workspace &ws, int n, int wh
   if (ws.oz.zs == nullptr || n > ws.oz.slice_rows) return cudaErrorInvalidValue;
   const int p = ws.p;
   const int NB = oz_nb(p), H = oz_halves(p), nbt = oz_nbt(p);
-  CUtensorMap ma, mb;
-  // the tile-contiguous planes seen as rows of 64 bf16 (one 16 KB box per tile)
-  cudaError_t e = encode_tile_map(&ma, ws.oz.zs, false,
-                                  (int64_t)kOzSlices * ws.oz.slice_rows * (ws.oz.ldk / OZ_BK),
-                                  OZ_BK, OZ_BK, OZ_BM);
-  if (e != cudaSuccess) return e;
-  e = encode_tile_map(&mb, ws.oz.xs[which], false, (int64_t)kOzSlices * nbt, n, ws.oz.ldk, NB);
+  CUtensorMap mb;
+  // the X planes (fp16 digits, 2-byte elements like bf16 for the copy)
+  cudaError_t e = encode_tile_map(&mb, ws.oz.xs[which], false, (int64_t)kOzSlices * nbt, n,
+                                  ws.oz.ldk, NB);
   if (e != cudaSuccess) return e;
   const int S = oz_splits(n, p, ws.num_sms);
   const int R = (n + OZ_BM - 1) / OZ_BM;
   const dim3 grid(R, S, H);
 #define PF_OZ(NBV)                                                                              \
   k_oz_product<NBV><<<grid, OzCfg<NBV>::THREADS, OzCfg<NBV>::SMEM, s>>>(                       \
-      ma, mb, n, p, nbt, (int)(ws.oz.slice_rows / OZ_BM), (int)(ws.oz.ldk / OZ_BK),          \
+      (const uint8_t *)ws.oz.zs, mb, n, p, nbt, (int)(ws.oz.slice_rows / OZ_BM),               \
+      (int)(ws.oz.ldk / OZ_BK),                                                                   \
       (int)(ws.oz.slice_rows / OZ_BM), S, ws.oz.ez, ws.oz.ex[which], ws.oz.part, ws.prm)
   if (NB == 16) PF_OZ(16);
   else PF_OZ(32);
 #undef PF_OZ
   PF_LAUNCHED();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  __nv_bfloat16 *xn = next >= 0 ? (__nv_bfloat16 *)ws.oz.xs[next] : nullptr;
+  __half *xn = next >= 0 ? (__half *)ws.oz.xs[next] : nullptr;
   int *exn = next >= 0 ? ws.oz.ex[next] : nullptr;
   auto vec_ok = [](const double *a, int64_t ld) {
     return a != nullptr && (reinterpret_cast<uintptr_t>(a) & 31) == 0 && (ld & 3) == 0;
@@ -1242,7 +1372,7 @@ cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t 
   const int zvec = ((reinterpret_cast<uintptr_t>(Z) & 31) == 0 && (ldz & 3) == 0) ? 1 : 0;
   k_oz_expand<<<grid, XP_THREADS, XP_SMEM, s>>>(
       mw, mv, n, (int)oz.slice_rows, rowptr, colind, vals, lam, oz.xdiag, oz.mchunk, oz.ew,
-      oz.ev, Z, ldz, zvec, p <= 32 ? 1 : 0, (__nv_bfloat16 *)oz.zs,
+      oz.ev, Z, ldz, zvec, p <= 32 ? 1 : 0, (uint8_t *)oz.zs,
       (int)(oz.slice_rows / OZ_BM),
       (int)(oz.ldk / OZ_BK), oz.ez, (int)(oz.slice_rows / OZ_BM), ws.prm, ws.prm, red);
   PF_LAUNCHED();

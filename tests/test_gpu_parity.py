@@ -70,7 +70,7 @@ def spectrum_matrix(n, p, seed, gap=1.0):
 # pf_filter / pf_rayleigh_ritz on a dense operator
 # ---------------------------------------------------------------------------
 
-# dense products: bf16 digit planes on the tensor cores (default) and FP64 FMAs
+# dense products: 8-bit digit planes on the tensor cores (default) and FP64 FMAs
 DENSE = [0, 1]
 
 

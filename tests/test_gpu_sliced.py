@@ -1,5 +1,6 @@
-"""The sliced dense product (bf16 digit planes of A and X on the tensor cores,
-exact fp32 level sums, int64 fold) against an extended-precision reference.
+"""The sliced dense product (int8 digit planes of A, fp16 planes of X, fp16
+MMAs on the tensor cores, exact fp32 level sums, int64 fold) against an
+extended-precision reference.
 
 Bound.  With rowmax_i = max_k |A_ik| and colmax_j = max_k |X_kj|, each term
 A_ik X_kj of the sum carries at most

@@ -9,7 +9,9 @@ with Python integers and fractions (no floating point) and check the facts the
 kernel relies on: digit ranges (8 significant bits: exact in bf16), the
 rounding error 2^(e-56), the bound 7 * 128 * 2^14 < 2^24 on a chunk's level
 sums (exact fp32 accumulation), and the product error bound that the GPU test
-asserts, n 2^-50 max|A_i.| max|X_.j|.
+asserts, n 2^-50 max|A_i.| max|X_.j|.  The planes of A are stored as bytes
+d + 128 under a margin exponent that keeps the leading digit in [-128, 127],
+and widened to fp16 on the GPU: both are checked here as well.
 """
 import math
 from fractions import Fraction
@@ -68,6 +70,58 @@ def test_extreme_digit_plus_128():
     d = digits(x, e)   # x 2^(55-e) = 2^55 - 4: digits 128, 0, ..., 0, -4
     assert d[0] == 128 and d[1:] == [0] * (KS - 2) + [-4]
     assert value(d, e) == Fraction(x)
+
+
+def exponent_margin(values):
+    """The exponent the A planes use: one more than `exponent` when the
+    largest |x| has its top six mantissa bits set (is within 2^-6 of the next
+    power of two in its binade), so that every |x| < 2^e (1 - 2^-7)."""
+    m = max(abs(v) for v in values)
+    if m == 0.0:
+        return -1021
+    f, e = math.frexp(m)               # m = f 2^e, 0.5 <= f < 1
+    top6 = int(f * 2 ** 7) & 0x3F      # mantissa bits 1..6 after the leading one
+    return e + 1 if top6 == 0x3F else e
+
+
+def stored_bytes(d):
+    """The A planes' bytes: the digits of v as bytes of v + 128 (1 + 256 + ...)."""
+    v = sum(d[s] * 256 ** (KS - 1 - s) for s in range(KS))
+    u = v + sum(128 * 256 ** k for k in range(KS))
+    assert u >= 0
+    return [(u >> (8 * (KS - 1 - s))) & 0xFF for s in range(KS)], u >> (8 * KS)
+
+
+def test_margin_exponent_puts_every_digit_in_a_byte():
+    """With the margin exponent the leading digit stays in [-128, 127], so the
+    seven digits of A are the seven bytes of v + 128 (1 + 256 + ... + 256^6)
+    with no carry out of the top byte, each byte minus 128 giving its digit."""
+    rng = np.random.default_rng(3)
+    rows = [rng.standard_normal(16) * 2.0 ** rng.integers(-30, 30) for _ in range(200)]
+    for k in range(60):  # largest entries just below a power of two
+        r = rng.standard_normal(16)
+        r[k % 16] = math.ldexp(1.0, k - 30) * (1 - 2.0 ** -(1 + k % 53))
+        rows.append(r)
+    for row in rows:
+        e = exponent_margin(row)
+        assert max(abs(x) for x in row) < 2.0 ** e * (1 - 2.0 ** -7)
+        for x in row:
+            d = digits(float(x), e)
+            assert all(-128 <= ds <= 127 for ds in d)
+            b, carry = stored_bytes(d)
+            assert carry == 0 and [bb - 128 for bb in b] == d
+            assert abs(value(d, e) - Fraction(float(x))) <= Fraction(2) ** (e - 56)
+
+
+def test_widening_a_byte_to_fp16_is_exact():
+    """The product widens a stored byte b = d + 128 to fp16 by placing b in the
+    mantissa of 1024 + b and subtracting 1152 in fp16: exact for every byte."""
+    b = np.arange(256)
+    x = (np.float16(1024) + b.astype(np.float16)).astype(np.float16)
+    # the bit pattern 0x6400 | b is 1024 + b
+    assert np.array_equal(x.view(np.uint16), (0x6400 | b).astype(np.uint16))
+    d = (x - np.float16(1152)).astype(np.float16)
+    assert np.array_equal(d.astype(np.int64), b - 128)
 
 
 def test_level_sums_fit_fp32():
