@@ -465,7 +465,7 @@ pf_status rr_core(pf_ctx *ctx, const Op &op, const double *Q, int64_t ldq, doubl
   PF_CUDA(launch_gram(s, ws, Q, ldq, ws.W, p, op.n, p, p, 0, &nb));
   // launch_gram leaves the reduced H = Q^T W in the first Gram slot
   phase(ctx, PF_PHASE_EIG);
-  PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, theta));
+  PF_CUDA(launch_jacobi(s, ws, ws.gpart, p, theta));
   if (resid != nullptr)
     PF_CUDA(launch_rotate_resid(s, ws, Q, ldq, ws.W, p, op.n, p, theta, V, ldv, resid));
   else  // Ritz vectors only (the solver steps do not use the residual norms)
@@ -622,7 +622,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     int nb = 0;
     PF_CUDA(launch_gram(s, ws, ws.W, p, ws.W, p, n, p, p, 0, &nb));
     phase(ctx, PF_PHASE_EIG);
-    PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, pr->theta));
+    PF_CUDA(launch_jacobi(s, ws, ws.gpart, p, pr->theta));
     PF_CUDA(launch_apply_right(s, ws, pr->U, pr->ldu, pr->V, pr->ldv, n, p, ws.Yeig, 0, 0));
     PF_CUDA(launch_apply_right(s, ws, ws.W, p, Yb[0], p, n, p, ws.Yeig, 0, 0));
     phase(ctx, PF_PHASE_UPDATE);
@@ -667,7 +667,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     int nb = 0;
     PF_CUDA(launch_gram(s, ws, ws.W, p, ws.W, p, n, p, p, 0, &nb));
     phase(ctx, PF_PHASE_EIG);
-    PF_CUDA(launch_jacobi_cluster(s, ws, ws.gpart, p, pr->theta));
+    PF_CUDA(launch_jacobi(s, ws, ws.gpart, p, pr->theta));
     PF_CUDA(launch_apply_right(s, ws, pr->U, pr->ldu, pr->V, pr->ldv, n, p, ws.Yeig, 0, 0));
     PF_CUDA(launch_apply_right(s, ws, ws.W, p, Yb[0], p, n, p, ws.Yeig, 0, 0));
     phase(ctx, PF_PHASE_UPDATE);

@@ -167,8 +167,8 @@ cudaError_t launch_chol_inv(cudaStream_t s, const Workspace &ws, int nparts, int
 cudaError_t launch_apply_right(cudaStream_t s, const Workspace &ws, const double *Y, int64_t ldy,
                                double *Q, int64_t ldq, int n, int p, const double *R, int upper,
                                int cond_flag);
-cudaError_t launch_jacobi_cluster(cudaStream_t s, const Workspace &ws, const double *H, int p,
-                                  double *theta);
+cudaError_t launch_jacobi(cudaStream_t s, const Workspace &ws, const double *H, int p,
+                          double *theta);
 cudaError_t launch_rotate_resid(cudaStream_t s, const Workspace &ws, const double *Q, int64_t ldq,
                                 const double *W, int64_t ldw, int n, int p, const double *theta,
                                 double *V, int64_t ldv, double *resid_out);

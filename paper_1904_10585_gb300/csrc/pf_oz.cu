@@ -88,22 +88,15 @@ struct OzCfg {
   // so that several tiles are in flight
   static constexpr int CW = 16;
   static constexpr int EPI = 4 * (NB / CW);      // epilogue warps
-#ifndef PF_OZ_CONV
-#define PF_OZ_CONV 6
-#endif
-  static constexpr int CONV = PF_OZ_CONV;        // warps widening the A planes
+  // warps widening the A planes (6, 6 and 6 stages measured fastest at
+  // n = 4096: 4 warps with 4 + 12 or 4 + 8 stages, and 2 warps, were slower)
+  static constexpr int CONV = 6;
   static constexpr int THREADS = 64 + 32 * EPI + 32 * CONV;
   static constexpr int LEVEL_COLS = kOzSlices * NB;
   static constexpr int NBUF = 2;
   static constexpr uint32_t TMEM_COLS = NBUF * LEVEL_COLS <= 256 ? 256u : 512u;
-#ifndef PF_OZ_SA
-#define PF_OZ_SA 6
-#endif
-#ifndef PF_OZ_SS
-#define PF_OZ_SS 6
-#endif
-  static constexpr int SA = PF_OZ_SA;            // A operand stages (fp16, 16 KB)
-  static constexpr int SS = PF_OZ_SS;            // A byte-plane stages (8 KB)
+  static constexpr int SA = 6;                   // A operand stages (fp16, 16 KB)
+  static constexpr int SS = 6;                   // A byte-plane stages (8 KB)
   static constexpr int B_BYTES = kOzSlices * NB * 128;
   static constexpr int MAXRUN = 256 / NB;        // X planes per MMA (N <= 256)
   static constexpr size_t SMEM = 1024 + (size_t)SA * OZ_A_BYTES + (size_t)OZ_SB * B_BYTES +
@@ -195,10 +188,6 @@ __device__ __forceinline__ void oz_digit_bits(long long v, uint32_t *f) {
   f[0] = __float_as_uint(__uint_as_float(kM + (hi >> 16)) - kB);
 }
 
-// Two digit patterns of oz_digit_bits as one word of bf16: lo in the low half
-__device__ __forceinline__ uint32_t oz_pack2(uint32_t lo, uint32_t hi) {
-  return __byte_perm(lo, hi, 0x7632);
-}
 __device__ __forceinline__ __nv_bfloat16 oz_bf16_of(uint32_t f) {
   return __ushort_as_bfloat16((unsigned short)(f >> 16));
 }
@@ -273,11 +262,6 @@ __device__ __forceinline__ void ld_v4_f64(const double *p, double *v) {
       : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
       : "l"(p)
       : "memory");
-}
-__device__ __forceinline__ void st_v8_b32(void *p, const uint32_t *a, const uint32_t *b) {
-  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a[0]),
-               "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3])
-               : "memory");
 }
 __device__ __forceinline__ void st_v4_b32(void *p, uint32_t a, uint32_t b, uint32_t c,
                                           uint32_t d) {
