@@ -4,14 +4,18 @@ One step = one whole solve of the workload through the hot path (interval,
 Chebyshev filter, CholQR2, Rayleigh-Ritz, prox/DRS update, KKT report) from a
 fresh initial state, run until the relative KKT residual is <= 1e-4 (checked
 every 10 iterations; a cap of ``max_iters`` iterations bounds it).  Default
-workload ``maxcut_n4096``: the max-cut SDP of an Erdos-Renyi graph (n = 4096,
-edge probability 0.01, weights +-1) solved by PFAM with a dense FP64
-iteration matrix, p = 32, degree 4.
+workload ``completion_n50000``, the largest configuration of the metric on
+one GPU: PSD matrix completion by PFPG, n = 50000, rank-20 ground truth, 1%
+symmetric uniform sampling (about 25M entries), p = 40, degree 4, the
+iteration matrix applied as low-rank + sparse.  ``--workload maxcut_n4096``
+is the max-cut SDP of an Erdos-Renyi graph (n = 4096, edge probability
+0.01, weights +-1) solved by PFAM with a dense FP64 iteration matrix, p = 32,
+degree 4.
 
 Metric: solves/s at KKT 1e-4 (whole job), with p50/p99 solve latency; the
-filter's dense product is reported against its roofline (the metric's
-"filter GB/s vs roofline"), and the device time of every phase of the step
-is measured with CUDA events over one traced solve.
+filter's product is reported against its roofline (the metric's "filter
+GB/s vs roofline", on the method's bytes), and the device time of every
+phase of the step is measured with CUDA events over one traced solve.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -40,7 +44,7 @@ import numpy as np  # noqa: E402
 
 import pf_synthetic as syn  # noqa: E402
 
-WORKLOAD = "maxcut_n4096"
+WORKLOAD = "completion_n50000"
 TOL = 1e-4
 CHECK_EVERY = 10
 FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 nominal (no measured FP64 peak is provided)
@@ -56,7 +60,7 @@ NCU_TRAFFIC_BYTES = {
 # Iterations the default workload's solve takes to reach KKT 1e-4 on the GPU;
 # the oracle follows the same trajectory (parity of every iteration), so the
 # reference arm scales its sampled iterations to this count.
-ITERS_TO_TOL = {"maxcut_n4096": 2740}
+ITERS_TO_TOL = {"maxcut_n4096": 2740, "completion_n50000": 750}
 SLICED_NOTE = ("7 int8 digit planes of Z (bytes in HBM, widened to fp16 in shared memory) and 7 "
                "fp16 planes of X on tcgen05 (TMA, TMEM), level sums exact in fp32, "
                "int64 fold, FP64 recurrence epilogue: an FP64-accurate product")
@@ -229,7 +233,8 @@ class WorkloadSpec:
     def sample_iters(self):
         return min(self.iters, {"maxcut_n4096": 15, "maxcut_n4096_structured": 15,
                                 "completion_n400": 100, "nce_n4000": 10,
-                                "svt_n5000": 20, "nnls_n10000": 15}.get(self.name, 1))
+                                "svt_n5000": 20, "nnls_n10000": 15,
+                                "completion_n50000": 2}.get(self.name, 1))
 
     def config(self):
         c = self.cfg
@@ -320,6 +325,14 @@ def run_reference(args):
     return 0
 
 
+def sparse_bytes(nnz, n, p, r):
+    """The method's bytes of one low-rank + sparse application (the CSR
+    product of the completion / SVT / NNLS operators): each entry's column
+    index and FP32-sized value (8 B), the row pointers, the n x r factor and
+    the n x p block read in FP64, the n x p result written in FP64."""
+    return 8.0 * nnz + 4.0 * (n + 1) + 8.0 * n * (r + p) + 8.0 * n * p
+
+
 class Workload(WorkloadSpec):
     """Device side of a configuration: problem buffers and the dominant
     kernel's operator."""
@@ -396,14 +409,15 @@ class Workload(WorkloadSpec):
             op = S.lowrank_sparse_operator(n, pr.fac[:, :2 * p], ones, self.rp, self.ci, pr.S,
                                            -1.0, 0.0)
             nnz = self.ci.numel()
-            return (op, "k_lrsp_apply (G X: CSR SpMM + rank-2p low-rank, FP64) + k_gram", "alu",
-                    2.0 * nnz * p + 8.0 * n * p * p, "TFLOP/s")
+            return (op, "k_split_pairs4 + k_lrsp_apply (G X: CSR SpMM + rank-2p low-rank)", "hbm",
+                    sparse_bytes(nnz, n, p, 2 * p), "GB/s")
         if self.kind == "svt":
             # Y X with Y = A*(x): the plain CSR product of the filter and the
             # Ritz step (the transposed product k_svt_spmm does the same work)
             op = S.lowrank_sparse_operator(n, None, None, self.rp, self.ci, pr.S, 1.0, 0.0)
             nnz = self.ci.numel()
-            return (op, "k_lrsp_apply (Y X, CSR SpMM, FP64)", "alu", 2.0 * nnz * p, "TFLOP/s")
+            return (op, "k_split_pairs4 + k_lrsp_apply (Y X, CSR SpMM)", "hbm",
+                    sparse_bytes(nnz, n, p, 0), "GB/s")
         if self.dense_f64() and self.sliced:
             # the method's bytes: the FP64 iteration matrix read once, X and
             # Y_prev read and Y_next written in FP64 (the digit planes the
@@ -424,8 +438,8 @@ class Workload(WorkloadSpec):
             self._keep = (th, Sv)
             op = S.lowrank_sparse_operator(n, pr.V, th, self.rp, self.ci, Sv, 1.0, 0.0)
             nnz = self.ci.numel()
-            return (op, "k_lrsp_apply (structured Z X: CSR SpMM + low-rank, FP64) + k_gram",
-                    "alu", 2.0 * nnz * p + 4.0 * n * p * p, "TFLOP/s")
+            return (op, "k_split_pairs4 + k_lrsp_apply (structured Z X: CSR SpMM + low-rank)",
+                    "hbm", sparse_bytes(nnz, n, p, p), "GB/s")
         if self.kind == "maxcut" and not self.lowprec:
             return (S.dense_operator(pr.Z),
                     "k_gemm_f64_splitk + k_combine (Y = Z X, dense FP64 filter product)",
@@ -441,8 +455,8 @@ class Workload(WorkloadSpec):
         op = S.lowrank_sparse_operator(n, pr.V, th, self.rp, self.ci, pr.S, -self.cfg["t"],
                                        -self.cfg["t"] * self.cfg["mu"])
         nnz = self.ci.numel()
-        return (op, "k_lrsp_apply (fused CSR SpMM + low-rank, FP64) + k_gram", "alu",
-                2.0 * nnz * p + 4.0 * n * p * p, "TFLOP/s")
+        return (op, "k_split_pairs4 + k_lrsp_apply (fused CSR SpMM + low-rank, FP64-accurate "
+                "Dot2 sums on the FP32 pipe)", "hbm", sparse_bytes(nnz, n, p, p), "GB/s")
 
 
 def run_ours(args):

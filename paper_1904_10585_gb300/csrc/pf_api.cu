@@ -955,7 +955,8 @@ pf_status pf_create(const pf_options *opt, int64_t n_max, void *stream, pf_ctx *
   const size_t sizes[] = {np, np, np, np, part, (size_t)kMaxGramBlocks * sq,
                           (size_t)kRedSlots * kMaxRedBlocks * kRedWidth, sq, sq, sq, kMaxP, kMaxP,
                           (size_t)n_max, (size_t)n_max, (size_t)(kLanczos + 2) * n_max,
-                          np /* Xs: n_max x p float pairs, 8 bytes each */};
+                          np + (size_t)n_max /* Xs: n_max x (p rounded up to even)
+                                                float pairs, 8 bytes each */};
   const int nsz = sizeof(sizes) / sizeof(sizes[0]);
   for (int i = 0; i < nsz; ++i) {
     off[i] = tot;

@@ -107,7 +107,7 @@ struct Workspace {
   double *Y[2];           // filter recurrence buffers, n_max x p
   double *W;              // op(Q), n_max x p
   double *Vprev;          // previous Ritz vectors (completion), n_max x p
-  float2 *Xs;             // the sparse product's input block as float pairs, n_max x p
+  float2 *Xs;             // a block as float pairs, n_max x (p rounded up to even)
   double *part;           // split-K partials, kMaxSplitK x n_max x p
   double *gpart;          // Gram partials, kMaxGramBlocks x p x p
   double *red;            // reduction partials, kRedSlots x kMaxRedBlocks x kRedWidth
@@ -428,6 +428,77 @@ __device__ __forceinline__ void df_fma(float s1, float s2, float x1, float x2, f
   const float te = __fadd_rn(__fsub_rn(a1, __fsub_rn(t, bp)), __fsub_rn(pp, bp));
   a1 = t;
   a2 = __fadd_rn(a2, __fadd_rn(te, q));
+}
+
+// a b for pairs whose product does not cancel: |error terms| << |a.h b.h|
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float ph = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -ph);
+  e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+  const float h = __fadd_rn(ph, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, ph)));
+}
+
+// Two pairs at once on the packed FP32 instructions of sm_100 and later
+// (add/sub/mul/fma .f32x2: one instruction, two lanes).  A packed register
+// holds lane 0 in its low half.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(f2x r, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// (a1, a2) += (v1 + v2)(x1 + x2) on two lanes of packed pairs: the Dot2
+// step of df_fma (the same operations and roundings per lane), with the
+// leading product's negative nv1 x1 formed first so that the product error
+// comes out of one FMA.  v1, nv1 = -v1 and v2 are given packed.
+__device__ __forceinline__ void df_fma2(f2x v1, f2x nv1, f2x v2, f2x x1, f2x x2, f2x &a1,
+                                        f2x &a2) {
+  const f2x ppn = mul2(nv1, x1);                    // -(v1 x1) rounded
+  const f2x pe = fma2(v1, x1, ppn);                 // the product's error, exact
+  const f2x q = fma2(v1, x2, fma2(v2, x1, pe));
+  const f2x t = sub2(a1, ppn);                      // a1 + p
+  const f2x bp = sub2(t, a1);
+  const f2x te = sub2(sub2(a1, sub2(t, bp)), add2(ppn, bp));
+  a1 = t;
+  a2 = add2(a2, add2(te, q));
+}
+// (a1, a2) += (b1, b2) on two lanes of packed pairs (TwoSum of the leading
+// parts, the low parts added to its error)
+__device__ __forceinline__ void df_add2(f2x b1, f2x b2, f2x &a1, f2x &a2) {
+  const f2x t = add2(a1, b1);
+  const f2x bp = sub2(t, a1);
+  const f2x te = add2(sub2(a1, sub2(t, bp)), sub2(b1, bp));
+  a1 = t;
+  a2 = add2(a2, add2(te, b2));
+}
+__device__ __forceinline__ f2x shfl_xor2(f2x v, int off) {
+  float a, b;
+  upk2(v, a, b);
+  return pk2(__shfl_xor_sync(0xffffffffu, a, off), __shfl_xor_sync(0xffffffffu, b, off));
 }
 
 __device__ __forceinline__ double block_reduce(double v, double *sh, int op) {

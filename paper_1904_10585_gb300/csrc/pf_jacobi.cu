@@ -64,38 +64,6 @@ __device__ __forceinline__ float2 df_lin(float2 al, float2 x, float2 be, float2 
   return make_float2(h, __fsub_rn(lo, __fsub_rn(h, sh)));
 }
 
-// Two pairs at once on the packed FP32 instructions of sm_100 and later
-// (add/sub/mul/fma .f32x2: one instruction, two lanes).  A packed register
-// holds lane 0 in its low half.
-typedef unsigned long long f2x;
-__device__ __forceinline__ f2x pk2(float a, float b) {
-  f2x r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void upk2(f2x r, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ f2x add2(f2x a, f2x b) {
-  f2x r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
-  f2x r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
-  f2x r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
-  f2x r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
 struct dpair {  // two pairs: lane e is h_e + l_e
   f2x h, l;
 };
@@ -132,15 +100,6 @@ __device__ __forceinline__ dpair df_lin2(const dcoef &c, dpair x, dpair y) {
 }
 
 __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
-// a b for pairs whose product does not cancel: |error terms| << |a.h b.h|
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-  const float ph = __fmul_rn(a.x, b.x);
-  float e = __fmaf_rn(a.x, b.x, -ph);
-  e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
-  const float h = __fadd_rn(ph, e);
-  return make_float2(h, __fsub_rn(e, __fsub_rn(h, ph)));
-}
-
 // The rotation of the pair (k, l) as pairs (c, s): the half-angle tangent
 // u = tan(theta / 2) = t / (1 + sqrt(1 + t^2)), t = tan(theta) the smaller
 // root of t^2 + 2 tau t - 1 = 0 with tau = (h_ll - h_kk) / (2 h_kl), from the

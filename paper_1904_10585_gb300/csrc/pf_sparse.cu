@@ -17,12 +17,11 @@ constexpr int WPB = NT / 32;  // warps per block
 // Low-rank + sparse operator with the Chebyshev epilogue:
 //   op(X)_i = sum_l Uf_il T_l. + sscale * sum_e S_e X_{col_e} + shift X_i
 //   Ynext   = alpha (op(X) - c X) - beta Yprev   (mode as in the dense path)
-// One warp per row.  The warp splits into NQ = 32 / LW lane groups that take
-// every NQ-th entry of the row (and every NQ-th term of the low-rank sum);
-// lane h of a group covers columns h, h + LW, ... (JG groups of LW).  LW = 16
-// or 8 is chosen so that LW * JG is p or just above it (p = 40: 8 lanes x 5),
-// which keeps the FP64 lanes busy.  The groups are combined by shuffles in a
-// fixed order.
+// Both sums run in double-float on the FP32 pipe (GB300 runs FP64 at 1/64 of
+// FP32): operands as float pairs, products accumulated by the Dot2 scheme
+// of Ogita, Rump and Oishi (TwoProduct of the leading parts, TwoSum of the
+// running sum, product errors and first-order terms in the low part; about
+// 2^-47 relative), two columns per packed .f32x2 instruction.
 // ---------------------------------------------------------------------------
 // The block X (n x p, ldx) as float pairs (df_split), row-major with ld p.
 __global__ void k_split_pairs(const double *__restrict__ X, int64_t ldx, int n, int p,
@@ -35,90 +34,128 @@ __global__ void k_split_pairs(const double *__restrict__ X, int64_t ldx, int n, 
   }
 }
 
-template <int LW, int JG>
+// The block X as column pairs of float pairs: row i holds pc = ceil(p / 2)
+// 16-byte groups, group c = (hi(2c), hi(2c + 1), lo(2c), lo(2c + 1)) (zero
+// past column p - 1), so that one 16-byte load gives a packed operand pair.
+__global__ void k_split_pairs4(const double *__restrict__ X, int64_t ldx, int n, int p,
+                               float4 *__restrict__ Xs4) {
+  const int pc = (p + 1) >> 1;
+  const int64_t total = (int64_t)n * pc;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / pc;
+    const int c = (int)(idx - i * pc);
+    const float2 u = df_split(X[i * ldx + 2 * c]);
+    const float2 v = 2 * c + 1 < p ? df_split(X[i * ldx + 2 * c + 1]) : make_float2(0.f, 0.f);
+    Xs4[idx] = make_float4(u.x, v.x, u.y, v.y);
+  }
+}
+
+// One warp per row, in eight groups of four lanes: lane h of a group covers
+// the column pairs c = h, h + 4, ... (JG of them: p <= 8 JG).  Group q takes
+// the row's entries q, q + 8, ... (each value split into a pair and scaled
+// by sscale as a pair, the gathered row of X as stored column pairs, 16
+// bytes per load) and the low-rank terms l = q, q + 8, ... (U_il split, T as
+// column pairs in shared memory).  The eight groups' sums combine by a fixed
+// xor tree of pair additions, and group q then finishes column pair q + 8k
+// of its lanes in FP64 (widening, shift, recurrence, store).
+template <int JG>
 __global__ void __launch_bounds__(NT) k_lrsp_apply(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const double *__restrict__ svals, int n, int p, const double *__restrict__ Uf, int64_t lduf,
     int r, const double *__restrict__ T, double sscale, double shift, const double *X, int64_t ldx,
     const double *Yprev, int64_t ldp, double *Ynext, int64_t ldn, const Params *__restrict__ prm,
     int mode, const int32_t *__restrict__ perm, const double *Xr, int64_t ldr,
-    const float2 *__restrict__ Xs) {
-  constexpr int NQ = 32 / LW;
-  __shared__ double Ts[kMaxP * kMaxP];
-  for (int idx = threadIdx.x; idx < r * p; idx += NT) Ts[idx] = T[idx];
+    const float4 *__restrict__ Xs4) {
+  const int pc = (p + 1) >> 1;  // column pairs
+  __shared__ float4 Ts[kMaxP * kMaxP / 2];  // T (r x p) as column pairs, r pc groups
+  for (int idx = threadIdx.x; idx < r * pc; idx += NT) {
+    const int l = idx / pc, c = idx - l * pc;
+    const float2 u = df_split(T[l * p + 2 * c]);
+    const float2 v = 2 * c + 1 < p ? df_split(T[l * p + 2 * c + 1]) : make_float2(0.f, 0.f);
+    Ts[idx] = make_float4(u.x, v.x, u.y, v.y);
+  }
   __syncthreads();
   double c = 0.0, alpha = 1.0;
   if (mode != MODE_PLAIN) {
     c = prm->c;
     alpha = (mode == MODE_FIRST ? 1.0 : 2.0) / prm->e;
   }
-  const int lane = threadIdx.x & 31, gq = lane / LW, gl = lane % LW;
+  const float2 ss = df_split(sscale);
+  const int lane = threadIdx.x & 31, gq = lane >> 2, h = lane & 3;
   const int warps = gridDim.x * WPB;
+  const double *Xb = Xr != nullptr ? Xr : X;  // the block of the shift and recurrence terms
+  const int64_t ldb = Xr != nullptr ? ldr : ldx;
   for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
-    double acc[JG], lr[JG];
+    f2x a1[JG], a2[JG];
 #pragma unroll
-    for (int g = 0; g < JG; ++g) acc[g] = lr[g] = 0.0;
+    for (int g = 0; g < JG; ++g) a1[g] = a2[g] = 0ull;
     if (svals != nullptr) {
-      // the sparse sum on the FP32 pipe: entry values and the block (Xs, the
-      // pairs of X) as float pairs, accumulated by the Dot2 scheme
-      float a1[JG], a2[JG];
-#pragma unroll
-      for (int g = 0; g < JG; ++g) a1[g] = a2[g] = 0.0f;
       const int e0 = rowptr[row], e1 = rowptr[row + 1];
       for (int base = e0; base < e1; base += 32) {
         const int my = base + lane;
         const int mcol = my < e1 ? colind[my] : 0;
-        const float2 mv = df_split(my < e1 ? svals[perm != nullptr ? perm[my] : my] : 0.0);
+        const float2 mv = df_mul(df_split(my < e1 ? svals[perm != nullptr ? perm[my] : my] : 0.0),
+                                 ss);
         const int cnt = min(32, e1 - base);
-        for (int k = 0; k < cnt; k += NQ) {
-          // group q takes entries q, q + NQ, ...; past the chunk's end
-          // (kk >= cnt, always < 32 here) the source lane holds col 0, value 0
+        for (int k = 0; k < cnt; k += 8) {
+          // group q takes entries k + q; past the chunk's end (kk >= cnt,
+          // always < 32 here) the source lane holds col 0, value 0
           const int kk = k + gq;
           const int col = __shfl_sync(0xffffffffu, mcol, kk);
           const float v1 = __shfl_sync(0xffffffffu, mv.x, kk);
           const float v2 = __shfl_sync(0xffffffffu, mv.y, kk);
-          const float2 *xr = Xs + (int64_t)col * p;
+          const f2x V1 = pk2(v1, v1), NV1 = pk2(-v1, -v1), V2 = pk2(v2, v2);
+          const float4 *xr = Xs4 + (int64_t)col * pc;
 #pragma unroll
           for (int g = 0; g < JG; ++g) {
-            const int j = gl + LW * g;
-            if (j < p) {
-              const float2 x = xr[j];
-              df_fma(v1, v2, x.x, x.y, a1[g], a2[g]);
+            const int cp = h + 4 * g;
+            if (cp < pc) {
+              const float4 x = xr[cp];
+              df_fma2(V1, NV1, V2, pk2(x.x, x.y), pk2(x.z, x.w), a1[g], a2[g]);
             }
           }
         }
       }
-#pragma unroll
-      for (int g = 0; g < JG; ++g) acc[g] = df_widen(a1[g]) + df_widen(a2[g]);
     }
-    // the block of the shift and recurrence terms (the input unless given)
-    const double *Xb = Xr != nullptr ? Xr : X;
-    const int64_t ldb = Xr != nullptr ? ldr : ldx;
-    // low-rank part, terms l = gq, gq + NQ, ...
-    const double *ur = Uf + (int64_t)row * lduf;
-    for (int l = gq; l < r; l += NQ) {
-      const double u = ur[l];
+    if (r > 0) {
+      const double *ur = Uf + (int64_t)row * lduf;
+      for (int l = gq; l < r; l += 8) {
+        const float2 u = df_split(ur[l]);
+        const f2x U1 = pk2(u.x, u.x), NU1 = pk2(-u.x, -u.x), U2 = pk2(u.y, u.y);
+        const float4 *tr = Ts + l * pc;
 #pragma unroll
-      for (int g = 0; g < JG; ++g) {
-        const int j = gl + LW * g;
-        if (j < p) lr[g] = fma(u, Ts[l * p + j], lr[g]);
+        for (int g = 0; g < JG; ++g) {
+          const int cp = h + 4 * g;
+          if (cp < pc) {
+            const float4 x = tr[cp];
+            df_fma2(U1, NU1, U2, pk2(x.x, x.y), pk2(x.z, x.w), a1[g], a2[g]);
+          }
+        }
       }
     }
 #pragma unroll
     for (int g = 0; g < JG; ++g) {
 #pragma unroll
-      for (int off = LW; off < 32; off <<= 1) {
-        acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], off);
-        lr[g] += __shfl_xor_sync(0xffffffffu, lr[g], off);
+      for (int off = 4; off < 32; off <<= 1) {
+        const f2x b1 = shfl_xor2(a1[g], off), b2 = shfl_xor2(a2[g], off);
+        df_add2(b1, b2, a1[g], a2[g]);
       }
     }
-    if (gq == 0) {
 #pragma unroll
-      for (int g = 0; g < JG; ++g) {
-        const int j = gl + LW * g;
-        if (j >= p) continue;
+    for (int g = 0; g < JG; ++g) {
+      const int cp = h + 4 * g;
+      if ((g & 7) != gq || cp >= pc) continue;
+      float s1[2], s2[2];
+      upk2(a1[g], s1[0], s1[1]);
+      upk2(a2[g], s2[0], s2[1]);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int j = 2 * cp + t;
+        if (j >= p) break;
+        const double o0 = df_widen(s1[t]) + df_widen(s2[t]);
         const double xij = Xb[(int64_t)row * ldb + j];
-        const double o = lr[g] + sscale * acc[g] + shift * xij;
+        const double o = fma(shift, xij, o0);
         double y;
         if (mode == MODE_PLAIN) y = o;
         else {
@@ -728,10 +765,10 @@ cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, con
   const int n = op.n, p = ws.p;
   int r = op.r;
   if (op.vals != nullptr) {
-    // the block as float pairs for the sparse sum (rows gathered by column)
-    int64_t nb = ((int64_t)n * p + 255) / 256;
+    // the block as column pairs of float pairs (rows gathered by column)
+    int64_t nb = ((int64_t)n * ((p + 1) / 2) + 255) / 256;
     if (nb > 8 * ws.num_sms) nb = 8 * ws.num_sms;
-    k_split_pairs<<<(int)nb, 256, 0, s>>>(X, ldx, n, p, ws.Xs);
+    k_split_pairs4<<<(int)nb, 256, 0, s>>>(X, ldx, n, p, reinterpret_cast<float4 *>(ws.Xs));
     PF_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -747,21 +784,25 @@ cudaError_t launch_lowrank_sparse_apply(cudaStream_t s, const Workspace &ws, con
   } else {
     r = 0;
   }
+  if (r * ((p + 1) / 2) > kMaxP * kMaxP / 2) return cudaErrorInvalidValue;
   int blocks = (n + WPB - 1) / WPB;
   if (blocks > 8 * ws.num_sms) blocks = 8 * ws.num_sms;
-#define PF_LRSP(LWV, JGV)                                                                     \
-  k_lrsp_apply<LWV, JGV><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf,      \
-                                               op.lduf, r, ws.T, op.sscale, op.shift, X, ldx,  \
-                                               Yprev, ldp, Ynext, ldn, ws.prm, mode, op.perm,  \
-                                               Xr, ldr, ws.Xs)
-  // 8-lane groups where 8 x ceil(p/8) < 16 x ceil(p/16) (p = 24, 40: no idle lanes)
-  if (p <= 8) { PF_LRSP(8, 1); }
-  else if (p <= 16) { PF_LRSP(16, 1); }
-  else if (p <= 24) { PF_LRSP(8, 3); }
-  else if (p <= 32) { PF_LRSP(16, 2); }
-  else if (p <= 40) { PF_LRSP(8, 5); }
-  else if (p <= 48) { PF_LRSP(16, 3); }
-  else { PF_LRSP(16, 4); }
+#define PF_LRSP(JGV)                                                                            \
+  k_lrsp_apply<JGV><<<blocks, NT, 0, s>>>(op.rowptr, op.colind, op.vals, n, p, op.Uf, op.lduf, r, \
+                                          ws.T, op.sscale, op.shift, X, ldx, Yprev, ldp, Ynext,  \
+                                          ldn, ws.prm, mode, op.perm, Xr, ldr,                   \
+                                          reinterpret_cast<const float4 *>(ws.Xs))
+  // JG column pairs per lane, 4 lanes: p <= 8 JG
+  switch ((p + 7) / 8) {
+    case 1: PF_LRSP(1); break;
+    case 2: PF_LRSP(2); break;
+    case 3: PF_LRSP(3); break;
+    case 4: PF_LRSP(4); break;
+    case 5: PF_LRSP(5); break;
+    case 6: PF_LRSP(6); break;
+    case 7: PF_LRSP(7); break;
+    default: PF_LRSP(8); break;
+  }
 #undef PF_LRSP
   PF_LAUNCHED();
   return cudaGetLastError();
