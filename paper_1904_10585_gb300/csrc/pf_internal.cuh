@@ -14,7 +14,7 @@ constexpr int kMaxP = PF_MAX_P;
 constexpr int kRedSlots = 6;        // independent reduction slots per step
 constexpr int kRedWidth = 4;        // doubles per block in a reduction slot
 constexpr int kMaxRedBlocks = 1024; // max blocks of a row reduction
-constexpr int kMaxGramBlocks = 256; // max blocks of a Gram (X^T Y) reduction
+constexpr int kMaxGramBlocks = 1024; // max blocks of a Gram (X^T Y) reduction (several per SM: the Dot2 chains need the warps)
 constexpr int kMaxSplitK = 16;      // max K-splits of the dense FP64 product
 // sliced tensor-core product (pf_oz.cu)
 constexpr int kOzSlices = 7;        // 8-bit digit planes per FP64 operand

@@ -188,7 +188,8 @@ cudaError_t launch_lowrank_sparse_apply32(cudaStream_t s, const Workspace &ws, c
   float *gp = reinterpret_cast<float *>(ws.gpart);
   if (r > 0 && Uf32 != nullptr) {
     int b = (n + 63) / 64;
-    if (b > kMaxGramBlocks) b = kMaxGramBlocks;
+    // at most 256 partials: k_lowrank_coef32 sums them in one sequence per entry
+    if (b > 256) b = 256;
     if (b < 1) b = 1;
     int rpb = (n + b - 1) / b;
     rpb = ((rpb + RC - 1) / RC) * RC;
