@@ -23,14 +23,18 @@ constexpr int WPB = NT / 32;  // warps per block
 // running sum, product errors and first-order terms in the low part; about
 // 2^-47 relative), two columns per packed .f32x2 instruction.
 // ---------------------------------------------------------------------------
-// The block X (n x p, ldx) as float pairs (df_split), row-major with ld p.
+// The block X (n x p, ldx) as float pairs (df_split), row-major with the even
+// row stride pe = p + (p & 1) (a zero pair pads odd p), so that two adjacent
+// elements of a row load as one 16-byte vector.
 __global__ void k_split_pairs(const double *__restrict__ X, int64_t ldx, int n, int p,
                               float2 *__restrict__ Xs) {
-  const int64_t total = (int64_t)n * p;
+  const int pe = p + (p & 1);
+  const int64_t total = (int64_t)n * pe;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / p, j = idx - i * p;
-    Xs[idx] = df_split(X[i * ldx + j]);
+    const int64_t i = idx / pe;
+    const int j = (int)(idx - i * pe);
+    Xs[idx] = j < p ? df_split(X[i * ldx + j]) : make_float2(0.f, 0.f);
   }
 }
 
@@ -578,51 +582,67 @@ __global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ re
 // ---------------------------------------------------------------------------
 // PSD completion: S = P_Omega(X - M) with X = V diag(max(theta,0)) V^T.
 // ---------------------------------------------------------------------------
-// S = P_Omega(X - M) with X = V diag(max(theta, 0)) V^T (one warp per row,
-// a lane per entry), its squared norm, and the Gershgorin row bounds of the
-// step's sparse part -tS - t mu I (Sec. 4.1, reading R4) for the interval.
-// Each entry's r_+-term dot product runs on the FP32 pipe by the Dot2 scheme
-// (the row's W = V theta+ and the pairs Vs of V as float pairs), so does
-// s = x - M (M is exact in fp32) and the |S| row sums; S is stored in FP64.
+// S = P_Omega(X - M) with X = V diag(max(theta, 0)) V^T, its squared norm,
+// and the Gershgorin row bounds of the step's sparse part -tS - t mu I
+// (Sec. 4.1, reading R4) for the interval.  One warp per row, four lanes per
+// entry, eight entries per step: lane h takes the term pairs (2c, 2c + 1),
+// c = h, h + 4, ... (JP of them), the row's W = V theta+ from shared memory
+// and V_col from the stored pairs, 16 bytes per load, in two independent
+// Dot2 chains (even and odd terms) on the FP32 pipe; so do s = x - M (M is
+// exact in fp32) and the |S| row sums.  S is stored in FP64.
+template <int JP>
 __global__ void __launch_bounds__(NT) k_completion_residual(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const float *__restrict__ mvals, int n, int p, const double *__restrict__ V, int64_t ldv,
     const double *__restrict__ theta, const float2 *__restrict__ Vs, double *__restrict__ S,
     double *__restrict__ red, double *__restrict__ red_ivl, const Params *__restrict__ prm) {
-  __shared__ float2 wv[WPB][kMaxP];
+  __shared__ float4 wv[WPB][kMaxP / 2];  // W as term pairs (hi, lo, hi, lo), zero past r_+
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int warps = gridDim.x * WPB;
   int rp = 0;
   for (int l = 0; l < p; ++l) rp += theta[l] > 0.0 ? 1 : 0;
+  const int pe = p + (p & 1), pcr = (rp + 1) >> 1;
   const double t = prm->t, mu = prm->mu;
   float q1 = 0.0f, q2 = 0.0f;  // sum of s^2
   double lo = INFINITY, hi = -INFINITY;
   for (int row = blockIdx.x * WPB + w; row < n; row += warps) {
-    for (int l = lane; l < rp; l += 32) wv[w][l] = df_split(V[(int64_t)row * ldv + l] * theta[l]);
+    for (int c = lane; c < pcr; c += 32) {
+      const int j0 = 2 * c, j1 = 2 * c + 1;
+      const float2 u = df_split(V[(int64_t)row * ldv + j0] * theta[j0]);
+      const float2 v = j1 < rp ? df_split(V[(int64_t)row * ldv + j1] * theta[j1])
+                               : make_float2(0.f, 0.f);
+      wv[w][c] = make_float4(u.x, u.y, v.x, v.y);
+    }
     __syncwarp();
     float o1 = 0.0f, o2 = 0.0f;  // sum of |S_ij|, j != i
     double dg = 0.0;
-    // four lanes per entry (terms l = gl, gl + 4, ...: each row of Vs is read
-    // as contiguous 32-byte pieces), eight entries per step
     const int gq = lane >> 2, gl = lane & 3;
     const int e1 = rowptr[row + 1];
     for (int base = rowptr[row]; base < e1; base += 8) {
       const int e = base + gq;
       const bool valid = e < e1;
       const int col = valid ? colind[e] : 0;
-      const float2 *vc = Vs + (int64_t)col * p;
-      float a1 = 0.0f, a2 = 0.0f;
-      if (valid)
-        for (int l = gl; l < rp; l += 4) {
-          const float2 x = vc[l];
-          df_fma(wv[w][l].x, wv[w][l].y, x.x, x.y, a1, a2);
+      const float4 *vc = reinterpret_cast<const float4 *>(Vs + (int64_t)col * pe);
+      float a1 = 0.0f, a2 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+      if (valid) {
+#pragma unroll
+        for (int k = 0; k < JP; ++k) {
+          const int c = gl + 4 * k;
+          if (c < pcr) {
+            const float4 x = vc[c];
+            const float4 wq = wv[w][c];
+            df_fma(wq.x, wq.y, x.x, x.y, a1, a2);
+            df_fma(wq.z, wq.w, x.z, x.w, b1, b2);
+          }
         }
+      }
+      df_add(b1, b2, a1, a2);
 #pragma unroll
       for (int off = 2; off > 0; off >>= 1) {
-        const float b1 = __shfl_xor_sync(0xffffffffu, a1, off);
-        const float b2 = __shfl_xor_sync(0xffffffffu, a2, off);
-        df_add(b1, b2, a1, a2);
+        const float c1 = __shfl_xor_sync(0xffffffffu, a1, off);
+        const float c2 = __shfl_xor_sync(0xffffffffu, a2, off);
+        df_add(c1, c2, a1, a2);
       }
       if (!valid || gl != 0) continue;
       // s = (a1 + a2) - M by TwoSum of a1 and -M
@@ -983,15 +1003,29 @@ cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, cons
                                        const double *V, int64_t ldv, const double *theta,
                                        double *S) {
   // V as float pairs (the rows the entries gather), then the entries
-  int64_t ns = ((int64_t)n * p + 255) / 256;
+  int64_t ns = ((int64_t)n * (p + (p & 1)) + 255) / 256;
   if (ns > 8 * ws.num_sms) ns = 8 * ws.num_sms;
   k_split_pairs<<<(int)ns, 256, 0, s>>>(V, ldv, n, p, ws.Xs);
   PF_LAUNCHED();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nb = red_blocks(n, ws.num_sms);
-  k_completion_residual<<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, V, ldv, theta, ws.Xs, S,
-                                          slot(ws, SLOT_SDDMM), slot(ws, SLOT_INTERVAL), ws.prm);
+#define PF_RESID(JPV)                                                                         \
+  k_completion_residual<JPV><<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, V, ldv, theta,   \
+                                               ws.Xs, S, slot(ws, SLOT_SDDMM),               \
+                                               slot(ws, SLOT_INTERVAL), ws.prm)
+  // JP term pairs per lane, 4 lanes per entry: p <= 8 JP
+  switch ((p + 7) / 8) {
+    case 1: PF_RESID(1); break;
+    case 2: PF_RESID(2); break;
+    case 3: PF_RESID(3); break;
+    case 4: PF_RESID(4); break;
+    case 5: PF_RESID(5); break;
+    case 6: PF_RESID(6); break;
+    case 7: PF_RESID(7); break;
+    default: PF_RESID(8); break;
+  }
+#undef PF_RESID
   PF_LAUNCHED();
   return cudaGetLastError();
 }
