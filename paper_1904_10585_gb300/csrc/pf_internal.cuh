@@ -367,14 +367,20 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // ---------------------------------------------------------------------------
 // The pair of x, with integer operations for 2^-60 <= |x| < 2^60 (the
 // conversion instructions from FP64 run on the slow FP64 pipe).
+// df_split outside float's comfortable exponent range (|x| < 2^-60 or
+// |x| >= 2^60, and Inf / NaN) by FP64 conversions.  A separate, never-inlined
+// function: inlined, the compiler evaluates this rare branch's FP64 pipe
+// conversions on every call (if-conversion), which on GB300's 1/64-rate FP64
+// pipe costs more than the whole integer split.
+static __device__ __noinline__ float2 df_split_wide(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
 __device__ __forceinline__ float2 df_split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   if ((b << 1) == 0ull) return make_float2(0.0f, 0.0f);  // +-0 (padding, zero entries)
   const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex < 1023 - 60 || ex >= 1023 + 60) {
-    const float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
-  }
+  if (ex < 1023 - 60 || ex >= 1023 + 60) return df_split_wide(x);
   // x = m 2^(ex - 1075), m of 53 bits; x1 keeps the top 24 bits (rounded to
   // nearest, ties to even), x2 = the rest (|rem| <= 2^28), rounded to 24 bits
   const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
@@ -398,15 +404,26 @@ __device__ __forceinline__ float2 df_split(double x) {
   }
   return make_float2(x1, x2);
 }
-// Exact float -> double with integer operations (zero, subnormals and
-// non-finite values by the conversion).
+// Exact float -> double with integer operations only (zero, subnormals,
+// Inf and NaN included: no FP64-pipe conversion, which the compiler would
+// otherwise evaluate on every call).
 __device__ __forceinline__ double df_widen(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned e8 = (u >> 23) & 0xFFu;
-  if (e8 == 0u || e8 == 0xFFu) return (double)f;
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e8 + 896u) << 52) |
-                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  const unsigned e8 = (u >> 23) & 0xFFu, man = u & 0x7FFFFFu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  unsigned long long d;
+  if (e8 == 0xFFu) {
+    d = sgn | (0x7FFull << 52) | ((unsigned long long)man << 29);
+  } else if (e8 != 0u) {
+    d = sgn | ((unsigned long long)(e8 + 896u) << 52) | ((unsigned long long)man << 29);
+  } else if (man == 0u) {
+    d = sgn;
+  } else {
+    // subnormal: man 2^-149 with its leading bit at msb (0..22)
+    const int msb = 31 - __clz(man);
+    d = sgn | ((unsigned long long)(msb + 874) << 52) |
+        (((unsigned long long)man << (52 - msb)) & 0xFFFFFFFFFFFFFull);
+  }
   return __longlong_as_double((long long)d);
 }
 // (a1, a2) += (b1, b2)
