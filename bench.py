@@ -51,11 +51,15 @@ FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 nominal (no measured FP64 peak is pr
 FP64_CUBLAS_MEASURED = 1.09    # torch float64 matmul 16384x16384x64 on this pool (context)
 HBM_PEAK_GBS = 6773.2          # measured STREAM-style copy on the GB300s
 # DRAM bytes (read + written) per launch of the roofline kernel, from an ncu
-# capture of the current kernel (None where no capture of it exists):
-# k_oz_product<32> at n = 4096, p = 32 read 120.02 MB and wrote 3.57 MB
-# (7.4 bytes an entry of the iteration matrix)
+# capture of the current kernel (None where no capture of it exists), keyed
+# by workload and dense-product mode: k_oz_product<32> at n = 4096, p = 32
+# read 120.02 MB and wrote 3.57 MB (7.4 bytes an entry of the iteration
+# matrix); k_lrsp_apply<5> at n = 50000 (25.0M entries, p = 40) read
+# 364.6 MB and wrote 16.0 MB (the FP64 residual values and int32 indices,
+# 12 bytes an entry, and the blocks)
 NCU_TRAFFIC_BYTES = {
-    "maxcut_n4096": 123.58e6,
+    ("maxcut_n4096", "sliced"): 123.58e6,
+    ("completion_n50000", "sliced"): 380.6e6,
 }
 # Iterations the default workload's solve takes to reach KKT 1e-4 on the GPU;
 # the oracle follows the same trajectory (parity of every iteration), so the
@@ -674,7 +678,7 @@ def run_ours(args):
                   "jacobi_sweeps_last": int(last.jacobi_sweeps)},
         "roofline": {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
-                     "traffic": NCU_TRAFFIC_BYTES.get(args.workload),
+                     "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.dense_product)),
                      "work_per_launch": work, "avg_launch_ms": apply_ms, "peak_source": peak_src,
                      "note": ("the metric's filter product; work = the method's algorithmic "
                               "bytes (FP64 iteration matrix and blocks)")},

@@ -105,7 +105,7 @@ typedef struct {
   int32_t adapt_guard;
   int32_t adapt_every;
   /* pf_dense_product of the FP64 dense products.  The sliced product keeps
-   * digit planes of A (7 bf16 copies, 14 bytes per entry of an
+   * digit planes of A (7 byte planes, 7 bytes per entry of an
    * n_max x n_max matrix) in device memory allocated by the context on the
    * first dense call outside a stream capture, and freed by pf_destroy.  */
   int32_t dense_product;

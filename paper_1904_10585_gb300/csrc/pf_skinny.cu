@@ -7,7 +7,7 @@
 //  * the right multiplication Q = Y R^{-1} (orth of Eq. (subspace-update),
 //    realised as CholQR2 = QR with positive diagonal R in exact arithmetic);
 //  * the Ritz rotation V = Q Y with residuals ||A v_i - theta_i v_i|| (Eq. (RR));
-//    the p x p eigensolve itself is the cluster Jacobi of pf_jacobi.cu.
+//    the p x p eigensolve itself is the double-float Jacobi of pf_jacobi.cu.
 #include "pf_internal.cuh"
 
 namespace pf {

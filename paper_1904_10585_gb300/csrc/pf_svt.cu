@@ -8,7 +8,7 @@
 //              Y^T through the transposed pattern), the recurrence fused into
 //              the second;
 //   CholQR2    (shared with the other problems);
-//   Ritz       B = Y Q, B^T B = Wr diag(theta) Wr^T (cluster Jacobi), right
+//   Ritz       B = Y Q, B^T B = Wr diag(theta) Wr^T (Jacobi), right
 //              vectors Q Wr, scaled left vectors L = B Wr (= U_left sigma);
 //   update     w = P_Omega(L diag((sigma - mu)_+ / sigma) (Q Wr)^T),
 //              x <- x + tau (m - w), and the report sums.
