@@ -357,6 +357,10 @@ class Workload(WorkloadSpec):
             self.rp, self.ci, self.cv = S.csr_to_device(self.inst.C, dev, torch.float64)
         else:
             self.rp, self.ci, self.cv = S.csr_to_device(self.inst.omega, dev)
+            # the sampling pattern is symmetric: the residual is formed on its
+            # upper triangle and mirrored through this map
+            self.mir = torch.from_numpy(S.mirror_map(self.inst.omega.rowptr,
+                                                     self.inst.omega.colind)).to(dev)
 
     def inputs(self):
         """Device tensors holding this workload's inputs (copied from the host
@@ -365,6 +369,8 @@ class Workload(WorkloadSpec):
             return [self.G, self.U0]
         if self.kind in ("svt", "nnls"):
             return [self.rp, self.ci, self.cv, self.tr, self.tc, self.tp, self.U0]
+        if self.kind == "completion":
+            return [self.rp, self.ci, self.cv, self.mir, self.U0]
         return [self.rp, self.ci, self.cv, self.U0]
 
     def problem_from(self, tensors):
@@ -374,12 +380,14 @@ class Workload(WorkloadSpec):
             return self.S.svt_problem(*tensors, *self.svt_params())
         if self.kind == "nnls":
             return self.S.nnls_problem(*tensors, mu_bar_rel=self.cfg["mu_bar_rel"])
+        if self.kind == "completion":
+            return self.problem(tensors[0], tensors[1], tensors[2], tensors[4], mirror=tensors[3])
         return self.problem(*tensors)
 
     def precision(self):
         return self.B.PF_PREC_BF16 if self.lowprec == "bf16" else self.B.PF_PREC_FP64
 
-    def problem(self, rp=None, ci=None, cv=None, U0=None):
+    def problem(self, rp=None, ci=None, cv=None, U0=None, mirror=None):
         S = self.S
         if self.kind == "nce":
             return S.nce_problem(self.G, self.U0 if U0 is None else U0,
@@ -399,7 +407,8 @@ class Workload(WorkloadSpec):
             if self.lowprec or self.structured:
                 return S.maxcut_problem(rp, ci, cv, U0, dense=False, lowprec=self.lowprec)
             return S.maxcut_problem(rp, ci, cv, U0)
-        return S.completion_problem(rp, ci, cv, U0, mu=self.cfg["mu"], t=self.cfg["t"])
+        return S.completion_problem(rp, ci, cv, U0, mu=self.cfg["mu"], t=self.cfg["t"],
+                                    mirror=self.mir if mirror is None else mirror)
 
     def kernel_op(self, pr):
         """(operator, description, bound, work per launch, unit) of the dominant kernel."""

@@ -201,6 +201,13 @@ typedef struct {
  *  ||X^{k+1} - X^k||_F / max(1, ||X^{k+1}||_F) once mu has reached mu_bar
  *  (at least 1 before), obj is mu ||X^k||_* + 1/2 ||A(X^k) - b||^2, r_plus
  *  the rank of X^{k+1}, dinf the step's mu.
+ * COMPLETION, optional t_perm (nnz int32, device): for a symmetric sampling
+ *  pattern (j in row i iff i in row j), the index of each entry's transposed
+ *  entry.  The sampled residual S = P_Omega(X - M) is then formed on the
+ *  entries with j >= i only and written to both places (X and M symmetric:
+ *  half the dot products).  pf_problem_init checks the map on the device and
+ *  returns PF_ERR_INVALID_ARG if some entry (i, j) does not map to (j, i).
+ *  NULL forms every entry.
  * t: MAXCUT step; if t <= 0 on entry to pf_problem_init it is set to
  *    10 sqrt(n)/||C||_F.  COMPLETION step (t = 1 matches the Lipschitz
  *    constant of P_Omega).
@@ -226,7 +233,8 @@ typedef struct {
                             maintained by the library under the width rule */
   const double *guard;   /* n x p random columns for width growth (ldg), read only */
   int64_t ldg;
-  const int32_t *t_rowptr; const int32_t *t_colind; const int32_t *t_perm;  /* SVT, NNLS */
+  const int32_t *t_rowptr; const int32_t *t_colind; const int32_t *t_perm;  /* SVT, NNLS;
+                            COMPLETION: t_perm optional, see below */
   double *fac; int64_t ldfac; double *fsv; int32_t rank_cap;                /* NNLS */
   void *Z_tf32; int64_t ldz_tf32;  /* MAXCUT, bf16 context, optional: fp32 shadow for the tf32 rung */
 } pf_problem;

@@ -547,6 +547,8 @@ pf_status check_problem(pf_ctx *ctx, const pf_problem *pr) {
   } else if (pr->kind == PF_PROBLEM_COMPLETION) {
     if (!pr->vals_f32 || !pr->S)
       return set_err(ctx, PF_ERR_INVALID_ARG, "completion needs vals_f32 (M on Omega) and S");
+    if (pr->t_perm != nullptr && (pr->nnz <= 0 || pr->nnz > INT32_MAX))
+      return set_err(ctx, PF_ERR_INVALID_ARG, "completion with a mirror map needs 0 < nnz < 2^31");
     if (!(pr->t > 0.0) || !(pr->mu >= 0.0))
       return set_err(ctx, PF_ERR_INVALID_ARG, "completion needs t > 0 and mu >= 0");
   } else {
@@ -777,7 +779,7 @@ pf_status step_body(pf_ctx *ctx, const pf_problem *pr) {
     phase(ctx, PF_PHASE_UPDATE);  // the sampled residual: the gradient of the prox step
     PF_CUDA(launch_save_prev(s, ws, pr->V, pr->ldv, pr->theta, n, p));
     PF_CUDA(launch_completion_residual(s, ws, pr->rowptr, pr->colind, pr->vals_f32, n, p, ws.Vprev,
-                                       p, ws.thprev, pr->S));
+                                       p, ws.thprev, pr->S, pr->t_perm, pr->nnz));
     // the residual kernel left the Gershgorin row bounds of -tS - t mu I
     phase(ctx, PF_PHASE_INTERVAL);
     PF_CUDA(launch_interval_final(s, ws, n, ws.thprev, p, nullptr, 0));
@@ -1233,6 +1235,18 @@ pf_status pf_problem_init(pf_ctx *ctx, pf_problem *pr) {
       PF_CUDA(launch_maxcut_lp_shadow(s, ws, ctx->opt.precision == PF_PREC_TF32, pr->rowptr,
                                       pr->colind, pr->vals_f64, n, p, pr->V, pr->ldv, pr->theta,
                                       pr->lam, pr->Z_lp, pr->ldz_lp));
+  }
+  if (pr->kind == PF_PROBLEM_COMPLETION && pr->t_perm != nullptr) {
+    // the mirror map must send (i, j) to (j, i): checked once per problem
+    int *bad = reinterpret_cast<int *>(ws.red + (int64_t)SLOT_MISC * kMaxRedBlocks * kRedWidth);
+    PF_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    PF_CUDA(launch_mirror_check(s, ws, pr->rowptr, pr->colind, pr->t_perm, n, pr->nnz, bad));
+    int hbad = 0;
+    PF_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+    if (hbad)
+      return set_err(ctx, PF_ERR_INVALID_ARG,
+                     "t_perm is not the mirror map of a symmetric sampling pattern");
   }
   PF_CUDA(cudaStreamSynchronize(s));
   PF_CUDA(cudaGetLastError());

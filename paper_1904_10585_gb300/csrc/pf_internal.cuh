@@ -245,7 +245,10 @@ cudaError_t launch_oz_expand(cudaStream_t s, const Workspace &ws, const int32_t 
 cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
                                        const int32_t *colind, const float *mvals, int n, int p,
                                        const double *V, int64_t ldv, const double *theta,
-                                       double *S);
+                                       double *S, const int32_t *mirror, int64_t nnz);
+cudaError_t launch_mirror_check(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                const int32_t *colind, const int32_t *mirror, int n, int64_t nnz,
+                                int *bad);
 cudaError_t launch_completion_kkt(cudaStream_t s, const Workspace &ws, const double *V, int64_t ldv,
                                   const double *theta, int n, int p);
 cudaError_t launch_save_prev(cudaStream_t s, const Workspace &ws, const double *V, int64_t ldv,

@@ -579,6 +579,30 @@ __global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ re
   prm->have_prev = 1;
 }
 
+// The first entry of [e0, e1) whose column is >= c (e1 if none), by the
+// whole warp (columns sorted within the row): a 32-way search (lane k tests
+// entry lo + k step) narrows [lo, hi] until at most 31 entries remain, then
+// one ballot over them.
+__device__ __forceinline__ int first_col_at_least(const int32_t *__restrict__ colind, int e0,
+                                                  int e1, int c, int lane) {
+  int lo = e0, hi = e1;  // the answer lies in [lo, hi]
+  while (hi - lo > 31) {
+    const int step = (hi - lo + 31) / 32;  // >= 1
+    const int idx = lo + lane * step;
+    const unsigned m = __ballot_sync(0xffffffffu, idx >= hi || colind[idx] >= c);
+    if (m == 0u) {  // every tested entry is below c
+      lo = lo + 31 * step + 1;
+      continue;
+    }
+    const int f = __ffs(m) - 1;  // tested entry f is >= c (or past the row), f - 1 is not
+    if (f > 0) lo = lo + (f - 1) * step + 1;
+    hi = min(hi, lo + (f > 0 ? step - 1 : 0));
+  }
+  const int idx = lo + lane;  // lane 31 is at or past hi
+  const unsigned m = __ballot_sync(0xffffffffu, idx >= hi || colind[idx] >= c);
+  return lo + (__ffs(m) - 1);
+}
+
 // ---------------------------------------------------------------------------
 // PSD completion: S = P_Omega(X - M) with X = V diag(max(theta,0)) V^T.
 // ---------------------------------------------------------------------------
@@ -590,12 +614,17 @@ __global__ void __launch_bounds__(NT) k_maxcut_kkt(const double *__restrict__ re
 // and V_col from the stored pairs, 16 bytes per load, in two independent
 // Dot2 chains (even and odd terms) on the FP32 pipe; so do s = x - M (M is
 // exact in fp32) and the |S| row sums.  S is stored in FP64.
-template <int JP>
+// SYM (a symmetric pattern with the map mirror[e] of each entry to its
+// transposed entry): only the entries with col >= row are formed, each
+// written to both places (half the dot products; ||S||^2 counts the
+// off-diagonal ones twice), and the row bounds come from k_completion_rowbounds.
+template <int JP, bool SYM>
 __global__ void __launch_bounds__(NT) k_completion_residual(
     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
     const float *__restrict__ mvals, int n, int p, const double *__restrict__ V, int64_t ldv,
     const double *__restrict__ theta, const float2 *__restrict__ Vs, double *__restrict__ S,
-    double *__restrict__ red, double *__restrict__ red_ivl, const Params *__restrict__ prm) {
+    double *__restrict__ red, double *__restrict__ red_ivl, const Params *__restrict__ prm,
+    const int32_t *__restrict__ mirror, int64_t nnz) {
   __shared__ float4 wv[WPB][kMaxP / 2];  // W as term pairs (hi, lo, hi, lo), zero past r_+
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -619,7 +648,8 @@ __global__ void __launch_bounds__(NT) k_completion_residual(
     double dg = 0.0;
     const int gq = lane >> 2, gl = lane & 3;
     const int e1 = rowptr[row + 1];
-    for (int base = rowptr[row]; base < e1; base += 8) {
+    const int ebeg = SYM ? first_col_at_least(colind, rowptr[row], e1, row, lane) : rowptr[row];
+    for (int base = ebeg; base < e1; base += 8) {
       const int e = base + gq;
       const bool valid = e < e1;
       const int col = valid ? colind[e] : 0;
@@ -652,6 +682,16 @@ __global__ void __launch_bounds__(NT) k_completion_residual(
       const float s2 = __fadd_rn(a2, __fadd_rn(__fsub_rn(a1, __fsub_rn(s1, bp)), __fsub_rn(m, bp)));
       const double sv = df_widen(s1) + df_widen(s2);
       S[e] = sv;
+      if constexpr (SYM) {
+        if (col != row) {
+          const int m2 = mirror[e];
+          if ((unsigned long long)m2 < (unsigned long long)nnz) S[m2] = sv;
+          df_fma(2.0f * s1, 2.0f * s2, s1, s2, q1, q2);  // the entry and its mirror
+        } else {
+          df_fma(s1, s2, s1, s2, q1, q2);
+        }
+        continue;
+      }
       df_fma(s1, s2, s1, s2, q1, q2);
       if (col == row) {
         dg += sv;
@@ -666,7 +706,83 @@ __global__ void __launch_bounds__(NT) k_completion_residual(
         o1 = tt;
       }
     }
-    // the row's sums over the warp (pairs by TwoSum, the diagonal is in one lane)
+    if constexpr (!SYM) {
+      // the row's sums over the warp (pairs by TwoSum, the diagonal is in one lane)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float b1 = __shfl_xor_sync(0xffffffffu, o1, off);
+        const float c2 = __shfl_xor_sync(0xffffffffu, o2, off);
+        const float tt = __fadd_rn(o1, b1);
+        const float bb = __fsub_rn(tt, o1);
+        o2 = __fadd_rn(__fadd_rn(o2, c2), __fadd_rn(__fsub_rn(o1, __fsub_rn(tt, bb)), __fsub_rn(b1, bb)));
+        o1 = tt;
+      }
+      const unsigned has = __ballot_sync(0xffffffffu, dg != 0.0);
+      dg = has ? __shfl_sync(0xffffffffu, dg, __ffs(has) - 1) : 0.0;
+      if (lane == 0) {
+        const double d = -t * dg - t * mu, o = t * (df_widen(o1) + df_widen(o2));
+        lo = fmin(lo, d - o);
+        hi = fmax(hi, d + o);
+      }
+    }
+    __syncwarp();
+  }
+  double ssq = df_widen(q1) + df_widen(q2);
+  ssq = block_reduce(ssq, sh, 0);
+  if (!SYM) {
+    lo = block_reduce(lo, sh, 1);
+    hi = block_reduce(hi, sh, 2);
+  }
+  if (threadIdx.x == 0) {
+    red[blockIdx.x * kRedWidth] = ssq;
+    if (!SYM) {
+      red_ivl[blockIdx.x * kRedWidth + 0] = lo;
+      red_ivl[blockIdx.x * kRedWidth + 1] = hi;
+    }
+  }
+}
+
+// The Gershgorin row bounds of -tS - t mu I (Sec. 4.1, reading R4) from the
+// stored S (after the symmetric residual): one warp per row, |S_ij| summed as
+// float pairs (TwoSum), the diagonal in FP64.  Same grid as the residual
+// kernel, so the interval's final reduction reads the same block count.
+__global__ void __launch_bounds__(NT) k_completion_rowbounds(
+    const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
+    const double *__restrict__ S, int n, double *__restrict__ red_ivl,
+    const Params *__restrict__ prm) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * WPB;
+  const double t = prm->t, mu = prm->mu;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int row = blockIdx.x * WPB + (threadIdx.x >> 5); row < n; row += warps) {
+    // four independent pair sums per lane (four loads in flight), combined
+    // in a fixed order
+    float o1 = 0.0f, o2 = 0.0f;
+    float p1[4] = {0.f, 0.f, 0.f, 0.f}, p2[4] = {0.f, 0.f, 0.f, 0.f};
+    double dg = 0.0;
+    const int e1 = rowptr[row + 1];
+    for (int e = rowptr[row] + lane; e < e1; e += 128) {
+      double v[4];
+      int c[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ek = e + 32 * k;
+        v[k] = ek < e1 ? S[ek] : 0.0;
+        c[k] = ek < e1 ? colind[ek] : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (c[k] == row) {
+          dg += v[k];
+        } else {
+          const float2 u = df_split(fabs(v[k]));
+          df_add(u.x, u.y, p1[k], p2[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) df_add(p1[k], p2[k], o1, o2);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       const float b1 = __shfl_xor_sync(0xffffffffu, o1, off);
@@ -683,16 +799,35 @@ __global__ void __launch_bounds__(NT) k_completion_residual(
       lo = fmin(lo, d - o);
       hi = fmax(hi, d + o);
     }
-    __syncwarp();
   }
-  double ssq = df_widen(q1) + df_widen(q2);
-  ssq = block_reduce(ssq, sh, 0);
   lo = block_reduce(lo, sh, 1);
   hi = block_reduce(hi, sh, 2);
   if (threadIdx.x == 0) {
-    red[blockIdx.x * kRedWidth] = ssq;
     red_ivl[blockIdx.x * kRedWidth + 0] = lo;
     red_ivl[blockIdx.x * kRedWidth + 1] = hi;
+  }
+}
+
+// Checks a mirror map of a CSR pattern: entry e = (i, j) must map to an
+// entry of row j whose column is i.  Sets *bad on any violation (or index
+// out of range); one thread per entry, the row of e by binary search.
+__global__ void k_mirror_check(const int32_t *__restrict__ rowptr,
+                               const int32_t *__restrict__ colind,
+                               const int32_t *__restrict__ mirror, int n, int64_t nnz,
+                               int *__restrict__ bad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n - 1;  // the row i with rowptr[i] <= e < rowptr[i + 1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rowptr[mid] <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const int i = lo, j = colind[e];
+    const int m = mirror[e];
+    const bool ok = m >= 0 && (int64_t)m < nnz && j >= 0 && j < n && rowptr[j] <= m &&
+                    m < rowptr[j + 1] && colind[m] == i;
+    if (!ok) atomicOr(bad, 1);
   }
 }
 
@@ -1001,7 +1136,7 @@ cudaError_t launch_maxcut_update(cudaStream_t s, const Workspace &ws, const int3
 cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
                                        const int32_t *colind, const float *mvals, int n, int p,
                                        const double *V, int64_t ldv, const double *theta,
-                                       double *S) {
+                                       double *S, const int32_t *mirror, int64_t nnz) {
   // V as float pairs (the rows the entries gather), then the entries
   int64_t ns = ((int64_t)n * (p + (p & 1)) + 255) / 256;
   if (ns > 8 * ws.num_sms) ns = 8 * ws.num_sms;
@@ -1010,10 +1145,17 @@ cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, cons
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nb = red_blocks(n, ws.num_sms);
-#define PF_RESID(JPV)                                                                         \
-  k_completion_residual<JPV><<<nb, NT, 0, s>>>(rowptr, colind, mvals, n, p, V, ldv, theta,   \
-                                               ws.Xs, S, slot(ws, SLOT_SDDMM),               \
-                                               slot(ws, SLOT_INTERVAL), ws.prm)
+#define PF_RESID(JPV)                                                                          \
+  do {                                                                                         \
+    if (mirror != nullptr)                                                                     \
+      k_completion_residual<JPV, true><<<nb, NT, 0, s>>>(                                      \
+          rowptr, colind, mvals, n, p, V, ldv, theta, ws.Xs, S, slot(ws, SLOT_SDDMM),          \
+          slot(ws, SLOT_INTERVAL), ws.prm, mirror, nnz);                                       \
+    else                                                                                       \
+      k_completion_residual<JPV, false><<<nb, NT, 0, s>>>(                                     \
+          rowptr, colind, mvals, n, p, V, ldv, theta, ws.Xs, S, slot(ws, SLOT_SDDMM),          \
+          slot(ws, SLOT_INTERVAL), ws.prm, nullptr, nnz);                                      \
+  } while (0)
   // JP term pairs per lane, 4 lanes per entry: p <= 8 JP
   switch ((p + 7) / 8) {
     case 1: PF_RESID(1); break;
@@ -1026,6 +1168,21 @@ cudaError_t launch_completion_residual(cudaStream_t s, const Workspace &ws, cons
     default: PF_RESID(8); break;
   }
 #undef PF_RESID
+  PF_LAUNCHED();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || mirror == nullptr) return e;
+  k_completion_rowbounds<<<nb, NT, 0, s>>>(rowptr, colind, S, n, slot(ws, SLOT_INTERVAL), ws.prm);
+  PF_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_check(cudaStream_t s, const Workspace &ws, const int32_t *rowptr,
+                                const int32_t *colind, const int32_t *mirror, int n, int64_t nnz,
+                                int *bad) {
+  int64_t nb = (nnz + 255) / 256;
+  if (nb > 8 * ws.num_sms) nb = 8 * ws.num_sms;
+  if (nb < 1) nb = 1;
+  k_mirror_check<<<(int)nb, 256, 0, s>>>(rowptr, colind, mirror, n, nnz, bad);
   PF_LAUNCHED();
   return cudaGetLastError();
 }

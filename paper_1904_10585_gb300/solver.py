@@ -6,6 +6,7 @@ from __future__ import annotations
 import dataclasses
 from typing import Optional
 
+import numpy as np
 import torch
 
 from . import _binding as B
@@ -144,6 +145,7 @@ class Problem:
     rank_cap: int = 0
     guard: Optional[torch.Tensor] = None   # n x p random columns for width growth
     Z_tf32: Optional[torch.Tensor] = None  # max-cut, bf16 context: fp32 shadow of the tf32 rung
+    mirror: Optional[torch.Tensor] = None  # completion, symmetric pattern: entry -> transposed entry
     p_active: int = 0                      # start width (0: the context's p)
     struct: Optional[B.pf_problem] = None
 
@@ -194,6 +196,8 @@ class Problem:
         else:
             s.vals_f32 = _ptr(self.vals)
             s.S = _ptr(self.S)
+            if self.mirror is not None:
+                s.t_perm = _ptr(self.mirror)
         self.struct = s
         return s
 
@@ -295,16 +299,31 @@ def nnls_problem(rowptr, colind, mvals_f64, t_rowptr, t_colind, t_perm, U0: torc
     return pr
 
 
-def completion_problem(rowptr, colind, mvals_f32, U0: torch.Tensor, mu: float, t: float = 1.0
-                       ) -> Problem:
+def completion_problem(rowptr, colind, mvals_f32, U0: torch.Tensor, mu: float, t: float = 1.0,
+                       mirror: Optional[torch.Tensor] = None) -> Problem:
+    """mirror (optional, int32 device tensor of nnz): for a symmetric sampling
+    pattern, the index of each entry's transposed entry (mirror_map); the
+    library then forms the sampled residual on the upper triangle only."""
     n, p = U0.shape
     dev = U0.device
     pr = Problem(kind=B.PF_PROBLEM_COMPLETION, n=n, rowptr=rowptr, colind=colind, vals=mvals_f32,
                  U=U0.clone(), V=torch.zeros(n, p, dtype=torch.float64, device=dev),
                  theta=torch.zeros(p, dtype=torch.float64, device=dev),
-                 S=torch.empty(colind.numel(), dtype=torch.float64, device=dev), t=t, mu=mu)
+                 S=torch.empty(colind.numel(), dtype=torch.float64, device=dev), t=t, mu=mu,
+                 mirror=mirror)
     pr.make_struct()
     return pr
+
+
+def mirror_map(rowptr: np.ndarray, colind: np.ndarray) -> np.ndarray:
+    """The transposed-entry map of a symmetric CSR pattern (host arrays):
+    entry e = (i, j) -> the index of (j, i).  Entries in (column, row) order
+    are the transposed CSR, which for a symmetric pattern has the same
+    positions, so the k-th of them is the mirror of entry k."""
+    n = len(rowptr) - 1
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    order = np.argsort(colind.astype(np.int64) * n + rows, kind="stable")
+    return order.astype(np.int32)
 
 
 def problem_init(ctx: Context, pr: Problem) -> None:

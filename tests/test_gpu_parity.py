@@ -236,19 +236,24 @@ def test_maxcut_deterministic(pf):
     assert torch.equal(a.Z, b.Z) and torch.equal(a.theta, b.theta)
 
 
-def run_completion_gpu(S, inst, p, d, iters, mu, t=1.0):
+def run_completion_gpu(S, inst, p, d, iters, mu, t=1.0, mirror=False):
     rp, ci, vals = S.csr_to_device(inst.omega, DEV)
+    mir = (torch.from_numpy(S.mirror_map(inst.omega.rowptr, inst.omega.colind)).to(DEV)
+           if mirror else None)
     with S.Context(p=p, n_max=inst.n, degree=d, stream=torch.cuda.Stream()) as ctx:
-        pr = S.completion_problem(rp, ci, vals, t64(inst.U0_raw[:, :p]), mu=mu, t=t)
+        pr = S.completion_problem(rp, ci, vals, t64(inst.U0_raw[:, :p]), mu=mu, t=t, mirror=mir)
         S.problem_init(ctx, pr)
         hist = [S.prox_step(ctx, pr) for _ in range(iters)]
         ctx.stream.synchronize()
         return pr, hist
 
 
+# mirror: the sampled residual formed on the upper triangle of the symmetric
+# pattern and mirrored (with the Gershgorin row bounds from a second pass)
+@pytest.mark.parametrize("mirror", [False, True])
 @pytest.mark.parametrize("n,rank,rate,p,d,iters", [(400, 8, 0.2, 16, 3, 100), (333, 5, 0.1, 40, 4, 30),
-                                                   (90, 2, 0.5, 8, 3, 40)])
-def test_completion_pfpg_parity(pf, n, rank, rate, p, d, iters):
+                                                   (90, 2, 0.5, 8, 3, 40), (1000, 6, 0.06, 33, 3, 12)])
+def test_completion_pfpg_parity(pf, n, rank, rate, p, d, iters, mirror):
     pkg, S = pf
     if n == 400:
         cfg, inst = syn.make_workload("completion_n400")
@@ -256,7 +261,7 @@ def test_completion_pfpg_parity(pf, n, rank, rate, p, d, iters):
         inst = syn.completion_instance(n, rank, rate, p, seed=n)
     mu = 0.05
     st, h_o = o.completion_solve(inst.omega, inst.U0_raw[:, :p], mu, 1.0, d, iters)
-    pr, h_g = run_completion_gpu(S, inst, p, d, iters, mu)
+    pr, h_g = run_completion_gpu(S, inst, p, d, iters, mu, mirror=mirror)
     for k, (a, b) in enumerate(zip(h_g, h_o)):
         assert abs(a.obj - b.obj) <= 1e-9 * max(1.0, abs(b.obj)), (k, a.obj, b.obj)
         assert a.r_plus == b.r_plus
@@ -264,6 +269,29 @@ def test_completion_pfpg_parity(pf, n, rank, rate, p, d, iters):
     Xg = (pr.V.cpu().numpy() * np.maximum(pr.theta.cpu().numpy(), 0)) @ pr.V.cpu().numpy().T
     Xo = (st.V * st.w) @ st.V.T
     np.testing.assert_allclose(Xg, Xo, atol=1e-9 * max(1.0, np.abs(Xo).max()))
+
+
+def test_completion_wrong_mirror_map_is_rejected(pf):
+    """A map that does not send (i, j) to (j, i) fails pf_problem_init (the
+    device check reads in-range indices only)."""
+    import ctypes
+    pkg, S = pf
+    inst = syn.completion_instance(120, 3, 0.3, 8, seed=5)
+    rp, ci, vals = S.csr_to_device(inst.omega, DEV)
+    nnz = ci.numel()
+    good = S.mirror_map(inst.omega.rowptr, inst.omega.colind)
+    for bad in (np.arange(nnz, dtype=np.int32), np.roll(good, 1),
+                np.where(np.arange(nnz) == 7, nnz + 5, good).astype(np.int32)):
+        with S.Context(p=8, n_max=120, degree=3, stream=torch.cuda.Stream()) as ctx:
+            pr = S.completion_problem(rp, ci, vals, t64(inst.U0_raw[:, :8]), mu=0.05,
+                                      mirror=torch.from_numpy(bad).to(DEV))
+            st = pkg.raw_call("pf_problem_init", ctx.handle, ctypes.byref(pr.struct))
+            assert st == pkg.PF_ERR_INVALID_ARG
+    with S.Context(p=8, n_max=120, degree=3, stream=torch.cuda.Stream()) as ctx:
+        pr = S.completion_problem(rp, ci, vals, t64(inst.U0_raw[:, :8]), mu=0.05,
+                                  mirror=torch.from_numpy(good).to(DEV))
+        S.problem_init(ctx, pr)
+        assert S.prox_step(ctx, pr).flags == 0
 
 
 # ---------------------------------------------------------------------------
