@@ -776,8 +776,11 @@ __global__ void __launch_bounds__(NT) k_completion_rowbounds(
         if (c[k] == row) {
           dg += v[k];
         } else {
-          const float2 u = df_split(fabs(v[k]));
-          df_add(u.x, u.y, p1[k], p2[k]);
+          // |v| as a pair: the pair of v with both signs flipped when v < 0
+          // (float sign flips; an FP64 fabs would occupy GB300's FP64 pipe)
+          const float2 u = df_split(v[k]);
+          const float sg = u.x < 0.0f ? -1.0f : 1.0f;
+          df_add(sg * u.x, sg * u.y, p1[k], p2[k]);
         }
       }
     }
