@@ -365,8 +365,9 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005):
 // TwoProduct of the leading parts (exact through an FMA), TwoSum of the
 // running sum (Knuth), and the product errors with the first-order terms
-// x1 y2 + x2 y1 summed in plain fp32.  The result carries a relative error of
-// about 2^-47 of sum |x_k y_k| (an FP64 dot product of m terms: m 2^-53).
+// x1 y2 + x2 y1 summed in plain fp32.  The result is within a few units of
+// m 2^-48 of sum |x_k y_k| for m terms (an FP64 dot product: m 2^-53);
+// tests/test_pair_arithmetic.py checks the bound against exact arithmetic.
 // ---------------------------------------------------------------------------
 // The pair of x, with integer operations for 2^-60 <= |x| < 2^60 (the
 // conversion instructions from FP64 run on the slow FP64 pipe).

@@ -107,8 +107,8 @@ __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a
 // 2^-23: the rotation annihilates h_kl to about 1e-6 of itself, and the
 // sweeps converge quadratically all the same); then c = (1 - u^2) / (1 + u^2)
 // and s = 2u / (1 + u^2) from the exact float u: u^2 exact, the reciprocal
-// refined to about 2^-48 by a Newton step and its FMA residual, so that
-// c^2 + s^2 = 1 to about 2^-47 whatever u is.
+// refined to about 2^-47 by a Newton step and its FMA residual, so that
+// c^2 + s^2 = 1 within a few units of 2^-46 whatever u is.
 __device__ __forceinline__ float rcp_fast(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

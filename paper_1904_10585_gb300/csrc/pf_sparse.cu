@@ -20,8 +20,9 @@ constexpr int WPB = NT / 32;  // warps per block
 // Both sums run in double-float on the FP32 pipe (GB300 runs FP64 at 1/64 of
 // FP32): operands as float pairs, products accumulated by the Dot2 scheme
 // of Ogita, Rump and Oishi (TwoProduct of the leading parts, TwoSum of the
-// running sum, product errors and first-order terms in the low part; about
-// 2^-47 relative), two columns per packed .f32x2 instruction.
+// running sum, product errors and first-order terms in the low part; within
+// a few units of m 2^-48 of sum |x_k y_k| for m terms), two columns per
+// packed .f32x2 instruction.
 // ---------------------------------------------------------------------------
 // The block X (n x p, ldx) as float pairs (df_split), row-major with the even
 // row stride pe = p + (p & 1) (a zero pair pads odd p), so that two adjacent
